@@ -1,0 +1,203 @@
+"""CPU oracle for occupancy-grid marching + packed volume rendering (test infrastructure).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
+baseline / reference arm may import this package. The product path never does.
+The arithmetic lives in ``oracle.c`` (plain C, see its header for the precision
+of each step and the readings of the paper); this module only compiles it and
+marshals numpy arrays through ``ctypes``.
+
+Entry points mirror the paper's two stages (Sec. 2.1 ray marching, Sec. 2.2
+differentiable rendering, Eq. 1) and the occupancy-grid update the paper
+borrows from Instant-NGP (Sec. 2.1, "Pruning Empty and Occluded Regions").
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+# The mutation test points this at a deliberately broken copy of the oracle to
+# show that the pins fail; nothing else sets it.
+_LIB_OVERRIDE = os.environ.get("NACC_ORACLE_LIB_OVERRIDE")
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11"]
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, strict IEEE float32/float64)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if _LIB_OVERRIDE:
+            L = ctypes.CDLL(_LIB_OVERRIDE)
+        else:
+            build()
+            L = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        i32, i64, f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+        L.oracle_march.restype = i64
+        L.oracle_march.argtypes = [P, P, P, P, i32, P, P, i32, i32, P, f32, f32, f32, f32, f32, i32, P, P, P, P, i64]
+        L.oracle_prune.restype = i64
+        L.oracle_prune.argtypes = [P, i32, P, P, P, f32, f32, P, P, P, P, P, P, i64]
+        L.oracle_render_weights.argtypes = [P, i32, P, P, P, P, P]
+        L.oracle_accumulate.argtypes = [P, i32, P, P, i32, P]
+        L.oracle_render_fwd.argtypes = [P, i32, P, P, P, P, P, P, P]
+        L.oracle_render_bwd.argtypes = [P, i32, P, P, P, P, P, P, P, P, P]
+        L.oracle_unpack_info.argtypes = [P, i32, P]
+        L.oracle_update_grid.argtypes = [P, P, i64, P, P, i64, f32, f32]
+        for f in ("oracle_render_weights", "oracle_accumulate", "oracle_render_fwd", "oracle_render_bwd",
+                  "oracle_unpack_info", "oracle_update_grid"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dt):
+    return None if a is None else np.ascontiguousarray(a, dtype=dt)
+
+
+@dataclass
+class Packed:
+    packed_info: np.ndarray  # (R, 2) int32 (offset, count)
+    t_starts: np.ndarray  # (M,) float32
+    t_ends: np.ndarray  # (M,) float32
+    ray_indices: np.ndarray  # (M,) int32
+
+    @property
+    def n_samples(self) -> int:
+        return int(self.t_starts.shape[0])
+
+
+def march(rays_o, rays_d, bits, res, aabb, near_plane=0.0, far_plane=1e10, dt_min=1e-2, dt_max=None,
+          cone=0.0, max_steps=1024, n_levels=1, n_slots=1, ray_time=None, ray_slot=None) -> Packed:
+    """Occupancy-grid ray marching (Sec. 2.1), float32 replica, dense lattice walk."""
+    o = _c(rays_o, np.float32).reshape(-1, 3)
+    d = _c(rays_d, np.float32).reshape(-1, 3)
+    R = o.shape[0]
+    bits = _c(bits, np.uint32)
+    res = np.ascontiguousarray(np.asarray(res, dtype=np.int32).reshape(3))
+    box = np.ascontiguousarray(np.asarray(aabb, dtype=np.float32).reshape(6))
+    tt = _c(ray_time, np.float32)
+    sl = _c(ray_slot, np.int32)
+    dt_max = dt_min if dt_max is None else dt_max
+    pi = np.zeros((R, 2), dtype=np.int32)
+    args = lambda ts, te, ri, cap: (
+        _p(o), _p(d), _p(tt), _p(sl), R, _p(bits), _p(res), n_levels, n_slots, _p(box),
+        near_plane, far_plane, dt_min, dt_max, cone, max_steps, _p(pi), _p(ts), _p(te), _p(ri), cap)
+    n = lib().oracle_march(*args(None, None, None, 0))
+    if n < 0:
+        raise ValueError("oracle_march: invalid arguments")
+    ts = np.empty(n, np.float32)
+    te = np.empty(n, np.float32)
+    ri = np.empty(n, np.int32)
+    n2 = lib().oracle_march(*args(ts, te, ri, n))
+    assert n2 == n
+    return Packed(pi, ts, te, ri)
+
+
+def prune(packed_info, t_starts, t_ends, sigmas, early_stop_eps, alpha_thre):
+    """Early-stop + alpha-threshold pruning and re-packing (Sec. 2.1), float32 decision.
+
+    Returns (Packed, keep_mask (M,) bool, optical_depth (M,) float32 = O_i).
+    """
+    pi = _c(packed_info, np.int32).reshape(-1, 2)
+    ts, te, sg = (_c(a, np.float32).reshape(-1) for a in (t_starts, t_ends, sigmas))
+    R, M = pi.shape[0], ts.shape[0]
+    keep = np.zeros(M, np.uint8)
+    od = np.zeros(M, np.float32)
+    pio = np.zeros((R, 2), np.int32)
+    args = lambda a, b, c, cap: (_p(pi), R, _p(ts), _p(te), _p(sg), early_stop_eps, alpha_thre, _p(keep), _p(od),
+                                 _p(pio), _p(a), _p(b), _p(c), cap)
+    n = lib().oracle_prune(*args(None, None, None, 0))
+    a, b, c = np.empty(n, np.float32), np.empty(n, np.float32), np.empty(n, np.int32)
+    lib().oracle_prune(*args(a, b, c, n))
+    return Packed(pio, a, b, c), keep.astype(bool), od
+
+
+def render_weights(packed_info, t_starts, t_ends, sigmas):
+    """Eq. 1 weights w_i = T_i alpha_i and transmittance T_i (float64)."""
+    pi = _c(packed_info, np.int32).reshape(-1, 2)
+    ts, te, sg = (_c(a, np.float32).reshape(-1) for a in (t_starts, t_ends, sigmas))
+    w = np.zeros(ts.shape[0], np.float64)
+    T = np.zeros(ts.shape[0], np.float64)
+    if lib().oracle_render_weights(_p(pi), pi.shape[0], _p(ts), _p(te), _p(sg), _p(w), _p(T)) != 0:
+        raise MemoryError
+    return w, T
+
+
+def accumulate(packed_info, weights, values=None):
+    """sum_i w_i v_i per ray (Sec. 2.2: any sample attribute); values (M, C) or None (C = 1)."""
+    pi = _c(packed_info, np.int32).reshape(-1, 2)
+    w = _c(weights, np.float64).reshape(-1)
+    if values is None:
+        v, C = None, 1
+    else:
+        v = _c(values, np.float32).reshape(w.shape[0], -1)
+        C = v.shape[1]
+    out = np.zeros((pi.shape[0], C), np.float64)
+    lib().oracle_accumulate(_p(pi), pi.shape[0], _p(w), _p(v), C, _p(out))
+    return out
+
+
+def render_fwd(packed_info, t_starts, t_ends, sigmas, rgbs):
+    """Eq. 1 quadrature: (color (R,3), opacity (R,), depth (R,)), float64."""
+    pi = _c(packed_info, np.int32).reshape(-1, 2)
+    ts, te, sg = (_c(a, np.float32).reshape(-1) for a in (t_starts, t_ends, sigmas))
+    rgb = _c(rgbs, np.float32).reshape(-1, 3)
+    R = pi.shape[0]
+    col, op, dp = np.zeros((R, 3)), np.zeros(R), np.zeros(R)
+    if lib().oracle_render_fwd(_p(pi), R, _p(ts), _p(te), _p(sg), _p(rgb), _p(col), _p(op), _p(dp)) != 0:
+        raise MemoryError
+    return col, op, dp
+
+
+def render_bwd(packed_info, t_starts, t_ends, sigmas, rgbs, g_color=None, g_opacity=None, g_depth=None):
+    """Analytic gradient of the Eq. 1 quadrature: (d_sigmas (M,), d_rgbs (M,3)), float64."""
+    pi = _c(packed_info, np.int32).reshape(-1, 2)
+    ts, te, sg = (_c(a, np.float32).reshape(-1) for a in (t_starts, t_ends, sigmas))
+    rgb = _c(rgbs, np.float32).reshape(-1, 3)
+    R, M = pi.shape[0], ts.shape[0]
+    gc = _c(g_color, np.float64)
+    ga = _c(g_opacity, np.float64)
+    gd = _c(g_depth, np.float64)
+    ds, dr = np.zeros(M), np.zeros((M, 3))
+    if lib().oracle_render_bwd(_p(pi), R, _p(ts), _p(te), _p(sg), _p(rgb), _p(gc), _p(ga), _p(gd), _p(ds), _p(dr)) != 0:
+        raise MemoryError
+    return ds, dr
+
+
+def unpack_info(packed_info, n_samples):
+    pi = _c(packed_info, np.int32).reshape(-1, 2)
+    ri = np.zeros(n_samples, np.int32)
+    lib().oracle_unpack_info(_p(pi), pi.shape[0], _p(ri))
+    return ri
+
+
+def update_grid(ema, cells, sigmas, decay, thre):
+    """Occupancy-grid EMA update (Sec. 2.1, via Instant-NGP App. E.2): returns (ema', bits')."""
+    e = np.array(ema, dtype=np.float32, copy=True).reshape(-1)
+    c = _c(cells, np.int32).reshape(-1)
+    s = _c(sigmas, np.float32).reshape(-1)
+    bits = np.zeros((e.size + 31) // 32, np.uint32)
+    if lib().oracle_update_grid(_p(e), _p(bits), e.size, _p(c), _p(s), c.size, decay, thre) != 0:
+        raise ValueError("cell index out of range")
+    return e, bits

@@ -1,0 +1,56 @@
+"""The oracle's pins have teeth: each plausible mistake below, planted in a copy of
+oracle.c compiled on the CPU, makes at least one pin in test_oracle_march.py or
+test_oracle_render.py fail. (Mistakes are planted only in the oracle, never in the
+CUDA path, and only on the CPU.)
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTANTS = [
+    ("cell index x/z transposed", "+ ix) * res[1];", "+ iz) * res[1];"),
+    ("lookup at interval start, not midpoint", "float mid = (ts + te) * 0.5f;", "float mid = ts;"),
+    ("slab exit taken as max", "if (tmax < t_out) t_out = tmax;", "if (tmax > t_out) t_out = tmax;"),
+    ("lattice end off by one", "tn = near + (float)(k + 1) * dt_min;", "tn = near + (float)(k + 2) * dt_min;"),
+    ("far not clipped", "float te = tn < far ? tn : far;", "float te = tn;"),
+    ("time bin rounded, not floored", "return (int)v;", "return (int)(v + 0.5f);"),
+    ("cascade level scale off by one", "ldexpf(1.0f, l)", "ldexpf(1.0f, l + 1)"),
+    ("cone step not clamped below", "if (dt < dt_min) dt = dt_min;", ""),
+    ("Eq. 1 alpha with the printed (dropped) minus sign", "double ai = 1.0 - exp(-tau);", "double ai = 1.0 - exp(tau);"),
+    ("inclusive transmittance", "double Ti = exp(-o_acc);", "double Ti = exp(-(o_acc + tau));"),
+    ("depth at interval start", "double tmid = ((double)t_starts[off + i] + (double)t_ends[off + i]) * 0.5;",
+     "double tmid = (double)t_starts[off + i];"),
+    ("gradient uses T_k for T_{k+1}", "double dtau = ak * Tn[k] - suffix;", "double dtau = ak * T[k] - suffix;"),
+    ("gradient suffix inclusive", "double dtau = ak * Tn[k] - suffix;", "double dtau = ak * Tn[k] - (suffix + ak * w[k]);"),
+    ("gradient missing delta", "d_sigmas[off + k] = delta * dtau;", "d_sigmas[off + k] = dtau;"),
+    ("gradient drops the depth term", "+ ga + gd * tmid;", "+ ga;"),
+    ("prune on inclusive optical depth", "if (use_t && !(o_acc <= thr_o)) k = 0;",
+     "if (use_t && !(o_acc + tau <= thr_o)) k = 0;"),
+    ("prune alpha on sigma, not sigma*delta", "float tau = sigmas[i] * delta;", "float tau = sigmas[i];"),
+    ("grid decay dropped", "ema[c] = (float)((double)decay * (double)ema[c]);", "ema[c] = ema[c];"),
+    ("grid NaN not ignored", "if (v == v && v > ema[c]) ema[c] = v;", "if (!(v <= ema[c])) ema[c] = v;"),
+]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, "mutation site not found: " + old
+    mutated = src.replace(old, new)
+    cpath = tmp_path / "mutant.c"
+    cpath.write_text(mutated)
+    lib = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11",
+                           "-o", str(lib), str(cpath), "-lm"])
+    env = dict(os.environ, NACC_ORACLE_LIB_OVERRIDE=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(HERE, "test_oracle_march.py"), os.path.join(HERE, "test_oracle_render.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "mutant '%s' survived every pin:\n%s" % (name, r.stdout[-2000:])
