@@ -1,0 +1,263 @@
+/*
+ * nacc.h -- C ABI of the GB300 (sm_103a) occupancy-grid ray marcher and packed
+ * differentiable volume renderer (the method of NerfAcc, arXiv 2210.04847).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every pointer named in a signature is a DEVICE pointer into memory the
+ *   caller owns (cudaMalloc / torch), unless the comment says "host". The
+ *   library never allocates device memory; scratch comes from a caller
+ *   workspace whose size is returned by the matching *_workspace_size() call.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Every call only enqueues work on that stream and returns; nothing
+ *   synchronises the host. Results are valid once the stream reaches them.
+ * - Return value (host): NACC_OK, or a negative NACC_ERR_* for arguments the
+ *   host can reject (null pointer where one is required, negative size,
+ *   unsupported parameter) and for launch failures (NACC_ERR_CUDA). Nothing is
+ *   enqueued when the call fails.
+ * - Device-side conditions (capacity exceeded, a bounded wait that gave up,
+ *   inconsistent packed_info) are OR-ed into `*d_status` (a device int32 the
+ *   caller zeroes; nullable = not reported) as NACC_STATUS_* bits. Kernels
+ *   never trap; on such a condition they skip the offending access and finish.
+ * - Arrays are contiguous, C order. Reals are float32, indices int32.
+ *   "Samples" are packed ray-major: packed_info (n_rays, 2) int32 holds
+ *   (offset, count) of each ray's run in the per-sample arrays
+ *   t_starts (n,), t_ends (n,), ray_indices (n,) -- the layout of the paper's
+ *   API listing (Sec. 3): packed_info, t_starts, t_ends, ray_indices.
+ *   Sample totals must stay below 2^31 (offsets are int32).
+ * - The sample interval of a ray r is [t_start, t_end] along o_r + t d_r;
+ *   rays_d are expected to be unit length (Sec. 3 listing: "normalized
+ *   directions"), but nothing depends on it.
+ */
+#ifndef NACC_H
+#define NACC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NACC_VERSION 100
+
+/* host return codes */
+#define NACC_OK 0
+#define NACC_ERR_INVALID_ARG (-1)
+#define NACC_ERR_CAPACITY (-2)
+#define NACC_ERR_CUDA (-3)
+#define NACC_ERR_TIMEOUT (-4)
+#define NACC_ERR_INTERNAL (-5)
+
+/* device status bits, OR-ed into *d_status */
+#define NACC_STATUS_CAPACITY 0x1    /* more samples than `capacity`; total still reported */
+#define NACC_STATUS_TIMEOUT 0x2     /* a bounded inter-block wait gave up; outputs invalid */
+#define NACC_STATUS_BAD_PACKED 0x4  /* a packed_info run lies outside [0, n_samples) */
+#define NACC_STATUS_BAD_INDEX 0x8   /* a grid slot or cell index out of range (skipped) */
+#define NACC_STATUS_OVERFLOW 0x10   /* a sample total reached 2^31 (int32 offsets) */
+
+#define NACC_MAX_LEVELS 16
+
+/*
+ * Binary occupancy grid (Sec. 2.1, "Pruning Empty and Occluded Regions"; the
+ * multi-level form follows the cascaded grids the paper's footnote cites for
+ * large scenes). One bit per cell, packed into uint32 words over the flat cell
+ * index
+ *     cell = ((slot * n_levels + level) * res[0] + ix) * res[1] + iy) * res[2] + iz
+ * (bit cell & 31 of word cell >> 5). Level 0 covers aabb = (lo xyz, hi xyz);
+ * level l >= 1 covers the level-0 box scaled by 2^l about its centre. A slot is
+ * an independent grid: a time bin of a dynamic scene, or a scene of a batch.
+ */
+typedef struct nacc_grid {
+    const uint32_t* bits; /* device, ceil(n_slots*n_levels*res0*res1*res2 / 32) words */
+    int32_t res[3];
+    int32_t n_levels; /* 1 .. NACC_MAX_LEVELS */
+    int32_t n_slots;  /* >= 1 */
+    float aabb[6];
+} nacc_grid;
+
+/*
+ * Marching parameters (Sec. 3 listing: near_plane, far_plane; the step rule is
+ * the paper's dense 1024-sample lattice of Sec. 4.1 generalised to
+ * cone-growing steps). cone == 0: uniform steps t_k = near + k * dt_min.
+ * cone > 0: t_{k+1} = t_k + clamp(t_k * cone, dt_min, dt_max).
+ */
+typedef struct nacc_march_params {
+    float near_plane;
+    float far_plane;
+    float dt_min;
+    float dt_max;
+    float cone;
+    int32_t max_steps; /* 1 .. 32768 lattice intervals per ray */
+} nacc_march_params;
+
+/* ------------------------------------------------------------------------- */
+/* Ray marching (Sec. 2.1 "Ray Marching", "GPU Memory Efficiency")           */
+/* ------------------------------------------------------------------------- */
+
+/* Bytes of device workspace nacc_march_rays needs for n_rays rays. */
+size_t nacc_march_workspace_size(int32_t n_rays, const nacc_march_params* params);
+
+/*
+ * Occupancy-grid ray marching with empty-space skipping, pruned while
+ * marching (Sec. 2.1: samples are produced only in non-empty space, so memory
+ * is never over-allocated). For every ray r (input order):
+ *   1. clip o_r + t d_r against the outermost level box (slab test, float32),
+ *      near = max(t_in, near_plane), far = min(t_out, far_plane); a ray that
+ *      misses, has near >= far, or holds a non-finite component gets none;
+ *   2. walk the lattice intervals [t_k, min(t_{k+1}, far)], t_k < far,
+ *      k < max_steps;
+ *   3. emit interval k iff the grid bit of the cell holding its midpoint
+ *      o + d (t_s + t_e)/2 is set, looking up the finest level whose box holds
+ *      the midpoint, in the grid slot of the ray.
+ * Every floating-point step is a separately rounded IEEE float32 operation
+ * (no contraction), so results are bit-reproducible.
+ *
+ * rays_o, rays_d   (n_rays, 3) float32.
+ * ray_time         (n_rays,) float32 or NULL: slot = clamp(floor(time*n_slots), 0, n_slots-1).
+ * ray_slot         (n_rays,) int32 or NULL: explicit slot (wins over ray_time);
+ *                  with both NULL every ray uses slot 0. Out-of-range slots emit
+ *                  nothing and raise NACC_STATUS_BAD_INDEX.
+ * grid, params     host structs (read during the call only).
+ * packed_info      (n_rays, 2) int32 out: (offset, count), offsets ray-major.
+ * t_starts, t_ends (capacity,) float32 out; ray_indices (capacity,) int32 out.
+ *                  Samples beyond `capacity` are not written.
+ * n_samples        device int64 out: the total number of samples (also when it
+ *                  exceeds capacity; then NACC_STATUS_CAPACITY is raised).
+ * workspace        nacc_march_workspace_size() bytes, 256-byte aligned; the
+ *                  call clears what it needs on `stream`.
+ * Errors: NACC_ERR_INVALID_ARG for null required pointers, n_rays < 0,
+ * capacity < 0, n_levels or max_steps out of range, res <= 0, a workspace too
+ * small; NACC_ERR_CUDA if a launch fails.
+ */
+int nacc_march_rays(const float* rays_o, const float* rays_d, const float* ray_time,
+                    const int32_t* ray_slot, int32_t n_rays, const nacc_grid* grid,
+                    const nacc_march_params* params, int32_t* packed_info, float* t_starts,
+                    float* t_ends, int32_t* ray_indices, int64_t capacity, int64_t* n_samples,
+                    int32_t* d_status, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Pruning by transmittance and opacity (Sec. 2.1 "Pruning Empty and         */
+/* Occluded Regions"; arguments early_stop_eps, alpha_thre of Sec. 3)        */
+/* ------------------------------------------------------------------------- */
+
+size_t nacc_prune_workspace_size(int32_t n_rays, int64_t n_samples);
+
+/*
+ * Keeps sample i of a ray iff T_i >= early_stop_eps and alpha_i >= alpha_thre,
+ * with tau_i = sigma_i (t_end,i - t_start,i), T_i = exp(-sum_{j<i} tau_j) over
+ * ALL input samples of the ray, alpha_i = 1 - exp(-tau_i) (Eq. 1), and writes
+ * the kept samples re-packed (ray-major, order preserved). The decision is
+ * taken in float32 as O_i <= -ln(eps) and tau_i >= -ln(1 - thre), both
+ * thresholds rounded once to float32; eps <= 0 (thre <= 0) switches that test
+ * off. sigmas must be >= 0 (the density of the user's field, queried without
+ * gradient per Sec. 2.1); once a ray's optical depth passes -ln(eps) the rest
+ * of the ray is not read.
+ *
+ * packed_info (n_rays,2), t_starts, t_ends, sigmas (n_samples,): input samples.
+ * packed_info_out (n_rays, 2); t_starts_out, t_ends_out, ray_indices_out
+ *   (capacity,): output; n_kept: device int64 out (total, also past capacity).
+ * keep_mask (n_samples,) uint8 or NULL: 1 where kept.
+ * workspace        nacc_prune_workspace_size() bytes, 256-byte aligned. After
+ *                  the call, the uint64 at byte offset 8 of the workspace holds
+ *                  the number of input samples the pass read (samples past a
+ *                  ray's termination point are not read).
+ */
+int nacc_prune_samples(const int32_t* packed_info, int32_t n_rays, const float* t_starts,
+                       const float* t_ends, const float* sigmas, int64_t n_samples,
+                       float early_stop_eps, float alpha_thre, int32_t* packed_info_out,
+                       float* t_starts_out, float* t_ends_out, int32_t* ray_indices_out,
+                       int64_t capacity, int64_t* n_kept, uint8_t* keep_mask, int32_t* d_status,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Differentiable rendering (Sec. 2.2, Eq. 1)                                */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Per-sample weights of Eq. 1: w_i = T_i alpha_i with T_i = exp(-sum_{j<i}
+ * sigma_j delta_j), alpha_i = 1 - exp(-sigma_i delta_i), delta_i = t_end -
+ * t_start (the printed formula drops the minus sign inside alpha; only this
+ * reading lies in [0, 1)). Parallel over samples within each ray (Sec. 2.2).
+ * weights, trans: (n_samples,) float32 out, each nullable.
+ */
+int nacc_render_weights(const int32_t* packed_info, int32_t n_rays, const float* t_starts,
+                        const float* t_ends, const float* sigmas, int64_t n_samples,
+                        float* weights, float* trans, int32_t* d_status, void* stream);
+
+/*
+ * Accumulates any per-sample attribute along rays (Sec. 2.2: "Any sample
+ * attributes ... can be rendered"): out[r, c] = sum_{i in ray r} w_i v_i[c].
+ * values (n_samples, n_channels) float32, or NULL for v = 1 (opacity).
+ * out (n_rays, n_channels) float32.
+ */
+int nacc_accumulate_along_rays(const int32_t* packed_info, int32_t n_rays, const float* weights,
+                               const float* values, int32_t n_channels, int64_t n_samples,
+                               float* out, int32_t* d_status, void* stream);
+
+/*
+ * Fused forward rendering, Eq. 1 (render_weights + accumulate_along_rays):
+ *   color[r] = sum w_i rgb_i (n_rays,3); opacity[r] = sum w_i (n_rays,);
+ *   depth[r] = sum w_i (t_s + t_e)/2 (n_rays,), unnormalised, black background.
+ * optical_depth (n_samples,) float32 out or NULL: O_i = sum_{j<i} tau_j, the
+ * state nacc_render_bwd can reuse instead of recomputing it.
+ */
+int nacc_render_fwd(const int32_t* packed_info, int32_t n_rays, const float* t_starts,
+                    const float* t_ends, const float* sigmas, const float* rgbs,
+                    int64_t n_samples, float* color, float* opacity, float* depth,
+                    float* optical_depth, int32_t* d_status, void* stream);
+
+/*
+ * Gradient of nacc_render_fwd (Sec. 2.2: every output of the radiance field
+ * receives gradients). With a_i = <g_color, rgb_i> + g_opacity + g_depth tmid_i:
+ *   dL/dsigma_k = delta_k (a_k T_{k+1} - sum_{i>k} a_i w_i),  dL/drgb_k = w_k g_color,
+ * the suffix sum taken as a true reverse segmented scan (no total-minus-prefix
+ * cancellation). T is recomputed from sigmas, or read from optical_depth when
+ * the forward pass saved it (bit-identical results either way).
+ * g_color (n_rays,3), g_opacity (n_rays,), g_depth (n_rays,): nullable (zero).
+ * d_sigmas (n_samples,), d_rgbs (n_samples,3): float32 out.
+ */
+int nacc_render_bwd(const int32_t* packed_info, int32_t n_rays, const float* t_starts,
+                    const float* t_ends, const float* sigmas, const float* rgbs,
+                    const float* optical_depth, int64_t n_samples, const float* g_color,
+                    const float* g_opacity, const float* g_depth, float* d_sigmas,
+                    float* d_rgbs, int32_t* d_status, void* stream);
+
+/* ray_indices[i] = r for every sample i of ray r (the inverse of packed_info). */
+int nacc_unpack_info(const int32_t* packed_info, int32_t n_rays, int64_t n_samples,
+                     int32_t* ray_indices, int32_t* d_status, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Occupancy-grid update (Sec. 2.1: the binary grid is "cached and updated   */
+/* during training", following Instant-NGP's Appendix E.2)                   */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * ema[c] <- decay * ema[c] for every cell c in [0, n_cells), then
+ * ema[cell_s] <- max(ema[cell_s], sigma_s) for every sample s (NaN sigmas are
+ * ignored), then bits = (ema > thre) packed as in nacc_grid. The caller draws
+ * the cells (uniform random cells in Instant-NGP's scheme) and evaluates its
+ * field at points inside them. Float32 state, one rounding per product:
+ * bit-exact and independent of sample order.
+ * ema (n_cells,) float32 in/out, values >= 0; bits ceil(n_cells/32) uint32 out;
+ * cells (n_samples,) int32 in [0, n_cells) (others raise NACC_STATUS_BAD_INDEX
+ * and are skipped); sigmas (n_samples,) float32.
+ */
+int nacc_update_occupancy_grid(float* ema, uint32_t* bits, int64_t n_cells, const int32_t* cells,
+                               const float* sigmas, int64_t n_samples, float decay, float thre,
+                               int32_t* d_status, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Utilities                                                                 */
+/* ------------------------------------------------------------------------- */
+
+/* Static, human-readable text of a host return code. */
+const char* nacc_error_string(int code);
+/* NACC_VERSION of the built library. */
+int nacc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NACC_H */

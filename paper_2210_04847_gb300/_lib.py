@@ -1,0 +1,342 @@
+"""Thin ctypes binding of ``libnacc.so`` (C ABI in ``include/nacc.h``).
+
+Argument marshalling only: every step of marching and rendering runs in the
+library's CUDA kernels. Functions take torch CUDA tensors (PyTorch provides the
+device memory and the stream), check dtype / device / contiguity / size, pass
+raw pointers and the current stream, and raise ``NaccError`` on a non-zero
+return code. There is no CPU fallback: if the library is missing, importing
+this module's entry points raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnacc.so")
+FIELD_LIB_PATH = os.path.join(_HERE, "libnacc_field.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_CAPACITY = -2
+ERR_CUDA = -3
+ERR_TIMEOUT = -4
+
+STATUS_CAPACITY = 0x1
+STATUS_TIMEOUT = 0x2
+STATUS_BAD_PACKED = 0x4
+STATUS_BAD_INDEX = 0x8
+STATUS_OVERFLOW = 0x10
+MAX_LEVELS = 16
+
+EXPORTS = (
+    "nacc_march_workspace_size", "nacc_march_rays", "nacc_prune_workspace_size", "nacc_prune_samples",
+    "nacc_render_weights", "nacc_accumulate_along_rays", "nacc_render_fwd", "nacc_render_bwd",
+    "nacc_unpack_info", "nacc_update_occupancy_grid", "nacc_error_string", "nacc_version",
+)
+
+
+class NaccError(RuntimeError):
+    pass
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [
+        ("bits", ctypes.c_void_p),
+        ("res", ctypes.c_int32 * 3),
+        ("n_levels", ctypes.c_int32),
+        ("n_slots", ctypes.c_int32),
+        ("aabb", ctypes.c_float * 6),
+    ]
+
+
+class MarchParams(ctypes.Structure):
+    _fields_ = [
+        ("near_plane", ctypes.c_float),
+        ("far_plane", ctypes.c_float),
+        ("dt_min", ctypes.c_float),
+        ("dt_max", ctypes.c_float),
+        ("cone", ctypes.c_float),
+        ("max_steps", ctypes.c_int32),
+    ]
+
+
+_lib = None
+_field = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libnacc.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libnacc.so is not built (run `python -m paper_2210_04847_gb300.build`): " + LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, f32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
+    GP, MP = ctypes.POINTER(Grid), ctypes.POINTER(MarchParams)
+    sig = {
+        "nacc_march_workspace_size": (sz, [i32, MP]),
+        "nacc_march_rays": (ctypes.c_int, [P, P, P, P, i32, GP, MP, P, P, P, P, i64, P, P, P, sz, P]),
+        "nacc_prune_workspace_size": (sz, [i32, i64]),
+        "nacc_prune_samples": (ctypes.c_int, [P, i32, P, P, P, i64, f32, f32, P, P, P, P, i64, P, P, P, P, sz, P]),
+        "nacc_render_weights": (ctypes.c_int, [P, i32, P, P, P, i64, P, P, P, P]),
+        "nacc_accumulate_along_rays": (ctypes.c_int, [P, i32, P, P, i32, i64, P, P, P]),
+        "nacc_render_fwd": (ctypes.c_int, [P, i32, P, P, P, P, i64, P, P, P, P, P, P]),
+        "nacc_render_bwd": (ctypes.c_int, [P, i32, P, P, P, P, P, i64, P, P, P, P, P, P, P]),
+        "nacc_unpack_info": (ctypes.c_int, [P, i32, i64, P, P, P]),
+        "nacc_update_occupancy_grid": (ctypes.c_int, [P, P, i64, P, P, i64, f32, f32, P, P]),
+        "nacc_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "nacc_version": (ctypes.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def load_field() -> ctypes.CDLL:
+    global _field
+    if _field is not None:
+        return _field
+    if not os.path.exists(FIELD_LIB_PATH):
+        raise ImportError("libnacc_field.so is not built: " + FIELD_LIB_PATH)
+    L = ctypes.CDLL(FIELD_LIB_PATH)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    L.nacc_field_samples.restype = ctypes.c_int
+    L.nacc_field_samples.argtypes = [P, P, P, P, P, P, i64, P, i32, P, P, P, P]
+    L.nacc_field_points.restype = ctypes.c_int
+    L.nacc_field_points.argtypes = [P, P, i64, P, i32, P, P]
+    _field = L
+    return L
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(t: Optional[torch.Tensor], dtype, name: str, numel: Optional[int] = None, optional=False):
+    if t is None:
+        if optional:
+            return
+        raise NaccError("%s is required" % name)
+    if not t.is_cuda:
+        raise NaccError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise NaccError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise NaccError("%s must be contiguous" % name)
+    if numel is not None and t.numel() < numel:
+        raise NaccError("%s holds %d elements, needs %d" % (name, t.numel(), numel))
+
+
+def _rc(code: int, fn: str):
+    if code != OK:
+        msg = load().nacc_error_string(code).decode()
+        raise NaccError("%s failed: %s (%d)" % (fn, msg, code))
+
+
+def make_grid(bits: torch.Tensor, res: Sequence[int], aabb: Sequence[float], n_levels=1, n_slots=1) -> Grid:
+    _check(bits, torch.int32, "grid bits")
+    g = Grid()
+    g.bits = bits.data_ptr()
+    for k in range(3):
+        g.res[k] = int(res[k])
+    g.n_levels = int(n_levels)
+    g.n_slots = int(n_slots)
+    for k in range(6):
+        g.aabb[k] = float(aabb[k])
+    return g
+
+
+def make_params(near_plane, far_plane, dt_min, dt_max=None, cone=0.0, max_steps=1024) -> MarchParams:
+    p = MarchParams()
+    p.near_plane = float(near_plane)
+    p.far_plane = float(far_plane)
+    p.dt_min = float(dt_min)
+    p.dt_max = float(dt_min if dt_max is None else dt_max)
+    p.cone = float(cone)
+    p.max_steps = int(max_steps)
+    return p
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI, without the nacc_ prefix)
+# ---------------------------------------------------------------------------
+
+
+def march_workspace_size(n_rays: int, params: MarchParams) -> int:
+    return int(load().nacc_march_workspace_size(int(n_rays), ctypes.byref(params)))
+
+
+def prune_workspace_size(n_rays: int, n_samples: int) -> int:
+    return int(load().nacc_prune_workspace_size(int(n_rays), int(n_samples)))
+
+
+def march_rays(rays_o, rays_d, grid: Grid, params: MarchParams, packed_info, t_starts, t_ends, ray_indices,
+               n_samples, d_status, workspace, ray_time=None, ray_slot=None, stream=None):
+    n = rays_o.shape[0]
+    _check(rays_o, torch.float32, "rays_o", 3 * n)
+    _check(rays_d, torch.float32, "rays_d", 3 * n)
+    _check(ray_time, torch.float32, "ray_time", n, optional=True)
+    _check(ray_slot, torch.int32, "ray_slot", n, optional=True)
+    _check(packed_info, torch.int32, "packed_info", 2 * n)
+    cap = t_starts.numel()
+    _check(t_starts, torch.float32, "t_starts")
+    _check(t_ends, torch.float32, "t_ends", cap)
+    _check(ray_indices, torch.int32, "ray_indices", cap)
+    _check(n_samples, torch.int64, "n_samples", 1)
+    _check(d_status, torch.int32, "d_status", 1, optional=True)
+    _check(workspace, torch.uint8, "workspace")
+    rc = load().nacc_march_rays(
+        _ptr(rays_o), _ptr(rays_d), _ptr(ray_time), _ptr(ray_slot), n, ctypes.byref(grid), ctypes.byref(params),
+        _ptr(packed_info), _ptr(t_starts), _ptr(t_ends), _ptr(ray_indices), cap, _ptr(n_samples), _ptr(d_status),
+        _ptr(workspace), workspace.numel(), _stream(stream))
+    _rc(rc, "nacc_march_rays")
+
+
+def prune_samples(packed_info, t_starts, t_ends, sigmas, n_samples_in: int, early_stop_eps, alpha_thre,
+                  packed_info_out, t_starts_out, t_ends_out, ray_indices_out, n_kept, d_status, workspace,
+                  keep_mask=None, stream=None):
+    n = packed_info.shape[0]
+    _check(packed_info, torch.int32, "packed_info", 2 * n)
+    for t, nm in ((t_starts, "t_starts"), (t_ends, "t_ends"), (sigmas, "sigmas")):
+        _check(t, torch.float32, nm, n_samples_in)
+    _check(packed_info_out, torch.int32, "packed_info_out", 2 * n)
+    cap = t_starts_out.numel()
+    _check(t_starts_out, torch.float32, "t_starts_out")
+    _check(t_ends_out, torch.float32, "t_ends_out", cap)
+    _check(ray_indices_out, torch.int32, "ray_indices_out", cap)
+    _check(n_kept, torch.int64, "n_kept", 1)
+    _check(keep_mask, torch.uint8, "keep_mask", n_samples_in, optional=True)
+    _check(d_status, torch.int32, "d_status", 1, optional=True)
+    _check(workspace, torch.uint8, "workspace")
+    rc = load().nacc_prune_samples(
+        _ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), int(n_samples_in), float(early_stop_eps),
+        float(alpha_thre), _ptr(packed_info_out), _ptr(t_starts_out), _ptr(t_ends_out), _ptr(ray_indices_out), cap,
+        _ptr(n_kept), _ptr(keep_mask), _ptr(d_status), _ptr(workspace), workspace.numel(), _stream(stream))
+    _rc(rc, "nacc_prune_samples")
+
+
+def render_weights(packed_info, t_starts, t_ends, sigmas, n_samples: int, weights=None, trans=None, d_status=None,
+                   stream=None):
+    n = packed_info.shape[0]
+    _check(packed_info, torch.int32, "packed_info", 2 * n)
+    for t, nm in ((t_starts, "t_starts"), (t_ends, "t_ends"), (sigmas, "sigmas")):
+        _check(t, torch.float32, nm, n_samples)
+    _check(weights, torch.float32, "weights", n_samples, optional=True)
+    _check(trans, torch.float32, "trans", n_samples, optional=True)
+    _check(d_status, torch.int32, "d_status", 1, optional=True)
+    rc = load().nacc_render_weights(_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), int(n_samples),
+                                    _ptr(weights), _ptr(trans), _ptr(d_status), _stream(stream))
+    _rc(rc, "nacc_render_weights")
+
+
+def accumulate_along_rays(packed_info, weights, values, n_channels: int, n_samples: int, out, d_status=None,
+                          stream=None):
+    n = packed_info.shape[0]
+    _check(packed_info, torch.int32, "packed_info", 2 * n)
+    _check(weights, torch.float32, "weights", n_samples)
+    _check(values, torch.float32, "values", n_samples * n_channels, optional=True)
+    _check(out, torch.float32, "out", n * n_channels)
+    _check(d_status, torch.int32, "d_status", 1, optional=True)
+    rc = load().nacc_accumulate_along_rays(_ptr(packed_info), n, _ptr(weights), _ptr(values), int(n_channels),
+                                           int(n_samples), _ptr(out), _ptr(d_status), _stream(stream))
+    _rc(rc, "nacc_accumulate_along_rays")
+
+
+def render_fwd(packed_info, t_starts, t_ends, sigmas, rgbs, n_samples: int, color, opacity, depth,
+               optical_depth=None, d_status=None, stream=None):
+    n = packed_info.shape[0]
+    _check(packed_info, torch.int32, "packed_info", 2 * n)
+    for t, nm in ((t_starts, "t_starts"), (t_ends, "t_ends"), (sigmas, "sigmas")):
+        _check(t, torch.float32, nm, n_samples)
+    _check(rgbs, torch.float32, "rgbs", 3 * n_samples)
+    _check(color, torch.float32, "color", 3 * n, optional=True)
+    _check(opacity, torch.float32, "opacity", n, optional=True)
+    _check(depth, torch.float32, "depth", n, optional=True)
+    _check(optical_depth, torch.float32, "optical_depth", n_samples, optional=True)
+    _check(d_status, torch.int32, "d_status", 1, optional=True)
+    rc = load().nacc_render_fwd(_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), _ptr(rgbs),
+                                int(n_samples), _ptr(color), _ptr(opacity), _ptr(depth), _ptr(optical_depth),
+                                _ptr(d_status), _stream(stream))
+    _rc(rc, "nacc_render_fwd")
+
+
+def render_bwd(packed_info, t_starts, t_ends, sigmas, rgbs, n_samples: int, g_color, g_opacity, g_depth, d_sigmas,
+               d_rgbs, optical_depth=None, d_status=None, stream=None):
+    n = packed_info.shape[0]
+    _check(packed_info, torch.int32, "packed_info", 2 * n)
+    for t, nm in ((t_starts, "t_starts"), (t_ends, "t_ends"), (sigmas, "sigmas")):
+        _check(t, torch.float32, nm, n_samples)
+    _check(rgbs, torch.float32, "rgbs", 3 * n_samples)
+    _check(optical_depth, torch.float32, "optical_depth", n_samples, optional=True)
+    _check(g_color, torch.float32, "g_color", 3 * n, optional=True)
+    _check(g_opacity, torch.float32, "g_opacity", n, optional=True)
+    _check(g_depth, torch.float32, "g_depth", n, optional=True)
+    _check(d_sigmas, torch.float32, "d_sigmas", n_samples)
+    _check(d_rgbs, torch.float32, "d_rgbs", 3 * n_samples)
+    _check(d_status, torch.int32, "d_status", 1, optional=True)
+    rc = load().nacc_render_bwd(_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), _ptr(rgbs),
+                                _ptr(optical_depth), int(n_samples), _ptr(g_color), _ptr(g_opacity), _ptr(g_depth),
+                                _ptr(d_sigmas), _ptr(d_rgbs), _ptr(d_status), _stream(stream))
+    _rc(rc, "nacc_render_bwd")
+
+
+def unpack_info(packed_info, n_samples: int, ray_indices, d_status=None, stream=None):
+    n = packed_info.shape[0]
+    _check(packed_info, torch.int32, "packed_info", 2 * n)
+    _check(ray_indices, torch.int32, "ray_indices", n_samples)
+    _check(d_status, torch.int32, "d_status", 1, optional=True)
+    rc = load().nacc_unpack_info(_ptr(packed_info), n, int(n_samples), _ptr(ray_indices), _ptr(d_status),
+                                 _stream(stream))
+    _rc(rc, "nacc_unpack_info")
+
+
+def update_occupancy_grid(ema, bits, cells, sigmas, decay, thre, d_status=None, stream=None):
+    n_cells = ema.numel()
+    _check(ema, torch.float32, "ema")
+    _check(bits, torch.int32, "bits", (n_cells + 31) // 32)
+    n = cells.numel()
+    _check(cells, torch.int32, "cells")
+    _check(sigmas, torch.float32, "sigmas", n)
+    _check(d_status, torch.int32, "d_status", 1, optional=True)
+    rc = load().nacc_update_occupancy_grid(_ptr(ema), _ptr(bits), n_cells, _ptr(cells), _ptr(sigmas), n,
+                                           float(decay), float(thre), _ptr(d_status), _stream(stream))
+    _rc(rc, "nacc_update_occupancy_grid")
+
+
+# ---------------------------------------------------------------------------
+# stand-in radiance field (benchmarks only; not part of the method)
+# ---------------------------------------------------------------------------
+
+
+def field_samples(rays_o, rays_d, ray_indices, t_starts, t_ends, n: int, blobs, rgb_wb, sigmas, rgbs=None,
+                  ray_time=None, stream=None):
+    rc = load_field().nacc_field_samples(_ptr(rays_o), _ptr(rays_d), _ptr(ray_time), _ptr(ray_indices),
+                                         _ptr(t_starts), _ptr(t_ends), int(n), _ptr(blobs), blobs.shape[0],
+                                         _ptr(rgb_wb), _ptr(sigmas), _ptr(rgbs), _stream(stream))
+    if rc != 0:
+        raise NaccError("nacc_field_samples failed (%d)" % rc)
+
+
+def field_points(xyz, n: int, blobs, sigmas, times=None, stream=None):
+    rc = load_field().nacc_field_points(_ptr(xyz), _ptr(times), int(n), _ptr(blobs), blobs.shape[0], _ptr(sigmas),
+                                        _stream(stream))
+    if rc != 0:
+        raise NaccError("nacc_field_points failed (%d)" % rc)

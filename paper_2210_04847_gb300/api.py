@@ -1,0 +1,232 @@
+"""User-facing API in the shape of the paper's listing (Sec. 3):
+
+    packed_info, t_starts, t_ends = ray_marching(rays_o, rays_d, grid=grid, sigma_fn=sigma_fn,
+                                                 near_plane=0.2, far_plane=1.0,
+                                                 early_stop_eps=1e-4, alpha_thre=1e-2)
+    color, opacity, depth = rendering(rgb_sigma_fn, packed_info, t_starts, t_ends)
+
+``sigma_fn(t_starts, t_ends, ray_indices) -> sigmas`` and
+``rgb_sigma_fn(t_starts, t_ends, ray_indices) -> (rgbs, sigmas)`` are the
+user's radiance field, queried at packed samples ((n, 1) interval tensors).
+Marching, pruning and rendering (forward and backward) run in the CUDA
+library; PyTorch only supplies device memory, streams and autograd plumbing.
+
+The plain (eager) path has one host synchronisation per stage that produces a
+data-dependent number of samples: reading the sample count to size the
+outputs. Capacity-based calls without that synchronisation are available in
+``paper_2210_04847_gb300._lib`` (and used by ``Pipeline``).
+"""
+from __future__ import annotations
+
+from typing import Callable, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+class OccupancyGrid:
+    """Binary occupancy grid with its float32 EMA density (Sec. 2.1).
+
+    ``bits`` is an int32 tensor holding the uint32 words of the bitfield
+    (layout of ``nacc_grid``); ``ema`` the per-cell float32 state the update
+    maintains.
+    """
+
+    def __init__(self, aabb: Sequence[float], res=128, n_levels: int = 1, n_slots: int = 1, device="cuda"):
+        self.aabb = tuple(float(v) for v in aabb)
+        self.res = (int(res),) * 3 if np.isscalar(res) else tuple(int(v) for v in res)
+        self.n_levels = int(n_levels)
+        self.n_slots = int(n_slots)
+        self.n_cells = self.res[0] * self.res[1] * self.res[2] * self.n_levels * self.n_slots
+        self.ema = torch.zeros(self.n_cells, dtype=torch.float32, device=device)
+        self.bits = torch.zeros((self.n_cells + 31) // 32, dtype=torch.int32, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+
+    @classmethod
+    def from_bits(cls, bits: np.ndarray, res, aabb, n_levels=1, n_slots=1, device="cuda"):
+        g = cls(aabb, res, n_levels, n_slots, device)
+        w = np.ascontiguousarray(bits, dtype=np.uint32).view(np.int32)
+        assert w.size == g.bits.numel(), "bit words do not match the grid size"
+        g.bits.copy_(torch.from_numpy(w))
+        return g
+
+    def struct(self) -> _lib.Grid:
+        return _lib.make_grid(self.bits, self.res, self.aabb, self.n_levels, self.n_slots)
+
+    def update(self, cells: torch.Tensor, sigmas: torch.Tensor, decay: float = 0.95, thre: float = 0.01):
+        """EMA update: ema = max(decay * ema, sigma at sampled cells); bits = ema > thre."""
+        _lib.update_occupancy_grid(self.ema, self.bits, cells, sigmas, decay, thre, self.status)
+
+    def state_dict(self):
+        return {"ema": self.ema.clone(), "bits": self.bits.clone(), "res": self.res, "aabb": self.aabb,
+                "n_levels": self.n_levels, "n_slots": self.n_slots}
+
+    def load_state_dict(self, sd):
+        self.ema.copy_(sd["ema"])
+        self.bits.copy_(sd["bits"])
+
+
+class _Scratch:
+    """Per-device cache of workspaces and counters, grown on demand."""
+
+    def __init__(self):
+        self.bufs = {}
+
+    def get(self, name, nbytes, device):
+        key = (name, str(device))
+        b = self.bufs.get(key)
+        if b is None or b.numel() < nbytes:
+            b = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+            self.bufs[key] = b
+        return b
+
+
+_SCRATCH = _Scratch()
+_CAP_HINT = {}
+
+
+def _check_status(status: torch.Tensor, what: str):
+    s = int(status.item())
+    if s & (_lib.STATUS_TIMEOUT | _lib.STATUS_BAD_PACKED | _lib.STATUS_OVERFLOW | _lib.STATUS_BAD_INDEX):
+        raise _lib.NaccError("%s: device status 0x%x" % (what, s))
+
+
+def march_rays(rays_o, rays_d, grid: OccupancyGrid, near_plane=0.0, far_plane=1e10, render_step_size=1e-2,
+               cone_angle=0.0, dt_max=None, max_steps=1024, ray_time=None, ray_slot=None):
+    """Occupancy-grid marching only. Returns (packed_info (R,2), t_starts (M,), t_ends (M,), ray_indices (M,))."""
+    dev = rays_o.device
+    rays_o = rays_o.contiguous().float()
+    rays_d = rays_d.contiguous().float()
+    R = rays_o.shape[0]
+    params = _lib.make_params(near_plane, far_plane, render_step_size, dt_max, cone_angle, max_steps)
+    ws = _SCRATCH.get("march_ws", _lib.march_workspace_size(R, params), dev)
+    packed = torch.empty((R, 2), dtype=torch.int32, device=dev)
+    counter = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    cap = max(_CAP_HINT.get(("march", R), 64 * R), 1)
+    for _ in range(2):
+        ts = torch.empty(cap, dtype=torch.float32, device=dev)
+        te = torch.empty(cap, dtype=torch.float32, device=dev)
+        ri = torch.empty(cap, dtype=torch.int32, device=dev)
+        status.zero_()
+        _lib.march_rays(rays_o, rays_d, grid.struct(), params, packed, ts, te, ri, counter, status, ws,
+                        ray_time=ray_time, ray_slot=ray_slot)
+        n = int(counter.item())  # the one host synchronisation of the eager path
+        _check_status(status, "march_rays")
+        if n <= cap:
+            break
+        cap = n
+    _CAP_HINT[("march", R)] = max(n, 1)
+    return packed, ts[:n], te[:n], ri[:n]
+
+
+def prune_samples(packed_info, t_starts, t_ends, sigmas, early_stop_eps=1e-4, alpha_thre=0.0):
+    """Early-stop / alpha pruning and re-packing. Returns (packed_info, t_starts, t_ends, ray_indices)."""
+    dev = packed_info.device
+    R = packed_info.shape[0]
+    M = t_starts.numel()
+    ws = _SCRATCH.get("prune_ws", _lib.prune_workspace_size(R, M), dev)
+    packed = torch.empty((R, 2), dtype=torch.int32, device=dev)
+    counter = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    ts = torch.empty(M, dtype=torch.float32, device=dev)
+    te = torch.empty(M, dtype=torch.float32, device=dev)
+    ri = torch.empty(M, dtype=torch.int32, device=dev)
+    _lib.prune_samples(packed_info.contiguous(), t_starts.contiguous().view(-1), t_ends.contiguous().view(-1),
+                       sigmas.contiguous().view(-1).float(), M, early_stop_eps, alpha_thre, packed, ts, te, ri,
+                       counter, status, ws)
+    n = int(counter.item())
+    _check_status(status, "prune_samples")
+    return packed, ts[:n], te[:n], ri[:n]
+
+
+def ray_marching(rays_o, rays_d, grid: OccupancyGrid, sigma_fn: Optional[Callable] = None, near_plane=0.0,
+                 far_plane=1e10, render_step_size=1e-2, cone_angle=0.0, dt_max=None, max_steps=1024,
+                 early_stop_eps=1e-4, alpha_thre=0.0, ray_time=None, ray_slot=None, return_ray_indices=False):
+    """March rays through the occupancy grid, then (if sigma_fn is given) prune by
+    transmittance < early_stop_eps and opacity < alpha_thre, with the density
+    queried without gradients (Sec. 2.1). Returns (packed_info, t_starts (n,1), t_ends (n,1))."""
+    packed, ts, te, ri = march_rays(rays_o, rays_d, grid, near_plane, far_plane, render_step_size, cone_angle,
+                                    dt_max, max_steps, ray_time, ray_slot)
+    if sigma_fn is not None and (early_stop_eps > 0 or alpha_thre > 0) and ts.numel() > 0:
+        with torch.no_grad():
+            sig = sigma_fn(ts.view(-1, 1), te.view(-1, 1), ri)
+        packed, ts, te, ri = prune_samples(packed, ts, te, sig, early_stop_eps, alpha_thre)
+    out = (packed, ts.view(-1, 1), te.view(-1, 1))
+    return out + (ri,) if return_ray_indices else out
+
+
+def unpack_info(packed_info: torch.Tensor, n_samples: int) -> torch.Tensor:
+    ri = torch.empty(n_samples, dtype=torch.int32, device=packed_info.device)
+    _lib.unpack_info(packed_info.contiguous(), n_samples, ri)
+    return ri
+
+
+class _RenderFn(torch.autograd.Function):
+    """Eq. 1 forward and its hand-written backward (reverse segmented scan)."""
+
+    @staticmethod
+    def forward(ctx, sigmas, rgbs, packed_info, t_starts, t_ends, save_optical_depth: bool):
+        R = packed_info.shape[0]
+        M = t_starts.numel()
+        dev = packed_info.device
+        sg = sigmas.detach().contiguous().view(-1).float()
+        rgb = rgbs.detach().contiguous().view(-1, 3).float()
+        color = torch.empty((R, 3), dtype=torch.float32, device=dev)
+        opacity = torch.empty((R, 1), dtype=torch.float32, device=dev)
+        depth = torch.empty((R, 1), dtype=torch.float32, device=dev)
+        od = torch.empty(M, dtype=torch.float32, device=dev) if save_optical_depth else None
+        _lib.render_fwd(packed_info, t_starts, t_ends, sg, rgb, M, color, opacity, depth, optical_depth=od)
+        ctx.save_for_backward(sg, rgb, packed_info, t_starts, t_ends, *( [od] if od is not None else [] ))
+        ctx.sig_shape = sigmas.shape
+        ctx.rgb_shape = rgbs.shape
+        return color, opacity, depth
+
+    @staticmethod
+    def backward(ctx, g_color, g_opacity, g_depth):
+        saved = ctx.saved_tensors
+        sg, rgb, packed_info, t_starts, t_ends = saved[:5]
+        od = saved[5] if len(saved) > 5 else None
+        M = t_starts.numel()
+        d_sig = torch.empty(M, dtype=torch.float32, device=sg.device)
+        d_rgb = torch.empty((M, 3), dtype=torch.float32, device=sg.device)
+        f = lambda g: None if g is None else g.contiguous().float()
+        _lib.render_bwd(packed_info, t_starts, t_ends, sg, rgb, M, f(g_color), f(g_opacity), f(g_depth), d_sig, d_rgb,
+                        optical_depth=od)
+        return d_sig.view(ctx.sig_shape), d_rgb.view(ctx.rgb_shape), None, None, None, None
+
+
+def render_packed(sigmas, rgbs, packed_info, t_starts, t_ends, save_optical_depth=False):
+    """Differentiable Eq. 1 over packed samples: (color (R,3), opacity (R,1), depth (R,1))."""
+    return _RenderFn.apply(sigmas, rgbs, packed_info.contiguous(), t_starts.contiguous().view(-1),
+                           t_ends.contiguous().view(-1), save_optical_depth)
+
+
+def rendering(rgb_sigma_fn: Callable, packed_info, t_starts, t_ends, ray_indices=None, save_optical_depth=False):
+    """Query the user's field with gradients and render (Sec. 2.2). Returns (color, opacity, depth)."""
+    if ray_indices is None:
+        ray_indices = unpack_info(packed_info, t_starts.numel())
+    rgbs, sigmas = rgb_sigma_fn(t_starts.view(-1, 1), t_ends.view(-1, 1), ray_indices)
+    return render_packed(sigmas, rgbs, packed_info, t_starts, t_ends, save_optical_depth)
+
+
+def render_weights(packed_info, t_starts, t_ends, sigmas):
+    """Per-sample Eq. 1 weights and transmittance (no gradient). Returns (weights, trans)."""
+    M = t_starts.numel()
+    w = torch.empty(M, dtype=torch.float32, device=packed_info.device)
+    T = torch.empty(M, dtype=torch.float32, device=packed_info.device)
+    _lib.render_weights(packed_info.contiguous(), t_starts.contiguous().view(-1), t_ends.contiguous().view(-1),
+                        sigmas.contiguous().view(-1).float(), M, w, T)
+    return w, T
+
+
+def accumulate_along_rays(weights, packed_info, values=None):
+    """sum_i w_i v_i per ray for any attribute (Sec. 2.2). values (M, C) or None (opacity)."""
+    M = weights.numel()
+    C = 1 if values is None else values.view(M, -1).shape[1]
+    out = torch.empty((packed_info.shape[0], C), dtype=torch.float32, device=weights.device)
+    v = None if values is None else values.contiguous().view(M, C).float()
+    _lib.accumulate_along_rays(packed_info.contiguous(), weights.contiguous().view(-1).float(), v, C, M, out)
+    return out

@@ -1,0 +1,159 @@
+// nacc_internal.cuh -- device helpers shared by the CUDA kernels of the library:
+// warp scans, status reporting, the bounded decoupled look-back used by the
+// single-pass compaction kernels, and host-side launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nacc.h"
+
+namespace nacc {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// status
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void raise_status(int32_t* d_status, int bits) {
+    if (d_status) atomicOr(d_status, bits);
+}
+
+// ---------------------------------------------------------------------------
+// warp scans (float32 and int)
+// ---------------------------------------------------------------------------
+
+// Inclusive prefix sum over the 32 lanes (Hillis-Steele, 5 shuffle steps).
+__device__ __forceinline__ float warp_incl_scan(float v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        float n = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v = v + n;
+    }
+    return v;
+}
+
+// Inclusive suffix sum (lane i gets sum over lanes i..31).
+__device__ __forceinline__ float warp_incl_suffix(float v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        float n = __shfl_down_sync(FULL, v, o);
+        if (lane + o < 32) v = v + n;
+    }
+    return v;
+}
+
+__device__ __forceinline__ int warp_incl_scan_int(int v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int n = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// decoupled look-back (single-pass scan over tiles taken in ticket order)
+// ---------------------------------------------------------------------------
+//
+// Tile j publishes one 64-bit word: flag in bits 62..63 (1 = aggregate of the
+// tile alone, 2 = inclusive prefix through the tile), value in bits 0..61.
+// Tiles are numbered by an atomic ticket taken when a block starts work on
+// them, so every tile a block waits for is held by a block that is already
+// running and publishes its aggregate without waiting: the wait always ends.
+// It is still bounded: after kSpinLimit polls the block reports
+// NACC_STATUS_TIMEOUT, stops waiting, and publishes a (wrong) prefix so that
+// no other block waits on it either.
+
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagInc = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Called by one full warp. Returns the exclusive prefix of tile `tile` (sum of
+// the aggregates of tiles 0..tile-1) and publishes the inclusive prefix.
+__device__ __forceinline__ unsigned long long lookback(unsigned long long* status, int tile,
+                                                       unsigned long long aggregate, int lane,
+                                                       int32_t* d_status) {
+    if (tile == 0) {
+        if (lane == 0) st_relaxed_u64(&status[0], kFlagInc | (aggregate & kValMask));
+        return 0ull;
+    }
+    if (lane == 0) st_relaxed_u64(&status[tile], kFlagAgg | (aggregate & kValMask));
+    unsigned long long excl = 0;
+    int base = tile - 1;
+    int spins = 0;
+    bool timed_out = false;
+    while (true) {
+        int j = base - lane;
+        unsigned long long s = j >= 0 ? ld_relaxed_u64(&status[j]) : (kFlagInc | 0ull);
+        unsigned pending = __ballot_sync(FULL, (s >> 62) == 0ull);
+        while (pending) {
+            if (++spins > kSpinLimit) {
+                timed_out = true;
+                break;
+            }
+            __nanosleep(spins < 64 ? 32 : 256);
+            if ((pending >> lane) & 1u) s = ld_relaxed_u64(&status[j]);
+            pending = __ballot_sync(FULL, (s >> 62) == 0ull);
+        }
+        if (timed_out) break;
+        unsigned inc = __ballot_sync(FULL, (s >> 62) == 2ull);
+        unsigned long long v = s & kValMask;
+        if (inc) {
+            int first = __ffs(inc) - 1;  // nearest predecessor holding an inclusive prefix
+            if (lane > first) v = 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+            excl += v;
+            break;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        excl += v;
+        base -= 32;
+    }
+    if (timed_out && lane == 0) raise_status(d_status, NACC_STATUS_TIMEOUT);
+    if (lane == 0) st_relaxed_u64(&status[tile], kFlagInc | ((excl + aggregate) & kValMask));
+    return excl;
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+
+struct DeviceInfo {
+    int device;
+    int sm_count;
+};
+
+DeviceInfo current_device();
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+inline int launch_status(cudaError_t e) { return e == cudaSuccess ? NACC_OK : NACC_ERR_CUDA; }
+
+}  // namespace nacc

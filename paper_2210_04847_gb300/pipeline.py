@@ -1,0 +1,135 @@
+"""One training step of the marching + rendering path on preallocated buffers.
+
+``HotPath`` holds capacity-sized device buffers for a workload and runs the
+paper's pipeline (Sec. 2 and the Sec. 3 listing) as separate stages through the
+C ABI:
+
+    march  -> [field: density, no gradient] -> prune -> [field: rgb + density]
+           -> render_fwd -> [loss gradient] -> render_bwd -> update_occupancy_grid
+
+The bracketed steps belong to the user (the radiance field and the loss); here
+the procedural stand-in field of ``libnacc_field.so`` plays that part. Each
+stage can be bracketed by CUDA events on the launching stream.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib, synth
+
+
+def to_device(a, device="cuda"):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(a).to(device)
+
+
+@dataclass
+class StepCounts:
+    n_marched: int
+    n_kept: int
+
+
+class StandInField:
+    """Procedural radiance field of a blob scene on the device (user side of the API)."""
+
+    def __init__(self, scene: synth.BlobScene, device="cuda"):
+        self.blobs = to_device(scene.device_params(), device)
+        self.wb = to_device(np.concatenate([scene.rgb_w.reshape(-1), scene.rgb_b]).astype(np.float32), device)
+
+    def samples(self, rays_o, rays_d, ray_indices, t_starts, t_ends, n, sigmas, rgbs=None, ray_time=None):
+        _lib.field_samples(rays_o, rays_d, ray_indices, t_starts, t_ends, n, self.blobs, self.wb, sigmas, rgbs,
+                           ray_time=ray_time)
+
+    def points(self, xyz, n, sigmas, times=None):
+        _lib.field_points(xyz, n, self.blobs, sigmas, times=times)
+
+
+class HotPath:
+    """Capacity-sized buffers and stage launchers for one workload."""
+
+    def __init__(self, w: synth.Workload, cap_marched: int, cap_kept: int, n_grid_samples: int = 0,
+                 device="cuda"):
+        R = w.n_rays
+        self.w = w
+        self.R = R
+        self.device = device
+        self.bits = to_device(w.bits, device)
+        self.n_cells = int(np.prod(w.res)) * w.n_levels * w.n_slots
+        self.ema = torch.zeros(self.n_cells, dtype=torch.float32, device=device)
+        self.params = _lib.make_params(w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone, w.max_steps)
+        self.grid = _lib.make_grid(self.bits, w.res, w.aabb, w.n_levels, w.n_slots)
+        f32, i32 = torch.float32, torch.int32
+        z = lambda n, dt=f32: torch.zeros(max(int(n), 1), dtype=dt, device=device)
+        self.cap_m, self.cap_k = int(cap_marched), int(cap_kept)
+        self.ws_march = z(_lib.march_workspace_size(R, self.params), torch.uint8)
+        self.pi_m = torch.zeros((R, 2), dtype=i32, device=device)
+        self.ts_m, self.te_m, self.ri_m, self.sig_m = z(self.cap_m), z(self.cap_m), z(self.cap_m, i32), z(self.cap_m)
+        self.ws_prune = z(_lib.prune_workspace_size(R, self.cap_m), torch.uint8)
+        self.pi_k = torch.zeros((R, 2), dtype=i32, device=device)
+        self.ts_k, self.te_k, self.ri_k = z(self.cap_k), z(self.cap_k), z(self.cap_k, i32)
+        self.sig_k, self.rgb_k = z(self.cap_k), torch.zeros((max(self.cap_k, 1), 3), dtype=f32, device=device)
+        self.color = torch.zeros((R, 3), dtype=f32, device=device)
+        self.opacity = torch.zeros(R, dtype=f32, device=device)
+        self.depth = torch.zeros(R, dtype=f32, device=device)
+        self.g_color = torch.zeros((R, 3), dtype=f32, device=device)
+        self.d_sig, self.d_rgb = z(self.cap_k), torch.zeros((max(self.cap_k, 1), 3), dtype=f32, device=device)
+        self.n_m = torch.zeros(1, dtype=torch.int64, device=device)
+        self.n_k = torch.zeros(1, dtype=torch.int64, device=device)
+        self.status = torch.zeros(1, dtype=i32, device=device)
+        self.n_grid = int(n_grid_samples)
+        self.cells = z(self.n_grid, i32)
+        self.cell_sig = z(self.n_grid)
+
+    # -- stages ------------------------------------------------------------
+    def march(self, rays_o, rays_d, ray_time=None, ray_slot=None):
+        _lib.march_rays(rays_o, rays_d, self.grid, self.params, self.pi_m, self.ts_m[: self.cap_m],
+                        self.te_m[: self.cap_m], self.ri_m[: self.cap_m], self.n_m, self.status, self.ws_march,
+                        ray_time=ray_time, ray_slot=ray_slot)
+
+    def prune(self, n_marched: int):
+        M = min(int(n_marched), self.cap_m)
+        _lib.prune_samples(self.pi_m, self.ts_m[:M], self.te_m[:M], self.sig_m[:M], M, self.w.early_stop_eps,
+                           self.w.alpha_thre, self.pi_k, self.ts_k[: self.cap_k], self.te_k[: self.cap_k],
+                           self.ri_k[: self.cap_k], self.n_k, self.status, self.ws_prune)
+
+    def render_fwd(self, n_kept: int):
+        S = min(int(n_kept), self.cap_k)
+        _lib.render_fwd(self.pi_k, self.ts_k[:S], self.te_k[:S], self.sig_k[:S], self.rgb_k[:S], S, self.color,
+                        self.opacity, self.depth, d_status=self.status)
+
+    def render_bwd(self, n_kept: int):
+        S = min(int(n_kept), self.cap_k)
+        _lib.render_bwd(self.pi_k, self.ts_k[:S], self.te_k[:S], self.sig_k[:S], self.rgb_k[:S], S, self.g_color,
+                        None, None, self.d_sig[:S], self.d_rgb[:S], d_status=self.status)
+
+    def grid_update(self, decay=0.95, thre=0.01, bits=None):
+        """EMA update of ``self.ema``; writes ``bits`` (default: the bitfield marched by this path)."""
+        _lib.update_occupancy_grid(self.ema, self.bits if bits is None else bits, self.cells[: self.n_grid],
+                                   self.cell_sig[: self.n_grid], decay, thre, self.status)
+
+    # -- user side (stand-in field, loss) ----------------------------------
+    def field_marched(self, field: StandInField, rays_o, rays_d, n_marched, ray_time=None):
+        M = min(int(n_marched), self.cap_m)
+        field.samples(rays_o, rays_d, self.ri_m, self.ts_m, self.te_m, M, self.sig_m, None, ray_time=ray_time)
+
+    def field_kept(self, field: StandInField, rays_o, rays_d, n_kept, ray_time=None):
+        S = min(int(n_kept), self.cap_k)
+        field.samples(rays_o, rays_d, self.ri_k, self.ts_k, self.te_k, S, self.sig_k, self.rgb_k, ray_time=ray_time)
+
+    def loss_grad(self, target):
+        # L = mean over rays and channels of (C - C*)^2  ->  dL/dC = 2 (C - C*) / (3R)
+        torch.sub(self.color, target, out=self.g_color)
+        self.g_color.mul_(2.0 / (3.0 * self.R))
+
+    def check_status(self, what=""):
+        s = int(self.status.item())
+        if s:
+            raise _lib.NaccError("%s: device status 0x%x" % (what, s))

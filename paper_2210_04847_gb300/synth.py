@@ -110,11 +110,13 @@ class BlobScene:
         x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
         c = self._centers_at(t)
         inv2s2 = 1.0 / (2.0 * self.scales * self.scales)
+        c2 = (c * c).sum(1)
         out = np.empty(x.shape[0], dtype=np.float64)
         for s in range(0, x.shape[0], chunk):
             xs = x[s : s + chunk]
-            d2 = ((xs[:, None, :] - c[None, :, :]) ** 2).sum(-1)
-            out[s : s + chunk] = (self.peaks[None, :] * np.exp(-d2 * inv2s2[None, :])).sum(-1)
+            # |x - c|^2 = |x|^2 - 2 x.c + |c|^2 (one matrix product per chunk)
+            d2 = np.maximum((xs * xs).sum(1)[:, None] - 2.0 * (xs @ c.T) + c2[None, :], 0.0)
+            out[s : s + chunk] = np.exp(-d2 * inv2s2[None, :]) @ self.peaks
         return out
 
     def rgb(self, x: np.ndarray) -> np.ndarray:
@@ -352,12 +354,18 @@ def tiny_config(seed: int = 0, device="cpu") -> Workload:
     )
 
 
-def bounded_config(seed: int = 0, n_rays: int = 1 << 18, n_cams: int = 100, device="cpu", batch: int = 0) -> Workload:
-    """Random rays of 100 cameras at 800x800 (fx = fy = 1111.1) on the r = 4 sphere,
-    64 blobs, 128^3 grid over [-1.5, 1.5]^3, dt = sqrt(3)*3/1024 (<= 1024 steps),
-    early stop 1e-4, alpha threshold 1e-2, seeded MSE target. ``batch`` selects
-    an independent draw of rays for the same scene."""
+def bounded_scene(seed: int = 0, device="cpu"):
+    """Scene and grid of the bounded workload: 64 blobs, 128^3 bits over [-1.5, 1.5]^3 (density > 0.01)."""
     scene = make_blob_scene(seed, 64)
+    aabb = (-1.5, -1.5, -1.5, 1.5, 1.5, 1.5)
+    bits = occupancy_bits(scene, aabb, (128, 128, 128), 1, 0.01, device=device)
+    return scene, aabb, bits
+
+
+def bounded_rays(seed: int, n_rays: int, batch: int = 0, n_cams: int = 100):
+    """Random (camera, pixel) rays of 100 cameras at 800x800 (fx = fy = 1111.1) on the r = 4
+    sphere looking at the origin, and a seeded target colour per ray. ``batch`` selects an
+    independent draw for the same cameras. Returns float32 (o, d, target)."""
     cams = sphere_cameras(seed, n_cams, 4.0)
     sb = 1000 + 16 * batch
     ci = rand_int(seed, sb + 1, n_rays, n_cams)
@@ -365,15 +373,24 @@ def bounded_config(seed: int = 0, n_rays: int = 1 << 18, n_cams: int = 100, devi
     px, py = (pix % 800).astype(np.float64), (pix // 800).astype(np.float64)
     pos = cams[ci]
     o, d = pinhole_rays(pos, np.zeros_like(pos), px, py, 1111.1, 1111.1, 400.0, 400.0)
-    aabb = (-1.5, -1.5, -1.5, 1.5, 1.5, 1.5)
-    bits = occupancy_bits(scene, aabb, (128, 128, 128), 1, 0.01, device=device)
-    dt = SQRT3 * 3.0 / 1024.0
     target = rand_uniform(seed, sb + 3, 3 * n_rays).reshape(n_rays, 3)
+    return _f32(o), _f32(d), _f32(target)
+
+
+def bounded_config(seed: int = 0, n_rays: int = 1 << 18, n_cams: int = 100, device="cpu", batch: int = 0,
+                   scene_grid=None) -> Workload:
+    """Random rays of 100 cameras at 800x800 (fx = fy = 1111.1) on the r = 4 sphere,
+    64 blobs, 128^3 grid over [-1.5, 1.5]^3, dt = sqrt(3)*3/1024 (<= 1024 steps),
+    early stop 1e-4, alpha threshold 1e-2, seeded MSE target. ``batch`` selects
+    an independent draw of rays for the same scene."""
+    scene, aabb, bits = scene_grid if scene_grid is not None else bounded_scene(seed, device)
+    o, d, target = bounded_rays(seed, n_rays, batch, n_cams)
+    dt = SQRT3 * 3.0 / 1024.0
+    name = ("bounded-2^%d-rays-64blobs-grid128" % int(round(math.log2(n_rays))) if n_rays & (n_rays - 1) == 0
+            else "bounded-%d-rays-64blobs-grid128" % n_rays)
     return Workload(
-        "bounded-2^%d-rays-64blobs-grid128" % int(round(math.log2(n_rays))) if n_rays & (n_rays - 1) == 0
-        else "bounded-%d-rays-64blobs-grid128" % n_rays,
-        _f32(o), _f32(d), bits, (128, 128, 128), 1, 1, aabb,
-        0.0, 1e10, dt, dt, 0.0, 1024, 1e-4, 1e-2, [scene], target_rgb=_f32(target),
+        name, o, d, bits, (128, 128, 128), 1, 1, aabb,
+        0.0, 1e10, dt, dt, 0.0, 1024, 1e-4, 1e-2, [scene], target_rgb=target,
     )
 
 

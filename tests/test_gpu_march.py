@@ -1,0 +1,106 @@
+"""GPU marching vs the oracle, bit-exact (Sec. 2.1 "Ray Marching"): sample counts,
+packed offsets, ray indices and the float32 interval bounds all identical."""
+import numpy as np
+import pytest
+
+from paper_2210_04847_gb300 import _lib, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from gpu_util import assert_march_equal, gpu_march, oracle_march  # noqa: E402
+
+
+def test_tiny_config_bitexact(orc):
+    w = synth.tiny_config(0, device="cuda")
+    assert_march_equal(gpu_march(w), oracle_march(orc, w))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_tiny_grids(orc, seed):
+    """Grids 2^3..8^3 with random bits; 1000 rays (32 tiles, ragged last tile) incl.
+    axis-parallel, inside-the-box, grazing and non-finite rays."""
+    res = [(2, 2, 2), (3, 5, 4), (8, 8, 8), (7, 3, 6)][seed]
+    n_cells = res[0] * res[1] * res[2]
+    occ = synth.rand_uniform(seed, 1, n_cells) < 0.4
+    n = 1000
+    o = synth.random_unit_vectors(seed, 2, n) * 3.0
+    tgt = synth.rand_uniform(seed, 3, 3 * n, -1.2, 1.2).reshape(n, 3)
+    d = tgt - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    d[:6] = np.eye(3)[[0, 1, 2, 0, 1, 2]] * np.array([1, 1, 1, -1, -1, -1])[:, None]
+    o[:6] = [[-2, 0.1, -0.3], [0.3, -2, -0.4], [0.2, 0.3, -2], [2, -0.2, 0.1], [-0.1, 2, 0.2], [0.1, 0.2, 2]]
+    o[6:40] = synth.rand_uniform(seed, 4, 102, -0.9, 0.9).reshape(34, 3)
+    o[40] = [np.nan, 0, 0]
+    d[41] = [np.inf, 0, 0]
+    o[42], d[42] = [-2, 1.0, 0.0], [1, 0, 0]  # grazing the y = 1 face
+    w = synth.Workload("tiny-random", o.astype(np.float32), d.astype(np.float32), synth.pack_bits(occ), res, 1, 1,
+                       (-1.0, -0.75, -1.25, 1.0, 1.25, 0.5), 0.0, 1e10, 0.05, 0.05, 0.0, 1024, 0.0, 0.0)
+    assert_march_equal(gpu_march(w), oracle_march(orc, w))
+
+
+def test_bounded_subset_bitexact(orc):
+    w = synth.bounded_config(0, n_rays=1 << 12, device="cuda")
+    g = gpu_march(w)
+    assert g[4] > 1000 * 100
+    assert_march_equal(g, oracle_march(orc, w))
+
+
+def test_near_far_planes_and_max_steps(orc):
+    w = synth.bounded_config(1, n_rays=2000, device="cuda")
+    w.near_plane, w.far_plane, w.max_steps = 3.1, 4.6, 200
+    assert_march_equal(gpu_march(w), oracle_march(orc, w))
+
+
+def test_cone_cascade_bitexact(orc):
+    """Unbounded scene: 4-level cascade of 128^3, cone steps clamp(t/256, 1e-3, 10)."""
+    w = synth.unbounded_config(0, n_rays=1 << 11, device="cuda")
+    g = gpu_march(w)
+    assert g[4] > 0
+    assert_march_equal(g, oracle_march(orc, w))
+
+
+def test_time_bins_bitexact(orc):
+    w = synth.dynamic_config(0, n_rays=1 << 11, n_bins=16, device="cuda")
+    assert_march_equal(gpu_march(w), oracle_march(orc, w))
+
+
+def test_scene_slots_bitexact(orc):
+    w = synth.batched_config(0, n_scenes=6, device="cuda", ray_scale=1.0 / 32)
+    assert_march_equal(gpu_march(w), oracle_march(orc, w))
+
+
+def test_capacity_overflow_reports_total(orc):
+    w = synth.tiny_config(0, device="cuda")
+    ora = oracle_march(orc, w)
+    cap = ora.n_samples // 3
+    pi, ts, te, ri, n, status = gpu_march(w, capacity=cap)
+    assert status & _lib.STATUS_CAPACITY
+    assert n == ora.n_samples
+    assert np.array_equal(pi, ora.packed_info)
+    assert np.array_equal(ts, ora.t_starts[:cap]) and np.array_equal(ri, ora.ray_indices[:cap])
+
+
+def test_empty_and_all_missing(orc):
+    w = synth.tiny_config(0, device="cuda")
+    w.rays_o = np.zeros((0, 3), np.float32)
+    w.rays_d = np.zeros((0, 3), np.float32)
+    pi, ts, te, ri, n, status = gpu_march(w, capacity=16)
+    assert n == 0 and status == 0
+    w = synth.tiny_config(0, device="cuda")
+    w.rays_o = np.tile(np.array([[5, 5, 5]], np.float32), (77, 1))
+    w.rays_d = np.tile(np.array([[1, 0, 0]], np.float32), (77, 1))
+    pi, ts, te, ri, n, status = gpu_march(w, capacity=16)
+    assert n == 0 and status == 0 and np.all(pi == 0)
+
+
+def test_max_steps_many_chunks(orc):
+    """max_steps = 32768 with a tiny step: long rays span 1024 ballot words."""
+    w = synth.tiny_config(0, device="cuda")
+    w.rays_o, w.rays_d = w.rays_o[:300], w.rays_d[:300]
+    w.dt_min = w.dt_max = 2e-4
+    w.max_steps = 32768
+    assert_march_equal(gpu_march(w), oracle_march(orc, w))
