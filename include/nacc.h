@@ -212,8 +212,12 @@ int nacc_render_fwd(const int32_t* packed_info, int32_t n_rays, const float* t_s
  * receives gradients). With a_i = <g_color, rgb_i> + g_opacity + g_depth tmid_i:
  *   dL/dsigma_k = delta_k (a_k T_{k+1} - sum_{i>k} a_i w_i),  dL/drgb_k = w_k g_color,
  * the suffix sum taken as a true reverse segmented scan (no total-minus-prefix
- * cancellation). T is recomputed from sigmas, or read from optical_depth when
- * the forward pass saved it (bit-identical results either way).
+ * cancellation) and evaluated in the centred form a_ref T_end + b_k T_{k+1} -
+ * sum_{i>k} b_i w_i, b_i = a_i - a_ref (a_ref: the ray's first sample), which
+ * equals the expression above exactly but keeps float32 error proportional to
+ * the variation of a along the ray. T is recomputed from sigmas, or read from
+ * optical_depth when the forward pass saved it (bit-identical results either
+ * way).
  * g_color (n_rays,3), g_opacity (n_rays,), g_depth (n_rays,): nullable (zero).
  * d_sigmas (n_samples,), d_rgbs (n_samples,3): float32 out.
  */

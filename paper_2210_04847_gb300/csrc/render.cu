@@ -259,7 +259,20 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const BwdArgs a) {
             __syncwarp();
         }
 
-        // pass B: chunks in reverse order, suffix sums of a_i w_i carried backwards
+        // Reference sample of the ray (its first): with b_i = a_i - a_ref and the
+        // telescoping sum_{i>k} w_i = T_{k+1} - T_end, the gradient
+        //   a_k T_{k+1} - sum_{i>k} a_i w_i = a_ref T_end + b_k T_{k+1} - sum_{i>k} b_i w_i
+        // is the same quantity, but the large near-cancelling terms a_ref T_{k+1}
+        // and a_ref sum w_i never appear: the float32 error scales with |b| (the
+        // variation of a along the ray), not with |a|.
+        const float r_ref = __ldg(a.rgbs + 3 * (size_t)off);
+        const float g_ref = __ldg(a.rgbs + 3 * (size_t)off + 1);
+        const float b_ref = __ldg(a.rgbs + 3 * (size_t)off + 2);
+        const float tm_ref = (__ldg(a.t_starts + off) + __ldg(a.t_ends + off)) * 0.5f;
+        const float a_ref = gc0 * r_ref + gc1 * g_ref + gc2 * b_ref + ga + gd * tm_ref;
+        float t_end = 0.0f;
+
+        // pass B: chunks in reverse order, suffix sums of b_i w_i carried backwards
         float carry_s = 0.0f;
         for (int c = nch - 1; c >= 0; --c) {
             float carry_o = 0.0f;
@@ -298,17 +311,18 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const BwdArgs a) {
             }
             const float T = expf(-O);
             const float T_next = expf(-__fadd_rn(O, tau));
+            if (c == nch - 1) t_end = __shfl_sync(FULL, T_next, (cnt - 1) & 31);
             const float w = T * -expm1f(-tau);
             const float tmid = (s0 + s1) * 0.5f;
-            const float av = gc0 * cr + gc1 * cg + gc2 * cb + ga + gd * tmid;
-            const float aw = valid ? av * w : 0.0f;
-            const float suf = warp_incl_suffix(aw, lane);
+            const float bv = gc0 * (cr - r_ref) + gc1 * (cg - g_ref) + gc2 * (cb - b_ref) + gd * (tmid - tm_ref);
+            const float bw = valid ? bv * w : 0.0f;
+            const float suf = warp_incl_suffix(bw, lane);
             float suf_excl = __shfl_down_sync(FULL, suf, 1);
             if (lane == 31) suf_excl = 0.0f;
             const float S = carry_s + suf_excl;
             carry_s = carry_s + __shfl_sync(FULL, suf, 0);
             if (valid) {
-                const float dtau = av * T_next - S;
+                const float dtau = a_ref * t_end + (bv * T_next - S);
                 a.d_sigmas[i] = (s1 - s0) * dtau;
                 a.d_rgbs[3 * i] = w * gc0;
                 a.d_rgbs[3 * i + 1] = w * gc1;
