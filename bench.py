@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--ref-rays", type=int, default=1 << 12, help="rays per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--knobs", default="", help="fixed launch-shape knobs, e.g. march_tile_rays=8,prune_tile_rays=8 "
+                    "(skips the autotuner)")
     return ap.parse_args()
 
 
@@ -315,6 +317,16 @@ def run_ours(args):
         xyz = synth.cell_positions(cells, jit, aabb, (128, 128, 128))
         grid_inputs.append((to_device(cells, dev), to_device(xyz.astype(np.float32), dev)))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # larger than the 126 MB L2
+    from paper_2210_04847_gb300 import autotune
+
+    if args.knobs:
+        tuned = {}
+        for kv in args.knobs.split(","):
+            k, v = kv.split("=")
+            _lib.tune_set(k.strip(), int(v))
+            tuned[k.strip()] = {"best": int(v), "fixed": True}
+    else:
+        tuned = autotune.tune_hot_path(hp, field, batches[0][0], batches[0][1])
 
     stages = ["march", "prune", "render_fwd", "render_bwd", "grid_update"]
     ev = {s: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for s in stages}
@@ -415,6 +427,7 @@ def run_ours(args):
             "l2": "flushed before every step (256 MB write); per-step working set > 1 GB",
             "timed": "march + prune + render_fwd + render_bwd + grid_update (field and loss are user code, untimed)",
         },
+        "tuned": {k: v["best"] for k, v in tuned.items()},
         "stages_ms": {s: round(avg[s], 4) for s in stages},
         "stage_gbs": {s: round(sb[s] / (avg[s] / 1e3) / 1e9, 1) for s in stages},
         "samples_per_step": {"marched": round(M_avg), "examined_by_prune": round(Mr_avg), "kept": round(S_avg)},

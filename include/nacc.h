@@ -154,7 +154,9 @@ size_t nacc_prune_workspace_size(int32_t n_rays, int64_t n_samples);
  * gradient per Sec. 2.1); once a ray's optical depth passes -ln(eps) the rest
  * of the ray is not read.
  *
- * packed_info (n_rays,2), t_starts, t_ends, sigmas (n_samples,): input samples.
+ * packed_info (n_rays,2), t_starts, t_ends, sigmas (n_samples,): input samples,
+ *   each 8-byte aligned; runs ascending and disjoint in ray order (as produced
+ *   by nacc_march_rays), else the ray is skipped and NACC_STATUS_BAD_PACKED set.
  * packed_info_out (n_rays, 2); t_starts_out, t_ends_out, ray_indices_out
  *   (capacity,): output; n_kept: device int64 out (total, also past capacity).
  * keep_mask (n_samples,) uint8 or NULL: 1 where kept.
@@ -250,6 +252,26 @@ int nacc_unpack_info(const int32_t* packed_info, int32_t n_rays, int64_t n_sampl
 int nacc_update_occupancy_grid(float* ema, uint32_t* bits, int64_t n_cells, const int32_t* cells,
                                const float* sigmas, int64_t n_samples, float decay, float thre,
                                int32_t* d_status, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Launch-shape tuning (process-wide table, read at each launch)             */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Knobs select among launch shapes that compute identical results; they only
+ * change speed. Defaults are valid for any input; an autotuner measures the
+ * variants on the caller's workload and sets the fastest. Not synchronised:
+ * change knobs only while no other host thread launches library work.
+ */
+#define NACC_TUNE_RENDER_FWD_PREFETCH 0 /* 0/1: issue the next chunk's loads early */
+#define NACC_TUNE_MARCH_TILE_RAYS 1     /* 1..32: rays per warp tile (upper bound) */
+#define NACC_TUNE_PRUNE_TILE_RAYS 2     /* 2..32, even: rays per warp tile */
+#define NACC_TUNE_COUNT 3
+
+/* Set a knob; NACC_ERR_INVALID_ARG for an unknown knob or out-of-range value. */
+int nacc_tune_set(int knob, int value);
+/* Current value of a knob (NACC_ERR_INVALID_ARG for an unknown knob). */
+int nacc_tune_get(int knob);
 
 /* ------------------------------------------------------------------------- */
 /* Utilities                                                                 */

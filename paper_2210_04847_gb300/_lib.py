@@ -35,8 +35,14 @@ MAX_LEVELS = 16
 EXPORTS = (
     "nacc_march_workspace_size", "nacc_march_rays", "nacc_prune_workspace_size", "nacc_prune_samples",
     "nacc_render_weights", "nacc_accumulate_along_rays", "nacc_render_fwd", "nacc_render_bwd",
-    "nacc_unpack_info", "nacc_update_occupancy_grid", "nacc_error_string", "nacc_version",
+    "nacc_unpack_info", "nacc_update_occupancy_grid", "nacc_tune_set", "nacc_tune_get", "nacc_error_string",
+    "nacc_version",
 )
+
+TUNE_RENDER_FWD_PREFETCH = 0
+TUNE_MARCH_TILE_RAYS = 1
+TUNE_PRUNE_TILE_RAYS = 2
+TUNE_KNOBS = {"render_fwd_prefetch": 0, "march_tile_rays": 1, "prune_tile_rays": 2}
 
 
 class NaccError(RuntimeError):
@@ -89,6 +95,8 @@ def load() -> ctypes.CDLL:
         "nacc_render_bwd": (ctypes.c_int, [P, i32, P, P, P, P, P, i64, P, P, P, P, P, P, P]),
         "nacc_unpack_info": (ctypes.c_int, [P, i32, i64, P, P, P]),
         "nacc_update_occupancy_grid": (ctypes.c_int, [P, P, i64, P, P, i64, f32, f32, P, P]),
+        "nacc_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+        "nacc_tune_get": (ctypes.c_int, [ctypes.c_int]),
         "nacc_error_string": (ctypes.c_char_p, [ctypes.c_int]),
         "nacc_version": (ctypes.c_int, []),
     }
@@ -319,6 +327,20 @@ def update_occupancy_grid(ema, bits, cells, sigmas, decay, thre, d_status=None, 
     rc = load().nacc_update_occupancy_grid(_ptr(ema), _ptr(bits), n_cells, _ptr(cells), _ptr(sigmas), n,
                                            float(decay), float(thre), _ptr(d_status), _stream(stream))
     _rc(rc, "nacc_update_occupancy_grid")
+
+
+def tune_set(knob, value: int):
+    """Set a launch-shape knob (name or NACC_TUNE_* index); results never change, only speed."""
+    k = TUNE_KNOBS[knob] if isinstance(knob, str) else int(knob)
+    _rc(load().nacc_tune_set(k, int(value)), "nacc_tune_set")
+
+
+def tune_get(knob) -> int:
+    k = TUNE_KNOBS[knob] if isinstance(knob, str) else int(knob)
+    v = load().nacc_tune_get(k)
+    if v < 0:
+        raise NaccError("unknown tuning knob %r" % (knob,))
+    return v
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,72 @@
+"""Autotuner for the library's launch shapes.
+
+Every knob of the library's tuning table (``nacc_tune_set``) selects among
+launch shapes that produce identical results; only the speed differs, and it
+depends on the workload (ray lengths, how much is pruned, grid occupancy). The
+tuner measures each candidate value on the caller's own buffers with CUDA
+events on the launching stream and keeps the fastest, one knob at a time.
+"""
+from __future__ import annotations
+
+import statistics
+from typing import Callable, Dict, Iterable
+
+import torch
+
+from . import _lib
+
+# Candidate values per knob (all valid for every input).
+CANDIDATES = {
+    "march_tile_rays": (2, 4, 8, 16, 32),
+    "prune_tile_rays": (2, 4, 8, 16, 32),
+    "render_fwd_prefetch": (0, 1),
+}
+
+
+def time_ms(fn: Callable[[], None], reps: int = 5, warmup: int = 1, before: Callable[[], None] = None) -> float:
+    """Median device time of ``fn`` (CUDA events on the current stream)."""
+    for _ in range(warmup):
+        if before:
+            before()
+        fn()
+    out = []
+    for _ in range(reps):
+        if before:
+            before()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.median(out)
+
+
+def tune_knob(knob: str, fn: Callable[[], None], candidates: Iterable[int] = None, reps: int = 5,
+              before: Callable[[], None] = None) -> Dict[str, object]:
+    """Time ``fn`` under each candidate value of ``knob``, set the fastest, return the record."""
+    cands = tuple(CANDIDATES[knob] if candidates is None else candidates)
+    times = {}
+    for v in cands:
+        _lib.tune_set(knob, v)
+        times[v] = time_ms(fn, reps=reps, before=before)
+    best = min(times, key=times.get)
+    _lib.tune_set(knob, best)
+    return {"knob": knob, "best": best, "ms": {str(k): round(t, 4) for k, t in times.items()}}
+
+
+def tune_hot_path(hp, field, rays_o, rays_d, reps: int = 5):
+    """Tune the knobs of one ``pipeline.HotPath`` on one batch of rays (leaves its buffers holding that batch)."""
+    rec = []
+    rec.append(tune_knob("march_tile_rays", lambda: hp.march(rays_o, rays_d), reps=reps))
+    hp.march(rays_o, rays_d)
+    M = int(hp.n_m.item())
+    hp.field_marched(field, rays_o, rays_d, M)
+    rec.append(tune_knob("prune_tile_rays", lambda: hp.prune(M), reps=reps))
+    hp.prune(M)
+    S = int(hp.n_k.item())
+    hp.field_kept(field, rays_o, rays_d, S)
+    rec.append(tune_knob("render_fwd_prefetch", lambda: hp.render_fwd(S), reps=reps))
+    torch.cuda.synchronize()
+    hp.check_status("autotune")
+    return {r["knob"]: r for r in rec}

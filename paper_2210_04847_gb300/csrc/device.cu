@@ -24,7 +24,33 @@ DeviceInfo current_device() {
     return info;
 }
 
+namespace {
+// Tuned launch-shape table: one int per knob, read at every launch.
+int g_tune[NACC_TUNE_COUNT] = {
+    1,  // NACC_TUNE_RENDER_FWD_PREFETCH
+    8,  // NACC_TUNE_MARCH_TILE_RAYS (upper bound; long lattices use fewer)
+    8,  // NACC_TUNE_PRUNE_TILE_RAYS
+};
+const int g_tune_lo[NACC_TUNE_COUNT] = {0, 1, 2};
+const int g_tune_hi[NACC_TUNE_COUNT] = {1, 32, 32};
+}  // namespace
+
+int tune_get(int knob) { return (knob >= 0 && knob < NACC_TUNE_COUNT) ? g_tune[knob] : 0; }
+
 }  // namespace nacc
+
+extern "C" int nacc_tune_set(int knob, int value) {
+    if (knob < 0 || knob >= NACC_TUNE_COUNT) return NACC_ERR_INVALID_ARG;
+    if (value < nacc::g_tune_lo[knob] || value > nacc::g_tune_hi[knob]) return NACC_ERR_INVALID_ARG;
+    if (knob == NACC_TUNE_PRUNE_TILE_RAYS && (value & 1)) return NACC_ERR_INVALID_ARG;
+    nacc::g_tune[knob] = value;
+    return NACC_OK;
+}
+
+extern "C" int nacc_tune_get(int knob) {
+    if (knob < 0 || knob >= NACC_TUNE_COUNT) return NACC_ERR_INVALID_ARG;
+    return nacc::g_tune[knob];
+}
 
 extern "C" const char* nacc_error_string(int code) {
     switch (code) {

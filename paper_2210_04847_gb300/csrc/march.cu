@@ -7,17 +7,21 @@
 // bit-reproducible (it is an integer result decided by float arithmetic).
 //
 // Design (single pass, no count/fill split):
-//   * A persistent grid of blocks takes tiles of rays in ticket order.
-//   * Uniform steps: one warp per ray, lane j evaluates lattice point 32c + j
-//     (the lattice is closed-form, t_k = near + k*dt), the occupancy test of
-//     the 32 midpoints is turned into one __ballot_sync word kept in shared
-//     memory, and __popc gives the ray's count.
+//   * Every warp works on its own tiles of consecutive rays, taken from a
+//     global atomic ticket (tile order = ticket order). No block-wide barrier
+//     is ever taken: each warp keeps its tile's ballot words in a private
+//     slice of shared memory.
+//   * Uniform steps: the warp walks one ray at a time, lane j evaluating
+//     lattice point 32c + j (the lattice is closed-form, t_k = near + k*dt);
+//     the occupancy test of the 32 midpoints becomes one __ballot_sync word and
+//     __popc gives the count. Lane i of the warp keeps ray i's count, chunk
+//     count and [near, far].
 //   * Cone steps (t_{k+1} = t_k + clamp(t_k*cone, dt_min, dt_max)): the
 //     lattice is a sequential float32 recurrence, so one thread walks one ray;
 //     it counts first and walks again to write.
-//   * The tile's sample total is turned into a global offset by a bounded
-//     decoupled look-back over earlier tiles; the warp then re-expands the
-//     ballot words into compacted, coalesced stores of (t_start, t_end, ray).
+//   * The tile's total becomes its global offset through a bounded decoupled
+//     look-back run by the warp itself; the warp then re-expands the ballot
+//     words into compacted, coalesced stores of (t_start, t_end, ray).
 #include <math.h>
 #include <string.h>
 
@@ -28,8 +32,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kTileUniform = 32;   // rays per tile, warp-per-ray walk
-constexpr int kTileCone = kThreads;  // rays per tile, thread-per-ray walk
+constexpr int kTileRaysMax = 32;  // rays per warp tile (uniform steps), lane i holds ray i
+constexpr int kTileCone = kThreads;  // rays per block tile (cone steps, thread-per-ray walk)
 
 struct Levels {
     float lo[NACC_MAX_LEVELS][3];
@@ -62,6 +66,7 @@ struct MarchArgs {
     unsigned int* ticket;
     int32_t n_tiles;
     int32_t mask_words;
+    int32_t tile_rays;
     Levels L;
 };
 
@@ -107,19 +112,20 @@ __device__ __forceinline__ int slot_of(const MarchArgs& a, int r) {
 }
 
 // Occupancy bit of point x: finest level whose box holds x, floor cell index.
+// i = floor(u) with 0 <= i < res is the same test as 0 <= u < res followed by
+// truncation (u is finite here: o, d and the lattice are finite).
 template <int MAXL>
 __device__ __forceinline__ bool occupied(const MarchArgs& a, float x0, float x1, float x2,
                                          unsigned slot_level0) {
 #pragma unroll
     for (int l = 0; l < MAXL; ++l) {
         if (l >= a.n_levels) break;
-        float u0 = __fmul_rn(__fsub_rn(x0, a.L.lo[l][0]), a.L.scale[l][0]);
-        float u1 = __fmul_rn(__fsub_rn(x1, a.L.lo[l][1]), a.L.scale[l][1]);
-        float u2 = __fmul_rn(__fsub_rn(x2, a.L.lo[l][2]), a.L.scale[l][2]);
-        if (u0 >= 0.0f && u0 < a.fres0 && u1 >= 0.0f && u1 < a.fres1 && u2 >= 0.0f && u2 < a.fres2) {
-            unsigned ix = (unsigned)u0, iy = (unsigned)u1, iz = (unsigned)u2;
-            unsigned cell = (((slot_level0 + l) * a.res0 + ix) * a.res1 + iy) * a.res2 + iz;
-            unsigned w = __ldg(a.bits + (cell >> 5));
+        const int i0 = __float2int_rd(__fmul_rn(__fsub_rn(x0, a.L.lo[l][0]), a.L.scale[l][0]));
+        const int i1 = __float2int_rd(__fmul_rn(__fsub_rn(x1, a.L.lo[l][1]), a.L.scale[l][1]));
+        const int i2 = __float2int_rd(__fmul_rn(__fsub_rn(x2, a.L.lo[l][2]), a.L.scale[l][2]));
+        if ((unsigned)i0 < (unsigned)a.res0 && (unsigned)i1 < (unsigned)a.res1 && (unsigned)i2 < (unsigned)a.res2) {
+            const unsigned cell = (((slot_level0 + l) * a.res0 + i0) * a.res1 + i1) * a.res2 + i2;
+            const unsigned w = __ldg(a.bits + (cell >> 5));
             return (w >> (cell & 31u)) & 1u;
         }
     }
@@ -130,43 +136,44 @@ __device__ __forceinline__ float lattice_t(float near, int k, float dt) {
     return __fadd_rn(near, __fmul_rn(__int2float_rn(k), dt));
 }
 
+// Number of lattice intervals of a ray: the k < max_steps with t_k < far. t_k is
+// non-decreasing in k, so it is the first k with t_k >= far (capped): a guess from
+// real arithmetic, then the exact float32 test moves it to the boundary (the
+// guess is off by at most a few steps).
+__device__ __forceinline__ int lattice_count(const MarchArgs& a, float near, float far, float dt) {
+    float g = (far - near) / dt;
+    int e = g < (float)a.max_steps ? (int)g : a.max_steps;
+    if (e < 0) e = 0;
+    while (e > 0 && !(lattice_t(near, e - 1, dt) < far)) --e;
+    while (e < a.max_steps && lattice_t(near, e, dt) < far) ++e;
+    return e;
+}
+
 // ---------------------------------------------------------------------------
 // uniform steps: warp per ray
 // ---------------------------------------------------------------------------
 
 template <int MAXL>
 __global__ void __launch_bounds__(kThreads) march_uniform_kernel(const MarchArgs a) {
-    extern __shared__ uint32_t s_masks[];  // [kTileUniform][mask_words]
-    __shared__ int s_count[kTileUniform];
-    __shared__ int s_nchunks[kTileUniform];
-    __shared__ float s_near[kTileUniform];
-    __shared__ float s_far[kTileUniform];
-    __shared__ int s_excl[kTileUniform];
-    __shared__ int s_tile;
-    __shared__ int s_next;
-    __shared__ long long s_tile_excl;
-
+    extern __shared__ uint32_t s_masks[];  // per warp: [tile_rays][mask_words]
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    uint32_t* wmask = s_masks + (size_t)warp * a.tile_rays * a.mask_words;
     const float dt = a.dt_min;
+    const unsigned lt = lanemask_lt();
 
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_tile = (int)atomicAdd(a.ticket, 1u);
-            s_next = 0;
-        }
-        __syncthreads();
-        const int tile = s_tile;
+        int tile = 0;
+        if (lane == 0) tile = (int)atomicAdd(a.ticket, 1u);
+        tile = __shfl_sync(FULL, tile, 0);
         if (tile >= a.n_tiles) break;
-        const int ray0 = tile * kTileUniform;
-        const int nr = min(kTileUniform, a.n_rays - ray0);
+        const int ray0 = tile * a.tile_rays;
+        const int nr = min(a.tile_rays, a.n_rays - ray0);
 
-        // phase 1: walk the lattice of every ray of the tile, ballot words -> smem
-        for (;;) {
-            int i = 0;
-            if (lane == 0) i = atomicAdd(&s_next, 1);
-            i = __shfl_sync(FULL, i, 0);
-            if (i >= nr) break;
+        // phase 1: walk the lattice of each ray of the tile, one ballot word per 32 points
+        int my_count = 0, my_nch = 0;
+        float my_near = 0.0f, my_far = 0.0f;
+        for (int i = 0; i < nr; ++i) {
             const int r = ray0 + i;
             float o[3], d[3];
 #pragma unroll
@@ -175,21 +182,22 @@ __global__ void __launch_bounds__(kThreads) march_uniform_kernel(const MarchArgs
                 d[k] = __ldg(a.rays_d + 3 * (size_t)r + k);
             }
             float near = 0.0f, far = 0.0f;
-            int count = 0, c = 0;
+            int count = 0, nch = 0;
             const int slot = slot_of(a, r);
             const bool slot_ok = slot >= 0 && slot < a.n_slots;
             if (!slot_ok && lane == 0) raise_status(a.d_status, NACC_STATUS_BAD_INDEX);
             if (slot_ok && clip_ray(a, o, d, near, far)) {
+                const int nk = lattice_count(a, near, far, dt);
+                nch = (nk + 31) >> 5;
                 const unsigned sl0 = (unsigned)slot * (unsigned)a.n_levels;
-                uint32_t* row = s_masks + (size_t)i * a.mask_words;
-                for (; c < a.mask_words; ++c) {
+                uint32_t* row = wmask + i * a.mask_words;
+                for (int c = 0; c < nch; ++c) {
                     const int k = (c << 5) + lane;
-                    const float ts = lattice_t(near, k, dt);
-                    const bool valid = (k < a.max_steps) && (ts < far);
-                    if (__ballot_sync(FULL, valid) == 0u) break;
                     bool occ = false;
-                    if (valid) {
-                        const float tn = lattice_t(near, k + 1, dt);
+                    if (k < nk) {
+                        const float kf = __int2float_rn(k);
+                        const float ts = __fadd_rn(near, __fmul_rn(kf, dt));
+                        const float tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
                         const float te = tn < far ? tn : far;
                         const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
                         const float x0 = __fadd_rn(o[0], __fmul_rn(d[0], mid));
@@ -202,68 +210,61 @@ __global__ void __launch_bounds__(kThreads) march_uniform_kernel(const MarchArgs
                     count += __popc(m);
                 }
             }
-            if (lane == 0) {
-                s_count[i] = count;
-                s_nchunks[i] = c;
-                s_near[i] = near;
-                s_far[i] = far;
+            if (lane == i) {
+                my_count = count;
+                my_nch = nch;
+                my_near = near;
+                my_far = far;
             }
         }
-        __syncthreads();
+        __syncwarp();
 
-        // phase 2: tile prefix, then the tile's global offset by look-back
-        if (warp == 0) {
-            const int cnt = lane < nr ? s_count[lane] : 0;
-            const int incl = warp_incl_scan_int(cnt, lane);
-            s_excl[lane] = incl - cnt;
-            const int agg = __shfl_sync(FULL, incl, 31);
-            const unsigned long long excl =
-                lookback(a.tile_status, tile, (unsigned long long)agg, lane, a.d_status);
-            if (lane == 0) {
-                s_tile_excl = (long long)excl;
-                if (tile == a.n_tiles - 1) {
-                    const long long total = (long long)excl + agg;
-                    *a.n_samples = total;
-                    if (total > a.capacity) raise_status(a.d_status, NACC_STATUS_CAPACITY);
-                    if (total > 0x7fffffffLL) raise_status(a.d_status, NACC_STATUS_OVERFLOW);
-                }
-            }
+        // phase 2: offsets inside the tile, then the tile's offset by look-back
+        const int incl = warp_incl_scan_int(my_count, lane);
+        const int agg = __shfl_sync(FULL, incl, 31);
+        const long long excl = (long long)lookback(a.tile_status, tile, (unsigned long long)agg, lane, a.d_status);
+        const int my_excl = incl - my_count;
+        if (lane < nr) {
+            const int2 pi = make_int2((int)(excl + my_excl), my_count);
+            reinterpret_cast<int2*>(a.packed_info)[ray0 + lane] = pi;
         }
-        __syncthreads();
+        if (lane == 0 && tile == a.n_tiles - 1) {
+            const long long total = excl + agg;
+            *a.n_samples = total;
+            if (total > a.capacity) raise_status(a.d_status, NACC_STATUS_CAPACITY);
+            if (total > 0x7fffffffLL) raise_status(a.d_status, NACC_STATUS_OVERFLOW);
+        }
 
-        // phase 3: expand the ballot words into compacted, coalesced stores
-        const long long tile_excl = s_tile_excl;
-        for (int i = warp; i < nr; i += kWarps) {
-            const int r = ray0 + i;
-            const int cnt = s_count[i];
-            const long long off = tile_excl + s_excl[i];
-            if (lane == 0) {
-                a.packed_info[2 * (size_t)r] = (int32_t)off;
-                a.packed_info[2 * (size_t)r + 1] = cnt;
-            }
-            if (cnt == 0) continue;
-            const float near = s_near[i], far = s_far[i];
-            const uint32_t* row = s_masks + (size_t)i * a.mask_words;
-            const int nch = s_nchunks[i];
-            long long base = off;
-            for (int c = 0; c < nch; ++c) {
-                const unsigned m = row[c];
-                if (m == 0u) continue;
-                if ((m >> lane) & 1u) {
-                    const int k = (c << 5) + lane;
-                    const long long pos = base + __popc(m & lanemask_lt());
-                    if (pos < a.capacity) {
-                        const float ts = lattice_t(near, k, dt);
-                        const float tn = lattice_t(near, k + 1, dt);
+        // phase 3: expand the ballot words into compacted, coalesced stores. Output
+        // positions fit 32 bits: the tile starts below capacity <= 2^31 - 1 and adds
+        // at most tile_rays * max_steps <= 2^18 samples.
+        if (excl < a.capacity) {
+            const unsigned cap = (unsigned)(a.capacity < 0x7fffffffLL ? a.capacity : 0x7fffffffLL);
+            for (int i = 0; i < nr; ++i) {
+                const int cnt = __shfl_sync(FULL, my_count, i);
+                if (cnt == 0) continue;
+                const int nch = __shfl_sync(FULL, my_nch, i);
+                const float near = __shfl_sync(FULL, my_near, i);
+                const float far = __shfl_sync(FULL, my_far, i);
+                const int r = ray0 + i;
+                const uint32_t* row = wmask + i * a.mask_words;
+                unsigned base = (unsigned)excl + (unsigned)__shfl_sync(FULL, my_excl, i);
+                for (int c = 0; c < nch; ++c) {
+                    const unsigned m = row[c];
+                    const unsigned pos = base + __popc(m & lt);
+                    if (((m >> lane) & 1u) && pos < cap) {
+                        const float kf = __int2float_rn((c << 5) + lane);
+                        const float ts = __fadd_rn(near, __fmul_rn(kf, dt));
+                        const float tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
                         a.t_starts[pos] = ts;
                         a.t_ends[pos] = tn < far ? tn : far;
                         a.ray_indices[pos] = r;
                     }
+                    base += __popc(m);
                 }
-                base += __popc(m);
             }
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
@@ -383,9 +384,20 @@ constexpr size_t kTicketBytes = 256;
 
 int mask_words_for(int32_t max_steps) { return (max_steps + 31) / 32; }
 
+// Rays per warp tile: up to 8, fewer when long lattices make the ballot rows
+// big (the warp's shared-memory slice stays within kWarpSmemBudget bytes).
+constexpr size_t kWarpSmemBudget = 4096;
+int tile_rays_for(int mask_words) {
+    int t = (int)(kWarpSmemBudget / ((size_t)mask_words * sizeof(uint32_t)));
+    const int cap = tune_get(NACC_TUNE_MARCH_TILE_RAYS);
+    if (t > cap) t = cap;
+    if (t < 1) t = 1;
+    return t;
+}
+
 size_t workspace_bytes_for(int32_t n_rays) {
-    const size_t tiles = (size_t)(n_rays + kTileUniform - 1) / kTileUniform;
-    return align_up(kTicketBytes + tiles * sizeof(unsigned long long), 256);
+    // the smallest warp tile is one ray: size for one status word per ray
+    return align_up(kTicketBytes + (size_t)n_rays * sizeof(unsigned long long), 256);
 }
 
 // Level boxes and cell scales, float32, in the order the method defines them.
@@ -415,14 +427,14 @@ void make_levels(const nacc_grid& g, Levels& L) {
 }
 
 template <typename K>
-int blocks_for(K kernel, size_t smem, int n_tiles) {
+int blocks_for(K kernel, size_t smem, int n_work_blocks) {
     const DeviceInfo dev = current_device();
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     const int want = dev.sm_count * per_sm;
-    return n_tiles < want ? n_tiles : want;
+    return n_work_blocks < want ? n_work_blocks : want;
 }
 
 }  // namespace
@@ -459,6 +471,7 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
         if (!(grid->aabb[k] < grid->aabb[3 + k])) return NACC_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < workspace_bytes_for(n_rays)) return NACC_ERR_INVALID_ARG;
     if (((uintptr_t)workspace & 255u) != 0) return NACC_ERR_INVALID_ARG;
+    if (((uintptr_t)packed_info & 7u) != 0) return NACC_ERR_INVALID_ARG;
 
     cudaStream_t st = (cudaStream_t)stream;
     if (n_rays == 0) return launch_status(cudaMemsetAsync(n_samples, 0, sizeof(int64_t), st));
@@ -495,10 +508,11 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
     a.ticket = (unsigned int*)workspace;
     a.tile_status = (unsigned long long*)((char*)workspace + kTicketBytes);
     a.mask_words = mask_words_for(p->max_steps);
+    a.tile_rays = tile_rays_for(a.mask_words);
     make_levels(*grid, a.L);
 
     const bool cone = p->cone > 0.0f;
-    a.n_tiles = cone ? (n_rays + kTileCone - 1) / kTileCone : (n_rays + kTileUniform - 1) / kTileUniform;
+    a.n_tiles = cone ? (n_rays + kTileCone - 1) / kTileCone : (n_rays + a.tile_rays - 1) / a.tile_rays;
     const size_t clear = kTicketBytes + (size_t)a.n_tiles * sizeof(unsigned long long);
     cudaError_t e = cudaMemsetAsync(workspace, 0, clear, st);
     if (e != cudaSuccess) return NACC_ERR_CUDA;
@@ -512,17 +526,17 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
             march_cone_kernel<NACC_MAX_LEVELS><<<blocks, kThreads, 0, st>>>(a);
         }
     } else {
-        const size_t smem = (size_t)kTileUniform * a.mask_words * sizeof(uint32_t);
+        const size_t smem = (size_t)kWarps * a.tile_rays * a.mask_words * sizeof(uint32_t);
         if (a.n_levels == 1) {
             if (smem > 48 * 1024)
                 cudaFuncSetAttribute(march_uniform_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            const int blocks = blocks_for(march_uniform_kernel<1>, smem, a.n_tiles);
+            const int blocks = blocks_for(march_uniform_kernel<1>, smem, (a.n_tiles + kWarps - 1) / kWarps);
             march_uniform_kernel<1><<<blocks, kThreads, smem, st>>>(a);
         } else {
             if (smem > 48 * 1024)
                 cudaFuncSetAttribute(march_uniform_kernel<NACC_MAX_LEVELS>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            const int blocks = blocks_for(march_uniform_kernel<NACC_MAX_LEVELS>, smem, a.n_tiles);
+            const int blocks = blocks_for(march_uniform_kernel<NACC_MAX_LEVELS>, smem, (a.n_tiles + kWarps - 1) / kWarps);
             march_uniform_kernel<NACC_MAX_LEVELS><<<blocks, kThreads, smem, st>>>(a);
         }
     }

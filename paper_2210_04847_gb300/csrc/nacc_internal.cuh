@@ -71,12 +71,12 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 //
 // Tile j publishes one 64-bit word: flag in bits 62..63 (1 = aggregate of the
 // tile alone, 2 = inclusive prefix through the tile), value in bits 0..61.
-// Tiles are numbered by an atomic ticket taken when a block starts work on
-// them, so every tile a block waits for is held by a block that is already
+// Tiles are numbered by an atomic ticket taken when a warp starts work on
+// them, so every tile a warp waits for is held by a warp that is already
 // running and publishes its aggregate without waiting: the wait always ends.
-// It is still bounded: after kSpinLimit polls the block reports
+// It is still bounded: after kSpinLimit polls the warp reports
 // NACC_STATUS_TIMEOUT, stops waiting, and publishes a (wrong) prefix so that
-// no other block waits on it either.
+// no other warp waits on it either.
 
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
@@ -151,6 +151,9 @@ struct DeviceInfo {
 };
 
 DeviceInfo current_device();
+
+// Current value of a tuning knob (NACC_TUNE_*), the library default unless set.
+int tune_get(int knob);
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 

@@ -3,15 +3,18 @@
 // Sec. 2.1 "Pruning Empty and Occluded Regions"; early_stop_eps and
 // alpha_thre of the Sec. 3 listing).
 //
-// Single pass over the input samples: per ray, a warp walks its samples in
-// chunks of 32 with coalesced loads, forms tau = sigma*delta, the exclusive
-// optical depth by a warp shuffle scan plus a running carry, and the keep
-// decision; one __ballot_sync word per chunk goes to a workspace row of the
-// ray. Once the optical depth passes -ln(eps) the rest of the ray is dropped
-// without being read. A bounded decoupled look-back turns the tile's kept
-// count into its output offset, and the warps re-expand the ballot words into
-// compacted stores. Compiled with -fmad=false (tau and the scan are explicitly
-// rounded float32 operations).
+// Single pass over the input samples. Each warp takes tiles of 8 consecutive
+// rays from an atomic ticket and walks two rays at a time (two independent
+// load streams), in chunks of 64 samples: lane j loads samples 2j and 2j+1 of
+// the chunk as one 8-byte vector per array (chunks start at an even index).
+// It forms tau = sigma*delta, the exclusive optical depth by a warp shuffle
+// scan of the lane pairs plus a running carry, and the keep decisions; two
+// __ballot_sync words per chunk (even and odd samples) go to a workspace row of
+// the ray. Once the optical depth passes -ln(eps) the rest of the ray is
+// dropped without being read. A bounded decoupled look-back run by the warp
+// turns the tile's kept count into its output offset, and the warp re-expands
+// the ballot words into compacted stores. Compiled with -fmad=false (tau and the
+// scan are explicitly rounded float32 operations).
 #include <math.h>
 #include <string.h>
 
@@ -21,8 +24,7 @@ namespace nacc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int kTile = 32;
+constexpr int kTileMax = 32;  // rays per warp tile (tuned, even); lane i holds ray i's run and results
 constexpr size_t kTicketBytes = 256;
 
 struct PruneArgs {
@@ -47,158 +49,234 @@ struct PruneArgs {
     unsigned long long* examined;  // input samples read, summed over rays (diagnostic)
     uint32_t* masks;
     int32_t n_tiles;
+    int32_t tile_rays;
 };
 
+// Row of ballot words of ray r whose run starts at `off`: two words per 64-sample
+// chunk. Rows of rays with ascending, disjoint runs never overlap: ray r needs at
+// most floor(cnt/32) + 2 words and the next row starts at least that far on.
+__device__ __forceinline__ uint32_t* mask_row(const PruneArgs& a, int off, int r) {
+    return a.masks + (off >> 5) + 2 * (size_t)r;
+}
+
+// One ray's walk state inside phase 1.
+struct RayWalk {
+    int off, cnt, abase, nch, c, count;
+    float carry;
+    uint32_t* row;
+    bool live;
+};
+
+__device__ __forceinline__ void walk_init(RayWalk& w, const PruneArgs& a, int off, int cnt, int r) {
+    w.off = off;
+    w.cnt = cnt;
+    w.abase = off & ~1;
+    w.nch = cnt > 0 ? (cnt + (off & 1) + 63) >> 6 : 0;
+    w.c = 0;
+    w.count = 0;
+    w.carry = 0.0f;
+    w.row = mask_row(a, off, r);
+    w.live = w.nch > 0;
+}
+
+struct Pair {
+    float s0[2], s1[2], sg[2];
+};
+
+// Samples j0 = abase + 64c + 2*lane and j0 + 1 (only those inside the array are read).
+__device__ __forceinline__ void walk_load(const RayWalk& w, const PruneArgs& a, int lane, Pair& p) {
+    p.s0[0] = p.s0[1] = p.s1[0] = p.s1[1] = p.sg[0] = p.sg[1] = 0.0f;
+    if (!w.live) return;
+    const long long j0 = (long long)w.abase + ((long long)w.c << 6) + 2 * lane;
+    if (j0 + 1 >= w.off && j0 < (long long)w.off + w.cnt) {
+        if (j0 + 1 < a.n_samples) {
+            const float2 u = __ldg(reinterpret_cast<const float2*>(a.t_starts + j0));
+            const float2 v = __ldg(reinterpret_cast<const float2*>(a.t_ends + j0));
+            const float2 g = __ldg(reinterpret_cast<const float2*>(a.sigmas + j0));
+            p.s0[0] = u.x; p.s0[1] = u.y;
+            p.s1[0] = v.x; p.s1[1] = v.y;
+            p.sg[0] = g.x; p.sg[1] = g.y;
+        } else {
+            p.s0[0] = __ldg(a.t_starts + j0);
+            p.s1[0] = __ldg(a.t_ends + j0);
+            p.sg[0] = __ldg(a.sigmas + j0);
+        }
+    }
+}
+
+// Decide one chunk of 64 samples of the ray (call with w.live, warp-uniform).
+__device__ __forceinline__ void walk_step(RayWalk& w, const PruneArgs& a, int lane, const Pair& p) {
+    const long long j0 = (long long)w.abase + ((long long)w.c << 6) + 2 * lane;
+    const long long end = (long long)w.off + w.cnt;
+    const bool v0 = j0 >= w.off && j0 < end;
+    const bool v1 = j0 + 1 >= w.off && j0 + 1 < end;
+    const float tau0 = v0 ? __fmul_rn(p.sg[0], __fsub_rn(p.s1[0], p.s0[0])) : 0.0f;
+    const float tau1 = v1 ? __fmul_rn(p.sg[1], __fsub_rn(p.s1[1], p.s0[1])) : 0.0f;
+    const float incl = warp_incl_scan(__fadd_rn(tau0, tau1), lane);
+    float excl = __shfl_up_sync(FULL, incl, 1);
+    if (lane == 0) excl = 0.0f;
+    const float O0 = __fadd_rn(w.carry, excl);
+    const float O1 = __fadd_rn(O0, tau0);
+    bool k0 = v0, k1 = v1;
+    if (a.use_t) {
+        k0 = k0 && (O0 <= a.thr_o);
+        k1 = k1 && (O1 <= a.thr_o);
+    }
+    if (a.use_a) {
+        k0 = k0 && (tau0 >= a.thr_tau);
+        k1 = k1 && (tau1 >= a.thr_tau);
+    }
+    const unsigned m0 = __ballot_sync(FULL, k0);
+    const unsigned m1 = __ballot_sync(FULL, k1);
+    if (lane == 0) {
+        w.row[2 * w.c] = m0;
+        w.row[2 * w.c + 1] = m1;
+    }
+    w.count += __popc(m0) + __popc(m1);
+    w.carry = __fadd_rn(w.carry, __shfl_sync(FULL, incl, 31));
+    ++w.c;
+    // every later O_i >= carry once tau >= 0: the rest of the ray is dropped unread
+    if (w.c >= w.nch || (a.use_t && !(w.carry <= a.thr_o))) w.live = false;
+}
+
 __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a) {
-    __shared__ int s_count[kTile];
-    __shared__ int s_nch[kTile];
-    __shared__ int s_off[kTile];
-    __shared__ int s_cnt[kTile];
-    __shared__ int s_excl[kTile];
-    __shared__ int s_tile;
-    __shared__ int s_next;
-    __shared__ int s_examined;
-    __shared__ long long s_tile_excl;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
 
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_tile = (int)atomicAdd(a.ticket, 1u);
-            s_next = 0;
-            s_examined = 0;
-        }
-        __syncthreads();
-        const int tile = s_tile;
+        int tile = 0;
+        if (lane == 0) tile = (int)atomicAdd(a.ticket, 1u);
+        tile = __shfl_sync(FULL, tile, 0);
         if (tile >= a.n_tiles) break;
-        const int ray0 = tile * kTile;
-        const int nr = min(kTile, a.n_rays - ray0);
+        const int ray0 = tile * a.tile_rays;
+        const int nr = min(a.tile_rays, a.n_rays - ray0);
 
-        // phase 1: decisions, one ballot word per 32 samples
-        for (;;) {
-            int i = 0;
-            if (lane == 0) i = atomicAdd(&s_next, 1);
-            i = __shfl_sync(FULL, i, 0);
-            if (i >= nr) break;
-            const int r = ray0 + i;
-            int off = a.packed_info[2 * (size_t)r];
-            int cnt = a.packed_info[2 * (size_t)r + 1];
-            // runs must be in bounds, ascending and disjoint in ray order (the
-            // layout marching and pruning produce): the ballot rows of the rays
-            // then never overlap
-            bool bad = off < 0 || cnt < 0 || (long long)off + cnt > a.n_samples;
-            if (r > 0) {
-                const long long prev_end = (long long)a.packed_info[2 * (size_t)r - 2] + a.packed_info[2 * (size_t)r - 1];
-                if ((long long)off < prev_end && cnt > 0) bad = true;
+        // runs of the tile's rays: must be in bounds, ascending and disjoint in ray
+        // order (the layout marching and pruning produce), so that the ballot rows
+        // of different rays never overlap
+        int my_off = 0, my_cnt = 0;
+        if (lane < nr) {
+            const int2 v = reinterpret_cast<const int2*>(a.packed_info)[ray0 + lane];
+            my_off = v.x;
+            my_cnt = v.y;
+        }
+        long long prev_end = __shfl_up_sync(FULL, (long long)my_off + my_cnt, 1);
+        if (lane == 0) {
+            prev_end = 0;
+            if (ray0 > 0) {
+                const int2 v = reinterpret_cast<const int2*>(a.packed_info)[ray0 - 1];
+                prev_end = (long long)v.x + v.y;
             }
+        }
+        if (lane < nr) {
+            bool bad = my_off < 0 || my_cnt < 0 || (long long)my_off + my_cnt > a.n_samples;
+            if (my_cnt > 0 && (long long)my_off < prev_end && (ray0 + lane) > 0) bad = true;
             if (bad) {
-                if (lane == 0) raise_status(a.d_status, NACC_STATUS_BAD_PACKED);
-                off = 0;
-                cnt = 0;
-            }
-            uint32_t* row = a.masks + (off >> 5) + r;
-            const int nch = (cnt + 31) >> 5;
-            float carry = 0.0f;
-            int count = 0, c = 0;
-            for (; c < nch; ++c) {
-                const int j = (c << 5) + lane;
-                const bool valid = j < cnt;
-                float tau = 0.0f;
-                if (valid) {
-                    const size_t idx = (size_t)off + j;
-                    const float s0 = __ldg(a.t_starts + idx);
-                    const float s1 = __ldg(a.t_ends + idx);
-                    const float sg = __ldg(a.sigmas + idx);
-                    tau = __fmul_rn(sg, __fsub_rn(s1, s0));
-                }
-                const float incl = warp_incl_scan(tau, lane);
-                float excl = __shfl_up_sync(FULL, incl, 1);
-                if (lane == 0) excl = 0.0f;
-                const float O = __fadd_rn(carry, excl);
-                bool keep = valid;
-                if (a.use_t && !(O <= a.thr_o)) keep = false;
-                if (a.use_a && !(tau >= a.thr_tau)) keep = false;
-                const unsigned m = __ballot_sync(FULL, keep);
-                if (lane == 0) row[c] = m;
-                count += __popc(m);
-                carry = __fadd_rn(carry, __shfl_sync(FULL, incl, 31));
-                if (a.use_t && !(carry <= a.thr_o)) {  // every later O_i >= carry: all dropped
-                    ++c;
-                    break;
-                }
-            }
-            if (lane == 0) {
-                s_count[i] = count;
-                s_nch[i] = c;
-                s_off[i] = off;
-                s_cnt[i] = cnt;
-                atomicAdd(&s_examined, min(cnt, c << 5));
+                raise_status(a.d_status, NACC_STATUS_BAD_PACKED);
+                my_off = 0;
+                my_cnt = 0;
             }
         }
-        __syncthreads();
 
-        if (warp == 0) {
-            const int cnt = lane < nr ? s_count[lane] : 0;
-            const int incl = warp_incl_scan_int(cnt, lane);
-            s_excl[lane] = incl - cnt;
-            const int agg = __shfl_sync(FULL, incl, 31);
-            const unsigned long long excl =
-                lookback(a.tile_status, tile, (unsigned long long)agg, lane, a.d_status);
-            if (lane == 0) {
-                s_tile_excl = (long long)excl;
-                atomicAdd(a.examined, (unsigned long long)s_examined);
-                if (tile == a.n_tiles - 1) {
-                    const long long total = (long long)excl + agg;
-                    *a.n_kept = total;
-                    if (total > a.capacity) raise_status(a.d_status, NACC_STATUS_CAPACITY);
-                    if (total > 0x7fffffffLL) raise_status(a.d_status, NACC_STATUS_OVERFLOW);
-                }
+        // phase 1: decisions, rays in pairs so two independent load streams are in flight
+        int my_count = 0, my_nch = 0;
+        for (int i = 0; i < nr; i += 2) {
+            RayWalk A, B;
+            walk_init(A, a, __shfl_sync(FULL, my_off, i), __shfl_sync(FULL, my_cnt, i), ray0 + i);
+            const int offB = __shfl_sync(FULL, my_off, (i + 1) & 31);
+            const int cntB = __shfl_sync(FULL, my_cnt, (i + 1) & 31);
+            walk_init(B, a, offB, i + 1 < nr ? cntB : 0, ray0 + i + 1);
+            while (A.live || B.live) {
+                Pair pa, pb;
+                walk_load(A, a, lane, pa);
+                walk_load(B, a, lane, pb);
+                if (A.live) walk_step(A, a, lane, pa);
+                if (B.live) walk_step(B, a, lane, pb);
+            }
+            if (lane == i) {
+                my_count = A.count;
+                my_nch = A.c;
+            }
+            if (lane == i + 1) {
+                my_count = B.count;
+                my_nch = B.c;
             }
         }
-        __syncthreads();
+        __syncwarp();
 
-        // phase 3: compacted stores of the kept samples
-        const long long tile_excl = s_tile_excl;
-        for (int i = warp; i < nr; i += kWarps) {
+        // phase 2: offsets inside the tile, then the tile's offset by look-back
+        const int incl = warp_incl_scan_int(my_count, lane);
+        const int agg = __shfl_sync(FULL, incl, 31);
+        int seen = lane < nr ? min(my_cnt, (my_nch << 6) - (my_off & 1)) : 0;
+        if (seen < 0) seen = 0;
+        for (int o = 16; o > 0; o >>= 1) seen += __shfl_xor_sync(FULL, seen, o);
+        const long long excl = (long long)lookback(a.tile_status, tile, (unsigned long long)agg, lane, a.d_status);
+        const int my_excl = incl - my_count;
+        if (lane < nr) {
+            const int2 pi = make_int2((int)(excl + my_excl), my_count);
+            reinterpret_cast<int2*>(a.packed_info_out)[ray0 + lane] = pi;
+        }
+        if (lane == 0) {
+            atomicAdd(a.examined, (unsigned long long)seen);
+            if (tile == a.n_tiles - 1) {
+                const long long total = excl + agg;
+                *a.n_kept = total;
+                if (total > a.capacity) raise_status(a.d_status, NACC_STATUS_CAPACITY);
+                if (total > 0x7fffffffLL) raise_status(a.d_status, NACC_STATUS_OVERFLOW);
+            }
+        }
+
+        // phase 3: compacted stores of the kept samples (and the optional mask)
+        for (int i = 0; i < nr; ++i) {
+            const int off = __shfl_sync(FULL, my_off, i);
+            const int cnt = __shfl_sync(FULL, my_cnt, i);
+            const int nch = __shfl_sync(FULL, my_nch, i);
             const int r = ray0 + i;
-            const int count = s_count[i];
-            const long long out = tile_excl + s_excl[i];
-            if (lane == 0) {
-                a.packed_info_out[2 * (size_t)r] = (int32_t)out;
-                a.packed_info_out[2 * (size_t)r + 1] = count;
-            }
-            const int off = s_off[i];
-            const int cnt = s_cnt[i];
-            const int nch = s_nch[i];
-            const uint32_t* row = a.masks + (off >> 5) + r;
-            long long base = out;
-            for (int c = 0; c < nch; ++c) {
-                const unsigned m = row[c];
-                const int j = (c << 5) + lane;
-                if (a.keep_mask && j < cnt) a.keep_mask[(size_t)off + j] = (uint8_t)((m >> lane) & 1u);
-                if (m == 0u) continue;
-                if ((m >> lane) & 1u) {
-                    const long long pos = base + __popc(m & lanemask_lt());
-                    if (pos < a.capacity) {
-                        const size_t idx = (size_t)off + j;
-                        a.t_starts_out[pos] = a.t_starts[idx];
-                        a.t_ends_out[pos] = a.t_ends[idx];
-                        a.ray_indices_out[pos] = r;
+            const long long end = (long long)off + cnt;
+            const long long abase = off & ~1;
+            const uint32_t* row = mask_row(a, off, r);
+            long long base = excl + __shfl_sync(FULL, my_excl, i);
+            for (int c0 = 0; c0 < nch; c0 += 16) {
+                // 16 chunks' ballot word pairs at once
+                const unsigned mw = (c0 + (lane >> 1) < nch) ? row[2 * c0 + lane] : 0u;
+                const int n = min(16, nch - c0);
+                for (int q = 0; q < n; ++q) {
+                    const unsigned m0 = __shfl_sync(FULL, mw, 2 * q);
+                    const unsigned m1 = __shfl_sync(FULL, mw, 2 * q + 1);
+                    const long long j0 = abase + ((long long)(c0 + q) << 6) + 2 * lane;
+                    const bool b0 = (m0 >> lane) & 1u, b1 = (m1 >> lane) & 1u;
+                    if (a.keep_mask) {
+                        if (j0 >= off && j0 < end) a.keep_mask[j0] = (uint8_t)b0;
+                        if (j0 + 1 >= off && j0 + 1 < end) a.keep_mask[j0 + 1] = (uint8_t)b1;
                     }
+                    const long long pos0 = base + __popc(m0 & lt) + __popc(m1 & lt);
+                    if (b0 && pos0 < a.capacity) {
+                        a.t_starts_out[pos0] = __ldg(a.t_starts + j0);
+                        a.t_ends_out[pos0] = __ldg(a.t_ends + j0);
+                        a.ray_indices_out[pos0] = r;
+                    }
+                    const long long pos1 = pos0 + (b0 ? 1 : 0);
+                    if (b1 && pos1 < a.capacity) {
+                        a.t_starts_out[pos1] = __ldg(a.t_starts + j0 + 1);
+                        a.t_ends_out[pos1] = __ldg(a.t_ends + j0 + 1);
+                        a.ray_indices_out[pos1] = r;
+                    }
+                    base += __popc(m0) + __popc(m1);
                 }
-                base += __popc(m);
             }
-            if (a.keep_mask)
-                for (int j = (nch << 5) + lane; j < cnt; j += 32) a.keep_mask[(size_t)off + j] = 0;
+            if (a.keep_mask) {
+                const long long from = abase + ((long long)nch << 6);
+                for (long long j = (from > off ? from : off) + lane; j < end; j += 32) a.keep_mask[j] = 0;
+            }
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
 size_t workspace_bytes_for(int32_t n_rays, int64_t n_samples) {
-    const size_t tiles = (size_t)(n_rays + kTile - 1) / kTile;
+    const size_t tiles = (size_t)(n_rays + 1) / 2;  // smallest tile: 2 rays
     const size_t head = align_up(kTicketBytes + tiles * sizeof(unsigned long long), 256);
-    const size_t words = (size_t)(n_samples >> 5) + (size_t)n_rays + 2;
+    const size_t words = (size_t)(n_samples >> 5) + 2 * (size_t)n_rays + 4;
     return align_up(head + words * sizeof(uint32_t), 256);
 }
 
@@ -227,6 +305,9 @@ extern "C" int nacc_prune_samples(const int32_t* packed_info, int32_t n_rays, co
     if (early_stop_eps != early_stop_eps || alpha_thre != alpha_thre) return NACC_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < workspace_bytes_for(n_rays, n_samples)) return NACC_ERR_INVALID_ARG;
     if (((uintptr_t)workspace & 255u) != 0) return NACC_ERR_INVALID_ARG;
+    if ((((uintptr_t)packed_info | (uintptr_t)packed_info_out | (uintptr_t)t_starts | (uintptr_t)t_ends |
+          (uintptr_t)sigmas) & 7u) != 0)
+        return NACC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     if (n_rays == 0) return launch_status(cudaMemsetAsync(n_kept, 0, sizeof(int64_t), st));
 
@@ -252,7 +333,8 @@ extern "C" int nacc_prune_samples(const int32_t* packed_info, int32_t n_rays, co
     a.n_kept = n_kept;
     a.keep_mask = keep_mask;
     a.d_status = d_status;
-    a.n_tiles = (n_rays + kTile - 1) / kTile;
+    a.tile_rays = tune_get(NACC_TUNE_PRUNE_TILE_RAYS);
+    a.n_tiles = (n_rays + a.tile_rays - 1) / a.tile_rays;
     a.ticket = (unsigned int*)workspace;
     a.examined = (unsigned long long*)((char*)workspace + 8);
     a.tile_status = (unsigned long long*)((char*)workspace + kTicketBytes);
@@ -267,7 +349,8 @@ extern "C" int nacc_prune_samples(const int32_t* packed_info, int32_t n_rays, co
         per_sm < 1)
         per_sm = 1;
     int blocks = dev.sm_count * per_sm;
-    if (blocks > a.n_tiles) blocks = a.n_tiles;
+    const int need = (a.n_tiles + kThreads / 32 - 1) / (kThreads / 32);
+    if (blocks > need) blocks = need;
     prune_kernel<<<blocks, kThreads, 0, st>>>(a);
     return launch_status(cudaGetLastError());
 }

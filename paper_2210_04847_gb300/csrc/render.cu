@@ -73,57 +73,214 @@ struct FwdArgs {
     int32_t* d_status;
 };
 
-__global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
+constexpr int kRenderThreads = 128;
+constexpr int kGroup = 8;  // consecutive rays per warp (lane i holds ray i's run)
+
+// Runs of the warp's group of rays; lanes >= nr and invalid runs hold (0, 0).
+__device__ __forceinline__ void load_group(const int32_t* packed_info, int ray0, int nr, int64_t n_samples,
+                                           int32_t* d_status, int lane, int& off, int& cnt) {
+    off = 0;
+    cnt = 0;
+    if (lane < nr) {
+        const int2 v = reinterpret_cast<const int2*>(packed_info)[ray0 + lane];
+        off = v.x;
+        cnt = v.y;
+        if (off < 0 || cnt < 0 || (long long)off + cnt > n_samples) {
+            raise_status(d_status, NACC_STATUS_BAD_PACKED);
+            off = 0;
+            cnt = 0;
+        }
+    }
+}
+
+// alpha = 1 - exp(-tau) for tau >= 0. Below 0.25 the Taylor series
+// t - t^2/2! + ... + t^8/8! in nested form (truncation < 4e-11 relative);
+// above it 1 - exp(-tau) with the fast exponential (absolute error < 1e-6,
+// relative < 4e-6 since alpha > 0.22 there).
+__device__ __forceinline__ float alpha_of(float t) {
+    float p = 1.0f - t * (1.0f / 8.0f);
+    p = 1.0f - t * (1.0f / 7.0f) * p;
+    p = 1.0f - t * (1.0f / 6.0f) * p;
+    p = 1.0f - t * (1.0f / 5.0f) * p;
+    p = 1.0f - t * (1.0f / 4.0f) * p;
+    p = 1.0f - t * (1.0f / 3.0f) * p;
+    p = 1.0f - t * 0.5f * p;
+    p = t * p;
+    const float q = 1.0f - __expf(-t);
+    return t < 0.25f ? p : q;
+}
+
+// Sum of 5 values over the warp with a butterfly that halves the number of
+// values a lane carries at each of the first steps (9 shuffles instead of 25).
+// Returns in lane 0 the total of v[0] and in lanes 4, 8, 12, 16 those of v[1..4].
+__device__ __forceinline__ float warp_sum5(float v0, float v1, float v2, float v3, float v4, int lane) {
+    float v[8] = {v0, v1, v2, v3, v4, 0.0f, 0.0f, 0.0f};
+    // step 16: keep half k in {4b..4b+3}, b = bit 4 of lane
+    const bool h16 = (lane & 16) != 0;
+    float u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float send = h16 ? v[k] : v[4 + k];
+        const float keep = h16 ? v[4 + k] : v[k];
+        u[k] = keep + __shfl_xor_sync(FULL, send, 16);
+    }
+    const bool h8 = (lane & 8) != 0;
+    float w2[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float send = h8 ? u[k] : u[2 + k];
+        const float keep = h8 ? u[2 + k] : u[k];
+        w2[k] = keep + __shfl_xor_sync(FULL, send, 8);
+    }
+    const bool h4 = (lane & 4) != 0;
+    float x = (h4 ? w2[1] : w2[0]) + __shfl_xor_sync(FULL, h4 ? w2[0] : w2[1], 4);
+    x += __shfl_xor_sync(FULL, x, 2);
+    x += __shfl_xor_sync(FULL, x, 1);
+    // lane bits (4,3,2) select the value index 4*b4 + 2*b3 + b2
+    return x;
+}
+
+// Two consecutive samples j0, j0 + 1 (j0 even) of a ray with run [lo, hi).
+struct Pair {
+    float s0[2], s1[2], sg[2], rgb[6];
+    bool v0, v1;
+};
+
+__device__ __forceinline__ void load_pair(const float* __restrict__ ts, const float* __restrict__ te,
+                                          const float* __restrict__ sig, const float* __restrict__ rgbs,
+                                          long long j0, long long lo, long long hi, Pair& q) {
+    q.v0 = j0 >= lo && j0 < hi;
+    q.v1 = j0 + 1 >= lo && j0 + 1 < hi;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) q.s0[k] = q.s1[k] = q.sg[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) q.rgb[k] = 0.0f;
+    if (q.v0 && q.v1) {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(ts + j0));
+        const float2 b = __ldg(reinterpret_cast<const float2*>(te + j0));
+        const float2 g = __ldg(reinterpret_cast<const float2*>(sig + j0));
+        const float2 c0 = __ldg(reinterpret_cast<const float2*>(rgbs + 3 * j0));
+        const float2 c1 = __ldg(reinterpret_cast<const float2*>(rgbs + 3 * j0 + 2));
+        const float2 c2 = __ldg(reinterpret_cast<const float2*>(rgbs + 3 * j0 + 4));
+        q.s0[0] = a.x; q.s0[1] = a.y;
+        q.s1[0] = b.x; q.s1[1] = b.y;
+        q.sg[0] = g.x; q.sg[1] = g.y;
+        q.rgb[0] = c0.x; q.rgb[1] = c0.y; q.rgb[2] = c1.x;
+        q.rgb[3] = c1.y; q.rgb[4] = c2.x; q.rgb[5] = c2.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (k == 0 ? q.v0 : q.v1) {
+                const long long j = j0 + k;
+                q.s0[k] = __ldg(ts + j);
+                q.s1[k] = __ldg(te + j);
+                q.sg[k] = __ldg(sig + j);
+                q.rgb[3 * k] = __ldg(rgbs + 3 * j);
+                q.rgb[3 * k + 1] = __ldg(rgbs + 3 * j + 1);
+                q.rgb[3 * k + 2] = __ldg(rgbs + 3 * j + 2);
+            }
+        }
+    }
+}
+
+// Exclusive optical depth of both samples of each lane's pair, given the carry of
+// earlier chunks; updates the carry. The same explicitly rounded operations in
+// every kernel, so forward, backward and saved values agree bit for bit.
+__device__ __forceinline__ void pair_optical_depth(float tau0, float tau1, float& carry, int lane, float& O0,
+                                                   float& O1) {
+    const float incl = warp_incl_scan(__fadd_rn(tau0, tau1), lane);
+    float excl = __shfl_up_sync(FULL, incl, 1);
+    if (lane == 0) excl = 0.0f;
+    O0 = __fadd_rn(carry, excl);
+    O1 = __fadd_rn(O0, tau0);
+    carry = __fadd_rn(carry, __shfl_sync(FULL, incl, 31));
+}
+
+// The warp walks the 64-sample chunks of its rays as one stream (lane j holds
+// samples 2j, 2j + 1 of a chunk, chunks start at an even index); the loads of
+// the next chunk (of the same ray or of the next one) are issued before the
+// current chunk is computed.
+template <bool PREFETCH>
+__global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(const FwdArgs a) {
     const int lane = threadIdx.x & 31;
-    for (int r = global_warp(); r < a.n_rays; r += n_global_warps()) {
-        int off, cnt;
-        load_run(a.packed_info, r, a.n_samples, a.d_status, lane, off, cnt);
-        float carry = 0.0f;
-        float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, op = 0.0f, dp = 0.0f;
-        for (int base = 0; base < cnt; base += 32) {
-            const int j = base + lane;
-            const bool valid = j < cnt;
-            const size_t i = (size_t)off + j;
-            float s0 = 0.0f, s1 = 0.0f, sg = 0.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
-            if (valid) {
-                s0 = __ldg(a.t_starts + i);
-                s1 = __ldg(a.t_ends + i);
-                sg = __ldg(a.sigmas + i);
-                cr = __ldg(a.rgbs + 3 * i);
-                cg = __ldg(a.rgbs + 3 * i + 1);
-                cb = __ldg(a.rgbs + 3 * i + 2);
-            }
-            const float tau = valid ? tau_of(s0, s1, sg) : 0.0f;
-            float total, incl;
-            const float O = chunk_optical_depth(tau, carry, lane, total, incl);
-            carry = __fadd_rn(carry, total);
-            if (valid) {
-                const float T = expf(-O);
-                const float alpha = -expm1f(-tau);
-                const float w = T * alpha;
-                const float tmid = (s0 + s1) * 0.5f;
-                c0 += w * cr;
-                c1 += w * cg;
-                c2 += w * cb;
-                op += w;
-                dp += w * tmid;
-                if (a.optical_depth) a.optical_depth[i] = O;
+    const int ray0 = global_warp() * kGroup;
+    if (ray0 >= a.n_rays) return;
+    const int nr = min(kGroup, a.n_rays - ray0);
+    int my_off, my_cnt;
+    load_group(a.packed_info, ray0, nr, a.n_samples, a.d_status, lane, my_off, my_cnt);
+    if (lane < nr && my_cnt == 0) {
+        const int r = ray0 + lane;
+        if (a.color) {
+            a.color[3 * (size_t)r] = 0.0f;
+            a.color[3 * (size_t)r + 1] = 0.0f;
+            a.color[3 * (size_t)r + 2] = 0.0f;
+        }
+        if (a.opacity) a.opacity[r] = 0.0f;
+        if (a.depth) a.depth[r] = 0.0f;
+    }
+    unsigned todo = __ballot_sync(FULL, my_cnt > 0);
+    if (todo == 0u) return;
+    int i = __ffs(todo) - 1;
+    todo &= todo - 1;
+    long long lo = __shfl_sync(FULL, my_off, i);
+    long long hi = lo + __shfl_sync(FULL, my_cnt, i);
+    long long j0 = (lo & ~1LL) + 2 * lane;
+    Pair nx;
+    if (PREFETCH) load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0, lo, hi, nx);
+    float carry = 0.0f;
+    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, op = 0.0f, dp = 0.0f;
+    for (;;) {
+        Pair q;
+        if (PREFETCH) {
+            q = nx;
+        } else {
+            load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0, lo, hi, q);
+        }
+        const int qi = i;
+        const long long qj0 = j0;
+        j0 += 64;
+        const bool ray_done = (j0 - 2 * lane) >= hi;
+        bool more = true;
+        if (ray_done) {
+            if (todo) {
+                i = __ffs(todo) - 1;
+                todo &= todo - 1;
+                lo = __shfl_sync(FULL, my_off, i);
+                hi = lo + __shfl_sync(FULL, my_cnt, i);
+                j0 = (lo & ~1LL) + 2 * lane;
+            } else {
+                more = false;
             }
         }
-        c0 = warp_sum(c0);
-        c1 = warp_sum(c1);
-        c2 = warp_sum(c2);
-        op = warp_sum(op);
-        dp = warp_sum(dp);
-        if (lane == 0) {
-            if (a.color) {
-                a.color[3 * (size_t)r] = c0;
-                a.color[3 * (size_t)r + 1] = c1;
-                a.color[3 * (size_t)r + 2] = c2;
-            }
-            if (a.opacity) a.opacity[r] = op;
-            if (a.depth) a.depth[r] = dp;
+        if (PREFETCH && more) load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0, lo, hi, nx);
+
+        const float tau0 = q.v0 ? tau_of(q.s0[0], q.s1[0], q.sg[0]) : 0.0f;
+        const float tau1 = q.v1 ? tau_of(q.s0[1], q.s1[1], q.sg[1]) : 0.0f;
+        float O0, O1;
+        pair_optical_depth(tau0, tau1, carry, lane, O0, O1);
+        const float w0 = q.v0 ? __expf(-O0) * alpha_of(tau0) : 0.0f;
+        const float w1 = q.v1 ? __expf(-O1) * alpha_of(tau1) : 0.0f;
+        c0 += w0 * q.rgb[0] + w1 * q.rgb[3];
+        c1 += w0 * q.rgb[1] + w1 * q.rgb[4];
+        c2 += w0 * q.rgb[2] + w1 * q.rgb[5];
+        op += w0 + w1;
+        dp += w0 * ((q.s0[0] + q.s1[0]) * 0.5f) + w1 * ((q.s0[1] + q.s1[1]) * 0.5f);
+        if (a.optical_depth) {
+            if (q.v0) a.optical_depth[qj0] = O0;
+            if (q.v1) a.optical_depth[qj0 + 1] = O1;
         }
+        if (ray_done) {
+            const float sum = warp_sum5(c0, c1, c2, op, dp, lane);
+            const size_t r = (size_t)ray0 + qi;
+            if (lane == 0 && a.color) a.color[3 * r] = sum;
+            if (lane == 4 && a.color) a.color[3 * r + 1] = sum;
+            if (lane == 8 && a.color) a.color[3 * r + 2] = sum;
+            if (lane == 12 && a.opacity) a.opacity[r] = sum;
+            if (lane == 16 && a.depth) a.depth[r] = sum;
+            carry = 0.0f;
+            c0 = c1 = c2 = op = dp = 0.0f;
+        }
+        if (!more) break;
     }
 }
 
@@ -221,40 +378,62 @@ struct BwdArgs {
     int32_t* d_status;
 };
 
-__device__ __forceinline__ float chunk_tau(const BwdArgs& a, int off, int cnt, int c, int lane) {
-    const int j = (c << 5) + lane;
-    if (j >= cnt) return 0.0f;
-    const size_t i = (size_t)off + j;
-    return tau_of(__ldg(a.t_starts + i), __ldg(a.t_ends + i), __ldg(a.sigmas + i));
+// tau of both samples of the lane's pair in chunk c of a ray (pass A of the backward).
+__device__ __forceinline__ void pair_tau(const BwdArgs& a, long long abase, long long lo, long long hi, int c, int lane,
+                                         float& tau0, float& tau1) {
+    const long long j0 = abase + ((long long)c << 6) + 2 * lane;
+    const bool v0 = j0 >= lo && j0 < hi, v1 = j0 + 1 >= lo && j0 + 1 < hi;
+    tau0 = tau1 = 0.0f;
+    if (v0 && v1) {
+        const float2 u = __ldg(reinterpret_cast<const float2*>(a.t_starts + j0));
+        const float2 v = __ldg(reinterpret_cast<const float2*>(a.t_ends + j0));
+        const float2 g = __ldg(reinterpret_cast<const float2*>(a.sigmas + j0));
+        tau0 = tau_of(u.x, v.x, g.x);
+        tau1 = tau_of(u.y, v.y, g.y);
+    } else if (v0) {
+        tau0 = tau_of(__ldg(a.t_starts + j0), __ldg(a.t_ends + j0), __ldg(a.sigmas + j0));
+    } else if (v1) {
+        tau1 = tau_of(__ldg(a.t_starts + j0 + 1), __ldg(a.t_ends + j0 + 1), __ldg(a.sigmas + j0 + 1));
+    }
 }
 
-__global__ void __launch_bounds__(kThreads) render_bwd_kernel(const BwdArgs a) {
-    __shared__ float s_carry[kWarps][kCarryCap];
+__global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(const BwdArgs a) {
+    __shared__ float s_carry[kRenderThreads / 32][kCarryCap];
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    float* carries = s_carry[wib];
-    for (int r = global_warp(); r < a.n_rays; r += n_global_warps()) {
-        int off, cnt;
-        load_run(a.packed_info, r, a.n_samples, a.d_status, lane, off, cnt);
+    float* carries = s_carry[threadIdx.x >> 5];
+    const int ray0 = global_warp() * kGroup;
+    if (ray0 >= a.n_rays) return;
+    const int nr = min(kGroup, a.n_rays - ray0);
+    int my_off, my_cnt;
+    load_group(a.packed_info, ray0, nr, a.n_samples, a.d_status, lane, my_off, my_cnt);
+    const bool saved = a.optical_depth != nullptr;
+    for (int ri = 0; ri < nr; ++ri) {
+        const long long lo = __shfl_sync(FULL, my_off, ri);
+        const int cnt = __shfl_sync(FULL, my_cnt, ri);
         if (cnt == 0) continue;
-        const int nch = (cnt + 31) >> 5;
+        const long long hi = lo + cnt;
+        const long long abase = lo & ~1LL;
+        const int r = ray0 + ri;
+        const int nch = (int)((hi - abase + 63) >> 6);
         const float gc0 = a.g_color ? a.g_color[3 * (size_t)r] : 0.0f;
         const float gc1 = a.g_color ? a.g_color[3 * (size_t)r + 1] : 0.0f;
         const float gc2 = a.g_color ? a.g_color[3 * (size_t)r + 2] : 0.0f;
         const float ga = a.g_opacity ? a.g_opacity[r] : 0.0f;
         const float gd = a.g_depth ? a.g_depth[r] : 0.0f;
-        const bool saved = a.optical_depth != nullptr;
 
-        // pass A (recompute mode): carry of optical depth at the start of each chunk
+        // pass A (recompute mode): optical-depth carry at the start of each chunk,
+        // the next chunk's loads in flight while the current one is scanned
         if (!saved) {
             float carry = 0.0f;
             const int keep = nch < kCarryCap ? nch : kCarryCap;
+            float n0, n1;
+            pair_tau(a, abase, lo, hi, 0, lane, n0, n1);
             for (int c = 0; c < keep; ++c) {
+                const float t0 = n0, t1 = n1;
+                if (c + 1 < keep) pair_tau(a, abase, lo, hi, c + 1, lane, n0, n1);
                 if (lane == 0) carries[c] = carry;
-                const float tau = chunk_tau(a, off, cnt, c, lane);
-                float total, incl;
-                chunk_optical_depth(tau, carry, lane, total, incl);
-                carry = __fadd_rn(carry, total);
+                float O0, O1;
+                pair_optical_depth(t0, t1, carry, lane, O0, O1);
             }
             __syncwarp();
         }
@@ -265,11 +444,14 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const BwdArgs a) {
         // is the same quantity, but the large near-cancelling terms a_ref T_{k+1}
         // and a_ref sum w_i never appear: the float32 error scales with |b| (the
         // variation of a along the ray), not with |a|.
-        const float r_ref = __ldg(a.rgbs + 3 * (size_t)off);
-        const float g_ref = __ldg(a.rgbs + 3 * (size_t)off + 1);
-        const float b_ref = __ldg(a.rgbs + 3 * (size_t)off + 2);
-        const float tm_ref = (__ldg(a.t_starts + off) + __ldg(a.t_ends + off)) * 0.5f;
+        const float r_ref = __ldg(a.rgbs + 3 * lo);
+        const float g_ref = __ldg(a.rgbs + 3 * lo + 1);
+        const float b_ref = __ldg(a.rgbs + 3 * lo + 2);
+        const float tm_ref = (__ldg(a.t_starts + lo) + __ldg(a.t_ends + lo)) * 0.5f;
         const float a_ref = gc0 * r_ref + gc1 * g_ref + gc2 * b_ref + ga + gd * tm_ref;
+        const long long last = hi - 1 - abase;  // position of the ray's last sample in its chunks
+        const int last_lane = (int)((last >> 1) & 31);
+        const bool last_odd = (last & 1) != 0;
         float t_end = 0.0f;
 
         // pass B: chunks in reverse order, suffix sums of b_i w_i carried backwards
@@ -281,52 +463,67 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(const BwdArgs a) {
                     carry_o = carries[c];
                 } else {  // rays longer than the shared-memory record: rescan from the last record
                     carry_o = carries[kCarryCap - 1];
-                    for (int q = kCarryCap - 1; q < c; ++q) {
-                        float total, incl;
-                        chunk_optical_depth(chunk_tau(a, off, cnt, q, lane), carry_o, lane, total, incl);
-                        carry_o = __fadd_rn(carry_o, total);
+                    for (int p = kCarryCap - 1; p < c; ++p) {
+                        float t0, t1, O0, O1;
+                        pair_tau(a, abase, lo, hi, p, lane, t0, t1);
+                        pair_optical_depth(t0, t1, carry_o, lane, O0, O1);
                     }
                 }
             }
-            const int j = (c << 5) + lane;
-            const bool valid = j < cnt;
-            const size_t i = (size_t)off + j;
-            float s0 = 0.0f, s1 = 0.0f, sg = 0.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f, Os = 0.0f;
-            if (valid) {
-                s0 = __ldg(a.t_starts + i);
-                s1 = __ldg(a.t_ends + i);
-                sg = __ldg(a.sigmas + i);
-                cr = __ldg(a.rgbs + 3 * i);
-                cg = __ldg(a.rgbs + 3 * i + 1);
-                cb = __ldg(a.rgbs + 3 * i + 2);
-                if (saved) Os = __ldg(a.optical_depth + i);
-            }
-            const float tau = valid ? tau_of(s0, s1, sg) : 0.0f;
-            float O;
+            const long long j0 = abase + ((long long)c << 6) + 2 * lane;
+            Pair q;
+            load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0, lo, hi, q);
+            const float tau0 = q.v0 ? tau_of(q.s0[0], q.s1[0], q.sg[0]) : 0.0f;
+            const float tau1 = q.v1 ? tau_of(q.s0[1], q.s1[1], q.sg[1]) : 0.0f;
+            float O0, O1;
             if (saved) {
-                O = Os;
+                O0 = q.v0 ? __ldg(a.optical_depth + j0) : 0.0f;
+                O1 = q.v1 ? __ldg(a.optical_depth + j0 + 1) : 0.0f;
+                if (!q.v0) O1 = q.v1 ? O1 : 0.0f;
             } else {
-                float total, incl;
-                O = chunk_optical_depth(tau, carry_o, lane, total, incl);
+                pair_optical_depth(tau0, tau1, carry_o, lane, O0, O1);
             }
-            const float T = expf(-O);
-            const float T_next = expf(-__fadd_rn(O, tau));
-            if (c == nch - 1) t_end = __shfl_sync(FULL, T_next, (cnt - 1) & 31);
-            const float w = T * -expm1f(-tau);
-            const float tmid = (s0 + s1) * 0.5f;
-            const float bv = gc0 * (cr - r_ref) + gc1 * (cg - g_ref) + gc2 * (cb - b_ref) + gd * (tmid - tm_ref);
-            const float bw = valid ? bv * w : 0.0f;
-            const float suf = warp_incl_suffix(bw, lane);
-            float suf_excl = __shfl_down_sync(FULL, suf, 1);
-            if (lane == 31) suf_excl = 0.0f;
-            const float S = carry_s + suf_excl;
+            // T of each sample and of the sample after it: T_{k+1} of the even
+            // sample is T of the odd one (O1 = O0 + tau0 by construction)
+            const float T0 = __expf(-O0);
+            const float T1 = __expf(-O1);
+            const float T2 = __expf(-__fadd_rn(O1, tau1));
+            const float Tn0 = q.v1 ? T1 : __expf(-__fadd_rn(O0, tau0));
+            if (c == nch - 1) t_end = __shfl_sync(FULL, last_odd ? T2 : Tn0, last_lane);
+            const float w0 = q.v0 ? T0 * alpha_of(tau0) : 0.0f;
+            const float w1 = q.v1 ? T1 * alpha_of(tau1) : 0.0f;
+            const float tm0 = (q.s0[0] + q.s1[0]) * 0.5f, tm1 = (q.s0[1] + q.s1[1]) * 0.5f;
+            const float b0 = gc0 * (q.rgb[0] - r_ref) + gc1 * (q.rgb[1] - g_ref) + gc2 * (q.rgb[2] - b_ref) +
+                             gd * (tm0 - tm_ref);
+            const float b1 = gc0 * (q.rgb[3] - r_ref) + gc1 * (q.rgb[4] - g_ref) + gc2 * (q.rgb[5] - b_ref) +
+                             gd * (tm1 - tm_ref);
+            const float bw0 = q.v0 ? b0 * w0 : 0.0f;
+            const float bw1 = q.v1 ? b1 * w1 : 0.0f;
+            const float suf = warp_incl_suffix(bw0 + bw1, lane);
+            float later = __shfl_down_sync(FULL, suf, 1);  // pairs of lanes > this one
+            if (lane == 31) later = 0.0f;
+            const float S1 = carry_s + later;
+            const float S0 = S1 + bw1;
             carry_s = carry_s + __shfl_sync(FULL, suf, 0);
-            if (valid) {
-                const float dtau = a_ref * t_end + (bv * T_next - S);
-                a.d_sigmas[i] = (s1 - s0) * dtau;
-                a.d_rgbs[3 * i] = w * gc0;
-                a.d_rgbs[3 * i + 1] = w * gc1;
-                a.d_rgbs[3 * i + 2] = w * gc2;
+            const float base_g = a_ref * t_end;
+            const float ds0 = (q.s1[0] - q.s0[0]) * (base_g + (b0 * Tn0 - S0));
+            const float ds1 = (q.s1[1] - q.s0[1]) * (base_g + (b1 * T2 - S1));
+            if (q.v0 && q.v1) {
+                *reinterpret_cast<float2*>(a.d_sigmas + j0) = make_float2(ds0, ds1);
+                float2* dr = reinterpret_cast<float2*>(a.d_rgbs + 3 * j0);
+                dr[0] = make_float2(w0 * gc0, w0 * gc1);
+                dr[1] = make_float2(w0 * gc2, w1 * gc0);
+                dr[2] = make_float2(w1 * gc1, w1 * gc2);
+            } else if (q.v0) {
+                a.d_sigmas[j0] = ds0;
+                a.d_rgbs[3 * j0] = w0 * gc0;
+                a.d_rgbs[3 * j0 + 1] = w0 * gc1;
+                a.d_rgbs[3 * j0 + 2] = w0 * gc2;
+            } else if (q.v1) {
+                a.d_sigmas[j0 + 1] = ds1;
+                a.d_rgbs[3 * j0 + 3] = w1 * gc0;
+                a.d_rgbs[3 * j0 + 4] = w1 * gc1;
+                a.d_rgbs[3 * j0 + 5] = w1 * gc2;
             }
         }
         __syncwarp();
@@ -359,6 +556,12 @@ int grid_for(K kernel, int n_rays) {
     return (int)(need < cap ? need : cap);
 }
 
+// one warp per group of kGroup consecutive rays
+int group_blocks(int n_rays) {
+    const long long groups = ((long long)n_rays + kGroup - 1) / kGroup;
+    return (int)((groups + kRenderThreads / 32 - 1) / (kRenderThreads / 32));
+}
+
 bool sizes_ok(int32_t n_rays, int64_t n_samples) {
     return n_rays >= 0 && n_samples >= 0 && n_samples < (1LL << 31);
 }
@@ -376,8 +579,14 @@ extern "C" int nacc_render_fwd(const int32_t* packed_info, int32_t n_rays, const
     if (n_rays > 0 && !packed_info) return NACC_ERR_INVALID_ARG;
     if (n_samples > 0 && (!t_starts || !t_ends || !sigmas || !rgbs)) return NACC_ERR_INVALID_ARG;
     if (n_rays == 0) return NACC_OK;
+    if ((((uintptr_t)packed_info | (uintptr_t)t_starts | (uintptr_t)t_ends | (uintptr_t)sigmas | (uintptr_t)rgbs |
+          (uintptr_t)optical_depth) & 7u) != 0)
+        return NACC_ERR_INVALID_ARG;
     FwdArgs a{packed_info, n_rays, t_starts, t_ends, sigmas, rgbs, n_samples, color, opacity, depth, optical_depth, d_status};
-    render_fwd_kernel<<<grid_for(render_fwd_kernel, n_rays), kThreads, 0, (cudaStream_t)stream>>>(a);
+    if (tune_get(NACC_TUNE_RENDER_FWD_PREFETCH))
+        render_fwd_kernel<true><<<group_blocks(n_rays), kRenderThreads, 0, (cudaStream_t)stream>>>(a);
+    else
+        render_fwd_kernel<false><<<group_blocks(n_rays), kRenderThreads, 0, (cudaStream_t)stream>>>(a);
     return launch_status(cudaGetLastError());
 }
 
@@ -415,9 +624,12 @@ extern "C" int nacc_render_bwd(const int32_t* packed_info, int32_t n_rays, const
     if (n_samples > 0 && (!t_starts || !t_ends || !sigmas || !rgbs || !d_sigmas || !d_rgbs))
         return NACC_ERR_INVALID_ARG;
     if (n_rays == 0) return NACC_OK;
+    if ((((uintptr_t)packed_info | (uintptr_t)t_starts | (uintptr_t)t_ends | (uintptr_t)sigmas | (uintptr_t)rgbs |
+          (uintptr_t)optical_depth | (uintptr_t)d_sigmas | (uintptr_t)d_rgbs) & 7u) != 0)
+        return NACC_ERR_INVALID_ARG;
     BwdArgs a{packed_info, n_rays, t_starts, t_ends, sigmas, rgbs, optical_depth, n_samples,
               g_color, g_opacity, g_depth, d_sigmas, d_rgbs, d_status};
-    render_bwd_kernel<<<grid_for(render_bwd_kernel, n_rays), kThreads, 0, (cudaStream_t)stream>>>(a);
+    render_bwd_kernel<<<group_blocks(n_rays), kRenderThreads, 0, (cudaStream_t)stream>>>(a);
     return launch_status(cudaGetLastError());
 }
 
