@@ -70,7 +70,7 @@ extern "C" {
  */
 typedef struct nacc_grid {
     const uint32_t* bits; /* device, ceil(n_slots*n_levels*res0*res1*res2 / 32) words */
-    int32_t res[3];
+    int32_t res[3];       /* 1 .. 2^22 cells per axis; total cells over all slots and levels < 2^31 */
     int32_t n_levels; /* 1 .. NACC_MAX_LEVELS */
     int32_t n_slots;  /* >= 1 */
     float aabb[6];
@@ -266,7 +266,11 @@ int nacc_update_occupancy_grid(float* ema, uint32_t* bits, int64_t n_cells, cons
 #define NACC_TUNE_RENDER_FWD_PREFETCH 0 /* 0/1: issue the next chunk's loads early */
 #define NACC_TUNE_MARCH_TILE_RAYS 1     /* 1..32: rays per warp tile (upper bound) */
 #define NACC_TUNE_PRUNE_TILE_RAYS 2     /* 2..32, even: rays per warp tile */
-#define NACC_TUNE_COUNT 3
+#define NACC_TUNE_MARCH_OCCUPANCY 3     /* 0: compiler's register use; 1: registers capped for 8 blocks/SM */
+#define NACC_TUNE_PRUNE_OCCUPANCY 4     /* 0: compiler's; 1: capped for 8 blocks/SM; 2: for 6 */
+#define NACC_TUNE_RENDER_OCCUPANCY 5    /* forward: 0: compiler's; 1: capped for 16 blocks/SM; 2: for 12 */
+#define NACC_TUNE_RENDER_BWD_OCCUPANCY 6 /* backward: 0: compiler's; 1: capped for 16 blocks/SM; 2: for 12 */
+#define NACC_TUNE_COUNT 7
 
 /* Set a knob; NACC_ERR_INVALID_ARG for an unknown knob or out-of-range value. */
 int nacc_tune_set(int knob, int value);

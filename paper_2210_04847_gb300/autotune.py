@@ -18,8 +18,12 @@ from . import _lib
 # Candidate values per knob (all valid for every input).
 CANDIDATES = {
     "march_tile_rays": (2, 4, 8, 16, 32),
+    "march_occupancy": (0, 1),
     "prune_tile_rays": (2, 4, 8, 16, 32),
+    "prune_occupancy": (0, 1, 2),
     "render_fwd_prefetch": (0, 1),
+    "render_fwd_occupancy": (0, 1, 2),
+    "render_bwd_occupancy": (0, 1, 2),
 }
 
 
@@ -58,15 +62,24 @@ def tune_knob(knob: str, fn: Callable[[], None], candidates: Iterable[int] = Non
 def tune_hot_path(hp, field, rays_o, rays_d, reps: int = 5):
     """Tune the knobs of one ``pipeline.HotPath`` on one batch of rays (leaves its buffers holding that batch)."""
     rec = []
-    rec.append(tune_knob("march_tile_rays", lambda: hp.march(rays_o, rays_d), reps=reps))
+    march = lambda: hp.march(rays_o, rays_d)
+    rec.append(tune_knob("march_tile_rays", march, reps=reps))
+    rec.append(tune_knob("march_occupancy", march, reps=reps))
     hp.march(rays_o, rays_d)
     M = int(hp.n_m.item())
     hp.field_marched(field, rays_o, rays_d, M)
-    rec.append(tune_knob("prune_tile_rays", lambda: hp.prune(M), reps=reps))
+    prune = lambda: hp.prune(M)
+    rec.append(tune_knob("prune_tile_rays", prune, reps=reps))
+    rec.append(tune_knob("prune_occupancy", prune, reps=reps))
     hp.prune(M)
     S = int(hp.n_k.item())
     hp.field_kept(field, rays_o, rays_d, S)
-    rec.append(tune_knob("render_fwd_prefetch", lambda: hp.render_fwd(S), reps=reps))
+    fwd = lambda: hp.render_fwd(S)
+    rec.append(tune_knob("render_fwd_prefetch", fwd, reps=reps))
+    rec.append(tune_knob("render_fwd_occupancy", fwd, reps=reps))
+    hp.render_fwd(S)
+    hp.g_color.uniform_(-1e-6, 1e-6)
+    rec.append(tune_knob("render_bwd_occupancy", lambda: hp.render_bwd(S), reps=reps))
     torch.cuda.synchronize()
     hp.check_status("autotune")
     return {r["knob"]: r for r in rec}

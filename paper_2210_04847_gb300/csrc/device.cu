@@ -30,9 +30,13 @@ int g_tune[NACC_TUNE_COUNT] = {
     1,  // NACC_TUNE_RENDER_FWD_PREFETCH
     8,  // NACC_TUNE_MARCH_TILE_RAYS (upper bound; long lattices use fewer)
     8,  // NACC_TUNE_PRUNE_TILE_RAYS
+    1,  // NACC_TUNE_MARCH_OCCUPANCY
+    2,  // NACC_TUNE_PRUNE_OCCUPANCY
+    2,  // NACC_TUNE_RENDER_OCCUPANCY
+    2,  // NACC_TUNE_RENDER_BWD_OCCUPANCY
 };
-const int g_tune_lo[NACC_TUNE_COUNT] = {0, 1, 2};
-const int g_tune_hi[NACC_TUNE_COUNT] = {1, 32, 32};
+const int g_tune_lo[NACC_TUNE_COUNT] = {0, 1, 2, 0, 0, 0, 0};
+const int g_tune_hi[NACC_TUNE_COUNT] = {1, 32, 32, 1, 2, 2, 2};
 }  // namespace
 
 int tune_get(int knob) { return (knob >= 0 && knob < NACC_TUNE_COUNT) ? g_tune[knob] : 0; }

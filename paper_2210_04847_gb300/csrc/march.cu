@@ -153,8 +153,8 @@ __device__ __forceinline__ int lattice_count(const MarchArgs& a, float near, flo
 // uniform steps: warp per ray
 // ---------------------------------------------------------------------------
 
-template <int MAXL>
-__global__ void __launch_bounds__(kThreads) march_uniform_kernel(const MarchArgs a) {
+template <int MAXL, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const MarchArgs a) {
     extern __shared__ uint32_t s_masks[];  // per warp: [tile_rays][mask_words]
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -437,6 +437,13 @@ int blocks_for(K kernel, size_t smem, int n_work_blocks) {
     return n_work_blocks < want ? n_work_blocks : want;
 }
 
+template <typename K>
+void launch_uniform(K kernel, size_t smem, int need, cudaStream_t st, const MarchArgs& a) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int blocks = blocks_for(kernel, smem, need);
+    kernel<<<blocks, kThreads, smem, st>>>(a);
+}
+
 }  // namespace
 }  // namespace nacc
 
@@ -459,6 +466,7 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
     if (capacity > 0 && (!t_starts || !t_ends || !ray_indices)) return NACC_ERR_INVALID_ARG;
     if (grid->n_levels < 1 || grid->n_levels > NACC_MAX_LEVELS || grid->n_slots < 1) return NACC_ERR_INVALID_ARG;
     if (grid->res[0] < 1 || grid->res[1] < 1 || grid->res[2] < 1) return NACC_ERR_INVALID_ARG;
+    if (grid->res[0] > (1 << 22) || grid->res[1] > (1 << 22) || grid->res[2] > (1 << 22)) return NACC_ERR_INVALID_ARG;
     const long long cells = (long long)grid->res[0] * grid->res[1] * grid->res[2] * grid->n_levels * grid->n_slots;
     if (cells >= (1LL << 31)) return NACC_ERR_INVALID_ARG;
     if (p->max_steps < 1 || p->max_steps > 32768) return NACC_ERR_INVALID_ARG;
@@ -527,17 +535,14 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
         }
     } else {
         const size_t smem = (size_t)kWarps * a.tile_rays * a.mask_words * sizeof(uint32_t);
+        const int need = (a.n_tiles + kWarps - 1) / kWarps;
+        const bool occ = tune_get(NACC_TUNE_MARCH_OCCUPANCY) != 0;
         if (a.n_levels == 1) {
-            if (smem > 48 * 1024)
-                cudaFuncSetAttribute(march_uniform_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            const int blocks = blocks_for(march_uniform_kernel<1>, smem, (a.n_tiles + kWarps - 1) / kWarps);
-            march_uniform_kernel<1><<<blocks, kThreads, smem, st>>>(a);
+            if (occ) launch_uniform(march_uniform_kernel<1, 8>, smem, need, st, a);
+            else launch_uniform(march_uniform_kernel<1, 1>, smem, need, st, a);
         } else {
-            if (smem > 48 * 1024)
-                cudaFuncSetAttribute(march_uniform_kernel<NACC_MAX_LEVELS>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            const int blocks = blocks_for(march_uniform_kernel<NACC_MAX_LEVELS>, smem, (a.n_tiles + kWarps - 1) / kWarps);
-            march_uniform_kernel<NACC_MAX_LEVELS><<<blocks, kThreads, smem, st>>>(a);
+            if (occ) launch_uniform(march_uniform_kernel<NACC_MAX_LEVELS, 8>, smem, need, st, a);
+            else launch_uniform(march_uniform_kernel<NACC_MAX_LEVELS, 1>, smem, need, st, a);
         }
     }
     return launch_status(cudaGetLastError());

@@ -139,7 +139,7 @@ __device__ __forceinline__ void walk_step(RayWalk& w, const PruneArgs& a, int la
     if (w.c >= w.nch || (a.use_t && !(w.carry <= a.thr_o))) w.live = false;
 }
 
-__global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a) {
+__device__ __forceinline__ void prune_body(const PruneArgs& a) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
 
@@ -273,6 +273,25 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a) {
     }
 }
 
+// Register-budget variants (minimum resident blocks per SM), chosen by a tuning knob.
+template <int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) prune_kernel(const PruneArgs a) {
+    prune_body(a);
+}
+
+// Persistent launch: as many blocks as fit on the GPU, at most `need`.
+template <typename K>
+void launch_persistent(K kernel, int need, cudaStream_t st, const PruneArgs& a) {
+    const DeviceInfo dev = current_device();
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int blocks = dev.sm_count * per_sm;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    kernel<<<blocks, kThreads, 0, st>>>(a);
+}
+
 size_t workspace_bytes_for(int32_t n_rays, int64_t n_samples) {
     const size_t tiles = (size_t)(n_rays + 1) / 2;  // smallest tile: 2 rays
     const size_t head = align_up(kTicketBytes + tiles * sizeof(unsigned long long), 256);
@@ -343,14 +362,11 @@ extern "C" int nacc_prune_samples(const int32_t* packed_info, int32_t n_rays, co
 
     cudaError_t e = cudaMemsetAsync(workspace, 0, kTicketBytes + (size_t)a.n_tiles * 8, st);
     if (e != cudaSuccess) return NACC_ERR_CUDA;
-    const DeviceInfo dev = current_device();
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prune_kernel, kThreads, 0) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    int blocks = dev.sm_count * per_sm;
     const int need = (a.n_tiles + kThreads / 32 - 1) / (kThreads / 32);
-    if (blocks > need) blocks = need;
-    prune_kernel<<<blocks, kThreads, 0, st>>>(a);
+    switch (tune_get(NACC_TUNE_PRUNE_OCCUPANCY)) {
+        case 1: launch_persistent(prune_kernel<8>, need, st, a); break;
+        case 2: launch_persistent(prune_kernel<6>, need, st, a); break;
+        default: launch_persistent(prune_kernel<1>, need, st, a); break;
+    }
     return launch_status(cudaGetLastError());
 }

@@ -93,21 +93,18 @@ __device__ __forceinline__ void load_group(const int32_t* packed_info, int ray0,
     }
 }
 
-// alpha = 1 - exp(-tau) for tau >= 0. Below 0.25 the Taylor series
-// t - t^2/2! + ... + t^8/8! in nested form (truncation < 4e-11 relative);
-// above it 1 - exp(-tau) with the fast exponential (absolute error < 1e-6,
-// relative < 4e-6 since alpha > 0.22 there).
+// alpha = 1 - exp(-tau) for tau >= 0. Below 1/16 the Taylor series
+// t (1 - t/2 (1 - t/3 (1 - t/4 (1 - t/5)))) (truncation below t^5/6! < 2e-8
+// relative); from 1/16 on 1 - exp(-tau) with the fast exponential (absolute
+// error below 2.5e-7, relative below 4e-6 since alpha > 0.06 there).
 __device__ __forceinline__ float alpha_of(float t) {
-    float p = 1.0f - t * (1.0f / 8.0f);
-    p = 1.0f - t * (1.0f / 7.0f) * p;
-    p = 1.0f - t * (1.0f / 6.0f) * p;
-    p = 1.0f - t * (1.0f / 5.0f) * p;
+    float p = 1.0f - t * (1.0f / 5.0f);
     p = 1.0f - t * (1.0f / 4.0f) * p;
     p = 1.0f - t * (1.0f / 3.0f) * p;
     p = 1.0f - t * 0.5f * p;
     p = t * p;
     const float q = 1.0f - __expf(-t);
-    return t < 0.25f ? p : q;
+    return t < 0.0625f ? p : q;
 }
 
 // Sum of 5 values over the warp with a butterfly that halves the number of
@@ -141,6 +138,8 @@ __device__ __forceinline__ float warp_sum5(float v0, float v1, float v2, float v
 }
 
 // Two consecutive samples j0, j0 + 1 (j0 even) of a ray with run [lo, hi).
+// Sample indices are below 2^31 (checked on the host), so 32-bit unsigned
+// arithmetic cannot wrap even 64 samples past the end.
 struct Pair {
     float s0[2], s1[2], sg[2], rgb[6];
     bool v0, v1;
@@ -148,7 +147,7 @@ struct Pair {
 
 __device__ __forceinline__ void load_pair(const float* __restrict__ ts, const float* __restrict__ te,
                                           const float* __restrict__ sig, const float* __restrict__ rgbs,
-                                          long long j0, long long lo, long long hi, Pair& q) {
+                                          unsigned j0, unsigned lo, unsigned hi, Pair& q) {
     q.v0 = j0 >= lo && j0 < hi;
     q.v1 = j0 + 1 >= lo && j0 + 1 < hi;
 #pragma unroll
@@ -171,7 +170,7 @@ __device__ __forceinline__ void load_pair(const float* __restrict__ ts, const fl
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             if (k == 0 ? q.v0 : q.v1) {
-                const long long j = j0 + k;
+                const unsigned j = j0 + k;
                 q.s0[k] = __ldg(ts + j);
                 q.s1[k] = __ldg(te + j);
                 q.sg[k] = __ldg(sig + j);
@@ -200,8 +199,8 @@ __device__ __forceinline__ void pair_optical_depth(float tau0, float tau1, float
 // samples 2j, 2j + 1 of a chunk, chunks start at an even index); the loads of
 // the next chunk (of the same ray or of the next one) are issued before the
 // current chunk is computed.
-template <bool PREFETCH>
-__global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(const FwdArgs a) {
+template <bool PREFETCH, int MINB>
+__global__ void __launch_bounds__(kRenderThreads, MINB) render_fwd_kernel(const FwdArgs a) {
     const int lane = threadIdx.x & 31;
     const int ray0 = global_warp() * kGroup;
     if (ray0 >= a.n_rays) return;
@@ -222,9 +221,9 @@ __global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(const FwdArg
     if (todo == 0u) return;
     int i = __ffs(todo) - 1;
     todo &= todo - 1;
-    long long lo = __shfl_sync(FULL, my_off, i);
-    long long hi = lo + __shfl_sync(FULL, my_cnt, i);
-    long long j0 = (lo & ~1LL) + 2 * lane;
+    unsigned lo = __shfl_sync(FULL, my_off, i);
+    unsigned hi = lo + __shfl_sync(FULL, my_cnt, i);
+    unsigned j0 = (lo & ~1u) + 2 * lane;
     Pair nx;
     if (PREFETCH) load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0, lo, hi, nx);
     float carry = 0.0f;
@@ -237,7 +236,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(const FwdArg
             load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0, lo, hi, q);
         }
         const int qi = i;
-        const long long qj0 = j0;
+        const unsigned qj0 = j0;
         j0 += 64;
         const bool ray_done = (j0 - 2 * lane) >= hi;
         bool more = true;
@@ -247,7 +246,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(const FwdArg
                 todo &= todo - 1;
                 lo = __shfl_sync(FULL, my_off, i);
                 hi = lo + __shfl_sync(FULL, my_cnt, i);
-                j0 = (lo & ~1LL) + 2 * lane;
+                j0 = (lo & ~1u) + 2 * lane;
             } else {
                 more = false;
             }
@@ -316,8 +315,8 @@ __global__ void __launch_bounds__(kThreads) render_weights_kernel(const WeightsA
             const float O = chunk_optical_depth(tau, carry, lane, total, incl);
             carry = __fadd_rn(carry, total);
             if (valid) {
-                const float T = expf(-O);
-                if (a.weights) a.weights[i] = T * -expm1f(-tau);
+                const float T = __expf(-O);
+                if (a.weights) a.weights[i] = T * alpha_of(tau);
                 if (a.trans) a.trans[i] = T;
             }
         }
@@ -379,9 +378,9 @@ struct BwdArgs {
 };
 
 // tau of both samples of the lane's pair in chunk c of a ray (pass A of the backward).
-__device__ __forceinline__ void pair_tau(const BwdArgs& a, long long abase, long long lo, long long hi, int c, int lane,
+__device__ __forceinline__ void pair_tau(const BwdArgs& a, unsigned abase, unsigned lo, unsigned hi, int c, int lane,
                                          float& tau0, float& tau1) {
-    const long long j0 = abase + ((long long)c << 6) + 2 * lane;
+    const unsigned j0 = abase + ((unsigned)c << 6) + 2 * lane;
     const bool v0 = j0 >= lo && j0 < hi, v1 = j0 + 1 >= lo && j0 + 1 < hi;
     tau0 = tau1 = 0.0f;
     if (v0 && v1) {
@@ -397,7 +396,8 @@ __device__ __forceinline__ void pair_tau(const BwdArgs& a, long long abase, long
     }
 }
 
-__global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(const BwdArgs a) {
+template <int MINB>
+__global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const BwdArgs a) {
     __shared__ float s_carry[kRenderThreads / 32][kCarryCap];
     const int lane = threadIdx.x & 31;
     float* carries = s_carry[threadIdx.x >> 5];
@@ -408,11 +408,11 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(const BwdArg
     load_group(a.packed_info, ray0, nr, a.n_samples, a.d_status, lane, my_off, my_cnt);
     const bool saved = a.optical_depth != nullptr;
     for (int ri = 0; ri < nr; ++ri) {
-        const long long lo = __shfl_sync(FULL, my_off, ri);
+        const unsigned lo = __shfl_sync(FULL, my_off, ri);
         const int cnt = __shfl_sync(FULL, my_cnt, ri);
         if (cnt == 0) continue;
-        const long long hi = lo + cnt;
-        const long long abase = lo & ~1LL;
+        const unsigned hi = lo + cnt;
+        const unsigned abase = lo & ~1u;
         const int r = ray0 + ri;
         const int nch = (int)((hi - abase + 63) >> 6);
         const float gc0 = a.g_color ? a.g_color[3 * (size_t)r] : 0.0f;
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(const BwdArg
         const float b_ref = __ldg(a.rgbs + 3 * lo + 2);
         const float tm_ref = (__ldg(a.t_starts + lo) + __ldg(a.t_ends + lo)) * 0.5f;
         const float a_ref = gc0 * r_ref + gc1 * g_ref + gc2 * b_ref + ga + gd * tm_ref;
-        const long long last = hi - 1 - abase;  // position of the ray's last sample in its chunks
+        const unsigned last = hi - 1 - abase;  // position of the ray's last sample in its chunks
         const int last_lane = (int)((last >> 1) & 31);
         const bool last_odd = (last & 1) != 0;
         float t_end = 0.0f;
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(const BwdArg
                     }
                 }
             }
-            const long long j0 = abase + ((long long)c << 6) + 2 * lane;
+            const unsigned j0 = abase + ((unsigned)c << 6) + 2 * lane;
             Pair q;
             load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0, lo, hi, q);
             const float tau0 = q.v0 ? tau_of(q.s0[0], q.s1[0], q.sg[0]) : 0.0f;
@@ -583,10 +583,23 @@ extern "C" int nacc_render_fwd(const int32_t* packed_info, int32_t n_rays, const
           (uintptr_t)optical_depth) & 7u) != 0)
         return NACC_ERR_INVALID_ARG;
     FwdArgs a{packed_info, n_rays, t_starts, t_ends, sigmas, rgbs, n_samples, color, opacity, depth, optical_depth, d_status};
-    if (tune_get(NACC_TUNE_RENDER_FWD_PREFETCH))
-        render_fwd_kernel<true><<<group_blocks(n_rays), kRenderThreads, 0, (cudaStream_t)stream>>>(a);
-    else
-        render_fwd_kernel<false><<<group_blocks(n_rays), kRenderThreads, 0, (cudaStream_t)stream>>>(a);
+    const int nb = group_blocks(n_rays);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool pf = tune_get(NACC_TUNE_RENDER_FWD_PREFETCH) != 0;
+    switch (tune_get(NACC_TUNE_RENDER_OCCUPANCY)) {
+        case 1:
+            if (pf) render_fwd_kernel<true, 16><<<nb, kRenderThreads, 0, st>>>(a);
+            else render_fwd_kernel<false, 16><<<nb, kRenderThreads, 0, st>>>(a);
+            break;
+        case 2:
+            if (pf) render_fwd_kernel<true, 12><<<nb, kRenderThreads, 0, st>>>(a);
+            else render_fwd_kernel<false, 12><<<nb, kRenderThreads, 0, st>>>(a);
+            break;
+        default:
+            if (pf) render_fwd_kernel<true, 1><<<nb, kRenderThreads, 0, st>>>(a);
+            else render_fwd_kernel<false, 1><<<nb, kRenderThreads, 0, st>>>(a);
+            break;
+    }
     return launch_status(cudaGetLastError());
 }
 
@@ -629,7 +642,13 @@ extern "C" int nacc_render_bwd(const int32_t* packed_info, int32_t n_rays, const
         return NACC_ERR_INVALID_ARG;
     BwdArgs a{packed_info, n_rays, t_starts, t_ends, sigmas, rgbs, optical_depth, n_samples,
               g_color, g_opacity, g_depth, d_sigmas, d_rgbs, d_status};
-    render_bwd_kernel<<<group_blocks(n_rays), kRenderThreads, 0, (cudaStream_t)stream>>>(a);
+    const int nb = group_blocks(n_rays);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (tune_get(NACC_TUNE_RENDER_BWD_OCCUPANCY)) {
+        case 1: render_bwd_kernel<16><<<nb, kRenderThreads, 0, st>>>(a); break;
+        case 2: render_bwd_kernel<12><<<nb, kRenderThreads, 0, st>>>(a); break;
+        default: render_bwd_kernel<1><<<nb, kRenderThreads, 0, st>>>(a); break;
+    }
     return launch_status(cudaGetLastError());
 }
 
