@@ -136,6 +136,32 @@ int nacc_march_rays(const float* rays_o, const float* rays_d, const float* ray_t
                     float* t_ends, int32_t* ray_indices, int64_t capacity, int64_t* n_samples,
                     int32_t* d_status, void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * Ray marching without any device allocation by the caller. The paper has no
+ * counterpart: this is an integration aid for callers that cannot allocate
+ * device memory at call time (a renderer with a fixed, pre-planned memory
+ * budget, a plugin inside a host application that owns the CUDA allocator).
+ * Same arguments, results and errors as nacc_march_rays, minus the workspace:
+ * the scratch lives in a fixed array of this library's device memory
+ * (256 + 8 * NACC_STATIC_MAX_RAYS bytes, held by every GPU that loads the
+ * library until the process exits). n_rays above NACC_STATIC_MAX_RAYS is
+ * rejected with NACC_ERR_INVALID_ARG before anything is enqueued.
+ * - The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any stream
+ *   capture on the device.
+ * - Every call on a device shares the one array. Each call clears the part it
+ *   uses on `stream` before use, but calls that overlap on the GPU (concurrent
+ *   streams, or host threads racing) corrupt each other's scratch: serialise
+ *   them, e.g. on one stream.
+ * - Nothing is allocated: no cudaMalloc, no cudaFree, no allocating library call.
+ */
+#define NACC_STATIC_MAX_RAYS (1 << 20)
+int nacc_march_rays_static(const float* rays_o, const float* rays_d, const float* ray_time,
+                           const int32_t* ray_slot, int32_t n_rays, const nacc_grid* grid,
+                           const nacc_march_params* params, int32_t* packed_info, float* t_starts,
+                           float* t_ends, int32_t* ray_indices, int64_t capacity, int64_t* n_samples,
+                           int32_t* d_status, void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Pruning by transmittance and opacity (Sec. 2.1 "Pruning Empty and         */
 /* Occluded Regions"; arguments early_stop_eps, alpha_thre of Sec. 3)        */

@@ -33,7 +33,8 @@ STATUS_OVERFLOW = 0x10
 MAX_LEVELS = 16
 
 EXPORTS = (
-    "nacc_march_workspace_size", "nacc_march_rays", "nacc_prune_workspace_size", "nacc_prune_samples",
+    "nacc_march_workspace_size", "nacc_march_rays", "nacc_march_rays_static", "nacc_prune_workspace_size",
+    "nacc_prune_samples",
     "nacc_render_weights", "nacc_accumulate_along_rays", "nacc_render_fwd", "nacc_render_bwd",
     "nacc_unpack_info", "nacc_update_occupancy_grid", "nacc_tune_set", "nacc_tune_get", "nacc_error_string",
     "nacc_version",
@@ -88,6 +89,7 @@ def load() -> ctypes.CDLL:
     sig = {
         "nacc_march_workspace_size": (sz, [i32, MP]),
         "nacc_march_rays": (ctypes.c_int, [P, P, P, P, i32, GP, MP, P, P, P, P, i64, P, P, P, sz, P]),
+        "nacc_march_rays_static": (ctypes.c_int, [P, P, P, P, i32, GP, MP, P, P, P, P, i64, P, P, P]),
         "nacc_prune_workspace_size": (sz, [i32, i64]),
         "nacc_prune_samples": (ctypes.c_int, [P, i32, P, P, P, i64, f32, f32, P, P, P, P, i64, P, P, P, P, sz, P]),
         "nacc_render_weights": (ctypes.c_int, [P, i32, P, P, P, i64, P, P, P, P]),
@@ -217,6 +219,32 @@ def march_rays(rays_o, rays_d, grid: Grid, params: MarchParams, packed_info, t_s
         _ptr(packed_info), _ptr(t_starts), _ptr(t_ends), _ptr(ray_indices), cap, _ptr(n_samples), _ptr(d_status),
         _ptr(workspace), workspace.numel(), _stream(stream))
     _rc(rc, "nacc_march_rays")
+
+
+STATIC_MAX_RAYS = 1 << 20
+
+
+def march_rays_static(rays_o, rays_d, grid: Grid, params: MarchParams, packed_info, t_starts, t_ends, ray_indices,
+                      n_samples, d_status, ray_time=None, ray_slot=None, stream=None):
+    """nacc_march_rays_static: marching with the library's fixed scratch array, for
+    callers that cannot allocate device memory (no workspace argument)."""
+    n = rays_o.shape[0]
+    _check(rays_o, torch.float32, "rays_o", 3 * n)
+    _check(rays_d, torch.float32, "rays_d", 3 * n)
+    _check(ray_time, torch.float32, "ray_time", n, optional=True)
+    _check(ray_slot, torch.int32, "ray_slot", n, optional=True)
+    _check(packed_info, torch.int32, "packed_info", 2 * n)
+    cap = t_starts.numel()
+    _check(t_starts, torch.float32, "t_starts")
+    _check(t_ends, torch.float32, "t_ends", cap)
+    _check(ray_indices, torch.int32, "ray_indices", cap)
+    _check(n_samples, torch.int64, "n_samples", 1)
+    _check(d_status, torch.int32, "d_status", 1, optional=True)
+    rc = load().nacc_march_rays_static(
+        _ptr(rays_o), _ptr(rays_d), _ptr(ray_time), _ptr(ray_slot), n, ctypes.byref(grid), ctypes.byref(params),
+        _ptr(packed_info), _ptr(t_starts), _ptr(t_ends), _ptr(ray_indices), cap, _ptr(n_samples), _ptr(d_status),
+        _stream(stream))
+    _rc(rc, "nacc_march_rays_static")
 
 
 def prune_samples(packed_info, t_starts, t_ends, sigmas, n_samples_in: int, early_stop_eps, alpha_thre,

@@ -30,7 +30,7 @@ COMMON = ARCH + [
 NO_FMAD = {"march.cu", "prune.cu"}
 
 LIBS = {
-    "libnacc.so": ["march.cu", "prune.cu", "render.cu", "grid.cu", "device.cu"],
+    "libnacc.so": ["march.cu", "march_static.cu", "prune.cu", "render.cu", "grid.cu", "device.cu"],
     "libnacc_field.so": ["field.cu"],
 }
 
