@@ -45,7 +45,19 @@ POOL = 4  # distinct ray batches cycled through the steps (L2 is flushed between
 # DRAM bytes (read + write) of one launch of the dominant kernel on this workload,
 # from one ncu capture, keyed by the SHA-256 of the kernel's source file. A
 # source change invalidates the figure (reported as null until re-captured).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/march_dram_bounded-2^18.md: 8464128 B read + 1476233984 B written
+    ("march", "ca8c733119bda80da874e473686db49dc068992310fb3087748c81a8c1f3c302"): 1484698112,
+}
+
+# What limits each stage (from the ncu captures summarised under profiles/).
+LIMITER = {
+    "march": "issue: bit-exact float32 lattice arithmetic, ~70% issue-active at ~25% DRAM",
+    "prune": "DRAM latency (long-scoreboard stalls)",
+    "render_fwd": "DRAM latency / issue",
+    "render_bwd": "DRAM latency (long-scoreboard stalls)",
+    "grid_update": "latency of 2^21 random atomics",
+}
 
 
 def parse():
@@ -435,7 +447,8 @@ def run_ours(args):
                      "frac": round(step_bytes / (mean_ms / 1e3) / 1e9 / peak, 4), "peak_gbs": peak,
                      "peak_kind": peak_kind},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind},
+                     "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes": int(sb[dom]), "limiter": LIMITER[dom]},
         "wall_s_timed_loop_incl_field": round(t_wall, 3),
         "gpu_launches": 6 * args.steps,
         "clocks": clk,
