@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rays", type=int, default=N_RAYS)
+    ap.add_argument("--workload", default="bounded", choices=["bounded", "tiny", "unbounded", "batched", "dynamic"],
+                    help="bounded (default) is the headline configuration; the others are the wider configurations")
+    ap.add_argument("--no-batched-compare", action="store_true")
     ap.add_argument("--cpu-rays", type=int, default=1 << 15, help="rays in the CPU-baseline sample")
     ap.add_argument("--ref-rays", type=int, default=1 << 12, help="rays per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -280,6 +283,22 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 
+WORKLOAD_CONFIG = {
+    "bounded": {"cameras": "100 x 800x800, fx=fy=1111.1, r=4", "scene": "64 Gaussian blobs",
+                "grid": "128^3 bitfield over [-1.5,1.5]^3 (density > 0.01)", "dt": "sqrt(3)*3/1024, max 1024 steps",
+                "early_stop_eps": 1e-4, "alpha_thre": 1e-2},
+    "tiny": {"cameras": "1 x 64x64, fx=fy=80, r=4", "scene": "8 Gaussian blobs", "grid": "64^3 (density > 0.01)",
+             "dt": "sqrt(3)*3/512", "pruning": "off"},
+    "unbounded": {"cameras": "64 inside radius 100, random directions", "scene": "256 blobs, log-uniform scale",
+                  "grid": "4-level cascade of 128^3, level-0 box [-125,125]^3",
+                  "dt": "cone: clamp(t/256, 1e-3, 10), t in [0.05, 1000]", "early_stop_eps": 1e-4, "alpha_thre": 1e-2},
+    "batched": {"scenes": "64 (8-256 blobs each, own 128^3 grid)", "rays": "lognormal per scene, scene-major",
+                "dt": "sqrt(3)*3/1024, max 1024 steps", "early_stop_eps": 1e-4, "alpha_thre": 1e-2},
+    "dynamic": {"scene": "128 moving blobs, t in [0,1]", "grid": "16 time bins x 128^3",
+                "dt": "sqrt(3)*3/1024, max 1024 steps", "early_stop_eps": 1e-4, "alpha_thre": 1e-2},
+}
+
+
 def run_ours(args):
     import torch
 
@@ -290,46 +309,40 @@ def run_ours(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
-    from paper_2210_04847_gb300 import _lib, api, synth
-    from paper_2210_04847_gb300.pipeline import HotPath, StandInField, to_device
+    from paper_2210_04847_gb300 import _lib, autotune
+    from paper_2210_04847_gb300.pipeline import HotPath
+    from paper_2210_04847_gb300.scenarios import make_scenario
 
-    R = args.rays
-    scene, aabb, bits_np = synth.bounded_scene(0, device=dev)
-    batches = []
-    for b in rank_batches(rank):
-        o, d, tgt = synth.bounded_rays(0, R, batch=b)
-        batches.append((to_device(o, dev), to_device(d, dev), to_device(tgt, dev), o, d, tgt))
-    w = synth.bounded_config(0, n_rays=R, scene_grid=(scene, aabb, bits_np), batch=rank_batches(rank)[0])
-    field = StandInField(scene, dev)
-    n_cells = 128 ** 3
+    sc = make_scenario(args.workload, rank, dev, n_rays=args.rays if args.workload == "bounded" else None)
+    w = sc.w
+    R = w.n_rays
+    n_pool = len(sc.batches)
 
-    # probe step to size the buffers (capacity + 30% slack)
-    probe = HotPath(w, cap_marched=R * w.max_steps, cap_kept=R * w.max_steps, n_grid_samples=0, device=dev)
-    o0, d0 = batches[0][0], batches[0][1]
-    probe.march(o0, d0)
+    # probe step to size the buffers (capacity + 30% slack): march with a generous
+    # capacity, then march + prune with exact capacities
+    b0 = sc.batches[0]
+    probe = HotPath(w, cap_marched=R * min(w.max_steps, 1024), cap_kept=1, device=dev)
+    probe.march(b0["o"], b0["d"], b0["time"], b0["slot"])
     M0 = int(probe.n_m.item())
-    probe.field_marched(field, o0, d0, M0)
+    del probe
+    torch.cuda.empty_cache()
+    probe = HotPath(w, cap_marched=M0, cap_kept=M0, device=dev)
+    probe.march(b0["o"], b0["d"], b0["time"], b0["slot"])
+    sc.field_marched(probe, 0, M0)
     probe.prune(M0)
     S0 = int(probe.n_k.item())
     probe.check_status("probe")
     del probe
     torch.cuda.empty_cache()
-    hp = HotPath(w, cap_marched=int(M0 * 1.3) + 4096, cap_kept=int(S0 * 1.3) + 4096,
-                 n_grid_samples=N_GRID_SAMPLES, device=dev)
+    hp = HotPath(w, cap_marched=int(M0 * 1.3) + 4096, cap_kept=int(S0 * 1.3) + 4096, n_grid_samples=sc.n_grid,
+                 device=dev)
     # The grid update refreshes its own EMA state (initialised from the density at the
-    # cell centres, the same rule that built the marched bitfield), so every step
-    # marches the same grid and the workload stays stationary.
-    dens = synth.density_at_cell_centres(scene, aabb, (128, 128, 128), 1, None, dev)
-    hp.ema.copy_(dens.float())
+    # cell centres, the same rule that built the marched bitfield) and writes its own
+    # bitfield, so every step marches the same grid and the workload stays stationary.
+    hp.ema.copy_(sc.ema_init())
     upd_bits = torch.zeros_like(hp.bits)
-    # grid-update samples of each step: uniform random cells, field at a jittered point in each (user side)
-    grid_inputs = []
-    for s in range(POOL):
-        cells, jit = synth.grid_update_samples(rank, s, N_GRID_SAMPLES, n_cells)
-        xyz = synth.cell_positions(cells, jit, aabb, (128, 128, 128))
-        grid_inputs.append((to_device(cells, dev), to_device(xyz.astype(np.float32), dev)))
+    grid_inputs = [sc.grid_inputs(s) for s in range(POOL)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # larger than the 126 MB L2
-    from paper_2210_04847_gb300 import autotune
 
     if args.knobs:
         tuned = {}
@@ -338,7 +351,7 @@ def run_ours(args):
             _lib.tune_set(k.strip(), int(v))
             tuned[k.strip()] = {"best": int(v), "fixed": True}
     else:
-        tuned = autotune.tune_hot_path(hp, field, batches[0][0], batches[0][1])
+        tuned = autotune.tune_hot_path(hp, sc, 0)
 
     stages = ["march", "prune", "render_fwd", "render_bwd", "grid_update"]
     ev = {s: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for s in stages}
@@ -347,28 +360,29 @@ def run_ours(args):
     m_read = []
 
     def step(i, timed):
-        o, d, tgt = batches[i % POOL][:3]
-        cells, xyz = grid_inputs[i % POOL]
+        b = i % n_pool
+        bt = sc.batches[b]
+        gi = grid_inputs[i % POOL]
         flush.zero_()
         ev["march"][0].record()
-        hp.march(o, d)
+        hp.march(bt["o"], bt["d"], bt["time"], bt["slot"])
         ev["march"][1].record()
         M = int(hp.n_m.item())
-        hp.field_marched(field, o, d, M)
+        sc.field_marched(hp, b, M)
         ev["prune"][0].record()
         hp.prune(M)
         ev["prune"][1].record()
         S = int(hp.n_k.item())
-        hp.field_kept(field, o, d, S)
+        sc.field_kept(hp, b, S)
         ev["render_fwd"][0].record()
         hp.render_fwd(S)
         ev["render_fwd"][1].record()
-        hp.loss_grad(tgt)
+        hp.loss_grad(bt["tgt"])
         ev["render_bwd"][0].record()
         hp.render_bwd(S)
         ev["render_bwd"][1].record()
-        field.points(xyz, N_GRID_SAMPLES, hp.cell_sig)
-        hp.cells.copy_(cells)
+        sc.grid_field(gi, hp.cell_sig)
+        hp.cells.copy_(gi["cells"])
         ev["grid_update"][0].record()
         hp.grid_update(bits=upd_bits)
         ev["grid_update"][1].record()
@@ -407,38 +421,39 @@ def run_ours(args):
     M_avg = sum(c[0] for c in counts) / len(counts)
     S_avg = sum(c[1] for c in counts) / len(counts)
     Mr_avg = sum(m_read) / len(m_read)
-    grid_bytes = (n_cells + 7) // 8
-    sb = stage_bytes(R, M_avg, Mr_avg, S_avg, grid_bytes, n_cells, N_GRID_SAMPLES)
+    grid_bytes = (sc.n_cells + 7) // 8
+    sb = stage_bytes(R, M_avg, Mr_avg, S_avg, grid_bytes, sc.n_cells, sc.n_grid)
     peak, peak_kind = measured_peaks()
     avg = {s: sum(v) / len(v) for s, v in stage_ms.items()}
     dom = max(stages, key=lambda s: avg[s])
     achieved = sb[dom] / (avg[dom] / 1e3) / 1e9
-    key = (dom, kernel_source_sha(dom))
-    traffic = NCU_TRAFFIC.get(key)
+    traffic = NCU_TRAFFIC.get((dom, kernel_source_sha(dom))) if args.workload == "bounded" and R == N_RAYS else None
     step_bytes = sum(sb.values())
 
+    extra = {}
+    if args.workload == "batched" and not args.no_batched_compare:
+        extra["per_scene_plain"] = run_per_scene_plain(args, sc, hp, dev)
     e2e = None
-    if not args.no_e2e:
-        e2e = run_e2e(args, dev, batches, grid_inputs, scene, aabb, bits_np, field)
+    if not args.no_e2e and args.workload == "bounded":
+        e2e = run_e2e(args, dev, sc)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(scene, aabb, bits_np, R, args.cpu_rays)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "bounded":
+        cpu = cpu_baseline(sc.scenes[0], w.aabb, w.bits, R, args.cpu_rays)
 
     if rank != 0:
         return 0
+    cfg = {"workload": w.name, "rays_per_step_per_gpu": R}
+    cfg.update(WORKLOAD_CONFIG[args.workload])
+    cfg.update({
+        "grid_update_samples": sc.n_grid, "parallelism": "rays sharded per GPU (weak), %d GPU(s)" % world,
+        "l2": "flushed before every step (256 MB write); per-step working set > 1 GB",
+        "timed": "march + prune + render_fwd + render_bwd + grid_update (field and loss are user code, untimed)",
+    })
     line = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms_all, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {
-            "workload": w.name, "rays_per_step_per_gpu": R, "cameras": "100 x 800x800, fx=fy=1111.1, r=4",
-            "scene": "64 Gaussian blobs", "grid": "128^3 bitfield over [-1.5,1.5]^3 (density > 0.01)",
-            "dt": "sqrt(3)*3/1024, max 1024 steps", "early_stop_eps": 1e-4, "alpha_thre": 1e-2,
-            "grid_update_samples": N_GRID_SAMPLES, "parallelism": "rays sharded per GPU (weak), %d GPU(s)" % world,
-            "l2": "flushed before every step (256 MB write); per-step working set > 1 GB",
-            "timed": "march + prune + render_fwd + render_bwd + grid_update (field and loss are user code, untimed)",
-        },
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
         "tuned": {k: v["best"] for k, v in tuned.items()},
         "stages_ms": {s: round(avg[s], 4) for s in stages},
         "stage_gbs": {s: round(sb[s] / (avg[s] / 1e3) / 1e9, 1) for s in stages},
@@ -455,24 +470,85 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
     }
+    line.update(extra)
     print(json.dumps(line))
     return 0
 
 
-def run_e2e(args, dev, batches, grid_inputs, scene, aabb, bits_np, field):
+def run_per_scene_plain(args, sc, hp_all, dev):
+    """The batched workload as 64 separate plain launch sequences (one per scene,
+    host synchronisation between stages), for comparison with the single launch
+    per stage over all scenes. Same kernels, same outputs."""
+    import torch
+
+    from paper_2210_04847_gb300 import synth
+    from paper_2210_04847_gb300.pipeline import HotPath
+
+    w = sc.w
+    counts = np.asarray(sc.rays_per_scene)
+    first = np.concatenate([[0], np.cumsum(counts)])
+    words_per_scene = int(np.prod(w.res)) // 32
+    bt = sc.batches[0]
+    per = []
+    for s in range(len(counts)):
+        a, e = int(first[s]), int(first[s + 1])
+        ws = synth.Workload("scene", w.rays_o[a:e], w.rays_d[a:e], w.bits[s * words_per_scene:(s + 1) * words_per_scene],
+                            w.res, 1, 1, w.aabb, w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone, w.max_steps,
+                            w.early_stop_eps, w.alpha_thre)
+        hp = HotPath(ws, cap_marched=(e - a) * w.max_steps, cap_kept=(e - a) * w.max_steps, device=dev)
+        per.append((a, e, hp))
+    o, d, tgt = bt["o"], bt["d"], bt["tgt"]
+    times = []
+    for rep in range(args.warmup + args.steps):
+        tot = 0.0
+        for s, (a, e, hp) in enumerate(per):
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+            oo, dd = o[a:e].contiguous(), d[a:e].contiguous()
+            evs[0].record()
+            hp.march(oo, dd)
+            evs[1].record()
+            M = int(hp.n_m.item())
+            sc.fields[s].samples(oo, dd, hp.ri_m, hp.ts_m, hp.te_m, M, hp.sig_m)
+            evs[2].record()
+            hp.prune(M)
+            evs[3].record()
+            S = int(hp.n_k.item())
+            sc.fields[s].samples(oo, dd, hp.ri_k, hp.ts_k, hp.te_k, S, hp.sig_k, hp.rgb_k)
+            evs[4].record()
+            hp.render_fwd(S)
+            evs[5].record()
+            hp.loss_grad(tgt[a:e])
+            evs[6].record()
+            hp.render_bwd(S)
+            evs[7].record()
+            torch.cuda.synchronize()
+            tot += sum(evs[2 * k].elapsed_time(evs[2 * k + 1]) for k in range(4))
+        if rep >= args.warmup:
+            times.append(tot)
+    ms = sum(times) / len(times)
+    return {"ms_per_step_march_prune_fwd_bwd": round(ms, 4), "rays_per_s": w.n_rays / (ms / 1e3),
+            "launch_sequences": len(per),
+            "note": "64 plain launch sequences (march, prune, render fwd, render bwd per scene, host sync between "
+                    "stages); compare with stages_ms of the single launches over all scenes (grid update excluded)"}
+
+
+def run_e2e(args, dev, sc):
     """Same metric through the public API: rays + targets copied from pinned host
     memory each step, colours and loss copied back; field time subtracted."""
     import torch
 
     from paper_2210_04847_gb300 import api, synth
 
-    R = args.rays
-    grid = api.OccupancyGrid.from_bits(bits_np, (128, 128, 128), aabb, device=dev)
+    R = sc.n_rays
+    aabb = sc.w.aabb
+    field = sc.fields[0]
+    grid = api.OccupancyGrid.from_bits(sc.w.bits, (128, 128, 128), aabb, device=dev)
     # the grid refreshed every step (its own EMA state, see run_ours)
     upd = api.OccupancyGrid(aabb, 128, device=dev)
-    upd.ema.copy_(synth.density_at_cell_centres(scene, aabb, (128, 128, 128), 1, None, dev).float())
-    host = [(torch.from_numpy(o).pin_memory(), torch.from_numpy(d).pin_memory(), torch.from_numpy(t).pin_memory())
-            for (_, _, _, o, d, t) in batches]
+    upd.ema.copy_(sc.ema_init())
+    host = [(torch.from_numpy(b["host"].rays_o).pin_memory(), torch.from_numpy(b["host"].rays_d).pin_memory(),
+             torch.from_numpy(b["host"].target_rgb).pin_memory()) for b in sc.batches]
+    grid_inputs = [sc.grid_inputs(s) for s in range(POOL)]
     out_host = torch.empty((R, 3), dtype=torch.float32).pin_memory()
     loss_host = torch.empty((), dtype=torch.float32).pin_memory()
     dt = synth.SQRT3 * 3.0 / 1024.0
@@ -505,8 +581,9 @@ def run_e2e(args, dev, batches, grid_inputs, scene, aabb, bits_np, field):
     sig_cells = torch.empty(N_GRID_SAMPLES, dtype=torch.float32, device=dev)
 
     def one(i):
-        ho, hd, ht = host[i % POOL]
-        cells, xyz = grid_inputs[i % POOL]
+        ho, hd, ht = host[i % len(host)]
+        gi = grid_inputs[i % POOL]
+        cells, xyz = gi["cells"], gi["xyz"]
         field_ms.clear()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()

@@ -59,21 +59,23 @@ def tune_knob(knob: str, fn: Callable[[], None], candidates: Iterable[int] = Non
     return {"knob": knob, "best": best, "ms": {str(k): round(t, 4) for k, t in times.items()}}
 
 
-def tune_hot_path(hp, field, rays_o, rays_d, reps: int = 5):
-    """Tune the knobs of one ``pipeline.HotPath`` on one batch of rays (leaves its buffers holding that batch)."""
+def tune_hot_path(hp, sc, batch: int = 0, reps: int = 5):
+    """Tune the knobs of one ``pipeline.HotPath`` on one batch of a ``scenarios.Scenario``
+    (leaves its buffers holding that batch)."""
+    bt = sc.batches[batch]
     rec = []
-    march = lambda: hp.march(rays_o, rays_d)
+    march = lambda: hp.march(bt["o"], bt["d"], bt["time"], bt["slot"])
     rec.append(tune_knob("march_tile_rays", march, reps=reps))
     rec.append(tune_knob("march_occupancy", march, reps=reps))
-    hp.march(rays_o, rays_d)
+    march()
     M = int(hp.n_m.item())
-    hp.field_marched(field, rays_o, rays_d, M)
+    sc.field_marched(hp, batch, M)
     prune = lambda: hp.prune(M)
     rec.append(tune_knob("prune_tile_rays", prune, reps=reps))
     rec.append(tune_knob("prune_occupancy", prune, reps=reps))
     hp.prune(M)
     S = int(hp.n_k.item())
-    hp.field_kept(field, rays_o, rays_d, S)
+    sc.field_kept(hp, batch, S)
     fwd = lambda: hp.render_fwd(S)
     rec.append(tune_knob("render_fwd_prefetch", fwd, reps=reps))
     rec.append(tune_knob("render_fwd_occupancy", fwd, reps=reps))

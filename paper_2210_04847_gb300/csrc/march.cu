@@ -17,8 +17,12 @@
 //     __popc gives the count. Lane i of the warp keeps ray i's count, chunk
 //     count and [near, far].
 //   * Cone steps (t_{k+1} = t_k + clamp(t_k*cone, dt_min, dt_max)): the
-//     lattice is a sequential float32 recurrence, so one thread walks one ray;
-//     it counts first and walks again to write.
+//     lattice is a sequential float32 recurrence that depends only on its start.
+//     Every ray that starts inside the outermost box starts at near_plane, so a
+//     one-thread prologue writes that shared lattice once per call into the
+//     workspace and the warps read t_k from it, lane-parallel, exactly as for
+//     uniform steps. A ray with another start has lane 0 extend its own
+//     recurrence 32 steps at a time into the warp's shared memory.
 //   * The tile's total becomes its global offset through a bounded decoupled
 //     look-back run by the warp itself; the warp then re-expands the ballot
 //     words into compacted, coalesced stores of (t_start, t_end, ray).
@@ -33,7 +37,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kTileRaysMax = 32;  // rays per warp tile (uniform steps), lane i holds ray i
-constexpr int kTileCone = kThreads;  // rays per block tile (cone steps, thread-per-ray walk)
 
 struct Levels {
     float lo[NACC_MAX_LEVELS][3];
@@ -67,6 +70,7 @@ struct MarchArgs {
     int32_t n_tiles;
     int32_t mask_words;
     int32_t tile_rays;
+    const float* cone_table;  // t_0 = near_plane, t_1, ..., t_max_steps (cone steps only)
     Levels L;
 };
 
@@ -150,15 +154,65 @@ __device__ __forceinline__ int lattice_count(const MarchArgs& a, float near, flo
 }
 
 // ---------------------------------------------------------------------------
-// uniform steps: warp per ray
+// cone lattice
 // ---------------------------------------------------------------------------
 
-template <int MAXL, int MINB>
+__device__ __forceinline__ float cone_step(const MarchArgs& a, float t) {
+    float dt = __fmul_rn(t, a.cone);
+    if (dt < a.dt_min) dt = a.dt_min;
+    if (dt > a.dt_max) dt = a.dt_max;
+    return __fadd_rn(t, dt);
+}
+
+// The lattice of rays starting at near_plane: table[k] = t_k, k = 0..max_steps.
+__global__ void cone_table_kernel(const MarchArgs a, float* table) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    float t = a.near_plane;
+    for (int k = 0; k <= a.max_steps; ++k) {
+        table[k] = t;
+        t = cone_step(a, t);
+    }
+}
+
+// First k in [0, max_steps] with table[k] >= far (the table is non-decreasing).
+__device__ __forceinline__ int table_count(const float* table, int max_steps, float far) {
+    int lo = 0, hi = max_steps;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(table + mid) < far) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Lane 0 extends a ray's own cone recurrence by 32 steps: buf[j] = t_{32c + j},
+// j = 0..32, starting from *t (t_{32c}); *t becomes t_{32c + 32}.
+__device__ __forceinline__ void cone_extend(const MarchArgs& a, float* buf, float& t, int lane) {
+    if (lane == 0) {
+        float v = t;
+#pragma unroll 1
+        for (int j = 0; j <= 32; ++j) {
+            buf[j] = v;
+            if (j < 32) v = cone_step(a, v);
+        }
+        t = v;
+    }
+    t = __shfl_sync(FULL, t, 0);
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// warp per ray (uniform steps, or cone steps through the lattice table)
+// ---------------------------------------------------------------------------
+
+template <int MAXL, int MINB, bool CONE>
 __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const MarchArgs a) {
     extern __shared__ uint32_t s_masks[];  // per warp: [tile_rays][mask_words]
+    __shared__ float s_lat[kWarps][36];    // cone steps with a ray-specific start
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     uint32_t* wmask = s_masks + (size_t)warp * a.tile_rays * a.mask_words;
+    float* lat = s_lat[warp];
     const float dt = a.dt_min;
     const unsigned lt = lanemask_lt();
 
@@ -187,17 +241,33 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
             const bool slot_ok = slot >= 0 && slot < a.n_slots;
             if (!slot_ok && lane == 0) raise_status(a.d_status, NACC_STATUS_BAD_INDEX);
             if (slot_ok && clip_ray(a, o, d, near, far)) {
-                const int nk = lattice_count(a, near, far, dt);
-                nch = (nk + 31) >> 5;
+                const bool shared = !CONE || near == a.near_plane;
+                // shared lattices know their length; an own cone lattice ends when t_k >= far
+                const int nk = !CONE ? lattice_count(a, near, far, dt)
+                                     : (shared ? table_count(a.cone_table, a.max_steps, far) : a.max_steps);
+                const int max_ch = (nk + 31) >> 5;
                 const unsigned sl0 = (unsigned)slot * (unsigned)a.n_levels;
                 uint32_t* row = wmask + i * a.mask_words;
-                for (int c = 0; c < nch; ++c) {
+                float tcur = near;
+                for (int c = 0; c < max_ch; ++c) {
                     const int k = (c << 5) + lane;
-                    bool occ = false;
-                    if (k < nk) {
+                    float ts, tn;
+                    if (!CONE) {
                         const float kf = __int2float_rn(k);
-                        const float ts = __fadd_rn(near, __fmul_rn(kf, dt));
-                        const float tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+                        ts = __fadd_rn(near, __fmul_rn(kf, dt));
+                        tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+                    } else if (shared) {
+                        ts = __ldg(a.cone_table + min(k, a.max_steps));
+                        tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                    } else {
+                        cone_extend(a, lat, tcur, lane);
+                        ts = lat[lane];
+                        tn = lat[lane + 1];
+                    }
+                    const bool valid = k < nk && ts < far;
+                    if (CONE && !shared && __ballot_sync(FULL, valid) == 0u) break;
+                    bool occ = false;
+                    if (valid) {
                         const float te = tn < far ? tn : far;
                         const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
                         const float x0 = __fadd_rn(o[0], __fmul_rn(d[0], mid));
@@ -208,6 +278,7 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
                     const unsigned m = __ballot_sync(FULL, occ);
                     if (lane == 0) row[c] = m;
                     count += __popc(m);
+                    nch = c + 1;
                 }
             }
             if (lane == i) {
@@ -237,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
 
         // phase 3: expand the ballot words into compacted, coalesced stores. Output
         // positions fit 32 bits: the tile starts below capacity <= 2^31 - 1 and adds
-        // at most tile_rays * max_steps <= 2^18 samples.
+        // at most tile_rays * max_steps <= 2^20 samples.
         if (excl < a.capacity) {
             const unsigned cap = (unsigned)(a.capacity < 0x7fffffffLL ? a.capacity : 0x7fffffffLL);
             for (int i = 0; i < nr; ++i) {
@@ -246,16 +317,29 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
                 const int nch = __shfl_sync(FULL, my_nch, i);
                 const float near = __shfl_sync(FULL, my_near, i);
                 const float far = __shfl_sync(FULL, my_far, i);
+                const bool shared = !CONE || near == a.near_plane;
                 const int r = ray0 + i;
                 const uint32_t* row = wmask + i * a.mask_words;
                 unsigned base = (unsigned)excl + (unsigned)__shfl_sync(FULL, my_excl, i);
+                float tcur = near;
                 for (int c = 0; c < nch; ++c) {
                     const unsigned m = row[c];
+                    const int k = (c << 5) + lane;
+                    float ts, tn;
+                    if (!CONE) {
+                        const float kf = __int2float_rn(k);
+                        ts = __fadd_rn(near, __fmul_rn(kf, dt));
+                        tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+                    } else if (shared) {
+                        ts = __ldg(a.cone_table + min(k, a.max_steps));
+                        tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                    } else {
+                        cone_extend(a, lat, tcur, lane);
+                        ts = lat[lane];
+                        tn = lat[lane + 1];
+                    }
                     const unsigned pos = base + __popc(m & lt);
                     if (((m >> lane) & 1u) && pos < cap) {
-                        const float kf = __int2float_rn((c << 5) + lane);
-                        const float ts = __fadd_rn(near, __fmul_rn(kf, dt));
-                        const float tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
                         a.t_starts[pos] = ts;
                         a.t_ends[pos] = tn < far ? tn : far;
                         a.ray_indices[pos] = r;
@@ -265,114 +349,6 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
             }
         }
         __syncwarp();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// cone steps: thread per ray (sequential float32 recurrence)
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ float cone_step(const MarchArgs& a, float t) {
-    float dt = __fmul_rn(t, a.cone);
-    if (dt < a.dt_min) dt = a.dt_min;
-    if (dt > a.dt_max) dt = a.dt_max;
-    return __fadd_rn(t, dt);
-}
-
-template <int MAXL>
-__device__ int walk_cone(const MarchArgs& a, const float o[3], const float d[3], float near, float far,
-                         unsigned sl0, int r, long long out, bool write) {
-    int count = 0;
-    float t = near;
-    for (int k = 0; k < a.max_steps; ++k) {
-        const float ts = t;
-        const float tn = cone_step(a, t);
-        t = tn;
-        if (!(ts < far)) break;
-        const float te = tn < far ? tn : far;
-        const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
-        const float x0 = __fadd_rn(o[0], __fmul_rn(d[0], mid));
-        const float x1 = __fadd_rn(o[1], __fmul_rn(d[1], mid));
-        const float x2 = __fadd_rn(o[2], __fmul_rn(d[2], mid));
-        if (occupied<MAXL>(a, x0, x1, x2, sl0)) {
-            if (write) {
-                const long long pos = out + count;
-                if (pos < a.capacity) {
-                    a.t_starts[pos] = ts;
-                    a.t_ends[pos] = te;
-                    a.ray_indices[pos] = r;
-                }
-            }
-            ++count;
-        }
-    }
-    return count;
-}
-
-template <int MAXL>
-__global__ void __launch_bounds__(kThreads) march_cone_kernel(const MarchArgs a) {
-    __shared__ int s_warp_tot[kWarps];
-    __shared__ int s_tile;
-    __shared__ long long s_tile_excl;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(a.ticket, 1u);
-        __syncthreads();
-        const int tile = s_tile;
-        if (tile >= a.n_tiles) break;
-        const int r = tile * kTileCone + threadIdx.x;
-        const bool have = r < a.n_rays;
-        float o[3] = {0, 0, 0}, d[3] = {0, 0, 0};
-        float near = 0.0f, far = 0.0f;
-        bool live = false;
-        unsigned sl0 = 0;
-        if (have) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                o[k] = __ldg(a.rays_o + 3 * (size_t)r + k);
-                d[k] = __ldg(a.rays_d + 3 * (size_t)r + k);
-            }
-            const int slot = slot_of(a, r);
-            if (slot >= 0 && slot < a.n_slots) {
-                sl0 = (unsigned)slot * (unsigned)a.n_levels;
-                live = clip_ray(a, o, d, near, far);
-            } else {
-                raise_status(a.d_status, NACC_STATUS_BAD_INDEX);
-            }
-        }
-        const int cnt = live ? walk_cone<MAXL>(a, o, d, near, far, sl0, r, 0, false) : 0;
-
-        // block-wide exclusive scan of the 256 counts
-        const int incl = warp_incl_scan_int(cnt, lane);
-        if (lane == 31) s_warp_tot[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            int wt = lane < kWarps ? s_warp_tot[lane] : 0;
-            const int wincl = warp_incl_scan_int(wt, lane);
-            if (lane < kWarps) s_warp_tot[lane] = wincl - wt;
-            const int agg = __shfl_sync(FULL, wincl, kWarps - 1);
-            const unsigned long long excl =
-                lookback(a.tile_status, tile, (unsigned long long)agg, lane, a.d_status);
-            if (lane == 0) {
-                s_tile_excl = (long long)excl;
-                if (tile == a.n_tiles - 1) {
-                    const long long total = (long long)excl + agg;
-                    *a.n_samples = total;
-                    if (total > a.capacity) raise_status(a.d_status, NACC_STATUS_CAPACITY);
-                    if (total > 0x7fffffffLL) raise_status(a.d_status, NACC_STATUS_OVERFLOW);
-                }
-            }
-        }
-        __syncthreads();
-        const long long off = s_tile_excl + s_warp_tot[warp] + (incl - cnt);
-        if (have) {
-            a.packed_info[2 * (size_t)r] = (int32_t)off;
-            a.packed_info[2 * (size_t)r + 1] = cnt;
-        }
-        if (cnt > 0) walk_cone<MAXL>(a, o, d, near, far, sl0, r, off, true);
-        __syncthreads();
     }
 }
 
@@ -395,9 +371,15 @@ int tile_rays_for(int mask_words) {
     return t;
 }
 
-size_t workspace_bytes_for(int32_t n_rays) {
+size_t status_bytes_for(int32_t n_rays) {
     // the smallest warp tile is one ray: size for one status word per ray
     return align_up(kTicketBytes + (size_t)n_rays * sizeof(unsigned long long), 256);
+}
+
+size_t workspace_bytes_for(int32_t n_rays, const nacc_march_params* p) {
+    size_t b = status_bytes_for(n_rays);
+    if (p && p->cone > 0.0f && p->max_steps >= 1) b += align_up(((size_t)p->max_steps + 1) * sizeof(float), 256);
+    return b;
 }
 
 // Level boxes and cell scales, float32, in the order the method defines them.
@@ -450,9 +432,8 @@ void launch_uniform(K kernel, size_t smem, int need, cudaStream_t st, const Marc
 using namespace nacc;
 
 extern "C" size_t nacc_march_workspace_size(int32_t n_rays, const nacc_march_params* params) {
-    (void)params;
     if (n_rays < 0) return 0;
-    return workspace_bytes_for(n_rays);
+    return workspace_bytes_for(n_rays, params);
 }
 
 extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const float* ray_time,
@@ -477,7 +458,7 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
         if (!(fabsf(grid->aabb[k]) < INFINITY)) return NACC_ERR_INVALID_ARG;
     for (int k = 0; k < 3; ++k)
         if (!(grid->aabb[k] < grid->aabb[3 + k])) return NACC_ERR_INVALID_ARG;
-    if (!workspace || workspace_bytes < workspace_bytes_for(n_rays)) return NACC_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < workspace_bytes_for(n_rays, p)) return NACC_ERR_INVALID_ARG;
     if (((uintptr_t)workspace & 255u) != 0) return NACC_ERR_INVALID_ARG;
     if (((uintptr_t)packed_info & 7u) != 0) return NACC_ERR_INVALID_ARG;
 
@@ -520,29 +501,33 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
     make_levels(*grid, a.L);
 
     const bool cone = p->cone > 0.0f;
-    a.n_tiles = cone ? (n_rays + kTileCone - 1) / kTileCone : (n_rays + a.tile_rays - 1) / a.tile_rays;
+    a.n_tiles = (n_rays + a.tile_rays - 1) / a.tile_rays;
     const size_t clear = kTicketBytes + (size_t)a.n_tiles * sizeof(unsigned long long);
     cudaError_t e = cudaMemsetAsync(workspace, 0, clear, st);
     if (e != cudaSuccess) return NACC_ERR_CUDA;
-
     if (cone) {
-        if (a.n_levels == 1) {
-            const int blocks = blocks_for(march_cone_kernel<1>, 0, a.n_tiles);
-            march_cone_kernel<1><<<blocks, kThreads, 0, st>>>(a);
+        float* table = (float*)((char*)workspace + status_bytes_for(n_rays));
+        a.cone_table = table;
+        cone_table_kernel<<<1, 32, 0, st>>>(a, table);
+    }
+    const size_t smem = (size_t)kWarps * a.tile_rays * a.mask_words * sizeof(uint32_t);
+    const int need = (a.n_tiles + kWarps - 1) / kWarps;
+    const bool occ = tune_get(NACC_TUNE_MARCH_OCCUPANCY) != 0;
+    if (a.n_levels == 1) {
+        if (cone) {
+            if (occ) launch_uniform(march_uniform_kernel<1, 8, true>, smem, need, st, a);
+            else launch_uniform(march_uniform_kernel<1, 1, true>, smem, need, st, a);
         } else {
-            const int blocks = blocks_for(march_cone_kernel<NACC_MAX_LEVELS>, 0, a.n_tiles);
-            march_cone_kernel<NACC_MAX_LEVELS><<<blocks, kThreads, 0, st>>>(a);
+            if (occ) launch_uniform(march_uniform_kernel<1, 8, false>, smem, need, st, a);
+            else launch_uniform(march_uniform_kernel<1, 1, false>, smem, need, st, a);
         }
     } else {
-        const size_t smem = (size_t)kWarps * a.tile_rays * a.mask_words * sizeof(uint32_t);
-        const int need = (a.n_tiles + kWarps - 1) / kWarps;
-        const bool occ = tune_get(NACC_TUNE_MARCH_OCCUPANCY) != 0;
-        if (a.n_levels == 1) {
-            if (occ) launch_uniform(march_uniform_kernel<1, 8>, smem, need, st, a);
-            else launch_uniform(march_uniform_kernel<1, 1>, smem, need, st, a);
+        if (cone) {
+            if (occ) launch_uniform(march_uniform_kernel<NACC_MAX_LEVELS, 8, true>, smem, need, st, a);
+            else launch_uniform(march_uniform_kernel<NACC_MAX_LEVELS, 1, true>, smem, need, st, a);
         } else {
-            if (occ) launch_uniform(march_uniform_kernel<NACC_MAX_LEVELS, 8>, smem, need, st, a);
-            else launch_uniform(march_uniform_kernel<NACC_MAX_LEVELS, 1>, smem, need, st, a);
+            if (occ) launch_uniform(march_uniform_kernel<NACC_MAX_LEVELS, 8, false>, smem, need, st, a);
+            else launch_uniform(march_uniform_kernel<NACC_MAX_LEVELS, 1, false>, smem, need, st, a);
         }
     }
     return launch_status(cudaGetLastError());

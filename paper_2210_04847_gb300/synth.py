@@ -122,7 +122,8 @@ class BlobScene:
     def rgb(self, x: np.ndarray) -> np.ndarray:
         """rgb(x) = sigmoid(W x + b) for points x (N, 3), float64."""
         x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
-        return 1.0 / (1.0 + np.exp(-(x @ self.rgb_w.T + self.rgb_b[None, :])))
+        with np.errstate(over="ignore"):  # far points saturate the sigmoid to 0 or 1
+            return 1.0 / (1.0 + np.exp(-(x @ self.rgb_w.T + self.rgb_b[None, :])))
 
     def device_params(self) -> np.ndarray:
         """Blob table as float32 rows (cx, cy, cz, 1/(2 s^2), peak, vx, vy, vz)."""
@@ -143,13 +144,16 @@ def make_blob_scene(
     ball: bool = False,
     speed: float = 0.0,
     stream_base: int = 0,
+    peak_scale_ref: Optional[float] = None,
 ) -> BlobScene:
     """Draw a blob scene.
 
     Centres uniform in the cube [-r, r]^3 (or the ball of radius r when
     ``ball``); scales uniform (or log-uniform) in ``scale_range``; peaks
     uniform in ``peak_range``; colour weights W ~ U[-2, 2]^{3x3},
-    b ~ U[-1, 1]^3; velocities U[-speed, speed]^3 when ``speed > 0``.
+    b ~ U[-1, 1]^3; velocities U[-speed, speed]^3 when ``speed > 0``. With
+    ``peak_scale_ref`` the peak is multiplied by ref / s, so every blob has the same
+    order of optical depth through its centre whatever its size.
     """
     s0 = stream_base
     if ball:
@@ -165,6 +169,8 @@ def make_blob_scene(
     else:
         scales = rand_uniform(seed, s0 + 3, n_blobs, *scale_range)
     peaks = rand_uniform(seed, s0 + 4, n_blobs, *peak_range)
+    if peak_scale_ref is not None:
+        peaks = peaks * (peak_scale_ref / scales)
     w = rand_uniform(seed, s0 + 5, 9, -2.0, 2.0).reshape(3, 3)
     b = rand_uniform(seed, s0 + 6, 3, -1.0, 1.0)
     vel = None
@@ -396,9 +402,11 @@ def bounded_config(seed: int = 0, n_rays: int = 1 << 18, n_cams: int = 100, devi
 
 def unbounded_config(seed: int = 0, n_rays: int = 1 << 20, n_cams: int = 64, device="cpu", batch: int = 0) -> Workload:
     """2^20 rays from 64 cameras inside radius 100 of a radius-1000 scene of 256
-    log-uniform-scale blobs; 4-level cascade of 128^3 (level-0 box [-125,125]^3);
-    cone step dt = clamp(t/256, 1e-3, 10), t in [0.05, 1000]."""
-    scene = make_blob_scene(seed, 256, center_radius=1000.0, scale_range=(0.1, 100.0), log_scale=True, ball=True)
+    log-uniform-scale blobs (scale in [0.1, 100], peak U[10, 50] * 0.1/scale);
+    4-level cascade of 128^3 (level-0 box [-125,125]^3); cone step
+    dt = clamp(t/256, 1e-3, 10), t in [0.05, 1000]."""
+    scene = make_blob_scene(seed, 256, center_radius=1000.0, scale_range=(0.1, 100.0), log_scale=True, ball=True,
+                            peak_scale_ref=0.1)
     g = random_unit_vectors(seed, 200, n_cams)
     cams = g * (100.0 * rand_uniform(seed, 201, n_cams) ** (1.0 / 3.0))[:, None]
     sb = 2000 + 16 * batch

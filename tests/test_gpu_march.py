@@ -104,3 +104,15 @@ def test_max_steps_many_chunks(orc):
     w.dt_min = w.dt_max = 2e-4
     w.max_steps = 32768
     assert_march_equal(gpu_march(w), oracle_march(orc, w))
+
+
+def test_cone_mixed_starts_bitexact(orc):
+    """Cone steps with rays starting outside the box (each ray its own recurrence from
+    t_in) and inside it (the lattice shared from near_plane), in one launch."""
+    w = synth.bounded_config(2, n_rays=3000, device="cuda")
+    inside = synth.rand_uniform(2, 7, 3 * 1000, -1.2, 1.2).reshape(1000, 3).astype(np.float32)
+    w.rays_o = np.ascontiguousarray(np.concatenate([w.rays_o[:2000], inside]))
+    w.cone, w.dt_min, w.dt_max, w.near_plane, w.max_steps = 1.0 / 64, 1e-3, 0.05, 0.05, 2048
+    g = gpu_march(w)
+    assert g[4] > 100000
+    assert_march_equal(g, oracle_march(orc, w))
