@@ -24,6 +24,16 @@ int nacc_field_samples(const float* rays_o, const float* rays_d, const float* ra
                        int64_t n, const float* blobs, int32_t n_blobs, const float* rgb_wb,
                        float* sigmas, float* rgbs, void* stream);
 
+/* Batch of scenes: the scene of a sample is the slot of its ray (ray_slot nullable =
+ * scene 0); scene s owns blob rows [blob_off[s], blob_off[s+1]) and colour weights
+ * rgb_wb[12 s ...]. The sample count is read from the device (*n_dev, at most
+ * n_max), so the call can be captured in a CUDA graph. */
+int nacc_field_samples_multi(const float* rays_o, const float* rays_d, const float* ray_time,
+                             const int32_t* ray_slot, const int32_t* ray_indices, const float* t_starts,
+                             const float* t_ends, const int64_t* n_dev, int64_t n_max, const float* blobs,
+                             const int32_t* blob_off, const float* rgb_wb, float* sigmas, float* rgbs,
+                             void* stream);
+
 /* Density at points xyz (n,3); times (n,) nullable (t = 0). */
 int nacc_field_points(const float* xyz, const float* times, int64_t n, const float* blobs,
                       int32_t n_blobs, float* sigmas, void* stream);

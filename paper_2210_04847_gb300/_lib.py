@@ -123,6 +123,8 @@ def load_field() -> ctypes.CDLL:
     L.nacc_field_samples.argtypes = [P, P, P, P, P, P, i64, P, i32, P, P, P, P]
     L.nacc_field_points.restype = ctypes.c_int
     L.nacc_field_points.argtypes = [P, P, i64, P, i32, P, P]
+    L.nacc_field_samples_multi.restype = ctypes.c_int
+    L.nacc_field_samples_multi.argtypes = [P, P, P, P, P, P, P, P, i64, P, P, P, P, P, P]
     _field = L
     return L
 
@@ -384,6 +386,16 @@ def field_samples(rays_o, rays_d, ray_indices, t_starts, t_ends, n: int, blobs, 
                                          _ptr(rgb_wb), _ptr(sigmas), _ptr(rgbs), _stream(stream))
     if rc != 0:
         raise NaccError("nacc_field_samples failed (%d)" % rc)
+
+
+def field_samples_multi(rays_o, rays_d, ray_slot, ray_indices, t_starts, t_ends, n_dev, n_max: int, blobs, blob_off,
+                        rgb_wb, sigmas, rgbs=None, ray_time=None, stream=None):
+    rc = load_field().nacc_field_samples_multi(_ptr(rays_o), _ptr(rays_d), _ptr(ray_time), _ptr(ray_slot),
+                                               _ptr(ray_indices), _ptr(t_starts), _ptr(t_ends), _ptr(n_dev), int(n_max),
+                                               _ptr(blobs), _ptr(blob_off), _ptr(rgb_wb), _ptr(sigmas), _ptr(rgbs),
+                                               _stream(stream))
+    if rc != 0:
+        raise NaccError("nacc_field_samples_multi failed (%d)" % rc)
 
 
 def field_points(xyz, n: int, blobs, sigmas, times=None, stream=None):

@@ -59,6 +59,39 @@ __global__ void __launch_bounds__(kThreads) points_kernel(const float* xyz, cons
         sigmas[i] = blob_density(tab, n_blobs, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], times ? times[i] : 0.0f);
 }
 
+// Field at sample midpoints for a batch of scenes: the scene of sample i is the
+// slot of its ray; scene s uses blob rows [blob_off[s], blob_off[s+1]) and colour
+// weights rgb_wb[12 s .. 12 s + 11]. The sample count is read on the device
+// (*n_dev, at most n_max), so the call can be captured in a CUDA graph.
+__global__ void __launch_bounds__(kThreads) samples_multi_kernel(const float* rays_o, const float* rays_d,
+                                                                const float* ray_time, const int32_t* ray_slot,
+                                                                const int32_t* ri, const float* ts, const float* te,
+                                                                const int64_t* n_dev, int64_t n_max,
+                                                                const float* blobs, const int32_t* blob_off,
+                                                                const float* wb_all, float* sigmas, float* rgbs) {
+    int64_t n = *n_dev;
+    if (n > n_max) n = n_max;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int r = ri[i];
+        const int s = ray_slot ? ray_slot[r] : 0;
+        const float mid = (ts[i] + te[i]) * 0.5f;
+        const float x = rays_o[3 * (size_t)r] + rays_d[3 * (size_t)r] * mid;
+        const float y = rays_o[3 * (size_t)r + 1] + rays_d[3 * (size_t)r + 1] * mid;
+        const float z = rays_o[3 * (size_t)r + 2] + rays_d[3 * (size_t)r + 2] * mid;
+        const float t = ray_time ? ray_time[r] : 0.0f;
+        const int b0 = blob_off[s], b1 = blob_off[s + 1];
+        sigmas[i] = blob_density(blobs + 8 * (size_t)b0, b1 - b0, x, y, z, t);
+        if (rgbs) {
+            const float* wb = wb_all + 12 * (size_t)s;
+            for (int c = 0; c < 3; ++c) {
+                const float v = wb[3 * c] * x + wb[3 * c + 1] * y + wb[3 * c + 2] * z + wb[9 + c];
+                rgbs[3 * i + c] = 1.0f / (1.0f + __expf(-v));
+            }
+        }
+    }
+}
+
 int grid_size(int64_t n) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -80,6 +113,19 @@ extern "C" int nacc_field_samples(const float* rays_o, const float* rays_d, cons
     if (smem > 48 * 1024) cudaFuncSetAttribute(samples_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     samples_kernel<<<grid_size(n), kThreads, smem, (cudaStream_t)stream>>>(
         rays_o, rays_d, ray_time, ray_indices, t_starts, t_ends, n, blobs, n_blobs, rgb_wb, sigmas, rgbs);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+extern "C" int nacc_field_samples_multi(const float* rays_o, const float* rays_d, const float* ray_time,
+                                        const int32_t* ray_slot, const int32_t* ray_indices, const float* t_starts,
+                                        const float* t_ends, const int64_t* n_dev, int64_t n_max, const float* blobs,
+                                        const int32_t* blob_off, const float* rgb_wb, float* sigmas, float* rgbs,
+                                        void* stream) {
+    if (n_max < 0 || !n_dev) return -1;
+    if (n_max == 0) return 0;
+    samples_multi_kernel<<<grid_size(n_max), kThreads, 0, (cudaStream_t)stream>>>(
+        rays_o, rays_d, ray_time, ray_slot, ray_indices, t_starts, t_ends, n_dev, n_max, blobs, blob_off, rgb_wb,
+        sigmas, rgbs);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

@@ -104,6 +104,32 @@ class Scenario:
             self.fields[s].points(xyz, idx.size, tmp)
             out[it] = tmp
 
+    # -- graph-capturable field (device-side counts, scene chosen per ray) ----
+    def _multi_tables(self):
+        if not hasattr(self, "_mt"):
+            tabs = [sc.device_params() for sc in self.scenes]
+            off = np.concatenate([[0], np.cumsum([t.shape[0] for t in tabs])]).astype(np.int32)
+            wb = np.stack([np.concatenate([sc.rgb_w.reshape(-1), sc.rgb_b]) for sc in self.scenes]).astype(np.float32)
+            self._mt = (to_device(np.concatenate(tabs), self.device), to_device(off, self.device),
+                        to_device(wb, self.device))
+        return self._mt
+
+    def field_marched_dev(self, hp, b):
+        from . import _lib
+
+        bt = self.batches[b]
+        blobs, off, wb = self._multi_tables()
+        _lib.field_samples_multi(bt["o"], bt["d"], bt["slot"], hp.ri_m, hp.ts_m, hp.te_m, hp.n_m, hp.cap_m, blobs,
+                                 off, wb, hp.sig_m, None, ray_time=bt["time"])
+
+    def field_kept_dev(self, hp, b):
+        from . import _lib
+
+        bt = self.batches[b]
+        blobs, off, wb = self._multi_tables()
+        _lib.field_samples_multi(bt["o"], bt["d"], bt["slot"], hp.ri_k, hp.ts_k, hp.te_k, hp.n_k, hp.cap_k, blobs,
+                                 off, wb, hp.sig_k, hp.rgb_k, ray_time=bt["time"])
+
     def ema_init(self):
         """float32 EMA grid initialised from the densities at the cell centres (the rule that built the bits)."""
         w = self.w

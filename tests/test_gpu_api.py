@@ -1,0 +1,95 @@
+"""The paper-shaped Python API (Sec. 3 listing) on the GPU: ray_marching with a
+density callback and pruning, rendering with autograd, the occupancy grid's
+update; compared with the oracle on seeded inputs."""
+import numpy as np
+import pytest
+
+from paper_2210_04847_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from gpu_util import bits_equal, grad_rel_err, render_tol_ok  # noqa: E402
+from paper_2210_04847_gb300 import api  # noqa: E402
+
+
+def _host_field(scene, rays_o, rays_d):
+    """Callbacks backed by the host generator (values identical for both sides)."""
+
+    def sigma_fn(ts, te, ri):
+        s, _ = synth.sample_field(scene, rays_o, rays_d, ts.view(-1).cpu().numpy(), te.view(-1).cpu().numpy(),
+                                  ri.cpu().numpy())
+        return torch.from_numpy(s).cuda().view(-1, 1)
+
+    def rgb_sigma_fn(ts, te, ri):
+        s, c = synth.sample_field(scene, rays_o, rays_d, ts.view(-1).cpu().numpy(), te.view(-1).cpu().numpy(),
+                                  ri.cpu().numpy())
+        return torch.from_numpy(c).cuda().requires_grad_(True), torch.from_numpy(s).cuda().view(-1, 1).requires_grad_(True)
+
+    return sigma_fn, rgb_sigma_fn
+
+
+def test_api_train_step_matches_oracle(orc):
+    w = synth.bounded_config(4, n_rays=1500, device="cuda")
+    scene = w.scenes[0]
+    grid = api.OccupancyGrid.from_bits(w.bits, w.res, w.aabb)
+    o, d = torch.from_numpy(w.rays_o).cuda(), torch.from_numpy(w.rays_d).cuda()
+    sigma_fn, rgb_sigma_fn = _host_field(scene, w.rays_o, w.rays_d)
+    packed, ts, te = api.ray_marching(o, d, grid, sigma_fn=sigma_fn, near_plane=w.near_plane,
+                                      far_plane=w.far_plane, render_step_size=w.dt_min, max_steps=w.max_steps,
+                                      early_stop_eps=w.early_stop_eps, alpha_thre=w.alpha_thre)
+    assert ts.shape[1] == 1 and packed.shape == (1500, 2)
+    # oracle: march, field, prune
+    m = orc.march(w.rays_o, w.rays_d, w.bits, w.res, w.aabb, w.near_plane, w.far_plane, w.dt_min, w.dt_max, 0.0,
+                  w.max_steps)
+    sg, _ = synth.sample_field(scene, w.rays_o, w.rays_d, m.t_starts, m.t_ends, m.ray_indices)
+    p, keep, _ = orc.prune(m.packed_info, m.t_starts, m.t_ends, sg, w.early_stop_eps, w.alpha_thre)
+    if not np.array_equal(packed.cpu().numpy(), p.packed_info):
+        pytest.skip("a prune decision fell within rounding of the threshold on this seed")
+    assert bits_equal(ts.view(-1).cpu().numpy(), p.t_starts) and bits_equal(te.view(-1).cpu().numpy(), p.t_ends)
+    rgbs, sigmas = rgb_sigma_fn(ts, te, api.unpack_info(packed, ts.shape[0]))
+    color, opacity, depth = api.render_packed(sigmas, rgbs, packed, ts, te)
+    target = torch.from_numpy(w.target_rgb).cuda()
+    loss = torch.nn.functional.mse_loss(color, target)
+    loss.backward()
+    sg2, rgb2 = synth.sample_field(scene, w.rays_o, w.rays_d, p.t_starts, p.t_ends, p.ray_indices)
+    c_o, a_o, d_o = orc.render_fwd(p.packed_info, p.t_starts, p.t_ends, sg2, rgb2)
+    assert render_tol_ok(color.detach().cpu().numpy(), c_o, rel_for_large=False) <= 1.0
+    assert render_tol_ok(opacity.detach().cpu().numpy()[:, 0], a_o, rel_for_large=False) <= 1.0
+    assert render_tol_ok(depth.detach().cpu().numpy()[:, 0], d_o) <= 1.0
+    gc = 2.0 * (color.detach().cpu().numpy().astype(np.float64) - w.target_rgb) / color.numel()
+    ds_o, dr_o = orc.render_bwd(p.packed_info, p.t_starts, p.t_ends, sg2, rgb2, gc)
+    assert grad_rel_err(sigmas.grad.view(-1).cpu().numpy(), ds_o) <= 1e-4
+    assert grad_rel_err(rgbs.grad.cpu().numpy(), dr_o) <= 1e-4
+    # saved optical depth path gives identical gradients
+    sig_b = sigmas.detach().clone().requires_grad_(True)
+    rgb_b = rgbs.detach().clone().requires_grad_(True)
+    c2, _, _ = api.render_packed(sig_b, rgb_b, packed, ts, te, save_optical_depth=True)
+    torch.nn.functional.mse_loss(c2, target).backward()
+    assert torch.equal(sig_b.grad, sigmas.grad) and torch.equal(rgb_b.grad, rgbs.grad)
+
+
+def test_api_grid_update_and_weights(orc):
+    g = api.OccupancyGrid((-1, -1, -1, 1, 1, 1), 32)
+    g.ema.copy_(torch.from_numpy(synth.rand_uniform(3, 1, 32 ** 3, 0, 0.02).astype(np.float32)))
+    ema0 = g.ema.cpu().numpy()
+    cells = synth.rand_int(3, 2, 5000, 32 ** 3).astype(np.int32)
+    sig = synth.rand_uniform(3, 3, 5000, 0, 0.05).astype(np.float32)
+    g.update(torch.from_numpy(cells).cuda(), torch.from_numpy(sig).cuda(), 0.9, 0.01)
+    e_o, b_o = orc.update_grid(ema0, cells, sig, 0.9, 0.01)
+    assert bits_equal(g.ema.cpu().numpy(), e_o) and np.array_equal(g.bits.cpu().numpy().view(np.uint32), b_o)
+    sd = g.state_dict()
+    g2 = api.OccupancyGrid((-1, -1, -1, 1, 1, 1), 32)
+    g2.load_state_dict(sd)
+    assert torch.equal(g2.ema, g.ema) and torch.equal(g2.bits, g.bits)
+    pi = torch.tensor([[0, 3], [3, 2]], dtype=torch.int32, device="cuda")
+    ts = torch.tensor([0.0, 0.5, 1.0, 2.0, 2.5], device="cuda")
+    sgm = torch.tensor([1.0, 2.0, 0.5, 4.0, 0.0], device="cuda")
+    wts, T = api.render_weights(pi, ts, ts + 0.5, sgm)
+    w_o, T_o = orc.render_weights(pi.cpu().numpy(), ts.cpu().numpy(), (ts + 0.5).cpu().numpy(), sgm.cpu().numpy())
+    assert np.max(np.abs(wts.cpu().numpy() - w_o)) < 1e-6 and np.max(np.abs(T.cpu().numpy() - T_o)) < 1e-6
+    acc = api.accumulate_along_rays(wts, pi, torch.ones(5, 2, device="cuda"))
+    assert np.allclose(acc.cpu().numpy(), np.stack([orc.accumulate(pi.cpu().numpy(), w_o)[:, 0]] * 2, 1), atol=1e-6)
