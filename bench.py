@@ -169,7 +169,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 
 
-def stage_bytes(R, M, M_read, S, grid_bytes, n_cells, n_grid):
+def stage_bytes(R, M, M_read, S, grid_bytes, n_cells, n_grid, saved_od=False):
     return {
         # read rays (24R), write packed_info (8R) and (t_start, t_end, ray) per sample (12M), read the bitfield once
         "march": 24 * R + 8 * R + 12 * M + grid_bytes,
@@ -177,9 +177,9 @@ def stage_bytes(R, M, M_read, S, grid_bytes, n_cells, n_grid):
         # write packed_info (8R) and the kept (t_start, t_end, ray) (12S)
         "prune": 8 * R + 12 * M_read + 8 * R + 12 * S,
         # read packed_info (8R) and (sigma, rgb, t_start, t_end) (24S); write rgb, opacity, depth (20R)
-        "render_fwd": 8 * R + 24 * S + 20 * R,
+        "render_fwd": 8 * R + 24 * S + 20 * R + (4 * S if saved_od else 0),
         # read g_color (12R), packed_info (8R), (sigma, rgb, t_start, t_end) (24S); write dsigma, drgb (16S)
-        "render_bwd": 12 * R + 8 * R + 24 * S + 16 * S,
+        "render_bwd": 12 * R + 8 * R + 24 * S + 16 * S + (4 * S if saved_od else 0),
         # read + write the float32 grid (8/cell), write the bits (1/8 per cell), read cells + sigmas (8/sample)
         "grid_update": 8 * n_cells + n_cells // 8 + 8 * n_grid,
     }
@@ -348,10 +348,13 @@ def run_ours(args):
         tuned = {}
         for kv in args.knobs.split(","):
             k, v = kv.split("=")
-            _lib.tune_set(k.strip(), int(v))
+            if k.strip() == "save_optical_depth":
+                hp.save_optical_depth = bool(int(v))
+            else:
+                _lib.tune_set(k.strip(), int(v))
             tuned[k.strip()] = {"best": int(v), "fixed": True}
     else:
-        tuned = autotune.tune_hot_path(hp, sc, 0)
+        tuned = autotune.tune_hot_path(hp, sc, 0, flush=flush.zero_)
 
     stages = ["march", "prune", "render_fwd", "render_bwd", "grid_update"]
     ev = {s: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for s in stages}
@@ -422,7 +425,7 @@ def run_ours(args):
     S_avg = sum(c[1] for c in counts) / len(counts)
     Mr_avg = sum(m_read) / len(m_read)
     grid_bytes = (sc.n_cells + 7) // 8
-    sb = stage_bytes(R, M_avg, Mr_avg, S_avg, grid_bytes, sc.n_cells, sc.n_grid)
+    sb = stage_bytes(R, M_avg, Mr_avg, S_avg, grid_bytes, sc.n_cells, sc.n_grid, hp.save_optical_depth)
     peak, peak_kind = measured_peaks()
     avg = {s: sum(v) / len(v) for s, v in stage_ms.items()}
     dom = max(stages, key=lambda s: avg[s])

@@ -19,8 +19,10 @@ from . import _lib
 CANDIDATES = {
     "march_tile_rays": (2, 4, 8, 16, 32),
     "march_occupancy": (0, 1),
+    "march_unroll": (0, 1),
     "prune_tile_rays": (2, 4, 8, 16, 32),
     "prune_occupancy": (0, 1, 2),
+    "prune_interleave": (2, 4),
     "render_fwd_prefetch": (0, 1),
     "render_fwd_occupancy": (0, 1, 2),
     "render_bwd_occupancy": (0, 1, 2),
@@ -59,29 +61,44 @@ def tune_knob(knob: str, fn: Callable[[], None], candidates: Iterable[int] = Non
     return {"knob": knob, "best": best, "ms": {str(k): round(t, 4) for k, t in times.items()}}
 
 
-def tune_hot_path(hp, sc, batch: int = 0, reps: int = 5):
+def tune_hot_path(hp, sc, batch: int = 0, reps: int = 7, flush: Callable[[], None] = None):
     """Tune the knobs of one ``pipeline.HotPath`` on one batch of a ``scenarios.Scenario``
-    (leaves its buffers holding that batch)."""
+    (leaves its buffers holding that batch). ``flush`` runs before every timed
+    repetition (e.g. a write larger than L2, as in the measured step)."""
     bt = sc.batches[batch]
     rec = []
+
+    def tk(knob, fn):
+        return tune_knob(knob, fn, reps=reps, before=flush)
+
     march = lambda: hp.march(bt["o"], bt["d"], bt["time"], bt["slot"])
-    rec.append(tune_knob("march_tile_rays", march, reps=reps))
-    rec.append(tune_knob("march_occupancy", march, reps=reps))
+    rec.append(tk("march_tile_rays", march))
+    rec.append(tk("march_occupancy", march))
+    rec.append(tk("march_unroll", march))
     march()
     M = int(hp.n_m.item())
     sc.field_marched(hp, batch, M)
     prune = lambda: hp.prune(M)
-    rec.append(tune_knob("prune_tile_rays", prune, reps=reps))
-    rec.append(tune_knob("prune_occupancy", prune, reps=reps))
+    rec.append(tk("prune_tile_rays", prune))
+    rec.append(tk("prune_occupancy", prune))
+    rec.append(tk("prune_interleave", prune))
     hp.prune(M)
     S = int(hp.n_k.item())
     sc.field_kept(hp, batch, S)
     fwd = lambda: hp.render_fwd(S)
-    rec.append(tune_knob("render_fwd_prefetch", fwd, reps=reps))
-    rec.append(tune_knob("render_fwd_occupancy", fwd, reps=reps))
+    rec.append(tk("render_fwd_prefetch", fwd))
+    rec.append(tk("render_fwd_occupancy", fwd))
     hp.render_fwd(S)
     hp.g_color.uniform_(-1e-6, 1e-6)
-    rec.append(tune_knob("render_bwd_occupancy", lambda: hp.render_bwd(S), reps=reps))
+    rec.append(tk("render_bwd_occupancy", lambda: hp.render_bwd(S)))
+    # forward + backward with the optical depth recomputed, or saved by the forward
+    times = {}
+    for saved in (False, True):
+        hp.save_optical_depth = saved
+        times[int(saved)] = time_ms(lambda: (hp.render_fwd(S), hp.render_bwd(S)), reps=reps, before=flush)
+    hp.save_optical_depth = times[1] < times[0]
+    rec.append({"knob": "save_optical_depth", "best": int(hp.save_optical_depth),
+                "ms": {str(k): round(v, 4) for k, v in times.items()}})
     torch.cuda.synchronize()
     hp.check_status("autotune")
     return {r["knob"]: r for r in rec}

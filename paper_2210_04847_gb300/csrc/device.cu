@@ -34,9 +34,11 @@ int g_tune[NACC_TUNE_COUNT] = {
     2,  // NACC_TUNE_PRUNE_OCCUPANCY
     2,  // NACC_TUNE_RENDER_OCCUPANCY
     2,  // NACC_TUNE_RENDER_BWD_OCCUPANCY
+    0,  // NACC_TUNE_MARCH_UNROLL
+    2,  // NACC_TUNE_PRUNE_INTERLEAVE
 };
-const int g_tune_lo[NACC_TUNE_COUNT] = {0, 1, 2, 0, 0, 0, 0};
-const int g_tune_hi[NACC_TUNE_COUNT] = {1, 32, 32, 1, 2, 2, 2};
+const int g_tune_lo[NACC_TUNE_COUNT] = {0, 1, 2, 0, 0, 0, 0, 0, 2};
+const int g_tune_hi[NACC_TUNE_COUNT] = {1, 32, 32, 1, 2, 2, 2, 1, 4};
 }  // namespace
 
 int tune_get(int knob) { return (knob >= 0 && knob < NACC_TUNE_COUNT) ? g_tune[knob] : 0; }
@@ -47,6 +49,7 @@ extern "C" int nacc_tune_set(int knob, int value) {
     if (knob < 0 || knob >= NACC_TUNE_COUNT) return NACC_ERR_INVALID_ARG;
     if (value < nacc::g_tune_lo[knob] || value > nacc::g_tune_hi[knob]) return NACC_ERR_INVALID_ARG;
     if (knob == NACC_TUNE_PRUNE_TILE_RAYS && (value & 1)) return NACC_ERR_INVALID_ARG;
+    if (knob == NACC_TUNE_PRUNE_INTERLEAVE && value != 2 && value != 4) return NACC_ERR_INVALID_ARG;
     nacc::g_tune[knob] = value;
     return NACC_OK;
 }

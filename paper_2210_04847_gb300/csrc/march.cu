@@ -205,7 +205,7 @@ __device__ __forceinline__ void cone_extend(const MarchArgs& a, float* buf, floa
 // warp per ray (uniform steps, or cone steps through the lattice table)
 // ---------------------------------------------------------------------------
 
-template <int MAXL, int MINB, bool CONE>
+template <int MAXL, int MINB, bool CONE, bool UNROLL2 = false>
 __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const MarchArgs a) {
     extern __shared__ uint32_t s_masks[];  // per warp: [tile_rays][mask_words]
     __shared__ float s_lat[kWarps][36];    // cone steps with a ray-specific start
@@ -248,6 +248,41 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
                 const int max_ch = (nk + 31) >> 5;
                 const unsigned sl0 = (unsigned)slot * (unsigned)a.n_levels;
                 uint32_t* row = wmask + i * a.mask_words;
+                if (!CONE && UNROLL2) {
+                    // two chunks per iteration: two independent chains and two grid
+                    // loads in flight per lane
+                    for (int c = 0; c < max_ch; c += 2) {
+                        const int k0 = (c << 5) + lane, k1 = k0 + 32;
+                        const float kf0 = __int2float_rn(k0), kf1 = __int2float_rn(k1);
+                        bool occ0 = false, occ1 = false;
+                        if (k0 < nk) {
+                            const float ts = __fadd_rn(near, __fmul_rn(kf0, dt));
+                            const float tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf0, 1.0f), dt));
+                            const float te = tn < far ? tn : far;
+                            const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
+                            occ0 = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)),
+                                                  __fadd_rn(o[1], __fmul_rn(d[1], mid)),
+                                                  __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0);
+                        }
+                        if (k1 < nk) {
+                            const float ts = __fadd_rn(near, __fmul_rn(kf1, dt));
+                            const float tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf1, 1.0f), dt));
+                            const float te = tn < far ? tn : far;
+                            const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
+                            occ1 = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)),
+                                                  __fadd_rn(o[1], __fmul_rn(d[1], mid)),
+                                                  __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0);
+                        }
+                        const unsigned m0 = __ballot_sync(FULL, occ0);
+                        const unsigned m1 = __ballot_sync(FULL, occ1);
+                        if (lane == 0) {
+                            row[c] = m0;
+                            if (c + 1 < max_ch) row[c + 1] = m1;
+                        }
+                        count += __popc(m0) + __popc(m1);
+                    }
+                    nch = max_ch;
+                } else {
                 float tcur = near;
                 for (int c = 0; c < max_ch; ++c) {
                     const int k = (c << 5) + lane;
@@ -279,6 +314,7 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
                     if (lane == 0) row[c] = m;
                     count += __popc(m);
                     nch = c + 1;
+                }
                 }
             }
             if (lane == i) {
@@ -513,10 +549,14 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
     const size_t smem = (size_t)kWarps * a.tile_rays * a.mask_words * sizeof(uint32_t);
     const int need = (a.n_tiles + kWarps - 1) / kWarps;
     const bool occ = tune_get(NACC_TUNE_MARCH_OCCUPANCY) != 0;
+    const bool unroll = tune_get(NACC_TUNE_MARCH_UNROLL) != 0;
     if (a.n_levels == 1) {
         if (cone) {
             if (occ) launch_uniform(march_uniform_kernel<1, 8, true>, smem, need, st, a);
             else launch_uniform(march_uniform_kernel<1, 1, true>, smem, need, st, a);
+        } else if (unroll) {
+            if (occ) launch_uniform(march_uniform_kernel<1, 8, false, true>, smem, need, st, a);
+            else launch_uniform(march_uniform_kernel<1, 1, false, true>, smem, need, st, a);
         } else {
             if (occ) launch_uniform(march_uniform_kernel<1, 8, false>, smem, need, st, a);
             else launch_uniform(march_uniform_kernel<1, 1, false>, smem, need, st, a);

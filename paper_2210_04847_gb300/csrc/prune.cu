@@ -139,6 +139,7 @@ __device__ __forceinline__ void walk_step(RayWalk& w, const PruneArgs& a, int la
     if (w.c >= w.nch || (a.use_t && !(w.carry <= a.thr_o))) w.live = false;
 }
 
+template <int IL>
 __device__ __forceinline__ void prune_body(const PruneArgs& a) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -178,28 +179,34 @@ __device__ __forceinline__ void prune_body(const PruneArgs& a) {
             }
         }
 
-        // phase 1: decisions, rays in pairs so two independent load streams are in flight
+        // phase 1: decisions, IL rays at a time so IL independent load streams are in flight
         int my_count = 0, my_nch = 0;
-        for (int i = 0; i < nr; i += 2) {
-            RayWalk A, B;
-            walk_init(A, a, __shfl_sync(FULL, my_off, i), __shfl_sync(FULL, my_cnt, i), ray0 + i);
-            const int offB = __shfl_sync(FULL, my_off, (i + 1) & 31);
-            const int cntB = __shfl_sync(FULL, my_cnt, (i + 1) & 31);
-            walk_init(B, a, offB, i + 1 < nr ? cntB : 0, ray0 + i + 1);
-            while (A.live || B.live) {
-                Pair pa, pb;
-                walk_load(A, a, lane, pa);
-                walk_load(B, a, lane, pb);
-                if (A.live) walk_step(A, a, lane, pa);
-                if (B.live) walk_step(B, a, lane, pb);
+        for (int i = 0; i < nr; i += IL) {
+            RayWalk W[IL];
+#pragma unroll
+            for (int j = 0; j < IL; ++j) {
+                const int off = __shfl_sync(FULL, my_off, (i + j) & 31);
+                const int cnt = __shfl_sync(FULL, my_cnt, (i + j) & 31);
+                walk_init(W[j], a, off, i + j < nr ? cnt : 0, ray0 + i + j);
             }
-            if (lane == i) {
-                my_count = A.count;
-                my_nch = A.c;
+            for (;;) {
+                bool any = false;
+#pragma unroll
+                for (int j = 0; j < IL; ++j) any |= W[j].live;
+                if (!any) break;
+                Pair P[IL];
+#pragma unroll
+                for (int j = 0; j < IL; ++j) walk_load(W[j], a, lane, P[j]);
+#pragma unroll
+                for (int j = 0; j < IL; ++j)
+                    if (W[j].live) walk_step(W[j], a, lane, P[j]);
             }
-            if (lane == i + 1) {
-                my_count = B.count;
-                my_nch = B.c;
+#pragma unroll
+            for (int j = 0; j < IL; ++j) {
+                if (lane == i + j) {
+                    my_count = W[j].count;
+                    my_nch = W[j].c;
+                }
             }
         }
         __syncwarp();
@@ -274,9 +281,9 @@ __device__ __forceinline__ void prune_body(const PruneArgs& a) {
 }
 
 // Register-budget variants (minimum resident blocks per SM), chosen by a tuning knob.
-template <int MINB>
+template <int MINB, int IL>
 __global__ void __launch_bounds__(kThreads, MINB) prune_kernel(const PruneArgs a) {
-    prune_body(a);
+    prune_body<IL>(a);
 }
 
 // Persistent launch: as many blocks as fit on the GPU, at most `need`.
@@ -363,10 +370,20 @@ extern "C" int nacc_prune_samples(const int32_t* packed_info, int32_t n_rays, co
     cudaError_t e = cudaMemsetAsync(workspace, 0, kTicketBytes + (size_t)a.n_tiles * 8, st);
     if (e != cudaSuccess) return NACC_ERR_CUDA;
     const int need = (a.n_tiles + kThreads / 32 - 1) / (kThreads / 32);
+    const bool il4 = tune_get(NACC_TUNE_PRUNE_INTERLEAVE) == 4;
     switch (tune_get(NACC_TUNE_PRUNE_OCCUPANCY)) {
-        case 1: launch_persistent(prune_kernel<8>, need, st, a); break;
-        case 2: launch_persistent(prune_kernel<6>, need, st, a); break;
-        default: launch_persistent(prune_kernel<1>, need, st, a); break;
+        case 1:
+            if (il4) launch_persistent(prune_kernel<8, 4>, need, st, a);
+            else launch_persistent(prune_kernel<8, 2>, need, st, a);
+            break;
+        case 2:
+            if (il4) launch_persistent(prune_kernel<6, 4>, need, st, a);
+            else launch_persistent(prune_kernel<6, 2>, need, st, a);
+            break;
+        default:
+            if (il4) launch_persistent(prune_kernel<1, 4>, need, st, a);
+            else launch_persistent(prune_kernel<1, 2>, need, st, a);
+            break;
     }
     return launch_status(cudaGetLastError());
 }

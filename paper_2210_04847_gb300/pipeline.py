@@ -84,6 +84,8 @@ class HotPath:
         self.n_m = torch.zeros(1, dtype=torch.int64, device=device)
         self.n_k = torch.zeros(1, dtype=torch.int64, device=device)
         self.status = torch.zeros(1, dtype=i32, device=device)
+        self.save_optical_depth = False  # forward stores O_i for the backward (instead of a recompute pass)
+        self.od = None
         self.n_grid = int(n_grid_samples)
         self.cells = z(self.n_grid, i32)
         self.cell_sig = z(self.n_grid)
@@ -100,15 +102,22 @@ class HotPath:
                            self.w.alpha_thre, self.pi_k, self.ts_k[: self.cap_k], self.te_k[: self.cap_k],
                            self.ri_k[: self.cap_k], self.n_k, self.status, self.ws_prune)
 
+    def _od(self):
+        if self.od is None:
+            self.od = torch.zeros(max(self.cap_k, 1), dtype=torch.float32, device=self.device)
+        return self.od
+
     def render_fwd(self, n_kept: int):
         S = min(int(n_kept), self.cap_k)
+        od = self._od()[:S] if self.save_optical_depth else None
         _lib.render_fwd(self.pi_k, self.ts_k[:S], self.te_k[:S], self.sig_k[:S], self.rgb_k[:S], S, self.color,
-                        self.opacity, self.depth, d_status=self.status)
+                        self.opacity, self.depth, optical_depth=od, d_status=self.status)
 
     def render_bwd(self, n_kept: int):
         S = min(int(n_kept), self.cap_k)
+        od = self._od()[:S] if self.save_optical_depth else None
         _lib.render_bwd(self.pi_k, self.ts_k[:S], self.te_k[:S], self.sig_k[:S], self.rgb_k[:S], S, self.g_color,
-                        None, None, self.d_sig[:S], self.d_rgb[:S], d_status=self.status)
+                        None, None, self.d_sig[:S], self.d_rgb[:S], optical_depth=od, d_status=self.status)
 
     def grid_update(self, decay=0.95, thre=0.01, bits=None):
         """EMA update of ``self.ema``; writes ``bits`` (default: the bitfield marched by this path)."""
