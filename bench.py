@@ -459,6 +459,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": mean_ms_all, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
         "tuned": {k: v["best"] for k, v in tuned.items()},
+        "tuning_ms": {k: v.get("ms") for k, v in tuned.items() if v.get("ms")},
         "stages_ms": {s: round(avg[s], 4) for s in stages},
         "stage_gbs": {s: round(sb[s] / (avg[s] / 1e3) / 1e9, 1) for s in stages},
         "samples_per_step": {"marched": round(M_avg), "examined_by_prune": round(Mr_avg), "kept": round(S_avg)},

@@ -48,14 +48,32 @@ def time_ms(fn: Callable[[], None], reps: int = 5, warmup: int = 1, before: Call
     return statistics.median(out)
 
 
-def tune_knob(knob: str, fn: Callable[[], None], candidates: Iterable[int] = None, reps: int = 5,
+def tune_knob(knob: str, fn: Callable[[], None], candidates: Iterable[int] = None, reps: int = 7,
               before: Callable[[], None] = None) -> Dict[str, object]:
-    """Time ``fn`` under each candidate value of ``knob``, set the fastest, return the record."""
+    """Time ``fn`` under each candidate value of ``knob`` and set the fastest.
+
+    Candidates are timed round-robin inside each repetition (so slow drifts of
+    clock or temperature hit all of them alike) and compared by their median.
+    """
     cands = tuple(CANDIDATES[knob] if candidates is None else candidates)
-    times = {}
-    for v in cands:
+    samples = {v: [] for v in cands}
+    for v in cands:  # one untimed run each (module loading, first-touch)
         _lib.tune_set(knob, v)
-        times[v] = time_ms(fn, reps=reps, before=before)
+        if before:
+            before()
+        fn()
+    for _ in range(reps):
+        for v in cands:
+            _lib.tune_set(knob, v)
+            if before:
+                before()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            samples[v].append(e0.elapsed_time(e1))
+    times = {v: statistics.median(t) for v, t in samples.items()}
     best = min(times, key=times.get)
     _lib.tune_set(knob, best)
     return {"knob": knob, "best": best, "ms": {str(k): round(t, 4) for k, t in times.items()}}
