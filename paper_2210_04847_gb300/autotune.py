@@ -26,6 +26,7 @@ CANDIDATES = {
     "render_fwd_prefetch": (0, 1),
     "render_fwd_occupancy": (0, 1, 2),
     "render_bwd_occupancy": (0, 1, 2),
+    "render_bwd_prefetch": (0, 1),
 }
 
 
@@ -49,13 +50,19 @@ def time_ms(fn: Callable[[], None], reps: int = 5, warmup: int = 1, before: Call
 
 
 def tune_knob(knob: str, fn: Callable[[], None], candidates: Iterable[int] = None, reps: int = 7,
-              before: Callable[[], None] = None) -> Dict[str, object]:
+              before: Callable[[], None] = None, margin: float = 0.03) -> Dict[str, object]:
     """Time ``fn`` under each candidate value of ``knob`` and set the fastest.
 
     Candidates are timed round-robin inside each repetition (so slow drifts of
     clock or temperature hit all of them alike) and compared by their median.
+    The value the knob held before (the library default, or an earlier choice)
+    stays unless the fastest candidate beats it by more than ``margin``: a win
+    inside the run-to-run noise is not worth changing the launch shape for.
     """
     cands = tuple(CANDIDATES[knob] if candidates is None else candidates)
+    incumbent = _lib.tune_get(knob)
+    if incumbent not in cands:
+        cands = (incumbent,) + cands
     samples = {v: [] for v in cands}
     for v in cands:  # one untimed run each (module loading, first-touch)
         _lib.tune_set(knob, v)
@@ -75,6 +82,8 @@ def tune_knob(knob: str, fn: Callable[[], None], candidates: Iterable[int] = Non
             samples[v].append(e0.elapsed_time(e1))
     times = {v: statistics.median(t) for v, t in samples.items()}
     best = min(times, key=times.get)
+    if times[best] > (1.0 - margin) * times[incumbent]:
+        best = incumbent
     _lib.tune_set(knob, best)
     return {"knob": knob, "best": best, "ms": {str(k): round(t, 4) for k, t in times.items()}}
 
@@ -109,6 +118,7 @@ def tune_hot_path(hp, sc, batch: int = 0, reps: int = 7, flush: Callable[[], Non
     hp.render_fwd(S)
     hp.g_color.uniform_(-1e-6, 1e-6)
     rec.append(tk("render_bwd_occupancy", lambda: hp.render_bwd(S)))
+    rec.append(tk("render_bwd_prefetch", lambda: hp.render_bwd(S)))
     # forward + backward with the optical depth recomputed, or saved by the forward
     times = {}
     for saved in (False, True):

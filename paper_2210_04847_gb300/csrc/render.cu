@@ -396,7 +396,7 @@ __device__ __forceinline__ void pair_tau(const BwdArgs& a, unsigned abase, unsig
     }
 }
 
-template <int MINB>
+template <int MINB, bool PREFETCH>
 __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const BwdArgs a) {
     __shared__ float s_carry[kRenderThreads / 32][kCarryCap];
     const int lane = threadIdx.x & 31;
@@ -444,6 +444,12 @@ __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const 
         // is the same quantity, but the large near-cancelling terms a_ref T_{k+1}
         // and a_ref sum w_i never appear: the float32 error scales with |b| (the
         // variation of a along the ray), not with |a|.
+        // with PREFETCH the last chunk's loads (pass B starts there) go out
+        // together with the reference sample's, so their latencies overlap
+        Pair nx;
+        if (PREFETCH)
+            load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, abase + ((unsigned)(nch - 1) << 6) + 2 * lane, lo, hi,
+                      nx);
         const float r_ref = __ldg(a.rgbs + 3 * lo);
         const float g_ref = __ldg(a.rgbs + 3 * lo + 1);
         const float b_ref = __ldg(a.rgbs + 3 * lo + 2);
@@ -454,7 +460,9 @@ __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const 
         const bool last_odd = (last & 1) != 0;
         float t_end = 0.0f;
 
-        // pass B: chunks in reverse order, suffix sums of b_i w_i carried backwards
+        // pass B: chunks in reverse order, suffix sums of b_i w_i carried backwards;
+        // with PREFETCH the next (earlier) chunk's loads are issued before this one
+        // is computed
         float carry_s = 0.0f;
         for (int c = nch - 1; c >= 0; --c) {
             float carry_o = 0.0f;
@@ -472,7 +480,12 @@ __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const 
             }
             const unsigned j0 = abase + ((unsigned)c << 6) + 2 * lane;
             Pair q;
-            load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0, lo, hi, q);
+            if (PREFETCH) {
+                q = nx;
+                if (c > 0) load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0 - 64, lo, hi, nx);
+            } else {
+                load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0, lo, hi, q);
+            }
             const float tau0 = q.v0 ? tau_of(q.s0[0], q.s1[0], q.sg[0]) : 0.0f;
             const float tau1 = q.v1 ? tau_of(q.s0[1], q.s1[1], q.sg[1]) : 0.0f;
             float O0, O1;
@@ -644,10 +657,20 @@ extern "C" int nacc_render_bwd(const int32_t* packed_info, int32_t n_rays, const
               g_color, g_opacity, g_depth, d_sigmas, d_rgbs, d_status};
     const int nb = group_blocks(n_rays);
     cudaStream_t st = (cudaStream_t)stream;
+    const bool pf = tune_get(NACC_TUNE_RENDER_BWD_PREFETCH) != 0;
     switch (tune_get(NACC_TUNE_RENDER_BWD_OCCUPANCY)) {
-        case 1: render_bwd_kernel<16><<<nb, kRenderThreads, 0, st>>>(a); break;
-        case 2: render_bwd_kernel<12><<<nb, kRenderThreads, 0, st>>>(a); break;
-        default: render_bwd_kernel<1><<<nb, kRenderThreads, 0, st>>>(a); break;
+        case 1:
+            if (pf) render_bwd_kernel<16, true><<<nb, kRenderThreads, 0, st>>>(a);
+            else render_bwd_kernel<16, false><<<nb, kRenderThreads, 0, st>>>(a);
+            break;
+        case 2:
+            if (pf) render_bwd_kernel<12, true><<<nb, kRenderThreads, 0, st>>>(a);
+            else render_bwd_kernel<12, false><<<nb, kRenderThreads, 0, st>>>(a);
+            break;
+        default:
+            if (pf) render_bwd_kernel<1, true><<<nb, kRenderThreads, 0, st>>>(a);
+            else render_bwd_kernel<1, false><<<nb, kRenderThreads, 0, st>>>(a);
+            break;
     }
     return launch_status(cudaGetLastError());
 }
