@@ -458,7 +458,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms_all, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
-        "tuned": {k: v["best"] for k, v in tuned.items()},
+        "tuned": dict({k: _lib.tune_get(k) for k in _lib.TUNE_KNOBS}, save_optical_depth=int(hp.save_optical_depth)),
         "tuning_ms": {k: v.get("ms") for k, v in tuned.items() if v.get("ms")},
         "stages_ms": {s: round(avg[s], 4) for s in stages},
         "stage_gbs": {s: round(sb[s] / (avg[s] / 1e3) / 1e9, 1) for s in stages},

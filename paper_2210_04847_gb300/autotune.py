@@ -49,29 +49,29 @@ def time_ms(fn: Callable[[], None], reps: int = 5, warmup: int = 1, before: Call
     return statistics.median(out)
 
 
-def tune_knob(knob: str, fn: Callable[[], None], candidates: Iterable[int] = None, reps: int = 7,
-              before: Callable[[], None] = None, margin: float = 0.03) -> Dict[str, object]:
-    """Time ``fn`` under each candidate value of ``knob`` and set the fastest.
+def tune_configs(name: str, configs, fn: Callable[[], None], reps: int = 7, before: Callable[[], None] = None,
+                 margin: float = 0.03) -> Dict[str, object]:
+    """Time ``fn`` under each configuration (a dict knob -> value) and set the
+    fastest. Configurations are timed round-robin inside each repetition (so
+    slow drifts of clock or temperature hit all of them alike) and compared by
+    their median. The first configuration is the incumbent: it stays unless
+    another beats it by more than ``margin`` (a win inside the run-to-run noise
+    is not worth changing the launch shape for)."""
+    configs = [dict(c) for c in configs]
 
-    Candidates are timed round-robin inside each repetition (so slow drifts of
-    clock or temperature hit all of them alike) and compared by their median.
-    The value the knob held before (the library default, or an earlier choice)
-    stays unless the fastest candidate beats it by more than ``margin``: a win
-    inside the run-to-run noise is not worth changing the launch shape for.
-    """
-    cands = tuple(CANDIDATES[knob] if candidates is None else candidates)
-    incumbent = _lib.tune_get(knob)
-    if incumbent not in cands:
-        cands = (incumbent,) + cands
-    samples = {v: [] for v in cands}
-    for v in cands:  # one untimed run each (module loading, first-touch)
-        _lib.tune_set(knob, v)
+    def apply(c):
+        for k, v in c.items():
+            _lib.tune_set(k, v)
+
+    samples = [[] for _ in configs]
+    for c in configs:  # one untimed run each (module loading, first-touch)
+        apply(c)
         if before:
             before()
         fn()
     for _ in range(reps):
-        for v in cands:
-            _lib.tune_set(knob, v)
+        for i, c in enumerate(configs):
+            apply(c)
             if before:
                 before()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -79,13 +79,27 @@ def tune_knob(knob: str, fn: Callable[[], None], candidates: Iterable[int] = Non
             fn()
             e1.record()
             torch.cuda.synchronize()
-            samples[v].append(e0.elapsed_time(e1))
-    times = {v: statistics.median(t) for v, t in samples.items()}
-    best = min(times, key=times.get)
-    if times[best] > (1.0 - margin) * times[incumbent]:
-        best = incumbent
-    _lib.tune_set(knob, best)
-    return {"knob": knob, "best": best, "ms": {str(k): round(t, 4) for k, t in times.items()}}
+            samples[i].append(e0.elapsed_time(e1))
+    times = [statistics.median(t) for t in samples]
+    best = min(range(len(configs)), key=lambda i: times[i])
+    if times[best] > (1.0 - margin) * times[0]:
+        best = 0
+    apply(configs[best])
+    label = lambda c: ",".join("%s=%d" % kv for kv in c.items())
+    return {"knob": name, "best": configs[best], "ms": {label(c): round(t, 4) for c, t in zip(configs, times)},
+            "best_ms": times[best]}
+
+
+def tune_knob(knob: str, fn: Callable[[], None], candidates: Iterable[int] = None, reps: int = 7,
+              before: Callable[[], None] = None, margin: float = 0.03) -> Dict[str, object]:
+    """Time ``fn`` under each candidate value of ``knob`` and set the fastest;
+    the value the knob held before is the incumbent (see ``tune_configs``)."""
+    cands = tuple(CANDIDATES[knob] if candidates is None else candidates)
+    incumbent = _lib.tune_get(knob)
+    order = (incumbent,) + tuple(v for v in cands if v != incumbent)
+    r = tune_configs(knob, [{knob: v} for v in order], fn, reps=reps, before=before, margin=margin)
+    return {"knob": knob, "best": r["best"][knob], "ms": {str(v): r["ms"]["%s=%d" % (knob, v)] for v in order},
+            "best_ms": r["best_ms"]}
 
 
 def tune_hot_path(hp, sc, batch: int = 0, reps: int = 7, flush: Callable[[], None] = None):

@@ -27,10 +27,10 @@ DeviceInfo current_device() {
 namespace {
 // Tuned launch-shape table: one int per knob, read at every launch.
 int g_tune[NACC_TUNE_COUNT] = {
-    1,  // NACC_TUNE_RENDER_FWD_PREFETCH
-    8,  // NACC_TUNE_MARCH_TILE_RAYS (upper bound; long lattices use fewer)
+    0,  // NACC_TUNE_RENDER_FWD_PREFETCH
+    4,  // NACC_TUNE_MARCH_TILE_RAYS (upper bound; long lattices use fewer)
     8,  // NACC_TUNE_PRUNE_TILE_RAYS
-    1,  // NACC_TUNE_MARCH_OCCUPANCY
+    0,  // NACC_TUNE_MARCH_OCCUPANCY
     2,  // NACC_TUNE_PRUNE_OCCUPANCY
     2,  // NACC_TUNE_RENDER_OCCUPANCY
     2,  // NACC_TUNE_RENDER_BWD_OCCUPANCY

@@ -68,7 +68,8 @@ struct MarchArgs {
     unsigned long long* tile_status;
     unsigned int* ticket;
     int32_t n_tiles;
-    int32_t mask_words;
+    int32_t mask_words;       // ballot words a ray's row can hold
+    int32_t row_stride;       // words between consecutive rows in shared memory (= mask_words)
     int32_t tile_rays;
     const float* cone_table;  // t_0 = near_plane, t_1, ..., t_max_steps (cone steps only)
     Levels L;
@@ -202,19 +203,183 @@ __device__ __forceinline__ void cone_extend(const MarchArgs& a, float* buf, floa
 }
 
 // ---------------------------------------------------------------------------
-// warp per ray (uniform steps, or cone steps through the lattice table)
+// lattice walk: the warp evaluates 32 lattice points of one ray at a time
 // ---------------------------------------------------------------------------
 
+// One ray, all 32 lanes: one ballot word per 32 lattice points into row[c].
+// count = samples, nch = ballot words written (row[0..nch)).
+template <int MAXL, bool CONE, bool UNROLL2>
+__device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3], const float d[3], float near,
+                                             float far, unsigned sl0, uint32_t* row, float* lat, int lane,
+                                             int& count_out, int& nch_out) {
+    const float dt = a.dt_min;
+    const bool shared = !CONE || near == a.near_plane;
+    // shared lattices know their length; an own cone lattice ends when t_k >= far
+    int nk = !CONE ? lattice_count(a, near, far, dt)
+                   : (shared ? table_count(a.cone_table, a.max_steps, far) : a.max_steps);
+    if (CONE && shared && nk > 32 * a.mask_words) {  // the host's bound on cone lattices was passed
+        if (lane == 0) raise_status(a.d_status, NACC_STATUS_OVERFLOW);
+        nk = 32 * a.mask_words;
+    }
+    const int max_ch = min((nk + 31) >> 5, a.mask_words);
+    int count = 0, nch = 0;
+    if (!CONE && UNROLL2) {
+        // two chunks per iteration: two independent chains and two grid loads in flight per lane
+        for (int c = 0; c < max_ch; c += 2) {
+            const int k0 = (c << 5) + lane, k1 = k0 + 32;
+            const float kf0 = __int2float_rn(k0), kf1 = __int2float_rn(k1);
+            bool occ0 = false, occ1 = false;
+            if (k0 < nk) {
+                const float ts = __fadd_rn(near, __fmul_rn(kf0, dt));
+                const float tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf0, 1.0f), dt));
+                const float te = tn < far ? tn : far;
+                const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
+                occ0 = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)), __fadd_rn(o[1], __fmul_rn(d[1], mid)),
+                                      __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0);
+            }
+            if (k1 < nk) {
+                const float ts = __fadd_rn(near, __fmul_rn(kf1, dt));
+                const float tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf1, 1.0f), dt));
+                const float te = tn < far ? tn : far;
+                const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
+                occ1 = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)), __fadd_rn(o[1], __fmul_rn(d[1], mid)),
+                                      __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0);
+            }
+            const unsigned m0 = __ballot_sync(FULL, occ0);
+            const unsigned m1 = __ballot_sync(FULL, occ1);
+            if (lane == 0) {
+                row[c] = m0;
+                if (c + 1 < max_ch) row[c + 1] = m1;
+            }
+            count += __popc(m0) + __popc(m1);
+        }
+        nch = max_ch;
+    } else {
+        float tcur = near;
+        int c = 0;
+        for (; c < max_ch; ++c) {
+            const int k = (c << 5) + lane;
+            float ts, tn;
+            if (!CONE) {
+                const float kf = __int2float_rn(k);
+                ts = __fadd_rn(near, __fmul_rn(kf, dt));
+                tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+            } else if (shared) {
+                ts = __ldg(a.cone_table + min(k, a.max_steps));
+                tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+            } else {
+                cone_extend(a, lat, tcur, lane);
+                ts = lat[lane];
+                tn = lat[lane + 1];
+            }
+            const bool valid = k < nk && ts < far;
+            if (CONE && !shared && __ballot_sync(FULL, valid) == 0u) break;
+            bool occ = false;
+            if (valid) {
+                const float te = tn < far ? tn : far;
+                const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
+                const float x0 = __fadd_rn(o[0], __fmul_rn(d[0], mid));
+                const float x1 = __fadd_rn(o[1], __fmul_rn(d[1], mid));
+                const float x2 = __fadd_rn(o[2], __fmul_rn(d[2], mid));
+                occ = occupied<MAXL>(a, x0, x1, x2, sl0);
+            }
+            const unsigned m = __ballot_sync(FULL, occ);
+            if (lane == 0) row[c] = m;
+            count += __popc(m);
+            nch = c + 1;
+        }
+        // an own cone lattice that still had points beyond the rows' capacity
+        if (CONE && !shared && c == a.mask_words && (c << 5) < a.max_steps && tcur < far && lane == 0)
+            raise_status(a.d_status, NACC_STATUS_OVERFLOW);
+    }
+    count_out = count;
+    nch_out = nch;
+}
+
+// ---------------------------------------------------------------------------
+// phases 2 and 3 of a tile (shared by both phase-1 strategies)
+// ---------------------------------------------------------------------------
+
+// Offsets inside the tile, the tile's offset by look-back, then the ballot words
+// expanded into compacted, coalesced stores of (t_start, t_end, ray). Lane i
+// holds ray i's count, first and last ballot words and [near, far].
+template <bool CONE>
+__device__ __forceinline__ void emit_tile(const MarchArgs& a, const uint32_t* wmask, int tile, int ray0, int nr,
+                                          int my_count, int my_c0, int my_nch, float my_near, float my_far,
+                                          float* lat, int lane) {
+    const float dt = a.dt_min;
+    const unsigned lt = lanemask_lt();
+    const int incl = warp_incl_scan_int(my_count, lane);
+    const int agg = __shfl_sync(FULL, incl, 31);
+    const long long excl = (long long)lookback(a.tile_status, tile, (unsigned long long)agg, lane, a.d_status);
+    const int my_excl = incl - my_count;
+    if (lane < nr) {
+        const int2 pi = make_int2((int)(excl + my_excl), my_count);
+        reinterpret_cast<int2*>(a.packed_info)[ray0 + lane] = pi;
+    }
+    if (lane == 0 && tile == a.n_tiles - 1) {
+        const long long total = excl + agg;
+        *a.n_samples = total;
+        if (total > a.capacity) raise_status(a.d_status, NACC_STATUS_CAPACITY);
+        if (total > 0x7fffffffLL) raise_status(a.d_status, NACC_STATUS_OVERFLOW);
+    }
+    // Output positions fit 32 bits: the tile starts below capacity <= 2^31 - 1
+    // and adds at most tile_rays * max_steps <= 2^20 samples.
+    if (excl >= a.capacity) return;
+    const unsigned cap = (unsigned)(a.capacity < 0x7fffffffLL ? a.capacity : 0x7fffffffLL);
+    for (int i = 0; i < nr; ++i) {
+        const int cnt = __shfl_sync(FULL, my_count, i);
+        if (cnt == 0) continue;
+        const int c0 = __shfl_sync(FULL, my_c0, i);
+        const int nch = __shfl_sync(FULL, my_nch, i);
+        const float near = __shfl_sync(FULL, my_near, i);
+        const float far = __shfl_sync(FULL, my_far, i);
+        const bool shared = !CONE || near == a.near_plane;
+        const int r = ray0 + i;
+        const uint32_t* row = wmask + i * a.row_stride;
+        unsigned base = (unsigned)excl + (unsigned)__shfl_sync(FULL, my_excl, i);
+        float tcur = near;
+        for (int c = c0; c < nch; ++c) {
+            const unsigned m = row[c];
+            if (shared && m == 0u) continue;  // an own cone lattice is extended chunk by chunk
+            const int k = (c << 5) + lane;
+            float ts, tn;
+            if (!CONE) {
+                const float kf = __int2float_rn(k);
+                ts = __fadd_rn(near, __fmul_rn(kf, dt));
+                tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+            } else if (shared) {
+                ts = __ldg(a.cone_table + min(k, a.max_steps));
+                tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+            } else {
+                cone_extend(a, lat, tcur, lane);
+                ts = lat[lane];
+                tn = lat[lane + 1];
+            }
+            const unsigned pos = base + __popc(m & lt);
+            if (((m >> lane) & 1u) && pos < cap) {
+                a.t_starts[pos] = ts;
+                a.t_ends[pos] = tn < far ? tn : far;
+                a.ray_indices[pos] = r;
+            }
+            base += __popc(m);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// Lattice walk: the warp takes the tile's rays one at a time.
 template <int MAXL, int MINB, bool CONE, bool UNROLL2 = false>
 __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const MarchArgs a) {
-    extern __shared__ uint32_t s_masks[];  // per warp: [tile_rays][mask_words]
+    extern __shared__ uint32_t s_masks[];  // per warp: [tile_rays][row_stride]
     __shared__ float s_lat[kWarps][36];    // cone steps with a ray-specific start
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    uint32_t* wmask = s_masks + (size_t)warp * a.tile_rays * a.mask_words;
+    uint32_t* wmask = s_masks + (size_t)warp * a.tile_rays * a.row_stride;
     float* lat = s_lat[warp];
-    const float dt = a.dt_min;
-    const unsigned lt = lanemask_lt();
 
     for (;;) {
         int tile = 0;
@@ -224,7 +389,6 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
         const int ray0 = tile * a.tile_rays;
         const int nr = min(a.tile_rays, a.n_rays - ray0);
 
-        // phase 1: walk the lattice of each ray of the tile, one ballot word per 32 points
         int my_count = 0, my_nch = 0;
         float my_near = 0.0f, my_far = 0.0f;
         for (int i = 0; i < nr; ++i) {
@@ -240,83 +404,9 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
             const int slot = slot_of(a, r);
             const bool slot_ok = slot >= 0 && slot < a.n_slots;
             if (!slot_ok && lane == 0) raise_status(a.d_status, NACC_STATUS_BAD_INDEX);
-            if (slot_ok && clip_ray(a, o, d, near, far)) {
-                const bool shared = !CONE || near == a.near_plane;
-                // shared lattices know their length; an own cone lattice ends when t_k >= far
-                const int nk = !CONE ? lattice_count(a, near, far, dt)
-                                     : (shared ? table_count(a.cone_table, a.max_steps, far) : a.max_steps);
-                const int max_ch = (nk + 31) >> 5;
-                const unsigned sl0 = (unsigned)slot * (unsigned)a.n_levels;
-                uint32_t* row = wmask + i * a.mask_words;
-                if (!CONE && UNROLL2) {
-                    // two chunks per iteration: two independent chains and two grid
-                    // loads in flight per lane
-                    for (int c = 0; c < max_ch; c += 2) {
-                        const int k0 = (c << 5) + lane, k1 = k0 + 32;
-                        const float kf0 = __int2float_rn(k0), kf1 = __int2float_rn(k1);
-                        bool occ0 = false, occ1 = false;
-                        if (k0 < nk) {
-                            const float ts = __fadd_rn(near, __fmul_rn(kf0, dt));
-                            const float tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf0, 1.0f), dt));
-                            const float te = tn < far ? tn : far;
-                            const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
-                            occ0 = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)),
-                                                  __fadd_rn(o[1], __fmul_rn(d[1], mid)),
-                                                  __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0);
-                        }
-                        if (k1 < nk) {
-                            const float ts = __fadd_rn(near, __fmul_rn(kf1, dt));
-                            const float tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf1, 1.0f), dt));
-                            const float te = tn < far ? tn : far;
-                            const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
-                            occ1 = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)),
-                                                  __fadd_rn(o[1], __fmul_rn(d[1], mid)),
-                                                  __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0);
-                        }
-                        const unsigned m0 = __ballot_sync(FULL, occ0);
-                        const unsigned m1 = __ballot_sync(FULL, occ1);
-                        if (lane == 0) {
-                            row[c] = m0;
-                            if (c + 1 < max_ch) row[c + 1] = m1;
-                        }
-                        count += __popc(m0) + __popc(m1);
-                    }
-                    nch = max_ch;
-                } else {
-                float tcur = near;
-                for (int c = 0; c < max_ch; ++c) {
-                    const int k = (c << 5) + lane;
-                    float ts, tn;
-                    if (!CONE) {
-                        const float kf = __int2float_rn(k);
-                        ts = __fadd_rn(near, __fmul_rn(kf, dt));
-                        tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
-                    } else if (shared) {
-                        ts = __ldg(a.cone_table + min(k, a.max_steps));
-                        tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
-                    } else {
-                        cone_extend(a, lat, tcur, lane);
-                        ts = lat[lane];
-                        tn = lat[lane + 1];
-                    }
-                    const bool valid = k < nk && ts < far;
-                    if (CONE && !shared && __ballot_sync(FULL, valid) == 0u) break;
-                    bool occ = false;
-                    if (valid) {
-                        const float te = tn < far ? tn : far;
-                        const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
-                        const float x0 = __fadd_rn(o[0], __fmul_rn(d[0], mid));
-                        const float x1 = __fadd_rn(o[1], __fmul_rn(d[1], mid));
-                        const float x2 = __fadd_rn(o[2], __fmul_rn(d[2], mid));
-                        occ = occupied<MAXL>(a, x0, x1, x2, sl0);
-                    }
-                    const unsigned m = __ballot_sync(FULL, occ);
-                    if (lane == 0) row[c] = m;
-                    count += __popc(m);
-                    nch = c + 1;
-                }
-                }
-            }
+            if (slot_ok && clip_ray(a, o, d, near, far))
+                walk_lattice<MAXL, CONE, UNROLL2>(a, o, d, near, far, (unsigned)slot * (unsigned)a.n_levels,
+                                                 wmask + i * a.row_stride, lat, lane, count, nch);
             if (lane == i) {
                 my_count = count;
                 my_nch = nch;
@@ -325,65 +415,7 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
             }
         }
         __syncwarp();
-
-        // phase 2: offsets inside the tile, then the tile's offset by look-back
-        const int incl = warp_incl_scan_int(my_count, lane);
-        const int agg = __shfl_sync(FULL, incl, 31);
-        const long long excl = (long long)lookback(a.tile_status, tile, (unsigned long long)agg, lane, a.d_status);
-        const int my_excl = incl - my_count;
-        if (lane < nr) {
-            const int2 pi = make_int2((int)(excl + my_excl), my_count);
-            reinterpret_cast<int2*>(a.packed_info)[ray0 + lane] = pi;
-        }
-        if (lane == 0 && tile == a.n_tiles - 1) {
-            const long long total = excl + agg;
-            *a.n_samples = total;
-            if (total > a.capacity) raise_status(a.d_status, NACC_STATUS_CAPACITY);
-            if (total > 0x7fffffffLL) raise_status(a.d_status, NACC_STATUS_OVERFLOW);
-        }
-
-        // phase 3: expand the ballot words into compacted, coalesced stores. Output
-        // positions fit 32 bits: the tile starts below capacity <= 2^31 - 1 and adds
-        // at most tile_rays * max_steps <= 2^20 samples.
-        if (excl < a.capacity) {
-            const unsigned cap = (unsigned)(a.capacity < 0x7fffffffLL ? a.capacity : 0x7fffffffLL);
-            for (int i = 0; i < nr; ++i) {
-                const int cnt = __shfl_sync(FULL, my_count, i);
-                if (cnt == 0) continue;
-                const int nch = __shfl_sync(FULL, my_nch, i);
-                const float near = __shfl_sync(FULL, my_near, i);
-                const float far = __shfl_sync(FULL, my_far, i);
-                const bool shared = !CONE || near == a.near_plane;
-                const int r = ray0 + i;
-                const uint32_t* row = wmask + i * a.mask_words;
-                unsigned base = (unsigned)excl + (unsigned)__shfl_sync(FULL, my_excl, i);
-                float tcur = near;
-                for (int c = 0; c < nch; ++c) {
-                    const unsigned m = row[c];
-                    const int k = (c << 5) + lane;
-                    float ts, tn;
-                    if (!CONE) {
-                        const float kf = __int2float_rn(k);
-                        ts = __fadd_rn(near, __fmul_rn(kf, dt));
-                        tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
-                    } else if (shared) {
-                        ts = __ldg(a.cone_table + min(k, a.max_steps));
-                        tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
-                    } else {
-                        cone_extend(a, lat, tcur, lane);
-                        ts = lat[lane];
-                        tn = lat[lane + 1];
-                    }
-                    const unsigned pos = base + __popc(m & lt);
-                    if (((m >> lane) & 1u) && pos < cap) {
-                        a.t_starts[pos] = ts;
-                        a.t_ends[pos] = tn < far ? tn : far;
-                        a.ray_indices[pos] = r;
-                    }
-                    base += __popc(m);
-                }
-            }
-        }
+        emit_tile<CONE>(a, wmask, tile, ray0, nr, my_count, 0, my_nch, my_near, my_far, lat, lane);
         __syncwarp();
     }
 }
@@ -394,7 +426,25 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
 
 constexpr size_t kTicketBytes = 256;
 
-int mask_words_for(int32_t max_steps) { return (max_steps + 31) / 32; }
+// Ballot words of the longest lattice. With cone steps the lattice from
+// near_plane is the densest (a later start only lengthens every step: the step
+// is non-decreasing in t) and no ray's far exceeds far_plane, so its length up
+// to far_plane bounds every ray's; 32 points of margin, and kernels check it.
+int mask_words_for(const nacc_march_params* p) {
+    const int full = (p->max_steps + 31) / 32;
+    if (!(p->cone > 0.0f)) return full;
+    float t = p->near_plane;
+    int k = 0;
+    while (k < p->max_steps && t < p->far_plane) {
+        float dt = t * p->cone;
+        if (dt < p->dt_min) dt = p->dt_min;
+        if (dt > p->dt_max) dt = p->dt_max;
+        t = t + dt;
+        ++k;
+    }
+    const int words = (k + 32 + 31) / 32;
+    return words < full ? words : full;
+}
 
 // Rays per warp tile: up to 8, fewer when long lattices make the ballot rows
 // big (the warp's shared-memory slice stays within kWarpSmemBudget bytes).
@@ -414,7 +464,8 @@ size_t status_bytes_for(int32_t n_rays) {
 
 size_t workspace_bytes_for(int32_t n_rays, const nacc_march_params* p) {
     size_t b = status_bytes_for(n_rays);
-    if (p && p->cone > 0.0f && p->max_steps >= 1) b += align_up(((size_t)p->max_steps + 1) * sizeof(float), 256);
+    if (p && p->cone > 0.0f && p->max_steps >= 1)
+        b += align_up(((size_t)p->max_steps + 1) * sizeof(float), 256);
     return b;
 }
 
@@ -460,6 +511,18 @@ void launch_uniform(K kernel, size_t smem, int need, cudaStream_t st, const Marc
     if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int blocks = blocks_for(kernel, smem, need);
     kernel<<<blocks, kThreads, smem, st>>>(a);
+}
+
+// Cascades (two or more levels); the single-level walk has its own unrolled variant.
+template <int MAXL>
+void launch_walk(bool cone, bool occ, size_t smem, int need, cudaStream_t st, const MarchArgs& a) {
+    if (cone) {
+        if (occ) launch_uniform(march_uniform_kernel<MAXL, 8, true>, smem, need, st, a);
+        else launch_uniform(march_uniform_kernel<MAXL, 1, true>, smem, need, st, a);
+    } else {
+        if (occ) launch_uniform(march_uniform_kernel<MAXL, 8, false>, smem, need, st, a);
+        else launch_uniform(march_uniform_kernel<MAXL, 1, false>, smem, need, st, a);
+    }
 }
 
 }  // namespace
@@ -532,11 +595,13 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
     a.d_status = d_status;
     a.ticket = (unsigned int*)workspace;
     a.tile_status = (unsigned long long*)((char*)workspace + kTicketBytes);
-    a.mask_words = mask_words_for(p->max_steps);
+    a.mask_words = mask_words_for(p);
+    const bool cone = p->cone > 0.0f;
+    const bool occ = tune_get(NACC_TUNE_MARCH_OCCUPANCY) != 0;
     a.tile_rays = tile_rays_for(a.mask_words);
+    a.row_stride = a.mask_words;
     make_levels(*grid, a.L);
 
-    const bool cone = p->cone > 0.0f;
     a.n_tiles = (n_rays + a.tile_rays - 1) / a.tile_rays;
     const size_t clear = kTicketBytes + (size_t)a.n_tiles * sizeof(unsigned long long);
     cudaError_t e = cudaMemsetAsync(workspace, 0, clear, st);
@@ -546,9 +611,8 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
         a.cone_table = table;
         cone_table_kernel<<<1, 32, 0, st>>>(a, table);
     }
-    const size_t smem = (size_t)kWarps * a.tile_rays * a.mask_words * sizeof(uint32_t);
+    const size_t smem = (size_t)kWarps * a.tile_rays * a.row_stride * sizeof(uint32_t);
     const int need = (a.n_tiles + kWarps - 1) / kWarps;
-    const bool occ = tune_get(NACC_TUNE_MARCH_OCCUPANCY) != 0;
     const bool unroll = tune_get(NACC_TUNE_MARCH_UNROLL) != 0;
     if (a.n_levels == 1) {
         if (cone) {
@@ -561,14 +625,10 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
             if (occ) launch_uniform(march_uniform_kernel<1, 8, false>, smem, need, st, a);
             else launch_uniform(march_uniform_kernel<1, 1, false>, smem, need, st, a);
         }
+    } else if (a.n_levels <= 4) {
+        launch_walk<4>(cone, occ, smem, need, st, a);
     } else {
-        if (cone) {
-            if (occ) launch_uniform(march_uniform_kernel<NACC_MAX_LEVELS, 8, true>, smem, need, st, a);
-            else launch_uniform(march_uniform_kernel<NACC_MAX_LEVELS, 1, true>, smem, need, st, a);
-        } else {
-            if (occ) launch_uniform(march_uniform_kernel<NACC_MAX_LEVELS, 8, false>, smem, need, st, a);
-            else launch_uniform(march_uniform_kernel<NACC_MAX_LEVELS, 1, false>, smem, need, st, a);
-        }
+        launch_walk<NACC_MAX_LEVELS>(cone, occ, smem, need, st, a);
     }
     return launch_status(cudaGetLastError());
 }

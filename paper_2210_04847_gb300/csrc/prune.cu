@@ -83,11 +83,12 @@ struct Pair {
     float s0[2], s1[2], sg[2];
 };
 
-// Samples j0 = abase + 64c + 2*lane and j0 + 1 (only those inside the array are read).
-__device__ __forceinline__ void walk_load(const RayWalk& w, const PruneArgs& a, int lane, Pair& p) {
+// Samples j0 = abase + 64c + 2*lane and j0 + 1 of chunk c (only those inside the
+// array are read).
+__device__ __forceinline__ void walk_load(const RayWalk& w, const PruneArgs& a, int lane, int c, Pair& p) {
     p.s0[0] = p.s0[1] = p.s1[0] = p.s1[1] = p.sg[0] = p.sg[1] = 0.0f;
-    if (!w.live) return;
-    const long long j0 = (long long)w.abase + ((long long)w.c << 6) + 2 * lane;
+    if (!w.live || c >= w.nch) return;
+    const long long j0 = (long long)w.abase + ((long long)c << 6) + 2 * lane;
     if (j0 + 1 >= w.off && j0 < (long long)w.off + w.cnt) {
         if (j0 + 1 < a.n_samples) {
             const float2 u = __ldg(reinterpret_cast<const float2*>(a.t_starts + j0));
@@ -139,6 +140,7 @@ __device__ __forceinline__ void walk_step(RayWalk& w, const PruneArgs& a, int la
     if (w.c >= w.nch || (a.use_t && !(w.carry <= a.thr_o))) w.live = false;
 }
 
+// IL rays walked at once (IL independent load streams in flight).
 template <int IL>
 __device__ __forceinline__ void prune_body(const PruneArgs& a) {
     const int lane = threadIdx.x & 31;
@@ -196,7 +198,7 @@ __device__ __forceinline__ void prune_body(const PruneArgs& a) {
                 if (!any) break;
                 Pair P[IL];
 #pragma unroll
-                for (int j = 0; j < IL; ++j) walk_load(W[j], a, lane, P[j]);
+                for (int j = 0; j < IL; ++j) walk_load(W[j], a, lane, W[j].c, P[j]);
 #pragma unroll
                 for (int j = 0; j < IL; ++j)
                     if (W[j].live) walk_step(W[j], a, lane, P[j]);
@@ -286,7 +288,6 @@ __global__ void __launch_bounds__(kThreads, MINB) prune_kernel(const PruneArgs a
     prune_body<IL>(a);
 }
 
-// Persistent launch: as many blocks as fit on the GPU, at most `need`.
 template <typename K>
 void launch_persistent(K kernel, int need, cudaStream_t st, const PruneArgs& a) {
     const DeviceInfo dev = current_device();
@@ -298,6 +299,14 @@ void launch_persistent(K kernel, int need, cudaStream_t st, const PruneArgs& a) 
     if (blocks < 1) blocks = 1;
     kernel<<<blocks, kThreads, 0, st>>>(a);
 }
+
+template <int MINB>
+void launch_variant(bool il4, int need, cudaStream_t st, const PruneArgs& a) {
+    if (il4) launch_persistent(prune_kernel<MINB, 4>, need, st, a);
+    else launch_persistent(prune_kernel<MINB, 2>, need, st, a);
+}
+
+// Persistent launch: as many blocks as fit on the GPU, at most `need`.
 
 size_t workspace_bytes_for(int32_t n_rays, int64_t n_samples) {
     const size_t tiles = (size_t)(n_rays + 1) / 2;  // smallest tile: 2 rays
@@ -372,18 +381,9 @@ extern "C" int nacc_prune_samples(const int32_t* packed_info, int32_t n_rays, co
     const int need = (a.n_tiles + kThreads / 32 - 1) / (kThreads / 32);
     const bool il4 = tune_get(NACC_TUNE_PRUNE_INTERLEAVE) == 4;
     switch (tune_get(NACC_TUNE_PRUNE_OCCUPANCY)) {
-        case 1:
-            if (il4) launch_persistent(prune_kernel<8, 4>, need, st, a);
-            else launch_persistent(prune_kernel<8, 2>, need, st, a);
-            break;
-        case 2:
-            if (il4) launch_persistent(prune_kernel<6, 4>, need, st, a);
-            else launch_persistent(prune_kernel<6, 2>, need, st, a);
-            break;
-        default:
-            if (il4) launch_persistent(prune_kernel<1, 4>, need, st, a);
-            else launch_persistent(prune_kernel<1, 2>, need, st, a);
-            break;
+        case 1: launch_variant<8>(il4, need, st, a); break;
+        case 2: launch_variant<6>(il4, need, st, a); break;
+        default: launch_variant<1>(il4, need, st, a); break;
     }
     return launch_status(cudaGetLastError());
 }
