@@ -87,10 +87,18 @@ _SCRATCH = _Scratch()
 _CAP_HINT = {}
 
 
-def _check_status(status: torch.Tensor, what: str):
-    s = int(status.item())
+def _count_and_status(dev):
+    """One int64 pair on the device: [count, status]; the status word is the low
+    half of the second element (read back together, one synchronisation)."""
+    cs = torch.zeros(2, dtype=torch.int64, device=dev)
+    return cs, cs[0:1], cs[1:2].view(torch.int32)[:1]
+
+
+def _read_count(cs: torch.Tensor, what: str) -> int:
+    n, s = cs.tolist()
     if s & (_lib.STATUS_TIMEOUT | _lib.STATUS_BAD_PACKED | _lib.STATUS_OVERFLOW | _lib.STATUS_BAD_INDEX):
         raise _lib.NaccError("%s: device status 0x%x" % (what, s))
+    return int(n)
 
 
 def march_rays(rays_o, rays_d, grid: OccupancyGrid, near_plane=0.0, far_plane=1e10, render_step_size=1e-2,
@@ -103,22 +111,23 @@ def march_rays(rays_o, rays_d, grid: OccupancyGrid, near_plane=0.0, far_plane=1e
     params = _lib.make_params(near_plane, far_plane, render_step_size, dt_max, cone_angle, max_steps)
     ws = _SCRATCH.get("march_ws", _lib.march_workspace_size(R, params), dev)
     packed = torch.empty((R, 2), dtype=torch.int32, device=dev)
-    counter = torch.zeros(1, dtype=torch.int64, device=dev)
-    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    cs, counter, status = _count_and_status(dev)
+    # output capacity: the last call's count on this batch size plus headroom, so
+    # batches of similar size march once (a larger one marches again, exactly sized)
     cap = max(_CAP_HINT.get(("march", R), 64 * R), 1)
-    for _ in range(2):
+    for attempt in range(2):
         ts = torch.empty(cap, dtype=torch.float32, device=dev)
         te = torch.empty(cap, dtype=torch.float32, device=dev)
         ri = torch.empty(cap, dtype=torch.int32, device=dev)
-        status.zero_()
+        if attempt:
+            cs.zero_()
         _lib.march_rays(rays_o, rays_d, grid.struct(), params, packed, ts, te, ri, counter, status, ws,
                         ray_time=ray_time, ray_slot=ray_slot)
-        n = int(counter.item())  # the one host synchronisation of the eager path
-        _check_status(status, "march_rays")
+        n = _read_count(cs, "march_rays")  # the one host synchronisation of the eager path
         if n <= cap:
             break
         cap = n
-    _CAP_HINT[("march", R)] = max(n, 1)
+    _CAP_HINT[("march", R)] = max(int(n * 1.08) + 1024, 1)
     return packed, ts[:n], te[:n], ri[:n]
 
 
@@ -129,16 +138,14 @@ def prune_samples(packed_info, t_starts, t_ends, sigmas, early_stop_eps=1e-4, al
     M = t_starts.numel()
     ws = _SCRATCH.get("prune_ws", _lib.prune_workspace_size(R, M), dev)
     packed = torch.empty((R, 2), dtype=torch.int32, device=dev)
-    counter = torch.zeros(1, dtype=torch.int64, device=dev)
-    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    cs, counter, status = _count_and_status(dev)
     ts = torch.empty(M, dtype=torch.float32, device=dev)
     te = torch.empty(M, dtype=torch.float32, device=dev)
     ri = torch.empty(M, dtype=torch.int32, device=dev)
     _lib.prune_samples(packed_info.contiguous(), t_starts.contiguous().view(-1), t_ends.contiguous().view(-1),
                        sigmas.contiguous().view(-1).float(), M, early_stop_eps, alpha_thre, packed, ts, te, ri,
                        counter, status, ws)
-    n = int(counter.item())
-    _check_status(status, "prune_samples")
+    n = _read_count(cs, "prune_samples")
     return packed, ts[:n], te[:n], ri[:n]
 
 

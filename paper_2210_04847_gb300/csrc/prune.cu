@@ -3,8 +3,8 @@
 // Sec. 2.1 "Pruning Empty and Occluded Regions"; early_stop_eps and
 // alpha_thre of the Sec. 3 listing).
 //
-// Single pass over the input samples. Each warp takes tiles of 8 consecutive
-// rays from an atomic ticket and walks two rays at a time (two independent
+// Single pass over the input samples. Each warp takes tiles of consecutive rays
+// from an atomic ticket and walks two (or four) rays at a time (independent
 // load streams), in chunks of 64 samples: lane j loads samples 2j and 2j+1 of
 // the chunk as one 8-byte vector per array (chunks start at an even index).
 // It forms tau = sigma*delta, the exclusive optical depth by a warp shuffle
@@ -24,7 +24,6 @@ namespace nacc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kTileMax = 32;  // rays per warp tile (tuned, even); lane i holds ray i's run and results
 constexpr size_t kTicketBytes = 256;
 
 struct PruneArgs {
@@ -140,7 +139,44 @@ __device__ __forceinline__ void walk_step(RayWalk& w, const PruneArgs& a, int la
     if (w.c >= w.nch || (a.use_t && !(w.carry <= a.thr_o))) w.live = false;
 }
 
-// IL rays walked at once (IL independent load streams in flight).
+// ---------------------------------------------------------------------------
+// phase 1, register walk: IL rays at a time, their chunks loaded into registers
+// ---------------------------------------------------------------------------
+
+template <int IL>
+__device__ __forceinline__ void phase1_walk(const PruneArgs& a, int ray0, int nr, int my_off, int my_cnt, int lane,
+                                            int& my_count, int& my_nch) {
+    for (int i = 0; i < nr; i += IL) {
+        RayWalk W[IL];
+#pragma unroll
+        for (int j = 0; j < IL; ++j) {
+            const int off = __shfl_sync(FULL, my_off, (i + j) & 31);
+            const int cnt = __shfl_sync(FULL, my_cnt, (i + j) & 31);
+            walk_init(W[j], a, off, i + j < nr ? cnt : 0, ray0 + i + j);
+        }
+        for (;;) {
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < IL; ++j) any |= W[j].live;
+            if (!any) break;
+            Pair P[IL];
+#pragma unroll
+            for (int j = 0; j < IL; ++j) walk_load(W[j], a, lane, W[j].c, P[j]);
+#pragma unroll
+            for (int j = 0; j < IL; ++j)
+                if (W[j].live) walk_step(W[j], a, lane, P[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < IL; ++j) {
+            if (lane == i + j) {
+                my_count = W[j].count;
+                my_nch = W[j].c;
+            }
+        }
+    }
+}
+
+// Tiles of consecutive rays; phase 1 walks IL rays at a time.
 template <int IL>
 __device__ __forceinline__ void prune_body(const PruneArgs& a) {
     const int lane = threadIdx.x & 31;
@@ -181,36 +217,9 @@ __device__ __forceinline__ void prune_body(const PruneArgs& a) {
             }
         }
 
-        // phase 1: decisions, IL rays at a time so IL independent load streams are in flight
+        // phase 1: keep decisions into the ballot rows, kept counts per ray
         int my_count = 0, my_nch = 0;
-        for (int i = 0; i < nr; i += IL) {
-            RayWalk W[IL];
-#pragma unroll
-            for (int j = 0; j < IL; ++j) {
-                const int off = __shfl_sync(FULL, my_off, (i + j) & 31);
-                const int cnt = __shfl_sync(FULL, my_cnt, (i + j) & 31);
-                walk_init(W[j], a, off, i + j < nr ? cnt : 0, ray0 + i + j);
-            }
-            for (;;) {
-                bool any = false;
-#pragma unroll
-                for (int j = 0; j < IL; ++j) any |= W[j].live;
-                if (!any) break;
-                Pair P[IL];
-#pragma unroll
-                for (int j = 0; j < IL; ++j) walk_load(W[j], a, lane, W[j].c, P[j]);
-#pragma unroll
-                for (int j = 0; j < IL; ++j)
-                    if (W[j].live) walk_step(W[j], a, lane, P[j]);
-            }
-#pragma unroll
-            for (int j = 0; j < IL; ++j) {
-                if (lane == i + j) {
-                    my_count = W[j].count;
-                    my_nch = W[j].c;
-                }
-            }
-        }
+        phase1_walk<IL>(a, ray0, nr, my_off, my_cnt, lane, my_count, my_nch);
         __syncwarp();
 
         // phase 2: offsets inside the tile, then the tile's offset by look-back
@@ -305,6 +314,7 @@ void launch_variant(bool il4, int need, cudaStream_t st, const PruneArgs& a) {
     if (il4) launch_persistent(prune_kernel<MINB, 4>, need, st, a);
     else launch_persistent(prune_kernel<MINB, 2>, need, st, a);
 }
+
 
 // Persistent launch: as many blocks as fit on the GPU, at most `need`.
 
