@@ -299,7 +299,8 @@ int nacc_update_occupancy_grid(float* ema, uint32_t* bits, int64_t n_cells, cons
 #define NACC_TUNE_MARCH_UNROLL 7        /* 0/1: uniform steps, two lattice chunks per loop iteration */
 #define NACC_TUNE_PRUNE_INTERLEAVE 8    /* 2 or 4: rays a pruning warp walks at once */
 #define NACC_TUNE_RENDER_BWD_PREFETCH 9 /* 0/1: backward issues the next chunk's loads early */
-#define NACC_TUNE_COUNT 10
+#define NACC_TUNE_MARCH_COARSE 10       /* 0/1: first test one lattice point in 32, fill chunks that lie in one cell */
+#define NACC_TUNE_COUNT 11
 
 /* Set a knob; NACC_ERR_INVALID_ARG for an unknown knob or out-of-range value. */
 int nacc_tune_set(int knob, int value);

@@ -45,7 +45,8 @@ TUNE_MARCH_TILE_RAYS = 1
 TUNE_PRUNE_TILE_RAYS = 2
 TUNE_KNOBS = {"render_fwd_prefetch": 0, "march_tile_rays": 1, "prune_tile_rays": 2, "march_occupancy": 3,
               "prune_occupancy": 4, "render_fwd_occupancy": 5, "render_bwd_occupancy": 6, "march_unroll": 7,
-              "prune_interleave": 8, "render_bwd_prefetch": 9}
+              "prune_interleave": 8, "render_bwd_prefetch": 9,
+              "march_coarse": 10}
 
 
 class NaccError(RuntimeError):

@@ -20,6 +20,7 @@ CANDIDATES = {
     "march_tile_rays": (2, 4, 8, 16, 32),
     "march_occupancy": (0, 1),
     "march_unroll": (0, 1),
+    "march_coarse": (0, 1),
     "prune_tile_rays": (2, 4, 8, 16, 32),
     "prune_occupancy": (0, 1, 2),
     "prune_interleave": (2, 4),
@@ -116,6 +117,7 @@ def tune_hot_path(hp, sc, batch: int = 0, reps: int = 7, flush: Callable[[], Non
     rec.append(tk("march_tile_rays", march))
     rec.append(tk("march_occupancy", march))
     rec.append(tk("march_unroll", march))
+    rec.append(tk("march_coarse", march))
     march()
     M = int(hp.n_m.item())
     sc.field_marched(hp, batch, M)

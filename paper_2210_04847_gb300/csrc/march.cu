@@ -208,7 +208,9 @@ __device__ __forceinline__ void cone_extend(const MarchArgs& a, float* buf, floa
 
 // One ray, all 32 lanes: one ballot word per 32 lattice points into row[c].
 // count = samples, nch = ballot words written (row[0..nch)).
-template <int MAXL, bool CONE, bool UNROLL2>
+// COARSE (shared lattices): first one point every 32 per lane, and chunks that
+// lie in a single cell take their word from one occupancy test (see below).
+template <int MAXL, bool CONE, bool UNROLL2, bool COARSE = false>
 __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3], const float d[3], float near,
                                              float far, unsigned sl0, uint32_t* row, float* lat, int lane,
                                              int& count_out, int& nch_out) {
@@ -223,7 +225,87 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
     }
     const int max_ch = min((nk + 31) >> 5, a.mask_words);
     int count = 0, nch = 0;
-    if (!CONE && UNROLL2) {
+    if (COARSE && shared) {
+        // Every cell index along each axis, at each level, is a monotone function
+        // of k (t_k, the midpoints and the rounded index arithmetic all are), and so
+        // is the index clamped to [-1, res]. If two points have the same clamped
+        // indices at every level, so does every point between them: they share the
+        // level that holds them and its cell. Lane j takes point 32(g + j) (the last
+        // point where that is past the lattice); chunk g + j (j < 31) whose first
+        // point and the next chunk's first point agree lies in one cell, and its
+        // ballot word follows from one occupancy test. The other chunks are tested
+        // point by point. Groups of 31 chunks.
+        int part = 0;  // samples of this lane's single-cell chunks
+        for (int g = 0; g < max_ch; g += 31) {
+            const int kp = min((g + lane) << 5, nk - 1);
+            float ts, tn;
+            if (!CONE) {
+                const float kf = __int2float_rn(kp);
+                ts = __fadd_rn(near, __fmul_rn(kf, dt));
+                tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+            } else {
+                ts = __ldg(a.cone_table + min(kp, a.max_steps));
+                tn = __ldg(a.cone_table + min(kp + 1, a.max_steps));
+            }
+            const float te = tn < far ? tn : far;
+            const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
+            const float x0 = __fadd_rn(o[0], __fmul_rn(d[0], mid));
+            const float x1 = __fadd_rn(o[1], __fmul_rn(d[1], mid));
+            const float x2 = __fadd_rn(o[2], __fmul_rn(d[2], mid));
+            bool same = true;
+#pragma unroll
+            for (int l = 0; l < MAXL; ++l) {
+                if (l >= a.n_levels) break;
+                const int i0 = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x0, a.L.lo[l][0]), a.L.scale[l][0])), -1),
+                                   a.res0);
+                const int i1 = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x1, a.L.lo[l][1]), a.L.scale[l][1])), -1),
+                                   a.res1);
+                const int i2 = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x2, a.L.lo[l][2]), a.L.scale[l][2])), -1),
+                                   a.res2);
+                const int n0 = __shfl_down_sync(FULL, i0, 1);
+                const int n1 = __shfl_down_sync(FULL, i1, 1);
+                const int n2 = __shfl_down_sync(FULL, i2, 1);
+                same = same && i0 == n0 && i1 == n1 && i2 == n2;
+            }
+            const bool occ_p = occupied<MAXL>(a, x0, x1, x2, sl0);
+            const int c = g + lane;
+            const bool exists = lane < 31 && c < max_ch;
+            const bool uni = exists && same;
+            if (uni) {
+                const int n = min(32, nk - (c << 5));
+                const uint32_t m = occ_p ? (n >= 32 ? ~0u : (1u << n) - 1u) : 0u;
+                row[c] = m;
+                part += __popc(m);
+            }
+            unsigned pend = __ballot_sync(FULL, exists && !uni);
+            while (pend) {
+                const int cc = g + __ffs(pend) - 1;
+                pend &= pend - 1;
+                const int k = (cc << 5) + lane;
+                float ks, kn;
+                if (!CONE) {
+                    const float kf = __int2float_rn(k);
+                    ks = __fadd_rn(near, __fmul_rn(kf, dt));
+                    kn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+                } else {
+                    ks = __ldg(a.cone_table + min(k, a.max_steps));
+                    kn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                }
+                bool occ = false;
+                if (k < nk && ks < far) {
+                    const float ke = kn < far ? kn : far;
+                    const float km = __fmul_rn(__fadd_rn(ks, ke), 0.5f);
+                    occ = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], km)), __fadd_rn(o[1], __fmul_rn(d[1], km)),
+                                         __fadd_rn(o[2], __fmul_rn(d[2], km)), sl0);
+                }
+                const unsigned m = __ballot_sync(FULL, occ);
+                if (lane == 0) row[cc] = m;
+                count += __popc(m);
+            }
+        }
+        count += __reduce_add_sync(FULL, part);
+        nch = max_ch;
+    } else if (!CONE && UNROLL2) {
         // two chunks per iteration: two independent chains and two grid loads in flight per lane
         for (int c = 0; c < max_ch; c += 2) {
             const int k0 = (c << 5) + lane, k1 = k0 + 32;
@@ -372,7 +454,7 @@ __device__ __forceinline__ void emit_tile(const MarchArgs& a, const uint32_t* wm
 // ---------------------------------------------------------------------------
 
 // Lattice walk: the warp takes the tile's rays one at a time.
-template <int MAXL, int MINB, bool CONE, bool UNROLL2 = false>
+template <int MAXL, int MINB, bool CONE, bool UNROLL2 = false, bool COARSE = false>
 __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const MarchArgs a) {
     extern __shared__ uint32_t s_masks[];  // per warp: [tile_rays][row_stride]
     __shared__ float s_lat[kWarps][36];    // cone steps with a ray-specific start
@@ -405,7 +487,7 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
             const bool slot_ok = slot >= 0 && slot < a.n_slots;
             if (!slot_ok && lane == 0) raise_status(a.d_status, NACC_STATUS_BAD_INDEX);
             if (slot_ok && clip_ray(a, o, d, near, far))
-                walk_lattice<MAXL, CONE, UNROLL2>(a, o, d, near, far, (unsigned)slot * (unsigned)a.n_levels,
+                walk_lattice<MAXL, CONE, UNROLL2, COARSE>(a, o, d, near, far, (unsigned)slot * (unsigned)a.n_levels,
                                                  wmask + i * a.row_stride, lat, lane, count, nch);
             if (lane == i) {
                 my_count = count;
@@ -513,16 +595,31 @@ void launch_uniform(K kernel, size_t smem, int need, cudaStream_t st, const Marc
     kernel<<<blocks, kThreads, smem, st>>>(a);
 }
 
-// Cascades (two or more levels); the single-level walk has its own unrolled variant.
-template <int MAXL>
-void launch_walk(bool cone, bool occ, size_t smem, int need, cudaStream_t st, const MarchArgs& a) {
+// Kernel variant for a level count, step rule and the tuning knobs.
+template <int MAXL, int MINB>
+void launch_variant(bool cone, bool unroll, bool coarse, size_t smem, int need, cudaStream_t st,
+                    const MarchArgs& a) {
     if (cone) {
-        if (occ) launch_uniform(march_uniform_kernel<MAXL, 8, true>, smem, need, st, a);
-        else launch_uniform(march_uniform_kernel<MAXL, 1, true>, smem, need, st, a);
+        if (coarse) launch_uniform(march_uniform_kernel<MAXL, MINB, true, false, true>, smem, need, st, a);
+        else launch_uniform(march_uniform_kernel<MAXL, MINB, true>, smem, need, st, a);
+    } else if (coarse) {
+        launch_uniform(march_uniform_kernel<MAXL, MINB, false, false, true>, smem, need, st, a);
     } else {
-        if (occ) launch_uniform(march_uniform_kernel<MAXL, 8, false>, smem, need, st, a);
-        else launch_uniform(march_uniform_kernel<MAXL, 1, false>, smem, need, st, a);
+        if constexpr (MAXL == 1) {  // two-chunk unrolling exists for the single-level uniform walk
+            if (unroll) {
+                launch_uniform(march_uniform_kernel<MAXL, MINB, false, true>, smem, need, st, a);
+                return;
+            }
+        }
+        launch_uniform(march_uniform_kernel<MAXL, MINB, false>, smem, need, st, a);
     }
+}
+
+template <int MAXL>
+void launch_walk(bool cone, bool occ, bool unroll, bool coarse, size_t smem, int need, cudaStream_t st,
+                 const MarchArgs& a) {
+    if (occ) launch_variant<MAXL, 8>(cone, unroll, coarse, smem, need, st, a);
+    else launch_variant<MAXL, 1>(cone, unroll, coarse, smem, need, st, a);
 }
 
 }  // namespace
@@ -614,21 +711,9 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
     const size_t smem = (size_t)kWarps * a.tile_rays * a.row_stride * sizeof(uint32_t);
     const int need = (a.n_tiles + kWarps - 1) / kWarps;
     const bool unroll = tune_get(NACC_TUNE_MARCH_UNROLL) != 0;
-    if (a.n_levels == 1) {
-        if (cone) {
-            if (occ) launch_uniform(march_uniform_kernel<1, 8, true>, smem, need, st, a);
-            else launch_uniform(march_uniform_kernel<1, 1, true>, smem, need, st, a);
-        } else if (unroll) {
-            if (occ) launch_uniform(march_uniform_kernel<1, 8, false, true>, smem, need, st, a);
-            else launch_uniform(march_uniform_kernel<1, 1, false, true>, smem, need, st, a);
-        } else {
-            if (occ) launch_uniform(march_uniform_kernel<1, 8, false>, smem, need, st, a);
-            else launch_uniform(march_uniform_kernel<1, 1, false>, smem, need, st, a);
-        }
-    } else if (a.n_levels <= 4) {
-        launch_walk<4>(cone, occ, smem, need, st, a);
-    } else {
-        launch_walk<NACC_MAX_LEVELS>(cone, occ, smem, need, st, a);
-    }
+    const bool coarse = tune_get(NACC_TUNE_MARCH_COARSE) != 0;
+    if (a.n_levels == 1) launch_walk<1>(cone, occ, unroll, coarse, smem, need, st, a);
+    else if (a.n_levels <= 4) launch_walk<4>(cone, occ, unroll, coarse, smem, need, st, a);
+    else launch_walk<NACC_MAX_LEVELS>(cone, occ, unroll, coarse, smem, need, st, a);
     return launch_status(cudaGetLastError());
 }

@@ -1,5 +1,5 @@
-"""Marching against the oracle, bit-exact, on inputs aimed at the float32 cell
-decisions: midpoints exactly on cell faces, directions with tiny or zero
+"""Marching against the oracle, bit-exact, with and without the coarse pass, on
+inputs aimed at the float32 cell decisions: midpoints exactly on cell faces, directions with tiny or zero
 components, directions far from unit length, origins far from the grid (large
 rounding), cascades with uniform steps, cells smaller than one step, a negative
 near plane, cone steps over a cascade, and whole full-size batches (every
@@ -18,7 +18,18 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no CUDA device", allow_module_level=True)
 
+from paper_2210_04847_gb300 import _lib  # noqa: E402
 from gpu_util import assert_march_equal, gpu_march, oracle_march  # noqa: E402
+
+
+@pytest.fixture(autouse=True, params=[0, 1], ids=["pointwise", "coarse"])
+def coarse(request):
+    """Every case with and without the coarse pass (chunks inside one cell filled
+    from a single occupancy test)."""
+    old = _lib.tune_get("march_coarse")
+    _lib.tune_set("march_coarse", request.param)
+    yield request.param
+    _lib.tune_set("march_coarse", old)
 
 def _workload(o, d, occ, res, aabb, n_levels=1, near=0.0, far=1e10, dt_min=0.05, dt_max=0.05, cone=0.0,
               max_steps=1024):
