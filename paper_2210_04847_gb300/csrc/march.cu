@@ -124,7 +124,7 @@ __device__ __forceinline__ bool occupied(const MarchArgs& a, float x0, float x1,
                                          unsigned slot_level0) {
 #pragma unroll
     for (int l = 0; l < MAXL; ++l) {
-        if (l >= a.n_levels) break;
+        if (MAXL > 1 && l >= a.n_levels) break;  // single-level kernels run only for n_levels == 1
         const int i0 = __float2int_rd(__fmul_rn(__fsub_rn(x0, a.L.lo[l][0]), a.L.scale[l][0]));
         const int i1 = __float2int_rd(__fmul_rn(__fsub_rn(x1, a.L.lo[l][1]), a.L.scale[l][1]));
         const int i2 = __float2int_rd(__fmul_rn(__fsub_rn(x2, a.L.lo[l][2]), a.L.scale[l][2]));
@@ -336,6 +336,56 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
             count += __popc(m0) + __popc(m1);
         }
         nch = max_ch;
+    } else if (shared) {
+        // closed-form or tabulated lattice: t_k < far for every k < nk, so every
+        // chunk below nk/32 is full and only the last one needs the bound test; the
+        // count is summed from the finished row
+        const int nfull = nk >> 5;
+        for (int c = 0; c < nfull; ++c) {
+            const int k = (c << 5) + lane;
+            float ts, tn;
+            if (!CONE) {
+                const float kf = __int2float_rn(k);
+                ts = __fadd_rn(near, __fmul_rn(kf, dt));
+                tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+            } else {
+                ts = __ldg(a.cone_table + min(k, a.max_steps));
+                tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+            }
+            const float te = tn < far ? tn : far;
+            const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
+            const bool occ = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)),
+                                            __fadd_rn(o[1], __fmul_rn(d[1], mid)),
+                                            __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0);
+            const unsigned m = __ballot_sync(FULL, occ);
+            if (lane == 0) row[c] = m;
+        }
+        if (nfull < max_ch) {
+            const int k = (nfull << 5) + lane;
+            float ts, tn;
+            if (!CONE) {
+                const float kf = __int2float_rn(k);
+                ts = __fadd_rn(near, __fmul_rn(kf, dt));
+                tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+            } else {
+                ts = __ldg(a.cone_table + min(k, a.max_steps));
+                tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+            }
+            bool occ = false;
+            if (k < nk && ts < far) {
+                const float te = tn < far ? tn : far;
+                const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
+                occ = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)), __fadd_rn(o[1], __fmul_rn(d[1], mid)),
+                                     __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0);
+            }
+            const unsigned m = __ballot_sync(FULL, occ);
+            if (lane == 0) row[nfull] = m;
+        }
+        nch = max_ch;
+        __syncwarp();
+        int part = 0;
+        for (int w = lane; w < nch; w += 32) part += __popc(row[w]);
+        count = __reduce_add_sync(FULL, part);
     } else {
         float tcur = near;
         int c = 0;
