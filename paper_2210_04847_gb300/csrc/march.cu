@@ -432,19 +432,35 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
 // phases 2 and 3 of a tile (shared by both phase-1 strategies)
 // ---------------------------------------------------------------------------
 
-// Offsets inside the tile, the tile's offset by look-back, then the ballot words
-// expanded into compacted, coalesced stores of (t_start, t_end, ray). Lane i
-// holds ray i's count, first and last ballot words and [near, far].
+// One tile between its ballot pass and its stores. Lane i holds ray i's sample
+// count, ballot words written, [near, far] and inclusive count within the tile.
+struct TileState {
+    int tile, ray0, nr, agg;
+    int my_count, my_nch, incl;
+    float my_near, my_far;
+};
+
+// After phase 1: counts within the tile, and the tile's total published for the
+// look-back (never waits).
+__device__ __forceinline__ void publish_tile(const MarchArgs& a, TileState& t, int lane) {
+    t.incl = warp_incl_scan_int(t.my_count, lane);
+    t.agg = __shfl_sync(FULL, t.incl, 31);
+    publish_aggregate(a.tile_status, t.tile, (unsigned long long)t.agg, lane);
+}
+
+// The tile's offset by look-back, then the ballot words expanded into
+// compacted, coalesced stores of (t_start, t_end, ray).
 template <bool CONE>
-__device__ __forceinline__ void emit_tile(const MarchArgs& a, const uint32_t* wmask, int tile, int ray0, int nr,
-                                          int my_count, int my_c0, int my_nch, float my_near, float my_far,
-                                          float* lat, int lane) {
+__device__ __forceinline__ void finish_tile(const MarchArgs& a, const uint32_t* wmask, const TileState& t,
+                                            float* lat, int lane) {
     const float dt = a.dt_min;
     const unsigned lt = lanemask_lt();
-    const int incl = warp_incl_scan_int(my_count, lane);
-    const int agg = __shfl_sync(FULL, incl, 31);
-    const long long excl = (long long)lookback(a.tile_status, tile, (unsigned long long)agg, lane, a.d_status);
-    const int my_excl = incl - my_count;
+    const int tile = t.tile, ray0 = t.ray0, nr = t.nr, agg = t.agg;
+    const int my_count = t.my_count, my_nch = t.my_nch;
+    const float my_near = t.my_near, my_far = t.my_far;
+    const long long excl =
+        (long long)resolve_prefix(a.tile_status, tile, (unsigned long long)agg, lane, a.d_status);
+    const int my_excl = t.incl - my_count;
     if (lane < nr) {
         const int2 pi = make_int2((int)(excl + my_excl), my_count);
         reinterpret_cast<int2*>(a.packed_info)[ray0 + lane] = pi;
@@ -462,7 +478,6 @@ __device__ __forceinline__ void emit_tile(const MarchArgs& a, const uint32_t* wm
     for (int i = 0; i < nr; ++i) {
         const int cnt = __shfl_sync(FULL, my_count, i);
         if (cnt == 0) continue;
-        const int c0 = __shfl_sync(FULL, my_c0, i);
         const int nch = __shfl_sync(FULL, my_nch, i);
         const float near = __shfl_sync(FULL, my_near, i);
         const float far = __shfl_sync(FULL, my_far, i);
@@ -471,7 +486,7 @@ __device__ __forceinline__ void emit_tile(const MarchArgs& a, const uint32_t* wm
         const uint32_t* row = wmask + i * a.row_stride;
         unsigned base = (unsigned)excl + (unsigned)__shfl_sync(FULL, my_excl, i);
         float tcur = near;
-        for (int c = c0; c < nch; ++c) {
+        for (int c = 0; c < nch; ++c) {
             const unsigned m = row[c];
             if (shared && m == 0u) continue;  // an own cone lattice is extended chunk by chunk
             const int k = (c << 5) + lane;
@@ -503,52 +518,75 @@ __device__ __forceinline__ void emit_tile(const MarchArgs& a, const uint32_t* wm
 // kernels
 // ---------------------------------------------------------------------------
 
-// Lattice walk: the warp takes the tile's rays one at a time.
+// Lattice walk: the warp takes the tile's rays one at a time. Tiles go two deep:
+// the warp runs the ballot pass of a new tile and publishes its total before it
+// waits for the offset of the tile it did before (whose rows sit in the other
+// half of the warp's shared memory), so the look-back rarely stalls.
 template <int MAXL, int MINB, bool CONE, bool UNROLL2 = false, bool COARSE = false>
 __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const MarchArgs a) {
-    extern __shared__ uint32_t s_masks[];  // per warp: [tile_rays][row_stride]
+    extern __shared__ uint32_t s_masks[];  // per warp: 2 x [tile_rays][row_stride]
     __shared__ float s_lat[kWarps][36];    // cone steps with a ray-specific start
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    uint32_t* wmask = s_masks + (size_t)warp * a.tile_rays * a.row_stride;
+    const size_t tile_words = (size_t)a.tile_rays * a.row_stride;
+    uint32_t* wbase = s_masks + (size_t)warp * 2 * tile_words;
     float* lat = s_lat[warp];
 
+    TileState prev;
+    bool have_prev = false;
+    int buf = 0;
     for (;;) {
         int tile = 0;
         if (lane == 0) tile = (int)atomicAdd(a.ticket, 1u);
         tile = __shfl_sync(FULL, tile, 0);
-        if (tile >= a.n_tiles) break;
-        const int ray0 = tile * a.tile_rays;
-        const int nr = min(a.tile_rays, a.n_rays - ray0);
-
-        int my_count = 0, my_nch = 0;
-        float my_near = 0.0f, my_far = 0.0f;
-        for (int i = 0; i < nr; ++i) {
-            const int r = ray0 + i;
-            float o[3], d[3];
+        const bool have = tile < a.n_tiles;
+        TileState cur;
+        if (have) {
+            uint32_t* wmask = wbase + buf * tile_words;
+            cur.tile = tile;
+            cur.ray0 = tile * a.tile_rays;
+            cur.nr = min(a.tile_rays, a.n_rays - cur.ray0);
+            int my_count = 0, my_nch = 0;
+            float my_near = 0.0f, my_far = 0.0f;
+            for (int i = 0; i < cur.nr; ++i) {
+                const int r = cur.ray0 + i;
+                float o[3], d[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                o[k] = __ldg(a.rays_o + 3 * (size_t)r + k);
-                d[k] = __ldg(a.rays_d + 3 * (size_t)r + k);
+                for (int k = 0; k < 3; ++k) {
+                    o[k] = __ldg(a.rays_o + 3 * (size_t)r + k);
+                    d[k] = __ldg(a.rays_d + 3 * (size_t)r + k);
+                }
+                float near = 0.0f, far = 0.0f;
+                int count = 0, nch = 0;
+                const int slot = slot_of(a, r);
+                const bool slot_ok = slot >= 0 && slot < a.n_slots;
+                if (!slot_ok && lane == 0) raise_status(a.d_status, NACC_STATUS_BAD_INDEX);
+                if (slot_ok && clip_ray(a, o, d, near, far))
+                    walk_lattice<MAXL, CONE, UNROLL2, COARSE>(a, o, d, near, far,
+                                                              (unsigned)slot * (unsigned)a.n_levels,
+                                                              wmask + i * a.row_stride, lat, lane, count, nch);
+                if (lane == i) {
+                    my_count = count;
+                    my_nch = nch;
+                    my_near = near;
+                    my_far = far;
+                }
             }
-            float near = 0.0f, far = 0.0f;
-            int count = 0, nch = 0;
-            const int slot = slot_of(a, r);
-            const bool slot_ok = slot >= 0 && slot < a.n_slots;
-            if (!slot_ok && lane == 0) raise_status(a.d_status, NACC_STATUS_BAD_INDEX);
-            if (slot_ok && clip_ray(a, o, d, near, far))
-                walk_lattice<MAXL, CONE, UNROLL2, COARSE>(a, o, d, near, far, (unsigned)slot * (unsigned)a.n_levels,
-                                                 wmask + i * a.row_stride, lat, lane, count, nch);
-            if (lane == i) {
-                my_count = count;
-                my_nch = nch;
-                my_near = near;
-                my_far = far;
-            }
+            __syncwarp();
+            cur.my_count = my_count;
+            cur.my_nch = my_nch;
+            cur.my_near = my_near;
+            cur.my_far = my_far;
+            publish_tile(a, cur, lane);
         }
-        __syncwarp();
-        emit_tile<CONE>(a, wmask, tile, ray0, nr, my_count, 0, my_nch, my_near, my_far, lat, lane);
-        __syncwarp();
+        if (have_prev) {
+            finish_tile<CONE>(a, wbase + (buf ^ 1) * tile_words, prev, lat, lane);
+            __syncwarp();
+        }
+        if (!have) break;
+        prev = cur;
+        have_prev = true;
+        buf ^= 1;
     }
 }
 
@@ -578,9 +616,9 @@ int mask_words_for(const nacc_march_params* p) {
     return words < full ? words : full;
 }
 
-// Rays per warp tile: up to 8, fewer when long lattices make the ballot rows
-// big (the warp's shared-memory slice stays within kWarpSmemBudget bytes).
-constexpr size_t kWarpSmemBudget = 4096;
+// Rays per warp tile: at most the knob, fewer when long lattices make the ballot
+// rows big (each of the warp's two tile buffers stays within kWarpSmemBudget bytes).
+constexpr size_t kWarpSmemBudget = 2048;
 int tile_rays_for(int mask_words) {
     int t = (int)(kWarpSmemBudget / ((size_t)mask_words * sizeof(uint32_t)));
     const int cap = tune_get(NACC_TUNE_MARCH_TILE_RAYS);
@@ -758,7 +796,7 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
         a.cone_table = table;
         cone_table_kernel<<<1, 32, 0, st>>>(a, table);
     }
-    const size_t smem = (size_t)kWarps * a.tile_rays * a.row_stride * sizeof(uint32_t);
+    const size_t smem = (size_t)kWarps * 2 * a.tile_rays * a.row_stride * sizeof(uint32_t);
     const int need = (a.n_tiles + kWarps - 1) / kWarps;
     const bool unroll = tune_get(NACC_TUNE_MARCH_UNROLL) != 0;
     const bool coarse = tune_get(NACC_TUNE_MARCH_COARSE) != 0;

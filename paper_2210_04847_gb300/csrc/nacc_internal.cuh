@@ -93,16 +93,21 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Called by one full warp. Returns the exclusive prefix of tile `tile` (sum of
-// the aggregates of tiles 0..tile-1) and publishes the inclusive prefix.
-__device__ __forceinline__ unsigned long long lookback(unsigned long long* status, int tile,
-                                                       unsigned long long aggregate, int lane,
-                                                       int32_t* d_status) {
-    if (tile == 0) {
-        if (lane == 0) st_relaxed_u64(&status[0], kFlagInc | (aggregate & kValMask));
-        return 0ull;
-    }
-    if (lane == 0) st_relaxed_u64(&status[tile], kFlagAgg | (aggregate & kValMask));
+// Publishes a tile's aggregate (tile 0: its inclusive prefix). Never waits.
+__device__ __forceinline__ void publish_aggregate(unsigned long long* status, int tile,
+                                                  unsigned long long aggregate, int lane) {
+    if (lane == 0) st_relaxed_u64(&status[tile], (tile == 0 ? kFlagInc : kFlagAgg) | (aggregate & kValMask));
+}
+
+// Called by one full warp after publish_aggregate(tile). Returns the exclusive
+// prefix of the tile (sum of the aggregates of tiles 0..tile-1) and publishes
+// its inclusive prefix. A warp may publish further tiles' aggregates before
+// resolving an earlier one: every tile it waits for has a lower ticket, and
+// the warp holding that ticket publishes its aggregate before it waits.
+__device__ __forceinline__ unsigned long long resolve_prefix(unsigned long long* status, int tile,
+                                                             unsigned long long aggregate, int lane,
+                                                             int32_t* d_status) {
+    if (tile == 0) return 0ull;
     unsigned long long excl = 0;
     int base = tile - 1;
     int spins = 0;
@@ -139,6 +144,14 @@ __device__ __forceinline__ unsigned long long lookback(unsigned long long* statu
     if (timed_out && lane == 0) raise_status(d_status, NACC_STATUS_TIMEOUT);
     if (lane == 0) st_relaxed_u64(&status[tile], kFlagInc | ((excl + aggregate) & kValMask));
     return excl;
+}
+
+// Both steps at once: publish the tile's aggregate, then wait for its prefix.
+__device__ __forceinline__ unsigned long long lookback(unsigned long long* status, int tile,
+                                                       unsigned long long aggregate, int lane,
+                                                       int32_t* d_status) {
+    publish_aggregate(status, tile, aggregate, lane);
+    return resolve_prefix(status, tile, aggregate, lane, d_status);
 }
 
 // ---------------------------------------------------------------------------

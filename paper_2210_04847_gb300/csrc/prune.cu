@@ -176,118 +176,152 @@ __device__ __forceinline__ void phase1_walk(const PruneArgs& a, int ray0, int nr
     }
 }
 
-// Tiles of consecutive rays; phase 1 walks IL rays at a time.
+// One tile between its decisions and its stores. Lane i holds ray i's run,
+// kept count, chunks read and inclusive kept prefix within the tile.
+struct TileState {
+    int tile, ray0, nr, agg;
+    int my_off, my_cnt, my_count, my_nch, incl;
+};
+
+// Phases 0 and 1 of a tile: validate the runs, decide every chunk (ballot rows
+// in the workspace), then publish the tile's kept total for the look-back.
+template <int IL>
+__device__ __forceinline__ void decide_tile(const PruneArgs& a, int tile, int lane, TileState& t) {
+    t.tile = tile;
+    t.ray0 = tile * a.tile_rays;
+    t.nr = min(a.tile_rays, a.n_rays - t.ray0);
+    const int ray0 = t.ray0, nr = t.nr;
+
+    // runs of the tile's rays: must be in bounds, ascending and disjoint in ray
+    // order (the layout marching and pruning produce), so that the ballot rows
+    // of different rays never overlap
+    int my_off = 0, my_cnt = 0;
+    if (lane < nr) {
+        const int2 v = reinterpret_cast<const int2*>(a.packed_info)[ray0 + lane];
+        my_off = v.x;
+        my_cnt = v.y;
+    }
+    long long prev_end = __shfl_up_sync(FULL, (long long)my_off + my_cnt, 1);
+    if (lane == 0) {
+        prev_end = 0;
+        if (ray0 > 0) {
+            const int2 v = reinterpret_cast<const int2*>(a.packed_info)[ray0 - 1];
+            prev_end = (long long)v.x + v.y;
+        }
+    }
+    if (lane < nr) {
+        bool bad = my_off < 0 || my_cnt < 0 || (long long)my_off + my_cnt > a.n_samples;
+        if (my_cnt > 0 && (long long)my_off < prev_end && (ray0 + lane) > 0) bad = true;
+        if (bad) {
+            raise_status(a.d_status, NACC_STATUS_BAD_PACKED);
+            my_off = 0;
+            my_cnt = 0;
+        }
+    }
+
+    // phase 1: keep decisions into the ballot rows, kept counts per ray
+    int my_count = 0, my_nch = 0;
+    phase1_walk<IL>(a, ray0, nr, my_off, my_cnt, lane, my_count, my_nch);
+    __syncwarp();
+    t.my_off = my_off;
+    t.my_cnt = my_cnt;
+    t.my_count = my_count;
+    t.my_nch = my_nch;
+    t.incl = warp_incl_scan_int(my_count, lane);
+    t.agg = __shfl_sync(FULL, t.incl, 31);
+    publish_aggregate(a.tile_status, tile, (unsigned long long)t.agg, lane);
+}
+
+// Phases 2 and 3 of a tile: its offset from the look-back, then the compacted
+// stores of the kept samples (and the optional mask).
+__device__ __forceinline__ void finish_tile(const PruneArgs& a, const TileState& t, int lane, unsigned lt) {
+    const int ray0 = t.ray0, nr = t.nr;
+    int seen = lane < nr ? min(t.my_cnt, (t.my_nch << 6) - (t.my_off & 1)) : 0;
+    if (seen < 0) seen = 0;
+    for (int o = 16; o > 0; o >>= 1) seen += __shfl_xor_sync(FULL, seen, o);
+    const long long excl =
+        (long long)resolve_prefix(a.tile_status, t.tile, (unsigned long long)t.agg, lane, a.d_status);
+    const int my_excl = t.incl - t.my_count;
+    if (lane < nr) {
+        const int2 pi = make_int2((int)(excl + my_excl), t.my_count);
+        reinterpret_cast<int2*>(a.packed_info_out)[ray0 + lane] = pi;
+    }
+    if (lane == 0) {
+        atomicAdd(a.examined, (unsigned long long)seen);
+        if (t.tile == a.n_tiles - 1) {
+            const long long total = excl + t.agg;
+            *a.n_kept = total;
+            if (total > a.capacity) raise_status(a.d_status, NACC_STATUS_CAPACITY);
+            if (total > 0x7fffffffLL) raise_status(a.d_status, NACC_STATUS_OVERFLOW);
+        }
+    }
+
+    for (int i = 0; i < nr; ++i) {
+        const int off = __shfl_sync(FULL, t.my_off, i);
+        const int cnt = __shfl_sync(FULL, t.my_cnt, i);
+        const int nch = __shfl_sync(FULL, t.my_nch, i);
+        const int r = ray0 + i;
+        const long long end = (long long)off + cnt;
+        const long long abase = off & ~1;
+        const uint32_t* row = mask_row(a, off, r);
+        long long base = excl + __shfl_sync(FULL, my_excl, i);
+        for (int c0 = 0; c0 < nch; c0 += 16) {
+            // 16 chunks' ballot word pairs at once
+            const unsigned mw = (c0 + (lane >> 1) < nch) ? row[2 * c0 + lane] : 0u;
+            const int n = min(16, nch - c0);
+            for (int q = 0; q < n; ++q) {
+                const unsigned m0 = __shfl_sync(FULL, mw, 2 * q);
+                const unsigned m1 = __shfl_sync(FULL, mw, 2 * q + 1);
+                const long long j0 = abase + ((long long)(c0 + q) << 6) + 2 * lane;
+                const bool b0 = (m0 >> lane) & 1u, b1 = (m1 >> lane) & 1u;
+                if (a.keep_mask) {
+                    if (j0 >= off && j0 < end) a.keep_mask[j0] = (uint8_t)b0;
+                    if (j0 + 1 >= off && j0 + 1 < end) a.keep_mask[j0 + 1] = (uint8_t)b1;
+                }
+                const long long pos0 = base + __popc(m0 & lt) + __popc(m1 & lt);
+                if (b0 && pos0 < a.capacity) {
+                    a.t_starts_out[pos0] = __ldg(a.t_starts + j0);
+                    a.t_ends_out[pos0] = __ldg(a.t_ends + j0);
+                    a.ray_indices_out[pos0] = r;
+                }
+                const long long pos1 = pos0 + (b0 ? 1 : 0);
+                if (b1 && pos1 < a.capacity) {
+                    a.t_starts_out[pos1] = __ldg(a.t_starts + j0 + 1);
+                    a.t_ends_out[pos1] = __ldg(a.t_ends + j0 + 1);
+                    a.ray_indices_out[pos1] = r;
+                }
+                base += __popc(m0) + __popc(m1);
+            }
+        }
+        if (a.keep_mask) {
+            const long long from = abase + ((long long)nch << 6);
+            for (long long j = (from > off ? from : off) + lane; j < end; j += 32) a.keep_mask[j] = 0;
+        }
+    }
+    __syncwarp();
+}
+
+// Tiles of consecutive rays taken from an atomic ticket, two deep: the warp
+// decides a new tile and publishes its total before it waits for the offset of
+// the tile it decided before (by then its predecessors have almost always
+// published), so the look-back rarely stalls.
 template <int IL>
 __device__ __forceinline__ void prune_body(const PruneArgs& a) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
-
+    TileState prev;
+    bool have_prev = false;
     for (;;) {
         int tile = 0;
         if (lane == 0) tile = (int)atomicAdd(a.ticket, 1u);
         tile = __shfl_sync(FULL, tile, 0);
-        if (tile >= a.n_tiles) break;
-        const int ray0 = tile * a.tile_rays;
-        const int nr = min(a.tile_rays, a.n_rays - ray0);
-
-        // runs of the tile's rays: must be in bounds, ascending and disjoint in ray
-        // order (the layout marching and pruning produce), so that the ballot rows
-        // of different rays never overlap
-        int my_off = 0, my_cnt = 0;
-        if (lane < nr) {
-            const int2 v = reinterpret_cast<const int2*>(a.packed_info)[ray0 + lane];
-            my_off = v.x;
-            my_cnt = v.y;
-        }
-        long long prev_end = __shfl_up_sync(FULL, (long long)my_off + my_cnt, 1);
-        if (lane == 0) {
-            prev_end = 0;
-            if (ray0 > 0) {
-                const int2 v = reinterpret_cast<const int2*>(a.packed_info)[ray0 - 1];
-                prev_end = (long long)v.x + v.y;
-            }
-        }
-        if (lane < nr) {
-            bool bad = my_off < 0 || my_cnt < 0 || (long long)my_off + my_cnt > a.n_samples;
-            if (my_cnt > 0 && (long long)my_off < prev_end && (ray0 + lane) > 0) bad = true;
-            if (bad) {
-                raise_status(a.d_status, NACC_STATUS_BAD_PACKED);
-                my_off = 0;
-                my_cnt = 0;
-            }
-        }
-
-        // phase 1: keep decisions into the ballot rows, kept counts per ray
-        int my_count = 0, my_nch = 0;
-        phase1_walk<IL>(a, ray0, nr, my_off, my_cnt, lane, my_count, my_nch);
-        __syncwarp();
-
-        // phase 2: offsets inside the tile, then the tile's offset by look-back
-        const int incl = warp_incl_scan_int(my_count, lane);
-        const int agg = __shfl_sync(FULL, incl, 31);
-        int seen = lane < nr ? min(my_cnt, (my_nch << 6) - (my_off & 1)) : 0;
-        if (seen < 0) seen = 0;
-        for (int o = 16; o > 0; o >>= 1) seen += __shfl_xor_sync(FULL, seen, o);
-        const long long excl = (long long)lookback(a.tile_status, tile, (unsigned long long)agg, lane, a.d_status);
-        const int my_excl = incl - my_count;
-        if (lane < nr) {
-            const int2 pi = make_int2((int)(excl + my_excl), my_count);
-            reinterpret_cast<int2*>(a.packed_info_out)[ray0 + lane] = pi;
-        }
-        if (lane == 0) {
-            atomicAdd(a.examined, (unsigned long long)seen);
-            if (tile == a.n_tiles - 1) {
-                const long long total = excl + agg;
-                *a.n_kept = total;
-                if (total > a.capacity) raise_status(a.d_status, NACC_STATUS_CAPACITY);
-                if (total > 0x7fffffffLL) raise_status(a.d_status, NACC_STATUS_OVERFLOW);
-            }
-        }
-
-        // phase 3: compacted stores of the kept samples (and the optional mask)
-        for (int i = 0; i < nr; ++i) {
-            const int off = __shfl_sync(FULL, my_off, i);
-            const int cnt = __shfl_sync(FULL, my_cnt, i);
-            const int nch = __shfl_sync(FULL, my_nch, i);
-            const int r = ray0 + i;
-            const long long end = (long long)off + cnt;
-            const long long abase = off & ~1;
-            const uint32_t* row = mask_row(a, off, r);
-            long long base = excl + __shfl_sync(FULL, my_excl, i);
-            for (int c0 = 0; c0 < nch; c0 += 16) {
-                // 16 chunks' ballot word pairs at once
-                const unsigned mw = (c0 + (lane >> 1) < nch) ? row[2 * c0 + lane] : 0u;
-                const int n = min(16, nch - c0);
-                for (int q = 0; q < n; ++q) {
-                    const unsigned m0 = __shfl_sync(FULL, mw, 2 * q);
-                    const unsigned m1 = __shfl_sync(FULL, mw, 2 * q + 1);
-                    const long long j0 = abase + ((long long)(c0 + q) << 6) + 2 * lane;
-                    const bool b0 = (m0 >> lane) & 1u, b1 = (m1 >> lane) & 1u;
-                    if (a.keep_mask) {
-                        if (j0 >= off && j0 < end) a.keep_mask[j0] = (uint8_t)b0;
-                        if (j0 + 1 >= off && j0 + 1 < end) a.keep_mask[j0 + 1] = (uint8_t)b1;
-                    }
-                    const long long pos0 = base + __popc(m0 & lt) + __popc(m1 & lt);
-                    if (b0 && pos0 < a.capacity) {
-                        a.t_starts_out[pos0] = __ldg(a.t_starts + j0);
-                        a.t_ends_out[pos0] = __ldg(a.t_ends + j0);
-                        a.ray_indices_out[pos0] = r;
-                    }
-                    const long long pos1 = pos0 + (b0 ? 1 : 0);
-                    if (b1 && pos1 < a.capacity) {
-                        a.t_starts_out[pos1] = __ldg(a.t_starts + j0 + 1);
-                        a.t_ends_out[pos1] = __ldg(a.t_ends + j0 + 1);
-                        a.ray_indices_out[pos1] = r;
-                    }
-                    base += __popc(m0) + __popc(m1);
-                }
-            }
-            if (a.keep_mask) {
-                const long long from = abase + ((long long)nch << 6);
-                for (long long j = (from > off ? from : off) + lane; j < end; j += 32) a.keep_mask[j] = 0;
-            }
-        }
-        __syncwarp();
+        const bool have = tile < a.n_tiles;
+        TileState cur;
+        if (have) decide_tile<IL>(a, tile, lane, cur);
+        if (have_prev) finish_tile(a, prev, lane, lt);
+        if (!have) break;
+        prev = cur;
+        have_prev = true;
     }
 }
 
