@@ -46,8 +46,8 @@ POOL = 4  # distinct ray batches cycled through the steps (L2 is flushed between
 # from one ncu capture, keyed by the SHA-256 of the kernel's source file. A
 # source change invalidates the figure (reported as null until re-captured).
 NCU_TRAFFIC = {
-    # profiles/march_dram_bounded-2^18.md: 8672256 B read + 1476600832 B written
-    ("march", "1aa9566e7f41f43ad8a12cb9fe2b7f7d0dd8a0ec3b9afdeb3ce43df20db1124b"): 1485273088,
+    # profiles/march_dram_bounded-2^18.md: 8005632 B read + 1477165056 B written
+    ("march", "f197aba666fa83658428a3edb6a129ea9e79be4b617ff6a4617ca940f5958b87"): 1485170688,
 }
 
 # What limits each stage (from the ncu captures summarised under profiles/).

@@ -266,31 +266,57 @@ __device__ __forceinline__ void finish_tile(const PruneArgs& a, const TileState&
         const uint32_t* row = mask_row(a, off, r);
         long long base = excl + __shfl_sync(FULL, my_excl, i);
         for (int c0 = 0; c0 < nch; c0 += 16) {
-            // 16 chunks' ballot word pairs at once
+            // 16 chunks' ballot word pairs at once; two chunks per step, both
+            // chunks' kept samples loaded (one 8-byte load per array per sample
+            // pair) before either is stored
             const unsigned mw = (c0 + (lane >> 1) < nch) ? row[2 * c0 + lane] : 0u;
             const int n = min(16, nch - c0);
-            for (int q = 0; q < n; ++q) {
-                const unsigned m0 = __shfl_sync(FULL, mw, 2 * q);
-                const unsigned m1 = __shfl_sync(FULL, mw, 2 * q + 1);
-                const long long j0 = abase + ((long long)(c0 + q) << 6) + 2 * lane;
-                const bool b0 = (m0 >> lane) & 1u, b1 = (m1 >> lane) & 1u;
-                if (a.keep_mask) {
-                    if (j0 >= off && j0 < end) a.keep_mask[j0] = (uint8_t)b0;
-                    if (j0 + 1 >= off && j0 + 1 < end) a.keep_mask[j0 + 1] = (uint8_t)b1;
+            for (int q = 0; q < n; q += 2) {
+                unsigned m[2][2];
+                long long j[2];
+                float2 ts[2], te[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const bool ex = q + h < n;
+                    m[h][0] = __shfl_sync(FULL, mw, (2 * (q + h)) & 31);
+                    m[h][1] = __shfl_sync(FULL, mw, (2 * (q + h) + 1) & 31);
+                    if (!ex) m[h][0] = m[h][1] = 0u;
+                    j[h] = abase + ((long long)(c0 + q + h) << 6) + 2 * lane;
+                    const bool k0 = (m[h][0] >> lane) & 1u, k1 = (m[h][1] >> lane) & 1u;
+                    ts[h] = te[h] = make_float2(0.0f, 0.0f);
+                    if (k0 || k1) {
+                        if (j[h] + 1 < a.n_samples) {
+                            ts[h] = __ldg(reinterpret_cast<const float2*>(a.t_starts + j[h]));
+                            te[h] = __ldg(reinterpret_cast<const float2*>(a.t_ends + j[h]));
+                        } else {  // the array's last sample, alone in its pair
+                            ts[h].x = __ldg(a.t_starts + j[h]);
+                            te[h].x = __ldg(a.t_ends + j[h]);
+                        }
+                    }
                 }
-                const long long pos0 = base + __popc(m0 & lt) + __popc(m1 & lt);
-                if (b0 && pos0 < a.capacity) {
-                    a.t_starts_out[pos0] = __ldg(a.t_starts + j0);
-                    a.t_ends_out[pos0] = __ldg(a.t_ends + j0);
-                    a.ray_indices_out[pos0] = r;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const unsigned m0 = m[h][0], m1 = m[h][1];
+                    const long long j0 = j[h];
+                    const bool b0 = (m0 >> lane) & 1u, b1 = (m1 >> lane) & 1u;
+                    if (a.keep_mask && q + h < n) {
+                        if (j0 >= off && j0 < end) a.keep_mask[j0] = (uint8_t)b0;
+                        if (j0 + 1 >= off && j0 + 1 < end) a.keep_mask[j0 + 1] = (uint8_t)b1;
+                    }
+                    const long long pos0 = base + __popc(m0 & lt) + __popc(m1 & lt);
+                    if (b0 && pos0 < a.capacity) {
+                        a.t_starts_out[pos0] = ts[h].x;
+                        a.t_ends_out[pos0] = te[h].x;
+                        a.ray_indices_out[pos0] = r;
+                    }
+                    const long long pos1 = pos0 + (b0 ? 1 : 0);
+                    if (b1 && pos1 < a.capacity) {
+                        a.t_starts_out[pos1] = ts[h].y;
+                        a.t_ends_out[pos1] = te[h].y;
+                        a.ray_indices_out[pos1] = r;
+                    }
+                    base += __popc(m0) + __popc(m1);
                 }
-                const long long pos1 = pos0 + (b0 ? 1 : 0);
-                if (b1 && pos1 < a.capacity) {
-                    a.t_starts_out[pos1] = __ldg(a.t_starts + j0 + 1);
-                    a.t_ends_out[pos1] = __ldg(a.t_ends + j0 + 1);
-                    a.ray_indices_out[pos1] = r;
-                }
-                base += __popc(m0) + __popc(m1);
             }
         }
         if (a.keep_mask) {
