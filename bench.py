@@ -180,8 +180,9 @@ def stage_bytes(R, M, M_read, S, grid_bytes, n_cells, n_grid, saved_od=False):
         "render_fwd": 8 * R + 24 * S + 20 * R + (4 * S if saved_od else 0),
         # read g_color (12R), packed_info (8R), (sigma, rgb, t_start, t_end) (24S); write dsigma, drgb (16S)
         "render_bwd": 12 * R + 8 * R + 24 * S + 16 * S + (4 * S if saved_od else 0),
-        # read + write the float32 grid (8/cell), write the bits (1/8 per cell), read cells + sigmas (8/sample)
-        "grid_update": 8 * n_cells + n_cells // 8 + 8 * n_grid,
+        # write the sampled cells + points (16/sample); read + write the float32 grid (8/cell), write
+        # the bits (1/8 per cell), read cells + sigmas (8/sample)
+        "grid_update": 16 * n_grid + 8 * n_cells + n_cells // 8 + 8 * n_grid,
     }
 
 
@@ -205,7 +206,7 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 
 
-def oracle_step_seconds(scene, aabb, bits, o, d, target, with_grid=True, n_cells=128 ** 3):
+def oracle_step_seconds(scene, aabb, bits, o, d, target, with_grid=True, res=(128, 128, 128)):
     """Time the oracle's stages on one sample of rays; the field (host numpy) is not timed."""
     import oracle
     from paper_2210_04847_gb300 import synth
@@ -227,7 +228,8 @@ def oracle_step_seconds(scene, aabb, bits, o, d, target, with_grid=True, n_cells
     t += time.perf_counter() - t0
     tg = 0.0
     if with_grid:
-        cells, _ = synth.grid_update_samples(0, 0, N_GRID_SAMPLES, n_cells)
+        n_cells = int(np.prod(res))
+        cells, _ = synth.grid_update_samples(0, 0, N_GRID_SAMPLES, res)
         sg = synth.rand_uniform(0, 77, N_GRID_SAMPLES).astype(np.float32) * 0.02
         ema = np.zeros(n_cells, np.float32)
         t0 = time.perf_counter()
@@ -358,6 +360,7 @@ def run_ours(args):
 
     stages = ["march", "prune", "render_fwd", "render_bwd", "grid_update"]
     ev = {s: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for s in stages}
+    ev_sample = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     stage_ms = {s: [] for s in stages}
     counts = []
     m_read = []
@@ -384,8 +387,13 @@ def run_ours(args):
         ev["render_bwd"][0].record()
         hp.render_bwd(S)
         ev["render_bwd"][1].record()
-        sc.grid_field(gi, hp.cell_sig)
-        hp.cells.copy_(gi["cells"])
+        # the update's random cells and points come from the library (device
+        # sampler, the same streams as the host generator behind grid_inputs, so
+        # gi describes the same points for the field's per-scene grouping)
+        ev_sample[0].record()
+        hp.sample_cells(rank, i % POOL)
+        ev_sample[1].record()
+        sc.grid_field(gi, hp.cell_sig, xyz=hp.cell_xyz, cells=hp.cells)
         ev["grid_update"][0].record()
         hp.grid_update(bits=upd_bits)
         ev["grid_update"][1].record()
@@ -396,6 +404,7 @@ def run_ours(args):
         if timed:
             for s in stages:
                 stage_ms[s].append(ev[s][0].elapsed_time(ev[s][1]))
+            stage_ms["grid_update"][-1] += ev_sample[0].elapsed_time(ev_sample[1])
             counts.append((M, S))
             m_read.append(int(hp.ws_prune[8:16].cpu().numpy().view(np.uint64)[0]))
 
@@ -611,7 +620,6 @@ def run_e2e(args, dev, sc):
     upd.ema.copy_(sc.ema_init())
     host = [(torch.from_numpy(b["host"].rays_o).pin_memory(), torch.from_numpy(b["host"].rays_d).pin_memory(),
              torch.from_numpy(b["host"].target_rgb).pin_memory()) for b in sc.batches]
-    grid_inputs = [sc.grid_inputs(s) for s in range(POOL)]
     out_host = torch.empty((R, 3), dtype=torch.float32).pin_memory()
     loss_host = torch.empty((), dtype=torch.float32).pin_memory()
     dt = synth.SQRT3 * 3.0 / 1024.0
@@ -645,8 +653,6 @@ def run_e2e(args, dev, sc):
 
     def one(i):
         ho, hd, ht = host[i % len(host)]
-        gi = grid_inputs[i % POOL]
-        cells, xyz = gi["cells"], gi["xyz"]
         field_ms.clear()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -660,6 +666,7 @@ def run_e2e(args, dev, sc):
         color, opacity, depth = api.rendering(timed_field(rgb_sigma_fn), packed, ts, te, ray_indices=ri)
         loss = torch.nn.functional.mse_loss(color, tgt)
         loss.backward()
+        cells, xyz = upd.sample_cells(N_GRID_SAMPLES, 0, i % POOL)
         timed_field(lambda: field.points(xyz, N_GRID_SAMPLES, sig_cells))()
         upd.update(cells, sig_cells, 0.95, 0.01)
         out_host.copy_(color.detach(), non_blocking=True)

@@ -279,6 +279,27 @@ int nacc_update_occupancy_grid(float* ema, uint32_t* bits, int64_t n_cells, cons
                                const float* sigmas, int64_t n_samples, float decay, float thre,
                                int32_t* d_status, void* stream);
 
+/*
+ * The update's random inputs (Instant-NGP's scheme that Sec. 2.1 follows):
+ * n uniform random cells of the whole grid (with replacement) and a uniform
+ * point inside each, at which the caller evaluates its field. Counter-based
+ * SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): draw i of stream k of seed s
+ * is mix(mix(s) + k * 0xD1B54A32D192ED03 + (i + 1) * 0x9E3779B97F4A7C15), mix
+ * the splitmix64 output function. Sample i: draws 2i, 2i+1 of stream `stream`
+ * give its cell coordinates by multiply-shift range reduction of their 32-bit
+ * halves, (h * extent) >> 32 (x, y: high, low half of the first draw; z and
+ * sl = slot * n_levels + level: high, low half of the second), cell =
+ * ((sl * res_x + x) * res_y + y) * res_z + z; draws 2i, 2i+1 of stream
+ * `stream` + 1 give its jitter (24-bit fields at bits 40 and 16 of the first
+ * and 40 of the second, times 2^-24); xyz_a = lo_a + (i_a + jitter_a) * cs_a in
+ * float32 (each operation rounded), with the level box formed as for marching
+ * (c = (lo + hi) / 2, h = (hi - lo) / 2, level l >= 1: c -+ h 2^l) and
+ * cs = (hi - lo) / res. Deterministic: the same arguments give the same bits.
+ * grid: the bits pointer is not read; cells (n,) int32 out; xyz (n,3) float32 out.
+ */
+int nacc_sample_grid_cells(uint64_t seed, uint64_t stream, int64_t n, const nacc_grid* grid,
+                           int32_t* cells, float* xyz, void* cuda_stream);
+
 /* ------------------------------------------------------------------------- */
 /* Launch-shape tuning (process-wide table, read at each launch)             */
 /* ------------------------------------------------------------------------- */

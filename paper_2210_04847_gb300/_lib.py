@@ -36,7 +36,8 @@ EXPORTS = (
     "nacc_march_workspace_size", "nacc_march_rays", "nacc_march_rays_static", "nacc_prune_workspace_size",
     "nacc_prune_samples",
     "nacc_render_weights", "nacc_accumulate_along_rays", "nacc_render_fwd", "nacc_render_bwd",
-    "nacc_unpack_info", "nacc_update_occupancy_grid", "nacc_tune_set", "nacc_tune_get", "nacc_error_string",
+    "nacc_unpack_info", "nacc_update_occupancy_grid", "nacc_sample_grid_cells", "nacc_tune_set", "nacc_tune_get",
+    "nacc_error_string",
     "nacc_version",
 )
 
@@ -100,6 +101,7 @@ def load() -> ctypes.CDLL:
         "nacc_render_bwd": (ctypes.c_int, [P, i32, P, P, P, P, P, i64, P, P, P, P, P, P, P]),
         "nacc_unpack_info": (ctypes.c_int, [P, i32, i64, P, P, P]),
         "nacc_update_occupancy_grid": (ctypes.c_int, [P, P, i64, P, P, i64, f32, f32, P, P]),
+        "nacc_sample_grid_cells": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, i64, GP, P, P, P]),
         "nacc_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
         "nacc_tune_get": (ctypes.c_int, [ctypes.c_int]),
         "nacc_error_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -360,6 +362,16 @@ def update_occupancy_grid(ema, bits, cells, sigmas, decay, thre, d_status=None, 
     rc = load().nacc_update_occupancy_grid(_ptr(ema), _ptr(bits), n_cells, _ptr(cells), _ptr(sigmas), n,
                                            float(decay), float(thre), _ptr(d_status), _stream(stream))
     _rc(rc, "nacc_update_occupancy_grid")
+
+
+def sample_grid_cells(seed: int, stream: int, n: int, grid: Grid, cells, xyz, cuda_stream=None):
+    """n uniform random cells of the grid and a uniform point in each (SplitMix64
+    streams `stream` for the cells and `stream` + 1 for the points)."""
+    _check(cells, torch.int32, "cells", n)
+    _check(xyz, torch.float32, "xyz", 3 * n)
+    rc = load().nacc_sample_grid_cells(int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream) & 0xFFFFFFFFFFFFFFFF, int(n),
+                                       ctypes.byref(grid), _ptr(cells), _ptr(xyz), _stream(cuda_stream))
+    _rc(rc, "nacc_sample_grid_cells")
 
 
 def tune_set(knob, value: int):

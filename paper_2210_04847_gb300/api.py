@@ -55,6 +55,17 @@ class OccupancyGrid:
     def struct(self) -> _lib.Grid:
         return _lib.make_grid(self.bits, self.res, self.aabb, self.n_levels, self.n_slots)
 
+    def sample_cells(self, n: int, seed: int = 0, step: int = 0):
+        """n uniform random cells of the grid (all levels and slots) and a uniform
+        point inside each, for the update: returns (cells (n,) int32, xyz (n,3)
+        float32). Deterministic in (seed, step): streams 50000 + 4*step (cells)
+        and 50001 + 4*step (points) of the counter-based generator."""
+        dev = self.bits.device
+        cells = torch.empty(n, dtype=torch.int32, device=dev)
+        xyz = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        _lib.sample_grid_cells(seed, 50000 + 4 * step, n, self.struct(), cells, xyz)
+        return cells, xyz
+
     def update(self, cells: torch.Tensor, sigmas: torch.Tensor, decay: float = 0.95, thre: float = 0.01):
         """EMA update: ema = max(decay * ema, sigma at sampled cells); bits = ema > thre."""
         _lib.update_occupancy_grid(self.ema, self.bits, cells, sigmas, decay, thre, self.status)

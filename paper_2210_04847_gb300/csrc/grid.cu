@@ -6,6 +6,9 @@
 //   ema[c] <- max(ema[c], sigma_s)     (every sample s in cell c)
 //   bits  = ema > thre
 //
+// The update's inputs come from nacc_sample_grid_cells (uniform random cells, a
+// uniform point in each, from a counter-based generator) and the caller's field.
+//
 // Two launches, 8.125 bytes of HBM traffic per cell plus the samples:
 //   1. decay_pack: one pass over the float32 grid, decays in place and writes
 //      the bit words of the decayed values (__ballot_sync gives a word per 32
@@ -59,10 +62,117 @@ __global__ void __launch_bounds__(kThreads) scatter_max_kernel(float* ema, uint3
     }
 }
 
+// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014; the 64-bit output mix of Vigna's splitmix64):
+// draw i (from 0) of stream k of seed s is mix(key + (i + 1) * gamma) with
+// key = mix(s) + k * kStreamMul. Counter-based: any draw is computed directly.
+constexpr unsigned long long kGamma = 0x9E3779B97F4A7C15ull;
+constexpr unsigned long long kStreamMul = 0xD1B54A32D192ED03ull;
+
+__host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+
+struct SampleArgs {
+    unsigned long long key_cells, key_jitter;
+    long long n;
+    int res[3];
+    int n_levels, n_sl;             // levels, levels * slots
+    float lo[NACC_MAX_LEVELS][3];   // level boxes in float32, formed as the marcher forms them
+    float cs[NACC_MAX_LEVELS][3];   // cell size (hi - lo) / res of each level
+    int32_t* cells;
+    float* xyz;
+};
+
+// Sample i: draws 2i, 2i+1 of the cell stream give the cell's coordinates by
+// multiply-shift range reduction of their 32-bit halves, (h * extent) >> 32:
+// x, y from the first draw's high and low halves, z and the (slot, level)
+// index sl from the second's; draws 2i, 2i+1 of the jitter stream give three
+// 24-bit fields (bits 40.., 16.. of the first, 40.. of the second) times 2^-24.
+// point_a = lo_a + (i_a + jitter_a) * cs_a in float32, each operation rounded.
+__global__ void __launch_bounds__(kThreads) sample_cells_kernel(const SampleArgs a) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < a.n; s += stride) {
+        const unsigned long long c0 = mix64(a.key_cells + (unsigned long long)(2 * s + 1) * kGamma);
+        const unsigned long long c1 = mix64(a.key_cells + (unsigned long long)(2 * s + 2) * kGamma);
+        // (h * extent) >> 32 of a 32-bit half h: the high word of the 32 x 32-bit product
+        const unsigned ix = __umulhi((unsigned)(c0 >> 32), (unsigned)a.res[0]);
+        const unsigned iy = __umulhi((unsigned)c0, (unsigned)a.res[1]);
+        const unsigned iz = __umulhi((unsigned)(c1 >> 32), (unsigned)a.res[2]);
+        const unsigned sl = __umulhi((unsigned)c1, (unsigned)a.n_sl);
+        a.cells[s] = (int32_t)(((sl * (unsigned)a.res[0] + ix) * (unsigned)a.res[1] + iy) * (unsigned)a.res[2] + iz);
+        const int lvl = (int)(sl % (unsigned)a.n_levels);
+        const unsigned long long q0 = mix64(a.key_jitter + (unsigned long long)(2 * s + 1) * kGamma);
+        const unsigned long long q1 = mix64(a.key_jitter + (unsigned long long)(2 * s + 2) * kGamma);
+        const float j[3] = {__uint2float_rn((unsigned)(q0 >> 40)) * (1.0f / 16777216.0f),
+                            __uint2float_rn((unsigned)((q0 >> 16) & 0xFFFFFFull)) * (1.0f / 16777216.0f),
+                            __uint2float_rn((unsigned)(q1 >> 40)) * (1.0f / 16777216.0f)};
+        const unsigned idx[3] = {ix, iy, iz};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float lo = a.lo[0][k], cs = a.cs[0][k];
+            for (int l = 1; l < a.n_levels; ++l)
+                if (l == lvl) {
+                    lo = a.lo[l][k];
+                    cs = a.cs[l][k];
+                }
+            a.xyz[3 * s + k] = __fadd_rn(lo, __fmul_rn(__fadd_rn(__uint2float_rn(idx[k]), j[k]), cs));
+        }
+    }
+}
+
 }  // namespace
 }  // namespace nacc
 
 using namespace nacc;
+
+extern "C" int nacc_sample_grid_cells(uint64_t seed, uint64_t stream, int64_t n, const nacc_grid* grid,
+                                      int32_t* cells, float* xyz, void* cuda_stream) {
+    if (n < 0 || !grid) return NACC_ERR_INVALID_ARG;
+    if (grid->n_levels < 1 || grid->n_levels > NACC_MAX_LEVELS || grid->n_slots < 1) return NACC_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k)
+        if (grid->res[k] < 1 || !(grid->aabb[k] < grid->aabb[3 + k])) return NACC_ERR_INVALID_ARG;
+    const long long n_cells =
+        (long long)grid->res[0] * grid->res[1] * grid->res[2] * grid->n_levels * grid->n_slots;
+    if (n_cells >= (1LL << 31)) return NACC_ERR_INVALID_ARG;
+    if (n == 0) return NACC_OK;
+    if (!cells || !xyz) return NACC_ERR_INVALID_ARG;
+    SampleArgs a;
+    a.key_cells = mix64(seed) + stream * kStreamMul;
+    a.key_jitter = mix64(seed) + (stream + 1) * kStreamMul;
+    a.n = n;
+    a.n_levels = grid->n_levels;
+    a.n_sl = grid->n_levels * grid->n_slots;
+    for (int k = 0; k < 3; ++k) {
+        a.res[k] = grid->res[k];
+        // level l: the level-0 box scaled by 2^l about its centre, in float32
+        const float lo = grid->aabb[k], hi = grid->aabb[3 + k];
+        const float c = (lo + hi) * 0.5f, h = (hi - lo) * 0.5f;
+        for (int l = 0; l < NACC_MAX_LEVELS; ++l) {
+            float llo = lo, lhi = hi;
+            if (l > 0) {
+                const float hl = h * ldexpf(1.0f, l);
+                llo = c - hl;
+                lhi = c + hl;
+            }
+            a.lo[l][k] = llo;
+            a.cs[l][k] = (lhi - llo) / (float)grid->res[k];
+        }
+    }
+    a.cells = cells;
+    a.xyz = xyz;
+    const DeviceInfo dev = current_device();
+    long long blocks = (n + kThreads - 1) / kThreads;
+    const long long cap = (long long)dev.sm_count * 8;
+    if (blocks > cap) blocks = cap;
+    sample_cells_kernel<<<(int)blocks, kThreads, 0, (cudaStream_t)cuda_stream>>>(a);
+    return launch_status(cudaGetLastError());
+}
 
 extern "C" int nacc_update_occupancy_grid(float* ema, uint32_t* bits, int64_t n_cells, const int32_t* cells,
                                           const float* sigmas, int64_t n_samples, float decay, float thre,

@@ -88,6 +88,7 @@ class HotPath:
         self.od = None
         self.n_grid = int(n_grid_samples)
         self.cells = z(self.n_grid, i32)
+        self.cell_xyz = torch.zeros((max(self.n_grid, 1), 3), dtype=f32, device=device)
         self.cell_sig = z(self.n_grid)
 
     # -- stages ------------------------------------------------------------
@@ -118,6 +119,11 @@ class HotPath:
         od = self._od()[:S] if self.save_optical_depth else None
         _lib.render_bwd(self.pi_k, self.ts_k[:S], self.te_k[:S], self.sig_k[:S], self.rgb_k[:S], S, self.g_color,
                         None, None, self.d_sig[:S], self.d_rgb[:S], optical_depth=od, d_status=self.status)
+
+    def sample_cells(self, seed: int, step: int):
+        """Random cells of the grid and a point in each for the update (``cells``, ``cell_xyz``)."""
+        if self.n_grid:
+            _lib.sample_grid_cells(seed, 50000 + 4 * step, self.n_grid, self.grid, self.cells, self.cell_xyz)
 
     def grid_update(self, decay=0.95, thre=0.01, bits=None):
         """EMA update of ``self.ema``; writes ``bits`` (default: the bitfield marched by this path)."""

@@ -77,7 +77,7 @@ class Scenario:
     def grid_inputs(self, step):
         """Uniform random cells over every slot and level, a jittered point in each, its time."""
         w = self.w
-        cells, jit = synth.grid_update_samples(self.rank, step, self.n_grid, self.n_cells)
+        cells, jit = synth.grid_update_samples(self.rank, step, self.n_grid, w.res, w.n_levels, w.n_slots)
         xyz = synth.cell_positions(cells, jit, w.aabb, w.res, w.n_levels)
         per_slot = int(np.prod(w.res)) * w.n_levels
         slot = cells.astype(np.int64) // per_slot
@@ -87,10 +87,16 @@ class Scenario:
         return dict(cells=to_device(cells, self.device), xyz=to_device(xyz.astype(np.float32), self.device),
                     times=times, slot=slot)
 
-    def grid_field(self, gi, out):
-        """Density of each grid-update point under its slot's scene."""
+    def grid_field(self, gi, out, xyz=None, cells=None):
+        """Density of each grid-update point under its slot's scene. ``xyz`` /
+        ``cells``: the device sampler's output for the same step (equal to
+        gi's); with one scene the field reads those directly."""
         if len(self.fields) == 1:
-            self.fields[0].points(gi["xyz"], self.n_grid, out, times=gi["times"])
+            times = gi["times"]
+            if times is not None and cells is not None:  # the point's time is its bin centre
+                per_slot = int(np.prod(self.w.res)) * self.w.n_levels
+                times = (((cells.long() // per_slot).double() + 0.5) / self.w.n_slots).float()
+            self.fields[0].points(gi["xyz"] if xyz is None else xyz, self.n_grid, out, times=times)
             return
         order = np.argsort(gi["slot"], kind="stable")
         # evaluate scene by scene on gathered points, then scatter back

@@ -489,15 +489,51 @@ def dynamic_config(seed: int = 0, n_rays: int = 1 << 19, n_bins: int = 16, devic
     )
 
 
-def grid_update_samples(seed: int, step: int, n: int, n_cells: int):
-    """Uniform random cells (with replacement) and jitters in [0, 1)^3 for one grid update."""
-    cells = rand_int(seed, 50000 + 4 * step, n, n_cells).astype(np.int32)
-    jit = rand_uniform(seed, 50001 + 4 * step, 3 * n).reshape(n, 3)
-    return cells, jit
+def grid_update_samples(seed: int, step: int, n: int, res, n_levels: int = 1, n_slots: int = 1):
+    """Uniform random cells (with replacement) and float32 jitters in [0, 1)^3 for
+    one grid update. Sample i takes draws 2i, 2i+1 of stream 50000 + 4*step for
+    its cell: each 32-bit half h gives a coordinate (h * extent) >> 32 (x, y from
+    the high and low halves of the first draw, z and the (slot, level) index from
+    the second); and draws 2i, 2i+1 of stream 50001 + 4*step for its jitter: the
+    24-bit fields at bits 40, 16 of the first and 40 of the second, times 2^-24.
+    Flat cell = ((sl * rx + x) * ry + y) * rz + z, sl = slot * n_levels + level."""
+    rx, ry, rz = (int(v) for v in res)
+    m32 = np.uint64(0xFFFFFFFF)
+    r = rand_u64(seed, 50000 + 4 * step, 2 * n).reshape(n, 2)
+    with np.errstate(over="ignore"):
+        ix = ((r[:, 0] >> np.uint64(32)) * np.uint64(rx)) >> np.uint64(32)
+        iy = ((r[:, 0] & m32) * np.uint64(ry)) >> np.uint64(32)
+        iz = ((r[:, 1] >> np.uint64(32)) * np.uint64(rz)) >> np.uint64(32)
+        sl = ((r[:, 1] & m32) * np.uint64(n_levels * n_slots)) >> np.uint64(32)
+    cells = (((sl.astype(np.int64) * rx + ix.astype(np.int64)) * ry + iy.astype(np.int64)) * rz
+             + iz.astype(np.int64)).astype(np.int32)
+    q = rand_u64(seed, 50001 + 4 * step, 2 * n).reshape(n, 2)
+    m24 = np.uint64(0xFFFFFF)
+    jit = np.stack([q[:, 0] >> np.uint64(40), (q[:, 0] >> np.uint64(16)) & m24, q[:, 1] >> np.uint64(40)], axis=1)
+    return cells, jit.astype(np.float32) * np.float32(2.0 ** -24)
+
+
+def level_boxes_f32(aabb: Sequence[float], n_levels: int):
+    """float32 boxes of a cascade, formed as the marcher forms them: c = (lo + hi) / 2,
+    h = (hi - lo) / 2, level l >= 1 = c -+ h * 2^l (each operation rounded to float32)."""
+    lo = np.asarray(aabb[:3], dtype=np.float32)
+    hi = np.asarray(aabb[3:], dtype=np.float32)
+    c = (lo + hi) * np.float32(0.5)
+    h = (hi - lo) * np.float32(0.5)
+    out = []
+    for lvl in range(n_levels):
+        if lvl == 0:
+            out.append((lo.copy(), hi.copy()))
+        else:
+            hl = h * np.float32(2.0**lvl)
+            out.append((c - hl, c + hl))
+    return out
 
 
 def cell_positions(cells: np.ndarray, jitter: np.ndarray, aabb, res, n_levels=1) -> np.ndarray:
-    """float64 world positions lo + (cell + jitter) * cell_size of flat cell indices."""
+    """float32 points lo + (cell index + jitter) * cell size inside flat cells, every
+    operation rounded to float32 (cell size = (hi - lo) / res of the cell's level;
+    level = (cell / res^3) mod n_levels)."""
     rx, ry, rz = res
     per_level = rx * ry * rz
     cells = np.asarray(cells, dtype=np.int64)
@@ -505,11 +541,11 @@ def cell_positions(cells: np.ndarray, jitter: np.ndarray, aabb, res, n_levels=1)
     lvl = (cells // per_level) % n_levels
     ix, rem = local // (ry * rz), local % (ry * rz)
     iy, iz = rem // rz, rem % rz
-    idx = np.stack([ix, iy, iz], axis=1).astype(np.float64)
-    boxes = level_boxes(aabb, n_levels)
+    idx = np.stack([ix, iy, iz], axis=1).astype(np.float32)
+    boxes = level_boxes_f32(aabb, n_levels)
     lo = np.stack([boxes[l][0] for l in range(n_levels)])[lvl]
-    hi = np.stack([boxes[l][1] for l in range(n_levels)])[lvl]
-    return lo + (idx + jitter) * (hi - lo) / np.array([rx, ry, rz], dtype=np.float64)
+    size = np.stack([(boxes[l][1] - boxes[l][0]) / np.asarray(res, dtype=np.float32) for l in range(n_levels)])[lvl]
+    return lo + (idx + np.asarray(jitter, dtype=np.float32)) * size
 
 
 def sample_field(scene: BlobScene, rays_o, rays_d, t_starts, t_ends, ray_indices, ray_time=None):

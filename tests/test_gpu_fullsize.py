@@ -153,7 +153,7 @@ def test_fullsize_grid_update_bitexact(orc):
     n_cells = 128 ** 3
     scene, aabb, _ = synth.bounded_scene(0, device="cuda")
     ema = synth.density_at_cell_centres(scene, aabb, (128, 128, 128), device="cuda").float().cpu().numpy()
-    cells, jit = synth.grid_update_samples(0, 0, 1 << 21, n_cells)
+    cells, jit = synth.grid_update_samples(0, 0, 1 << 21, (128, 128, 128))
     xyz = synth.cell_positions(cells, jit, aabb, (128, 128, 128))
     sig = scene.density(xyz).astype(np.float32)
     e_t = torch.from_numpy(ema.copy()).cuda()
