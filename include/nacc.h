@@ -125,7 +125,9 @@ size_t nacc_march_workspace_size(int32_t n_rays, const nacc_march_params* params
  * n_samples        device int64 out: the total number of samples (also when it
  *                  exceeds capacity; then NACC_STATUS_CAPACITY is raised).
  * workspace        nacc_march_workspace_size() bytes, 256-byte aligned; the
- *                  call clears what it needs on `stream`.
+ *                  call clears what it needs on `stream`. After the call, the
+ *                  uint64 at byte offset 8 holds the number of lattice points
+ *                  the call examined (summed over rays; a diagnostic).
  * Errors: NACC_ERR_INVALID_ARG for null required pointers, n_rays < 0,
  * capacity < 0, n_levels or max_steps out of range, res <= 0, a workspace too
  * small; NACC_ERR_CUDA if a launch fails.

@@ -67,6 +67,7 @@ struct MarchArgs {
     int32_t* d_status;
     unsigned long long* tile_status;
     unsigned int* ticket;
+    unsigned long long* lattice_points;  // diagnostic: lattice points examined, summed over rays
     int32_t n_tiles;
     int32_t mask_words;       // ballot words a ray's row can hold
     int32_t row_stride;       // words between consecutive rows in shared memory (= mask_words)
@@ -213,7 +214,7 @@ __device__ __forceinline__ void cone_extend(const MarchArgs& a, float* buf, floa
 template <int MAXL, bool CONE, bool UNROLL2, bool COARSE = false>
 __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3], const float d[3], float near,
                                              float far, unsigned sl0, uint32_t* row, float* lat, int lane,
-                                             int& count_out, int& nch_out) {
+                                             int& count_out, int& nch_out, int& pts_out) {
     const float dt = a.dt_min;
     const bool shared = !CONE || near == a.near_plane;
     // shared lattices know their length; an own cone lattice ends when t_k >= far
@@ -225,6 +226,7 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
     }
     const int max_ch = min((nk + 31) >> 5, a.mask_words);
     int count = 0, nch = 0;
+    pts_out = shared ? nk : 0;  // own cone lattices are counted as they are walked
     if (COARSE && shared) {
         // Every cell index along each axis, at each level, is a monotone function
         // of k (t_k, the midpoints and the rounded index arithmetic all are), and so
@@ -405,7 +407,9 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
                 tn = lat[lane + 1];
             }
             const bool valid = k < nk && ts < far;
-            if (CONE && !shared && __ballot_sync(FULL, valid) == 0u) break;
+            const unsigned vmask = __ballot_sync(FULL, valid);
+            if (CONE && !shared && vmask == 0u) break;
+            if (!shared) pts_out += __popc(vmask);
             bool occ = false;
             if (valid) {
                 const float te = tn < far ? tn : far;
@@ -548,6 +552,7 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
             cur.nr = min(a.tile_rays, a.n_rays - cur.ray0);
             int my_count = 0, my_nch = 0;
             float my_near = 0.0f, my_far = 0.0f;
+            long long tile_pts = 0;
             for (int i = 0; i < cur.nr; ++i) {
                 const int r = cur.ray0 + i;
                 float o[3], d[3];
@@ -557,14 +562,15 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
                     d[k] = __ldg(a.rays_d + 3 * (size_t)r + k);
                 }
                 float near = 0.0f, far = 0.0f;
-                int count = 0, nch = 0;
+                int count = 0, nch = 0, pts = 0;
                 const int slot = slot_of(a, r);
                 const bool slot_ok = slot >= 0 && slot < a.n_slots;
                 if (!slot_ok && lane == 0) raise_status(a.d_status, NACC_STATUS_BAD_INDEX);
                 if (slot_ok && clip_ray(a, o, d, near, far))
                     walk_lattice<MAXL, CONE, UNROLL2, COARSE>(a, o, d, near, far,
                                                               (unsigned)slot * (unsigned)a.n_levels,
-                                                              wmask + i * a.row_stride, lat, lane, count, nch);
+                                                              wmask + i * a.row_stride, lat, lane, count, nch, pts);
+                tile_pts += pts;
                 if (lane == i) {
                     my_count = count;
                     my_nch = nch;
@@ -573,6 +579,7 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
                 }
             }
             __syncwarp();
+            if (lane == 0 && tile_pts > 0) atomicAdd(a.lattice_points, (unsigned long long)tile_pts);
             cur.my_count = my_count;
             cur.my_nch = my_nch;
             cur.my_near = my_near;
@@ -779,6 +786,7 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
     a.n_samples = n_samples;
     a.d_status = d_status;
     a.ticket = (unsigned int*)workspace;
+    a.lattice_points = (unsigned long long*)((char*)workspace + 8);
     a.tile_status = (unsigned long long*)((char*)workspace + kTicketBytes);
     a.mask_words = mask_words_for(p);
     const bool cone = p->cone > 0.0f;

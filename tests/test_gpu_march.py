@@ -116,3 +116,36 @@ def test_cone_mixed_starts_bitexact(orc):
     g = gpu_march(w)
     assert g[4] > 100000
     assert_march_equal(g, oracle_march(orc, w))
+
+
+@pytest.mark.parametrize("cfg", ["bounded", "cone"])
+def test_lattice_point_counter(orc, cfg):
+    """The workspace's lattice-point counter equals the samples the oracle emits on
+    the same rays over an all-ones grid (where every lattice point is a sample)."""
+    if cfg == "bounded":
+        w = synth.bounded_config(3, n_rays=3000, device="cuda")
+    else:
+        w = synth.unbounded_config(3, n_rays=1500, device="cuda")
+        inside = w.rays_o.copy()
+        inside[:500] = inside[:500] * 20.0  # some rays start outside the outermost box (own lattices)
+        w.rays_o = np.ascontiguousarray(inside)
+    o, d = torch.from_numpy(w.rays_o).cuda(), torch.from_numpy(w.rays_d).cuda()
+    params = _lib.make_params(w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone, w.max_steps)
+    R = w.n_rays
+    ws = torch.zeros(_lib.march_workspace_size(R, params), dtype=torch.uint8, device="cuda")
+    cap = 8_000_000
+    pi = torch.zeros((R, 2), dtype=torch.int32, device="cuda")
+    ts, te = torch.zeros(cap, device="cuda"), torch.zeros(cap, device="cuda")
+    ri = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    n = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    bits = torch.from_numpy(w.bits.view(np.int32)).cuda()
+    _lib.march_rays(o, d, _lib.make_grid(bits, w.res, w.aabb, w.n_levels, w.n_slots), params, pi, ts, te, ri, n, st,
+                    ws)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    counted = int(ws[8:16].cpu().numpy().view(np.uint64)[0])
+    ones = np.full_like(w.bits, 0xFFFFFFFF)
+    full = orc.march(w.rays_o, w.rays_d, ones, w.res, w.aabb, w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone,
+                     w.max_steps, n_levels=w.n_levels, n_slots=w.n_slots)
+    assert counted == full.n_samples > 0
