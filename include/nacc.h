@@ -226,6 +226,31 @@ int nacc_accumulate_along_rays(const int32_t* packed_info, int32_t n_rays, const
                                float* out, int32_t* d_status, void* stream);
 
 /*
+ * Gradient of nacc_render_weights for any upstream gradient g_i = dL/dw_i
+ * (Sec. 2.2: gradients reach the field through the weights of any attribute):
+ *   dL/dsigma_k = delta_k (g_k T_{k+1} - sum_{i>k} g_i w_i),
+ * by the same reverse segmented scan and centred form as nacc_render_bwd
+ * (with a_i = g_i); T recomputed from sigmas.
+ * g_weights (n_samples,) float32 in; d_sigmas (n_samples,) float32 out; the
+ * float arrays and packed_info 8-byte aligned.
+ */
+int nacc_render_weights_bwd(const int32_t* packed_info, int32_t n_rays, const float* t_starts,
+                            const float* t_ends, const float* sigmas, int64_t n_samples,
+                            const float* g_weights, float* d_sigmas, int32_t* d_status, void* stream);
+
+/*
+ * Gradient of nacc_accumulate_along_rays for g = dL/dout (n_rays, n_channels):
+ *   dL/dw_i = sum_c g[r, c] v_i[c] (v = 1 when values is NULL),
+ *   dL/dv_i[c] = w_i g[r, c]   (sample i in ray r).
+ * d_weights (n_samples,) and d_values (n_samples, n_channels) float32 out,
+ * each nullable (d_values needs values).
+ */
+int nacc_accumulate_along_rays_bwd(const int32_t* packed_info, int32_t n_rays, const float* weights,
+                                   const float* values, int32_t n_channels, int64_t n_samples,
+                                   const float* g_out, float* d_weights, float* d_values,
+                                   int32_t* d_status, void* stream);
+
+/*
  * Fused forward rendering, Eq. 1 (render_weights + accumulate_along_rays):
  *   color[r] = sum w_i rgb_i (n_rays,3); opacity[r] = sum w_i (n_rays,);
  *   depth[r] = sum w_i (t_s + t_e)/2 (n_rays,), unnormalised, black background.

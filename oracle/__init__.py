@@ -58,9 +58,12 @@ def lib():
         L.oracle_accumulate.argtypes = [P, i32, P, P, i32, P]
         L.oracle_render_fwd.argtypes = [P, i32, P, P, P, P, P, P, P]
         L.oracle_render_bwd.argtypes = [P, i32, P, P, P, P, P, P, P, P, P]
+        L.oracle_render_weights_bwd.argtypes = [P, i32, P, P, P, P, P]
+        L.oracle_accumulate_bwd.argtypes = [P, i32, P, P, i32, P, P, P]
         L.oracle_unpack_info.argtypes = [P, i32, P]
         L.oracle_update_grid.argtypes = [P, P, i64, P, P, i64, f32, f32]
         for f in ("oracle_render_weights", "oracle_accumulate", "oracle_render_fwd", "oracle_render_bwd",
+                  "oracle_render_weights_bwd", "oracle_accumulate_bwd",
                   "oracle_unpack_info", "oracle_update_grid"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -183,6 +186,30 @@ def render_bwd(packed_info, t_starts, t_ends, sigmas, rgbs, g_color=None, g_opac
     if lib().oracle_render_bwd(_p(pi), R, _p(ts), _p(te), _p(sg), _p(rgb), _p(gc), _p(ga), _p(gd), _p(ds), _p(dr)) != 0:
         raise MemoryError
     return ds, dr
+
+
+def render_weights_bwd(packed_info, t_starts, t_ends, sigmas, g_weights):
+    """dL/dsigma for an upstream dL/dw (float64): delta_k (g_k T_{k+1} - sum_{i>k} g_i w_i)."""
+    pi = _c(packed_info, np.int32).reshape(-1, 2)
+    ts, te, sg = (_c(a, np.float32).reshape(-1) for a in (t_starts, t_ends, sigmas))
+    g = _c(g_weights, np.float64).reshape(-1)
+    ds = np.zeros(ts.shape[0])
+    if lib().oracle_render_weights_bwd(_p(pi), pi.shape[0], _p(ts), _p(te), _p(sg), _p(g), _p(ds)) != 0:
+        raise MemoryError
+    return ds
+
+
+def accumulate_bwd(packed_info, weights, values, g_out):
+    """(dL/dw (M,), dL/dv (M, C) or None) of out[r] = sum_i w_i v_i for dL/dout (R, C), float64."""
+    pi = _c(packed_info, np.int32).reshape(-1, 2)
+    w = _c(weights, np.float64).reshape(-1)
+    g = _c(g_out, np.float64).reshape(pi.shape[0], -1)
+    C = g.shape[1]
+    v = None if values is None else _c(values, np.float32).reshape(w.shape[0], C)
+    dw = np.zeros(w.shape[0])
+    dv = None if v is None else np.zeros((w.shape[0], C))
+    lib().oracle_accumulate_bwd(_p(pi), pi.shape[0], _p(w), _p(v), C, _p(g), _p(dw), _p(dv))
+    return dw, dv
 
 
 def unpack_info(packed_info, n_samples):

@@ -384,6 +384,55 @@ int oracle_render_bwd(const int32_t* packed_info, int32_t n_rays, const float* t
     return 0;
 }
 
+/* Gradient of the weights alone for an upstream g_i = dL/dw_i: with
+ * w_i = T_i alpha_i, dw_i/dtau_k = -w_i (k < i), T_{i+1} (k = i), 0 (k > i), so
+ * dL/dtau_k = g_k T_{k+1} - sum_{i>k} g_i w_i and dL/dsigma_k = delta_k dL/dtau_k
+ * (the R5 derivation with a_i = g_i). */
+int oracle_render_weights_bwd(const int32_t* packed_info, int32_t n_rays, const float* t_starts,
+                              const float* t_ends, const float* sigmas, const double* g_weights,
+                              double* d_sigmas) {
+    int64_t m = or_max_count(packed_info, n_rays);
+    double* w = (double*)malloc(sizeof(double) * m);
+    double* T = (double*)malloc(sizeof(double) * m);
+    double* Tn = (double*)malloc(sizeof(double) * m);
+    if (!w || !T || !Tn) { free(w); free(T); free(Tn); return -1; }
+    for (int32_t r = 0; r < n_rays; ++r) {
+        int64_t off = packed_info[2 * (int64_t)r], cnt = packed_info[2 * (int64_t)r + 1];
+        or_ray_weights(off, cnt, t_starts, t_ends, sigmas, w, T, Tn);
+        double suffix = 0.0;
+        for (int64_t k = cnt - 1; k >= 0; --k) {
+            double gk = g_weights[off + k];
+            double delta = (double)t_ends[off + k] - (double)t_starts[off + k];
+            d_sigmas[off + k] = delta * (gk * Tn[k] - suffix);
+            suffix += gk * w[k];
+        }
+    }
+    free(w);
+    free(T);
+    free(Tn);
+    return 0;
+}
+
+/* Gradient of the accumulation out[r, c] = sum_i w_i v_i[c]:
+ * dL/dw_i = sum_c g[r, c] v_i[c] (v = 1 without values), dL/dv_i[c] = w_i g[r, c]. */
+int oracle_accumulate_bwd(const int32_t* packed_info, int32_t n_rays, const double* weights,
+                          const float* values, int32_t n_channels, const double* g_out, double* d_weights,
+                          double* d_values) {
+    for (int32_t r = 0; r < n_rays; ++r) {
+        int64_t off = packed_info[2 * (int64_t)r], cnt = packed_info[2 * (int64_t)r + 1];
+        for (int64_t i = off; i < off + cnt; ++i) {
+            double dw = 0.0;
+            for (int32_t c = 0; c < n_channels; ++c) {
+                double g = g_out[(int64_t)r * n_channels + c];
+                dw += values ? g * (double)values[i * n_channels + c] : g;
+                if (d_values) d_values[i * n_channels + c] = weights[i] * g;
+            }
+            d_weights[i] = dw;
+        }
+    }
+    return 0;
+}
+
 /* Ray index of every packed sample (the inverse of packed_info). */
 int oracle_unpack_info(const int32_t* packed_info, int32_t n_rays, int32_t* ray_indices) {
     for (int32_t r = 0; r < n_rays; ++r) {

@@ -35,7 +35,8 @@ MAX_LEVELS = 16
 EXPORTS = (
     "nacc_march_workspace_size", "nacc_march_rays", "nacc_march_rays_static", "nacc_prune_workspace_size",
     "nacc_prune_samples",
-    "nacc_render_weights", "nacc_accumulate_along_rays", "nacc_render_fwd", "nacc_render_bwd",
+    "nacc_render_weights", "nacc_accumulate_along_rays", "nacc_render_weights_bwd",
+    "nacc_accumulate_along_rays_bwd", "nacc_render_fwd", "nacc_render_bwd",
     "nacc_unpack_info", "nacc_update_occupancy_grid", "nacc_sample_grid_cells", "nacc_tune_set", "nacc_tune_get",
     "nacc_error_string",
     "nacc_version",
@@ -97,6 +98,8 @@ def load() -> ctypes.CDLL:
         "nacc_prune_samples": (ctypes.c_int, [P, i32, P, P, P, i64, f32, f32, P, P, P, P, i64, P, P, P, P, sz, P]),
         "nacc_render_weights": (ctypes.c_int, [P, i32, P, P, P, i64, P, P, P, P]),
         "nacc_accumulate_along_rays": (ctypes.c_int, [P, i32, P, P, i32, i64, P, P, P]),
+        "nacc_render_weights_bwd": (ctypes.c_int, [P, i32, P, P, P, i64, P, P, P, P]),
+        "nacc_accumulate_along_rays_bwd": (ctypes.c_int, [P, i32, P, P, i32, i64, P, P, P, P, P]),
         "nacc_render_fwd": (ctypes.c_int, [P, i32, P, P, P, P, i64, P, P, P, P, P, P]),
         "nacc_render_bwd": (ctypes.c_int, [P, i32, P, P, P, P, P, i64, P, P, P, P, P, P, P]),
         "nacc_unpack_info": (ctypes.c_int, [P, i32, i64, P, P, P]),
@@ -301,6 +304,36 @@ def accumulate_along_rays(packed_info, weights, values, n_channels: int, n_sampl
     rc = load().nacc_accumulate_along_rays(_ptr(packed_info), n, _ptr(weights), _ptr(values), int(n_channels),
                                            int(n_samples), _ptr(out), _ptr(d_status), _stream(stream))
     _rc(rc, "nacc_accumulate_along_rays")
+
+
+def render_weights_bwd(packed_info, t_starts, t_ends, sigmas, n_samples: int, g_weights, d_sigmas, d_status=None,
+                       stream=None):
+    n = packed_info.shape[0]
+    _check(packed_info, torch.int32, "packed_info", 2 * n)
+    for t, nm in ((t_starts, "t_starts"), (t_ends, "t_ends"), (sigmas, "sigmas"), (g_weights, "g_weights"),
+                  (d_sigmas, "d_sigmas")):
+        _check(t, torch.float32, nm, n_samples)
+    _check(d_status, torch.int32, "d_status", 1, optional=True)
+    rc = load().nacc_render_weights_bwd(_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas),
+                                        int(n_samples), _ptr(g_weights), _ptr(d_sigmas), _ptr(d_status),
+                                        _stream(stream))
+    _rc(rc, "nacc_render_weights_bwd")
+
+
+def accumulate_along_rays_bwd(packed_info, weights, values, n_channels: int, n_samples: int, g_out, d_weights=None,
+                              d_values=None, d_status=None, stream=None):
+    n = packed_info.shape[0]
+    _check(packed_info, torch.int32, "packed_info", 2 * n)
+    _check(weights, torch.float32, "weights", n_samples)
+    _check(values, torch.float32, "values", n_samples * n_channels, optional=True)
+    _check(g_out, torch.float32, "g_out", n * n_channels)
+    _check(d_weights, torch.float32, "d_weights", n_samples, optional=True)
+    _check(d_values, torch.float32, "d_values", n_samples * n_channels, optional=True)
+    _check(d_status, torch.int32, "d_status", 1, optional=True)
+    rc = load().nacc_accumulate_along_rays_bwd(_ptr(packed_info), n, _ptr(weights), _ptr(values), int(n_channels),
+                                               int(n_samples), _ptr(g_out), _ptr(d_weights), _ptr(d_values),
+                                               _ptr(d_status), _stream(stream))
+    _rc(rc, "nacc_accumulate_along_rays_bwd")
 
 
 def render_fwd(packed_info, t_starts, t_ends, sigmas, rgbs, n_samples: int, color, opacity, depth,

@@ -230,21 +230,72 @@ def rendering(rgb_sigma_fn: Callable, packed_info, t_starts, t_ends, ray_indices
     return render_packed(sigmas, rgbs, packed_info, t_starts, t_ends, save_optical_depth)
 
 
+class _WeightsFn(torch.autograd.Function):
+    """Eq. 1 weights; backward: any dL/dw to dL/dsigma (reverse segmented scan)."""
+
+    @staticmethod
+    def forward(ctx, sigmas, packed_info, t_starts, t_ends):
+        M = t_starts.numel()
+        dev = packed_info.device
+        sg = sigmas.detach().contiguous().view(-1).float()
+        w = torch.empty(M, dtype=torch.float32, device=dev)
+        T = torch.empty(M, dtype=torch.float32, device=dev)
+        _lib.render_weights(packed_info, t_starts, t_ends, sg, M, w, T)
+        ctx.save_for_backward(sg, packed_info, t_starts, t_ends)
+        ctx.sig_shape = sigmas.shape
+        ctx.mark_non_differentiable(T)
+        return w, T
+
+    @staticmethod
+    def backward(ctx, g_w, g_T):
+        sg, packed_info, t_starts, t_ends = ctx.saved_tensors
+        M = t_starts.numel()
+        d_sig = torch.empty(M, dtype=torch.float32, device=sg.device)
+        g = torch.zeros(M, dtype=torch.float32, device=sg.device) if g_w is None else g_w.contiguous().float()
+        _lib.render_weights_bwd(packed_info, t_starts, t_ends, sg, M, g, d_sig)
+        return d_sig.view(ctx.sig_shape), None, None, None
+
+
 def render_weights(packed_info, t_starts, t_ends, sigmas):
-    """Per-sample Eq. 1 weights and transmittance (no gradient). Returns (weights, trans)."""
-    M = t_starts.numel()
-    w = torch.empty(M, dtype=torch.float32, device=packed_info.device)
-    T = torch.empty(M, dtype=torch.float32, device=packed_info.device)
-    _lib.render_weights(packed_info.contiguous(), t_starts.contiguous().view(-1), t_ends.contiguous().view(-1),
-                        sigmas.contiguous().view(-1).float(), M, w, T)
-    return w, T
+    """Per-sample Eq. 1 weights and transmittance, differentiable w.r.t. sigmas
+    through the weights (Sec. 2.2). Returns (weights (M,), trans (M,))."""
+    return _WeightsFn.apply(sigmas, packed_info.contiguous(), t_starts.contiguous().view(-1),
+                            t_ends.contiguous().view(-1))
+
+
+class _AccumulateFn(torch.autograd.Function):
+    """sum_i w_i v_i per ray; backward: dL/dw_i = <g_r, v_i>, dL/dv_i = w_i g_r."""
+
+    @staticmethod
+    def forward(ctx, weights, values, packed_info):
+        M = weights.numel()
+        w = weights.detach().contiguous().view(-1).float()
+        v = None if values is None else values.detach().contiguous().view(M, -1).float()
+        C = 1 if v is None else v.shape[1]
+        out = torch.empty((packed_info.shape[0], C), dtype=torch.float32, device=w.device)
+        _lib.accumulate_along_rays(packed_info, w, v, C, M, out)
+        ctx.save_for_backward(w, *([] if v is None else [v]), packed_info)
+        ctx.has_values = v is not None
+        ctx.shapes = (weights.shape, None if values is None else values.shape)
+        return out
+
+    @staticmethod
+    def backward(ctx, g_out):
+        saved = ctx.saved_tensors
+        w, packed_info = saved[0], saved[-1]
+        v = saved[1] if ctx.has_values else None
+        M = w.numel()
+        C = 1 if v is None else v.shape[1]
+        dw = torch.empty(M, dtype=torch.float32, device=w.device) if ctx.needs_input_grad[0] else None
+        dv = (torch.empty((M, C), dtype=torch.float32, device=w.device)
+              if v is not None and ctx.needs_input_grad[1] else None)
+        if dw is not None or dv is not None:
+            _lib.accumulate_along_rays_bwd(packed_info, w, v, C, M, g_out.contiguous().float(), dw, dv)
+        return (None if dw is None else dw.view(ctx.shapes[0]),
+                None if dv is None else dv.view(ctx.shapes[1]), None)
 
 
 def accumulate_along_rays(weights, packed_info, values=None):
-    """sum_i w_i v_i per ray for any attribute (Sec. 2.2). values (M, C) or None (opacity)."""
-    M = weights.numel()
-    C = 1 if values is None else values.view(M, -1).shape[1]
-    out = torch.empty((packed_info.shape[0], C), dtype=torch.float32, device=weights.device)
-    v = None if values is None else values.contiguous().view(M, C).float()
-    _lib.accumulate_along_rays(packed_info.contiguous(), weights.contiguous().view(-1).float(), v, C, M, out)
-    return out
+    """sum_i w_i v_i per ray for any attribute (Sec. 2.2), differentiable w.r.t.
+    weights and values. values (M, C) or None (opacity). Returns (R, C)."""
+    return _AccumulateFn.apply(weights, values, packed_info.contiguous())

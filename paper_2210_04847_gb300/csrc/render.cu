@@ -182,6 +182,40 @@ __device__ __forceinline__ void load_pair(const float* __restrict__ ts, const fl
     }
 }
 
+// As load_pair, with the upstream weight gradients of the two samples in
+// rgb[0] and rgb[3] (weights mode of the backward).
+__device__ __forceinline__ void load_pair_w(const float* __restrict__ ts, const float* __restrict__ te,
+                                            const float* __restrict__ sig, const float* __restrict__ gw,
+                                            unsigned j0, unsigned lo, unsigned hi, Pair& q) {
+    q.v0 = j0 >= lo && j0 < hi;
+    q.v1 = j0 + 1 >= lo && j0 + 1 < hi;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) q.s0[k] = q.s1[k] = q.sg[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) q.rgb[k] = 0.0f;
+    if (q.v0 && q.v1) {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(ts + j0));
+        const float2 b = __ldg(reinterpret_cast<const float2*>(te + j0));
+        const float2 g = __ldg(reinterpret_cast<const float2*>(sig + j0));
+        const float2 w = __ldg(reinterpret_cast<const float2*>(gw + j0));
+        q.s0[0] = a.x; q.s0[1] = a.y;
+        q.s1[0] = b.x; q.s1[1] = b.y;
+        q.sg[0] = g.x; q.sg[1] = g.y;
+        q.rgb[0] = w.x; q.rgb[3] = w.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (k == 0 ? q.v0 : q.v1) {
+                const unsigned j = j0 + k;
+                q.s0[k] = __ldg(ts + j);
+                q.s1[k] = __ldg(te + j);
+                q.sg[k] = __ldg(sig + j);
+                q.rgb[3 * k] = __ldg(gw + j);
+            }
+        }
+    }
+}
+
 // Exclusive optical depth of both samples of each lane's pair, given the carry of
 // earlier chunks; updates the carry. The same explicitly rounded operations in
 // every kernel, so forward, backward and saved values agree bit for bit.
@@ -356,6 +390,41 @@ __global__ void __launch_bounds__(kThreads) accumulate_kernel(const AccArgs a) {
     }
 }
 
+struct AccBwdArgs {
+    const int32_t* packed_info;
+    int32_t n_rays;
+    const float* weights;
+    const float* values;
+    int32_t n_channels;
+    int64_t n_samples;
+    const float* g_out;
+    float* d_weights;
+    float* d_values;
+    int32_t* d_status;
+};
+
+// Gradient of accumulate_along_rays, warp per ray: dL/dw_i = sum_c g[r,c] v_i[c]
+// and dL/dv_i[c] = w_i g[r,c].
+__global__ void __launch_bounds__(kThreads) accumulate_bwd_kernel(const AccBwdArgs a) {
+    const int lane = threadIdx.x & 31;
+    for (int r = global_warp(); r < a.n_rays; r += n_global_warps()) {
+        int off, cnt;
+        load_run(a.packed_info, r, a.n_samples, a.d_status, lane, off, cnt);
+        const float* g = a.g_out + (size_t)r * a.n_channels;
+        for (int j = lane; j < cnt; j += 32) {
+            const size_t i = (size_t)off + j;
+            const float w = __ldg(a.weights + i);
+            float dw = 0.0f;
+            for (int c = 0; c < a.n_channels; ++c) {
+                const float gc = __ldg(g + c);
+                dw += a.values ? gc * __ldg(a.values + i * a.n_channels + c) : gc;
+                if (a.d_values) a.d_values[i * a.n_channels + c] = w * gc;
+            }
+            if (a.d_weights) a.d_weights[i] = dw;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // backward: reverse segmented scan
 // ---------------------------------------------------------------------------
@@ -375,6 +444,7 @@ struct BwdArgs {
     float* d_sigmas;
     float* d_rgbs;
     int32_t* d_status;
+    const float* g_weights;  // weights mode: dL/dw_i (no rgb, g_color, d_rgbs)
 };
 
 // tau of both samples of the lane's pair in chunk c of a ray (pass A of the backward).
@@ -396,7 +466,9 @@ __device__ __forceinline__ void pair_tau(const BwdArgs& a, unsigned abase, unsig
     }
 }
 
-template <int MINB, bool PREFETCH>
+// WEIGHTS: the gradient of nacc_render_weights (a_i = dL/dw_i read from
+// g_weights; only d_sigmas is written).
+template <int MINB, bool PREFETCH, bool WEIGHTS = false>
 __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const BwdArgs a) {
     __shared__ float s_carry[kRenderThreads / 32][kCarryCap];
     const int lane = threadIdx.x & 31;
@@ -415,11 +487,11 @@ __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const 
         const unsigned abase = lo & ~1u;
         const int r = ray0 + ri;
         const int nch = (int)((hi - abase + 63) >> 6);
-        const float gc0 = a.g_color ? a.g_color[3 * (size_t)r] : 0.0f;
-        const float gc1 = a.g_color ? a.g_color[3 * (size_t)r + 1] : 0.0f;
-        const float gc2 = a.g_color ? a.g_color[3 * (size_t)r + 2] : 0.0f;
-        const float ga = a.g_opacity ? a.g_opacity[r] : 0.0f;
-        const float gd = a.g_depth ? a.g_depth[r] : 0.0f;
+        const float gc0 = !WEIGHTS && a.g_color ? a.g_color[3 * (size_t)r] : 0.0f;
+        const float gc1 = !WEIGHTS && a.g_color ? a.g_color[3 * (size_t)r + 1] : 0.0f;
+        const float gc2 = !WEIGHTS && a.g_color ? a.g_color[3 * (size_t)r + 2] : 0.0f;
+        const float ga = !WEIGHTS && a.g_opacity ? a.g_opacity[r] : 0.0f;
+        const float gd = !WEIGHTS && a.g_depth ? a.g_depth[r] : 0.0f;
 
         // pass A (recompute mode): optical-depth carry at the start of each chunk,
         // the next chunk's loads in flight while the current one is scanned
@@ -447,14 +519,19 @@ __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const 
         // with PREFETCH the last chunk's loads (pass B starts there) go out
         // together with the reference sample's, so their latencies overlap
         Pair nx;
-        if (PREFETCH)
+        if (PREFETCH && !WEIGHTS)
             load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, abase + ((unsigned)(nch - 1) << 6) + 2 * lane, lo, hi,
                       nx);
-        const float r_ref = __ldg(a.rgbs + 3 * lo);
-        const float g_ref = __ldg(a.rgbs + 3 * lo + 1);
-        const float b_ref = __ldg(a.rgbs + 3 * lo + 2);
-        const float tm_ref = (__ldg(a.t_starts + lo) + __ldg(a.t_ends + lo)) * 0.5f;
-        const float a_ref = gc0 * r_ref + gc1 * g_ref + gc2 * b_ref + ga + gd * tm_ref;
+        float r_ref = 0.0f, g_ref = 0.0f, b_ref = 0.0f, tm_ref = 0.0f, a_ref;
+        if constexpr (WEIGHTS) {
+            a_ref = __ldg(a.g_weights + lo);
+        } else {
+            r_ref = __ldg(a.rgbs + 3 * lo);
+            g_ref = __ldg(a.rgbs + 3 * lo + 1);
+            b_ref = __ldg(a.rgbs + 3 * lo + 2);
+            tm_ref = (__ldg(a.t_starts + lo) + __ldg(a.t_ends + lo)) * 0.5f;
+            a_ref = gc0 * r_ref + gc1 * g_ref + gc2 * b_ref + ga + gd * tm_ref;
+        }
         const unsigned last = hi - 1 - abase;  // position of the ray's last sample in its chunks
         const int last_lane = (int)((last >> 1) & 31);
         const bool last_odd = (last & 1) != 0;
@@ -480,7 +557,9 @@ __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const 
             }
             const unsigned j0 = abase + ((unsigned)c << 6) + 2 * lane;
             Pair q;
-            if (PREFETCH) {
+            if constexpr (WEIGHTS) {
+                load_pair_w(a.t_starts, a.t_ends, a.sigmas, a.g_weights, j0, lo, hi, q);
+            } else if (PREFETCH) {
                 q = nx;
                 if (c > 0) load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0 - 64, lo, hi, nx);
             } else {
@@ -506,10 +585,16 @@ __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const 
             const float w0 = q.v0 ? T0 * alpha_of(tau0) : 0.0f;
             const float w1 = q.v1 ? T1 * alpha_of(tau1) : 0.0f;
             const float tm0 = (q.s0[0] + q.s1[0]) * 0.5f, tm1 = (q.s0[1] + q.s1[1]) * 0.5f;
-            const float b0 = gc0 * (q.rgb[0] - r_ref) + gc1 * (q.rgb[1] - g_ref) + gc2 * (q.rgb[2] - b_ref) +
-                             gd * (tm0 - tm_ref);
-            const float b1 = gc0 * (q.rgb[3] - r_ref) + gc1 * (q.rgb[4] - g_ref) + gc2 * (q.rgb[5] - b_ref) +
-                             gd * (tm1 - tm_ref);
+            float b0, b1;
+            if constexpr (WEIGHTS) {
+                b0 = q.rgb[0] - a_ref;
+                b1 = q.rgb[3] - a_ref;
+            } else {
+                b0 = gc0 * (q.rgb[0] - r_ref) + gc1 * (q.rgb[1] - g_ref) + gc2 * (q.rgb[2] - b_ref) +
+                     gd * (tm0 - tm_ref);
+                b1 = gc0 * (q.rgb[3] - r_ref) + gc1 * (q.rgb[4] - g_ref) + gc2 * (q.rgb[5] - b_ref) +
+                     gd * (tm1 - tm_ref);
+            }
             const float bw0 = q.v0 ? b0 * w0 : 0.0f;
             const float bw1 = q.v1 ? b1 * w1 : 0.0f;
             const float suf = warp_incl_suffix(bw0 + bw1, lane);
@@ -521,7 +606,15 @@ __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const 
             const float base_g = a_ref * t_end;
             const float ds0 = (q.s1[0] - q.s0[0]) * (base_g + (b0 * Tn0 - S0));
             const float ds1 = (q.s1[1] - q.s0[1]) * (base_g + (b1 * T2 - S1));
-            if (q.v0 && q.v1) {
+            if constexpr (WEIGHTS) {
+                if (q.v0 && q.v1) {
+                    *reinterpret_cast<float2*>(a.d_sigmas + j0) = make_float2(ds0, ds1);
+                } else if (q.v0) {
+                    a.d_sigmas[j0] = ds0;
+                } else if (q.v1) {
+                    a.d_sigmas[j0 + 1] = ds1;
+                }
+            } else if (q.v0 && q.v1) {
                 *reinterpret_cast<float2*>(a.d_sigmas + j0) = make_float2(ds0, ds1);
                 float2* dr = reinterpret_cast<float2*>(a.d_rgbs + 3 * j0);
                 dr[0] = make_float2(w0 * gc0, w0 * gc1);
@@ -640,6 +733,42 @@ extern "C" int nacc_accumulate_along_rays(const int32_t* packed_info, int32_t n_
     return launch_status(cudaGetLastError());
 }
 
+extern "C" int nacc_accumulate_along_rays_bwd(const int32_t* packed_info, int32_t n_rays, const float* weights,
+                                              const float* values, int32_t n_channels, int64_t n_samples,
+                                              const float* g_out, float* d_weights, float* d_values,
+                                              int32_t* d_status, void* stream) {
+    if (!sizes_ok(n_rays, n_samples) || n_channels < 1) return NACC_ERR_INVALID_ARG;
+    if (n_rays > 0 && (!packed_info || !g_out)) return NACC_ERR_INVALID_ARG;
+    if (n_samples > 0 && !weights) return NACC_ERR_INVALID_ARG;
+    if (d_values && !values) return NACC_ERR_INVALID_ARG;
+    if (n_rays == 0 || (!d_weights && !d_values)) return NACC_OK;
+    AccBwdArgs a{packed_info, n_rays, weights, values, n_channels, n_samples, g_out, d_weights, d_values, d_status};
+    accumulate_bwd_kernel<<<grid_for(accumulate_bwd_kernel, n_rays), kThreads, 0, (cudaStream_t)stream>>>(a);
+    return launch_status(cudaGetLastError());
+}
+
+extern "C" int nacc_render_weights_bwd(const int32_t* packed_info, int32_t n_rays, const float* t_starts,
+                                       const float* t_ends, const float* sigmas, int64_t n_samples,
+                                       const float* g_weights, float* d_sigmas, int32_t* d_status, void* stream) {
+    if (!sizes_ok(n_rays, n_samples)) return NACC_ERR_INVALID_ARG;
+    if (n_rays > 0 && !packed_info) return NACC_ERR_INVALID_ARG;
+    if (n_samples > 0 && (!t_starts || !t_ends || !sigmas || !g_weights || !d_sigmas)) return NACC_ERR_INVALID_ARG;
+    if (n_rays == 0) return NACC_OK;
+    if ((((uintptr_t)packed_info | (uintptr_t)t_starts | (uintptr_t)t_ends | (uintptr_t)sigmas |
+          (uintptr_t)g_weights | (uintptr_t)d_sigmas) & 7u) != 0)
+        return NACC_ERR_INVALID_ARG;
+    BwdArgs a{packed_info, n_rays, t_starts, t_ends, sigmas, nullptr, nullptr, n_samples,
+              nullptr, nullptr, nullptr, d_sigmas, nullptr, d_status, g_weights};
+    const int nb = group_blocks(n_rays);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (tune_get(NACC_TUNE_RENDER_BWD_OCCUPANCY)) {
+        case 1: render_bwd_kernel<16, false, true><<<nb, kRenderThreads, 0, st>>>(a); break;
+        case 2: render_bwd_kernel<12, false, true><<<nb, kRenderThreads, 0, st>>>(a); break;
+        default: render_bwd_kernel<1, false, true><<<nb, kRenderThreads, 0, st>>>(a); break;
+    }
+    return launch_status(cudaGetLastError());
+}
+
 extern "C" int nacc_render_bwd(const int32_t* packed_info, int32_t n_rays, const float* t_starts,
                                const float* t_ends, const float* sigmas, const float* rgbs,
                                const float* optical_depth, int64_t n_samples, const float* g_color,
@@ -654,7 +783,7 @@ extern "C" int nacc_render_bwd(const int32_t* packed_info, int32_t n_rays, const
           (uintptr_t)optical_depth | (uintptr_t)d_sigmas | (uintptr_t)d_rgbs) & 7u) != 0)
         return NACC_ERR_INVALID_ARG;
     BwdArgs a{packed_info, n_rays, t_starts, t_ends, sigmas, rgbs, optical_depth, n_samples,
-              g_color, g_opacity, g_depth, d_sigmas, d_rgbs, d_status};
+              g_color, g_opacity, g_depth, d_sigmas, d_rgbs, d_status, nullptr};
     const int nb = group_blocks(n_rays);
     cudaStream_t st = (cudaStream_t)stream;
     const bool pf = tune_get(NACC_TUNE_RENDER_BWD_PREFETCH) != 0;

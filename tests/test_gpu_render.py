@@ -218,6 +218,56 @@ def test_render_weights_and_accumulate(scene, orc):
     assert np.max(np.abs(out1.cpu().numpy() - ref1)) <= 1e-5
 
 
+def _gpu_weights_bwd(pi, ts, te, sg, g):
+    M = ts.shape[0]
+    ds = torch.full((max(M, 1),), float("nan"), device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _lib.render_weights_bwd(dev(pi), dev(ts), dev(te), dev(sg), M, dev(g), ds[:M], d_status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    return ds[:M].cpu().numpy()
+
+
+def test_render_weights_bwd_parity(scene, orc):
+    """dL/dsigma for a random dL/dw on the pruned bounded samples (ragged rays)."""
+    p, sg = scene["p"], scene["sig2"]
+    M = p.n_samples
+    g = synth.rand_uniform(5, 1, M, -1, 1).astype(np.float32)
+    ds = _gpu_weights_bwd(p.packed_info, p.t_starts, p.t_ends, sg, g)
+    ds_o = orc.render_weights_bwd(p.packed_info, p.t_starts, p.t_ends, sg, g.astype(np.float64))
+    assert grad_rel_err(ds, ds_o) <= 1e-4
+
+
+def test_render_weights_bwd_long_ray_and_empty(orc):
+    """One ray of 9000 samples (past the shared-memory carry record), an empty ray, a one-sample ray."""
+    n = 9000
+    ts = np.concatenate([1.0 + 0.001 * np.arange(n), [3.0]]).astype(np.float32)
+    te = np.concatenate([1.0 + 0.001 * np.arange(1, n + 1), [3.5]]).astype(np.float32)
+    sg = synth.rand_uniform(6, 1, n + 1, 0, 2).astype(np.float32)
+    g = synth.rand_uniform(6, 2, n + 1, -1, 1).astype(np.float32)
+    pi = np.array([[0, n], [n, 0], [n, 1]], np.int32)
+    ds = _gpu_weights_bwd(pi, ts, te, sg, g)
+    ds_o = orc.render_weights_bwd(pi, ts, te, sg, g.astype(np.float64))
+    assert grad_rel_err(ds, ds_o) <= 1e-4
+
+
+@pytest.mark.parametrize("C", [1, 3, 7])
+def test_accumulate_bwd_parity(scene, orc, C):
+    p, rgb = scene["p"], scene["rgb2"]
+    R, M = p.packed_info.shape[0], p.n_samples
+    w = synth.rand_uniform(C, 11, M, 0, 1).astype(np.float32)
+    vals = None if C == 1 else synth.rand_uniform(C, 12, M * C, -1, 1).reshape(M, C).astype(np.float32)
+    g = synth.rand_uniform(C, 13, R * C, -1, 1).reshape(R, C).astype(np.float32)
+    dw = torch.full((M,), float("nan"), device="cuda")
+    dv = None if vals is None else torch.full((M, C), float("nan"), device="cuda")
+    _lib.accumulate_along_rays_bwd(dev(p.packed_info), dev(w), dev(vals), C, M, dev(g), dw, dv)
+    torch.cuda.synchronize()
+    dw_o, dv_o = orc.accumulate_bwd(p.packed_info, w.astype(np.float64), vals, g.astype(np.float64))
+    assert np.max(np.abs(dw.cpu().numpy() - dw_o)) <= 1e-5 * max(1.0, np.abs(dw_o).max())
+    if vals is not None:
+        assert np.max(np.abs(dv.cpu().numpy() - dv_o)) <= 1e-6
+
+
 def test_unpack_info(scene, orc):
     p = scene["p"]
     ri = torch.full((p.n_samples,), -1, dtype=torch.int32, device="cuda")

@@ -35,6 +35,13 @@ MUTANTS = [
     ("prune alpha on sigma, not sigma*delta", "float tau = sigmas[i] * delta;", "float tau = sigmas[i];"),
     ("grid decay dropped", "ema[c] = (float)((double)decay * (double)ema[c]);", "ema[c] = ema[c];"),
     ("grid NaN not ignored", "if (v == v && v > ema[c]) ema[c] = v;", "if (!(v <= ema[c])) ema[c] = v;"),
+    ("weights gradient uses T_k for T_{k+1}", "d_sigmas[off + k] = delta * (gk * Tn[k] - suffix);",
+     "d_sigmas[off + k] = delta * (gk * T[k] - suffix);"),
+    ("weights gradient suffix without the weights", "suffix += gk * w[k];", "suffix += gk;"),
+    ("accumulate gradient of values without the weight", "d_values[i * n_channels + c] = weights[i] * g;",
+     "d_values[i * n_channels + c] = g;"),
+    ("accumulate gradient of weights ignores values", "dw += values ? g * (double)values[i * n_channels + c] : g;",
+     "dw += g;"),
 ]
 
 

@@ -166,6 +166,100 @@ def test_gradient_slab_closed_form(orc):
     assert np.all(dr == 0)
 
 
+def _ragged_dyadic(seed, n_rays=6):
+    """Rays of 1..16 samples (the first 16) with dyadic edges and densities, as above."""
+    counts = [1 + int(v) for v in synth.rand_int(seed, 1, n_rays, 16)]
+    counts[0] = 16
+    M = sum(counts)
+    pi = _packed(counts)
+    q = 2.0**-10
+    ts = np.zeros(M, np.float32)
+    te = np.zeros(M, np.float32)
+    for r, (off, cnt) in enumerate(pi):
+        d = (1 + synth.rand_int(seed, 10 + r, cnt, 64)) * q * 4
+        e = 1.0 + np.concatenate([[0], np.cumsum(d)])
+        ts[off : off + cnt], te[off : off + cnt] = e[:-1], e[1:]
+    sg = (synth.rand_int(seed, 2, M, 4096) * q).astype(np.float32)
+    return pi, ts, te, sg
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_weights_gradient_central_differences(orc, seed):
+    """dL/dsigma of L = sum_i g_i w_i against central differences of the float64 weights."""
+    pi, ts, te, sg = _ragged_dyadic(seed)
+    M = sg.shape[0]
+    g = synth.rand_uniform(seed, 7, M, -1, 1)
+    ds = orc.render_weights_bwd(pi, ts, te, sg, g)
+    h = 2.0**-12
+    fd = np.zeros(M)
+    for i in range(M):
+        sp, sm = sg.copy(), sg.copy()
+        sp[i] += np.float32(h)
+        sm[i] -= np.float32(h)
+        fd[i] = (float((orc.render_weights(pi, ts, te, sp)[0] * g).sum())
+                 - float((orc.render_weights(pi, ts, te, sm)[0] * g).sum())) / (2 * h)
+    assert np.max(np.abs(ds - fd)) / max(np.abs(fd).max(), 1e-12) < 1e-6
+
+
+def test_weights_gradient_single_sample_closed_form(orc):
+    """One sample: w = 1 - exp(-sigma delta), so dL/dsigma = g delta exp(-sigma delta)."""
+    ts = np.array([0.5, 1.0, 2.0], np.float32)
+    te = np.array([0.75, 1.5, 2.125], np.float32)
+    sg = np.array([0.0, 2.0, 40.0], np.float32)
+    g = np.array([1.5, -0.25, 3.0])
+    ds = orc.render_weights_bwd(_packed([1, 1, 1]), ts, te, sg, g)
+    delta = te.astype(np.float64) - ts
+    np.testing.assert_allclose(ds, g * delta * np.exp(-sg.astype(np.float64) * delta), rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("C", [1, 3, 7])
+def test_accumulate_gradient_central_differences(orc, C):
+    """dL/dw and dL/dv of L = sum g * accumulate(w, v): central differences of the forward (linear)."""
+    pi, ts, te, sg = _ragged_dyadic(11 + C)
+    M = sg.shape[0]
+    w = synth.rand_uniform(C, 1, M, 0, 1)
+    v = (synth.rand_int(C, 2, M * C, 1024) * 2.0**-10).astype(np.float32).reshape(M, C)
+    g = synth.rand_uniform(C, 3, pi.shape[0] * C, -1, 1).reshape(-1, C)
+    dw, dv = orc.accumulate_bwd(pi, w, v, g)
+    h = 2.0**-10  # L is linear in w: a large step has no truncation error and little rounding
+    for i in range(0, M, 2):
+        wp, wm = w.copy(), w.copy()
+        wp[i] += h
+        wm[i] -= h
+        fd = (float((orc.accumulate(pi, wp, v) * g).sum()) - float((orc.accumulate(pi, wm, v) * g).sum())) / (2 * h)
+        assert abs(dw[i] - fd) < 1e-9
+        for c in range(C):
+            vp, vm = v.copy(), v.copy()
+            vp[i, c] += np.float32(2.0**-12)
+            vm[i, c] -= np.float32(2.0**-12)
+            fd = (float((orc.accumulate(pi, w, vp) * g).sum())
+                  - float((orc.accumulate(pi, w, vm) * g).sum())) / (2 * 2.0**-12)
+            assert abs(dv[i, c] - fd) < 1e-9
+    dw1, dv1 = orc.accumulate_bwd(pi, w, None, g[:, :1])
+    assert dv1 is None
+    np.testing.assert_allclose(dw1, np.repeat(g[:, 0], pi[:, 1]), rtol=0, atol=0)
+
+
+def test_render_gradient_is_the_composition(orc):
+    """render = accumulate(render_weights): the fused gradient equals weights_bwd of
+    accumulate_bwd's dL/dw, and its d rgb equals accumulate_bwd's d values."""
+    pi, ts, te, sg = _ragged_dyadic(21)
+    M, R = sg.shape[0], pi.shape[0]
+    rgb = (synth.rand_int(21, 3, 3 * M, 1024) * 2.0**-10).reshape(M, 3).astype(np.float32)
+    gc = synth.rand_uniform(21, 4, 3 * R, -1, 1).reshape(R, 3)
+    ga = synth.rand_uniform(21, 5, R, -1, 1)
+    gd = synth.rand_uniform(21, 6, R, -1, 1)
+    ds, dr = orc.render_bwd(pi, ts, te, sg, rgb, gc, ga, gd)
+    w, _ = orc.render_weights(pi, ts, te, sg)
+    tm = ((ts.astype(np.float64) + te) * 0.5).astype(np.float32)
+    vals = np.concatenate([rgb, np.ones((M, 1), np.float32), tm[:, None]], axis=1)
+    g = np.concatenate([gc, ga[:, None], gd[:, None]], axis=1)
+    dw, dv = orc.accumulate_bwd(pi, w, vals, g)
+    ds2 = orc.render_weights_bwd(pi, ts, te, sg, dw)
+    np.testing.assert_allclose(ds2, ds, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(dv[:, :3], dr, rtol=1e-12, atol=0)
+
+
 # ---------------------------------------------------------------------------
 # pruning
 # ---------------------------------------------------------------------------
