@@ -67,7 +67,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rays", type=int, default=N_RAYS)
-    ap.add_argument("--workload", default="bounded", choices=["bounded", "tiny", "unbounded", "batched", "dynamic"],
+    ap.add_argument("--workload", default="bounded",
+                    choices=["bounded", "tiny", "unbounded", "contracted", "batched", "dynamic"],
                     help="bounded (default) is the headline configuration; the others are the wider configurations")
     ap.add_argument("--no-batched-compare", action="store_true")
     ap.add_argument("--cpu-rays", type=int, default=1 << 15, help="rays in the CPU-baseline sample")
@@ -329,6 +330,10 @@ WORKLOAD_CONFIG = {
     "unbounded": {"cameras": "64 inside radius 100, random directions", "scene": "256 blobs, log-uniform scale",
                   "grid": "4-level cascade of 128^3, level-0 box [-125,125]^3",
                   "dt": "cone: clamp(t/256, 1e-3, 10), t in [0.05, 1000]", "early_stop_eps": 1e-4, "alpha_thre": 1e-2},
+    "contracted": {"cameras": "64 inside radius 100, random directions", "scene": "256 blobs, log-uniform scale",
+                   "grid": "one 128^3 grid over contracted space (Mip-NeRF 360 Eq. 10), box [-125,125]^3 = unit ball",
+                   "dt": "cone: clamp(t/256, 1e-3, 10), t in [0.05, 1000]", "early_stop_eps": 1e-4,
+                   "alpha_thre": 1e-2},
     "batched": {"scenes": "64 (8-256 blobs each, own 128^3 grid)", "rays": "lognormal per scene, scene-major",
                 "dt": "sqrt(3)*3/1024, max 1024 steps", "early_stop_eps": 1e-4, "alpha_thre": 1e-2},
     "dynamic": {"scene": "128 moving blobs, t in [0,1]", "grid": "16 time bins x 128^3",

@@ -67,13 +67,22 @@ extern "C" {
  * (bit cell & 31 of word cell >> 5). Level 0 covers aabb = (lo xyz, hi xyz);
  * level l >= 1 covers the level-0 box scaled by 2^l about its centre. A slot is
  * an independent grid: a time bin of a dynamic scene, or a scene of a batch.
+ *
+ * contraction = 1 (unbounded scenes, Sec. 2.1 "Scene Contraction", with the
+ * contraction of Mip-NeRF 360, its Eq. 10): one level; a point x is normalised
+ * by the box, x_n = (x - c) * (1 / h) (c = (lo + hi) / 2, h = (hi - lo) / 2),
+ * contracted, x_c = x_n if |x_n|^2 <= 1 else x_n * (2 - 1/|x_n|) / |x_n|, and
+ * looked up in a grid spanning [-2, 2]^3: cell i = floor((x_c + 2) * res / 4).
+ * All in float32, every operation rounded ((x0^2 + x1^2) + x2^2, IEEE sqrt and
+ * division). Rays are not clipped by the box: they march [near_plane, far_plane].
  */
 typedef struct nacc_grid {
     const uint32_t* bits; /* device, ceil(n_slots*n_levels*res0*res1*res2 / 32) words */
     int32_t res[3];       /* 1 .. 2^22 cells per axis; total cells over all slots and levels < 2^31 */
-    int32_t n_levels; /* 1 .. NACC_MAX_LEVELS */
+    int32_t n_levels; /* 1 .. NACC_MAX_LEVELS (1 with contraction) */
     int32_t n_slots;  /* >= 1 */
     float aabb[6];
+    int32_t contraction; /* 0: boxes (cascade); 1: contracted unbounded space */
 } nacc_grid;
 
 /*
@@ -321,7 +330,11 @@ int nacc_update_occupancy_grid(float* ema, uint32_t* bits, int64_t n_cells, cons
  * and 40 of the second, times 2^-24); xyz_a = lo_a + (i_a + jitter_a) * cs_a in
  * float32 (each operation rounded), with the level box formed as for marching
  * (c = (lo + hi) / 2, h = (hi - lo) / 2, level l >= 1: c -+ h 2^l) and
- * cs = (hi - lo) / res. Deterministic: the same arguments give the same bits.
+ * cs = (hi - lo) / res. With contraction the cell and point are drawn in
+ * contracted space (box [-2, 2]^3) and the point is mapped back to the world:
+ * r^2 = (p0^2 + p1^2) + p2^2; r^2 <= 1: x_n = p; else x_n = p / ((2 - r) r)
+ * (NaN for r >= 2, cells the contraction never reaches); xyz = c + h x_n with
+ * the box's c, h. Deterministic: the same arguments give the same bits.
  * grid: the bits pointer is not read; cells (n,) int32 out; xyz (n,3) float32 out.
  */
 int nacc_sample_grid_cells(uint64_t seed, uint64_t stream, int64_t n, const nacc_grid* grid,

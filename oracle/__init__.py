@@ -51,7 +51,8 @@ def lib():
         P = ctypes.c_void_p
         i32, i64, f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float
         L.oracle_march.restype = i64
-        L.oracle_march.argtypes = [P, P, P, P, i32, P, P, i32, i32, P, f32, f32, f32, f32, f32, i32, P, P, P, P, i64]
+        L.oracle_march.argtypes = [P, P, P, P, i32, P, P, i32, i32, P, f32, f32, f32, f32, f32, i32, i32, P, P, P, P,
+                                   i64]
         L.oracle_prune.restype = i64
         L.oracle_prune.argtypes = [P, i32, P, P, P, f32, f32, P, P, P, P, P, P, i64]
         L.oracle_render_weights.argtypes = [P, i32, P, P, P, P, P]
@@ -91,7 +92,7 @@ class Packed:
 
 
 def march(rays_o, rays_d, bits, res, aabb, near_plane=0.0, far_plane=1e10, dt_min=1e-2, dt_max=None,
-          cone=0.0, max_steps=1024, n_levels=1, n_slots=1, ray_time=None, ray_slot=None) -> Packed:
+          cone=0.0, max_steps=1024, n_levels=1, n_slots=1, ray_time=None, ray_slot=None, contraction=0) -> Packed:
     """Occupancy-grid ray marching (Sec. 2.1), float32 replica, dense lattice walk."""
     o = _c(rays_o, np.float32).reshape(-1, 3)
     d = _c(rays_d, np.float32).reshape(-1, 3)
@@ -105,7 +106,8 @@ def march(rays_o, rays_d, bits, res, aabb, near_plane=0.0, far_plane=1e10, dt_mi
     pi = np.zeros((R, 2), dtype=np.int32)
     args = lambda ts, te, ri, cap: (
         _p(o), _p(d), _p(tt), _p(sl), R, _p(bits), _p(res), n_levels, n_slots, _p(box),
-        near_plane, far_plane, dt_min, dt_max, cone, max_steps, _p(pi), _p(ts), _p(te), _p(ri), cap)
+        near_plane, far_plane, dt_min, dt_max, cone, max_steps, int(contraction), _p(pi), _p(ts), _p(te), _p(ri),
+        cap)
     n = lib().oracle_march(*args(None, None, None, 0))
     if n < 0:
         raise ValueError("oracle_march: invalid arguments")

@@ -155,17 +155,47 @@ static int or_occupied(const float x[3], int slot, const uint32_t* bits, const i
     return 0;
 }
 
+/* M3 for unbounded scenes (Sec. 2.1 "Scene Contraction", the contraction of
+ * Mip-NeRF 360's Eq. 10): x normalised by the box, x_n = (x - c) * (1/h); inside
+ * the unit ball (|x_n|^2 <= 1) unchanged, outside scaled by (2 - 1/|x_n|)/|x_n|;
+ * the grid spans [-2, 2]^3: u = (x_c + 2) * (res/4), empty outside [0, res). */
+static int or_occupied_contracted(const float x[3], int slot, const uint32_t* bits, const int32_t res[3],
+                                  const float c[3], const float inv_h[3]) {
+    float xn[3], u[3];
+    for (int a = 0; a < 3; ++a) xn[a] = (x[a] - c[a]) * inv_h[a];
+    float n2 = (xn[0] * xn[0] + xn[1] * xn[1]) + xn[2] * xn[2];
+    if (!(n2 <= 1.0f)) {
+        float n = sqrtf(n2);
+        float sc = (2.0f - 1.0f / n) / n;
+        for (int a = 0; a < 3; ++a) xn[a] = xn[a] * sc;
+    }
+    for (int a = 0; a < 3; ++a) {
+        u[a] = (xn[a] + 2.0f) * ((float)res[a] * 0.25f);
+        if (!(u[a] >= 0.0f && u[a] < (float)res[a])) return 0;
+    }
+    int64_t ix = (int64_t)u[0], iy = (int64_t)u[1], iz = (int64_t)u[2];
+    int64_t cell = (((int64_t)slot * res[0] + ix) * res[1] + iy) * res[2] + iz;
+    return (int)((bits[cell >> 5] >> (cell & 31)) & 1u);
+}
+
 /* Ray marching (Sec. 2.1): returns the total number of emitted samples;
- * writes packed_info for every ray and samples up to `capacity`. */
+ * writes packed_info for every ray and samples up to `capacity`. With
+ * contraction (one level) rays are not clipped: they march [near_plane, far_plane]. */
 int64_t oracle_march(const float* rays_o, const float* rays_d, const float* ray_time,
                      const int32_t* ray_slot, int32_t n_rays, const uint32_t* bits,
                      const int32_t res[3], int32_t n_levels, int32_t n_slots, const float aabb[6],
                      float near_plane, float far_plane, float dt_min, float dt_max, float cone,
-                     int32_t max_steps, int32_t* packed_info, float* t_starts, float* t_ends,
-                     int32_t* ray_indices, int64_t capacity) {
+                     int32_t max_steps, int32_t contraction, int32_t* packed_info, float* t_starts,
+                     float* t_ends, int32_t* ray_indices, int64_t capacity) {
     or_levels L;
     if (n_levels < 1 || n_levels > OR_MAX_LEVELS) return -1;
+    if (contraction && n_levels != 1) return -1;
     or_make_levels(aabb, n_levels, res, &L);
+    float cc[3], inv_h[3];
+    for (int a = 0; a < 3; ++a) {
+        cc[a] = (aabb[a] + aabb[3 + a]) * 0.5f;
+        inv_h[a] = 1.0f / ((aabb[3 + a] - aabb[a]) * 0.5f);
+    }
     const float* blo = L.lo[n_levels - 1];
     const float* bhi = L.hi[n_levels - 1];
     int64_t total = 0;
@@ -175,7 +205,16 @@ int64_t oracle_march(const float* rays_o, const float* rays_d, const float* ray_
         int64_t start = total;
         float near, far;
         int slot = or_slot(ray_time, ray_slot, r, n_slots);
-        if (slot >= 0 && slot < n_slots && or_clip(o, d, blo, bhi, near_plane, far_plane, &near, &far)) {
+        int marching;
+        if (contraction) {
+            marching = or_finite(o[0]) && or_finite(o[1]) && or_finite(o[2]) && or_finite(d[0]) &&
+                       or_finite(d[1]) && or_finite(d[2]) && near_plane < far_plane;
+            near = near_plane;
+            far = far_plane;
+        } else {
+            marching = or_clip(o, d, blo, bhi, near_plane, far_plane, &near, &far);
+        }
+        if (slot >= 0 && slot < n_slots && marching) {
             float t = near;
             for (int32_t k = 0; k < max_steps; ++k) {
                 float ts, tn;
@@ -195,7 +234,8 @@ int64_t oracle_march(const float* rays_o, const float* rays_d, const float* ray_
                 float mid = (ts + te) * 0.5f;
                 float x[3];
                 for (int a = 0; a < 3; ++a) x[a] = o[a] + d[a] * mid;
-                if (or_occupied(x, slot, bits, res, n_levels, &L)) {
+                if (contraction ? or_occupied_contracted(x, slot, bits, res, cc, inv_h)
+                                : or_occupied(x, slot, bits, res, n_levels, &L)) {
                     if (total < capacity) {
                         t_starts[total] = ts;
                         t_ends[total] = te;

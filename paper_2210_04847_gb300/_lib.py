@@ -62,6 +62,7 @@ class Grid(ctypes.Structure):
         ("n_levels", ctypes.c_int32),
         ("n_slots", ctypes.c_int32),
         ("aabb", ctypes.c_float * 6),
+        ("contraction", ctypes.c_int32),
     ]
 
 
@@ -171,9 +172,11 @@ def _rc(code: int, fn: str):
         raise NaccError("%s failed: %s (%d)" % (fn, msg, code))
 
 
-def make_grid(bits: torch.Tensor, res: Sequence[int], aabb: Sequence[float], n_levels=1, n_slots=1) -> Grid:
+def make_grid(bits: torch.Tensor, res: Sequence[int], aabb: Sequence[float], n_levels=1, n_slots=1,
+              contraction: int = 0) -> Grid:
     _check(bits, torch.int32, "grid bits")
     g = Grid()
+    g.contraction = int(contraction)
     g.bits = bits.data_ptr()
     for k in range(3):
         g.res[k] = int(res[k])

@@ -34,26 +34,28 @@ class OccupancyGrid:
     maintains.
     """
 
-    def __init__(self, aabb: Sequence[float], res=128, n_levels: int = 1, n_slots: int = 1, device="cuda"):
+    def __init__(self, aabb: Sequence[float], res=128, n_levels: int = 1, n_slots: int = 1, device="cuda",
+                 contraction: int = 0):
         self.aabb = tuple(float(v) for v in aabb)
         self.res = (int(res),) * 3 if np.isscalar(res) else tuple(int(v) for v in res)
         self.n_levels = int(n_levels)
         self.n_slots = int(n_slots)
+        self.contraction = int(contraction)  # 1: unbounded scene, contracted space (Sec. 2.1)
         self.n_cells = self.res[0] * self.res[1] * self.res[2] * self.n_levels * self.n_slots
         self.ema = torch.zeros(self.n_cells, dtype=torch.float32, device=device)
         self.bits = torch.zeros((self.n_cells + 31) // 32, dtype=torch.int32, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
 
     @classmethod
-    def from_bits(cls, bits: np.ndarray, res, aabb, n_levels=1, n_slots=1, device="cuda"):
-        g = cls(aabb, res, n_levels, n_slots, device)
+    def from_bits(cls, bits: np.ndarray, res, aabb, n_levels=1, n_slots=1, device="cuda", contraction=0):
+        g = cls(aabb, res, n_levels, n_slots, device, contraction)
         w = np.ascontiguousarray(bits, dtype=np.uint32).view(np.int32)
         assert w.size == g.bits.numel(), "bit words do not match the grid size"
         g.bits.copy_(torch.from_numpy(w))
         return g
 
     def struct(self) -> _lib.Grid:
-        return _lib.make_grid(self.bits, self.res, self.aabb, self.n_levels, self.n_slots)
+        return _lib.make_grid(self.bits, self.res, self.aabb, self.n_levels, self.n_slots, self.contraction)
 
     def sample_cells(self, n: int, seed: int = 0, step: int = 0):
         """n uniform random cells of the grid (all levels and slots) and a uniform
@@ -72,7 +74,7 @@ class OccupancyGrid:
 
     def state_dict(self):
         return {"ema": self.ema.clone(), "bits": self.bits.clone(), "res": self.res, "aabb": self.aabb,
-                "n_levels": self.n_levels, "n_slots": self.n_slots}
+                "n_levels": self.n_levels, "n_slots": self.n_slots, "contraction": self.contraction}
 
     def load_state_dict(self, sd):
         self.ema.copy_(sd["ema"])

@@ -83,6 +83,8 @@ struct SampleArgs {
     long long n;
     int res[3];
     int n_levels, n_sl;             // levels, levels * slots
+    int contraction;                // points drawn in contracted space, mapped back to the world
+    float cc[3], hh[3];             // contraction: box centre and half size
     float lo[NACC_MAX_LEVELS][3];   // level boxes in float32, formed as the marcher forms them
     float cs[NACC_MAX_LEVELS][3];   // cell size (hi - lo) / res of each level
     int32_t* cells;
@@ -113,6 +115,7 @@ __global__ void __launch_bounds__(kThreads) sample_cells_kernel(const SampleArgs
                             __uint2float_rn((unsigned)((q0 >> 16) & 0xFFFFFFull)) * (1.0f / 16777216.0f),
                             __uint2float_rn((unsigned)(q1 >> 40)) * (1.0f / 16777216.0f)};
         const unsigned idx[3] = {ix, iy, iz};
+        float p[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             float lo = a.lo[0][k], cs = a.cs[0][k];
@@ -121,8 +124,22 @@ __global__ void __launch_bounds__(kThreads) sample_cells_kernel(const SampleArgs
                     lo = a.lo[l][k];
                     cs = a.cs[l][k];
                 }
-            a.xyz[3 * s + k] = __fadd_rn(lo, __fmul_rn(__fadd_rn(__uint2float_rn(idx[k]), j[k]), cs));
+            p[k] = __fadd_rn(lo, __fmul_rn(__fadd_rn(__uint2float_rn(idx[k]), j[k]), cs));
         }
+        if (a.contraction) {
+            // p is in contracted space [-2, 2]^3: back to the world, x_c / ((2 - r) r)
+            // outside the unit ball, then c + h x_n; unreachable points (r >= 2) are NaN
+            const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(p[0], p[0]), __fmul_rn(p[1], p[1])), __fmul_rn(p[2], p[2]));
+            float sc = 1.0f;
+            if (!(r2 <= 1.0f)) {
+                const float r = __fsqrt_rn(r2);
+                sc = r < 2.0f ? __fdiv_rn(1.0f, __fmul_rn(__fsub_rn(2.0f, r), r)) : __int_as_float(0x7fc00000);
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) p[k] = __fadd_rn(a.cc[k], __fmul_rn(a.hh[k], __fmul_rn(p[k], sc)));
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a.xyz[3 * s + k] = p[k];
     }
 }
 
@@ -135,6 +152,7 @@ extern "C" int nacc_sample_grid_cells(uint64_t seed, uint64_t stream, int64_t n,
                                       int32_t* cells, float* xyz, void* cuda_stream) {
     if (n < 0 || !grid) return NACC_ERR_INVALID_ARG;
     if (grid->n_levels < 1 || grid->n_levels > NACC_MAX_LEVELS || grid->n_slots < 1) return NACC_ERR_INVALID_ARG;
+    if (grid->contraction != 0 && (grid->contraction != 1 || grid->n_levels != 1)) return NACC_ERR_INVALID_ARG;
     for (int k = 0; k < 3; ++k)
         if (grid->res[k] < 1 || !(grid->aabb[k] < grid->aabb[3 + k])) return NACC_ERR_INVALID_ARG;
     const long long n_cells =
@@ -148,11 +166,16 @@ extern "C" int nacc_sample_grid_cells(uint64_t seed, uint64_t stream, int64_t n,
     a.n = n;
     a.n_levels = grid->n_levels;
     a.n_sl = grid->n_levels * grid->n_slots;
+    a.contraction = grid->contraction;
     for (int k = 0; k < 3; ++k) {
         a.res[k] = grid->res[k];
         // level l: the level-0 box scaled by 2^l about its centre, in float32
-        const float lo = grid->aabb[k], hi = grid->aabb[3 + k];
+        // (contraction: one level spanning [-2, 2] in contracted space)
+        const float lo = grid->contraction ? -2.0f : grid->aabb[k];
+        const float hi = grid->contraction ? 2.0f : grid->aabb[3 + k];
         const float c = (lo + hi) * 0.5f, h = (hi - lo) * 0.5f;
+        a.cc[k] = (grid->aabb[k] + grid->aabb[3 + k]) * 0.5f;
+        a.hh[k] = (grid->aabb[3 + k] - grid->aabb[k]) * 0.5f;
         for (int l = 0; l < NACC_MAX_LEVELS; ++l) {
             float llo = lo, lhi = hi;
             if (l > 0) {

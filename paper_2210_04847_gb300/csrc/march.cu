@@ -36,7 +36,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kTileRaysMax = 32;  // rays per warp tile (uniform steps), lane i holds ray i
 
 struct Levels {
     float lo[NACC_MAX_LEVELS][3];
@@ -73,6 +72,9 @@ struct MarchArgs {
     int32_t row_stride;       // words between consecutive rows in shared memory (= mask_words)
     int32_t tile_rays;
     const float* cone_table;  // t_0 = near_plane, t_1, ..., t_max_steps (cone steps only)
+    int32_t contract;         // contracted unbounded space (one level, no box clip)
+    float cc[3], inv_h[3];    // contraction: box centre and 1 / half size
+    float qres[3];            // contraction: res / 4 (the grid spans [-2, 2])
     Levels L;
 };
 
@@ -85,6 +87,11 @@ __device__ __forceinline__ bool clip_ray(const MarchArgs& a, const float o[3], c
 #pragma unroll
     for (int k = 0; k < 3; ++k)
         if (!finite32(o[k]) || !finite32(d[k])) return false;
+    if (a.contract) {  // unbounded: the whole [near_plane, far_plane]
+        near = a.near_plane;
+        far = a.far_plane;
+        return near < far;
+    }
     float t_in = -INFINITY, t_out = INFINITY;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -120,22 +127,44 @@ __device__ __forceinline__ int slot_of(const MarchArgs& a, int r) {
 // Occupancy bit of point x: finest level whose box holds x, floor cell index.
 // i = floor(u) with 0 <= i < res is the same test as 0 <= u < res followed by
 // truncation (u is finite here: o, d and the lattice are finite).
+// MAXL == 0: contracted unbounded space (one level, see nacc_grid).
 template <int MAXL>
 __device__ __forceinline__ bool occupied(const MarchArgs& a, float x0, float x1, float x2,
                                          unsigned slot_level0) {
+    if constexpr (MAXL == 0) {
+        float x[3] = {__fmul_rn(__fsub_rn(x0, a.cc[0]), a.inv_h[0]), __fmul_rn(__fsub_rn(x1, a.cc[1]), a.inv_h[1]),
+                      __fmul_rn(__fsub_rn(x2, a.cc[2]), a.inv_h[2])};
+        const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(x[0], x[0]), __fmul_rn(x[1], x[1])), __fmul_rn(x[2], x[2]));
+        if (!(n2 <= 1.0f)) {
+            const float n = __fsqrt_rn(n2);
+            const float s = __fdiv_rn(__fsub_rn(2.0f, __fdiv_rn(1.0f, n)), n);
 #pragma unroll
-    for (int l = 0; l < MAXL; ++l) {
-        if (MAXL > 1 && l >= a.n_levels) break;  // single-level kernels run only for n_levels == 1
-        const int i0 = __float2int_rd(__fmul_rn(__fsub_rn(x0, a.L.lo[l][0]), a.L.scale[l][0]));
-        const int i1 = __float2int_rd(__fmul_rn(__fsub_rn(x1, a.L.lo[l][1]), a.L.scale[l][1]));
-        const int i2 = __float2int_rd(__fmul_rn(__fsub_rn(x2, a.L.lo[l][2]), a.L.scale[l][2]));
+            for (int k = 0; k < 3; ++k) x[k] = __fmul_rn(x[k], s);
+        }
+        const int i0 = __float2int_rd(__fmul_rn(__fadd_rn(x[0], 2.0f), a.qres[0]));
+        const int i1 = __float2int_rd(__fmul_rn(__fadd_rn(x[1], 2.0f), a.qres[1]));
+        const int i2 = __float2int_rd(__fmul_rn(__fadd_rn(x[2], 2.0f), a.qres[2]));
         if ((unsigned)i0 < (unsigned)a.res0 && (unsigned)i1 < (unsigned)a.res1 && (unsigned)i2 < (unsigned)a.res2) {
-            const unsigned cell = (((slot_level0 + l) * a.res0 + i0) * a.res1 + i1) * a.res2 + i2;
+            const unsigned cell = ((slot_level0 * a.res0 + i0) * a.res1 + i1) * a.res2 + i2;
             const unsigned w = __ldg(a.bits + (cell >> 5));
             return (w >> (cell & 31u)) & 1u;
         }
+        return false;
+    } else {
+#pragma unroll
+        for (int l = 0; l < MAXL; ++l) {
+            if (MAXL > 1 && l >= a.n_levels) break;  // single-level kernels run only for n_levels == 1
+            const int i0 = __float2int_rd(__fmul_rn(__fsub_rn(x0, a.L.lo[l][0]), a.L.scale[l][0]));
+            const int i1 = __float2int_rd(__fmul_rn(__fsub_rn(x1, a.L.lo[l][1]), a.L.scale[l][1]));
+            const int i2 = __float2int_rd(__fmul_rn(__fsub_rn(x2, a.L.lo[l][2]), a.L.scale[l][2]));
+            if ((unsigned)i0 < (unsigned)a.res0 && (unsigned)i1 < (unsigned)a.res1 && (unsigned)i2 < (unsigned)a.res2) {
+                const unsigned cell = (((slot_level0 + l) * a.res0 + i0) * a.res1 + i1) * a.res2 + i2;
+                const unsigned w = __ldg(a.bits + (cell >> 5));
+                return (w >> (cell & 31u)) & 1u;
+            }
+        }
+        return false;
     }
-    return false;
 }
 
 __device__ __forceinline__ float lattice_t(float near, int k, float dt) {
@@ -227,7 +256,7 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
     const int max_ch = min((nk + 31) >> 5, a.mask_words);
     int count = 0, nch = 0;
     pts_out = shared ? nk : 0;  // own cone lattices are counted as they are walked
-    if (COARSE && shared) {
+    if (COARSE && MAXL > 0 && shared) {  // contracted indices are not monotone along a ray
         // Every cell index along each axis, at each level, is a monotone function
         // of k (t_k, the midpoints and the rounded index arithmetic all are), and so
         // is the index clamped to [-1, res]. If two points have the same clamped
@@ -694,11 +723,16 @@ void launch_uniform(K kernel, size_t smem, int need, cudaStream_t st, const Marc
 template <int MAXL, int MINB>
 void launch_variant(bool cone, bool unroll, bool coarse, size_t smem, int need, cudaStream_t st,
                     const MarchArgs& a) {
+    if constexpr (MAXL == 0) coarse = false;  // contracted space: no coarse pass
     if (cone) {
-        if (coarse) launch_uniform(march_uniform_kernel<MAXL, MINB, true, false, true>, smem, need, st, a);
-        else launch_uniform(march_uniform_kernel<MAXL, MINB, true>, smem, need, st, a);
+        if constexpr (MAXL > 0)
+            if (coarse) {
+                launch_uniform(march_uniform_kernel<MAXL, MINB, true, false, true>, smem, need, st, a);
+                return;
+            }
+        launch_uniform(march_uniform_kernel<MAXL, MINB, true>, smem, need, st, a);
     } else if (coarse) {
-        launch_uniform(march_uniform_kernel<MAXL, MINB, false, false, true>, smem, need, st, a);
+        if constexpr (MAXL > 0) launch_uniform(march_uniform_kernel<MAXL, MINB, false, false, true>, smem, need, st, a);
     } else {
         if constexpr (MAXL == 1) {  // two-chunk unrolling exists for the single-level uniform walk
             if (unroll) {
@@ -737,6 +771,7 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
     if (n_rays > 0 && (!rays_o || !rays_d || !packed_info || !grid->bits)) return NACC_ERR_INVALID_ARG;
     if (capacity > 0 && (!t_starts || !t_ends || !ray_indices)) return NACC_ERR_INVALID_ARG;
     if (grid->n_levels < 1 || grid->n_levels > NACC_MAX_LEVELS || grid->n_slots < 1) return NACC_ERR_INVALID_ARG;
+    if (grid->contraction != 0 && (grid->contraction != 1 || grid->n_levels != 1)) return NACC_ERR_INVALID_ARG;
     if (grid->res[0] < 1 || grid->res[1] < 1 || grid->res[2] < 1) return NACC_ERR_INVALID_ARG;
     if (grid->res[0] > (1 << 22) || grid->res[1] > (1 << 22) || grid->res[2] > (1 << 22)) return NACC_ERR_INVALID_ARG;
     const long long cells = (long long)grid->res[0] * grid->res[1] * grid->res[2] * grid->n_levels * grid->n_slots;
@@ -794,6 +829,13 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
     a.tile_rays = tile_rays_for(a.mask_words);
     a.row_stride = a.mask_words;
     make_levels(*grid, a.L);
+    a.contract = grid->contraction;
+    for (int k = 0; k < 3; ++k) {
+        const float lo = grid->aabb[k], hi = grid->aabb[3 + k];
+        a.cc[k] = (lo + hi) * 0.5f;
+        a.inv_h[k] = 1.0f / ((hi - lo) * 0.5f);
+        a.qres[k] = (float)grid->res[k] * 0.25f;
+    }
 
     a.n_tiles = (n_rays + a.tile_rays - 1) / a.tile_rays;
     const size_t clear = kTicketBytes + (size_t)a.n_tiles * sizeof(unsigned long long);
@@ -808,7 +850,8 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
     const int need = (a.n_tiles + kWarps - 1) / kWarps;
     const bool unroll = tune_get(NACC_TUNE_MARCH_UNROLL) != 0;
     const bool coarse = tune_get(NACC_TUNE_MARCH_COARSE) != 0;
-    if (a.n_levels == 1) launch_walk<1>(cone, occ, unroll, coarse, smem, need, st, a);
+    if (a.contract) launch_walk<0>(cone, occ, false, false, smem, need, st, a);
+    else if (a.n_levels == 1) launch_walk<1>(cone, occ, unroll, coarse, smem, need, st, a);
     else if (a.n_levels <= 4) launch_walk<4>(cone, occ, unroll, coarse, smem, need, st, a);
     else launch_walk<NACC_MAX_LEVELS>(cone, occ, unroll, coarse, smem, need, st, a);
     return launch_status(cudaGetLastError());

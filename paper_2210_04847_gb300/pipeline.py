@@ -65,7 +65,7 @@ class HotPath:
         self.n_cells = int(np.prod(w.res)) * w.n_levels * w.n_slots
         self.ema = torch.zeros(self.n_cells, dtype=torch.float32, device=device)
         self.params = _lib.make_params(w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone, w.max_steps)
-        self.grid = _lib.make_grid(self.bits, w.res, w.aabb, w.n_levels, w.n_slots)
+        self.grid = _lib.make_grid(self.bits, w.res, w.aabb, w.n_levels, w.n_slots, w.contraction)
         f32, i32 = torch.float32, torch.int32
         z = lambda n, dt=f32: torch.zeros(max(int(n), 1), dtype=dt, device=device)
         self.cap_m, self.cap_k = int(cap_marched), int(cap_kept)

@@ -9,6 +9,7 @@ time of the point). Workloads:
 * ``bounded``   2^18 rays, 100 cameras at 800x800, 64 blobs, one 128^3 grid
 * ``tiny``      one 64x64 camera, 8 blobs, 64^3 grid, no pruning
 * ``unbounded`` 2^20 rays from inside a radius-1000 scene, 4-level cascade, cone steps
+* ``contracted`` the unbounded scene and rays, one 128^3 grid over contracted space
 * ``batched``   64 scenes (8-256 blobs, own 128^3 grid each), lognormal rays per scene
 * ``dynamic``   2^19 rays over 16 time bins of 128 moving blobs, one grid per bin
 """
@@ -78,7 +79,7 @@ class Scenario:
         """Uniform random cells over every slot and level, a jittered point in each, its time."""
         w = self.w
         cells, jit = synth.grid_update_samples(self.rank, step, self.n_grid, w.res, w.n_levels, w.n_slots)
-        xyz = synth.cell_positions(cells, jit, w.aabb, w.res, w.n_levels)
+        xyz = synth.cell_positions(cells, jit, w.aabb, w.res, w.n_levels, contraction=w.contraction)
         per_slot = int(np.prod(w.res)) * w.n_levels
         slot = cells.astype(np.int64) // per_slot
         times = None
@@ -139,6 +140,8 @@ class Scenario:
     def ema_init(self):
         """float32 EMA grid initialised from the densities at the cell centres (the rule that built the bits)."""
         w = self.w
+        if w.contraction:
+            return synth.density_at_contracted_centres(self.scenes[0], w.aabb, w.res, self.device).float()
         if w.n_slots == 1:
             return synth.density_at_cell_centres(self.scenes[0], w.aabb, w.res, w.n_levels, None,
                                                  self.device).float()
@@ -161,6 +164,9 @@ def make_scenario(name: str, rank: int = 0, device="cuda", n_rays=None, pool: in
         w = synth.tiny_config(0, device=device)
         w.target_rgb = synth.rand_uniform(0, 77, 3 * w.n_rays).reshape(-1, 3).astype(np.float32)
         return Scenario(name, [w], w.scenes, device, n_grid_samples=1 << 16, rank=rank)
+    if name == "contracted":
+        ws = [synth.contracted_config(0, n_rays=n_rays or (1 << 20), device=device, batch=b) for b in batches[:1]]
+        return Scenario(name, ws, ws[0].scenes, device, rank=rank)
     if name == "unbounded":
         ws = [synth.unbounded_config(0, n_rays=n_rays or (1 << 20), device=device, batch=b) for b in batches[:1]]
         return Scenario(name, ws, ws[0].scenes, device, rank=rank)

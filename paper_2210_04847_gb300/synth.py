@@ -300,6 +300,53 @@ def occupancy_bits(scene: BlobScene, aabb, res, n_levels=1, thre=0.01, t=None, d
     return pack_bits((dens > thre).cpu().numpy())
 
 
+def uncontract(xc: np.ndarray) -> np.ndarray:
+    """Inverse of the Mip-NeRF 360 contraction (Eq. 10 there) for points of the
+    open radius-2 ball, float64: |x_c| <= 1 unchanged, else x_c / ((2 - |x_c|) |x_c|)."""
+    xc = np.asarray(xc, dtype=np.float64)
+    r = np.linalg.norm(xc, axis=-1, keepdims=True)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        s = np.where(r <= 1.0, 1.0, 1.0 / ((2.0 - r) * r))
+    return xc * s
+
+
+def contracted_cell_centres(aabb, res) -> tuple:
+    """World points of the cell centres of a contracted grid over [-2, 2]^3 (the box
+    normalises the unit ball: world = c + h * uncontract(x_c)) and the mask of
+    cells whose centre lies inside the radius-2 ball (the others are unreachable)."""
+    rx, ry, rz = (int(v) for v in res)
+    axes = [-2.0 + (np.arange(r, dtype=np.float64) + 0.5) * (4.0 / r) for r in (rx, ry, rz)]
+    xc = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, 3)
+    inside = np.linalg.norm(xc, axis=1) < 2.0
+    lo = np.asarray(aabb[:3], np.float64)
+    hi = np.asarray(aabb[3:], np.float64)
+    world = 0.5 * (lo + hi) + 0.5 * (hi - lo) * uncontract(np.where(inside[:, None], xc, 0.0))
+    return world, inside
+
+
+def density_at_contracted_centres(scene: BlobScene, aabb, res, device="cpu"):
+    """float64 density at the world point of every cell centre of a contracted grid
+    (flat cell order); 0 for cells outside the radius-2 ball."""
+    import torch
+
+    world, inside = contracted_cell_centres(aabb, res)
+    c = torch.as_tensor(scene.centers, device=device)
+    inv2s2 = torch.as_tensor(1.0 / (2.0 * scene.scales**2), device=device)
+    peaks = torch.as_tensor(scene.peaks, device=device)
+    dens = torch.empty(world.shape[0], dtype=torch.float64, device=device)
+    for s in range(0, world.shape[0], 1 << 16):
+        x = torch.as_tensor(world[s : s + (1 << 16)], device=device)
+        d2 = ((x[:, None, :] - c[None, :, :]) ** 2).sum(-1)
+        dens[s : s + (1 << 16)] = torch.exp(-d2 * inv2s2[None, :]) @ peaks
+    return dens * torch.as_tensor(inside, device=device)
+
+
+def occupancy_bits_contracted(scene: BlobScene, aabb, res, thre=0.01, device="cpu") -> np.ndarray:
+    """uint32 words of a contracted grid: bit = density(world point of the cell
+    centre) > thre; cells outside the radius-2 ball are empty."""
+    return pack_bits((density_at_contracted_centres(scene, aabb, res, device) > thre).cpu().numpy())
+
+
 # ----------------------------------------------------------------------------
 # Workload configurations (bounded/unbounded/batched/dynamic scenes)
 # ----------------------------------------------------------------------------
@@ -333,6 +380,7 @@ class Workload:
     target_rgb: Optional[np.ndarray] = None  # (R, 3) float32
     backward: bool = True
     meta: dict = field(default_factory=dict)
+    contraction: int = 0  # 1: contracted unbounded space (one level; see nacc_grid)
 
     @property
     def n_rays(self) -> int:
@@ -420,6 +468,18 @@ def unbounded_config(seed: int = 0, n_rays: int = 1 << 20, n_cams: int = 64, dev
         "unbounded-cascade4x128-cone", _f32(o), _f32(d), bits, (128, 128, 128), 4, 1, aabb,
         0.05, 1000.0, 1e-3, 10.0, 1.0 / 256.0, 4096, 1e-4, 1e-2, [scene], target_rgb=_f32(target),
     )
+
+
+def contracted_config(seed: int = 0, n_rays: int = 1 << 20, n_cams: int = 64, device="cpu", batch: int = 0,
+                      res: int = 128) -> Workload:
+    """The unbounded scene and rays of ``unbounded_config`` with the contracted grid
+    instead of the cascade: one res^3 grid over the contraction of the space, the
+    box [-125, 125]^3 normalising the unit ball, same cone steps and planes."""
+    w = unbounded_config(seed, n_rays=n_rays, n_cams=n_cams, device=device, batch=batch)
+    bits = occupancy_bits_contracted(w.scenes[0], w.aabb, (res, res, res), 0.01, device=device)
+    w.name = "unbounded-contracted-grid%d-cone" % res
+    w.bits, w.res, w.n_levels, w.contraction = bits, (res, res, res), 1, 1
+    return w
 
 
 def batched_config(seed: int = 0, n_scenes: int = 64, device="cpu", ray_scale: float = 1.0) -> Workload:
@@ -530,10 +590,24 @@ def level_boxes_f32(aabb: Sequence[float], n_levels: int):
     return out
 
 
-def cell_positions(cells: np.ndarray, jitter: np.ndarray, aabb, res, n_levels=1) -> np.ndarray:
+def cell_positions(cells: np.ndarray, jitter: np.ndarray, aabb, res, n_levels=1, contraction=0) -> np.ndarray:
     """float32 points lo + (cell index + jitter) * cell size inside flat cells, every
     operation rounded to float32 (cell size = (hi - lo) / res of the cell's level;
-    level = (cell / res^3) mod n_levels)."""
+    level = (cell / res^3) mod n_levels). With contraction the point is drawn in
+    the contracted box [-2, 2]^3 and mapped back to the world (nacc_sample_grid_cells)."""
+    if contraction:
+        p = cell_positions(cells, jitter, (-2.0, -2.0, -2.0, 2.0, 2.0, 2.0), res, 1)
+        r2 = (p[:, 0] * p[:, 0] + p[:, 1] * p[:, 1]) + p[:, 2] * p[:, 2]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            r = np.sqrt(r2)
+            sc = np.where(r2 <= np.float32(1), np.float32(1),
+                          np.where(r < np.float32(2), np.float32(1) / ((np.float32(2) - r) * r), np.float32(np.nan)))
+        sc = sc.astype(np.float32)
+        lo = np.asarray(aabb[:3], np.float32)
+        hi = np.asarray(aabb[3:], np.float32)
+        c = (lo + hi) * np.float32(0.5)
+        h = (hi - lo) * np.float32(0.5)
+        return (c + h * (p * sc[:, None])).astype(np.float32)
     rx, ry, rz = res
     per_level = rx * ry * rz
     cells = np.asarray(cells, dtype=np.int64)

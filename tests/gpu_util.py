@@ -17,7 +17,7 @@ def dev(a, dtype=None):
 
 
 def grid_struct(bits_t, w: synth.Workload):
-    return _lib.make_grid(bits_t, w.res, w.aabb, w.n_levels, w.n_slots)
+    return _lib.make_grid(bits_t, w.res, w.aabb, w.n_levels, w.n_slots, w.contraction)
 
 
 def gpu_march(w: synth.Workload, capacity=None, rays=None, n_levels=None):
@@ -46,7 +46,8 @@ def _run_march(o, d, bits, w, params, ws, capacity):
     ri = torch.full((capacity,), -1, dtype=torch.int32, device="cuda")
     total = torch.full((1,), -1, dtype=torch.int64, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    _lib.march_rays(o, d, _lib.make_grid(bits, w.res, w.aabb, w.n_levels, w.n_slots), params, packed, ts, te, ri,
+    _lib.march_rays(o, d, _lib.make_grid(bits, w.res, w.aabb, w.n_levels, w.n_slots, w.contraction), params, packed,
+                    ts, te, ri,
                     total, status, ws, ray_time=dev(w.ray_time), ray_slot=dev(w.ray_slot))
     torch.cuda.synchronize()
     n = int(total.item())
@@ -59,7 +60,8 @@ def oracle_march(orc, w: synth.Workload, rays=None):
     o = w.rays_o if rays is None else rays[0]
     d = w.rays_d if rays is None else rays[1]
     return orc.march(o, d, w.bits, w.res, w.aabb, w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone,
-                     w.max_steps, n_levels=w.n_levels, n_slots=w.n_slots, ray_time=w.ray_time, ray_slot=w.ray_slot)
+                     w.max_steps, n_levels=w.n_levels, n_slots=w.n_slots, ray_time=w.ray_time, ray_slot=w.ray_slot,
+                     contraction=w.contraction)
 
 
 def bits_equal(a, b):

@@ -14,11 +14,17 @@ if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no CUDA device", allow_module_level=True)
 
 
-def _host(seed, step, n, aabb, res, n_levels, n_slots):
+def _host(seed, step, n, aabb, res, n_levels, n_slots, contraction=0):
     cells, jit = synth.grid_update_samples(seed, step, n, res, n_levels, n_slots)
-    xyz = synth.cell_positions(cells, jit, aabb, res, n_levels)
+    xyz = synth.cell_positions(cells, jit, aabb, res, n_levels, contraction=contraction)
     assert xyz.dtype == np.float32
     return cells, xyz
+
+
+def _same_points(a, b):
+    """Bit-identical float32 points; NaN (unreachable contracted cells) compared as a mask."""
+    na, nb = np.isnan(a), np.isnan(b)
+    return np.array_equal(na, nb) and np.array_equal(a[~na].view(np.uint32), b[~nb].view(np.uint32))
 
 
 @pytest.mark.parametrize("res,n_levels,n_slots,aabb", [
@@ -34,6 +40,17 @@ def test_device_sampling_matches_host_generator(res, n_levels, n_slots, aabb):
         hc, hx = _host(seed, step, n, aabb, res, n_levels, n_slots)
         assert np.array_equal(cells.cpu().numpy(), hc)
         assert np.array_equal(xyz.cpu().numpy().view(np.uint32), hx.view(np.uint32))
+
+
+def test_contracted_grid_sampling_matches_host_generator():
+    """Cells and points of a contracted grid: drawn in [-2, 2]^3, mapped back to the world."""
+    aabb = (-125.0, -125.0, -125.0, 125.0, 125.0, 125.0)
+    g = api.OccupancyGrid(aabb, (64, 64, 64), 1, 2, contraction=1)
+    cells, xyz = g.sample_cells(1 << 16, 3, 1)
+    hc, hx = _host(3, 1, 1 << 16, aabb, (64, 64, 64), 1, 2, contraction=1)
+    assert np.array_equal(cells.cpu().numpy(), hc)
+    assert _same_points(xyz.cpu().numpy(), hx)
+    assert 0.4 < np.isnan(hx[:, 0]).mean() < 0.6  # the corners outside the radius-2 ball
 
 
 def test_fullsize_sampling_and_update_in_cells():

@@ -144,6 +144,49 @@ def test_cone_equal_step_bounds(orc):
     assert_march_equal(gpu_march(w), oracle_march(orc, w))
 
 
+@pytest.mark.parametrize("cone", [False, True])
+def test_contracted_space_random_rays(orc, cone):
+    """Unbounded scenes (Sec. 2.1 "Scene Contraction"): rays from inside and outside
+    the box, marched over [near, far] with no clip, looked up in contracted space."""
+    n = 700
+    o, d = _random_rays(16, n, spread=3.0, box=1.5)
+    o[:300] = synth.rand_uniform(16, 7, 900, -0.8, 0.8).reshape(300, 3)
+    res = (32, 32, 32)
+    occ = synth.rand_uniform(16, 5, 2 * 32 ** 3) < 0.4
+    slot = (synth.rand_uniform(16, 8, n) < 0.5).astype(np.int32)
+    if cone:
+        w = _workload(o, d, occ, res, (-1, -1, -1, 1, 1, 1), near=0.05, far=200.0, dt_min=1e-3, dt_max=1.0,
+                      cone=1.0 / 128, max_steps=4096)
+    else:
+        w = _workload(o, d, occ, res, (-1, -1, -1, 1, 1, 1), near=0.0, far=6.0, dt_min=0.004, dt_max=0.004,
+                      max_steps=2048)
+    w.n_slots, w.ray_slot, w.contraction = 2, slot, 1
+    g = gpu_march(w)
+    assert g[4] > 0
+    assert_march_equal(g, oracle_march(orc, w))
+
+
+def test_contracted_axis_case(orc):
+    """The oracle's analytic pin, on the GPU: only cell (14, 8, 8) of 16^3 is occupied,
+    the ray runs along +x from the centre with dt = 1/64: samples k = 128..255."""
+    occ = np.zeros((16, 16, 16), bool)
+    occ[14, 8, 8] = True
+    w = _workload(np.zeros((1, 3)), np.array([[1.0, 0.0, 0.0]]), occ.reshape(-1), (16, 16, 16),
+                  (-1, -1, -1, 1, 1, 1), near=0.0, far=100.0, dt_min=1.0 / 64, dt_max=1.0 / 64, max_steps=8192)
+    w.contraction = 1
+    g = gpu_march(w)
+    assert g[4] == 128
+    assert_march_equal(g, oracle_march(orc, w))
+
+
+def test_contracted_unbounded_scene(orc):
+    """The unbounded scene with a 128^3 contracted grid instead of the cascade (2^12 rays)."""
+    w = synth.contracted_config(0, n_rays=1 << 12, device="cuda")
+    g = gpu_march(w, capacity=12_000_000)
+    assert g[4] > 0
+    assert_march_equal(g, oracle_march(orc, w))
+
+
 @functools.lru_cache(maxsize=1)
 def _whole_batch(name):
     import oracle

@@ -312,3 +312,42 @@ def test_time_bins_and_slots(orc):
     slots = np.array([2, 0, 2, 3, 1, 2, 2, 0, 3], np.int32)
     p = orc.march(o, d, bits, res, aabb, 0.0, 1e10, 0.25, 0.25, 0.0, 100, n_slots=n_slots, ray_slot=slots)
     assert p.packed_info[:, 1].tolist() == [8 if s == 2 else 0 for s in slots]
+
+
+# ---------------------------------------------------------------------------
+# contracted unbounded space (Sec. 2.1 "Scene Contraction"; Mip-NeRF 360 Eq. 10)
+# ---------------------------------------------------------------------------
+
+
+def test_contraction_identity_inside_unit_ball(orc):
+    """Inside the unit ball the contraction is the identity: rays that stay inside
+    march exactly as on a plain grid over [-2, 2]^3 (u = (x + 2) res / 4 both ways)."""
+    res = (16, 16, 16)
+    occ = synth.rand_uniform(31, 1, 16 ** 3) < 0.5
+    bits = synth.pack_bits(occ)
+    n = 200
+    # |o| <= 0.25 sqrt(3) < 0.44 and t <= 0.5: every point stays inside the unit ball
+    o = synth.rand_uniform(31, 2, 3 * n, -0.25, 0.25).reshape(n, 3).astype(np.float32)
+    d = synth.random_unit_vectors(31, 3, n).astype(np.float32)
+    args = dict(near_plane=0.0, far_plane=0.5, dt_min=0.01, dt_max=0.01, max_steps=1024)
+    c = orc.march(o, d, bits, res, (-1, -1, -1, 1, 1, 1), contraction=1, **args)
+    p = orc.march(o, d, bits, res, (-2, -2, -2, 2, 2, 2), **args)
+    assert c.n_samples > 0
+    assert np.array_equal(c.packed_info, p.packed_info)
+    assert np.array_equal(c.t_starts, p.t_starts) and np.array_equal(c.ray_indices, p.ray_indices)
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_contraction_along_an_axis(orc, sign):
+    """On the x axis a point at distance t > 1 maps to x_c = 2 - 1/t. With 16 cells
+    over [-2, 2], cell 14 (cell 1 for -x) holds x_c in [1.5, 1.75): t in [2, 4). Only
+    that cell is occupied, dt = 1/64 from t = 0: the samples are exactly k = 128..255."""
+    res = (16, 16, 16)
+    occ = np.zeros((16, 16, 16), bool)
+    occ[14 if sign > 0 else 1, 8, 8] = True
+    o = np.zeros((1, 3), np.float32)
+    d = np.array([[sign, 0.0, 0.0]], np.float32)
+    m = orc.march(o, d, synth.pack_bits(occ.reshape(-1)), res, (-1, -1, -1, 1, 1, 1), near_plane=0.0,
+                  far_plane=100.0, dt_min=1.0 / 64, dt_max=1.0 / 64, max_steps=8192, contraction=1)
+    assert m.n_samples == 128
+    np.testing.assert_array_equal(m.t_starts, np.arange(128, 256, dtype=np.float32) / 64)

@@ -35,6 +35,9 @@ MUTANTS = [
     ("prune alpha on sigma, not sigma*delta", "float tau = sigmas[i] * delta;", "float tau = sigmas[i];"),
     ("grid decay dropped", "ema[c] = (float)((double)decay * (double)ema[c]);", "ema[c] = ema[c];"),
     ("grid NaN not ignored", "if (v == v && v > ema[c]) ema[c] = v;", "if (!(v <= ema[c])) ema[c] = v;"),
+    ("contraction without the 1/|x| factor", "float sc = (2.0f - 1.0f / n) / n;", "float sc = (2.0f - 1.0f / n);"),
+    ("contracted grid spans [-1, 1]", "u[a] = (xn[a] + 2.0f) * ((float)res[a] * 0.25f);",
+     "u[a] = (xn[a] + 1.0f) * ((float)res[a] * 0.5f);"),
     ("weights gradient uses T_k for T_{k+1}", "d_sigmas[off + k] = delta * (gk * Tn[k] - suffix);",
      "d_sigmas[off + k] = delta * (gk * T[k] - suffix);"),
     ("weights gradient suffix without the weights", "suffix += gk * w[k];", "suffix += gk;"),
