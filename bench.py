@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rays", type=int, default=N_RAYS)
     ap.add_argument("--workload", default="bounded",
-                    choices=["bounded", "tiny", "unbounded", "contracted", "batched", "dynamic"],
+                    choices=["bounded", "tiny", "unbounded", "contracted", "batched", "dynamic", "dynamic_shared"],
                     help="bounded (default) is the headline configuration; the others are the wider configurations")
     ap.add_argument("--no-batched-compare", action="store_true")
     ap.add_argument("--cpu-rays", type=int, default=1 << 15, help="rays in the CPU-baseline sample")
@@ -336,6 +336,8 @@ WORKLOAD_CONFIG = {
                    "alpha_thre": 1e-2},
     "batched": {"scenes": "64 (8-256 blobs each, own 128^3 grid)", "rays": "lognormal per scene, scene-major",
                 "dt": "sqrt(3)*3/1024, max 1024 steps", "early_stop_eps": 1e-4, "alpha_thre": 1e-2},
+    "dynamic_shared": {"scene": "128 moving blobs, t in [0,1]", "grid": "one 128^3 grid for all times (OR of 16 bins)",
+                       "dt": "sqrt(3)*3/1024, max 1024 steps", "early_stop_eps": 1e-4, "alpha_thre": 1e-2},
     "dynamic": {"scene": "128 moving blobs, t in [0,1]", "grid": "16 time bins x 128^3",
                 "dt": "sqrt(3)*3/1024, max 1024 steps", "early_stop_eps": 1e-4, "alpha_thre": 1e-2},
 }

@@ -12,6 +12,7 @@ time of the point). Workloads:
 * ``contracted`` the unbounded scene and rays, one 128^3 grid over contracted space
 * ``batched``   64 scenes (8-256 blobs, own 128^3 grid each), lognormal rays per scene
 * ``dynamic``   2^19 rays over 16 time bins of 128 moving blobs, one grid per bin
+* ``dynamic_shared`` the same with one grid for all times (maximum over time)
 """
 from __future__ import annotations
 
@@ -173,6 +174,9 @@ def make_scenario(name: str, rank: int = 0, device="cuda", n_rays=None, pool: in
     if name == "batched":
         w = synth.batched_config(0, device=device)
         return Scenario(name, [w], w.scenes, device, rank=rank)
+    if name == "dynamic_shared":
+        ws = [synth.dynamic_shared_config(0, n_rays=n_rays or (1 << 19), device=device, batch=b) for b in batches[:2]]
+        return Scenario(name, ws, ws[0].scenes, device, rank=rank)
     if name == "dynamic":
         ws = [synth.dynamic_config(0, n_rays=n_rays or (1 << 19), device=device, batch=b) for b in batches[:2]]
         return Scenario(name, ws, ws[0].scenes, device, rank=rank)

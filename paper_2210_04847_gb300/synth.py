@@ -549,6 +549,18 @@ def dynamic_config(seed: int = 0, n_rays: int = 1 << 19, n_bins: int = 16, devic
     )
 
 
+def dynamic_shared_config(seed: int = 0, n_rays: int = 1 << 19, n_bins: int = 16, device="cpu",
+                          batch: int = 0) -> Workload:
+    """The dynamic scene and rays with one grid shared by all times (the paper's
+    D-NeRF setting, Sec. 4: the grid holds the maximum over time): the bitwise OR
+    of the per-bin grids of ``dynamic_config``."""
+    w = dynamic_config(seed, n_rays=n_rays, n_bins=n_bins, device=device, batch=batch)
+    w.bits = np.bitwise_or.reduce(w.bits.reshape(n_bins, -1), axis=0)
+    w.n_slots = 1
+    w.name = "dynamic-shared-grid128"
+    return w
+
+
 def grid_update_samples(seed: int, step: int, n: int, res, n_levels: int = 1, n_slots: int = 1):
     """Uniform random cells (with replacement) and float32 jitters in [0, 1)^3 for
     one grid update. Sample i takes draws 2i, 2i+1 of stream 50000 + 4*step for

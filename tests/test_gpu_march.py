@@ -149,3 +149,10 @@ def test_lattice_point_counter(orc, cfg):
     full = orc.march(w.rays_o, w.rays_d, ones, w.res, w.aabb, w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone,
                      w.max_steps, n_levels=w.n_levels, n_slots=w.n_slots)
     assert counted == full.n_samples > 0
+
+
+def test_shared_time_grid_bitexact(orc):
+    """One grid for all times (the maximum over time) with per-ray times: every ray reads slot 0."""
+    w = synth.dynamic_shared_config(0, n_rays=1 << 11, device="cuda")
+    assert w.n_slots == 1 and w.ray_time is not None
+    assert_march_equal(gpu_march(w), oracle_march(orc, w))
