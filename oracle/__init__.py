@@ -63,6 +63,13 @@ def lib():
         L.oracle_accumulate_bwd.argtypes = [P, i32, P, P, i32, P, P, P]
         L.oracle_unpack_info.argtypes = [P, i32, P]
         L.oracle_update_grid.argtypes = [P, P, i64, P, P, i64, f32, f32]
+        L.oracle_field_sigma.restype = f32
+        L.oracle_field_sigma.argtypes = [P, P, P, P]
+        L.oracle_field_query.restype = ctypes.c_int
+        L.oracle_field_query.argtypes = [P, P, P, P, i64, P]
+        L.oracle_march_fused.restype = i64
+        L.oracle_march_fused.argtypes = [P, P, i32, P, P, i32, P, f32, f32, f32, f32, f32, i32, i32, P, P, P, f32,
+                                         f32, P, P, P, P, P, i64]
         for f in ("oracle_render_weights", "oracle_accumulate", "oracle_render_fwd", "oracle_render_bwd",
                   "oracle_render_weights_bwd", "oracle_accumulate_bwd",
                   "oracle_unpack_info", "oracle_update_grid"):
@@ -230,3 +237,46 @@ def update_grid(ema, cells, sigmas, decay, thre):
     if lib().oracle_update_grid(_p(e), _p(bits), e.size, _p(c), _p(s), c.size, decay, thre) != 0:
         raise ValueError("cell index out of range")
     return e, bits
+
+
+def field_query(field, field_box, xyz):
+    """Density field of the fused path (F1 in oracle.c): trilinear between the
+    vertex values field[i, j, k] of a lattice over field_box = (lo, hi), zero
+    outside; float32 replica. Returns sigma (n,) float32."""
+    g = _c(field, np.float32)
+    G = np.ascontiguousarray(np.asarray(g.shape, dtype=np.int32).reshape(3))
+    box = np.ascontiguousarray(np.asarray(field_box, dtype=np.float32).reshape(6))
+    x = _c(xyz, np.float32).reshape(-1, 3)
+    out = np.zeros(x.shape[0], np.float32)
+    if lib().oracle_field_query(_p(g), _p(G), _p(box), _p(x), x.shape[0], _p(out)) != 0:
+        raise ValueError("oracle_field_query: invalid field")
+    return out
+
+
+def march_fused(rays_o, rays_d, bits, res, aabb, field, field_box, early_stop_eps, alpha_thre, near_plane=0.0,
+                far_plane=1e10, dt_min=1e-2, dt_max=None, cone=0.0, max_steps=1024, n_levels=1, contraction=0):
+    """Fused march + density + prune for inference (F2 in oracle.c, Sec. 2.1):
+    what prune() keeps of march()'s samples with sigma = field_query() at each
+    sample's midpoint. Returns (Packed of the kept samples, sigmas (S,) float32)."""
+    o = _c(rays_o, np.float32).reshape(-1, 3)
+    d = _c(rays_d, np.float32).reshape(-1, 3)
+    R = o.shape[0]
+    bits = _c(bits, np.uint32)
+    res = np.ascontiguousarray(np.asarray(res, dtype=np.int32).reshape(3))
+    box = np.ascontiguousarray(np.asarray(aabb, dtype=np.float32).reshape(6))
+    g = _c(field, np.float32)
+    G = np.ascontiguousarray(np.asarray(g.shape, dtype=np.int32).reshape(3))
+    fbox = np.ascontiguousarray(np.asarray(field_box, dtype=np.float32).reshape(6))
+    dt_max = dt_min if dt_max is None else dt_max
+    pi = np.zeros((R, 2), dtype=np.int32)
+    args = lambda ts, te, ri, sg, cap: (
+        _p(o), _p(d), R, _p(bits), _p(res), n_levels, _p(box), near_plane, far_plane, dt_min, dt_max, cone,
+        max_steps, int(contraction), _p(g), _p(G), _p(fbox), early_stop_eps, alpha_thre, _p(pi), _p(ts), _p(te),
+        _p(ri), _p(sg), cap)
+    n = lib().oracle_march_fused(*args(None, None, None, None, 0))
+    if n < 0:
+        raise ValueError("oracle_march_fused: invalid arguments")
+    ts, te, sg = np.empty(n, np.float32), np.empty(n, np.float32), np.empty(n, np.float32)
+    ri = np.empty(n, np.int32)
+    assert lib().oracle_march_fused(*args(ts, te, ri, sg, n)) == n
+    return Packed(pi, ts, te, ri), sg

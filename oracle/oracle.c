@@ -23,6 +23,8 @@
  *   grid update      float64 product of two float32 numbers (exact), stored to
  *                    the float32 state grid (so it equals a correctly rounded
  *                    float32 product); bits thresholded on the stored value.
+ *   density field    float32 replica of a fixed operation order (its values
+ *                    feed the fused path's keep decision, an integer result).
  *
  * Readings of the paper (it is silent on all of these):
  *   M1 ray-box clip: slab test per axis in float32; an axis with d == 0 keeps
@@ -53,6 +55,10 @@
  *   R5 gradient (ours, calculus on Eq. 1): with a_i = <g_C, rgb_i> + g_A +
  *      g_D tmid_i, dL/dtau_k = a_k T_{k+1} - sum_{i>k} a_i w_i,
  *      dL/dsigma_k = delta_k dL/dtau_k, dL/drgb_k = w_k g_C.
+ *   F1 density field of the fused inference path: trilinear between the
+ *      vertex values of a lattice over a box, zero outside (see F1 below).
+ *   F2 fused march + prune: V1 applied to the M1-M4 samples with F1's sigma
+ *      at each sample's midpoint (see F2 below).
  *   G2 grid update: ema <- decay*ema for every cell, then
  *      ema[c] <- max(ema[c], sigma_s) for each sample s in cell c (NaN sigma
  *      ignored); bits = ema > thre.
@@ -498,4 +504,113 @@ int oracle_update_grid(float* ema, uint32_t* bits, int64_t n_cells, const int32_
     for (int64_t c = 0; c < n_cells; ++c)
         if (ema[c] > thre) bits[c >> 5] |= 1u << (c & 31);
     return 0;
+}
+
+/* ----- density field and the fused march + prune (inference) ------------- */
+
+/* F1: the density field of the fused path is a grid of sigma values at the
+ * vertices of a G0 x G1 x G2 lattice over the box [lo, hi] (vertex (i, j, k) at
+ * lo + (hi - lo) * (i, j, k) / (G - 1), z fastest in memory), interpolated
+ * trilinearly between vertices, and zero outside the box. Float32 in this order:
+ * s_a = (G_a - 1) / (hi_a - lo_a); u_a = (x_a - lo_a) * s_a; outside unless
+ * 0 <= u_a <= G_a - 1; i_a = min(floor(u_a), G_a - 2); f_a = u_a - i_a;
+ * lerp(p, q, f) = p + f * (q - p) along z, then y, then x. */
+static float or_lerp(float p, float q, float f) { return p + f * (q - p); }
+
+float oracle_field_sigma(const float* grid, const int32_t G[3], const float box[6], const float x[3]) {
+    int i[3];
+    float f[3];
+    for (int a = 0; a < 3; ++a) {
+        float s = (float)(G[a] - 1) / (box[3 + a] - box[a]);
+        float u = (x[a] - box[a]) * s;
+        if (!(u >= 0.0f && u <= (float)(G[a] - 1))) return 0.0f;
+        i[a] = (int)floorf(u);
+        if (i[a] > G[a] - 2) i[a] = G[a] - 2;
+        f[a] = u - (float)i[a];
+    }
+    float v[2][2][2];
+    for (int dx = 0; dx < 2; ++dx)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dz = 0; dz < 2; ++dz)
+                v[dx][dy][dz] = grid[((int64_t)(i[0] + dx) * G[1] + (i[1] + dy)) * G[2] + (i[2] + dz)];
+    float c00 = or_lerp(v[0][0][0], v[0][0][1], f[2]);
+    float c01 = or_lerp(v[0][1][0], v[0][1][1], f[2]);
+    float c10 = or_lerp(v[1][0][0], v[1][0][1], f[2]);
+    float c11 = or_lerp(v[1][1][0], v[1][1][1], f[2]);
+    float c0 = or_lerp(c00, c01, f[1]);
+    float c1 = or_lerp(c10, c11, f[1]);
+    return or_lerp(c0, c1, f[0]);
+}
+
+static int or_field_ok(const int32_t G[3], const float box[6]) {
+    for (int a = 0; a < 3; ++a)
+        if (G[a] < 2 || !(box[a] < box[3 + a])) return 0;
+    return 1;
+}
+
+int oracle_field_query(const float* grid, const int32_t G[3], const float box[6], const float* xyz, int64_t n,
+                       float* sigmas) {
+    if (!or_field_ok(G, box)) return -1;
+    for (int64_t s = 0; s < n; ++s) sigmas[s] = oracle_field_sigma(grid, G, box, xyz + 3 * s);
+    return 0;
+}
+
+/* F2, the fused path (Sec. 2.1 "Pruning Empty and Occluded Regions": the
+ * transmittance is taken from the field's density while marching, and marching
+ * ends where it falls below eps). Its result is, by definition, what V1 keeps of
+ * the samples M1-M4 emit, with sigma_i = F1 at the midpoint x = o + d*mid that
+ * M3 looks up: the march stops where the optical depth passes -ln(eps), which
+ * changes the work done but not the samples kept. Written here as exactly that
+ * composition. sigmas_out (nullable) receives sigma of each kept sample. */
+int64_t oracle_march_fused(const float* rays_o, const float* rays_d, int32_t n_rays, const uint32_t* bits,
+                           const int32_t res[3], int32_t n_levels, const float aabb[6], float near_plane,
+                           float far_plane, float dt_min, float dt_max, float cone, int32_t max_steps,
+                           int32_t contraction, const float* field, const int32_t G[3], const float fbox[6],
+                           float early_stop_eps, float alpha_thre, int32_t* packed_info_out, float* t_starts_out,
+                           float* t_ends_out, int32_t* ray_indices_out, float* sigmas_out, int64_t capacity) {
+    if (!or_field_ok(G, fbox)) return -1;
+    int32_t* pi = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)(n_rays > 0 ? n_rays : 1));
+    if (!pi) return -1;
+    int64_t m = oracle_march(rays_o, rays_d, NULL, NULL, n_rays, bits, res, n_levels, 1, aabb, near_plane, far_plane,
+                             dt_min, dt_max, cone, max_steps, contraction, pi, NULL, NULL, NULL, 0);
+    if (m < 0) {
+        free(pi);
+        return -1;
+    }
+    size_t mm = (size_t)(m > 0 ? m : 1);
+    float* ts = (float*)malloc(sizeof(float) * mm);
+    float* te = (float*)malloc(sizeof(float) * mm);
+    int32_t* ri = (int32_t*)malloc(sizeof(int32_t) * mm);
+    float* sg = (float*)malloc(sizeof(float) * mm);
+    uint8_t* keep = (uint8_t*)malloc(mm);
+    int64_t total = -1;
+    if (ts && te && ri && sg && keep) {
+        oracle_march(rays_o, rays_d, NULL, NULL, n_rays, bits, res, n_levels, 1, aabb, near_plane, far_plane, dt_min,
+                     dt_max, cone, max_steps, contraction, pi, ts, te, ri, m);
+        for (int64_t i = 0; i < m; ++i) {
+            const float* o = rays_o + 3 * (int64_t)ri[i];
+            const float* d = rays_d + 3 * (int64_t)ri[i];
+            float mid = (ts[i] + te[i]) * 0.5f;
+            float x[3];
+            for (int a = 0; a < 3; ++a) x[a] = o[a] + d[a] * mid;
+            sg[i] = oracle_field_sigma(field, G, fbox, x);
+        }
+        total = oracle_prune(pi, n_rays, ts, te, sg, early_stop_eps, alpha_thre, keep, NULL, packed_info_out,
+                             t_starts_out, t_ends_out, ray_indices_out, capacity);
+        if (sigmas_out) {
+            int64_t j = 0;
+            for (int64_t i = 0; i < m; ++i)
+                if (keep[i]) {
+                    if (j < capacity) sigmas_out[j] = sg[i];
+                    ++j;
+                }
+        }
+    }
+    free(pi);
+    free(ts);
+    free(te);
+    free(ri);
+    free(sg);
+    free(keep);
+    return total;
 }

@@ -1,7 +1,7 @@
 """The oracle's pins have teeth: each plausible mistake below, planted in a copy of
-oracle.c compiled on the CPU, makes at least one pin in test_oracle_march.py or
-test_oracle_render.py fail. (Mistakes are planted only in the oracle, never in the
-CUDA path, and only on the CPU.)
+oracle.c compiled on the CPU, makes at least one pin in test_oracle_march.py,
+test_oracle_render.py or test_oracle_fused.py fail. (Mistakes are planted only in
+the oracle, never in the CUDA path, and only on the CPU.)
 """
 import os
 import subprocess
@@ -45,6 +45,17 @@ MUTANTS = [
      "d_values[i * n_channels + c] = g;"),
     ("accumulate gradient of weights ignores values", "dw += values ? g * (double)values[i * n_channels + c] : g;",
      "dw += g;"),
+    ("density lerp along y uses the z fraction", "float c0 = or_lerp(c00, c01, f[1]);",
+     "float c0 = or_lerp(c00, c01, f[2]);"),
+    ("density vertices x-fastest", "grid[((int64_t)(i[0] + dx) * G[1] + (i[1] + dy)) * G[2] + (i[2] + dz)]",
+     "grid[((int64_t)(i[2] + dz) * G[1] + (i[1] + dy)) * G[0] + (i[0] + dx)]"),
+    ("density scale by G, not G - 1", "float s = (float)(G[a] - 1) / (box[3 + a] - box[a]);",
+     "float s = (float)G[a] / (box[3 + a] - box[a]);"),
+    ("density far face outside", "if (!(u >= 0.0f && u <= (float)(G[a] - 1))) return 0.0f;",
+     "if (!(u >= 0.0f && u < (float)(G[a] - 1))) return 0.0f;"),
+    ("fused density at interval start", "float mid = (ts[i] + te[i]) * 0.5f;", "float mid = ts[i];"),
+    ("fused sigma output not compacted", "if (j < capacity) sigmas_out[j] = sg[i];",
+     "if (j < capacity) sigmas_out[j] = sg[j];"),
 ]
 
 
@@ -61,6 +72,7 @@ def test_mutant_is_caught(tmp_path, name, old, new):
                            "-o", str(lib), str(cpath), "-lm"])
     env = dict(os.environ, NACC_ORACLE_LIB_OVERRIDE=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(HERE, "test_oracle_march.py"), os.path.join(HERE, "test_oracle_render.py")],
+                        os.path.join(HERE, "test_oracle_march.py"), os.path.join(HERE, "test_oracle_render.py"),
+                        os.path.join(HERE, "test_oracle_fused.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "mutant '%s' survived every pin:\n%s" % (name, r.stdout[-2000:])
