@@ -81,13 +81,14 @@ struct MarchArgs {
 __device__ __forceinline__ bool finite32(float v) { return fabsf(v) <= 3.402823466e+38f; }
 
 // Slab clip against the outermost level box, float32 (ties and zero
-// directions as the oracle defines them).
+// directions as the oracle defines them). CONTRACT: contracted space has no box.
+template <bool CONTRACT>
 __device__ __forceinline__ bool clip_ray(const MarchArgs& a, const float o[3], const float d[3],
                                          float& near, float& far) {
 #pragma unroll
     for (int k = 0; k < 3; ++k)
         if (!finite32(o[k]) || !finite32(d[k])) return false;
-    if (a.contract) {  // unbounded: the whole [near_plane, far_plane]
+    if (CONTRACT) {  // unbounded: the whole [near_plane, far_plane]
         near = a.near_plane;
         far = a.far_plane;
         return near < far;
@@ -581,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
             cur.nr = min(a.tile_rays, a.n_rays - cur.ray0);
             int my_count = 0, my_nch = 0;
             float my_near = 0.0f, my_far = 0.0f;
-            long long tile_pts = 0;
+            int tile_pts = 0;  // at most tile_rays * max_steps
             for (int i = 0; i < cur.nr; ++i) {
                 const int r = cur.ray0 + i;
                 float o[3], d[3];
@@ -595,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
                 const int slot = slot_of(a, r);
                 const bool slot_ok = slot >= 0 && slot < a.n_slots;
                 if (!slot_ok && lane == 0) raise_status(a.d_status, NACC_STATUS_BAD_INDEX);
-                if (slot_ok && clip_ray(a, o, d, near, far))
+                if (slot_ok && clip_ray<MAXL == 0>(a, o, d, near, far))
                     walk_lattice<MAXL, CONE, UNROLL2, COARSE>(a, o, d, near, far,
                                                               (unsigned)slot * (unsigned)a.n_levels,
                                                               wmask + i * a.row_stride, lat, lane, count, nch, pts);
@@ -747,7 +748,7 @@ void launch_variant(bool cone, bool unroll, bool coarse, size_t smem, int need, 
 template <int MAXL>
 void launch_walk(bool cone, bool occ, bool unroll, bool coarse, size_t smem, int need, cudaStream_t st,
                  const MarchArgs& a) {
-    if (occ) launch_variant<MAXL, 8>(cone, unroll, coarse, smem, need, st, a);
+    if (occ) launch_variant<MAXL, 4>(cone, unroll, coarse, smem, need, st, a);
     else launch_variant<MAXL, 1>(cone, unroll, coarse, smem, need, st, a);
 }
 
