@@ -68,13 +68,18 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rays", type=int, default=N_RAYS)
     ap.add_argument("--workload", default="bounded",
-                    choices=["bounded", "tiny", "unbounded", "contracted", "batched", "dynamic", "dynamic_shared"],
-                    help="bounded (default) is the headline configuration; the others are the wider configurations")
+                    choices=["bounded", "tiny", "unbounded", "contracted", "batched", "dynamic", "dynamic_shared",
+                             "inference"],
+                    help="bounded (default) is the headline configuration; the others are the wider configurations "
+                         "(inference: the fused march with the density field's transmittance + render forward)")
     ap.add_argument("--no-batched-compare", action="store_true")
     ap.add_argument("--cpu-rays", type=int, default=1 << 15, help="rays in the CPU-baseline sample")
     ap.add_argument("--ref-rays", type=int, default=1 << 12, help="rays per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--pixel-stride", type=int, default=1,
+                    help="inference workload: every n-th pixel of each image (smaller cases for profiling)")
+    ap.add_argument("--no-two-call", action="store_true", help="inference workload: skip the two-call comparison")
     ap.add_argument("--knobs", default="", help="fixed launch-shape knobs, e.g. march_tile_rays=8,prune_tile_rays=8 "
                     "(skips the autotuner)")
     return ap.parse_args()
@@ -537,6 +542,264 @@ def run_ours(args):
     return 0
 
 
+INFER_METRIC = "rays/s (inference: march with the density field's transmittance + render fwd) on one GB300"
+
+
+def run_inference(args):
+    """Inference on whole 800x800 images of the bounded scene: nacc_march_fused
+    (marching that evaluates the baked density grid and stops each ray where
+    T < 1e-4, writing only the kept samples) + render forward, timed beside the
+    two-call path on the same images (march -> density at the marched samples ->
+    prune -> density at the kept samples -> render forward). The colour of the kept
+    samples comes from the stand-in field (the user's network, untimed)."""
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    from paper_2210_04847_gb300 import _lib, autotune, synth
+    from paper_2210_04847_gb300.pipeline import StandInField, to_device
+
+    sg = synth.bounded_scene(0, device=dev)
+    wls = [synth.inference_config(0, camera=rank * POOL + b, scene_grid=sg) for b in range(POOL)]
+    if args.pixel_stride > 1:
+        for x in wls:
+            x.rays_o = np.ascontiguousarray(x.rays_o[::args.pixel_stride])
+            x.rays_d = np.ascontiguousarray(x.rays_d[::args.pixel_stride])
+    w = wls[0]
+    R = w.n_rays
+    eps, thre = w.early_stop_eps, w.alpha_thre
+    field = StandInField(sg[0], dev)
+    dens = to_device(w.field, dev)
+    fld = _lib.make_density_field(dens, w.field_box)
+    bits = to_device(w.bits, dev)
+    grid = _lib.make_grid(bits, w.res, w.aabb, 1, 1, 0)
+    params = _lib.make_params(w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone, w.max_steps)
+    batches = [(to_device(x.rays_o, dev), to_device(x.rays_d, dev)) for x in wls]
+    f32, i32 = torch.float32, torch.int32
+    z = lambda n, dt=f32: torch.zeros(max(int(n), 1), dtype=dt, device=dev)
+    ws_m = z(_lib.march_workspace_size(R, params), torch.uint8)
+    st = z(1, i32)
+    cnt = z(1, torch.int64)
+    pi_f, pi_m, pi_k = (torch.zeros((R, 2), dtype=i32, device=dev) for _ in range(3))
+    e = z(0)
+    # sizes: both marchers report their totals with capacity 0 (nothing written)
+    M_max = S_max = 0
+    for o, d in batches:
+        if not args.no_two_call:
+            _lib.march_rays(o, d, grid, params, pi_m, e, e, z(0, i32), cnt, st, ws_m)
+            M_max = max(M_max, int(cnt.item()))
+        _lib.march_fused(o, d, grid, params, fld, eps, thre, pi_f, e, e, z(0, i32), None, cnt, st, ws_m)
+        S_max = max(S_max, int(cnt.item()))
+    st.zero_()
+    cap_m, cap_s = int(M_max * 1.02) + 4096, int(S_max * 1.05) + 4096
+    ts_f, te_f, ri_f, sg_f = z(cap_s), z(cap_s), z(cap_s, i32), z(cap_s)
+    ts_m, te_m, ri_m, sg_m = z(cap_m), z(cap_m), z(cap_m, i32), z(cap_m)
+    ts_k, te_k, ri_k, sg_k = z(cap_s), z(cap_s), z(cap_s, i32), z(cap_s)
+    ws_p = z(_lib.prune_workspace_size(R, cap_m), torch.uint8)
+    rgb, tmp = torch.zeros((cap_s, 3), dtype=f32, device=dev), z(cap_s)
+    color, opacity, depth = torch.zeros((R, 3), dtype=f32, device=dev), z(R), z(R)
+    n_f, n_m, n_k = z(1, torch.int64), z(1, torch.int64), z(1, torch.int64)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    evs = lambda k: [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+
+    def fused_step(i):
+        o, d = batches[i % POOL]
+        flush.zero_()
+        ev = evs(4)
+        ev[0].record()
+        _lib.march_fused(o, d, grid, params, fld, eps, thre, pi_f, ts_f, te_f, ri_f, sg_f, n_f, st, ws_m)
+        ev[1].record()
+        S = int(n_f.item())
+        field.samples(o, d, ri_f, ts_f, te_f, S, tmp, rgb)  # the user's network: colour of the kept samples
+        ev[2].record()
+        _lib.render_fwd(pi_f, ts_f, te_f, sg_f, rgb, S, color, opacity, depth, d_status=st)
+        ev[3].record()
+        torch.cuda.synchronize()
+        if int(st.item()) != 0 or S > cap_s:
+            raise RuntimeError("fused step %d: status 0x%x, %d samples" % (i, int(st.item()), S))
+        lat = int(ws_m[8:16].cpu().numpy().view(np.uint64)[0])
+        return {"march_fused": ev[0].elapsed_time(ev[1]), "render_fwd": ev[2].elapsed_time(ev[3])}, S, lat
+
+    def two_call_step(i):
+        o, d = batches[i % POOL]
+        flush.zero_()
+        ev = evs(8)
+        ev[0].record()
+        _lib.march_rays(o, d, grid, params, pi_m, ts_m, te_m, ri_m, n_m, st, ws_m)
+        ev[1].record()
+        M = int(n_m.item())
+        ev[2].record()
+        _lib.density_field_at_samples(fld, o, d, ri_m, ts_m, te_m, M, sg_m, st)
+        _lib.prune_samples(pi_m, ts_m, te_m, sg_m, M, eps, thre, pi_k, ts_k, te_k, ri_k, n_k, st, ws_p)
+        ev[3].record()
+        S = int(n_k.item())
+        field.samples(o, d, ri_k, ts_k, te_k, S, tmp, rgb)
+        ev[4].record()
+        _lib.density_field_at_samples(fld, o, d, ri_k, ts_k, te_k, S, sg_k, st)
+        _lib.render_fwd(pi_k, ts_k, te_k, sg_k, rgb, S, color, opacity, depth, d_status=st)
+        ev[5].record()
+        torch.cuda.synchronize()
+        if int(st.item()) != 0 or M > cap_m or S > cap_s:
+            raise RuntimeError("two-call step %d: status 0x%x" % (i, int(st.item())))
+        return {"march": ev[0].elapsed_time(ev[1]), "density_prune": ev[2].elapsed_time(ev[3]),
+                "density_render_fwd": ev[4].elapsed_time(ev[5])}, M, S
+
+    # launch shape of the fused kernel: register cap and rays per warp tile, timed on
+    # the first image (median of 5, L2 flushed before each run)
+    tuning = {}
+    if args.knobs:
+        for kv in args.knobs.split(","):
+            k, v = kv.split("=")
+            _lib.tune_set(k.strip(), int(v))
+    else:
+        o0, d0 = batches[0]
+
+        def fused_once():
+            _lib.march_fused(o0, d0, grid, params, fld, eps, thre, pi_f, ts_f, te_f, ri_f, sg_f, n_f, st, ws_m)
+
+        for knob, cands in (("fused_occupancy", (0, 1)), ("march_tile_rays", (2, 4, 8, 16))):
+            ms = {}
+            for v in cands:
+                _lib.tune_set(knob, v)
+                ms[v] = autotune.time_ms(fused_once, reps=5, warmup=1, before=flush.zero_)
+            best = min(ms, key=ms.get)
+            _lib.tune_set(knob, best)
+            tuning[knob] = {str(k): round(v, 4) for k, v in ms.items()}
+    for i in range(args.warmup):
+        fused_step(i)
+        if not args.no_two_call:
+            two_call_step(i)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    clocks = ClockSampler(int(vis) if vis.isdigit() else local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    fused = [fused_step(args.warmup + i) for i in range(args.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    two = [] if args.no_two_call else [two_call_step(args.warmup + i) for i in range(args.steps)]
+
+    avg = lambda rows, k: sum(r[0][k] for r in rows) / len(rows)
+    f_ms = {k: avg(fused, k) for k in ("march_fused", "render_fwd")}
+    t_ms = {k: avg(two, k) for k in ("march", "density_prune", "density_render_fwd")} if two else {}
+    mean_ms = sum(f_ms.values())
+    mean_two = sum(t_ms.values())
+    mean_ms_all = max_over_ranks(mean_ms, world, dev)
+    value = sum_over_ranks(R, world, dev) / (mean_ms_all / 1e3)
+    S = sum(r[1] for r in fused) / len(fused)
+    lat = sum(r[2] for r in fused) / len(fused)
+    M2 = sum(r[1] for r in two) / len(two) if two else 0
+    S2 = sum(r[2] for r in two) / len(two) if two else 0
+    field_bytes = 4 * int(np.prod(w.field.shape))
+    grid_bytes = (int(np.prod(w.res)) + 7) // 8
+    # read rays (24R), write packed_info (8R) and (t_start, t_end, ray, sigma) per kept sample (16S), read
+    # the bitfield and the density lattice once
+    fused_bytes = 24 * R + 8 * R + 16 * S + grid_bytes + field_bytes
+    render_bytes = 8 * R + 24 * S + 20 * R
+    peak, peak_kind = measured_peaks()
+    achieved = fused_bytes / (f_ms["march_fused"] / 1e3) / 1e9
+    if rank != 0:
+        return 0
+    line = {
+        "metric": INFER_METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms_all, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "rays_per_step_per_gpu": R,
+                   "images": "one whole 800x800 image per step (fx=fy=1111.1, camera on r=4), %d cameras cycled"
+                             % POOL,
+                   "pixel_stride": args.pixel_stride,
+                   "scene": "64 Gaussian blobs", "grid": "128^3 bitfield over [-1.5,1.5]^3 (density > 0.01)",
+                   "density_field": "blob density baked at 129^3 lattice vertices, trilinear",
+                   "dt": "sqrt(3)*3/1024, max 1024 steps", "early_stop_eps": eps, "alpha_thre": thre,
+                   "parallelism": "images sharded per GPU (weak), %d GPU(s)" % world,
+                   "l2": "flushed before every step (256 MB write)",
+                   "timed": "march_fused + render_fwd (the colour query is user code, untimed)"},
+        "tuned": {k: _lib.tune_get(k) for k in ("fused_occupancy", "march_tile_rays")},
+        "tuning_ms": tuning,
+        "stages_ms": {k: round(v, 4) for k, v in f_ms.items()},
+        "samples_per_step": {"kept": round(S), "lattice_points": round(lat)},
+        "rates": {"kept_samples_per_s": round(S / (mean_ms / 1e3)),
+                  "march_lattice_steps_per_s": round(lat / (f_ms["march_fused"] / 1e3))},
+        "step_hbm": {"algorithmic_bytes": int(fused_bytes + render_bytes),
+                     "gbs": round((fused_bytes + render_bytes) / (mean_ms / 1e3) / 1e9, 1),
+                     "frac": round((fused_bytes + render_bytes) / (mean_ms / 1e3) / 1e9 / peak, 4),
+                     "peak_gbs": peak, "peak_kind": peak_kind},
+        "roofline": {"bound": "hbm", "kernel": "march_fused", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                     "algorithmic_bytes": int(fused_bytes),
+                     "limiter": "issue: bit-exact float32 lattice arithmetic plus the trilinear density per "
+                                "occupied point"},
+        "two_call": None if not two else {"ms_per_step": round(mean_two, 4), "rays_per_s": R / (mean_two / 1e3),
+                     "stages_ms": {k: round(v, 4) for k, v in t_ms.items()},
+                     "samples_written": round(M2 + S2), "kept": round(S2),
+                     "note": "march -> density at the marched samples -> prune -> density at the kept samples -> "
+                             "render fwd, same images, timed after the fused loop"},
+        "fused_speedup": round(mean_two / mean_ms, 3) if two else None,
+        "samples_written_fused_vs_two_call": [round(S), round(M2 + S2)],
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "cpu_baseline": None,
+        "e2e": None if args.no_e2e else run_inference_e2e(args, dev, wls, sg, field),
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_inference_e2e(args, dev, wls, sg, field):
+    """The inference step through the public API: rays copied from pinned host
+    memory, api.march_with_density, the colour query (user code, timed by events and
+    subtracted), api.render_packed without autograd, colours copied back."""
+    import torch
+
+    from paper_2210_04847_gb300 import api
+
+    w = wls[0]
+    R = w.n_rays
+    grid = api.OccupancyGrid.from_bits(sg[2], w.res, w.aabb, device=dev)
+    dens = api.DensityGrid(torch.from_numpy(w.field).to(dev), w.field_box)
+    host = [(torch.from_numpy(x.rays_o).pin_memory(), torch.from_numpy(x.rays_d).pin_memory()) for x in wls]
+    out_host = torch.empty((R, 3), dtype=torch.float32).pin_memory()
+
+    def one(i):
+        ho, hd = host[i % len(host)]
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record()
+        o = ho.to(dev, non_blocking=True)
+        d = hd.to(dev, non_blocking=True)
+        packed, ts, te, sig, ri = api.march_with_density(o, d, grid, dens, render_step_size=w.dt_min,
+                                                         max_steps=w.max_steps, early_stop_eps=w.early_stop_eps,
+                                                         alpha_thre=w.alpha_thre, return_ray_indices=True)
+        n = ts.shape[0]
+        e[1].record()
+        rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        tmp = torch.empty(n, dtype=torch.float32, device=dev)
+        field.samples(o, d, ri, ts.view(-1), te.view(-1), n, tmp, rgb)
+        e[2].record()
+        with torch.no_grad():
+            color, _, _ = api.render_packed(sig.view(-1), rgb, packed, ts, te)
+        out_host.copy_(color, non_blocking=True)
+        e[3].record()
+        torch.cuda.synchronize()
+        return e[0].elapsed_time(e[3]) - e[1].elapsed_time(e[2])
+
+    for i in range(args.warmup):
+        one(i)
+    ms = [one(args.warmup + i) for i in range(args.steps)]
+    mean = sum(ms) / len(ms)
+    return {"value": R / (mean / 1e3), "unit": "rays/s", "ms_per_step": round(mean, 4),
+            "h2d_bytes_per_step": 24 * R, "d2h_bytes_per_step": 12 * R,
+            "note": "public API (march_with_density + render_packed), host-pinned rays in, colours out; the colour "
+                    "query is timed by events and subtracted"}
+
+
 def run_graph(args, sc, hp):
     """The whole step (march, field, prune, field, render fwd, loss, render bwd) over
     all scenes captured once in a CUDA graph and replayed: no host synchronisation,
@@ -739,6 +1002,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "inference":
+        return run_inference(args)
     return run_ours(args)
 
 

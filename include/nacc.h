@@ -210,6 +210,76 @@ int nacc_prune_samples(const int32_t* packed_info, int32_t n_rays, const float* 
                        void* workspace, size_t workspace_bytes, void* stream);
 
 /* ------------------------------------------------------------------------- */
+/* Inference: marching that stops on the field's transmittance (Sec. 2.1     */
+/* "Pruning Empty and Occluded Regions", "GPU Memory Efficiency")            */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * A density field the library evaluates itself (for instance a trained
+ * radiance field's density baked onto a grid): float32 sigma at the vertices
+ * of a res[0] x res[1] x res[2] lattice over the box aabb = (lo xyz, hi xyz),
+ * vertex (i, j, k) at lo + (hi - lo) * (i, j, k) / (res - 1), stored x-major,
+ * z fastest. Between vertices sigma is trilinear; outside the box it is 0.
+ * Float32, in this order per axis a: s_a = (res_a - 1) / (hi_a - lo_a),
+ * u_a = (x_a - lo_a) * s_a (outside unless 0 <= u_a <= res_a - 1),
+ * i_a = min(floor(u_a), res_a - 2), f_a = u_a - i_a; then
+ * lerp(p, q, f) = p + f (q - p) along z, then y, then x (no contraction).
+ * Values must be finite and >= 0 (a density).
+ */
+typedef struct nacc_density_field {
+    const float* sigma; /* device, res[0]*res[1]*res[2] float32 (caller-owned) */
+    int32_t res[3];     /* vertices per axis, each >= 2, product < 2^31 */
+    float aabb[6];      /* lo x, y, z, hi x, y, z; lo < hi, finite */
+} nacc_density_field;
+
+/*
+ * Marching with the field's transmittance for inference: the samples kept are
+ * exactly those nacc_prune_samples(early_stop_eps, alpha_thre) keeps of the
+ * samples nacc_march_rays emits, with sigma_i = the field at each sample's
+ * midpoint x = o + d (t_s + t_e)/2 (the point the occupancy lookup uses). The
+ * march of a ray ends where its optical depth passes -ln(eps) (Sec. 2.1: the
+ * transmittance needs the density, queried without gradient), and samples that
+ * are dropped are never written, so memory holds only the kept set.
+ * Differences to the two-call path: the keep decisions are taken on the same
+ * float32 tau_i; the optical depth O_i is summed in another order (32 lattice
+ * points per warp-wide shuffle scan), so a decision can differ only where O_i
+ * lies within float32 summation error of -ln(eps).
+ *
+ * Arguments as nacc_march_rays (rays use grid slot 0; no time or slot input),
+ * plus:
+ * field            host struct (read during the call only), see above.
+ * early_stop_eps, alpha_thre  as nacc_prune_samples (<= 0 switches a test off).
+ * sigmas           (capacity,) float32 out or NULL: sigma of each kept sample.
+ * n_samples        device int64 out: the number of KEPT samples.
+ * workspace        nacc_march_workspace_size(n_rays, params) bytes, 256-byte
+ *                  aligned. After the call the uint64 at byte offset 8 holds
+ *                  the number of lattice points examined (up to each ray's end).
+ * Errors: those of nacc_march_rays; NACC_ERR_INVALID_ARG for a missing or
+ * malformed field or NaN thresholds.
+ */
+int nacc_march_fused(const float* rays_o, const float* rays_d, int32_t n_rays, const nacc_grid* grid,
+                     const nacc_march_params* params, const nacc_density_field* field, float early_stop_eps,
+                     float alpha_thre, int32_t* packed_info, float* t_starts, float* t_ends,
+                     int32_t* ray_indices, float* sigmas, int64_t capacity, int64_t* n_samples,
+                     int32_t* d_status, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * sigma of the field at each sample's midpoint: sigmas[s] = field at
+ * o_r + d_r (t_starts[s] + t_ends[s]) / 2 with r = ray_indices[s] (the same
+ * float32 operations as nacc_march_fused). rays_o, rays_d (n_rays, 3);
+ * ray_indices, t_starts, t_ends, sigmas (n_samples,). A ray index outside
+ * [0, n_rays) gives sigma 0 and raises NACC_STATUS_BAD_INDEX in d_status.
+ */
+int nacc_density_field_at_samples(const nacc_density_field* field, const float* rays_o, const float* rays_d,
+                                  int32_t n_rays, const int32_t* ray_indices, const float* t_starts,
+                                  const float* t_ends, int64_t n_samples, float* sigmas, int32_t* d_status,
+                                  void* stream);
+
+/* sigma of the field at points xyz (n, 3) float32 into sigmas (n,). */
+int nacc_density_field_query(const nacc_density_field* field, const float* xyz, int64_t n, float* sigmas,
+                             void* stream);
+
+/* ------------------------------------------------------------------------- */
 /* Differentiable rendering (Sec. 2.2, Eq. 1)                                */
 /* ------------------------------------------------------------------------- */
 
@@ -361,7 +431,8 @@ int nacc_sample_grid_cells(uint64_t seed, uint64_t stream, int64_t n, const nacc
 #define NACC_TUNE_PRUNE_INTERLEAVE 8    /* 2 or 4: rays a pruning warp walks at once */
 #define NACC_TUNE_RENDER_BWD_PREFETCH 9 /* 0/1: backward issues the next chunk's loads early */
 #define NACC_TUNE_MARCH_COARSE 10       /* 0/1: first test one lattice point in 32, fill chunks that lie in one cell */
-#define NACC_TUNE_COUNT 11
+#define NACC_TUNE_FUSED_OCCUPANCY 11    /* 0: compiler's register use; 1: nacc_march_fused capped at 64 registers */
+#define NACC_TUNE_COUNT 12
 
 /* Set a knob; NACC_ERR_INVALID_ARG for an unknown knob or out-of-range value. */
 int nacc_tune_set(int knob, int value);

@@ -34,7 +34,7 @@ MAX_LEVELS = 16
 
 EXPORTS = (
     "nacc_march_workspace_size", "nacc_march_rays", "nacc_march_rays_static", "nacc_prune_workspace_size",
-    "nacc_prune_samples",
+    "nacc_prune_samples", "nacc_march_fused", "nacc_density_field_at_samples", "nacc_density_field_query",
     "nacc_render_weights", "nacc_accumulate_along_rays", "nacc_render_weights_bwd",
     "nacc_accumulate_along_rays_bwd", "nacc_render_fwd", "nacc_render_bwd",
     "nacc_unpack_info", "nacc_update_occupancy_grid", "nacc_sample_grid_cells", "nacc_tune_set", "nacc_tune_get",
@@ -48,7 +48,7 @@ TUNE_PRUNE_TILE_RAYS = 2
 TUNE_KNOBS = {"render_fwd_prefetch": 0, "march_tile_rays": 1, "prune_tile_rays": 2, "march_occupancy": 3,
               "prune_occupancy": 4, "render_fwd_occupancy": 5, "render_bwd_occupancy": 6, "march_unroll": 7,
               "prune_interleave": 8, "render_bwd_prefetch": 9,
-              "march_coarse": 10}
+              "march_coarse": 10, "fused_occupancy": 11}
 
 
 class NaccError(RuntimeError):
@@ -63,6 +63,14 @@ class Grid(ctypes.Structure):
         ("n_slots", ctypes.c_int32),
         ("aabb", ctypes.c_float * 6),
         ("contraction", ctypes.c_int32),
+    ]
+
+
+class DensityField(ctypes.Structure):
+    _fields_ = [
+        ("sigma", ctypes.c_void_p),
+        ("res", ctypes.c_int32 * 3),
+        ("aabb", ctypes.c_float * 6),
     ]
 
 
@@ -91,12 +99,16 @@ def load() -> ctypes.CDLL:
     L = ctypes.CDLL(LIB_PATH)
     P, i32, i64, f32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
     GP, MP = ctypes.POINTER(Grid), ctypes.POINTER(MarchParams)
+    FP = ctypes.POINTER(DensityField)
     sig = {
         "nacc_march_workspace_size": (sz, [i32, MP]),
         "nacc_march_rays": (ctypes.c_int, [P, P, P, P, i32, GP, MP, P, P, P, P, i64, P, P, P, sz, P]),
         "nacc_march_rays_static": (ctypes.c_int, [P, P, P, P, i32, GP, MP, P, P, P, P, i64, P, P, P]),
         "nacc_prune_workspace_size": (sz, [i32, i64]),
         "nacc_prune_samples": (ctypes.c_int, [P, i32, P, P, P, i64, f32, f32, P, P, P, P, i64, P, P, P, P, sz, P]),
+        "nacc_march_fused": (ctypes.c_int, [P, P, i32, GP, MP, FP, f32, f32, P, P, P, P, P, i64, P, P, P, sz, P]),
+        "nacc_density_field_at_samples": (ctypes.c_int, [FP, P, P, i32, P, P, P, i64, P, P, P]),
+        "nacc_density_field_query": (ctypes.c_int, [FP, P, i64, P, P]),
         "nacc_render_weights": (ctypes.c_int, [P, i32, P, P, P, i64, P, P, P, P]),
         "nacc_accumulate_along_rays": (ctypes.c_int, [P, i32, P, P, i32, i64, P, P, P]),
         "nacc_render_weights_bwd": (ctypes.c_int, [P, i32, P, P, P, i64, P, P, P, P]),
@@ -187,6 +199,20 @@ def make_grid(bits: torch.Tensor, res: Sequence[int], aabb: Sequence[float], n_l
     return g
 
 
+def make_density_field(sigma: torch.Tensor, aabb: Sequence[float]) -> DensityField:
+    """nacc_density_field over a (G0, G1, G2) float32 CUDA tensor of vertex values."""
+    _check(sigma, torch.float32, "density field")
+    if sigma.dim() != 3:
+        raise NaccError("density field must be a 3-d tensor of vertex values")
+    f = DensityField()
+    f.sigma = sigma.data_ptr()
+    for k in range(3):
+        f.res[k] = int(sigma.shape[k])
+    for k in range(6):
+        f.aabb[k] = float(aabb[k])
+    return f
+
+
 def make_params(near_plane, far_plane, dt_min, dt_max=None, cone=0.0, max_steps=1024) -> MarchParams:
     p = MarchParams()
     p.near_plane = float(near_plane)
@@ -257,6 +283,52 @@ def march_rays_static(rays_o, rays_d, grid: Grid, params: MarchParams, packed_in
         _ptr(packed_info), _ptr(t_starts), _ptr(t_ends), _ptr(ray_indices), cap, _ptr(n_samples), _ptr(d_status),
         _stream(stream))
     _rc(rc, "nacc_march_rays_static")
+
+
+def march_fused(rays_o, rays_d, grid: Grid, params: MarchParams, field: DensityField, early_stop_eps, alpha_thre,
+                packed_info, t_starts, t_ends, ray_indices, sigmas, n_samples, d_status, workspace, stream=None):
+    """nacc_march_fused: marching that stops on the density field's transmittance
+    (inference); writes only the kept samples (and their sigma when given)."""
+    n = rays_o.shape[0]
+    _check(rays_o, torch.float32, "rays_o", 3 * n)
+    _check(rays_d, torch.float32, "rays_d", 3 * n)
+    _check(packed_info, torch.int32, "packed_info", 2 * n)
+    cap = t_starts.numel()
+    _check(t_starts, torch.float32, "t_starts")
+    _check(t_ends, torch.float32, "t_ends", cap)
+    _check(ray_indices, torch.int32, "ray_indices", cap)
+    _check(sigmas, torch.float32, "sigmas", cap, optional=True)
+    _check(n_samples, torch.int64, "n_samples", 1)
+    _check(d_status, torch.int32, "d_status", 1, optional=True)
+    _check(workspace, torch.uint8, "workspace")
+    rc = load().nacc_march_fused(
+        _ptr(rays_o), _ptr(rays_d), n, ctypes.byref(grid), ctypes.byref(params), ctypes.byref(field),
+        float(early_stop_eps), float(alpha_thre), _ptr(packed_info), _ptr(t_starts), _ptr(t_ends),
+        _ptr(ray_indices), _ptr(sigmas), cap, _ptr(n_samples), _ptr(d_status), _ptr(workspace), workspace.numel(),
+        _stream(stream))
+    _rc(rc, "nacc_march_fused")
+
+
+def density_field_at_samples(field: DensityField, rays_o, rays_d, ray_indices, t_starts, t_ends, n_samples: int,
+                             sigmas, d_status=None, stream=None):
+    n = rays_o.shape[0]
+    _check(rays_o, torch.float32, "rays_o", 3 * n)
+    _check(rays_d, torch.float32, "rays_d", 3 * n)
+    for t, name in ((t_starts, "t_starts"), (t_ends, "t_ends"), (sigmas, "sigmas")):
+        _check(t, torch.float32, name, n_samples)
+    _check(ray_indices, torch.int32, "ray_indices", n_samples)
+    _check(d_status, torch.int32, "d_status", 1, optional=True)
+    rc = load().nacc_density_field_at_samples(
+        ctypes.byref(field), _ptr(rays_o), _ptr(rays_d), n, _ptr(ray_indices), _ptr(t_starts), _ptr(t_ends),
+        int(n_samples), _ptr(sigmas), _ptr(d_status), _stream(stream))
+    _rc(rc, "nacc_density_field_at_samples")
+
+
+def density_field_query(field: DensityField, xyz, n: int, sigmas, stream=None):
+    _check(xyz, torch.float32, "xyz", 3 * n)
+    _check(sigmas, torch.float32, "sigmas", n)
+    rc = load().nacc_density_field_query(ctypes.byref(field), _ptr(xyz), int(n), _ptr(sigmas), _stream(stream))
+    _rc(rc, "nacc_density_field_query")
 
 
 def prune_samples(packed_info, t_starts, t_ends, sigmas, n_samples_in: int, early_stop_eps, alpha_thre,

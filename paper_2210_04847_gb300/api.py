@@ -144,6 +144,73 @@ def march_rays(rays_o, rays_d, grid: OccupancyGrid, near_plane=0.0, far_plane=1e
     return packed, ts[:n], te[:n], ri[:n]
 
 
+class DensityGrid:
+    """A density field the library evaluates inside its kernels (the fused
+    inference path): float32 sigma at the vertices of a lattice over ``aabb``
+    (``sigma[i, j, k]`` at lo + (hi - lo) (i, j, k) / (res - 1)), trilinear in
+    between, zero outside (``nacc_density_field``)."""
+
+    def __init__(self, sigma: torch.Tensor, aabb: Sequence[float]):
+        if sigma.dim() != 3 or min(sigma.shape) < 2:
+            raise ValueError("sigma must be (G0, G1, G2) vertex values with every G >= 2")
+        self.sigma = sigma.contiguous().float()
+        self.aabb = tuple(float(v) for v in aabb)
+
+    def struct(self) -> _lib.DensityField:
+        return _lib.make_density_field(self.sigma, self.aabb)
+
+    def __call__(self, xyz: torch.Tensor) -> torch.Tensor:
+        """sigma at points xyz (n, 3)."""
+        x = xyz.contiguous().float().view(-1, 3)
+        out = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        _lib.density_field_query(self.struct(), x, x.shape[0], out)
+        return out
+
+    def at_samples(self, rays_o, rays_d, t_starts, t_ends, ray_indices) -> torch.Tensor:
+        """sigma at each sample's midpoint (the point the marcher looks up)."""
+        n = t_starts.numel()
+        out = torch.empty(n, dtype=torch.float32, device=t_starts.device)
+        _lib.density_field_at_samples(self.struct(), rays_o.contiguous().float(), rays_d.contiguous().float(),
+                                      ray_indices.contiguous(), t_starts.contiguous().view(-1),
+                                      t_ends.contiguous().view(-1), n, out)
+        return out
+
+
+def march_with_density(rays_o, rays_d, grid: OccupancyGrid, density: DensityGrid, near_plane=0.0, far_plane=1e10,
+                       render_step_size=1e-2, cone_angle=0.0, dt_max=None, max_steps=1024, early_stop_eps=1e-4,
+                       alpha_thre=0.0, return_ray_indices=False):
+    """Inference: march the occupancy grid with the density field's transmittance
+    evaluated in the same kernel, so each ray stops where T < early_stop_eps and
+    only the kept samples are written (Sec. 2.1). Same samples as ``ray_marching``
+    with ``sigma_fn = density.at_samples``. Returns (packed_info, t_starts (n,1),
+    t_ends (n,1), sigmas (n,1)[, ray_indices])."""
+    dev = rays_o.device
+    rays_o = rays_o.contiguous().float()
+    rays_d = rays_d.contiguous().float()
+    R = rays_o.shape[0]
+    params = _lib.make_params(near_plane, far_plane, render_step_size, dt_max, cone_angle, max_steps)
+    ws = _SCRATCH.get("march_ws", _lib.march_workspace_size(R, params), dev)
+    packed = torch.empty((R, 2), dtype=torch.int32, device=dev)
+    cs, counter, status = _count_and_status(dev)
+    cap = max(_CAP_HINT.get(("fused", R), 16 * R), 1)
+    for attempt in range(2):
+        ts = torch.empty(cap, dtype=torch.float32, device=dev)
+        te = torch.empty(cap, dtype=torch.float32, device=dev)
+        ri = torch.empty(cap, dtype=torch.int32, device=dev)
+        sg = torch.empty(cap, dtype=torch.float32, device=dev)
+        if attempt:
+            cs.zero_()
+        _lib.march_fused(rays_o, rays_d, grid.struct(), params, density.struct(), early_stop_eps, alpha_thre,
+                         packed, ts, te, ri, sg, counter, status, ws)
+        n = _read_count(cs, "march_with_density")
+        if n <= cap:
+            break
+        cap = n
+    _CAP_HINT[("fused", R)] = max(int(n * 1.08) + 1024, 1)
+    out = (packed, ts[:n].view(-1, 1), te[:n].view(-1, 1), sg[:n].view(-1, 1))
+    return out + (ri[:n],) if return_ray_indices else out
+
+
 def prune_samples(packed_info, t_starts, t_ends, sigmas, early_stop_eps=1e-4, alpha_thre=0.0):
     """Early-stop / alpha pruning and re-packing. Returns (packed_info, t_starts, t_ends, ray_indices)."""
     dev = packed_info.device

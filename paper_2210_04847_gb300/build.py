@@ -27,10 +27,10 @@ COMMON = ARCH + [
 ]
 # Units whose float results decide integers (which samples exist) compile with
 # no multiply-add contraction; the others may contract.
-NO_FMAD = {"march.cu", "prune.cu"}
+NO_FMAD = {"march.cu", "prune.cu", "fused.cu"}
 
 LIBS = {
-    "libnacc.so": ["march.cu", "march_static.cu", "prune.cu", "render.cu", "grid.cu", "device.cu"],
+    "libnacc.so": ["march.cu", "march_static.cu", "fused.cu", "prune.cu", "render.cu", "grid.cu", "device.cu"],
     "libnacc_field.so": ["field.cu"],
 }
 

@@ -300,6 +300,28 @@ def occupancy_bits(scene: BlobScene, aabb, res, n_levels=1, thre=0.01, t=None, d
     return pack_bits((dens > thre).cpu().numpy())
 
 
+def density_at_vertices(scene: BlobScene, aabb, res, device="cpu") -> np.ndarray:
+    """The stand-in field's density at the vertices of a res[0] x res[1] x res[2]
+    lattice over ``aabb`` (vertex (i, j, k) at lo + (hi - lo) (i, j, k) / (res - 1)),
+    float64 evaluation stored as float32 (G0, G1, G2): a density grid of the kind
+    a trained field is baked into for inference. Separable per blob, as above."""
+    import torch
+
+    c = scene.centers
+    inv2s2 = 1.0 / (2.0 * scene.scales**2)
+    axes = []
+    for a in range(3):
+        lo, hi, g = float(aabb[a]), float(aabb[3 + a]), int(res[a])
+        xs = lo + np.arange(g, dtype=np.float64) * ((hi - lo) / (g - 1))
+        axes.append(np.exp(-((xs[None, :] - c[:, a : a + 1]) ** 2) * inv2s2[:, None]))
+    gx = torch.as_tensor(axes[0] * scene.peaks[:, None], device=device)
+    gy = torch.as_tensor(axes[1], device=device)
+    gz = torch.as_tensor(axes[2], device=device)
+    yz = (gy[:, :, None] * gz[:, None, :]).reshape(gy.shape[0], -1)
+    dens = (gx.T @ yz).reshape(int(res[0]), int(res[1]), int(res[2]))
+    return np.ascontiguousarray(dens.cpu().numpy(), dtype=np.float32)
+
+
 def uncontract(xc: np.ndarray) -> np.ndarray:
     """Inverse of the Mip-NeRF 360 contraction (Eq. 10 there) for points of the
     open radius-2 ball, float64: |x_c| <= 1 unchanged, else x_c / ((2 - |x_c|) |x_c|)."""
@@ -381,6 +403,8 @@ class Workload:
     backward: bool = True
     meta: dict = field(default_factory=dict)
     contraction: int = 0  # 1: contracted unbounded space (one level; see nacc_grid)
+    field: Optional[np.ndarray] = None  # (G0, G1, G2) float32 density at lattice vertices (inference)
+    field_box: Optional[tuple] = None  # box of the density lattice
 
     @property
     def n_rays(self) -> int:
@@ -445,6 +469,28 @@ def bounded_config(seed: int = 0, n_rays: int = 1 << 18, n_cams: int = 100, devi
     return Workload(
         name, o, d, bits, (128, 128, 128), 1, 1, aabb,
         0.0, 1e10, dt, dt, 0.0, 1024, 1e-4, 1e-2, [scene], target_rgb=target,
+    )
+
+
+def inference_config(seed: int = 0, camera: int = 0, field_res: int = 129, device="cpu",
+                     scene_grid=None) -> Workload:
+    """One whole 800x800 image (fx = fy = 1111.1) of the bounded scene from camera
+    ``camera`` of the bounded workload's 100 on the r = 4 sphere, pixel-major; the
+    bounded workload's 128^3 occupancy grid and step; the scene's density baked
+    at field_res^3 lattice vertices over the same box (the field the fused
+    inference path evaluates). Early stop 1e-4, alpha threshold 1e-2."""
+    scene, aabb, bits = scene_grid if scene_grid is not None else bounded_scene(seed, device)
+    cam = sphere_cameras(seed, 100, 4.0)[camera % 100][None, :]
+    py, px = np.meshgrid(np.arange(800, dtype=np.float64), np.arange(800, dtype=np.float64), indexing="ij")
+    px, py = px.reshape(-1), py.reshape(-1)
+    pos = np.repeat(cam, px.size, axis=0)
+    o, d = pinhole_rays(pos, np.zeros_like(pos), px, py, 1111.1, 1111.1, 400.0, 400.0)
+    dt = SQRT3 * 3.0 / 1024.0
+    fr = (int(field_res),) * 3
+    return Workload(
+        "inference-800x800-grid128-field%d" % field_res, _f32(o), _f32(d), bits, (128, 128, 128),
+        1, 1, aabb, 0.0, 1e10, dt, dt, 0.0, 1024, 1e-4, 1e-2, [scene], backward=False,
+        field=density_at_vertices(scene, aabb, fr, device), field_box=tuple(aabb), meta={"camera": camera % 100},
     )
 
 

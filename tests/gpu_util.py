@@ -1,5 +1,7 @@
 """Helpers of the GPU parity tests: run the CUDA path through the C ABI on
 seeded inputs and bring results back as numpy; compare with the oracle."""
+import math
+
 import numpy as np
 import torch
 
@@ -98,3 +100,20 @@ def grad_rel_err(got, ref):
     floor = 1e-3 * np.max(np.abs(ref))
     den = np.maximum(np.abs(ref), max(floor, 1e-30))
     return float(np.max(np.abs(got - ref) / den))
+
+
+def near_threshold(pi, ts, te, sg, eps, od):
+    """Samples whose optical depth od (float32 or float64, per input sample) lies
+    within the float32 summation error bound of -ln(eps): the only samples where
+    two float32 summation orders may take different keep decisions."""
+    tau = sg.astype(np.float64) * (te.astype(np.float64) - ts.astype(np.float64))
+    flag = np.zeros(ts.shape[0], bool)
+    thr = -math.log(eps)
+    for off, cnt in pi:
+        if cnt == 0:
+            continue
+        t = np.abs(tau[off : off + cnt])
+        absum = np.concatenate([[0.0], np.cumsum(t)[:-1]])
+        bound = (np.arange(cnt) + 40) * 2.0**-23 * absum + 1e-6
+        flag[off : off + cnt] = np.abs(od[off : off + cnt].astype(np.float64) - thr) <= bound
+    return flag

@@ -20,7 +20,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no CUDA device", allow_module_level=True)
 
-from gpu_util import bits_equal, dev, grad_rel_err, oracle_march, render_tol_ok  # noqa: E402
+from gpu_util import bits_equal, dev, grad_rel_err, near_threshold, oracle_march, render_tol_ok  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -49,28 +49,13 @@ def _gpu_prune(pi, ts, te, sg, eps, thre, capacity=None):
     return {k: v.cpu().numpy() for k, v in out.items()}
 
 
-def _near_threshold(pi, ts, te, sg, eps, od_oracle):
-    """Samples whose optical depth lies within the float32 summation error bound of -ln(eps)."""
-    tau = sg.astype(np.float64) * (te.astype(np.float64) - ts.astype(np.float64))
-    flag = np.zeros(ts.shape[0], bool)
-    thr = -math.log(eps)
-    for off, cnt in pi:
-        if cnt == 0:
-            continue
-        t = np.abs(tau[off : off + cnt])
-        absum = np.concatenate([[0.0], np.cumsum(t)[:-1]])
-        bound = (np.arange(cnt) + 40) * 2.0**-23 * absum + 1e-6
-        flag[off : off + cnt] = np.abs(od_oracle[off : off + cnt].astype(np.float64) - thr) <= bound
-    return flag
-
-
 def test_prune_parity(scene):
     w, m, sig = scene["w"], scene["m"], scene["sig"]
     g = _gpu_prune(m.packed_info, m.t_starts, m.t_ends, sig, w.early_stop_eps, w.alpha_thre)
     assert g["st"][0] == 0
     keep_g = g["keep"][: m.n_samples].astype(bool)
     keep_o = scene["keep"]
-    near = _near_threshold(m.packed_info, m.t_starts, m.t_ends, sig, w.early_stop_eps, scene["od"])
+    near = near_threshold(m.packed_info, m.t_starts, m.t_ends, sig, w.early_stop_eps, scene["od"])
     diff = keep_g != keep_o
     assert not (diff & ~near).any(), "keep decisions differ away from the threshold"
     flipped_rays = set(np.searchsorted(m.packed_info[:, 0], np.nonzero(diff)[0], side="right") - 1)
