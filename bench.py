@@ -48,6 +48,8 @@ POOL = 4  # distinct ray batches cycled through the steps (L2 is flushed between
 NCU_TRAFFIC = {
     # profiles/march_dram_bounded-2^18.md: 7927552 B read + 1476811776 B written
     ("march", "6c83e937d944d78d0ea8cba9eede8121b3e3164f091d2ca913df1f5ab93e26bd"): 1484739328,
+    # profiles/march_fused_inference-800x800.md: 22538752 B read + 1169636096 B written (camera 0's image)
+    ("march_fused", "75040a7da6bdfb31b279bd2041c0266f0e6d4c564093101aec05fd2a2731c575"): 1192174848,
 }
 
 # What limits each stage (from the ncu captures summarised under profiles/).
@@ -194,7 +196,7 @@ def stage_bytes(R, M, M_read, S, grid_bytes, n_cells, n_grid, saved_od=False):
 
 def kernel_source_sha(stage: str) -> str:
     f = {"march": "march.cu", "prune": "prune.cu", "render_fwd": "render.cu", "render_bwd": "render.cu",
-         "grid_update": "grid.cu"}[stage]
+         "grid_update": "grid.cu", "march_fused": "fused.cu"}[stage]
     with open(os.path.join(ROOT, "paper_2210_04847_gb300", "csrc", f), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()
 
@@ -733,7 +735,9 @@ def run_inference(args):
                      "frac": round((fused_bytes + render_bytes) / (mean_ms / 1e3) / 1e9 / peak, 4),
                      "peak_gbs": peak, "peak_kind": peak_kind},
         "roofline": {"bound": "hbm", "kernel": "march_fused", "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                     "traffic": NCU_TRAFFIC.get(("march_fused", kernel_source_sha("march_fused")))
+                     if args.pixel_stride == 1 else None,
                      "algorithmic_bytes": int(fused_bytes),
                      "limiter": "issue: bit-exact float32 lattice arithmetic plus the trilinear density per "
                                 "occupied point"},
