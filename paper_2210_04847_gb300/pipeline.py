@@ -14,7 +14,6 @@ stage can be bracketed by CUDA events on the launching stream.
 from __future__ import annotations
 
 from dataclasses import dataclass
-from typing import Optional
 
 import numpy as np
 import torch

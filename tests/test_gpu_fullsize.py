@@ -1,5 +1,6 @@
 """Parity at the benchmark's full size and launch configuration (2^18 rays of the
-bounded workload through pipeline.HotPath, the buffers and calls bench.py times).
+bounded workload through pipeline.HotPath, the buffers and calls bench.py times;
+a whole 800x800 image through the fused inference path).
 
 The oracle cannot march 2^18 rays x 1024 steps and render them inside a test, so
 it checks a seeded sample of rays one by one (marching of a ray depends on that ray
@@ -165,3 +166,60 @@ def test_fullsize_grid_update_bitexact(orc):
     assert int(st.item()) == 0
     assert bits_equal(e_t.cpu().numpy(), e_o)
     assert np.array_equal(b_t.cpu().numpy().view(np.uint32), b_o)
+
+
+def test_fullsize_fused_inference_image_sampled_rays(orc):
+    """The fused inference path on a whole 800x800 image (the launch bench.py
+    --workload inference times): sampled rays against the oracle (march -> density
+    at the midpoints -> prune), bit-exact except rays with a decision within
+    float32 summation error of -ln(eps); whole-image packing properties on the
+    device."""
+    from gpu_util import near_threshold
+
+    w = synth.inference_config(0, camera=0)
+    Rf = w.n_rays
+    o, d = to_device(w.rays_o), to_device(w.rays_d)
+    bits = to_device(w.bits)
+    grid = _lib.make_grid(bits, w.res, w.aabb, 1, 1, 0)
+    params = _lib.make_params(w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone, w.max_steps)
+    fld = _lib.make_density_field(to_device(w.field), w.field_box)
+    ws = torch.zeros(_lib.march_workspace_size(Rf, params), dtype=torch.uint8, device="cuda")
+    cap = 100_000_000
+    pi = torch.zeros((Rf, 2), dtype=torch.int32, device="cuda")
+    ts, te, sg = (torch.zeros(cap, device="cuda") for _ in range(3))
+    ri = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    n = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _lib.march_fused(o, d, grid, params, fld, w.early_stop_eps, w.alpha_thre, pi, ts, te, ri, sg, n, st, ws)
+    torch.cuda.synchronize()
+    S = int(n.item())
+    assert int(st.item()) == 0 and 50_000_000 < S < cap
+    # whole image: contiguous runs, ray indices, ordered non-overlapping intervals, sigma > 0 where kept
+    pl = pi.long()
+    assert int(pl[:, 1].sum()) == S and bool(torch.all(pl[1:, 0] == pl[:-1, 0] + pl[:-1, 1]))
+    assert bool(torch.all(ri[:S].long() == torch.repeat_interleave(torch.arange(Rf, device="cuda"), pl[:, 1])))
+    same = ri[1:S] == ri[: S - 1]
+    assert bool(torch.all(ts[1:S][same] >= te[: S - 1][same])) and bool(torch.all(sg[:S] > 0))
+    # sampled rays against the oracle
+    sample = np.sort(synth.rand_int(98, 1, 64, Rf).astype(np.int64))
+    so, sd = w.rays_o[sample], w.rays_d[sample]
+    m = orc.march(so, sd, w.bits, w.res, w.aabb, w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone, w.max_steps)
+    mid = ((m.t_starts + m.t_ends) * np.float32(0.5)).astype(np.float32)
+    sig = orc.field_query(w.field, w.field_box, (so[m.ray_indices] + sd[m.ray_indices] * mid[:, None]).astype(np.float32))
+    p, keep, od = orc.prune(m.packed_info, m.t_starts, m.t_ends, sig, w.early_stop_eps, w.alpha_thre)
+    near = near_threshold(m.packed_info, m.t_starts, m.t_ends, sig, w.early_stop_eps, od)
+    pin = pi.cpu().numpy()
+    kept_sig = sig[keep]
+    flipped = 0
+    for k, r in enumerate(sample):
+        off, cnt = pin[r]
+        ooff, ocnt = p.packed_info[k]
+        if cnt == ocnt and bits_equal(_gather(ts, off, cnt), p.t_starts[ooff : ooff + ocnt]):
+            assert bits_equal(_gather(te, off, cnt), p.t_ends[ooff : ooff + ocnt])
+            assert bits_equal(_gather(sg, off, cnt), kept_sig[ooff : ooff + ocnt])
+            continue
+        mo, mc = m.packed_info[k]
+        assert near[mo : mo + mc].any(), "ray %d differs away from the early-stop threshold" % r
+        flipped += 1
+    assert flipped <= 1
+    assert p.n_samples > 1000

@@ -7,8 +7,6 @@ within the float32 summation error bound of the threshold; colour / opacity /
 depth within 1e-5 (depth 1e-5 relative above 1); gradients within 1e-4
 relative (floor 1e-3 of the largest magnitude); grid update bit-exact.
 """
-import math
-
 import numpy as np
 import pytest
 

@@ -4,7 +4,6 @@ timing aggregates the maximum step time and the total ray count over ranks."""
 import os
 import socket
 
-import pytest
 import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
