@@ -188,6 +188,7 @@ def make_grid(bits: torch.Tensor, res: Sequence[int], aabb: Sequence[float], n_l
               contraction: int = 0) -> Grid:
     _check(bits, torch.int32, "grid bits")
     g = Grid()
+    g._keepalive = bits  # the struct holds a raw pointer: keep the tensor alive with it
     g.contraction = int(contraction)
     g.bits = bits.data_ptr()
     for k in range(3):
@@ -205,6 +206,7 @@ def make_density_field(sigma: torch.Tensor, aabb: Sequence[float]) -> DensityFie
     if sigma.dim() != 3:
         raise NaccError("density field must be a 3-d tensor of vertex values")
     f = DensityField()
+    f._keepalive = sigma  # the struct holds a raw pointer: keep the tensor alive with it
     f.sigma = sigma.data_ptr()
     for k in range(3):
         f.res[k] = int(sigma.shape[k])

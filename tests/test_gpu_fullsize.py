@@ -182,7 +182,8 @@ def test_fullsize_fused_inference_image_sampled_rays(orc):
     bits = to_device(w.bits)
     grid = _lib.make_grid(bits, w.res, w.aabb, 1, 1, 0)
     params = _lib.make_params(w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone, w.max_steps)
-    fld = _lib.make_density_field(to_device(w.field), w.field_box)
+    field_t = to_device(w.field)
+    fld = _lib.make_density_field(field_t, w.field_box)
     ws = torch.zeros(_lib.march_workspace_size(Rf, params), dtype=torch.uint8, device="cuda")
     cap = 100_000_000
     pi = torch.zeros((Rf, 2), dtype=torch.int32, device="cuda")
