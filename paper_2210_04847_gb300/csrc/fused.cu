@@ -98,7 +98,7 @@ __device__ __forceinline__ void fused_walk(const FusedArgs& A, const float o[3],
     const MarchArgs& a = A.m;
     const bool shared = !CONE || near == a.near_plane;
     int nk = !CONE ? lattice_count(a, near, far, a.dt_min)
-                   : (shared ? table_count(a.cone_table, a.max_steps, far) : a.max_steps);
+                   : (shared ? table_count(a.cone_table, a.max_steps, far, lane) : a.max_steps);
     if (CONE && shared && nk > 32 * a.mask_words) {
         if (lane == 0) raise_status(a.d_status, NACC_STATUS_OVERFLOW);
         nk = 32 * a.mask_words;

@@ -47,7 +47,7 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
     const bool shared = !CONE || near == a.near_plane;
     // shared lattices know their length; an own cone lattice ends when t_k >= far
     int nk = !CONE ? lattice_count(a, near, far, dt)
-                   : (shared ? table_count(a.cone_table, a.max_steps, far) : a.max_steps);
+                   : (shared ? table_count(a.cone_table, a.max_steps, far, lane) : a.max_steps);
     if (CONE && shared && nk > 32 * a.mask_words) {  // the host's bound on cone lattices was passed
         if (lane == 0) raise_status(a.d_status, NACC_STATUS_OVERFLOW);
         nk = 32 * a.mask_words;

@@ -56,6 +56,7 @@ struct MarchArgs {
     int32_t contract;         // contracted unbounded space (one level, no box clip)
     float cc[3], inv_h[3];    // contraction: box centre and 1 / half size
     float qres[3];            // contraction: res / 4 (the grid spans [-2, 2])
+    float inv_dt;             // 1 / dt_min, for the first guess of a uniform lattice's length
     Levels L;
 };
 
@@ -81,7 +82,7 @@ __device__ __forceinline__ bool clip_ray(const MarchArgs& a, const float o[3], c
             if (o[k] < a.L.box_lo[k] || o[k] > a.L.box_hi[k]) return false;
             continue;
         }
-        float inv = __fdiv_rn(1.0f, d[k]);
+        float inv = __frcp_rn(d[k]);  // the correctly rounded 1/d, as the IEEE division gives
         float t0 = __fmul_rn(__fsub_rn(a.L.box_lo[k], o[k]), inv);
         float t1 = __fmul_rn(__fsub_rn(a.L.box_hi[k], o[k]), inv);
         float tmin = t0 < t1 ? t0 : t1;
@@ -155,10 +156,10 @@ __device__ __forceinline__ float lattice_t(float near, int k, float dt) {
 
 // Number of lattice intervals of a ray: the k < max_steps with t_k < far. t_k is
 // non-decreasing in k, so it is the first k with t_k >= far (capped): a guess from
-// real arithmetic, then the exact float32 test moves it to the boundary (the
-// guess is off by at most a few steps).
+// real arithmetic (the span times 1/dt), then the exact float32 test moves it to
+// the boundary (the guess is off by at most a few steps).
 __device__ __forceinline__ int lattice_count(const MarchArgs& a, float near, float far, float dt) {
-    float g = (far - near) / dt;
+    float g = (far - near) * a.inv_dt;
     int e = g < (float)a.max_steps ? (int)g : a.max_steps;
     if (e < 0) e = 0;
     while (e > 0 && !(lattice_t(near, e - 1, dt) < far)) --e;
@@ -187,13 +188,20 @@ __global__ void cone_table_kernel(const MarchArgs a, float* table) {
     }
 }
 
-// First k in [0, max_steps] with table[k] >= far (the table is non-decreasing).
-__device__ __forceinline__ int table_count(const float* table, int max_steps, float far) {
-    int lo = 0, hi = max_steps;
+// First k in [0, max_steps] with table[k] >= far (max_steps if none below it; the
+// table is non-decreasing), found by the whole warp: each round probes 32 evenly
+// spaced candidates, and the probes below far form a prefix of the lanes, which
+// narrows the range by a factor of 32 (three rounds for 4096 steps).
+__device__ __forceinline__ int table_count(const float* table, int max_steps, float far, int lane) {
+    int lo = 0, hi = max_steps;  // table[k] < far for every k < lo; the answer is in [lo, hi]
     while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(table + mid) < far) lo = mid + 1;
-        else hi = mid;
+        const int step = (hi - lo + 31) >> 5;
+        const int k = lo + lane * step;
+        const unsigned below = __ballot_sync(FULL, k < hi && __ldg(table + k) < far);
+        const int nb = __popc(below);
+        if (nb == 0) break;  // table[lo] >= far
+        hi = min(lo + nb * step, hi);
+        lo = lo + (nb - 1) * step + 1;
     }
     return lo;
 }
@@ -339,6 +347,7 @@ int march_setup(const float* rays_o, const float* rays_d, const float* ray_time,
     a.near_plane = p->near_plane;
     a.far_plane = p->far_plane;
     a.dt_min = p->dt_min;
+    a.inv_dt = 1.0f / p->dt_min;
     a.dt_max = p->dt_max;
     a.cone = p->cone;
     a.max_steps = p->max_steps;
