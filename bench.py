@@ -45,10 +45,10 @@ POOL = 4  # distinct ray batches cycled through the steps (L2 is flushed between
 # from one ncu capture, keyed by the SHA-256 of the kernel's source file. A
 # source change invalidates the figure (reported as null until re-captured).
 NCU_TRAFFIC = {
-    # profiles/march_dram_bounded-2^18.md: 7927552 B read + 1476811776 B written
-    ("march", "6c83e937d944d78d0ea8cba9eede8121b3e3164f091d2ca913df1f5ab93e26bd"): 1484739328,
-    # profiles/march_fused_inference-800x800.md: 22538752 B read + 1169636096 B written (camera 0's image)
-    ("march_fused", "75040a7da6bdfb31b279bd2041c0266f0e6d4c564093101aec05fd2a2731c575"): 1192174848,
+    # profiles/march_dram_bounded-2^18.md: 7960832 B read + 1476889600 B written
+    ("march", "9621414803e06b8a6c50ce7bc2043ffbf9089d1ed8a984123f45910167f9ea14"): 1484850432,
+    # profiles/march_fused_inference-800x800.md: 22238976 B read + 1169516544 B written (camera 0's image)
+    ("march_fused", "2335f145b362d44a6673d8a8faa4167b28e80af11fb579d3863c6c275a679001"): 1191755520,
 }
 
 # What limits each stage (from the ncu captures summarised under profiles/).

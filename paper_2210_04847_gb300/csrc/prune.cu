@@ -58,18 +58,20 @@ __device__ __forceinline__ uint32_t* mask_row(const PruneArgs& a, int off, int r
     return a.masks + (off >> 5) + 2 * (size_t)r;
 }
 
-// One ray's walk state inside phase 1.
+// One ray's walk state inside phase 1 (32-bit indices: n_samples < 2^31).
 struct RayWalk {
-    int off, cnt, abase, nch, c, count;
+    int j;        // this lane's first sample of the current chunk: (off & ~1) + 64 c + 2 lane
+    int off, cnt; // the ray's run [off, off + cnt)
+    int nch, c, count;
     float carry;
     uint32_t* row;
     bool live;
 };
 
-__device__ __forceinline__ void walk_init(RayWalk& w, const PruneArgs& a, int off, int cnt, int r) {
+__device__ __forceinline__ void walk_init(RayWalk& w, const PruneArgs& a, int off, int cnt, int r, int lane) {
     w.off = off;
     w.cnt = cnt;
-    w.abase = off & ~1;
+    w.j = (off & ~1) + 2 * lane;
     w.nch = cnt > 0 ? (cnt + (off & 1) + 63) >> 6 : 0;
     w.c = 0;
     w.count = 0;
@@ -80,44 +82,39 @@ __device__ __forceinline__ void walk_init(RayWalk& w, const PruneArgs& a, int of
 
 struct Pair {
     float s0[2], s1[2], sg[2];
+    bool v0, v1;  // samples j and j + 1 belong to the ray
 };
 
-// Samples j0 = abase + 64c + 2*lane and j0 + 1 of chunk c (only those inside the
-// array are read).
-__device__ __forceinline__ void walk_load(const RayWalk& w, const PruneArgs& a, int lane, int c, Pair& p) {
+// Samples j and j + 1 of the lane in the current chunk (only those inside the ray
+// are read; a pair whose second sample is inside is read as one 8-byte vector).
+__device__ __forceinline__ void walk_load(const RayWalk& w, const PruneArgs& a, Pair& p) {
     p.s0[0] = p.s0[1] = p.s1[0] = p.s1[1] = p.sg[0] = p.sg[1] = 0.0f;
-    if (!w.live || c >= w.nch) return;
-    const long long j0 = (long long)w.abase + ((long long)c << 6) + 2 * lane;
-    if (j0 + 1 >= w.off && j0 < (long long)w.off + w.cnt) {
-        if (j0 + 1 < a.n_samples) {
-            const float2 u = __ldg(reinterpret_cast<const float2*>(a.t_starts + j0));
-            const float2 v = __ldg(reinterpret_cast<const float2*>(a.t_ends + j0));
-            const float2 g = __ldg(reinterpret_cast<const float2*>(a.sigmas + j0));
-            p.s0[0] = u.x; p.s0[1] = u.y;
-            p.s1[0] = v.x; p.s1[1] = v.y;
-            p.sg[0] = g.x; p.sg[1] = g.y;
-        } else {
-            p.s0[0] = __ldg(a.t_starts + j0);
-            p.s1[0] = __ldg(a.t_ends + j0);
-            p.sg[0] = __ldg(a.sigmas + j0);
-        }
+    p.v0 = w.live && (unsigned)(w.j - w.off) < (unsigned)w.cnt;
+    p.v1 = w.live && (unsigned)(w.j + 1 - w.off) < (unsigned)w.cnt;
+    if (p.v1) {
+        const float2 u = __ldg(reinterpret_cast<const float2*>(a.t_starts + w.j));
+        const float2 v = __ldg(reinterpret_cast<const float2*>(a.t_ends + w.j));
+        const float2 g = __ldg(reinterpret_cast<const float2*>(a.sigmas + w.j));
+        p.s0[0] = u.x; p.s0[1] = u.y;
+        p.s1[0] = v.x; p.s1[1] = v.y;
+        p.sg[0] = g.x; p.sg[1] = g.y;
+    } else if (p.v0) {
+        p.s0[0] = __ldg(a.t_starts + w.j);
+        p.s1[0] = __ldg(a.t_ends + w.j);
+        p.sg[0] = __ldg(a.sigmas + w.j);
     }
 }
 
 // Decide one chunk of 64 samples of the ray (call with w.live, warp-uniform).
 __device__ __forceinline__ void walk_step(RayWalk& w, const PruneArgs& a, int lane, const Pair& p) {
-    const long long j0 = (long long)w.abase + ((long long)w.c << 6) + 2 * lane;
-    const long long end = (long long)w.off + w.cnt;
-    const bool v0 = j0 >= w.off && j0 < end;
-    const bool v1 = j0 + 1 >= w.off && j0 + 1 < end;
-    const float tau0 = v0 ? __fmul_rn(p.sg[0], __fsub_rn(p.s1[0], p.s0[0])) : 0.0f;
-    const float tau1 = v1 ? __fmul_rn(p.sg[1], __fsub_rn(p.s1[1], p.s0[1])) : 0.0f;
+    const float tau0 = p.v0 ? __fmul_rn(p.sg[0], __fsub_rn(p.s1[0], p.s0[0])) : 0.0f;
+    const float tau1 = p.v1 ? __fmul_rn(p.sg[1], __fsub_rn(p.s1[1], p.s0[1])) : 0.0f;
     const float incl = warp_incl_scan(__fadd_rn(tau0, tau1), lane);
     float excl = __shfl_up_sync(FULL, incl, 1);
     if (lane == 0) excl = 0.0f;
     const float O0 = __fadd_rn(w.carry, excl);
     const float O1 = __fadd_rn(O0, tau0);
-    bool k0 = v0, k1 = v1;
+    bool k0 = p.v0, k1 = p.v1;
     if (a.use_t) {
         k0 = k0 && (O0 <= a.thr_o);
         k1 = k1 && (O1 <= a.thr_o);
@@ -135,6 +132,7 @@ __device__ __forceinline__ void walk_step(RayWalk& w, const PruneArgs& a, int la
     w.count += __popc(m0) + __popc(m1);
     w.carry = __fadd_rn(w.carry, __shfl_sync(FULL, incl, 31));
     ++w.c;
+    w.j += 64;
     // every later O_i >= carry once tau >= 0: the rest of the ray is dropped unread
     if (w.c >= w.nch || (a.use_t && !(w.carry <= a.thr_o))) w.live = false;
 }
@@ -152,7 +150,7 @@ __device__ __forceinline__ void phase1_walk(const PruneArgs& a, int ray0, int nr
         for (int j = 0; j < IL; ++j) {
             const int off = __shfl_sync(FULL, my_off, (i + j) & 31);
             const int cnt = __shfl_sync(FULL, my_cnt, (i + j) & 31);
-            walk_init(W[j], a, off, i + j < nr ? cnt : 0, ray0 + i + j);
+            walk_init(W[j], a, off, i + j < nr ? cnt : 0, ray0 + i + j, lane);
         }
         for (;;) {
             bool any = false;
@@ -161,7 +159,7 @@ __device__ __forceinline__ void phase1_walk(const PruneArgs& a, int ray0, int nr
             if (!any) break;
             Pair P[IL];
 #pragma unroll
-            for (int j = 0; j < IL; ++j) walk_load(W[j], a, lane, W[j].c, P[j]);
+            for (int j = 0; j < IL; ++j) walk_load(W[j], a, P[j]);
 #pragma unroll
             for (int j = 0; j < IL; ++j)
                 if (W[j].live) walk_step(W[j], a, lane, P[j]);
