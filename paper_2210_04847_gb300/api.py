@@ -55,7 +55,11 @@ class OccupancyGrid:
         return g
 
     def struct(self) -> _lib.Grid:
-        return _lib.make_grid(self.bits, self.res, self.aabb, self.n_levels, self.n_slots, self.contraction)
+        s = getattr(self, "_struct", None)
+        if s is None or s._keepalive is not self.bits:  # built once per bits tensor
+            s = _lib.make_grid(self.bits, self.res, self.aabb, self.n_levels, self.n_slots, self.contraction)
+            self._struct = s
+        return s
 
     def sample_cells(self, n: int, seed: int = 0, step: int = 0):
         """n uniform random cells of the grid (all levels and slots) and a uniform
@@ -98,12 +102,27 @@ class _Scratch:
 
 _SCRATCH = _Scratch()
 _CAP_HINT = {}
+_PARAMS = {}
+
+
+def _params(near_plane, far_plane, render_step_size, dt_max, cone_angle, max_steps) -> _lib.MarchParams:
+    key = (near_plane, far_plane, render_step_size, dt_max, cone_angle, max_steps)
+    p = _PARAMS.get(key)
+    if p is None:
+        p = _PARAMS[key] = _lib.make_params(near_plane, far_plane, render_step_size, dt_max, cone_angle, max_steps)
+    return p
 
 
 def _count_and_status(dev):
     """One int64 pair on the device: [count, status]; the status word is the low
-    half of the second element (read back together, one synchronisation)."""
-    cs = torch.zeros(2, dtype=torch.int64, device=dev)
+    half of the second element (read back together, one synchronisation). One
+    buffer per device, zeroed on the stream before each use (every caller reads it
+    back before returning)."""
+    cs = _SCRATCH.bufs.get(("count_status", str(dev)))
+    if cs is None:
+        cs = _SCRATCH.bufs[("count_status", str(dev))] = torch.zeros(2, dtype=torch.int64, device=dev)
+    else:
+        cs.zero_()
     return cs, cs[0:1], cs[1:2].view(torch.int32)[:1]
 
 
@@ -121,7 +140,7 @@ def march_rays(rays_o, rays_d, grid: OccupancyGrid, near_plane=0.0, far_plane=1e
     rays_o = rays_o.contiguous().float()
     rays_d = rays_d.contiguous().float()
     R = rays_o.shape[0]
-    params = _lib.make_params(near_plane, far_plane, render_step_size, dt_max, cone_angle, max_steps)
+    params = _params(near_plane, far_plane, render_step_size, dt_max, cone_angle, max_steps)
     ws = _SCRATCH.get("march_ws", _lib.march_workspace_size(R, params), dev)
     packed = torch.empty((R, 2), dtype=torch.int32, device=dev)
     cs, counter, status = _count_and_status(dev)
@@ -157,7 +176,10 @@ class DensityGrid:
         self.aabb = tuple(float(v) for v in aabb)
 
     def struct(self) -> _lib.DensityField:
-        return _lib.make_density_field(self.sigma, self.aabb)
+        s = getattr(self, "_struct", None)
+        if s is None or s._keepalive is not self.sigma:
+            s = self._struct = _lib.make_density_field(self.sigma, self.aabb)
+        return s
 
     def __call__(self, xyz: torch.Tensor) -> torch.Tensor:
         """sigma at points xyz (n, 3)."""
@@ -188,7 +210,7 @@ def march_with_density(rays_o, rays_d, grid: OccupancyGrid, density: DensityGrid
     rays_o = rays_o.contiguous().float()
     rays_d = rays_d.contiguous().float()
     R = rays_o.shape[0]
-    params = _lib.make_params(near_plane, far_plane, render_step_size, dt_max, cone_angle, max_steps)
+    params = _params(near_plane, far_plane, render_step_size, dt_max, cone_angle, max_steps)
     ws = _SCRATCH.get("march_ws", _lib.march_workspace_size(R, params), dev)
     packed = torch.empty((R, 2), dtype=torch.int32, device=dev)
     cs, counter, status = _count_and_status(dev)
