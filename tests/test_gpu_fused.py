@@ -316,3 +316,70 @@ def test_api_march_with_density_then_render(inf):
     color, opacity, depth = api.render_packed(sg.view(-1), rgb, packed, ts.view(-1), te.view(-1))
     assert torch.isfinite(color).all() and float(opacity.max()) <= 1.0 + 1e-6
     assert float(opacity.mean()) > 0.05
+
+
+@pytest.mark.parametrize("eps,thre", [(1.0, 0.0), (0.5, 0.5), (1e-8, 0.999), (0.9999, 1e-6)])
+def test_fused_extreme_thresholds(orc, eps, thre):
+    w = _subset(synth.inference_config(0, field_res=33), 401)
+    m, sig, od, p, p_sig = oracle_reference(orc, w, eps, thre)
+    g = gpu_fused(w, eps, thre)
+    assert_fused_matches(g, m, sig, od, p, p_sig, eps)
+
+
+def test_fused_multislot_grid_uses_slot_zero(inf):
+    """A grid with several slots: the fused path (no time or slot input) uses slot 0."""
+    w = inf
+    other = np.zeros_like(w.bits)  # slot 1: empty
+    two = np.concatenate([w.bits, other])
+    o, d = dev(w.rays_o), dev(w.rays_d)
+    ft = dev(w.field)
+    params = _lib.make_params(w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone, w.max_steps)
+    R = o.shape[0]
+    out = []
+    for bits_np, slots in ((w.bits, 1), (two, 2)):
+        bits = dev(bits_np)
+        grid = _lib.make_grid(bits, w.res, w.aabb, 1, slots, 0)
+        ws = torch.zeros(_lib.march_workspace_size(R, params), dtype=torch.uint8, device="cuda")
+        pi = torch.zeros((R, 2), dtype=torch.int32, device="cuda")
+        cap = R * 1024
+        ts, te, sg = (torch.zeros(cap, device="cuda") for _ in range(3))
+        ri = torch.zeros(cap, dtype=torch.int32, device="cuda")
+        n = torch.zeros(1, dtype=torch.int64, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        _lib.march_fused(o, d, grid, params, _lib.make_density_field(ft, w.field_box), w.early_stop_eps,
+                         w.alpha_thre, pi, ts, te, ri, sg, n, st, ws)
+        torch.cuda.synchronize()
+        k = int(n.item())
+        out.append((pi.cpu().numpy(), ts[:k].cpu().numpy(), sg[:k].cpu().numpy(), int(st.item())))
+    assert out[0][3] == 0 and out[1][3] == 0
+    assert np.array_equal(out[0][0], out[1][0]) and bits_equal(out[0][1], out[1][1]) and bits_equal(out[0][2], out[1][2])
+
+
+def test_fused_nonfinite_rays_emit_nothing(inf):
+    o = inf.rays_o[:64].copy()
+    d = inf.rays_d[:64].copy()
+    o[3, 0] = np.nan
+    d[7, 1] = np.inf
+    o[11, 2] = -np.inf
+    g = gpu_fused(inf, rays=(o, d))
+    ref = gpu_fused(inf, rays=(inf.rays_o[:64], inf.rays_d[:64]))
+    assert g["status"] == 0
+    for r in (3, 7, 11):
+        assert g["pi"][r, 1] == 0
+    keep = [r for r in range(64) if r not in (3, 7, 11)]
+    assert np.array_equal(g["pi"][keep, 1], ref["pi"][keep, 1])
+
+
+def test_api_march_with_density_empty_batch(inf):
+    from paper_2210_04847_gb300 import api
+
+    grid = api.OccupancyGrid.from_bits(inf.bits, inf.res, inf.aabb, device="cuda")
+    dens = api.DensityGrid(dev(inf.field), inf.field_box)
+    z = torch.zeros((0, 3), device="cuda")
+    packed, ts, te, sg = api.march_with_density(z, z, grid, dens, render_step_size=inf.dt_min)
+    assert packed.shape == (0, 2) and ts.shape == (0, 1) and sg.shape == (0, 1)
+    # rays that miss the box: packed counts zero, no samples
+    o = torch.tensor([[5.0, 5.0, 5.0], [0.0, 9.0, 0.0]], device="cuda")
+    d = torch.tensor([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]], device="cuda")
+    packed, ts, te, sg = api.march_with_density(o, d, grid, dens, render_step_size=inf.dt_min)
+    assert packed[:, 1].sum().item() == 0 and ts.numel() == 0
