@@ -67,7 +67,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--rays", type=int, default=N_RAYS)
+    ap.add_argument("--rays", type=int, default=N_RAYS,
+                    help="rays per step (bounded: 2^18 by default; unbounded, contracted, dynamic: their own size unless given)")
     ap.add_argument("--workload", default="bounded",
                     choices=["bounded", "tiny", "unbounded", "contracted", "batched", "dynamic", "dynamic_shared",
                              "inference"],
@@ -363,7 +364,7 @@ def run_ours(args):
     from paper_2210_04847_gb300.pipeline import HotPath
     from paper_2210_04847_gb300.scenarios import make_scenario
 
-    sc = make_scenario(args.workload, rank, dev, n_rays=args.rays if args.workload == "bounded" else None)
+    sc = make_scenario(args.workload, rank, dev, n_rays=args.rays if args.rays != N_RAYS or args.workload == "bounded" else None)
     w = sc.w
     R = w.n_rays
     n_pool = len(sc.batches)
