@@ -45,6 +45,41 @@ __global__ void __launch_bounds__(kThreads) decay_pack_kernel(float* ema, uint32
     }
 }
 
+// The same pass, four cells per thread (one 16-byte load and store) over whole
+// warp steps of 128 cells, two steps in flight per thread: cell 4 lane + j of a
+// step is bit 4 (lane % 8) + j of the step's word lane / 8, so each word gathers
+// the four-bit groups of eight lanes by three shuffles.
+__global__ void __launch_bounds__(kThreads) decay_pack4_kernel(float4* __restrict__ ema4,
+                                                               uint32_t* __restrict__ bits, int64_t n_steps,
+                                                               float decay, float thre) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_steps; w += 2 * warps) {
+        const int64_t w2 = w + warps;
+        const bool two = w2 < n_steps;
+        float4 v = ema4[(w << 5) + lane];
+        float4 u = two ? ema4[(w2 << 5) + lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float4& q = h ? u : v;
+            if (h && !two) break;
+            q.x = __fmul_rn(decay, q.x);
+            q.y = __fmul_rn(decay, q.y);
+            q.z = __fmul_rn(decay, q.z);
+            q.w = __fmul_rn(decay, q.w);
+            const int64_t step = h ? w2 : w;
+            ema4[(step << 5) + lane] = q;
+            unsigned word = ((unsigned)(q.x > thre) | ((unsigned)(q.y > thre) << 1) | ((unsigned)(q.z > thre) << 2) |
+                             ((unsigned)(q.w > thre) << 3))
+                            << (4 * (lane & 7));
+            word |= __shfl_xor_sync(FULL, word, 1);
+            word |= __shfl_xor_sync(FULL, word, 2);
+            word |= __shfl_xor_sync(FULL, word, 4);
+            if ((lane & 7) == 0) bits[(step << 2) + (lane >> 3)] = word;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) scatter_max_kernel(float* ema, uint32_t* bits, int64_t n_cells,
                                                                const int32_t* cells, const float* sigmas,
                                                                int64_t n, float thre, int32_t* d_status) {
@@ -133,7 +168,7 @@ __global__ void __launch_bounds__(kThreads) sample_cells_kernel(const SampleArgs
             float sc = 1.0f;
             if (!(r2 <= 1.0f)) {
                 const float r = __fsqrt_rn(r2);
-                sc = r < 2.0f ? __fdiv_rn(1.0f, __fmul_rn(__fsub_rn(2.0f, r), r)) : __int_as_float(0x7fc00000);
+                sc = r < 2.0f ? __frcp_rn(__fmul_rn(__fsub_rn(2.0f, r), r)) : __int_as_float(0x7fc00000);
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) p[k] = __fadd_rn(a.cc[k], __fmul_rn(a.hh[k], __fmul_rn(p[k], sc)));
@@ -207,11 +242,24 @@ extern "C" int nacc_update_occupancy_grid(float* ema, uint32_t* bits, int64_t n_
     cudaStream_t st = (cudaStream_t)stream;
     const DeviceInfo dev = current_device();
     if (n_cells > 0) {
-        const int64_t words = (n_cells + 31) >> 5;
-        int64_t blocks = (words * 32 + kThreads - 1) / kThreads;
         const int64_t cap = (int64_t)dev.sm_count * 8;
-        if (blocks > cap) blocks = cap;
-        decay_pack_kernel<<<(int)blocks, kThreads, 0, st>>>(ema, bits, n_cells, decay, thre);
+        // whole 128-cell steps four cells per thread when the state is 16-byte aligned,
+        // the rest (and unaligned states) one cell per thread
+        const int64_t steps = (((uintptr_t)ema & 15u) == 0) ? n_cells >> 7 : 0;
+        if (steps > 0) {
+            int64_t blocks = (steps * 32 + kThreads - 1) / kThreads;
+            if (blocks > cap) blocks = cap;
+            decay_pack4_kernel<<<(int)blocks, kThreads, 0, st>>>(reinterpret_cast<float4*>(ema), bits, steps, decay,
+                                                                  thre);
+        }
+        const int64_t done = steps << 7;
+        if (done < n_cells) {
+            const int64_t words = ((n_cells - done) + 31) >> 5;
+            int64_t blocks = (words * 32 + kThreads - 1) / kThreads;
+            if (blocks > cap) blocks = cap;
+            decay_pack_kernel<<<(int)blocks, kThreads, 0, st>>>(ema + done, bits + (done >> 5), n_cells - done,
+                                                                 decay, thre);
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return NACC_ERR_CUDA;
     }

@@ -120,7 +120,7 @@ __device__ __forceinline__ bool occupied(const MarchArgs& a, float x0, float x1,
         const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(x[0], x[0]), __fmul_rn(x[1], x[1])), __fmul_rn(x[2], x[2]));
         if (!(n2 <= 1.0f)) {
             const float n = __fsqrt_rn(n2);
-            const float s = __fdiv_rn(__fsub_rn(2.0f, __fdiv_rn(1.0f, n)), n);
+            const float s = __fdiv_rn(__fsub_rn(2.0f, __frcp_rn(n)), n);  // __frcp_rn(n) is the correctly rounded 1/n
 #pragma unroll
             for (int k = 0; k < 3; ++k) x[k] = __fmul_rn(x[k], s);
         }

@@ -272,15 +272,19 @@ def test_render_bad_packed_info_is_reported():
     assert op.cpu().numpy()[1] == 0.0
 
 
-@pytest.mark.parametrize("n_cells", [64 ** 3, 1000, 33])
-def test_grid_update_bitexact(orc, n_cells):
+@pytest.mark.parametrize("n_cells,shift", [(64 ** 3, 0), (1000, 0), (33, 0), (128 * 77 + 96, 0), (1000, 1),
+                                           (64 ** 3, 3)])
+def test_grid_update_bitexact(orc, n_cells, shift):
+    """Whole 128-cell steps (16-byte aligned state, four cells per thread), ragged
+    tails and unaligned states (one cell per thread) give the oracle's grid."""
     ema = synth.rand_uniform(5, 1, n_cells, 0, 0.03).astype(np.float32)
     n = 1 << 16
     cells = synth.rand_int(5, 2, n, n_cells).astype(np.int32)
     sig = (synth.rand_uniform(5, 3, n) ** 3 * 0.05).astype(np.float32)
     sig[::97] = np.nan
     sig[1::89] = -1.0
-    e_t, b_t = dev(ema), torch.zeros((n_cells + 31) // 32, dtype=torch.int32, device="cuda")
+    e_t = dev(np.concatenate([np.zeros(shift, np.float32), ema]))[shift:]  # shift > 0: not 16-byte aligned
+    b_t = torch.zeros((n_cells + 31) // 32, dtype=torch.int32, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     _lib.update_occupancy_grid(e_t, b_t, dev(cells), dev(sig), 0.95, 0.01, st)
     torch.cuda.synchronize()
