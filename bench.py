@@ -195,10 +195,15 @@ def stage_bytes(R, M, M_read, S, grid_bytes, n_cells, n_grid, saved_od=False):
 
 
 def kernel_source_sha(stage: str) -> str:
-    f = {"march": "march.cu", "prune": "prune.cu", "render_fwd": "render.cu", "render_bwd": "render.cu",
-         "grid_update": "grid.cu", "march_fused": "fused.cu"}[stage]
-    with open(os.path.join(ROOT, "paper_2210_04847_gb300", "csrc", f), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()
+    """SHA-256 over the sources a stage's kernel is compiled from."""
+    files = {"march": ("march.cu", "march_common.cuh", "nacc_internal.cuh"), "prune": ("prune.cu", "nacc_internal.cuh"),
+             "render_fwd": ("render.cu",), "render_bwd": ("render.cu",), "grid_update": ("grid.cu",),
+             "march_fused": ("fused.cu", "march_common.cuh", "nacc_internal.cuh")}[stage]
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2210_04847_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def measured_peaks():
