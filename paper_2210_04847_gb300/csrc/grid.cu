@@ -81,12 +81,13 @@ __global__ void __launch_bounds__(kThreads) decay_pack4_kernel(float4* __restric
 }
 
 __global__ void __launch_bounds__(kThreads) scatter_max_kernel(float* ema, uint32_t* bits, int64_t n_cells,
-                                                               const int32_t* cells, const float* sigmas,
-                                                               int64_t n, float thre, int32_t* d_status) {
+                                                               const int32_t* __restrict__ cells,
+                                                               const float* __restrict__ sigmas, int64_t n, float thre,
+                                                               int32_t* d_status) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += stride) {
-        const int c = cells[s];
-        const float v = sigmas[s];
+        const int c = __ldg(cells + s);
+        const float v = __ldg(sigmas + s);
         if (c < 0 || (int64_t)c >= n_cells) {
             raise_status(d_status, NACC_STATUS_BAD_INDEX);
             continue;
@@ -264,9 +265,11 @@ extern "C" int nacc_update_occupancy_grid(float* ema, uint32_t* bits, int64_t n_
         if (e != cudaSuccess) return NACC_ERR_CUDA;
     }
     if (n_samples > 0) {
+        // one sample per thread (up to 2^31 - 1 blocks): every thread's loads and
+        // fire-and-forget atomics are in flight at once; the latency of the random
+        // updates, not the issue rate, bounds this pass
         int64_t blocks = (n_samples + kThreads - 1) / kThreads;
-        const int64_t cap = (int64_t)dev.sm_count * 8;
-        if (blocks > cap) blocks = cap;
+        if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
         scatter_max_kernel<<<(int)blocks, kThreads, 0, st>>>(ema, bits, n_cells, cells, sigmas, n_samples, thre,
                                                              d_status);
     }
