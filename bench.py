@@ -45,10 +45,10 @@ POOL = 4  # distinct ray batches cycled through the steps (L2 is flushed between
 # from one ncu capture, keyed by the SHA-256 of the kernel's source file. A
 # source change invalidates the figure (reported as null until re-captured).
 NCU_TRAFFIC = {
-    # profiles/march_dram_bounded-2^18.md: 7960832 B read + 1476889600 B written
-    ("march", "9621414803e06b8a6c50ce7bc2043ffbf9089d1ed8a984123f45910167f9ea14"): 1484850432,
-    # profiles/march_fused_inference-800x800.md: 22238976 B read + 1169516544 B written (camera 0's image)
-    ("march_fused", "2335f145b362d44a6673d8a8faa4167b28e80af11fb579d3863c6c275a679001"): 1191755520,
+    # profiles/march_dram_bounded-2^18.md: 7927040 B read + 1476724480 B written
+    ("march", "8c7b903e4b1cfc7191f5e4bd608daf2ebccecaa5d4101ca8b15d2eb0b1be155c"): 1484651520,
+    # profiles/march_fused_inference-800x800.md: 22437376 B read + 1169642240 B written (camera 0's image)
+    ("march_fused", "c86e1bad5b55ca339d49805cf9ac418869661e8853df2abc21f41da92b781990"): 1192079616,
 }
 
 # What limits each stage (from the ncu captures summarised under profiles/).
