@@ -68,7 +68,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rays", type=int, default=N_RAYS,
-                    help="rays per step (bounded: 2^18 by default; unbounded, contracted, dynamic: their own size unless given)")
+                    help="rays per step (bounded: 2^18 by default; unbounded, contracted, dynamic: their own size "
+                         "unless given)")
     ap.add_argument("--workload", default="bounded",
                     choices=["bounded", "tiny", "unbounded", "contracted", "batched", "dynamic", "dynamic_shared",
                              "inference"],
@@ -369,7 +370,8 @@ def run_ours(args):
     from paper_2210_04847_gb300.pipeline import HotPath
     from paper_2210_04847_gb300.scenarios import make_scenario
 
-    sc = make_scenario(args.workload, rank, dev, n_rays=args.rays if args.rays != N_RAYS or args.workload == "bounded" else None)
+    n_rays = args.rays if args.rays != N_RAYS or args.workload == "bounded" else None
+    sc = make_scenario(args.workload, rank, dev, n_rays=n_rays)
     w = sc.w
     R = w.n_rays
     n_pool = len(sc.batches)
@@ -424,33 +426,41 @@ def run_ours(args):
         b = i % n_pool
         bt = sc.batches[b]
         gi = grid_inputs[i % POOL]
+        # each stage's call is marshalled before its start event is recorded, so the
+        # events bracket the C call and its kernels, not Python argument handling
         flush.zero_()
+        run = hp.march(bt["o"], bt["d"], bt["time"], bt["slot"], defer=True)
         ev["march"][0].record()
-        hp.march(bt["o"], bt["d"], bt["time"], bt["slot"])
+        run()
         ev["march"][1].record()
         M = int(hp.n_m.item())
         sc.field_marched(hp, b, M)
+        run = hp.prune(M, defer=True)
         ev["prune"][0].record()
-        hp.prune(M)
+        run()
         ev["prune"][1].record()
         S = int(hp.n_k.item())
         sc.field_kept(hp, b, S)
+        run = hp.render_fwd(S, defer=True)
         ev["render_fwd"][0].record()
-        hp.render_fwd(S)
+        run()
         ev["render_fwd"][1].record()
         hp.loss_grad(bt["tgt"])
+        run = hp.render_bwd(S, defer=True)
         ev["render_bwd"][0].record()
-        hp.render_bwd(S)
+        run()
         ev["render_bwd"][1].record()
         # the update's random cells and points come from the library (device
         # sampler, the same streams as the host generator behind grid_inputs, so
         # gi describes the same points for the field's per-scene grouping)
+        run = hp.sample_cells(rank, i % POOL, defer=True)
         ev_sample[0].record()
-        hp.sample_cells(rank, i % POOL)
+        run()
         ev_sample[1].record()
         sc.grid_field(gi, hp.cell_sig, xyz=hp.cell_xyz, cells=hp.cells)
+        run = hp.grid_update(bits=upd_bits, defer=True)
         ev["grid_update"][0].record()
-        hp.grid_update(bits=upd_bits)
+        run()
         ev["grid_update"][1].record()
         torch.cuda.synchronize()
         hp.check_status("step %d" % i)
@@ -618,13 +628,16 @@ def run_inference(args):
         o, d = batches[i % POOL]
         flush.zero_()
         ev = evs(4)
+        run = _lib.march_fused(o, d, grid, params, fld, eps, thre, pi_f, ts_f, te_f, ri_f, sg_f, n_f, st, ws_m,
+                               defer=True)
         ev[0].record()
-        _lib.march_fused(o, d, grid, params, fld, eps, thre, pi_f, ts_f, te_f, ri_f, sg_f, n_f, st, ws_m)
+        run()
         ev[1].record()
         S = int(n_f.item())
         field.samples(o, d, ri_f, ts_f, te_f, S, tmp, rgb)  # the user's network: colour of the kept samples
+        run = _lib.render_fwd(pi_f, ts_f, te_f, sg_f, rgb, S, color, opacity, depth, d_status=st, defer=True)
         ev[2].record()
-        _lib.render_fwd(pi_f, ts_f, te_f, sg_f, rgb, S, color, opacity, depth, d_status=st)
+        run()
         ev[3].record()
         torch.cuda.synchronize()
         if int(st.item()) != 0 or S > cap_s:
@@ -636,19 +649,25 @@ def run_inference(args):
         o, d = batches[i % POOL]
         flush.zero_()
         ev = evs(8)
+        run = _lib.march_rays(o, d, grid, params, pi_m, ts_m, te_m, ri_m, n_m, st, ws_m, defer=True)
         ev[0].record()
-        _lib.march_rays(o, d, grid, params, pi_m, ts_m, te_m, ri_m, n_m, st, ws_m)
+        run()
         ev[1].record()
         M = int(n_m.item())
+        runs = (_lib.density_field_at_samples(fld, o, d, ri_m, ts_m, te_m, M, sg_m, st, defer=True),
+                _lib.prune_samples(pi_m, ts_m, te_m, sg_m, M, eps, thre, pi_k, ts_k, te_k, ri_k, n_k, st, ws_p,
+                                   defer=True))
         ev[2].record()
-        _lib.density_field_at_samples(fld, o, d, ri_m, ts_m, te_m, M, sg_m, st)
-        _lib.prune_samples(pi_m, ts_m, te_m, sg_m, M, eps, thre, pi_k, ts_k, te_k, ri_k, n_k, st, ws_p)
+        for run in runs:
+            run()
         ev[3].record()
         S = int(n_k.item())
         field.samples(o, d, ri_k, ts_k, te_k, S, tmp, rgb)
+        runs = (_lib.density_field_at_samples(fld, o, d, ri_k, ts_k, te_k, S, sg_k, st, defer=True),
+                _lib.render_fwd(pi_k, ts_k, te_k, sg_k, rgb, S, color, opacity, depth, d_status=st, defer=True))
         ev[4].record()
-        _lib.density_field_at_samples(fld, o, d, ri_k, ts_k, te_k, S, sg_k, st)
-        _lib.render_fwd(pi_k, ts_k, te_k, sg_k, rgb, S, color, opacity, depth, d_status=st)
+        for run in runs:
+            run()
         ev[5].record()
         torch.cuda.synchronize()
         if int(st.item()) != 0 or M > cap_m or S > cap_s:

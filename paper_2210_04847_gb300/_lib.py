@@ -178,6 +178,20 @@ def _check(t: Optional[torch.Tensor], dtype, name: str, numel: Optional[int] = N
         raise NaccError("%s holds %d elements, needs %d" % (name, t.numel(), numel))
 
 
+def _call(name: str, args, defer: bool):
+    """Call C entry point ``name`` with marshalled ``args``; with ``defer`` return
+    a callable that makes the call later (marshalling and checks already done, so
+    the call itself costs only the C function: a timed region can start right
+    before it)."""
+    fn = getattr(load(), name)
+    if defer:
+        def run():
+            _rc(fn(*args), name)
+        return run
+    _rc(fn(*args), name)
+    return None
+
+
 def _rc(code: int, fn: str):
     if code != OK:
         msg = load().nacc_error_string(code).decode()
@@ -240,7 +254,7 @@ def prune_workspace_size(n_rays: int, n_samples: int) -> int:
 
 
 def march_rays(rays_o, rays_d, grid: Grid, params: MarchParams, packed_info, t_starts, t_ends, ray_indices,
-               n_samples, d_status, workspace, ray_time=None, ray_slot=None, stream=None):
+               n_samples, d_status, workspace, ray_time=None, ray_slot=None, stream=None, defer: bool = False):
     n = rays_o.shape[0]
     _check(rays_o, torch.float32, "rays_o", 3 * n)
     _check(rays_d, torch.float32, "rays_d", 3 * n)
@@ -254,11 +268,10 @@ def march_rays(rays_o, rays_d, grid: Grid, params: MarchParams, packed_info, t_s
     _check(n_samples, torch.int64, "n_samples", 1)
     _check(d_status, torch.int32, "d_status", 1, optional=True)
     _check(workspace, torch.uint8, "workspace")
-    rc = load().nacc_march_rays(
-        _ptr(rays_o), _ptr(rays_d), _ptr(ray_time), _ptr(ray_slot), n, ctypes.byref(grid), ctypes.byref(params),
-        _ptr(packed_info), _ptr(t_starts), _ptr(t_ends), _ptr(ray_indices), cap, _ptr(n_samples), _ptr(d_status),
-        _ptr(workspace), workspace.numel(), _stream(stream))
-    _rc(rc, "nacc_march_rays")
+    args = (_ptr(rays_o), _ptr(rays_d), _ptr(ray_time), _ptr(ray_slot), n, ctypes.byref(grid), ctypes.byref(params),
+            _ptr(packed_info), _ptr(t_starts), _ptr(t_ends), _ptr(ray_indices), cap, _ptr(n_samples),
+            _ptr(d_status), _ptr(workspace), workspace.numel(), _stream(stream))
+    return _call("nacc_march_rays", args, defer)
 
 
 STATIC_MAX_RAYS = 1 << 20
@@ -288,7 +301,8 @@ def march_rays_static(rays_o, rays_d, grid: Grid, params: MarchParams, packed_in
 
 
 def march_fused(rays_o, rays_d, grid: Grid, params: MarchParams, field: DensityField, early_stop_eps, alpha_thre,
-                packed_info, t_starts, t_ends, ray_indices, sigmas, n_samples, d_status, workspace, stream=None):
+                packed_info, t_starts, t_ends, ray_indices, sigmas, n_samples, d_status, workspace, stream=None,
+                defer: bool = False):
     """nacc_march_fused: marching that stops on the density field's transmittance
     (inference); writes only the kept samples (and their sigma when given)."""
     n = rays_o.shape[0]
@@ -303,16 +317,15 @@ def march_fused(rays_o, rays_d, grid: Grid, params: MarchParams, field: DensityF
     _check(n_samples, torch.int64, "n_samples", 1)
     _check(d_status, torch.int32, "d_status", 1, optional=True)
     _check(workspace, torch.uint8, "workspace")
-    rc = load().nacc_march_fused(
-        _ptr(rays_o), _ptr(rays_d), n, ctypes.byref(grid), ctypes.byref(params), ctypes.byref(field),
-        float(early_stop_eps), float(alpha_thre), _ptr(packed_info), _ptr(t_starts), _ptr(t_ends),
-        _ptr(ray_indices), _ptr(sigmas), cap, _ptr(n_samples), _ptr(d_status), _ptr(workspace), workspace.numel(),
-        _stream(stream))
-    _rc(rc, "nacc_march_fused")
+    args = (_ptr(rays_o), _ptr(rays_d), n, ctypes.byref(grid), ctypes.byref(params), ctypes.byref(field),
+            float(early_stop_eps), float(alpha_thre), _ptr(packed_info), _ptr(t_starts), _ptr(t_ends),
+            _ptr(ray_indices), _ptr(sigmas), cap, _ptr(n_samples), _ptr(d_status), _ptr(workspace),
+            workspace.numel(), _stream(stream))
+    return _call("nacc_march_fused", args, defer)
 
 
 def density_field_at_samples(field: DensityField, rays_o, rays_d, ray_indices, t_starts, t_ends, n_samples: int,
-                             sigmas, d_status=None, stream=None):
+                             sigmas, d_status=None, stream=None, defer: bool = False):
     n = rays_o.shape[0]
     _check(rays_o, torch.float32, "rays_o", 3 * n)
     _check(rays_d, torch.float32, "rays_d", 3 * n)
@@ -320,10 +333,9 @@ def density_field_at_samples(field: DensityField, rays_o, rays_d, ray_indices, t
         _check(t, torch.float32, name, n_samples)
     _check(ray_indices, torch.int32, "ray_indices", n_samples)
     _check(d_status, torch.int32, "d_status", 1, optional=True)
-    rc = load().nacc_density_field_at_samples(
-        ctypes.byref(field), _ptr(rays_o), _ptr(rays_d), n, _ptr(ray_indices), _ptr(t_starts), _ptr(t_ends),
-        int(n_samples), _ptr(sigmas), _ptr(d_status), _stream(stream))
-    _rc(rc, "nacc_density_field_at_samples")
+    args = (ctypes.byref(field), _ptr(rays_o), _ptr(rays_d), n, _ptr(ray_indices), _ptr(t_starts), _ptr(t_ends),
+            int(n_samples), _ptr(sigmas), _ptr(d_status), _stream(stream))
+    return _call("nacc_density_field_at_samples", args, defer)
 
 
 def density_field_query(field: DensityField, xyz, n: int, sigmas, stream=None):
@@ -335,7 +347,7 @@ def density_field_query(field: DensityField, xyz, n: int, sigmas, stream=None):
 
 def prune_samples(packed_info, t_starts, t_ends, sigmas, n_samples_in: int, early_stop_eps, alpha_thre,
                   packed_info_out, t_starts_out, t_ends_out, ray_indices_out, n_kept, d_status, workspace,
-                  keep_mask=None, stream=None):
+                  keep_mask=None, stream=None, defer: bool = False):
     n = packed_info.shape[0]
     _check(packed_info, torch.int32, "packed_info", 2 * n)
     for t, nm in ((t_starts, "t_starts"), (t_ends, "t_ends"), (sigmas, "sigmas")):
@@ -349,11 +361,11 @@ def prune_samples(packed_info, t_starts, t_ends, sigmas, n_samples_in: int, earl
     _check(keep_mask, torch.uint8, "keep_mask", n_samples_in, optional=True)
     _check(d_status, torch.int32, "d_status", 1, optional=True)
     _check(workspace, torch.uint8, "workspace")
-    rc = load().nacc_prune_samples(
-        _ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), int(n_samples_in), float(early_stop_eps),
-        float(alpha_thre), _ptr(packed_info_out), _ptr(t_starts_out), _ptr(t_ends_out), _ptr(ray_indices_out), cap,
-        _ptr(n_kept), _ptr(keep_mask), _ptr(d_status), _ptr(workspace), workspace.numel(), _stream(stream))
-    _rc(rc, "nacc_prune_samples")
+    args = (_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), int(n_samples_in),
+            float(early_stop_eps), float(alpha_thre), _ptr(packed_info_out), _ptr(t_starts_out), _ptr(t_ends_out),
+            _ptr(ray_indices_out), cap, _ptr(n_kept), _ptr(keep_mask), _ptr(d_status), _ptr(workspace),
+            workspace.numel(), _stream(stream))
+    return _call("nacc_prune_samples", args, defer)
 
 
 def render_weights(packed_info, t_starts, t_ends, sigmas, n_samples: int, weights=None, trans=None, d_status=None,
@@ -414,7 +426,7 @@ def accumulate_along_rays_bwd(packed_info, weights, values, n_channels: int, n_s
 
 
 def render_fwd(packed_info, t_starts, t_ends, sigmas, rgbs, n_samples: int, color, opacity, depth,
-               optical_depth=None, d_status=None, stream=None):
+               optical_depth=None, d_status=None, stream=None, defer: bool = False):
     n = packed_info.shape[0]
     _check(packed_info, torch.int32, "packed_info", 2 * n)
     for t, nm in ((t_starts, "t_starts"), (t_ends, "t_ends"), (sigmas, "sigmas")):
@@ -425,14 +437,13 @@ def render_fwd(packed_info, t_starts, t_ends, sigmas, rgbs, n_samples: int, colo
     _check(depth, torch.float32, "depth", n, optional=True)
     _check(optical_depth, torch.float32, "optical_depth", n_samples, optional=True)
     _check(d_status, torch.int32, "d_status", 1, optional=True)
-    rc = load().nacc_render_fwd(_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), _ptr(rgbs),
-                                int(n_samples), _ptr(color), _ptr(opacity), _ptr(depth), _ptr(optical_depth),
-                                _ptr(d_status), _stream(stream))
-    _rc(rc, "nacc_render_fwd")
+    return _call("nacc_render_fwd", (_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), _ptr(rgbs),
+                                     int(n_samples), _ptr(color), _ptr(opacity), _ptr(depth), _ptr(optical_depth),
+                                     _ptr(d_status), _stream(stream)), defer)
 
 
 def render_bwd(packed_info, t_starts, t_ends, sigmas, rgbs, n_samples: int, g_color, g_opacity, g_depth, d_sigmas,
-               d_rgbs, optical_depth=None, d_status=None, stream=None):
+               d_rgbs, optical_depth=None, d_status=None, stream=None, defer: bool = False):
     n = packed_info.shape[0]
     _check(packed_info, torch.int32, "packed_info", 2 * n)
     for t, nm in ((t_starts, "t_starts"), (t_ends, "t_ends"), (sigmas, "sigmas")):
@@ -445,10 +456,9 @@ def render_bwd(packed_info, t_starts, t_ends, sigmas, rgbs, n_samples: int, g_co
     _check(d_sigmas, torch.float32, "d_sigmas", n_samples)
     _check(d_rgbs, torch.float32, "d_rgbs", 3 * n_samples)
     _check(d_status, torch.int32, "d_status", 1, optional=True)
-    rc = load().nacc_render_bwd(_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), _ptr(rgbs),
-                                _ptr(optical_depth), int(n_samples), _ptr(g_color), _ptr(g_opacity), _ptr(g_depth),
-                                _ptr(d_sigmas), _ptr(d_rgbs), _ptr(d_status), _stream(stream))
-    _rc(rc, "nacc_render_bwd")
+    return _call("nacc_render_bwd", (_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), _ptr(rgbs),
+                                     _ptr(optical_depth), int(n_samples), _ptr(g_color), _ptr(g_opacity), _ptr(g_depth),
+                                     _ptr(d_sigmas), _ptr(d_rgbs), _ptr(d_status), _stream(stream)), defer)
 
 
 def unpack_info(packed_info, n_samples: int, ray_indices, d_status=None, stream=None):
@@ -461,7 +471,7 @@ def unpack_info(packed_info, n_samples: int, ray_indices, d_status=None, stream=
     _rc(rc, "nacc_unpack_info")
 
 
-def update_occupancy_grid(ema, bits, cells, sigmas, decay, thre, d_status=None, stream=None):
+def update_occupancy_grid(ema, bits, cells, sigmas, decay, thre, d_status=None, stream=None, defer: bool = False):
     n_cells = ema.numel()
     _check(ema, torch.float32, "ema")
     _check(bits, torch.int32, "bits", (n_cells + 31) // 32)
@@ -469,19 +479,17 @@ def update_occupancy_grid(ema, bits, cells, sigmas, decay, thre, d_status=None, 
     _check(cells, torch.int32, "cells")
     _check(sigmas, torch.float32, "sigmas", n)
     _check(d_status, torch.int32, "d_status", 1, optional=True)
-    rc = load().nacc_update_occupancy_grid(_ptr(ema), _ptr(bits), n_cells, _ptr(cells), _ptr(sigmas), n,
-                                           float(decay), float(thre), _ptr(d_status), _stream(stream))
-    _rc(rc, "nacc_update_occupancy_grid")
+    return _call("nacc_update_occupancy_grid", (_ptr(ema), _ptr(bits), n_cells, _ptr(cells), _ptr(sigmas), n,
+                                                float(decay), float(thre), _ptr(d_status), _stream(stream)), defer)
 
 
-def sample_grid_cells(seed: int, stream: int, n: int, grid: Grid, cells, xyz, cuda_stream=None):
+def sample_grid_cells(seed: int, stream: int, n: int, grid: Grid, cells, xyz, cuda_stream=None, defer: bool = False):
     """n uniform random cells of the grid and a uniform point in each (SplitMix64
     streams `stream` for the cells and `stream` + 1 for the points)."""
     _check(cells, torch.int32, "cells", n)
     _check(xyz, torch.float32, "xyz", 3 * n)
-    rc = load().nacc_sample_grid_cells(int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream) & 0xFFFFFFFFFFFFFFFF, int(n),
-                                       ctypes.byref(grid), _ptr(cells), _ptr(xyz), _stream(cuda_stream))
-    _rc(rc, "nacc_sample_grid_cells")
+    return _call("nacc_sample_grid_cells", (int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream) & 0xFFFFFFFFFFFFFFFF, int(n),
+                                            ctypes.byref(grid), _ptr(cells), _ptr(xyz), _stream(cuda_stream)), defer)
 
 
 def tune_set(knob, value: int):

@@ -91,43 +91,48 @@ class HotPath:
         self.cell_sig = z(self.n_grid)
 
     # -- stages ------------------------------------------------------------
-    def march(self, rays_o, rays_d, ray_time=None, ray_slot=None):
-        _lib.march_rays(rays_o, rays_d, self.grid, self.params, self.pi_m, self.ts_m[: self.cap_m],
-                        self.te_m[: self.cap_m], self.ri_m[: self.cap_m], self.n_m, self.status, self.ws_march,
-                        ray_time=ray_time, ray_slot=ray_slot)
+    # Each stage runs now, or with defer=True returns the marshalled call to run
+    # later (so a timed region can start right before the C call).
+    def march(self, rays_o, rays_d, ray_time=None, ray_slot=None, defer=False):
+        return _lib.march_rays(rays_o, rays_d, self.grid, self.params, self.pi_m, self.ts_m[: self.cap_m],
+                               self.te_m[: self.cap_m], self.ri_m[: self.cap_m], self.n_m, self.status, self.ws_march,
+                               ray_time=ray_time, ray_slot=ray_slot, defer=defer)
 
-    def prune(self, n_marched: int):
+    def prune(self, n_marched: int, defer=False):
         M = min(int(n_marched), self.cap_m)
-        _lib.prune_samples(self.pi_m, self.ts_m[:M], self.te_m[:M], self.sig_m[:M], M, self.w.early_stop_eps,
-                           self.w.alpha_thre, self.pi_k, self.ts_k[: self.cap_k], self.te_k[: self.cap_k],
-                           self.ri_k[: self.cap_k], self.n_k, self.status, self.ws_prune)
+        return _lib.prune_samples(self.pi_m, self.ts_m[:M], self.te_m[:M], self.sig_m[:M], M, self.w.early_stop_eps,
+                                  self.w.alpha_thre, self.pi_k, self.ts_k[: self.cap_k], self.te_k[: self.cap_k],
+                                  self.ri_k[: self.cap_k], self.n_k, self.status, self.ws_prune, defer=defer)
 
     def _od(self):
         if self.od is None:
             self.od = torch.zeros(max(self.cap_k, 1), dtype=torch.float32, device=self.device)
         return self.od
 
-    def render_fwd(self, n_kept: int):
+    def render_fwd(self, n_kept: int, defer=False):
         S = min(int(n_kept), self.cap_k)
         od = self._od()[:S] if self.save_optical_depth else None
-        _lib.render_fwd(self.pi_k, self.ts_k[:S], self.te_k[:S], self.sig_k[:S], self.rgb_k[:S], S, self.color,
-                        self.opacity, self.depth, optical_depth=od, d_status=self.status)
+        return _lib.render_fwd(self.pi_k, self.ts_k[:S], self.te_k[:S], self.sig_k[:S], self.rgb_k[:S], S, self.color,
+                               self.opacity, self.depth, optical_depth=od, d_status=self.status, defer=defer)
 
-    def render_bwd(self, n_kept: int):
+    def render_bwd(self, n_kept: int, defer=False):
         S = min(int(n_kept), self.cap_k)
         od = self._od()[:S] if self.save_optical_depth else None
-        _lib.render_bwd(self.pi_k, self.ts_k[:S], self.te_k[:S], self.sig_k[:S], self.rgb_k[:S], S, self.g_color,
-                        None, None, self.d_sig[:S], self.d_rgb[:S], optical_depth=od, d_status=self.status)
+        return _lib.render_bwd(self.pi_k, self.ts_k[:S], self.te_k[:S], self.sig_k[:S], self.rgb_k[:S], S, self.g_color,
+                               None, None, self.d_sig[:S], self.d_rgb[:S], optical_depth=od, d_status=self.status,
+                               defer=defer)
 
-    def sample_cells(self, seed: int, step: int):
+    def sample_cells(self, seed: int, step: int, defer=False):
         """Random cells of the grid and a point in each for the update (``cells``, ``cell_xyz``)."""
         if self.n_grid:
-            _lib.sample_grid_cells(seed, 50000 + 4 * step, self.n_grid, self.grid, self.cells, self.cell_xyz)
+            return _lib.sample_grid_cells(seed, 50000 + 4 * step, self.n_grid, self.grid, self.cells, self.cell_xyz,
+                                          defer=defer)
+        return (lambda: None) if defer else None
 
-    def grid_update(self, decay=0.95, thre=0.01, bits=None):
+    def grid_update(self, decay=0.95, thre=0.01, bits=None, defer=False):
         """EMA update of ``self.ema``; writes ``bits`` (default: the bitfield marched by this path)."""
-        _lib.update_occupancy_grid(self.ema, self.bits if bits is None else bits, self.cells[: self.n_grid],
-                                   self.cell_sig[: self.n_grid], decay, thre, self.status)
+        return _lib.update_occupancy_grid(self.ema, self.bits if bits is None else bits, self.cells[: self.n_grid],
+                                          self.cell_sig[: self.n_grid], decay, thre, self.status, defer=defer)
 
     # -- user side (stand-in field, loss) ----------------------------------
     def field_marched(self, field: StandInField, rays_o, rays_d, n_marched, ray_time=None):
