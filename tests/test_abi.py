@@ -89,3 +89,51 @@ def test_workspace_sizes(libs):
     assert lib.nacc_march_workspace_size(1 << 18, ctypes.byref(p)) >= (1 << 18) // 32 * 8
     assert lib.nacc_march_workspace_size(1 << 18, ctypes.byref(p)) % 256 == 0
     assert lib.nacc_prune_workspace_size(1000, 1 << 20) >= ((1 << 20) // 32 + 1000) * 4
+
+
+def test_fused_and_density_field_arguments_rejected_on_host(libs):
+    lib, _ = libs
+    g = _lib.Grid()
+    g.res[0] = g.res[1] = g.res[2] = 4
+    g.n_levels, g.n_slots = 1, 1
+    for k in range(3):
+        g.aabb[k], g.aabb[3 + k] = -1.0, 1.0
+    p = _lib.make_params(0.0, 1e10, 0.01, None, 0.0, 64)
+    f = _lib.DensityField()
+    f.sigma = 4096
+    f.res[0] = f.res[1] = f.res[2] = 3
+    for k in range(3):
+        f.aabb[k], f.aabb[3 + k] = -1.0, 1.0
+    ws = ctypes.c_void_p(1 << 20)  # never touched: every call below is rejected first
+
+    def fused(field=f, grid=g, eps=1e-4, thre=1e-2, n_rays=0, n_samples=ctypes.c_void_p(256), wsb=1 << 16):
+        return lib.nacc_march_fused(None, None, n_rays, ctypes.byref(grid), ctypes.byref(p),
+                                    ctypes.byref(field) if field is not None else None, eps, thre, None, None, None,
+                                    None, None, 0, n_samples, None, ws, wsb, None)
+
+    assert fused(field=None) == _lib.ERR_INVALID_ARG
+    bad = _lib.DensityField.from_buffer_copy(f)
+    bad.res[2] = 1
+    assert fused(field=bad) == _lib.ERR_INVALID_ARG
+    bad = _lib.DensityField.from_buffer_copy(f)
+    bad.aabb[1], bad.aabb[4] = 1.0, -1.0
+    assert fused(field=bad) == _lib.ERR_INVALID_ARG
+    bad = _lib.DensityField.from_buffer_copy(f)
+    bad.sigma = None
+    assert fused(field=bad) == _lib.ERR_INVALID_ARG
+    assert fused(eps=float("nan")) == _lib.ERR_INVALID_ARG
+    assert fused(thre=float("nan")) == _lib.ERR_INVALID_ARG
+    assert fused(n_samples=None) == _lib.ERR_INVALID_ARG
+    assert fused(n_rays=4) == _lib.ERR_INVALID_ARG  # rays and packed_info missing
+    assert fused(wsb=0) == _lib.ERR_INVALID_ARG
+    g2 = _lib.Grid.from_buffer_copy(g)
+    g2.contraction, g2.n_levels = 1, 2  # contraction needs one level
+    assert fused(grid=g2) == _lib.ERR_INVALID_ARG
+    assert lib.nacc_density_field_query(None, None, 1, None, None) == _lib.ERR_INVALID_ARG
+    assert lib.nacc_density_field_query(ctypes.byref(f), None, -1, None, None) == _lib.ERR_INVALID_ARG
+    assert lib.nacc_density_field_query(ctypes.byref(f), None, 5, None, None) == _lib.ERR_INVALID_ARG
+    assert lib.nacc_density_field_at_samples(ctypes.byref(f), None, None, 0, None, None, None, -1, None, None,
+                                             None) == _lib.ERR_INVALID_ARG
+    assert lib.nacc_density_field_at_samples(ctypes.byref(f), None, None, 4, None, None, None, 3, None, None,
+                                             None) == _lib.ERR_INVALID_ARG
+    assert lib.nacc_density_field_query(ctypes.byref(f), None, 0, None, None) == _lib.OK  # nothing to do
