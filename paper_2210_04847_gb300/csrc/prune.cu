@@ -144,31 +144,50 @@ __device__ __forceinline__ void walk_step(RayWalk& w, const PruneArgs& a, int la
 template <int IL>
 __device__ __forceinline__ void phase1_walk(const PruneArgs& a, int ray0, int nr, int my_off, int my_cnt, int lane,
                                             int& my_count, int& my_nch) {
-    for (int i = 0; i < nr; i += IL) {
-        RayWalk W[IL];
+    // IL rays in flight; a slot whose ray has ended takes the tile's next ray, so
+    // the warp keeps IL load streams going while the tile has rays left
+    RayWalk W[IL];
+    int held[IL];  // tile-local index of the ray in each slot, -1 when empty
+    int next = 0;
+    auto start = [&](int j) {
+        held[j] = -1;
+        W[j].live = false;
+        while (next < nr) {
+            const int r = next++;
+            const int off = __shfl_sync(FULL, my_off, r & 31);
+            const int cnt = __shfl_sync(FULL, my_cnt, r & 31);
+            walk_init(W[j], a, off, cnt, ray0 + r, lane);
+            if (W[j].live) {
+                held[j] = r;
+                return;
+            }
+            if (lane == r) {  // a ray without samples
+                my_count = 0;
+                my_nch = 0;
+            }
+        }
+    };
+#pragma unroll
+    for (int j = 0; j < IL; ++j) start(j);
+    for (;;) {
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < IL; ++j) any |= W[j].live;
+        if (!any) break;
+        Pair P[IL];
+#pragma unroll
+        for (int j = 0; j < IL; ++j) walk_load(W[j], a, P[j]);
+#pragma unroll
+        for (int j = 0; j < IL; ++j)
+            if (W[j].live) walk_step(W[j], a, lane, P[j]);
 #pragma unroll
         for (int j = 0; j < IL; ++j) {
-            const int off = __shfl_sync(FULL, my_off, (i + j) & 31);
-            const int cnt = __shfl_sync(FULL, my_cnt, (i + j) & 31);
-            walk_init(W[j], a, off, i + j < nr ? cnt : 0, ray0 + i + j, lane);
-        }
-        for (;;) {
-            bool any = false;
-#pragma unroll
-            for (int j = 0; j < IL; ++j) any |= W[j].live;
-            if (!any) break;
-            Pair P[IL];
-#pragma unroll
-            for (int j = 0; j < IL; ++j) walk_load(W[j], a, P[j]);
-#pragma unroll
-            for (int j = 0; j < IL; ++j)
-                if (W[j].live) walk_step(W[j], a, lane, P[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < IL; ++j) {
-            if (lane == i + j) {
-                my_count = W[j].count;
-                my_nch = W[j].c;
+            if (!W[j].live && held[j] >= 0) {
+                if (lane == held[j]) {
+                    my_count = W[j].count;
+                    my_nch = W[j].c;
+                }
+                start(j);
             }
         }
     }
