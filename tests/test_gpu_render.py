@@ -323,3 +323,39 @@ def test_alpha_accuracy_single_sample_rays():
     assert np.all(T.cpu().numpy() == 1.0)
     assert np.max(np.abs(got - exact)) <= 2.5e-7
     assert np.max(np.abs(got - exact) / np.maximum(exact, 1e-300)) <= 4e-6
+
+
+@pytest.mark.parametrize("tile_rays", [2, 4, 8, 32])
+def test_prune_uneven_rays_every_tile_shape(orc, tile_rays):
+    """Runs of very different lengths (empty, one sample, thousands) side by side in
+    every tile shape: the decision walk refills a freed slot with the tile's next
+    ray, and the result must not depend on how rays share a warp."""
+    rng = np.random.default_rng(41)
+    lens = rng.choice([0, 0, 1, 2, 33, 63, 64, 65, 500, 3000], size=700)
+    off = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    pi = np.stack([off, lens], axis=1).astype(np.int32)
+    M = int(lens.sum())
+    ts = np.zeros(M, np.float32)
+    for o, c in pi:
+        ts[o : o + c] = np.arange(c, dtype=np.float32) * np.float32(0.01) + np.float32(0.5)
+    te = (ts + np.float32(0.01)).astype(np.float32)
+    sg = (rng.random(M) ** 4 * 60).astype(np.float32)  # mostly thin, some opaque: early stops at many depths
+    p, keep, od = orc.prune(pi, ts, te, sg, 1e-4, 1e-2)
+    old = _lib.tune_get("prune_tile_rays")
+    try:
+        _lib.tune_set("prune_tile_rays", tile_rays)
+        g = _gpu_prune(pi, ts, te, sg, 1e-4, 1e-2)
+    finally:
+        _lib.tune_set("prune_tile_rays", old)
+    assert g["st"][0] == 0
+    keep_g = g["keep"][:M].astype(bool)
+    near = near_threshold(pi, ts, te, sg, 1e-4, od)
+    assert not ((keep_g != keep) & ~near).any()
+    flipped = set(np.searchsorted(pi[:, 0], np.nonzero(keep_g != keep)[0], side="right") - 1)
+    for r in range(len(lens)):
+        if r in flipped:
+            continue
+        (og, cg), (oo, co) = g["pi"][r], p.packed_info[r]
+        assert cg == co and bits_equal(g["ts"][og : og + cg], p.t_starts[oo : oo + co])
+        assert np.all(g["ri"][og : og + cg] == r)
+    assert len(flipped) <= 2 and p.n_samples > 1000
