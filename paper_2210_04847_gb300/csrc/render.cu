@@ -74,7 +74,7 @@ struct FwdArgs {
 };
 
 constexpr int kRenderThreads = 128;
-constexpr int kGroup = 8;  // consecutive rays per warp (lane i holds ray i's run)
+constexpr int kGroup = 4;  // consecutive rays per warp (lane i holds ray i's run)
 
 // Runs of the warp's group of rays; lanes >= nr and invalid runs hold (0, 0).
 __device__ __forceinline__ void load_group(const int32_t* packed_info, int ray0, int nr, int64_t n_samples,
