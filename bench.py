@@ -793,15 +793,14 @@ def run_inference_e2e(args, dev, wls, sg, field):
     R = w.n_rays
     grid = api.OccupancyGrid.from_bits(sg[2], w.res, w.aabb, device=dev)
     dens = api.DensityGrid(torch.from_numpy(w.field).to(dev), w.field_box)
-    host = [(torch.from_numpy(x.rays_o).pin_memory(), torch.from_numpy(x.rays_d).pin_memory()) for x in wls]
+    host = [torch.from_numpy(np.concatenate([x.rays_o.ravel(), x.rays_d.ravel()])).pin_memory() for x in wls]
     out_host = torch.empty((R, 3), dtype=torch.float32).pin_memory()
 
     def one(i):
-        ho, hd = host[i % len(host)]
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         e[0].record()
-        o = ho.to(dev, non_blocking=True)
-        d = hd.to(dev, non_blocking=True)
+        flat = host[i % len(host)].to(dev, non_blocking=True)
+        o, d = flat[: 3 * R].view(R, 3), flat[3 * R:].view(R, 3)
         packed, ts, te, sig, ri = api.march_with_density(o, d, grid, dens, render_step_size=w.dt_min,
                                                          max_steps=w.max_steps, early_stop_eps=w.early_stop_eps,
                                                          alpha_thre=w.alpha_thre, return_ray_indices=True)
@@ -957,8 +956,9 @@ def run_e2e(args, dev, sc):
     # the grid refreshed every step (its own EMA state, see run_ours)
     upd = api.OccupancyGrid(aabb, 128, device=dev)
     upd.ema.copy_(sc.ema_init())
-    host = [(torch.from_numpy(b["host"].rays_o).pin_memory(), torch.from_numpy(b["host"].rays_d).pin_memory(),
-             torch.from_numpy(b["host"].target_rgb).pin_memory()) for b in sc.batches]
+    # rays and targets of a batch in one pinned buffer (o | d | target), one copy per step
+    host = [torch.from_numpy(np.concatenate([b["host"].rays_o.ravel(), b["host"].rays_d.ravel(),
+                                             b["host"].target_rgb.ravel()])).pin_memory() for b in sc.batches]
     out_host = torch.empty((R, 3), dtype=torch.float32).pin_memory()
     loss_host = torch.empty((), dtype=torch.float32).pin_memory()
     dt = synth.SQRT3 * 3.0 / 1024.0
@@ -991,13 +991,11 @@ def run_e2e(args, dev, sc):
     sig_cells = torch.empty(N_GRID_SAMPLES, dtype=torch.float32, device=dev)
 
     def one(i):
-        ho, hd, ht = host[i % len(host)]
         field_ms.clear()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        o = ho.to(dev, non_blocking=True)
-        d = hd.to(dev, non_blocking=True)
-        tgt = ht.to(dev, non_blocking=True)
+        flat = host[i % len(host)].to(dev, non_blocking=True)
+        o, d, tgt = (flat[k * 3 * R:(k + 1) * 3 * R].view(R, 3) for k in range(3))
         state["o"], state["d"] = o, d
         # the grid update first, as a training loop does at the start of each step
         cells, xyz = upd.sample_cells(N_GRID_SAMPLES, 0, i % POOL)
