@@ -4,8 +4,10 @@
 // backward pass.
 //
 // Every kernel gives one warp to one ray at a time and walks the ray's run of
-// samples in chunks of 32 (parallel over samples inside the ray, Sec. 2.2),
-// with coalesced loads. The exclusive optical depth O_i = sum_{j<i} tau_j is a
+// samples in chunks (parallel over samples inside the ray, Sec. 2.2), with
+// coalesced loads: the fused forward and backward take 64 samples per chunk, two
+// consecutive samples per lane as 8-byte loads; the weights and accumulation
+// kernels take 32. The exclusive optical depth O_i = sum_{j<i} tau_j is a
 // warp shuffle scan plus a carry between chunks; the operations that form it
 // are explicitly rounded, so the forward and backward kernels (and the saved
 // optical-depth path) produce the same O_i bit for bit.
@@ -19,7 +21,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kCarryCap = 128;  // chunk carries kept in shared memory per warp (4096 samples)
+constexpr int kCarryCap = 128;  // chunk carries kept in shared memory per warp (8192 samples)
 
 __device__ __forceinline__ bool load_run(const int32_t* packed_info, int r, int64_t n_samples,
                                          int32_t* d_status, int lane, int& off, int& cnt) {
