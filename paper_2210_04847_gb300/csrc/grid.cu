@@ -11,8 +11,9 @@
 //
 // Two launches, 8.125 bytes of HBM traffic per cell plus the samples:
 //   1. decay_pack: one pass over the float32 grid, decays in place and writes
-//      the bit words of the decayed values (__ballot_sync gives a word per 32
-//      cells);
+//      the bit words of the decayed values (four cells per thread with 16-byte
+//      accesses over whole 128-cell steps of an aligned grid; elsewhere one cell
+//      per thread, __ballot_sync giving a word per 32 cells);
 //   2. scatter: per sample, atomicMax on the float bits (valid because every
 //      value is >= 0, so the int order is the float order) and, when the sample
 //      alone passes the threshold, atomicOr of its bit. Since max only grows,

@@ -4,8 +4,9 @@
 // alpha_thre of the Sec. 3 listing).
 //
 // Single pass over the input samples. Each warp takes tiles of consecutive rays
-// from an atomic ticket and walks two (or four) rays at a time (independent
-// load streams), in chunks of 64 samples: lane j loads samples 2j and 2j+1 of
+// from an atomic ticket and keeps two (or four) rays in flight (independent
+// load streams; a slot whose ray has ended takes the tile's next ray), in
+// chunks of 64 samples: lane j loads samples 2j and 2j+1 of
 // the chunk as one 8-byte vector per array (chunks start at an even index).
 // It forms tau = sigma*delta, the exclusive optical depth by a warp shuffle
 // scan of the lane pairs plus a running carry, and the keep decisions; two
