@@ -195,6 +195,19 @@ def stage_bytes(R, M, M_read, S, grid_bytes, n_cells, n_grid, saved_od=False):
     }
 
 
+def launches_per_step(w, n_cells: int, n_grid: int, ema_ptr: int) -> int:
+    """Library kernels one timed step launches: march (plus the cone-table prologue
+    for cone steps), prune, render forward, render backward, the grid sampler, the
+    decay pass (four cells per thread over whole 128-cell steps of an aligned
+    grid, one cell per thread for the rest) and the scatter."""
+    n = 4 + (1 if w.cone > 0 else 0)
+    if n_grid > 0:
+        n += 2  # sampler + scatter
+    steps = n_cells >> 7 if ema_ptr % 16 == 0 else 0
+    n += (1 if steps > 0 else 0) + (1 if (steps << 7) < n_cells else 0)
+    return n
+
+
 def kernel_source_sha(stage: str) -> str:
     """SHA-256 over the sources a stage's kernel is compiled from."""
     files = {"march": ("march.cu", "march_common.cuh", "nacc_internal.cuh"), "prune": ("prune.cu", "nacc_internal.cuh"),
@@ -549,7 +562,7 @@ def run_ours(args):
                      "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes": int(sb[dom]), "limiter": LIMITER[dom]},
         "wall_s_timed_loop_incl_field": round(t_wall, 3),
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": launches_per_step(w, sc.n_cells, sc.n_grid, hp.ema.data_ptr()) * args.steps,
         "clocks": clk,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -772,7 +785,7 @@ def run_inference(args):
                              "render fwd, same images, timed after the fused loop"},
         "fused_speedup": round(mean_two / mean_ms, 3) if two else None,
         "samples_written_fused_vs_two_call": [round(S), round(M2 + S2)],
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 2 * args.steps,  # march_fused_kernel + render_fwd_kernel per step
         "clocks": clk,
         "cpu_baseline": None,
         "e2e": None if args.no_e2e else run_inference_e2e(args, dev, wls, sg, field),
