@@ -377,6 +377,9 @@ int nacc_unpack_info(const int32_t* packed_info, int32_t n_rays, int64_t n_sampl
  * the cells (uniform random cells in Instant-NGP's scheme) and evaluates its
  * field at points inside them. Float32 state, one rounding per product:
  * bit-exact and independent of sample order.
+ * The paper's criterion, empty where the opacity of a step is below a threshold
+ * (Sec. 2.1), is this test with thre = -ln(1 - alpha_thre) / dt: for dt > 0,
+ * 1 - exp(-ema dt) > alpha_thre exactly when ema > -ln(1 - alpha_thre) / dt.
  * ema (n_cells,) float32 in/out, values >= 0; bits ceil(n_cells/32) uint32 out;
  * cells (n_samples,) int32 in [0, n_cells) (others raise NACC_STATUS_BAD_INDEX
  * and are skipped); sigmas (n_samples,) float32.

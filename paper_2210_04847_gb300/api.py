@@ -18,12 +18,22 @@ outputs. Capacity-based calls without that synchronisation are available in
 """
 from __future__ import annotations
 
+import math
 from typing import Callable, Optional, Sequence
 
 import numpy as np
 import torch
 
 from . import _lib
+
+
+def alpha_to_density_threshold(alpha_thre: float, dt: float) -> float:
+    """Density threshold equivalent to an opacity threshold for steps of length dt:
+    1 - exp(-sigma dt) > alpha_thre  <=>  sigma > -ln(1 - alpha_thre) / dt, computed in
+    float64 and rounded once to float32 (the precision of the grid's comparison)."""
+    if not (0.0 <= alpha_thre < 1.0) or not (dt > 0.0):
+        raise ValueError("need 0 <= alpha_thre < 1 and dt > 0")
+    return float(np.float32(-math.log1p(-alpha_thre) / dt))
 
 
 class OccupancyGrid:
@@ -72,8 +82,14 @@ class OccupancyGrid:
         _lib.sample_grid_cells(seed, 50000 + 4 * step, n, self.struct(), cells, xyz)
         return cells, xyz
 
-    def update(self, cells: torch.Tensor, sigmas: torch.Tensor, decay: float = 0.95, thre: float = 0.01):
-        """EMA update: ema = max(decay * ema, sigma at sampled cells); bits = ema > thre."""
+    def update(self, cells: torch.Tensor, sigmas: torch.Tensor, decay: float = 0.95, thre: float = 0.01,
+               alpha_step: Optional[float] = None):
+        """EMA update: ema = max(decay * ema, sigma at sampled cells); bits = ema > thre.
+        With ``alpha_step`` = dt the criterion is the opacity of a step of that
+        length, 1 - exp(-ema dt) > thre (the paper's "empty where alpha < 1e-2",
+        Sec. 2.1), applied as the equivalent density threshold."""
+        if alpha_step is not None:
+            thre = alpha_to_density_threshold(thre, alpha_step)
         _lib.update_occupancy_grid(self.ema, self.bits, cells, sigmas, decay, thre, self.status)
 
     def state_dict(self):

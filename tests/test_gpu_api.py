@@ -81,6 +81,13 @@ def test_api_grid_update_and_weights(orc):
     g.update(torch.from_numpy(cells).cuda(), torch.from_numpy(sig).cuda(), 0.9, 0.01)
     e_o, b_o = orc.update_grid(ema0, cells, sig, 0.9, 0.01)
     assert bits_equal(g.ema.cpu().numpy(), e_o) and np.array_equal(g.bits.cpu().numpy().view(np.uint32), b_o)
+    # the opacity criterion (alpha of a step dt above 0.01) is the converted density threshold
+    ga = api.OccupancyGrid((-1, -1, -1, 1, 1, 1), 32)
+    ga.ema.copy_(torch.from_numpy(ema0))
+    ga.update(torch.from_numpy(cells).cuda(), torch.from_numpy(sig).cuda(), 0.9, 0.01, alpha_step=0.5)
+    e_a, b_a = orc.update_grid(ema0, cells, sig, 0.9, api.alpha_to_density_threshold(0.01, 0.5))
+    assert bits_equal(ga.ema.cpu().numpy(), e_a) and np.array_equal(ga.bits.cpu().numpy().view(np.uint32), b_a)
+    assert not np.array_equal(b_a, b_o)  # a different threshold (0.0201 against 0.01)
     sd = g.state_dict()
     g2 = api.OccupancyGrid((-1, -1, -1, 1, 1, 1), 32)
     g2.load_state_dict(sd)
