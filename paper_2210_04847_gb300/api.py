@@ -149,10 +149,32 @@ def _read_count(cs: torch.Tensor, what: str) -> int:
     return int(n)
 
 
-def march_rays(rays_o, rays_d, grid: OccupancyGrid, near_plane=0.0, far_plane=1e10, render_step_size=1e-2,
-               cone_angle=0.0, dt_max=None, max_steps=1024, ray_time=None, ray_slot=None):
-    """Occupancy-grid marching only. Returns (packed_info (R,2), t_starts (M,), t_ends (M,), ray_indices (M,))."""
+_NO_GRID = {}
+
+
+def _no_grid(device) -> OccupancyGrid:
+    """Marching without an occupancy grid (the paper's listing calls ray_marching
+    without one): every lattice step between near_plane and far_plane is a sample.
+    Realised as a one-cell grid over contracted space with its bit set: contracted
+    rays are not clipped to a box, and every contracted point (|x_c| < 2) falls in
+    the one cell of [-2, 2]^3. The box is +-1e6, so points within that radius are
+    not contracted at all and points far beyond it stay below |x_c| = 2 in float32."""
+    key = str(device)
+    g = _NO_GRID.get(key)
+    if g is None:
+        g = OccupancyGrid((-1e6, -1e6, -1e6, 1e6, 1e6, 1e6), 1, device=device, contraction=1)
+        g.bits.fill_(1)
+        _NO_GRID[key] = g
+    return g
+
+
+def march_rays(rays_o, rays_d, grid: Optional[OccupancyGrid] = None, near_plane=0.0, far_plane=1e10,
+               render_step_size=1e-2, cone_angle=0.0, dt_max=None, max_steps=1024, ray_time=None, ray_slot=None):
+    """Occupancy-grid marching only (grid None: every step between the planes).
+    Returns (packed_info (R,2), t_starts (M,), t_ends (M,), ray_indices (M,))."""
     dev = rays_o.device
+    if grid is None:
+        grid = _no_grid(dev)
     rays_o = rays_o.contiguous().float()
     rays_d = rays_d.contiguous().float()
     R = rays_o.shape[0]
@@ -267,12 +289,13 @@ def prune_samples(packed_info, t_starts, t_ends, sigmas, early_stop_eps=1e-4, al
     return packed, ts[:n], te[:n], ri[:n]
 
 
-def ray_marching(rays_o, rays_d, grid: OccupancyGrid, sigma_fn: Optional[Callable] = None, near_plane=0.0,
-                 far_plane=1e10, render_step_size=1e-2, cone_angle=0.0, dt_max=None, max_steps=1024,
+def ray_marching(rays_o, rays_d, grid: Optional[OccupancyGrid] = None, sigma_fn: Optional[Callable] = None,
+                 near_plane=0.0, far_plane=1e10, render_step_size=1e-2, cone_angle=0.0, dt_max=None, max_steps=1024,
                  early_stop_eps=1e-4, alpha_thre=0.0, ray_time=None, ray_slot=None, return_ray_indices=False):
-    """March rays through the occupancy grid, then (if sigma_fn is given) prune by
-    transmittance < early_stop_eps and opacity < alpha_thre, with the density
-    queried without gradients (Sec. 2.1). Returns (packed_info, t_starts (n,1), t_ends (n,1))."""
+    """March rays through the occupancy grid (or, with grid None, every step between
+    the planes), then (if sigma_fn is given) prune by transmittance < early_stop_eps
+    and opacity < alpha_thre, with the density queried without gradients (Sec. 2.1).
+    Returns (packed_info, t_starts (n,1), t_ends (n,1))."""
     packed, ts, te, ri = march_rays(rays_o, rays_d, grid, near_plane, far_plane, render_step_size, cone_angle,
                                     dt_max, max_steps, ray_time, ray_slot)
     if sigma_fn is not None and (early_stop_eps > 0 or alpha_thre > 0) and ts.numel() > 0:

@@ -141,3 +141,47 @@ def test_weights_and_accumulate_compose_to_render(orc):
     assert grad_rel_err(s2.grad.cpu().numpy(), ds_o) <= 1e-3
     for r_ in (r1, r2):
         assert grad_rel_err(r_.grad.cpu().numpy(), dr_o) <= 1e-4
+
+
+def test_paper_listing_without_a_grid(orc):
+    """The paper's Sec. 3 listing calls ray_marching without an occupancy grid:
+    every lattice step between near_plane and far_plane is marched, then pruned
+    with the field's density, then rendered with gradients."""
+    from paper_2210_04847_gb300 import api as nerfacc
+
+    rng = np.random.default_rng(8)
+    n = 300
+    rays_o = torch.from_numpy(rng.uniform(-0.5, 0.5, (n, 3)).astype(np.float32)).cuda()
+    d = rng.normal(size=(n, 3))
+    rays_d = torch.from_numpy((d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)).cuda()
+    w_field = torch.tensor([[2.0, -1.0, 0.5], [0.3, 0.2, -0.4], [-0.6, 0.9, 0.1]], device="cuda", requires_grad=True)
+
+    def query(ts, te, ri):
+        pos = rays_o[ri] + rays_d[ri] * (ts + te) / 2.0
+        sig = 30.0 * torch.exp(-4.0 * (pos * pos).sum(-1, keepdim=True))
+        return torch.sigmoid(pos @ w_field), sig
+
+    def sigma_fn(ts, te, ri):
+        return query(ts, te, ri)[1]
+
+    def rgb_sigma_fn(ts, te, ri):
+        return query(ts, te, ri)
+
+    # the listing's call, verbatim
+    packed_info, t_starts, t_ends = nerfacc.ray_marching(
+        rays_o, rays_d, sigma_fn=sigma_fn, near_plane=0.2, far_plane=1.0,
+        early_stop_eps=1e-4, alpha_thre=1e-2,
+    )
+    color, opacity, depth = nerfacc.rendering(rgb_sigma_fn, packed_info, t_starts, t_ends)
+    loss = torch.nn.functional.mse_loss(color, torch.full_like(color, 0.5))
+    loss.backward()
+    assert torch.isfinite(w_field.grad).all() and float(w_field.grad.abs().sum()) > 0
+    # marching without a grid: every step of the lattice between the planes
+    m = orc.march(rays_o.cpu().numpy(), rays_d.cpu().numpy(), np.array([1], np.uint32), (1, 1, 1),
+                  (-1e6, -1e6, -1e6, 1e6, 1e6, 1e6), 0.2, 1.0, 1e-2, 1e-2, 0.0, 1024, contraction=1)
+    near, dt = np.float32(0.2), np.float32(0.01)
+    k_max = sum(1 for k in range(200) if near + np.float32(k) * dt < np.float32(1.0))  # float32 lattice: 81
+    assert np.all(m.packed_info[:, 1] == k_max)
+    packed, ts, te, ri = nerfacc.march_rays(rays_o, rays_d, near_plane=0.2, far_plane=1.0)
+    assert np.array_equal(packed.cpu().numpy(), m.packed_info) and bits_equal(ts.cpu().numpy(), m.t_starts)
+    assert float(opacity.max()) > 0.5 and float(opacity.min()) >= 0.0
