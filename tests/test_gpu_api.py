@@ -184,4 +184,4 @@ def test_paper_listing_without_a_grid(orc):
     assert np.all(m.packed_info[:, 1] == k_max)
     packed, ts, te, ri = nerfacc.march_rays(rays_o, rays_d, near_plane=0.2, far_plane=1.0)
     assert np.array_equal(packed.cpu().numpy(), m.packed_info) and bits_equal(ts.cpu().numpy(), m.t_starts)
-    assert float(opacity.max()) > 0.5 and float(opacity.min()) >= 0.0
+    assert float(opacity.detach().max()) > 0.5 and float(opacity.detach().min()) >= 0.0
