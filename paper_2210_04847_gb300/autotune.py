@@ -17,7 +17,7 @@ from . import _lib
 
 # Candidate values per knob (all valid for every input).
 CANDIDATES = {
-    "march_tile_rays": (2, 4, 8, 16, 32),
+    "march_tile_rays": (1, 2, 4, 8, 16, 32),
     "march_occupancy": (0, 1),
     "march_unroll": (0, 1),
     "march_coarse": (0, 1),
