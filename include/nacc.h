@@ -426,7 +426,8 @@ int nacc_sample_grid_cells(uint64_t seed, uint64_t stream, int64_t n, const nacc
 #define NACC_TUNE_RENDER_FWD_PREFETCH 0 /* 0/1: issue the next chunk's loads early */
 #define NACC_TUNE_MARCH_TILE_RAYS 1     /* 1..32: rays per warp tile (upper bound) */
 #define NACC_TUNE_PRUNE_TILE_RAYS 2     /* 2..32, even: rays per warp tile */
-#define NACC_TUNE_MARCH_OCCUPANCY 3     /* 0: compiler's register use; 1: registers capped at 64 (4 blocks/SM) */
+#define NACC_TUNE_MARCH_OCCUPANCY 3     /* 0: compiler's register use; 1: registers capped at 64 (4 blocks/SM);
+                                          the one-level uniform-step walk is always capped */
 #define NACC_TUNE_PRUNE_OCCUPANCY 4     /* 0: compiler's; 1: capped for 8 blocks/SM; 2: for 6 */
 #define NACC_TUNE_RENDER_OCCUPANCY 5    /* forward: 0: compiler's; 1: capped for 16 blocks/SM; 2: for 12 */
 #define NACC_TUNE_RENDER_BWD_OCCUPANCY 6 /* backward: 0: compiler's; 1: capped for 16 blocks/SM; 2: for 12 */

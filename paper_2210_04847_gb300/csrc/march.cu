@@ -39,6 +39,21 @@ namespace {
 // count = samples, nch = ballot words written (row[0..nch)).
 // COARSE (shared lattices): first one point every 32 per lane, and chunks that
 // lie in a single cell take their word from one occupancy test (see below).
+// occupied<1> in two halves, so that a caller can have the load in flight while it
+// works on another point: the bitfield word that holds x's cell (0 when x is
+// outside the grid) and the cell's index. Bit (cell & 31) of the word is the
+// occupancy bit of x.
+__device__ __forceinline__ unsigned level0_word(const MarchArgs& a, float x0, float x1, float x2,
+                                                unsigned slot_level0, unsigned& cell) {
+    const int i0 = __float2int_rd(__fmul_rn(__fsub_rn(x0, a.L.lo[0][0]), a.L.scale[0][0]));
+    const int i1 = __float2int_rd(__fmul_rn(__fsub_rn(x1, a.L.lo[0][1]), a.L.scale[0][1]));
+    const int i2 = __float2int_rd(__fmul_rn(__fsub_rn(x2, a.L.lo[0][2]), a.L.scale[0][2]));
+    cell = ((slot_level0 * a.res0 + i0) * a.res1 + i1) * a.res2 + i2;
+    const bool in =
+        (unsigned)i0 < (unsigned)a.res0 && (unsigned)i1 < (unsigned)a.res1 && (unsigned)i2 < (unsigned)a.res2;
+    return in ? __ldg(a.bits + (cell >> 5)) : 0u;
+}
+
 template <int MAXL, bool CONE, bool UNROLL2, bool COARSE = false>
 __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3], const float d[3], float near,
                                              float far, unsigned sl0, uint32_t* row, float* lat, int lane,
@@ -171,24 +186,53 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
         // chunk below nk/32 is full and only the last one needs the bound test; the
         // count is summed from the finished row
         const int nfull = nk >> 5;
-        for (int c = 0; c < nfull; ++c) {
-            const int k = (c << 5) + lane;
-            float ts, tn;
-            if (!CONE) {
+        if constexpr (!CONE && MAXL == 1) {
+            // Uniform steps on one level: each chunk's bitfield word is loaded one
+            // chunk ahead, so that load's latency overlaps the ballot and row store
+            // of the chunk before it. The last look-ahead is the partial chunk's (or
+            // one past the lattice): its load stays inside the grid and its result
+            // is not used.
+            auto probe = [&](int k, unsigned& cell) -> unsigned {
                 const float kf = __int2float_rn(k);
-                ts = __fadd_rn(near, __fmul_rn(kf, dt));
-                tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
-            } else {
-                ts = __ldg(a.cone_table + min(k, a.max_steps));
-                tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                const float ts = __fadd_rn(near, __fmul_rn(kf, dt));
+                const float tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+                const float te = tn < far ? tn : far;
+                const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
+                return level0_word(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)), __fadd_rn(o[1], __fmul_rn(d[1], mid)),
+                                   __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0, cell);
+            };
+            if (nfull > 0) {
+                unsigned cell;
+                unsigned w = probe(lane, cell);
+                for (int c = 0; c < nfull; ++c) {
+                    unsigned cell_n;
+                    const unsigned w_n = probe(((c + 1) << 5) + lane, cell_n);
+                    const unsigned m = __ballot_sync(FULL, (w >> (cell & 31u)) & 1u);
+                    if (lane == 0) row[c] = m;
+                    cell = cell_n;
+                    w = w_n;
+                }
             }
-            const float te = tn < far ? tn : far;
-            const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
-            const bool occ = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)),
-                                            __fadd_rn(o[1], __fmul_rn(d[1], mid)),
-                                            __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0);
-            const unsigned m = __ballot_sync(FULL, occ);
-            if (lane == 0) row[c] = m;
+        } else {
+            for (int c = 0; c < nfull; ++c) {
+                const int k = (c << 5) + lane;
+                float ts, tn;
+                if (!CONE) {
+                    const float kf = __int2float_rn(k);
+                    ts = __fadd_rn(near, __fmul_rn(kf, dt));
+                    tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+                } else {
+                    ts = __ldg(a.cone_table + min(k, a.max_steps));
+                    tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                }
+                const float te = tn < far ? tn : far;
+                const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
+                const bool occ = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)),
+                                                __fadd_rn(o[1], __fmul_rn(d[1], mid)),
+                                                __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0);
+                const unsigned m = __ballot_sync(FULL, occ);
+                if (lane == 0) row[c] = m;
+            }
         }
         if (nfull < max_ch) {
             const int k = (nfull << 5) + lane;
@@ -464,6 +508,9 @@ void launch_variant(bool cone, bool unroll, bool coarse, size_t smem, int need, 
 template <int MAXL>
 void launch_walk(bool cone, bool occ, bool unroll, bool coarse, size_t smem, int need, cudaStream_t st,
                  const MarchArgs& a) {
+    // The single-level uniform walk keeps one bitfield load in flight; it is built
+    // for 64 registers (4 blocks of 256 threads per SM) and always launched so.
+    if (MAXL == 1 && !cone && !unroll && !coarse) occ = true;
     if (occ) launch_variant<MAXL, 4>(cone, unroll, coarse, smem, need, st, a);
     else launch_variant<MAXL, 1>(cone, unroll, coarse, smem, need, st, a);
 }
