@@ -53,7 +53,7 @@ NCU_TRAFFIC = {
 
 # What limits each stage (from the ncu captures summarised under profiles/).
 LIMITER = {
-    "march": "issue: bit-exact float32 lattice arithmetic, ~70% issue-active at ~25% DRAM",
+    "march": "issue: bit-exact float32 lattice arithmetic, ~74% issue-active at ~32% DRAM",
     "prune": "DRAM latency (long-scoreboard stalls)",
     "render_fwd": "DRAM latency / issue",
     "render_bwd": "DRAM latency (long-scoreboard stalls)",
