@@ -187,6 +187,41 @@ def test_contracted_unbounded_scene(orc):
     assert_march_equal(g, oracle_march(orc, w))
 
 
+@pytest.mark.parametrize("max_steps", [1024, 32, 33])
+@pytest.mark.parametrize("far_plane", [1e10, 1.5])
+def test_lattice_lengths_around_chunk_boundaries(orc, far_plane, max_steps):
+    """One level, uniform steps, rays along the axes from inside the box [-1, 1]^3
+    whose lattices hold 0-129 points (around multiples of 32). Each ray ends at the box
+    face, the far plane or max_steps, either halfway through a step or exactly on a
+    lattice point (t_k < far is strict). So the chunk after a ray's last one lies
+    outside the grid, inside it, or past max_steps. The exit distances are multiples
+    of 1/128 and dt = 1/64, so every t and the clip are exact in float32."""
+    dt = 1.0 / 64
+    res = (16, 16, 16)
+    occ = np.ones(16 ** 3, bool)
+    occ[::3] = False
+    n_pts = [0, 1, 2, 31, 32, 33, 63, 64, 65, 95, 96, 97, 127, 128]
+    o, d = [], []
+    for axis in range(3):
+        for sign in (1.0, -1.0):
+            for n in n_pts:
+                for frac in (0.5, 0.0):
+                    exit_dist = (n + frac) * dt
+                    if exit_dist > 2.0:
+                        continue
+                    p = np.array([0.1, -0.3, 0.45])
+                    p[axis] = sign * (1.0 - exit_dist)
+                    v = np.zeros(3)
+                    v[axis] = sign
+                    o.append(p)
+                    d.append(v)
+    w = _workload(np.array(o), np.array(d), occ, res, (-1, -1, -1, 1, 1, 1), far=far_plane, dt_min=dt, dt_max=dt,
+                  max_steps=max_steps)
+    g = gpu_march(w)
+    assert g[4] > 0
+    assert_march_equal(g, oracle_march(orc, w))
+
+
 @functools.lru_cache(maxsize=1)
 def _whole_batch(name):
     import oracle
