@@ -45,8 +45,8 @@ POOL = 4  # distinct ray batches cycled through the steps (L2 is flushed between
 # from one ncu capture, keyed by the SHA-256 of the kernel's source file. A
 # source change invalidates the figure (reported as null until re-captured).
 NCU_TRAFFIC = {
-    # profiles/march_dram_bounded-2^18.md: 9198336 B read + 1477568000 B written
-    ("march", "cb0a5abd88bf87a6885d69f6b98f777cf0cca635cdd6174c2b1649d8fc24e7aa"): 1486766336,
+    # profiles/march_dram_bounded-2^18.md: 9070336 B read + 1477548544 B written
+    ("march", "2bbafd758c7197be50a94f2fa9a44fac3fb5ab3389194cc2aaa80ab2867e80af"): 1486618880,
     # profiles/march_fused_inference-800x800.md: 22437376 B read + 1169642240 B written (camera 0's image)
     ("march_fused", "c86e1bad5b55ca339d49805cf9ac418869661e8853df2abc21f41da92b781990"): 1192079616,
 }

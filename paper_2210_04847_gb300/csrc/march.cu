@@ -15,7 +15,9 @@
 //     lattice point 32c + j (the lattice is closed-form, t_k = near + k*dt);
 //     the occupancy test of the 32 midpoints becomes one __ballot_sync word and
 //     __popc gives the count. Lane i of the warp keeps ray i's count, chunk
-//     count and [near, far].
+//     count and [near, far]. On a one-level grid each chunk's bitfield word is
+//     loaded one chunk ahead, so that load overlaps the ballot of the chunk
+//     before it.
 //   * Cone steps (t_{k+1} = t_k + clamp(t_k*cone, dt_min, dt_max)): the
 //     lattice is a sequential float32 recurrence that depends only on its start.
 //     Every ray that starts inside the outermost box starts at near_plane, so a
@@ -35,10 +37,6 @@ namespace {
 // lattice walk: the warp evaluates 32 lattice points of one ray at a time
 // ---------------------------------------------------------------------------
 
-// One ray, all 32 lanes: one ballot word per 32 lattice points into row[c].
-// count = samples, nch = ballot words written (row[0..nch)).
-// COARSE (shared lattices): first one point every 32 per lane, and chunks that
-// lie in a single cell take their word from one occupancy test (see below).
 // occupied<1> in two halves, so that a caller can have the load in flight while it
 // works on another point: the bitfield word that holds x's cell (0 when x is
 // outside the grid) and the cell's index. Bit (cell & 31) of the word is the
@@ -54,6 +52,10 @@ __device__ __forceinline__ unsigned level0_word(const MarchArgs& a, float x0, fl
     return in ? __ldg(a.bits + (cell >> 5)) : 0u;
 }
 
+// One ray, all 32 lanes: one ballot word per 32 lattice points into row[c].
+// count = samples, nch = ballot words written (row[0..nch)).
+// COARSE (shared lattices): first one point every 32 per lane, and chunks that
+// lie in a single cell take their word from one occupancy test (see below).
 template <int MAXL, bool CONE, bool UNROLL2, bool COARSE = false>
 __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3], const float d[3], float near,
                                              float far, unsigned sl0, uint32_t* row, float* lat, int lane,
