@@ -234,7 +234,22 @@ def test_render_weights_bwd_long_ray_and_empty(orc):
     assert grad_rel_err(ds, ds_o) <= 1e-4
 
 
-@pytest.mark.parametrize("C", [1, 3, 7])
+@pytest.mark.parametrize("C", [1, 4, 7, 16, 33])
+def test_accumulate_many_channels(scene, orc, C):
+    """Per-ray sums of C-channel attributes (Sec. 2.2: any sample attribute), up to
+    one channel past a warp's width, on the ragged pruned samples."""
+    p = scene["p"]
+    R, M = p.packed_info.shape[0], p.n_samples
+    w = synth.rand_uniform(C, 21, M, 0, 1).astype(np.float32)
+    vals = synth.rand_uniform(C, 22, M * C, -1, 1).reshape(M, C).astype(np.float32)
+    out = torch.full((R, C), float("nan"), device="cuda")
+    _lib.accumulate_along_rays(dev(p.packed_info), dev(w), dev(vals), C, M, out)
+    torch.cuda.synchronize()
+    ref = orc.accumulate(p.packed_info, w.astype(np.float64), vals)
+    assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("C", [1, 3, 7, 16, 33])
 def test_accumulate_bwd_parity(scene, orc, C):
     p, rgb = scene["p"], scene["rgb2"]
     R, M = p.packed_info.shape[0], p.n_samples
