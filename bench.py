@@ -72,9 +72,11 @@ def parse():
                          "unless given)")
     ap.add_argument("--workload", default="bounded",
                     choices=["bounded", "tiny", "unbounded", "contracted", "batched", "dynamic", "dynamic_shared",
-                             "inference"],
+                             "inference", "attributes"],
                     help="bounded (default) is the headline configuration; the others are the wider configurations "
-                         "(inference: the fused march with the density field's transmittance + render forward)")
+                         "(inference: the fused march with the density field's transmittance + render forward; "
+                         "attributes: Eq. 1 weights and C-channel accumulation with their gradients)")
+    ap.add_argument("--channels", type=int, default=16, help="attributes workload: channels per sample")
     ap.add_argument("--no-batched-compare", action="store_true")
     ap.add_argument("--cpu-rays", type=int, default=1 << 15, help="rays in the CPU-baseline sample")
     ap.add_argument("--ref-rays", type=int, default=1 << 12, help="rays per reference-arm step")
@@ -794,6 +796,151 @@ def run_inference(args):
     return 0
 
 
+ATTR_METRIC = ("rays/s (Eq. 1 weights + per-ray sums of C-channel sample attributes, forward and backward) "
+               "on one GB300")
+
+
+def run_attributes(args):
+    """Rendering of arbitrary sample attributes (Sec. 2.2): per step, on the kept
+    samples of a bounded-scene batch, the Eq. 1 weights (nacc_render_weights), the
+    per-ray sums of C-channel attributes (nacc_accumulate_along_rays), their gradient
+    for a given dL/dout (nacc_accumulate_along_rays_bwd) and dL/dsigma from the
+    resulting dL/dw (nacc_render_weights_bwd). The samples come from marching,
+    the stand-in density and pruning, done once before timing; the attributes and
+    dL/dout are seeded uniform draws on the device."""
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    from paper_2210_04847_gb300 import _lib
+    from paper_2210_04847_gb300.pipeline import HotPath
+    from paper_2210_04847_gb300.scenarios import make_scenario
+
+    C = int(args.channels)
+    if C < 1:
+        raise ValueError("--channels must be >= 1")
+    sc = make_scenario("bounded", rank, dev, n_rays=args.rays, pool=2)
+    w = sc.w
+    R = sc.n_rays
+    cap = R * min(w.max_steps, 1024)
+    hp = HotPath(w, cap_marched=cap, cap_kept=cap // 2, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1000 * rank + C)
+    f32 = torch.float32
+    sets = []
+    for b in range(len(sc.batches)):
+        bt = sc.batches[b]
+        hp.march(bt["o"], bt["d"])
+        M = int(hp.n_m.item())
+        sc.field_marched(hp, b, M)
+        hp.prune(M)
+        S = int(hp.n_k.item())
+        if int(hp.status.item()) != 0 or M > hp.cap_m or S > hp.cap_k:
+            raise RuntimeError("attributes setup: status 0x%x, %d marched, %d kept" % (int(hp.status.item()), M, S))
+        sc.field_kept(hp, b, S)
+        sets.append({
+            "S": S, "pi": hp.pi_k.clone(), "ts": hp.ts_k[:S].clone(), "te": hp.te_k[:S].clone(),
+            "sig": hp.sig_k[:S].clone(),
+            "vals": torch.rand((S, C), generator=gen, device=dev, dtype=f32) * 2 - 1,
+            "g_out": torch.rand((R, C), generator=gen, device=dev, dtype=f32) * 2 - 1,
+            "w": torch.empty(S, dtype=f32, device=dev), "T": torch.empty(S, dtype=f32, device=dev),
+            "out": torch.empty((R, C), dtype=f32, device=dev), "dw": torch.empty(S, dtype=f32, device=dev),
+            "dv": torch.empty((S, C), dtype=f32, device=dev), "dsig": torch.empty(S, dtype=f32, device=dev)})
+    del hp
+    torch.cuda.empty_cache()
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    names = ("weights", "accumulate", "accumulate_bwd", "weights_bwd")
+
+    def step(i):
+        x = sets[i % len(sets)]
+        S = x["S"]
+        flush.zero_()
+        runs = (_lib.render_weights(x["pi"], x["ts"], x["te"], x["sig"], S, x["w"], x["T"], d_status=st, defer=True),
+                _lib.accumulate_along_rays(x["pi"], x["w"], x["vals"], C, S, x["out"], d_status=st, defer=True),
+                _lib.accumulate_along_rays_bwd(x["pi"], x["w"], x["vals"], C, S, x["g_out"], x["dw"], x["dv"],
+                                               d_status=st, defer=True),
+                _lib.render_weights_bwd(x["pi"], x["ts"], x["te"], x["sig"], S, x["dw"], x["dsig"], d_status=st,
+                                        defer=True))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(runs) + 1)]
+        ev[0].record()
+        for k, run in enumerate(runs):
+            run()
+            ev[k + 1].record()
+        return ev, S
+
+    def collect(rows):
+        torch.cuda.synchronize()
+        if int(st.item()) != 0:
+            raise RuntimeError("attributes: device status 0x%x" % int(st.item()))
+        return [({n: ev[k].elapsed_time(ev[k + 1]) for k, n in enumerate(names)}, S) for ev, S in rows]
+
+    collect([step(i) for i in range(args.warmup)])
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    clocks = ClockSampler(int(vis) if vis.isdigit() else local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    rows = collect([step(args.warmup + i) for i in range(args.steps)])
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = {n: sum(r[0][n] for r in rows) / len(rows) for n in names}
+    S = sum(r[1] for r in rows) / len(rows)
+    mean_ms = sum(ms.values())
+    mean_ms_all = max_over_ranks(mean_ms, world, dev)
+    value = sum_over_ranks(R, world, dev) / (mean_ms_all / 1e3)
+    sb = {
+        # read packed_info (8R) and (t_start, t_end, sigma) (12S); write w and T (8S)
+        "weights": 8 * R + 20 * S,
+        # read packed_info (8R), w (4S) and the attributes (4CS); write the sums (4CR)
+        "accumulate": 8 * R + 4 * S + 4 * C * S + 4 * C * R,
+        # read packed_info (8R), w (4S), the attributes (4CS) and dL/dout (4CR); write dL/dw (4S), dL/dv (4CS)
+        "accumulate_bwd": 8 * R + 8 * S + 8 * C * S + 4 * C * R,
+        # read packed_info (8R), (t_start, t_end, sigma) (12S) and dL/dw (4S); write dL/dsigma (4S)
+        "weights_bwd": 8 * R + 20 * S,
+    }
+    peak, peak_kind = measured_peaks()
+    dom = max(ms, key=ms.get)
+    achieved = sb[dom] / (ms[dom] / 1e3) / 1e9
+    step_bytes = sum(sb.values())
+    if rank != 0:
+        return 0
+    line = {
+        "metric": ATTR_METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms_all, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "attributes-bounded-%d-rays-C%d" % (R, C), "rays_per_step_per_gpu": R,
+                   "channels": C, "samples": "kept samples of the bounded workload (march, stand-in density, "
+                                           "prune; untimed)",
+                   "attributes": "uniform [-1, 1) per sample and channel, seeded, on the device",
+                   "parallelism": "rays sharded per GPU (weak), %d GPU(s)" % world,
+                   "l2": "flushed before every step (256 MB write)",
+                   "timed": "render_weights + accumulate + accumulate_bwd + render_weights_bwd"},
+        "stages_ms": {k: round(v, 4) for k, v in ms.items()},
+        "stage_gbs": {k: round(sb[k] / (ms[k] / 1e3) / 1e9, 1) for k in names},
+        "samples_per_step": {"kept": round(S)},
+        "step_hbm": {"algorithmic_bytes": int(step_bytes), "gbs": round(step_bytes / (mean_ms / 1e3) / 1e9, 1),
+                     "frac": round(step_bytes / (mean_ms / 1e3) / 1e9 / peak, 4), "peak_gbs": peak,
+                     "peak_kind": peak_kind},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes": int(sb[dom])},
+        "gpu_launches": len(names) * args.steps,
+        "clocks": clk,
+        "cpu_baseline": None,
+        "e2e": None,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_inference_e2e(args, dev, wls, sg, field):
     """The inference step through the public API: rays copied from pinned host
     memory, api.march_with_density, the colour query (user code, timed by events and
@@ -1044,6 +1191,8 @@ def main():
         return run_reference(args)
     if args.workload == "inference":
         return run_inference(args)
+    if args.workload == "attributes":
+        return run_attributes(args)
     return run_ours(args)
 
 

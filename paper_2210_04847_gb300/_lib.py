@@ -369,7 +369,7 @@ def prune_samples(packed_info, t_starts, t_ends, sigmas, n_samples_in: int, earl
 
 
 def render_weights(packed_info, t_starts, t_ends, sigmas, n_samples: int, weights=None, trans=None, d_status=None,
-                   stream=None):
+                   stream=None, defer: bool = False):
     n = packed_info.shape[0]
     _check(packed_info, torch.int32, "packed_info", 2 * n)
     for t, nm in ((t_starts, "t_starts"), (t_ends, "t_ends"), (sigmas, "sigmas")):
@@ -377,40 +377,38 @@ def render_weights(packed_info, t_starts, t_ends, sigmas, n_samples: int, weight
     _check(weights, torch.float32, "weights", n_samples, optional=True)
     _check(trans, torch.float32, "trans", n_samples, optional=True)
     _check(d_status, torch.int32, "d_status", 1, optional=True)
-    rc = load().nacc_render_weights(_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), int(n_samples),
-                                    _ptr(weights), _ptr(trans), _ptr(d_status), _stream(stream))
-    _rc(rc, "nacc_render_weights")
+    return _call("nacc_render_weights", (_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas),
+                                         int(n_samples), _ptr(weights), _ptr(trans), _ptr(d_status), _stream(stream)),
+                 defer)
 
 
 def accumulate_along_rays(packed_info, weights, values, n_channels: int, n_samples: int, out, d_status=None,
-                          stream=None):
+                          stream=None, defer: bool = False):
     n = packed_info.shape[0]
     _check(packed_info, torch.int32, "packed_info", 2 * n)
     _check(weights, torch.float32, "weights", n_samples)
     _check(values, torch.float32, "values", n_samples * n_channels, optional=True)
     _check(out, torch.float32, "out", n * n_channels)
     _check(d_status, torch.int32, "d_status", 1, optional=True)
-    rc = load().nacc_accumulate_along_rays(_ptr(packed_info), n, _ptr(weights), _ptr(values), int(n_channels),
-                                           int(n_samples), _ptr(out), _ptr(d_status), _stream(stream))
-    _rc(rc, "nacc_accumulate_along_rays")
+    return _call("nacc_accumulate_along_rays", (_ptr(packed_info), n, _ptr(weights), _ptr(values), int(n_channels),
+                                                int(n_samples), _ptr(out), _ptr(d_status), _stream(stream)), defer)
 
 
 def render_weights_bwd(packed_info, t_starts, t_ends, sigmas, n_samples: int, g_weights, d_sigmas, d_status=None,
-                       stream=None):
+                       stream=None, defer: bool = False):
     n = packed_info.shape[0]
     _check(packed_info, torch.int32, "packed_info", 2 * n)
     for t, nm in ((t_starts, "t_starts"), (t_ends, "t_ends"), (sigmas, "sigmas"), (g_weights, "g_weights"),
                   (d_sigmas, "d_sigmas")):
         _check(t, torch.float32, nm, n_samples)
     _check(d_status, torch.int32, "d_status", 1, optional=True)
-    rc = load().nacc_render_weights_bwd(_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas),
-                                        int(n_samples), _ptr(g_weights), _ptr(d_sigmas), _ptr(d_status),
-                                        _stream(stream))
-    _rc(rc, "nacc_render_weights_bwd")
+    return _call("nacc_render_weights_bwd", (_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas),
+                                             int(n_samples), _ptr(g_weights), _ptr(d_sigmas), _ptr(d_status),
+                                             _stream(stream)), defer)
 
 
 def accumulate_along_rays_bwd(packed_info, weights, values, n_channels: int, n_samples: int, g_out, d_weights=None,
-                              d_values=None, d_status=None, stream=None):
+                              d_values=None, d_status=None, stream=None, defer: bool = False):
     n = packed_info.shape[0]
     _check(packed_info, torch.int32, "packed_info", 2 * n)
     _check(weights, torch.float32, "weights", n_samples)
@@ -419,10 +417,9 @@ def accumulate_along_rays_bwd(packed_info, weights, values, n_channels: int, n_s
     _check(d_weights, torch.float32, "d_weights", n_samples, optional=True)
     _check(d_values, torch.float32, "d_values", n_samples * n_channels, optional=True)
     _check(d_status, torch.int32, "d_status", 1, optional=True)
-    rc = load().nacc_accumulate_along_rays_bwd(_ptr(packed_info), n, _ptr(weights), _ptr(values), int(n_channels),
-                                               int(n_samples), _ptr(g_out), _ptr(d_weights), _ptr(d_values),
-                                               _ptr(d_status), _stream(stream))
-    _rc(rc, "nacc_accumulate_along_rays_bwd")
+    return _call("nacc_accumulate_along_rays_bwd", (_ptr(packed_info), n, _ptr(weights), _ptr(values),
+                                                    int(n_channels), int(n_samples), _ptr(g_out), _ptr(d_weights),
+                                                    _ptr(d_values), _ptr(d_status), _stream(stream)), defer)
 
 
 def render_fwd(packed_info, t_starts, t_ends, sigmas, rgbs, n_samples: int, color, opacity, depth,

@@ -374,20 +374,46 @@ struct AccArgs {
     int32_t* d_status;
 };
 
+// Warp per ray; each lane keeps one channel. For C <= 32 a step covers P = 32 / C
+// consecutive samples (lane l: channel l % C of sample l / C), so the warp reads one
+// contiguous run of P*C values; the P partial sums of a channel are then added
+// over lanes C apart. For C > 32 a step is one sample, 32 channels at a time.
 __global__ void __launch_bounds__(kThreads) accumulate_kernel(const AccArgs a) {
     const int lane = threadIdx.x & 31;
+    const int C = a.n_channels;
     for (int r = global_warp(); r < a.n_rays; r += n_global_warps()) {
         int off, cnt;
         load_run(a.packed_info, r, a.n_samples, a.d_status, lane, off, cnt);
-        for (int c = 0; c < a.n_channels; ++c) {
+        if (C <= 32) {
+            const int P = 32 / C, L = P * C;
+            const int ch = lane % C;
             float acc = 0.0f;
-            for (int j = lane; j < cnt; j += 32) {
-                const size_t i = (size_t)off + j;
-                const float w = __ldg(a.weights + i);
-                acc += a.values ? w * __ldg(a.values + i * a.n_channels + c) : w;
+            if (lane < L) {
+#pragma unroll 4
+                for (int s = lane / C; s < cnt; s += P) {
+                    const size_t i = (size_t)off + s;
+                    const float w = __ldg(a.weights + i);
+                    acc += a.values ? w * __ldg(a.values + i * C + ch) : w;
+                }
             }
-            acc = warp_sum(acc);
-            if (lane == 0) a.out[(size_t)r * a.n_channels + c] = acc;
+            for (int o = C; o < L; o <<= 1) {
+                const float y = __shfl_down_sync(FULL, acc, o);
+                if (lane + o < L) acc += y;
+            }
+            if (lane < C) a.out[(size_t)r * C + lane] = acc;
+        } else {
+            for (int cg = 0; cg < C; cg += 32) {
+                const int c = cg + lane;
+                if (c >= C) continue;
+                float acc = 0.0f;
+#pragma unroll 4
+                for (int s = 0; s < cnt; ++s) {
+                    const size_t i = (size_t)off + s;
+                    const float w = __ldg(a.weights + i);
+                    acc += a.values ? w * __ldg(a.values + i * C + c) : w;
+                }
+                a.out[(size_t)r * C + c] = acc;
+            }
         }
     }
 }
@@ -406,23 +432,69 @@ struct AccBwdArgs {
 };
 
 // Gradient of accumulate_along_rays, warp per ray: dL/dw_i = sum_c g[r,c] v_i[c]
-// and dL/dv_i[c] = w_i g[r,c].
+// and dL/dv_i[c] = w_i g[r,c]. Lanes keep one channel as in the forward: for
+// C <= 32 a step covers 32 / C samples, dL/dv is one contiguous run of stores, and
+// each sample's dL/dw is a sum over its C lanes (shuffles that stay inside the
+// group). For C > 32 a step is one sample, 32 channels at a time.
 __global__ void __launch_bounds__(kThreads) accumulate_bwd_kernel(const AccBwdArgs a) {
     const int lane = threadIdx.x & 31;
+    const int C = a.n_channels;
     for (int r = global_warp(); r < a.n_rays; r += n_global_warps()) {
         int off, cnt;
         load_run(a.packed_info, r, a.n_samples, a.d_status, lane, off, cnt);
-        const float* g = a.g_out + (size_t)r * a.n_channels;
-        for (int j = lane; j < cnt; j += 32) {
-            const size_t i = (size_t)off + j;
-            const float w = __ldg(a.weights + i);
-            float dw = 0.0f;
-            for (int c = 0; c < a.n_channels; ++c) {
-                const float gc = __ldg(g + c);
-                dw += a.values ? gc * __ldg(a.values + i * a.n_channels + c) : gc;
-                if (a.d_values) a.d_values[i * a.n_channels + c] = w * gc;
+        const float* g = a.g_out + (size_t)r * C;
+        if (C <= 32) {
+            const int P = 32 / C, L = P * C;
+            const int ch = lane % C, sub = lane / C;
+            const float gc = lane < L ? __ldg(g + ch) : 0.0f;
+            // kU steps at a time, their loads issued before any of them is reduced.
+            // A sample's C lanes share one s, so a group past the ray's end is
+            // skipped whole.
+            constexpr int kU = 4;
+            for (int s0 = 0; s0 < cnt; s0 += kU * P) {  // warp-uniform
+                float v[kU], wt[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int s = s0 + u * P + sub;
+                    const bool ok = lane < L && s < cnt;
+                    const size_t i = (size_t)off + s;
+                    v[u] = ok ? (a.values ? __ldg(a.values + i * C + ch) : 1.0f) : 0.0f;
+                    wt[u] = (ok && a.d_values) ? __ldg(a.weights + i) : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int s = s0 + u * P + sub;
+                    const bool ok = lane < L && s < cnt;
+                    const size_t i = (size_t)off + s;
+                    if (ok && a.d_values) a.d_values[i * C + ch] = wt[u] * gc;
+                    if (a.d_weights) {
+                        float prod = gc * v[u];
+                        for (int o = 1; o < C; o <<= 1) {
+                            const float y = __shfl_down_sync(FULL, prod, o);
+                            if (ch + o < C) prod += y;
+                        }
+                        if (ok && ch == 0) a.d_weights[i] = prod;
+                    }
+                }
             }
-            if (a.d_weights) a.d_weights[i] = dw;
+        } else {
+            for (int s = 0; s < cnt; ++s) {
+                const size_t i = (size_t)off + s;
+                const float w = __ldg(a.weights + i);
+                float dw = 0.0f;
+                for (int cg = 0; cg < C; cg += 32) {
+                    const int c = cg + lane;
+                    if (c < C) {
+                        const float gc = __ldg(g + c);
+                        dw += a.values ? gc * __ldg(a.values + i * C + c) : gc;
+                        if (a.d_values) a.d_values[i * C + c] = w * gc;
+                    }
+                }
+                if (a.d_weights) {
+                    dw = warp_sum(dw);
+                    if (lane == 0) a.d_weights[i] = dw;
+                }
+            }
         }
     }
 }
