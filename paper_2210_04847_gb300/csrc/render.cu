@@ -431,51 +431,92 @@ struct AccBwdArgs {
     int32_t* d_status;
 };
 
-// Gradient of accumulate_along_rays, warp per ray: dL/dw_i = sum_c g[r,c] v_i[c]
-// and dL/dv_i[c] = w_i g[r,c]. Lanes keep one channel as in the forward: for
-// C <= 32 a step covers 32 / C samples, dL/dv is one contiguous run of stores, and
-// each sample's dL/dw is a sum over its C lanes (shuffles that stay inside the
-// group). For C > 32 a step is one sample, 32 channels at a time.
-__global__ void __launch_bounds__(kThreads) accumulate_bwd_kernel(const AccBwdArgs a) {
+// The same gradient for C <= 4 channels: a lane per sample, its values one short
+// run (no shared memory, so more warps per SM than the tiled kernel).
+__global__ void __launch_bounds__(kThreads) accumulate_bwd_narrow_kernel(const AccBwdArgs a) {
     const int lane = threadIdx.x & 31;
     const int C = a.n_channels;
     for (int r = global_warp(); r < a.n_rays; r += n_global_warps()) {
         int off, cnt;
         load_run(a.packed_info, r, a.n_samples, a.d_status, lane, off, cnt);
         const float* g = a.g_out + (size_t)r * C;
+        for (int j = lane; j < cnt; j += 32) {
+            const size_t i = (size_t)off + j;
+            const float w = __ldg(a.weights + i);
+            float dw = 0.0f;
+            for (int c = 0; c < C; ++c) {
+                const float gc = __ldg(g + c);
+                dw += a.values ? gc * __ldg(a.values + i * C + c) : gc;
+                if (a.d_values) a.d_values[i * C + c] = w * gc;
+            }
+            if (a.d_weights) a.d_weights[i] = dw;
+        }
+    }
+}
+
+// Gradient of accumulate_along_rays, warp per ray: dL/dw_i = sum_c g[r,c] v_i[c]
+// and dL/dv_i[c] = w_i g[r,c]. For 4 < C <= 32 the ray goes in tiles of 32 samples:
+// the warp reads the tile's values as one contiguous run (four loads in flight
+// per lane), writes dL/dv in the same order, and stages the values in shared
+// memory with an odd row stride. Lane j then sums sample j's C products from
+// there, with no bank conflicts. For C > 32 a step is one sample, 32 channels at
+// a time.
+__global__ void __launch_bounds__(kThreads) accumulate_bwd_kernel(const AccBwdArgs a) {
+    __shared__ float s_v[kWarps][32 * 33];
+    __shared__ float s_g[kWarps][32];
+    __shared__ float s_w[kWarps][32];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int C = a.n_channels;
+    float* sv = s_v[warp];
+    float* sg = s_g[warp];
+    float* sw = s_w[warp];
+    const int stride = C | 1;
+    const int q = C <= 32 ? 32 / C : 0, rem = C <= 32 ? 32 - q * C : 0;  // +32 elements: +q samples, +rem channels
+    const int s_first = C <= 32 ? lane / C : 0, c_first = C <= 32 ? lane - s_first * C : 0;
+    for (int r = global_warp(); r < a.n_rays; r += n_global_warps()) {
+        int off, cnt;
+        load_run(a.packed_info, r, a.n_samples, a.d_status, lane, off, cnt);
+        const float* g = a.g_out + (size_t)r * C;
         if (C <= 32) {
-            const int P = 32 / C, L = P * C;
-            const int ch = lane % C, sub = lane / C;
-            const float gc = lane < L ? __ldg(g + ch) : 0.0f;
-            // kU steps at a time, their loads issued before any of them is reduced.
-            // A sample's C lanes share one s, so a group past the ray's end is
-            // skipped whole.
-            constexpr int kU = 4;
-            for (int s0 = 0; s0 < cnt; s0 += kU * P) {  // warp-uniform
-                float v[kU], wt[kU];
+            if (lane < C) sg[lane] = __ldg(g + lane);
+            for (int j0 = 0; j0 < cnt; j0 += 32) {
+                const int n = min(32, cnt - j0);
+                const size_t sbase = (size_t)off + j0;
+                const size_t ebase = sbase * C;
+                const int E = n * C;
+                if (lane < n) sw[lane] = __ldg(a.weights + sbase + lane);
+                __syncwarp();
+                int s = s_first, c = c_first;
+                for (int e0 = 0; e0 < E; e0 += 128) {
+                    float v[4];
 #pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    const int s = s0 + u * P + sub;
-                    const bool ok = lane < L && s < cnt;
-                    const size_t i = (size_t)off + s;
-                    v[u] = ok ? (a.values ? __ldg(a.values + i * C + ch) : 1.0f) : 0.0f;
-                    wt[u] = (ok && a.d_values) ? __ldg(a.weights + i) : 0.0f;
-                }
+                    for (int u = 0; u < 4; ++u) {
+                        const int e = e0 + 32 * u + lane;
+                        v[u] = e < E ? (a.values ? __ldg(a.values + ebase + e) : 1.0f) : 0.0f;
+                    }
 #pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    const int s = s0 + u * P + sub;
-                    const bool ok = lane < L && s < cnt;
-                    const size_t i = (size_t)off + s;
-                    if (ok && a.d_values) a.d_values[i * C + ch] = wt[u] * gc;
-                    if (a.d_weights) {
-                        float prod = gc * v[u];
-                        for (int o = 1; o < C; o <<= 1) {
-                            const float y = __shfl_down_sync(FULL, prod, o);
-                            if (ch + o < C) prod += y;
+                    for (int u = 0; u < 4; ++u) {
+                        const int e = e0 + 32 * u + lane;
+                        if (e < E) {
+                            sv[s * stride + c] = v[u];
+                            if (a.d_values) a.d_values[ebase + e] = sw[s] * sg[c];
                         }
-                        if (ok && ch == 0) a.d_weights[i] = prod;
+                        s += q;
+                        c += rem;
+                        if (c >= C) {
+                            c -= C;
+                            ++s;
+                        }
                     }
                 }
+                __syncwarp();
+                if (a.d_weights && lane < n) {
+                    float dw = 0.0f;
+                    for (int k = 0; k < C; ++k) dw += sg[k] * sv[lane * stride + k];
+                    a.d_weights[sbase + lane] = dw;
+                }
+                __syncwarp();
             }
         } else {
             for (int s = 0; s < cnt; ++s) {
@@ -817,7 +858,11 @@ extern "C" int nacc_accumulate_along_rays_bwd(const int32_t* packed_info, int32_
     if (d_values && !values) return NACC_ERR_INVALID_ARG;
     if (n_rays == 0 || (!d_weights && !d_values)) return NACC_OK;
     AccBwdArgs a{packed_info, n_rays, weights, values, n_channels, n_samples, g_out, d_weights, d_values, d_status};
-    accumulate_bwd_kernel<<<grid_for(accumulate_bwd_kernel, n_rays), kThreads, 0, (cudaStream_t)stream>>>(a);
+    if (n_channels <= 4)
+        accumulate_bwd_narrow_kernel<<<grid_for(accumulate_bwd_narrow_kernel, n_rays), kThreads, 0,
+                                       (cudaStream_t)stream>>>(a);
+    else
+        accumulate_bwd_kernel<<<grid_for(accumulate_bwd_kernel, n_rays), kThreads, 0, (cudaStream_t)stream>>>(a);
     return launch_status(cudaGetLastError());
 }
 
