@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define NACC_VERSION 100
+#define NACC_VERSION 200
 
 /* host return codes */
 #define NACC_OK 0
@@ -153,10 +153,14 @@ int nacc_march_rays(const float* rays_o, const float* rays_d, const float* ray_t
  * device memory at call time (a renderer with a fixed, pre-planned memory
  * budget, a plugin inside a host application that owns the CUDA allocator).
  * Same arguments, results and errors as nacc_march_rays, minus the workspace:
- * the scratch lives in a fixed array of this library's device memory
- * (256 + 8 * NACC_STATIC_MAX_RAYS bytes, held by every GPU that loads the
- * library until the process exits). n_rays above NACC_STATIC_MAX_RAYS is
- * rejected with NACC_ERR_INVALID_ARG before anything is enqueued.
+ * the scratch lives in a fixed array of this library's device memory, held by
+ * every GPU that loads the library until the process exits: the look-back words
+ * of up to NACC_STATIC_MAX_RAYS rays (256 + 8 * NACC_STATIC_MAX_RAYS bytes) and
+ * the cone-step lattice table of up to NACC_STATIC_MAX_STEPS steps
+ * (4 * (NACC_STATIC_MAX_STEPS + 1) bytes, rounded up to 256), about 8.1 MiB in
+ * all. Every call nacc_march_rays accepts fits, uniform or cone steps, for any
+ * n_rays up to the limit; n_rays above NACC_STATIC_MAX_RAYS is rejected with
+ * NACC_ERR_INVALID_ARG before anything is enqueued.
  * - The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any stream
  *   capture on the device.
@@ -167,6 +171,7 @@ int nacc_march_rays(const float* rays_o, const float* rays_d, const float* ray_t
  * - Nothing is allocated: no cudaMalloc, no cudaFree, no allocating library call.
  */
 #define NACC_STATIC_MAX_RAYS (1 << 20)
+#define NACC_STATIC_MAX_STEPS 32768 /* = the largest max_steps of nacc_march_params */
 int nacc_march_rays_static(const float* rays_o, const float* rays_d, const float* ray_time,
                            const int32_t* ray_slot, int32_t n_rays, const nacc_grid* grid,
                            const nacc_march_params* params, int32_t* packed_info, float* t_starts,
@@ -312,10 +317,16 @@ int nacc_accumulate_along_rays(const int32_t* packed_info, int32_t n_rays, const
  * (with a_i = g_i); T recomputed from sigmas.
  * g_weights (n_samples,) float32 in; d_sigmas (n_samples,) float32 out; the
  * float arrays and packed_info 8-byte aligned.
+ * g_ref (n_rays,) float32 in, or NULL. When given, the upstream gradient is
+ * split in two parts, g_i = g_ref[r] + g_weights[i] (sample i in ray r), the
+ * form nacc_accumulate_along_rays_bwd writes in its centred mode: the scan takes
+ * g_ref[r] as its reference and g_weights[i] as the centred term, so the float32
+ * error of the result scales with the variation of g along the ray.
  */
 int nacc_render_weights_bwd(const int32_t* packed_info, int32_t n_rays, const float* t_starts,
                             const float* t_ends, const float* sigmas, int64_t n_samples,
-                            const float* g_weights, float* d_sigmas, int32_t* d_status, void* stream);
+                            const float* g_weights, const float* g_ref, float* d_sigmas,
+                            int32_t* d_status, void* stream);
 
 /*
  * Gradient of nacc_accumulate_along_rays for g = dL/dout (n_rays, n_channels):
@@ -323,10 +334,18 @@ int nacc_render_weights_bwd(const int32_t* packed_info, int32_t n_rays, const fl
  *   dL/dv_i[c] = w_i g[r, c]   (sample i in ray r).
  * d_weights (n_samples,) and d_values (n_samples, n_channels) float32 out,
  * each nullable (d_values needs values).
+ * g_ref (n_rays,) float32 in/out, or NULL (needs d_weights). Centred mode: the
+ * gradient of each ray's weights is written in two parts, d_weights[i] =
+ * sum_c g[r, c] (v_i[c] - v_1[c]) with v_1 the values of the ray's first sample,
+ * and sum_c g[r, c] v_1[c] ADDED to g_ref[r] (rays without samples leave it
+ * unchanged); the parts sum to dL/dw_i. The per-sample part is formed from value
+ * differences before any rounding, so nacc_render_weights_bwd given both parts
+ * keeps the precision of the fused nacc_render_bwd. Adding lets several
+ * accumulations of the same weights share one g_ref (the caller zeroes it once).
  */
 int nacc_accumulate_along_rays_bwd(const int32_t* packed_info, int32_t n_rays, const float* weights,
                                    const float* values, int32_t n_channels, int64_t n_samples,
-                                   const float* g_out, float* d_weights, float* d_values,
+                                   const float* g_out, float* d_weights, float* d_values, float* g_ref,
                                    int32_t* d_status, void* stream);
 
 /*
@@ -442,6 +461,32 @@ int nacc_sample_grid_cells(uint64_t seed, uint64_t stream, int64_t n, const nacc
 int nacc_tune_set(int knob, int value);
 /* Current value of a knob (NACC_ERR_INVALID_ARG for an unknown knob). */
 int nacc_tune_get(int knob);
+
+/* ------------------------------------------------------------------------- */
+/* Test hooks of the bounded inter-warp waits (process-wide, read at launch)  */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Marching, pruning and the fused inference march find each tile's output
+ * offset by a decoupled look-back: a warp waits for the tiles before it to
+ * publish their totals. Every wait is bounded: after a poll budget it gives up,
+ * raises NACC_STATUS_TIMEOUT, and publishes a prefix no larger than the true one,
+ * so the call still returns and every store stays below the true total (and
+ * below capacity). These hooks exist so a test can make the waits run out on
+ * purpose and check that path; they are not for production use and compute
+ * invalid results while set to anything but their defaults.
+ * NACC_TEST_HOOK_SPIN_LIMIT: polls before a wait gives up, 0 .. 2^22
+ *   (default 2^22: about a second with the back-off between polls).
+ * NACC_TEST_HOOK_WITHHOLD_FIRST_TILE: 0 (default) or 1. With 1 the first tile
+ *   never publishes its total, so every wait that reaches it runs out.
+ * Not synchronised: change hooks only while no other host thread launches
+ * library work. NACC_ERR_INVALID_ARG for an unknown hook or a value out of range.
+ */
+#define NACC_TEST_HOOK_SPIN_LIMIT 0
+#define NACC_TEST_HOOK_WITHHOLD_FIRST_TILE 1
+#define NACC_TEST_HOOK_COUNT 2
+int nacc_test_hook_set(int hook, int value);
+int nacc_test_hook_get(int hook);
 
 /* ------------------------------------------------------------------------- */
 /* Utilities                                                                 */

@@ -38,7 +38,7 @@ EXPORTS = (
     "nacc_render_weights", "nacc_accumulate_along_rays", "nacc_render_weights_bwd",
     "nacc_accumulate_along_rays_bwd", "nacc_render_fwd", "nacc_render_bwd",
     "nacc_unpack_info", "nacc_update_occupancy_grid", "nacc_sample_grid_cells", "nacc_tune_set", "nacc_tune_get",
-    "nacc_error_string",
+    "nacc_test_hook_set", "nacc_test_hook_get", "nacc_error_string",
     "nacc_version",
 )
 
@@ -111,8 +111,8 @@ def load() -> ctypes.CDLL:
         "nacc_density_field_query": (ctypes.c_int, [FP, P, i64, P, P]),
         "nacc_render_weights": (ctypes.c_int, [P, i32, P, P, P, i64, P, P, P, P]),
         "nacc_accumulate_along_rays": (ctypes.c_int, [P, i32, P, P, i32, i64, P, P, P]),
-        "nacc_render_weights_bwd": (ctypes.c_int, [P, i32, P, P, P, i64, P, P, P, P]),
-        "nacc_accumulate_along_rays_bwd": (ctypes.c_int, [P, i32, P, P, i32, i64, P, P, P, P, P]),
+        "nacc_render_weights_bwd": (ctypes.c_int, [P, i32, P, P, P, i64, P, P, P, P, P]),
+        "nacc_accumulate_along_rays_bwd": (ctypes.c_int, [P, i32, P, P, i32, i64, P, P, P, P, P, P]),
         "nacc_render_fwd": (ctypes.c_int, [P, i32, P, P, P, P, i64, P, P, P, P, P, P]),
         "nacc_render_bwd": (ctypes.c_int, [P, i32, P, P, P, P, P, i64, P, P, P, P, P, P, P]),
         "nacc_unpack_info": (ctypes.c_int, [P, i32, i64, P, P, P]),
@@ -120,6 +120,8 @@ def load() -> ctypes.CDLL:
         "nacc_sample_grid_cells": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, i64, GP, P, P, P]),
         "nacc_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
         "nacc_tune_get": (ctypes.c_int, [ctypes.c_int]),
+        "nacc_test_hook_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+        "nacc_test_hook_get": (ctypes.c_int, [ctypes.c_int]),
         "nacc_error_string": (ctypes.c_char_p, [ctypes.c_int]),
         "nacc_version": (ctypes.c_int, []),
     }
@@ -275,6 +277,7 @@ def march_rays(rays_o, rays_d, grid: Grid, params: MarchParams, packed_info, t_s
 
 
 STATIC_MAX_RAYS = 1 << 20
+STATIC_MAX_STEPS = 32768
 
 
 def march_rays_static(rays_o, rays_d, grid: Grid, params: MarchParams, packed_info, t_starts, t_ends, ray_indices,
@@ -395,20 +398,24 @@ def accumulate_along_rays(packed_info, weights, values, n_channels: int, n_sampl
 
 
 def render_weights_bwd(packed_info, t_starts, t_ends, sigmas, n_samples: int, g_weights, d_sigmas, d_status=None,
-                       stream=None, defer: bool = False):
+                       g_ref=None, stream=None, defer: bool = False):
+    """dL/dsigma for dL/dw = g_weights, or g_ref[ray] + g_weights when g_ref (n_rays,) is given."""
     n = packed_info.shape[0]
     _check(packed_info, torch.int32, "packed_info", 2 * n)
     for t, nm in ((t_starts, "t_starts"), (t_ends, "t_ends"), (sigmas, "sigmas"), (g_weights, "g_weights"),
                   (d_sigmas, "d_sigmas")):
         _check(t, torch.float32, nm, n_samples)
+    _check(g_ref, torch.float32, "g_ref", n, optional=True)
     _check(d_status, torch.int32, "d_status", 1, optional=True)
     return _call("nacc_render_weights_bwd", (_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas),
-                                             int(n_samples), _ptr(g_weights), _ptr(d_sigmas), _ptr(d_status),
-                                             _stream(stream)), defer)
+                                             int(n_samples), _ptr(g_weights), _ptr(g_ref), _ptr(d_sigmas),
+                                             _ptr(d_status), _stream(stream)), defer)
 
 
 def accumulate_along_rays_bwd(packed_info, weights, values, n_channels: int, n_samples: int, g_out, d_weights=None,
-                              d_values=None, d_status=None, stream=None, defer: bool = False):
+                              d_values=None, d_status=None, g_ref=None, stream=None, defer: bool = False):
+    """dL/dw and dL/dv of the per-ray sums; with g_ref (n_rays,) the centred mode
+    (d_weights relative to each ray's first sample, that sample's part added to g_ref)."""
     n = packed_info.shape[0]
     _check(packed_info, torch.int32, "packed_info", 2 * n)
     _check(weights, torch.float32, "weights", n_samples)
@@ -416,10 +423,12 @@ def accumulate_along_rays_bwd(packed_info, weights, values, n_channels: int, n_s
     _check(g_out, torch.float32, "g_out", n * n_channels)
     _check(d_weights, torch.float32, "d_weights", n_samples, optional=True)
     _check(d_values, torch.float32, "d_values", n_samples * n_channels, optional=True)
+    _check(g_ref, torch.float32, "g_ref", n, optional=True)
     _check(d_status, torch.int32, "d_status", 1, optional=True)
     return _call("nacc_accumulate_along_rays_bwd", (_ptr(packed_info), n, _ptr(weights), _ptr(values),
                                                     int(n_channels), int(n_samples), _ptr(g_out), _ptr(d_weights),
-                                                    _ptr(d_values), _ptr(d_status), _stream(stream)), defer)
+                                                    _ptr(d_values), _ptr(g_ref), _ptr(d_status), _stream(stream)),
+                 defer)
 
 
 def render_fwd(packed_info, t_starts, t_ends, sigmas, rgbs, n_samples: int, color, opacity, depth,
@@ -493,6 +502,25 @@ def tune_set(knob, value: int):
     """Set a launch-shape knob (name or NACC_TUNE_* index); results never change, only speed."""
     k = TUNE_KNOBS[knob] if isinstance(knob, str) else int(knob)
     _rc(load().nacc_tune_set(k, int(value)), "nacc_tune_set")
+
+
+TEST_HOOKS = {"spin_limit": 0, "withhold_first_tile": 1}
+SPIN_LIMIT_DEFAULT = 1 << 22
+
+
+def test_hook_set(hook, value: int):
+    """Set a look-back test hook (name or NACC_TEST_HOOK_* index). Tests only:
+    results are invalid while a hook is away from its default."""
+    k = TEST_HOOKS[hook] if isinstance(hook, str) else int(hook)
+    _rc(load().nacc_test_hook_set(k, int(value)), "nacc_test_hook_set")
+
+
+def test_hook_get(hook) -> int:
+    k = TEST_HOOKS[hook] if isinstance(hook, str) else int(hook)
+    v = load().nacc_test_hook_get(k)
+    if v < 0:
+        raise NaccError("unknown test hook %r" % (hook,))
+    return v
 
 
 def tune_get(knob) -> int:

@@ -361,10 +361,14 @@ def rendering(rgb_sigma_fn: Callable, packed_info, t_starts, t_ends, ray_indices
 
 
 class _WeightsFn(torch.autograd.Function):
-    """Eq. 1 weights; backward: any dL/dw to dL/dsigma (reverse segmented scan)."""
+    """Eq. 1 weights; backward: any dL/dw to dL/dsigma (reverse segmented scan).
+
+    ``g_ref`` (n_rays,) collects the per-ray part of dL/dw that centred
+    accumulations of these weights hand over (see ``accumulate_along_rays``); the
+    backward adds it back: dL/dw_i = g_ref[ray of i] + (incoming gradient)_i."""
 
     @staticmethod
-    def forward(ctx, sigmas, packed_info, t_starts, t_ends):
+    def forward(ctx, sigmas, packed_info, t_starts, t_ends, g_ref):
         M = t_starts.numel()
         dev = packed_info.device
         sg = sigmas.detach().contiguous().view(-1).float()
@@ -372,6 +376,7 @@ class _WeightsFn(torch.autograd.Function):
         T = torch.empty(M, dtype=torch.float32, device=dev)
         _lib.render_weights(packed_info, t_starts, t_ends, sg, M, w, T)
         ctx.save_for_backward(sg, packed_info, t_starts, t_ends)
+        ctx.g_ref = g_ref
         ctx.sig_shape = sigmas.shape
         ctx.mark_non_differentiable(T)
         return w, T
@@ -382,22 +387,38 @@ class _WeightsFn(torch.autograd.Function):
         M = t_starts.numel()
         d_sig = torch.empty(M, dtype=torch.float32, device=sg.device)
         g = torch.zeros(M, dtype=torch.float32, device=sg.device) if g_w is None else g_w.contiguous().float()
-        _lib.render_weights_bwd(packed_info, t_starts, t_ends, sg, M, g, d_sig)
-        return d_sig.view(ctx.sig_shape), None, None, None
+        g_ref = ctx.g_ref
+        _lib.render_weights_bwd(packed_info, t_starts, t_ends, sg, M, g, d_sig, g_ref=g_ref)
+        g_ref.zero_()  # handed over: a second backward through the graph starts from zero again
+        return d_sig.view(ctx.sig_shape), None, None, None, None
 
 
 def render_weights(packed_info, t_starts, t_ends, sigmas):
     """Per-sample Eq. 1 weights and transmittance, differentiable w.r.t. sigmas
-    through the weights (Sec. 2.2). Returns (weights (M,), trans (M,))."""
-    return _WeightsFn.apply(sigmas, packed_info.contiguous(), t_starts.contiguous().view(-1),
-                            t_ends.contiguous().view(-1))
+    through the weights (Sec. 2.2). Returns (weights (M,), trans (M,)).
+
+    When the returned ``weights`` tensor itself is passed to
+    ``accumulate_along_rays`` (with the same ``packed_info``), the gradient
+    between the two is carried in centred form: the accumulation's backward hands
+    autograd dL/dw_i minus the value at the ray's first sample and keeps that
+    per-ray value on the side, and this function's backward adds it back. Errors
+    then scale with how much dL/dw varies along a ray, as in the fused
+    ``render_packed``. The gradient is exact either way; only a hook or
+    ``retain_grad`` on ``weights`` sees the centred values."""
+    pi = packed_info.contiguous()
+    g_ref = torch.zeros(pi.shape[0], dtype=torch.float32, device=pi.device)
+    w, T = _WeightsFn.apply(sigmas, pi, t_starts.contiguous().view(-1), t_ends.contiguous().view(-1), g_ref)
+    w._nacc_centre = (g_ref, pi, w._version)
+    return w, T
 
 
 class _AccumulateFn(torch.autograd.Function):
-    """sum_i w_i v_i per ray; backward: dL/dw_i = <g_r, v_i>, dL/dv_i = w_i g_r."""
+    """sum_i w_i v_i per ray; backward: dL/dw_i = <g_r, v_i>, dL/dv_i = w_i g_r.
+    With ``g_ref`` (weights straight from ``render_weights``) dL/dw is handed back
+    centred: <g_r, v_i - v_first>, and <g_r, v_first> is added to g_ref[r]."""
 
     @staticmethod
-    def forward(ctx, weights, values, packed_info):
+    def forward(ctx, weights, values, packed_info, g_ref):
         M = weights.numel()
         w = weights.detach().contiguous().view(-1).float()
         v = None if values is None else values.detach().contiguous().view(M, -1).float()
@@ -405,6 +426,7 @@ class _AccumulateFn(torch.autograd.Function):
         out = torch.empty((packed_info.shape[0], C), dtype=torch.float32, device=w.device)
         _lib.accumulate_along_rays(packed_info, w, v, C, M, out)
         ctx.save_for_backward(w, *([] if v is None else [v]), packed_info)
+        ctx.g_ref = g_ref
         ctx.has_values = v is not None
         ctx.shapes = (weights.shape, None if values is None else values.shape)
         return out
@@ -419,13 +441,24 @@ class _AccumulateFn(torch.autograd.Function):
         dw = torch.empty(M, dtype=torch.float32, device=w.device) if ctx.needs_input_grad[0] else None
         dv = (torch.empty((M, C), dtype=torch.float32, device=w.device)
               if v is not None and ctx.needs_input_grad[1] else None)
+        g_ref = ctx.g_ref if dw is not None else None
         if dw is not None or dv is not None:
-            _lib.accumulate_along_rays_bwd(packed_info, w, v, C, M, g_out.contiguous().float(), dw, dv)
+            _lib.accumulate_along_rays_bwd(packed_info, w, v, C, M, g_out.contiguous().float(), dw, dv, g_ref=g_ref)
         return (None if dw is None else dw.view(ctx.shapes[0]),
-                None if dv is None else dv.view(ctx.shapes[1]), None)
+                None if dv is None else dv.view(ctx.shapes[1]), None, None)
 
 
 def accumulate_along_rays(weights, packed_info, values=None):
     """sum_i w_i v_i per ray for any attribute (Sec. 2.2), differentiable w.r.t.
     weights and values. values (M, C) or None (opacity). Returns (R, C)."""
-    return _AccumulateFn.apply(weights, values, packed_info.contiguous())
+    pi = packed_info.contiguous()
+    g_ref = None
+    centre = getattr(weights, "_nacc_centre", None)
+    if centre is not None:
+        ref, ref_pi, version = centre
+        # the centred hand-over only for the weights tensor render_weights returned,
+        # unmodified, over the same rays
+        if version == weights._version and (ref_pi is pi or (ref_pi.data_ptr() == pi.data_ptr()
+                                                             and ref_pi.shape == pi.shape)):
+            g_ref = ref
+    return _AccumulateFn.apply(weights, values, pi, g_ref)

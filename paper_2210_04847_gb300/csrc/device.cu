@@ -46,6 +46,18 @@ const int g_tune_hi[NACC_TUNE_COUNT] = {1, 32, 32, 1, 2, 2, 2, 1, 4, 1, 1, 1};
 
 int tune_get(int knob) { return (knob >= 0 && knob < NACC_TUNE_COUNT) ? g_tune[knob] : 0; }
 
+namespace {
+// Test hooks of the look-back waits, read at every launch (defaults: the full
+// poll budget, every tile publishes).
+int g_hook[NACC_TEST_HOOK_COUNT] = {kSpinLimit, 0};
+const int g_hook_lo[NACC_TEST_HOOK_COUNT] = {0, 0};
+const int g_hook_hi[NACC_TEST_HOOK_COUNT] = {kSpinLimit, 1};
+}  // namespace
+
+LookbackHooks lookback_hooks() {
+    return LookbackHooks{g_hook[NACC_TEST_HOOK_SPIN_LIMIT], g_hook[NACC_TEST_HOOK_WITHHOLD_FIRST_TILE]};
+}
+
 }  // namespace nacc
 
 extern "C" int nacc_tune_set(int knob, int value) {
@@ -60,6 +72,18 @@ extern "C" int nacc_tune_set(int knob, int value) {
 extern "C" int nacc_tune_get(int knob) {
     if (knob < 0 || knob >= NACC_TUNE_COUNT) return NACC_ERR_INVALID_ARG;
     return nacc::g_tune[knob];
+}
+
+extern "C" int nacc_test_hook_set(int hook, int value) {
+    if (hook < 0 || hook >= NACC_TEST_HOOK_COUNT) return NACC_ERR_INVALID_ARG;
+    if (value < nacc::g_hook_lo[hook] || value > nacc::g_hook_hi[hook]) return NACC_ERR_INVALID_ARG;
+    nacc::g_hook[hook] = value;
+    return NACC_OK;
+}
+
+extern "C" int nacc_test_hook_get(int hook) {
+    if (hook < 0 || hook >= NACC_TEST_HOOK_COUNT) return NACC_ERR_INVALID_ARG;
+    return nacc::g_hook[hook];
 }
 
 extern "C" const char* nacc_error_string(int code) {

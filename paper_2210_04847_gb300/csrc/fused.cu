@@ -174,7 +174,7 @@ __device__ __forceinline__ void fused_finish(const FusedArgs& A, const uint32_t*
     const MarchArgs& a = A.m;
     const unsigned lt = lanemask_lt();
     const long long excl =
-        (long long)resolve_prefix(a.tile_status, t.tile, (unsigned long long)t.agg, lane, a.d_status);
+        (long long)resolve_prefix(a.tile_status, t.tile, (unsigned long long)t.agg, lane, a.d_status, a.hooks);
     const int my_excl = t.incl - t.my_count;
     if (lane < t.nr) {
         const int2 pi = make_int2((int)(excl + my_excl), t.my_count);
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, MINB) march_fused_kernel(const Fused
             cur.my_far = my_far;
             cur.incl = warp_incl_scan_int(cur.my_count, lane);
             cur.agg = __shfl_sync(FULL, cur.incl, 31);
-            publish_aggregate(a.tile_status, cur.tile, (unsigned long long)cur.agg, lane);
+            publish_aggregate(a.tile_status, cur.tile, (unsigned long long)cur.agg, lane, a.hooks);
         }
         if (have_prev) {
             fused_finish<CONE>(A, wbase + (buf ^ 1) * tile_words, prev, lat, lane);
@@ -411,6 +411,7 @@ extern "C" int nacc_march_fused(const float* rays_o, const float* rays_d, int32_
     a.ticket = (unsigned int*)workspace;
     a.lattice_points = (unsigned long long*)((char*)workspace + 8);
     a.tile_status = (unsigned long long*)((char*)workspace + kTicketBytes);
+    a.hooks = lookback_hooks();
     a.tile_rays = tile_rays_for(a.mask_words);
     A.sigmas_out = capacity > 0 ? sigmas : nullptr;
     A.use_t = early_stop_eps > 0.0f;

@@ -323,7 +323,7 @@ struct TileState {
 __device__ __forceinline__ void publish_tile(const MarchArgs& a, TileState& t, int lane) {
     t.incl = warp_incl_scan_int(t.my_count, lane);
     t.agg = __shfl_sync(FULL, t.incl, 31);
-    publish_aggregate(a.tile_status, t.tile, (unsigned long long)t.agg, lane);
+    publish_aggregate(a.tile_status, t.tile, (unsigned long long)t.agg, lane, a.hooks);
 }
 
 // The tile's offset by look-back, then the ballot words expanded into
@@ -337,7 +337,7 @@ __device__ __forceinline__ void finish_tile(const MarchArgs& a, const uint32_t* 
     const int my_count = t.my_count, my_nch = t.my_nch;
     const float my_near = t.my_near, my_far = t.my_far;
     const long long excl =
-        (long long)resolve_prefix(a.tile_status, tile, (unsigned long long)agg, lane, a.d_status);
+        (long long)resolve_prefix(a.tile_status, tile, (unsigned long long)agg, lane, a.d_status, a.hooks);
     const int my_excl = t.incl - my_count;
     if (lane < nr) {
         const int2 pi = make_int2((int)(excl + my_excl), my_count);
@@ -556,6 +556,7 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
     a.ticket = (unsigned int*)workspace;
     a.lattice_points = (unsigned long long*)((char*)workspace + 8);
     a.tile_status = (unsigned long long*)((char*)workspace + kTicketBytes);
+    a.hooks = lookback_hooks();
     const bool cone = p->cone > 0.0f;
     const bool occ = tune_get(NACC_TUNE_MARCH_OCCUPANCY) != 0;
     a.tile_rays = tile_rays_for(a.mask_words);

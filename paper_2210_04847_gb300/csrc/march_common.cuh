@@ -57,6 +57,7 @@ struct MarchArgs {
     float cc[3], inv_h[3];    // contraction: box centre and 1 / half size
     float qres[3];            // contraction: res / 4 (the grid spans [-2, 2])
     float inv_dt;             // 1 / dt_min, for the first guess of a uniform lattice's length
+    LookbackHooks hooks;      // look-back poll budget (test hooks)
     Levels L;
 };
 

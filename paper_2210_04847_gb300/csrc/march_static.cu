@@ -15,8 +15,14 @@
 namespace {
 
 // Ticket (256 bytes) + one look-back word per ray, for up to NACC_STATIC_MAX_RAYS
-// rays. Every GPU that loads the library holds this array until the process exits.
-constexpr size_t kStaticScratchBytes = 256 + (size_t)NACC_STATIC_MAX_RAYS * sizeof(unsigned long long);
+// rays, then the cone-step lattice table (t_0 .. t_max_steps, float32) for the
+// largest max_steps any marching call accepts (32768), each part rounded up to
+// 256 bytes as nacc_march_workspace_size lays them out. Every valid call fits.
+// Every GPU that loads the library holds this array until the process exits.
+constexpr size_t kStaticStatusBytes =
+    (256 + (size_t)NACC_STATIC_MAX_RAYS * sizeof(unsigned long long) + 255) / 256 * 256;
+constexpr size_t kStaticTableBytes = ((size_t)(NACC_STATIC_MAX_STEPS + 1) * sizeof(float) + 255) / 256 * 256;
+constexpr size_t kStaticScratchBytes = kStaticStatusBytes + kStaticTableBytes;
 static __device__ __align__(256) unsigned char g_march_scratch[kStaticScratchBytes];
 
 // Device address of g_march_scratch per device. In host code the array's name is

@@ -74,14 +74,26 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // Tiles are numbered by an atomic ticket taken when a warp starts work on
 // them, so every tile a warp waits for is held by a warp that is already
 // running and publishes its aggregate without waiting: the wait always ends.
-// It is still bounded: after kSpinLimit polls the warp reports
-// NACC_STATUS_TIMEOUT, stops waiting, and publishes a (wrong) prefix so that
-// no other warp waits on it either.
+// It is still bounded: after spin_limit polls (2^22 by default, about a second
+// with the back-off below) the warp reports NACC_STATUS_TIMEOUT, stops waiting,
+// and publishes a (too small) prefix so that no other warp waits on it either.
+// Every prefix is then at most the true one, so every store stays below the
+// true total.
+//
+// Two test hooks (nacc_test_hook_set) reach these waits: the poll budget, and a
+// switch under which tile 0 never publishes its prefix, so that every wait that
+// reaches it runs out. A test uses them to check the timeout path on the GPU
+// without any fault, trap or unbounded loop.
 
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
 constexpr int kSpinLimit = 1 << 22;
+
+struct LookbackHooks {
+    int spin_limit;      // polls before a wait gives up (default kSpinLimit)
+    int withhold_first;  // 1: tile 0's prefix is never published (test only)
+};
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
     unsigned long long v;
@@ -95,8 +107,10 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
 
 // Publishes a tile's aggregate (tile 0: its inclusive prefix). Never waits.
 __device__ __forceinline__ void publish_aggregate(unsigned long long* status, int tile,
-                                                  unsigned long long aggregate, int lane) {
-    if (lane == 0) st_relaxed_u64(&status[tile], (tile == 0 ? kFlagInc : kFlagAgg) | (aggregate & kValMask));
+                                                  unsigned long long aggregate, int lane,
+                                                  const LookbackHooks& hooks) {
+    if (lane == 0 && !(tile == 0 && hooks.withhold_first))
+        st_relaxed_u64(&status[tile], (tile == 0 ? kFlagInc : kFlagAgg) | (aggregate & kValMask));
 }
 
 // Called by one full warp after publish_aggregate(tile). Returns the exclusive
@@ -106,7 +120,8 @@ __device__ __forceinline__ void publish_aggregate(unsigned long long* status, in
 // the warp holding that ticket publishes its aggregate before it waits.
 __device__ __forceinline__ unsigned long long resolve_prefix(unsigned long long* status, int tile,
                                                              unsigned long long aggregate, int lane,
-                                                             int32_t* d_status) {
+                                                             int32_t* d_status, const LookbackHooks& hooks) {
+    const int spin_limit = hooks.spin_limit;
     if (tile == 0) return 0ull;
     unsigned long long excl = 0;
     int base = tile - 1;
@@ -117,7 +132,7 @@ __device__ __forceinline__ unsigned long long resolve_prefix(unsigned long long*
         unsigned long long s = j >= 0 ? ld_relaxed_u64(&status[j]) : (kFlagInc | 0ull);
         unsigned pending = __ballot_sync(FULL, (s >> 62) == 0ull);
         while (pending) {
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 timed_out = true;
                 break;
             }
@@ -146,13 +161,6 @@ __device__ __forceinline__ unsigned long long resolve_prefix(unsigned long long*
     return excl;
 }
 
-// Both steps at once: publish the tile's aggregate, then wait for its prefix.
-__device__ __forceinline__ unsigned long long lookback(unsigned long long* status, int tile,
-                                                       unsigned long long aggregate, int lane,
-                                                       int32_t* d_status) {
-    publish_aggregate(status, tile, aggregate, lane);
-    return resolve_prefix(status, tile, aggregate, lane, d_status);
-}
 
 // ---------------------------------------------------------------------------
 // host helpers
@@ -167,6 +175,9 @@ DeviceInfo current_device();
 
 // Current value of a tuning knob (NACC_TUNE_*), the library default unless set.
 int tune_get(int knob);
+
+// The look-back settings in force (test hooks; defaults unless a test set them).
+LookbackHooks lookback_hooks();
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 

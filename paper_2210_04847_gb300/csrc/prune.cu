@@ -50,6 +50,7 @@ struct PruneArgs {
     uint32_t* masks;
     int32_t n_tiles;
     int32_t tile_rays;
+    LookbackHooks hooks;  // look-back poll budget (test hooks)
 };
 
 // Row of ballot words of ray r whose run starts at `off`: two words per 64-sample
@@ -247,7 +248,7 @@ __device__ __forceinline__ void decide_tile(const PruneArgs& a, int tile, int la
     t.my_nch = my_nch;
     t.incl = warp_incl_scan_int(my_count, lane);
     t.agg = __shfl_sync(FULL, t.incl, 31);
-    publish_aggregate(a.tile_status, tile, (unsigned long long)t.agg, lane);
+    publish_aggregate(a.tile_status, tile, (unsigned long long)t.agg, lane, a.hooks);
 }
 
 // Phases 2 and 3 of a tile: its offset from the look-back, then the compacted
@@ -258,7 +259,7 @@ __device__ __forceinline__ void finish_tile(const PruneArgs& a, const TileState&
     if (seen < 0) seen = 0;
     for (int o = 16; o > 0; o >>= 1) seen += __shfl_xor_sync(FULL, seen, o);
     const long long excl =
-        (long long)resolve_prefix(a.tile_status, t.tile, (unsigned long long)t.agg, lane, a.d_status);
+        (long long)resolve_prefix(a.tile_status, t.tile, (unsigned long long)t.agg, lane, a.d_status, a.hooks);
     const int my_excl = t.incl - t.my_count;
     if (lane < nr) {
         const int2 pi = make_int2((int)(excl + my_excl), t.my_count);
@@ -461,6 +462,7 @@ extern "C" int nacc_prune_samples(const int32_t* packed_info, int32_t n_rays, co
     a.ticket = (unsigned int*)workspace;
     a.examined = (unsigned long long*)((char*)workspace + 8);
     a.tile_status = (unsigned long long*)((char*)workspace + kTicketBytes);
+    a.hooks = lookback_hooks();
     const size_t head = align_up(kTicketBytes + (size_t)a.n_tiles * sizeof(unsigned long long), 256);
     a.masks = (uint32_t*)((char*)workspace + head);
 

@@ -428,25 +428,49 @@ struct AccBwdArgs {
     const float* g_out;
     float* d_weights;
     float* d_values;
+    float* g_ref;  // centred mode: per-ray dL/dw of the first sample, added in
     int32_t* d_status;
 };
+
+// Centred mode (g_ref given): dL/dw_i is written as sum_c g[r,c] (v_i[c] - v_1[c]),
+// v_1 the values of the ray's first sample, and sum_c g[r,c] v_1[c] is added to
+// g_ref[r]. The two parts add up to dL/dw_i, but the per-sample part is formed
+// from value differences before any rounding, so its float32 error scales with
+// how much the values vary along the ray rather than with their size. The
+// weights backward takes g_ref as the reference of its centred scan.
+__device__ __forceinline__ void add_g_ref(const AccBwdArgs& a, int r, int off, int cnt, int lane) {
+    if (!a.g_ref || cnt == 0) return;
+    const int C = a.n_channels;
+    const float* g = a.g_out + (size_t)r * C;
+    float ref = 0.0f;
+    for (int c = lane; c < C; c += 32) ref += __ldg(g + c) * (a.values ? __ldg(a.values + (size_t)off * C + c) : 1.0f);
+    ref = warp_sum(ref);
+    if (lane == 0) a.g_ref[r] += ref;
+}
 
 // The same gradient for C <= 4 channels: a lane per sample, its values one short
 // run (no shared memory, so more warps per SM than the tiled kernel).
 __global__ void __launch_bounds__(kThreads) accumulate_bwd_narrow_kernel(const AccBwdArgs a) {
     const int lane = threadIdx.x & 31;
     const int C = a.n_channels;
+    const bool centre = a.g_ref != nullptr;
     for (int r = global_warp(); r < a.n_rays; r += n_global_warps()) {
         int off, cnt;
         load_run(a.packed_info, r, a.n_samples, a.d_status, lane, off, cnt);
+        add_g_ref(a, r, off, cnt, lane);
         const float* g = a.g_out + (size_t)r * C;
+        const float* v1 = a.values ? a.values + (size_t)off * C : nullptr;  // the ray's first sample
         for (int j = lane; j < cnt; j += 32) {
             const size_t i = (size_t)off + j;
             const float w = __ldg(a.weights + i);
             float dw = 0.0f;
             for (int c = 0; c < C; ++c) {
                 const float gc = __ldg(g + c);
-                dw += a.values ? gc * __ldg(a.values + i * C + c) : gc;
+                if (centre) {
+                    if (a.values) dw += gc * (__ldg(a.values + i * C + c) - __ldg(v1 + c));
+                } else {
+                    dw += a.values ? gc * __ldg(a.values + i * C + c) : gc;
+                }
                 if (a.d_values) a.d_values[i * C + c] = w * gc;
             }
             if (a.d_weights) a.d_weights[i] = dw;
@@ -465,12 +489,15 @@ __global__ void __launch_bounds__(kThreads) accumulate_bwd_kernel(const AccBwdAr
     __shared__ float s_v[kWarps][32 * 33];
     __shared__ float s_g[kWarps][32];
     __shared__ float s_w[kWarps][32];
+    __shared__ float s_v1[kWarps][32];  // centred mode: the ray's first sample's values
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int C = a.n_channels;
+    const bool centre = a.g_ref != nullptr;
     float* sv = s_v[warp];
     float* sg = s_g[warp];
     float* sw = s_w[warp];
+    float* sv1 = s_v1[warp];
     const int stride = C | 1;
     const int q = C <= 32 ? 32 / C : 0, rem = C <= 32 ? 32 - q * C : 0;  // +32 elements: +q samples, +rem channels
     const int s_first = C <= 32 ? lane / C : 0, c_first = C <= 32 ? lane - s_first * C : 0;
@@ -478,8 +505,10 @@ __global__ void __launch_bounds__(kThreads) accumulate_bwd_kernel(const AccBwdAr
         int off, cnt;
         load_run(a.packed_info, r, a.n_samples, a.d_status, lane, off, cnt);
         const float* g = a.g_out + (size_t)r * C;
+        add_g_ref(a, r, off, cnt, lane);
         if (C <= 32) {
             if (lane < C) sg[lane] = __ldg(g + lane);
+            if (centre && lane < C) sv1[lane] = cnt > 0 && a.values ? __ldg(a.values + (size_t)off * C + lane) : 1.0f;
             for (int j0 = 0; j0 < cnt; j0 += 32) {
                 const int n = min(32, cnt - j0);
                 const size_t sbase = (size_t)off + j0;
@@ -513,7 +542,11 @@ __global__ void __launch_bounds__(kThreads) accumulate_bwd_kernel(const AccBwdAr
                 __syncwarp();
                 if (a.d_weights && lane < n) {
                     float dw = 0.0f;
-                    for (int k = 0; k < C; ++k) dw += sg[k] * sv[lane * stride + k];
+                    if (centre) {
+                        for (int k = 0; k < C; ++k) dw += sg[k] * (sv[lane * stride + k] - sv1[k]);
+                    } else {
+                        for (int k = 0; k < C; ++k) dw += sg[k] * sv[lane * stride + k];
+                    }
                     a.d_weights[sbase + lane] = dw;
                 }
                 __syncwarp();
@@ -527,7 +560,11 @@ __global__ void __launch_bounds__(kThreads) accumulate_bwd_kernel(const AccBwdAr
                     const int c = cg + lane;
                     if (c < C) {
                         const float gc = __ldg(g + c);
-                        dw += a.values ? gc * __ldg(a.values + i * C + c) : gc;
+                        if (centre) {
+                            if (a.values) dw += gc * (__ldg(a.values + i * C + c) - __ldg(a.values + (size_t)off * C + c));
+                        } else {
+                            dw += a.values ? gc * __ldg(a.values + i * C + c) : gc;
+                        }
                         if (a.d_values) a.d_values[i * C + c] = w * gc;
                     }
                 }
@@ -560,6 +597,7 @@ struct BwdArgs {
     float* d_rgbs;
     int32_t* d_status;
     const float* g_weights;  // weights mode: dL/dw_i (no rgb, g_color, d_rgbs)
+    const float* g_ref;      // weights mode, centred input: dL/dw_i = g_ref[r] + g_weights[i]
 };
 
 // tau of both samples of the lane's pair in chunk c of a ray (pass A of the backward).
@@ -637,9 +675,17 @@ __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const 
         if (PREFETCH && !WEIGHTS)
             load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, abase + ((unsigned)(nch - 1) << 6) + 2 * lane, lo, hi,
                       nx);
-        float r_ref = 0.0f, g_ref = 0.0f, b_ref = 0.0f, tm_ref = 0.0f, a_ref;
+        // weights mode: a_i = g_weights[i] with a_ref = a_1 (b_i = a_i - a_1), or,
+        // with g_ref, a_i = g_ref[r] + g_weights[i], the reference given and b_i the
+        // centred input itself
+        float r_ref = 0.0f, g_ref = 0.0f, b_ref = 0.0f, tm_ref = 0.0f, a_ref, a_sub = 0.0f;
         if constexpr (WEIGHTS) {
-            a_ref = __ldg(a.g_weights + lo);
+            if (a.g_ref) {
+                a_ref = __ldg(a.g_ref + r);
+            } else {
+                a_ref = __ldg(a.g_weights + lo);
+                a_sub = a_ref;
+            }
         } else {
             r_ref = __ldg(a.rgbs + 3 * lo);
             g_ref = __ldg(a.rgbs + 3 * lo + 1);
@@ -702,8 +748,8 @@ __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const 
             const float tm0 = (q.s0[0] + q.s1[0]) * 0.5f, tm1 = (q.s0[1] + q.s1[1]) * 0.5f;
             float b0, b1;
             if constexpr (WEIGHTS) {
-                b0 = q.rgb[0] - a_ref;
-                b1 = q.rgb[3] - a_ref;
+                b0 = q.rgb[0] - a_sub;
+                b1 = q.rgb[3] - a_sub;
             } else {
                 b0 = gc0 * (q.rgb[0] - r_ref) + gc1 * (q.rgb[1] - g_ref) + gc2 * (q.rgb[2] - b_ref) +
                      gd * (tm0 - tm_ref);
@@ -851,13 +897,15 @@ extern "C" int nacc_accumulate_along_rays(const int32_t* packed_info, int32_t n_
 extern "C" int nacc_accumulate_along_rays_bwd(const int32_t* packed_info, int32_t n_rays, const float* weights,
                                               const float* values, int32_t n_channels, int64_t n_samples,
                                               const float* g_out, float* d_weights, float* d_values,
-                                              int32_t* d_status, void* stream) {
+                                              float* g_ref, int32_t* d_status, void* stream) {
     if (!sizes_ok(n_rays, n_samples) || n_channels < 1) return NACC_ERR_INVALID_ARG;
     if (n_rays > 0 && (!packed_info || !g_out)) return NACC_ERR_INVALID_ARG;
     if (n_samples > 0 && !weights) return NACC_ERR_INVALID_ARG;
     if (d_values && !values) return NACC_ERR_INVALID_ARG;
+    if (g_ref && !d_weights) return NACC_ERR_INVALID_ARG;
     if (n_rays == 0 || (!d_weights && !d_values)) return NACC_OK;
-    AccBwdArgs a{packed_info, n_rays, weights, values, n_channels, n_samples, g_out, d_weights, d_values, d_status};
+    AccBwdArgs a{packed_info, n_rays, weights, values, n_channels, n_samples, g_out, d_weights, d_values, g_ref,
+                 d_status};
     if (n_channels <= 4)
         accumulate_bwd_narrow_kernel<<<grid_for(accumulate_bwd_narrow_kernel, n_rays), kThreads, 0,
                                        (cudaStream_t)stream>>>(a);
@@ -868,7 +916,8 @@ extern "C" int nacc_accumulate_along_rays_bwd(const int32_t* packed_info, int32_
 
 extern "C" int nacc_render_weights_bwd(const int32_t* packed_info, int32_t n_rays, const float* t_starts,
                                        const float* t_ends, const float* sigmas, int64_t n_samples,
-                                       const float* g_weights, float* d_sigmas, int32_t* d_status, void* stream) {
+                                       const float* g_weights, const float* g_ref, float* d_sigmas,
+                                       int32_t* d_status, void* stream) {
     if (!sizes_ok(n_rays, n_samples)) return NACC_ERR_INVALID_ARG;
     if (n_rays > 0 && !packed_info) return NACC_ERR_INVALID_ARG;
     if (n_samples > 0 && (!t_starts || !t_ends || !sigmas || !g_weights || !d_sigmas)) return NACC_ERR_INVALID_ARG;
@@ -877,7 +926,7 @@ extern "C" int nacc_render_weights_bwd(const int32_t* packed_info, int32_t n_ray
           (uintptr_t)g_weights | (uintptr_t)d_sigmas) & 7u) != 0)
         return NACC_ERR_INVALID_ARG;
     BwdArgs a{packed_info, n_rays, t_starts, t_ends, sigmas, nullptr, nullptr, n_samples,
-              nullptr, nullptr, nullptr, d_sigmas, nullptr, d_status, g_weights};
+              nullptr, nullptr, nullptr, d_sigmas, nullptr, d_status, g_weights, g_ref};
     const int nb = group_blocks(n_rays);
     cudaStream_t st = (cudaStream_t)stream;
     switch (tune_get(NACC_TUNE_RENDER_BWD_OCCUPANCY)) {
@@ -902,7 +951,7 @@ extern "C" int nacc_render_bwd(const int32_t* packed_info, int32_t n_rays, const
           (uintptr_t)optical_depth | (uintptr_t)d_sigmas | (uintptr_t)d_rgbs) & 7u) != 0)
         return NACC_ERR_INVALID_ARG;
     BwdArgs a{packed_info, n_rays, t_starts, t_ends, sigmas, rgbs, optical_depth, n_samples,
-              g_color, g_opacity, g_depth, d_sigmas, d_rgbs, d_status, nullptr};
+              g_color, g_opacity, g_depth, d_sigmas, d_rgbs, d_status, nullptr, nullptr};
     const int nb = group_blocks(n_rays);
     cudaStream_t st = (cudaStream_t)stream;
     const bool pf = tune_get(NACC_TUNE_RENDER_BWD_PREFETCH) != 0;

@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(libs):
 
 def test_version_and_error_strings(libs):
     lib, _ = libs
-    assert lib.nacc_version() == 100
+    assert lib.nacc_version() == 200
     assert lib.nacc_error_string(-1) == b"invalid argument"
     assert lib.nacc_error_string(12345) == b"unknown error code"
 
@@ -137,3 +137,15 @@ def test_fused_and_density_field_arguments_rejected_on_host(libs):
     assert lib.nacc_density_field_at_samples(ctypes.byref(f), None, None, 4, None, None, None, 3, None, None,
                                              None) == _lib.ERR_INVALID_ARG
     assert lib.nacc_density_field_query(ctypes.byref(f), None, 0, None, None) == _lib.OK  # nothing to do
+
+
+def test_lookback_test_hooks_validate_and_default(libs):
+    lib, _ = libs
+    assert lib.nacc_test_hook_get(0) == 1 << 22 and lib.nacc_test_hook_get(1) == 0
+    assert lib.nacc_test_hook_set(0, -1) == _lib.ERR_INVALID_ARG
+    assert lib.nacc_test_hook_set(0, (1 << 22) + 1) == _lib.ERR_INVALID_ARG
+    assert lib.nacc_test_hook_set(1, 2) == _lib.ERR_INVALID_ARG
+    assert lib.nacc_test_hook_set(2, 0) == _lib.ERR_INVALID_ARG
+    assert lib.nacc_test_hook_get(7) == _lib.ERR_INVALID_ARG
+    assert lib.nacc_test_hook_set(0, 17) == _lib.OK and lib.nacc_test_hook_get(0) == 17
+    assert lib.nacc_test_hook_set(0, 1 << 22) == _lib.OK and lib.nacc_test_hook_get(0) == 1 << 22

@@ -266,6 +266,47 @@ def test_accumulate_bwd_parity(scene, orc, C):
         assert np.max(np.abs(dv.cpu().numpy() - dv_o)) <= 1e-6
 
 
+@pytest.mark.parametrize("C", [1, 3, 7, 16, 33])
+def test_accumulate_bwd_centred_then_weights_bwd(scene, orc, C):
+    """Centred mode of the accumulation gradient: d_weights holds dL/dw_i minus the
+    ray's first sample's value, which is added to g_ref (here on top of a seeded
+    start value, to check that it adds). Fed to the weights gradient with g_ref,
+    dL/dsigma meets the 1e-4 bar against the float64 oracle of the composition."""
+    p, sg = scene["p"], scene["sig2"]
+    R, M = p.packed_info.shape[0], p.n_samples
+    w_o, _ = orc.render_weights(p.packed_info, p.t_starts, p.t_ends, sg)
+    w = w_o.astype(np.float32)
+    # values that vary little along a ray on top of a large common part: the case
+    # where the uncentred float32 dL/dw loses the differences the scan needs
+    base = synth.rand_uniform(C, 31, C, 0.5, 2.0).astype(np.float32)
+    vals = None if C == 1 else (base[None, :] + synth.rand_uniform(C, 32, M * C, -1e-3, 1e-3).reshape(M, C)
+                                ).astype(np.float32)
+    g = synth.rand_uniform(C, 33, R * C, -1, 1).reshape(R, C).astype(np.float32)
+    g_ref0 = synth.rand_uniform(C, 34, R, -0.5, 0.5).astype(np.float32)
+    dw = torch.full((M,), float("nan"), device="cuda")
+    g_ref = dev(g_ref0.copy())
+    _lib.accumulate_along_rays_bwd(dev(p.packed_info), dev(w), dev(vals), C, M, dev(g), dw, None, g_ref=g_ref)
+    torch.cuda.synchronize()
+    dw_o, _ = orc.accumulate_bwd(p.packed_info, w.astype(np.float64), vals, g.astype(np.float64))
+    first = np.repeat(p.packed_info[:, 0], p.packed_info[:, 1])
+    ray = np.repeat(np.arange(R), p.packed_info[:, 1])
+    has = p.packed_info[:, 1] > 0
+    ref_ray = np.where(has, dw_o[np.minimum(p.packed_info[:, 0], max(M - 1, 0))], 0.0)
+    got_ref = g_ref.cpu().numpy().astype(np.float64) - g_ref0
+    assert np.max(np.abs(got_ref - ref_ray)) <= 1e-5 * max(1.0, np.abs(ref_ray).max())
+    centred_o = dw_o - dw_o[first]
+    spread = np.abs(centred_o).max() if M else 0.0
+    assert np.max(np.abs(dw.cpu().numpy() - centred_o), initial=0.0) <= 1e-5 * max(spread, 1e-6)
+    # the weights gradient from the two parts (g_ref holds the seeded start too)
+    ds = torch.full((M,), float("nan"), device="cuda")
+    _lib.render_weights_bwd(dev(p.packed_info), dev(p.t_starts), dev(p.t_ends), dev(sg), M, dw, ds,
+                            g_ref=g_ref)
+    torch.cuda.synchronize()
+    g_full = dw_o + g_ref0[ray].astype(np.float64)
+    ds_o = orc.render_weights_bwd(p.packed_info, p.t_starts, p.t_ends, sg, g_full)
+    assert grad_rel_err(ds.cpu().numpy(), ds_o) <= 1e-4
+
+
 def test_unpack_info(scene, orc):
     p = scene["p"]
     ri = torch.full((p.n_samples,), -1, dtype=torch.int32, device="cuda")

@@ -63,6 +63,60 @@ def test_static_scratch_matches_workspace_entry_point_on_two_calls():
         _same(_host(ref), _host(got))
 
 
+def test_static_scratch_cone_steps_on_a_cascade_match_workspace_entry_point():
+    """Cone steps need the lattice table beside the look-back words; the fixed array
+    holds it for every max_steps a call accepts. Two calls in a row on the 4-level
+    unbounded cascade give exactly what the workspace entry point gives."""
+    for batch, R in ((0, 2000), (1, 3500)):
+        w = synth.unbounded_config(6, n_rays=R, batch=batch, device="cuda")
+        bits = torch.from_numpy(w.bits.view(np.int32)).cuda()
+        grid = _lib.make_grid(bits, w.res, w.aabb, w.n_levels)
+        params = _lib.make_params(w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone, w.max_steps)
+        o = torch.from_numpy(w.rays_o).cuda()
+        d = torch.from_numpy(w.rays_d).cuda()
+        cap = R * 512
+        ws = torch.zeros(_lib.march_workspace_size(R, params), dtype=torch.uint8, device="cuda")
+        ref = _outputs(R, cap)
+        _lib.march_rays(o, d, grid, params, *ref[:4], ref[4], ref[5], ws)
+        got = _outputs(R, cap)
+        _lib.march_rays_static(o, d, grid, params, *got[:4], got[4], got[5])
+        _same(_host(ref), _host(got))
+
+
+def test_static_scratch_accepts_the_largest_cone_call_and_rejects_one_ray_more():
+    """At the ray limit with cone steps and the largest max_steps the call is
+    accepted (counts only: capacity 0) and agrees with the workspace entry point;
+    one ray more is rejected before anything is enqueued."""
+    R = _lib.STATIC_MAX_RAYS
+    gen = torch.Generator("cuda").manual_seed(5)
+    o = (torch.rand((R, 3), device="cuda", generator=gen) - 0.5) * 2.0
+    d = torch.nn.functional.normalize(torch.randn((R, 3), device="cuda", generator=gen), dim=1)
+    bits = torch.full((32 ** 3 // 32,), 0x0F0F0F0F, dtype=torch.int32, device="cuda")
+    grid = _lib.make_grid(bits, (32, 32, 32), (-1.5, -1.5, -1.5, 1.5, 1.5, 1.5), 1)
+    params = _lib.make_params(0.01, 6.0, 1e-3, 0.05, 1.0 / 128.0, _lib.STATIC_MAX_STEPS)
+    empty_f = torch.empty(0, device="cuda")
+    empty_i = torch.empty(0, dtype=torch.int32, device="cuda")
+    res = []
+    for static in (False, True):
+        pi = torch.full((R, 2), -1, dtype=torch.int32, device="cuda")
+        n = torch.zeros(1, dtype=torch.int64, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        if static:
+            _lib.march_rays_static(o, d, grid, params, pi, empty_f, empty_f, empty_i, n, st)
+        else:
+            ws = torch.zeros(_lib.march_workspace_size(R, params), dtype=torch.uint8, device="cuda")
+            _lib.march_rays(o, d, grid, params, pi, empty_f, empty_f, empty_i, n, st, ws)
+        torch.cuda.synchronize()
+        res.append((pi.cpu().numpy(), int(n.item()), int(st.item())))
+    assert res[0][1] > 0 and res[0][1] == res[1][1]
+    assert res[0][2] == res[1][2] == _lib.STATUS_CAPACITY  # counted, nothing stored
+    assert np.array_equal(res[0][0], res[1][0])
+    lib = _lib.load()
+    rc = lib.nacc_march_rays_static(None, None, None, None, R + 1, grid, params, None, None, None, None, 0,
+                                    None, None, None)
+    assert rc == _lib.ERR_INVALID_ARG
+
+
 def test_static_scratch_rejects_too_many_rays():
     lib = _lib.load()
     g = _lib.Grid()
