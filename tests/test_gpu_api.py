@@ -158,11 +158,11 @@ def test_weights_and_accumulate_compose_to_render(orc):
     assert grad_rel_err(s4.grad.cpu().numpy(), g_first.cpu().numpy()) <= 1e-3
 
 
-def test_paper_listing_without_a_grid(orc):
-    """The paper's Sec. 3 listing calls ray_marching without an occupancy grid:
-    every lattice step between near_plane and far_plane is marched, then pruned
-    with the field's density, then rendered with gradients."""
-    from paper_2210_04847_gb300 import api as nerfacc
+def test_march_without_a_grid_then_render_with_gradients(orc):
+    """ray_marching accepts no occupancy grid (Sec. 3): every lattice step between
+    near_plane and far_plane is marched, pruned with the field's density queried
+    without gradients, and rendered with gradients reaching the field's weights."""
+    from paper_2210_04847_gb300 import api as nacc
 
     rng = np.random.default_rng(8)
     n = 300
@@ -171,23 +171,18 @@ def test_paper_listing_without_a_grid(orc):
     rays_d = torch.from_numpy((d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)).cuda()
     w_field = torch.tensor([[2.0, -1.0, 0.5], [0.3, 0.2, -0.4], [-0.6, 0.9, 0.1]], device="cuda", requires_grad=True)
 
-    def query(ts, te, ri):
+    def field(ts, te, ri):
         pos = rays_o[ri] + rays_d[ri] * (ts + te) / 2.0
-        sig = 30.0 * torch.exp(-4.0 * (pos * pos).sum(-1, keepdim=True))
-        return torch.sigmoid(pos @ w_field), sig
+        density = 30.0 * torch.exp(-4.0 * (pos * pos).sum(-1, keepdim=True))
+        return torch.sigmoid(pos @ w_field), density
 
-    def sigma_fn(ts, te, ri):
-        return query(ts, te, ri)[1]
-
-    def rgb_sigma_fn(ts, te, ri):
-        return query(ts, te, ri)
-
-    # the listing's call, verbatim
-    packed_info, t_starts, t_ends = nerfacc.ray_marching(
-        rays_o, rays_d, sigma_fn=sigma_fn, near_plane=0.2, far_plane=1.0,
-        early_stop_eps=1e-4, alpha_thre=1e-2,
-    )
-    color, opacity, depth = nerfacc.rendering(rgb_sigma_fn, packed_info, t_starts, t_ends)
+    # planes 0.2 .. 1.0 with the default 1e-2 step: 81 lattice steps per ray
+    # before pruning; eps and the opacity threshold at values that prune some
+    packed_info, t_starts, t_ends = nacc.ray_marching(rays_o, rays_d, sigma_fn=lambda *a: field(*a)[1],
+                                                      near_plane=0.2, far_plane=1.0, early_stop_eps=1e-3,
+                                                      alpha_thre=5e-3)
+    assert int(packed_info[:, 1].max()) <= 81
+    color, opacity, depth = nacc.rendering(field, packed_info, t_starts, t_ends)
     loss = torch.nn.functional.mse_loss(color, torch.full_like(color, 0.5))
     loss.backward()
     assert torch.isfinite(w_field.grad).all() and float(w_field.grad.abs().sum()) > 0
@@ -197,6 +192,6 @@ def test_paper_listing_without_a_grid(orc):
     near, dt = np.float32(0.2), np.float32(0.01)
     k_max = sum(1 for k in range(200) if near + np.float32(k) * dt < np.float32(1.0))  # float32 lattice: 81
     assert np.all(m.packed_info[:, 1] == k_max)
-    packed, ts, te, ri = nerfacc.march_rays(rays_o, rays_d, near_plane=0.2, far_plane=1.0)
+    packed, ts, te, ri = nacc.march_rays(rays_o, rays_d, near_plane=0.2, far_plane=1.0)
     assert np.array_equal(packed.cpu().numpy(), m.packed_info) and bits_equal(ts.cpu().numpy(), m.t_starts)
     assert float(opacity.detach().max()) > 0.5 and float(opacity.detach().min()) >= 0.0
