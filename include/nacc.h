@@ -396,16 +396,28 @@ int nacc_unpack_info(const int32_t* packed_info, int32_t n_rays, int64_t n_sampl
  * the cells (uniform random cells in Instant-NGP's scheme) and evaluates its
  * field at points inside them. Float32 state, one rounding per product:
  * bit-exact and independent of sample order.
- * The paper's criterion, empty where the opacity of a step is below a threshold
- * (Sec. 2.1), is this test with thre = -ln(1 - alpha_thre) / dt: for dt > 0,
- * 1 - exp(-ema dt) > alpha_thre exactly when ema > -ln(1 - alpha_thre) / dt.
+ * alpha_step = 0: thre is a density threshold (bits = ema > thre).
+ * alpha_step > 0: the paper's criterion (Sec. 2.1), a cell is empty where the
+ * opacity of a step of length alpha_step is below thre (0 <= thre < 1): bit =
+ * 1 - exp(-ema alpha_step) > thre, applied as its equivalent density threshold
+ * nacc_density_threshold(thre, alpha_step). Negative or NaN alpha_step, or thre
+ * outside [0, 1) with alpha_step > 0: NACC_ERR_INVALID_ARG.
  * ema (n_cells,) float32 in/out, values >= 0; bits ceil(n_cells/32) uint32 out;
  * cells (n_samples,) int32 in [0, n_cells) (others raise NACC_STATUS_BAD_INDEX
  * and are skipped); sigmas (n_samples,) float32.
  */
 int nacc_update_occupancy_grid(float* ema, uint32_t* bits, int64_t n_cells, const int32_t* cells,
                                const float* sigmas, int64_t n_samples, float decay, float thre,
-                               int32_t* d_status, void* stream);
+                               float alpha_step, int32_t* d_status, void* stream);
+
+/*
+ * Density threshold of the opacity criterion (host only, no device work): for
+ * steps of length dt > 0, 1 - exp(-sigma dt) > alpha_thre exactly when
+ * sigma > -ln(1 - alpha_thre) / dt; returned computed in double and rounded once
+ * to float32 (the precision of the grid's comparison). NaN unless
+ * 0 <= alpha_thre < 1 and 0 < dt < inf.
+ */
+float nacc_density_threshold(float alpha_thre, float dt);
 
 /*
  * The update's random inputs (Instant-NGP's scheme that Sec. 2.1 follows):

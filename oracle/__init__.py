@@ -228,14 +228,23 @@ def unpack_info(packed_info, n_samples):
     return ri
 
 
-def update_grid(ema, cells, sigmas, decay, thre):
-    """Occupancy-grid EMA update (Sec. 2.1, via Instant-NGP App. E.2): returns (ema', bits')."""
+def update_grid(ema, cells, sigmas, decay, thre, alpha_step=None):
+    """Occupancy-grid EMA update (Sec. 2.1, via Instant-NGP App. E.2): returns (ema', bits').
+    With ``alpha_step`` = dt the bits follow the paper's opacity criterion itself: a
+    cell is occupied where 1 - exp(-ema dt) > thre, evaluated in float64 on the
+    float32 state (the density threshold of the library's form is not used)."""
     e = np.array(ema, dtype=np.float32, copy=True).reshape(-1)
     c = _c(cells, np.int32).reshape(-1)
     s = _c(sigmas, np.float32).reshape(-1)
     bits = np.zeros((e.size + 31) // 32, np.uint32)
-    if lib().oracle_update_grid(_p(e), _p(bits), e.size, _p(c), _p(s), c.size, decay, thre) != 0:
+    if lib().oracle_update_grid(_p(e), _p(bits), e.size, _p(c), _p(s), c.size, decay,
+                                thre if alpha_step is None else np.inf) != 0:
         raise ValueError("cell index out of range")
+    if alpha_step is not None:
+        occ = (1.0 - np.exp(-e.astype(np.float64) * float(alpha_step))) > float(thre)
+        pad = np.zeros(bits.size * 32, bool)
+        pad[:e.size] = occ
+        bits = (pad.reshape(-1, 32).astype(np.uint64) << np.arange(32, dtype=np.uint64)).sum(1).astype(np.uint32)
     return e, bits
 
 

@@ -37,7 +37,7 @@ EXPORTS = (
     "nacc_prune_samples", "nacc_march_fused", "nacc_density_field_at_samples", "nacc_density_field_query",
     "nacc_render_weights", "nacc_accumulate_along_rays", "nacc_render_weights_bwd",
     "nacc_accumulate_along_rays_bwd", "nacc_render_fwd", "nacc_render_bwd",
-    "nacc_unpack_info", "nacc_update_occupancy_grid", "nacc_sample_grid_cells", "nacc_tune_set", "nacc_tune_get",
+    "nacc_unpack_info", "nacc_update_occupancy_grid", "nacc_density_threshold", "nacc_sample_grid_cells", "nacc_tune_set", "nacc_tune_get",
     "nacc_test_hook_set", "nacc_test_hook_get", "nacc_error_string",
     "nacc_version",
 )
@@ -116,7 +116,8 @@ def load() -> ctypes.CDLL:
         "nacc_render_fwd": (ctypes.c_int, [P, i32, P, P, P, P, i64, P, P, P, P, P, P]),
         "nacc_render_bwd": (ctypes.c_int, [P, i32, P, P, P, P, P, i64, P, P, P, P, P, P, P]),
         "nacc_unpack_info": (ctypes.c_int, [P, i32, i64, P, P, P]),
-        "nacc_update_occupancy_grid": (ctypes.c_int, [P, P, i64, P, P, i64, f32, f32, P, P]),
+        "nacc_update_occupancy_grid": (ctypes.c_int, [P, P, i64, P, P, i64, f32, f32, f32, P, P]),
+        "nacc_density_threshold": (ctypes.c_float, [f32, f32]),
         "nacc_sample_grid_cells": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, i64, GP, P, P, P]),
         "nacc_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
         "nacc_tune_get": (ctypes.c_int, [ctypes.c_int]),
@@ -477,7 +478,9 @@ def unpack_info(packed_info, n_samples: int, ray_indices, d_status=None, stream=
     _rc(rc, "nacc_unpack_info")
 
 
-def update_occupancy_grid(ema, bits, cells, sigmas, decay, thre, d_status=None, stream=None, defer: bool = False):
+def update_occupancy_grid(ema, bits, cells, sigmas, decay, thre, d_status=None, alpha_step: float = 0.0, stream=None,
+                          defer: bool = False):
+    """EMA update; alpha_step > 0 makes thre the opacity threshold of a step of that length."""
     n_cells = ema.numel()
     _check(ema, torch.float32, "ema")
     _check(bits, torch.int32, "bits", (n_cells + 31) // 32)
@@ -486,7 +489,14 @@ def update_occupancy_grid(ema, bits, cells, sigmas, decay, thre, d_status=None, 
     _check(sigmas, torch.float32, "sigmas", n)
     _check(d_status, torch.int32, "d_status", 1, optional=True)
     return _call("nacc_update_occupancy_grid", (_ptr(ema), _ptr(bits), n_cells, _ptr(cells), _ptr(sigmas), n,
-                                                float(decay), float(thre), _ptr(d_status), _stream(stream)), defer)
+                                                float(decay), float(thre), float(alpha_step), _ptr(d_status),
+                                                _stream(stream)), defer)
+
+
+def density_threshold(alpha_thre: float, dt: float) -> float:
+    """nacc_density_threshold: the density threshold equivalent to an opacity threshold
+    for steps of length dt (NaN for invalid arguments). Host only."""
+    return float(load().nacc_density_threshold(float(alpha_thre), float(dt)))
 
 
 def sample_grid_cells(seed: int, stream: int, n: int, grid: Grid, cells, xyz, cuda_stream=None, defer: bool = False):

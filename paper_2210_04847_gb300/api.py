@@ -18,22 +18,12 @@ outputs. Capacity-based calls without that synchronisation are available in
 """
 from __future__ import annotations
 
-import math
 from typing import Callable, Optional, Sequence
 
 import numpy as np
 import torch
 
 from . import _lib
-
-
-def alpha_to_density_threshold(alpha_thre: float, dt: float) -> float:
-    """Density threshold equivalent to an opacity threshold for steps of length dt:
-    1 - exp(-sigma dt) > alpha_thre  <=>  sigma > -ln(1 - alpha_thre) / dt, computed in
-    float64 and rounded once to float32 (the precision of the grid's comparison)."""
-    if not (0.0 <= alpha_thre < 1.0) or not (dt > 0.0):
-        raise ValueError("need 0 <= alpha_thre < 1 and dt > 0")
-    return float(np.float32(-math.log1p(-alpha_thre) / dt))
 
 
 class OccupancyGrid:
@@ -87,10 +77,9 @@ class OccupancyGrid:
         """EMA update: ema = max(decay * ema, sigma at sampled cells); bits = ema > thre.
         With ``alpha_step`` = dt the criterion is the opacity of a step of that
         length, 1 - exp(-ema dt) > thre (the paper's "empty where alpha < 1e-2",
-        Sec. 2.1), applied as the equivalent density threshold."""
-        if alpha_step is not None:
-            thre = alpha_to_density_threshold(thre, alpha_step)
-        _lib.update_occupancy_grid(self.ema, self.bits, cells, sigmas, decay, thre, self.status)
+        Sec. 2.1), applied by the library as the equivalent density threshold."""
+        _lib.update_occupancy_grid(self.ema, self.bits, cells, sigmas, decay, thre, self.status,
+                                   alpha_step=0.0 if alpha_step is None else float(alpha_step))
 
     def state_dict(self):
         return {"ema": self.ema.clone(), "bits": self.bits.clone(), "res": self.res, "aabb": self.aabb,

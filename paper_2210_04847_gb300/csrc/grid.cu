@@ -234,13 +234,25 @@ extern "C" int nacc_sample_grid_cells(uint64_t seed, uint64_t stream, int64_t n,
     return launch_status(cudaGetLastError());
 }
 
+extern "C" float nacc_density_threshold(float alpha_thre, float dt) {
+    // 1 - exp(-sigma dt) > alpha  <=>  sigma > -ln(1 - alpha) / dt  (dt > 0), in
+    // double, rounded once to the float32 of the grid's comparison
+    if (!(alpha_thre >= 0.0f && alpha_thre < 1.0f) || !(dt > 0.0f) || !(dt < INFINITY)) return NAN;
+    return (float)(-log1p(-(double)alpha_thre) / (double)dt);
+}
+
 extern "C" int nacc_update_occupancy_grid(float* ema, uint32_t* bits, int64_t n_cells, const int32_t* cells,
                                           const float* sigmas, int64_t n_samples, float decay, float thre,
-                                          int32_t* d_status, void* stream) {
+                                          float alpha_step, int32_t* d_status, void* stream) {
     if (n_cells < 0 || n_samples < 0 || n_cells >= (1LL << 31)) return NACC_ERR_INVALID_ARG;
     if (n_cells > 0 && (!ema || !bits)) return NACC_ERR_INVALID_ARG;
     if (n_samples > 0 && (!cells || !sigmas)) return NACC_ERR_INVALID_ARG;
-    if (decay != decay || thre != thre) return NACC_ERR_INVALID_ARG;
+    if (decay != decay || thre != thre || alpha_step != alpha_step || alpha_step < 0.0f) return NACC_ERR_INVALID_ARG;
+    if (alpha_step > 0.0f) {  // thre is the opacity threshold of a step of length alpha_step
+        thre = nacc_density_threshold(thre, alpha_step);
+        if (thre != thre) return NACC_ERR_INVALID_ARG;
+    }
+    if (n_cells == 0 && n_samples == 0) return NACC_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const DeviceInfo dev = current_device();
     if (n_cells > 0) {

@@ -77,9 +77,9 @@ def test_invalid_arguments_rejected_on_host(libs):
     assert lib.nacc_render_bwd(None, -2, None, None, None, None, None, 0, None, None, None, None, None, None,
                                None) == _lib.ERR_INVALID_ARG
     assert lib.nacc_accumulate_along_rays(None, 1, None, None, 0, 0, None, None, None) == _lib.ERR_INVALID_ARG
-    assert lib.nacc_update_occupancy_grid(None, None, -1, None, None, 0, 0.9, 0.1, None, None) == \
+    assert lib.nacc_update_occupancy_grid(None, None, -1, None, None, 0, 0.9, 0.1, 0.0, None, None) == \
         _lib.ERR_INVALID_ARG
-    assert lib.nacc_update_occupancy_grid(None, None, 10, None, None, 0, 0.9, 0.1, None, None) == \
+    assert lib.nacc_update_occupancy_grid(None, None, 10, None, None, 0, 0.9, 0.1, 0.0, None, None) == \
         _lib.ERR_INVALID_ARG
 
 

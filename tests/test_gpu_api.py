@@ -85,8 +85,14 @@ def test_api_grid_update_and_weights(orc):
     ga = api.OccupancyGrid((-1, -1, -1, 1, 1, 1), 32)
     ga.ema.copy_(torch.from_numpy(ema0))
     ga.update(torch.from_numpy(cells).cuda(), torch.from_numpy(sig).cuda(), 0.9, 0.01, alpha_step=0.5)
-    e_a, b_a = orc.update_grid(ema0, cells, sig, 0.9, api.alpha_to_density_threshold(0.01, 0.5))
-    assert bits_equal(ga.ema.cpu().numpy(), e_a) and np.array_equal(ga.bits.cpu().numpy().view(np.uint32), b_a)
+    e_a, b_a = orc.update_grid(ema0, cells, sig, 0.9, 0.01, alpha_step=0.5)
+    assert bits_equal(ga.ema.cpu().numpy(), e_a)
+    # the oracle decides with the opacity criterion in float64; the library with its
+    # float32 density threshold: they may differ only within rounding of the threshold
+    got = np.unpackbits(ga.bits.cpu().numpy().view(np.uint32).view(np.uint8), bitorder="little")[:32 ** 3]
+    ref = np.unpackbits(b_a.view(np.uint8), bitorder="little")[:32 ** 3]
+    near = np.abs(e_a.astype(np.float64) - (-np.log1p(-0.01) / 0.5)) <= 1e-6 * 0.0201
+    assert np.array_equal(got[~near], ref[~near]) and near.sum() <= 2
     assert not np.array_equal(b_a, b_o)  # a different threshold (0.0201 against 0.01)
     sd = g.state_dict()
     g2 = api.OccupancyGrid((-1, -1, -1, 1, 1, 1), 32)

@@ -341,3 +341,20 @@ def test_grid_scatter_max_and_threshold(orc):
     ema[[0, 31, 32, 63, 64, 69]] = [1, 0.02, 0.01, 0.011, 5, 0.0099]
     _, bits = orc.update_grid(ema, np.zeros(0, np.int32), np.zeros(0, np.float32), 1.0, 0.01)
     assert bits.tolist() == [(1 << 0) | (1 << 31), 1 << 31, 1 << 0]
+
+
+def test_grid_opacity_criterion(orc):
+    """alpha mode: occupied where a step of length dt would be at least that opaque.
+    Dyadic densities on either side of -ln(1 - 0.5)/dt = ln 2/dt (dt = 1/4: 2.7726),
+    including 0 (never occupied with alpha >= 0) and a decay that moves one across."""
+    ema = np.array([0.0, 2.5, 2.75, 2.78125, 3.0, 100.0, 5.5, 5.5625], np.float32)
+    _, bits = orc.update_grid(ema, np.zeros(0, np.int32), np.zeros(0, np.float32), 1.0, 0.5, alpha_step=0.25)
+    assert np.nonzero(synth.unpack_bits(bits, 8))[0].tolist() == [3, 4, 5, 6, 7]
+    e2, bits = orc.update_grid(ema, np.zeros(0, np.int32), np.zeros(0, np.float32), 0.5, 0.5, alpha_step=0.25)
+    assert np.nonzero(synth.unpack_bits(bits, 8))[0].tolist() == [5, 7]  # 5.5625 -> 2.78125 stays, 5.5 -> 2.75 not
+    # away from the threshold the criterion and its density form agree
+    ema = synth.rand_uniform(4, 9, 5000, 0, 0.05).astype(np.float32)
+    _, b_alpha = orc.update_grid(ema, np.zeros(0, np.int32), np.zeros(0, np.float32), 1.0, 0.01, alpha_step=0.5)
+    _, b_dens = orc.update_grid(ema, np.zeros(0, np.int32), np.zeros(0, np.float32), 1.0,
+                                float(np.float32(-np.log1p(-0.01) / 0.5)))
+    assert np.array_equal(b_alpha, b_dens)
