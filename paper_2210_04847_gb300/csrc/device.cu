@@ -55,7 +55,7 @@ const int g_hook_hi[NACC_TEST_HOOK_COUNT] = {kSpinLimit, 1};
 }  // namespace
 
 LookbackHooks lookback_hooks() {
-    return LookbackHooks{g_hook[NACC_TEST_HOOK_SPIN_LIMIT], g_hook[NACC_TEST_HOOK_WITHHOLD_FIRST_TILE]};
+    return LookbackHooks{g_hook[NACC_TEST_HOOK_WITHHOLD_FIRST_TILE] ? 0ull : kFlagInc, g_hook[NACC_TEST_HOOK_SPIN_LIMIT]};
 }
 
 }  // namespace nacc

@@ -91,8 +91,8 @@ constexpr unsigned long long kValMask = (1ull << 62) - 1;
 constexpr int kSpinLimit = 1 << 22;
 
 struct LookbackHooks {
-    int spin_limit;      // polls before a wait gives up (default kSpinLimit)
-    int withhold_first;  // 1: tile 0's prefix is never published (test only)
+    unsigned long long first_flag;  // flag tile 0 publishes: kFlagInc, or 0 ("pending") to withhold it (test only)
+    int spin_limit;                 // polls before a wait gives up (default kSpinLimit)
 };
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
@@ -109,8 +109,9 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
 __device__ __forceinline__ void publish_aggregate(unsigned long long* status, int tile,
                                                   unsigned long long aggregate, int lane,
                                                   const LookbackHooks& hooks) {
-    if (lane == 0 && !(tile == 0 && hooks.withhold_first))
-        st_relaxed_u64(&status[tile], (tile == 0 ? kFlagInc : kFlagAgg) | (aggregate & kValMask));
+    // (a branch around the store instead of the flag value costs the pruning
+    // kernel hundreds of bytes of register spills under its 6-blocks cap)
+    if (lane == 0) st_relaxed_u64(&status[tile], (tile == 0 ? hooks.first_flag : kFlagAgg) | (aggregate & kValMask));
 }
 
 // Called by one full warp after publish_aggregate(tile). Returns the exclusive
