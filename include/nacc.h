@@ -148,6 +148,48 @@ int nacc_march_rays(const float* rays_o, const float* rays_d, const float* ray_t
                     int32_t* d_status, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * One scene of a batch whose scenes each have their own occupancy grid
+ * (Sec. 2.1: the grid is kept per scene). Same meaning as nacc_grid with one
+ * slot: bits (device) holds the scene's levels from word 0, res, n_levels, aabb
+ * and contraction as there. n_rays: the scene's rays, which are consecutive in
+ * the batch, scenes in array order.
+ */
+typedef struct nacc_scene_desc {
+    const uint32_t* bits;
+    int32_t res[3];
+    int32_t n_levels;
+    float aabb[6];
+    int32_t contraction; /* the same for every scene of a call */
+    int32_t n_rays;
+} nacc_scene_desc;
+
+/* Bytes of device workspace nacc_march_rays_batched needs. */
+size_t nacc_march_batched_workspace_size(int32_t n_scenes, int32_t n_rays, const nacc_march_params* params);
+
+/*
+ * nacc_march_rays over a batch of scenes with per-scene grids, in one
+ * persistent launch: ray r of scene s (rays of scene s are the n_rays of
+ * scenes[s] that follow those of scenes 0..s-1) is clipped against scene s's
+ * outermost box and looked up in scene s's grid; everything else (step rule,
+ * outputs, capacity, status, bit-exact float32 arithmetic) is as in
+ * nacc_march_rays. The output is packed ray-major over the whole batch, so it is
+ * also scene-major; ray_indices are indices into the batch.
+ * scenes           host array of n_scenes >= 1 descriptors (read during the
+ *                  call only; the library copies their geometry into the
+ *                  workspace with a kernel launch on `stream`, so the call can be
+ *                  captured in a CUDA graph).
+ * workspace        nacc_march_batched_workspace_size() bytes, 256-byte aligned.
+ * Errors: those of nacc_march_rays; NACC_ERR_INVALID_ARG for an invalid scene
+ * grid, negative or inconsistent ray counts (their sum must be n_rays), or
+ * scenes that differ in contraction.
+ */
+int nacc_march_rays_batched(const nacc_scene_desc* scenes, int32_t n_scenes, const float* rays_o,
+                            const float* rays_d, int32_t n_rays, const nacc_march_params* params,
+                            int32_t* packed_info, float* t_starts, float* t_ends, int32_t* ray_indices,
+                            int64_t capacity, int64_t* n_samples, int32_t* d_status, void* workspace,
+                            size_t workspace_bytes, void* stream);
+
+/*
  * Ray marching without any device allocation by the caller. The paper has no
  * counterpart: this is an integration aid for callers that cannot allocate
  * device memory at call time (a renderer with a fixed, pre-planned memory

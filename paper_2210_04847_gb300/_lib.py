@@ -33,7 +33,8 @@ STATUS_OVERFLOW = 0x10
 MAX_LEVELS = 16
 
 EXPORTS = (
-    "nacc_march_workspace_size", "nacc_march_rays", "nacc_march_rays_static", "nacc_prune_workspace_size",
+    "nacc_march_workspace_size", "nacc_march_rays", "nacc_march_rays_static", "nacc_march_batched_workspace_size",
+    "nacc_march_rays_batched", "nacc_prune_workspace_size",
     "nacc_prune_samples", "nacc_march_fused", "nacc_density_field_at_samples", "nacc_density_field_query",
     "nacc_render_weights", "nacc_accumulate_along_rays", "nacc_render_weights_bwd",
     "nacc_accumulate_along_rays_bwd", "nacc_render_fwd", "nacc_render_bwd",
@@ -63,6 +64,18 @@ class Grid(ctypes.Structure):
         ("n_slots", ctypes.c_int32),
         ("aabb", ctypes.c_float * 6),
         ("contraction", ctypes.c_int32),
+    ]
+
+
+class SceneDesc(ctypes.Structure):
+    """nacc_scene_desc: one scene of a batch with its own grid."""
+    _fields_ = [
+        ("bits", ctypes.c_void_p),
+        ("res", ctypes.c_int32 * 3),
+        ("n_levels", ctypes.c_int32),
+        ("aabb", ctypes.c_float * 6),
+        ("contraction", ctypes.c_int32),
+        ("n_rays", ctypes.c_int32),
     ]
 
 
@@ -104,6 +117,9 @@ def load() -> ctypes.CDLL:
         "nacc_march_workspace_size": (sz, [i32, MP]),
         "nacc_march_rays": (ctypes.c_int, [P, P, P, P, i32, GP, MP, P, P, P, P, i64, P, P, P, sz, P]),
         "nacc_march_rays_static": (ctypes.c_int, [P, P, P, P, i32, GP, MP, P, P, P, P, i64, P, P, P]),
+        "nacc_march_batched_workspace_size": (sz, [i32, i32, MP]),
+        "nacc_march_rays_batched": (ctypes.c_int, [ctypes.POINTER(SceneDesc), i32, P, P, i32, MP, P, P, P, P, i64, P,
+                                                   P, P, sz, P]),
         "nacc_prune_workspace_size": (sz, [i32, i64]),
         "nacc_prune_samples": (ctypes.c_int, [P, i32, P, P, P, i64, f32, f32, P, P, P, P, i64, P, P, P, P, sz, P]),
         "nacc_march_fused": (ctypes.c_int, [P, P, i32, GP, MP, FP, f32, f32, P, P, P, P, P, i64, P, P, P, sz, P]),
@@ -217,6 +233,27 @@ def make_grid(bits: torch.Tensor, res: Sequence[int], aabb: Sequence[float], n_l
     return g
 
 
+def make_scenes(scenes) -> ctypes.Array:
+    """Array of nacc_scene_desc from (bits tensor, res, aabb, n_levels, contraction, n_rays)
+    tuples; the array keeps the bits tensors alive."""
+    arr = (SceneDesc * len(scenes))()
+    keep = []
+    for k, (bits, res, aabb, n_levels, contraction, n_rays) in enumerate(scenes):
+        _check(bits, torch.int32, "scene bits")
+        d = arr[k]
+        d.bits = bits.data_ptr()
+        keep.append(bits)
+        for j in range(3):
+            d.res[j] = int(res[j])
+        d.n_levels = int(n_levels)
+        for j in range(6):
+            d.aabb[j] = float(aabb[j])
+        d.contraction = int(contraction)
+        d.n_rays = int(n_rays)
+    arr._keepalive = keep
+    return arr
+
+
 def make_density_field(sigma: torch.Tensor, aabb: Sequence[float]) -> DensityField:
     """nacc_density_field over a (G0, G1, G2) float32 CUDA tensor of vertex values."""
     _check(sigma, torch.float32, "density field")
@@ -275,6 +312,31 @@ def march_rays(rays_o, rays_d, grid: Grid, params: MarchParams, packed_info, t_s
             _ptr(packed_info), _ptr(t_starts), _ptr(t_ends), _ptr(ray_indices), cap, _ptr(n_samples),
             _ptr(d_status), _ptr(workspace), workspace.numel(), _stream(stream))
     return _call("nacc_march_rays", args, defer)
+
+
+def march_batched_workspace_size(n_scenes: int, n_rays: int, params: MarchParams) -> int:
+    return int(load().nacc_march_batched_workspace_size(int(n_scenes), int(n_rays), ctypes.byref(params)))
+
+
+def march_rays_batched(scenes, rays_o, rays_d, params: MarchParams, packed_info, t_starts, t_ends, ray_indices,
+                       n_samples, d_status, workspace, stream=None, defer: bool = False):
+    """nacc_march_rays_batched: one launch over scenes with their own grids
+    (``scenes`` from ``make_scenes``; rays scene-major)."""
+    n = rays_o.shape[0]
+    _check(rays_o, torch.float32, "rays_o", 3 * n)
+    _check(rays_d, torch.float32, "rays_d", 3 * n)
+    _check(packed_info, torch.int32, "packed_info", 2 * n)
+    cap = t_starts.numel()
+    _check(t_starts, torch.float32, "t_starts")
+    _check(t_ends, torch.float32, "t_ends", cap)
+    _check(ray_indices, torch.int32, "ray_indices", cap)
+    _check(n_samples, torch.int64, "n_samples", 1)
+    _check(d_status, torch.int32, "d_status", 1, optional=True)
+    _check(workspace, torch.uint8, "workspace")
+    args = (scenes, len(scenes), _ptr(rays_o), _ptr(rays_d), n, ctypes.byref(params), _ptr(packed_info),
+            _ptr(t_starts), _ptr(t_ends), _ptr(ray_indices), cap, _ptr(n_samples), _ptr(d_status), _ptr(workspace),
+            workspace.numel(), _stream(stream))
+    return _call("nacc_march_rays_batched", args, defer)
 
 
 STATIC_MAX_RAYS = 1 << 20

@@ -41,24 +41,25 @@ namespace {
 // works on another point: the bitfield word that holds x's cell (0 when x is
 // outside the grid) and the cell's index. Bit (cell & 31) of the word is the
 // occupancy bit of x.
-__device__ __forceinline__ unsigned level0_word(const MarchArgs& a, float x0, float x1, float x2,
-                                                unsigned slot_level0, unsigned& cell) {
-    const int i0 = __float2int_rd(__fmul_rn(__fsub_rn(x0, a.L.lo[0][0]), a.L.scale[0][0]));
-    const int i1 = __float2int_rd(__fmul_rn(__fsub_rn(x1, a.L.lo[0][1]), a.L.scale[0][1]));
-    const int i2 = __float2int_rd(__fmul_rn(__fsub_rn(x2, a.L.lo[0][2]), a.L.scale[0][2]));
-    cell = ((slot_level0 * a.res0 + i0) * a.res1 + i1) * a.res2 + i2;
+template <typename G>
+__device__ __forceinline__ unsigned level0_word(const G& g, float x0, float x1, float x2, unsigned slot_level0,
+                                                unsigned& cell) {
+    const int i0 = __float2int_rd(__fmul_rn(__fsub_rn(x0, g.lo(0, 0)), g.scale(0, 0)));
+    const int i1 = __float2int_rd(__fmul_rn(__fsub_rn(x1, g.lo(0, 1)), g.scale(0, 1)));
+    const int i2 = __float2int_rd(__fmul_rn(__fsub_rn(x2, g.lo(0, 2)), g.scale(0, 2)));
+    cell = ((slot_level0 * g.res0() + i0) * g.res1() + i1) * g.res2() + i2;
     const bool in =
-        (unsigned)i0 < (unsigned)a.res0 && (unsigned)i1 < (unsigned)a.res1 && (unsigned)i2 < (unsigned)a.res2;
-    return in ? __ldg(a.bits + (cell >> 5)) : 0u;
+        (unsigned)i0 < (unsigned)g.res0() && (unsigned)i1 < (unsigned)g.res1() && (unsigned)i2 < (unsigned)g.res2();
+    return in ? __ldg(g.bits() + (cell >> 5)) : 0u;
 }
 
 // One ray, all 32 lanes: one ballot word per 32 lattice points into row[c].
 // count = samples, nch = ballot words written (row[0..nch)).
 // COARSE (shared lattices): first one point every 32 per lane, and chunks that
 // lie in a single cell take their word from one occupancy test (see below).
-template <int MAXL, bool CONE, bool UNROLL2, bool COARSE = false>
-__device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3], const float d[3], float near,
-                                             float far, unsigned sl0, uint32_t* row, float* lat, int lane,
+template <int MAXL, bool CONE, bool UNROLL2, bool COARSE, typename G>
+__device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, const float o[3], const float d[3],
+                                             float near, float far, unsigned sl0, uint32_t* row, float* lat, int lane,
                                              int& count_out, int& nch_out, int& pts_out) {
     const float dt = a.dt_min;
     const bool shared = !CONE || near == a.near_plane;
@@ -83,8 +84,8 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
         // ballot word follows from one occupancy test. The other chunks are tested
         // point by point. Groups of 31 chunks.
         int part = 0;  // samples of this lane's single-cell chunks
-        for (int g = 0; g < max_ch; g += 31) {
-            const int kp = min((g + lane) << 5, nk - 1);
+        for (int grp = 0; grp < max_ch; grp += 31) {
+            const int kp = min((grp + lane) << 5, nk - 1);
             float ts, tn;
             if (!CONE) {
                 const float kf = __int2float_rn(kp);
@@ -102,20 +103,20 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
             bool same = true;
 #pragma unroll
             for (int l = 0; l < MAXL; ++l) {
-                if (l >= a.n_levels) break;
-                const int i0 = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x0, a.L.lo[l][0]), a.L.scale[l][0])), -1),
-                                   a.res0);
-                const int i1 = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x1, a.L.lo[l][1]), a.L.scale[l][1])), -1),
-                                   a.res1);
-                const int i2 = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x2, a.L.lo[l][2]), a.L.scale[l][2])), -1),
-                                   a.res2);
+                if (l >= g.n_levels()) break;
+                const int i0 = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x0, g.lo(l, 0)), g.scale(l, 0))), -1),
+                                   g.res0());
+                const int i1 = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x1, g.lo(l, 1)), g.scale(l, 1))), -1),
+                                   g.res1());
+                const int i2 = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x2, g.lo(l, 2)), g.scale(l, 2))), -1),
+                                   g.res2());
                 const int n0 = __shfl_down_sync(FULL, i0, 1);
                 const int n1 = __shfl_down_sync(FULL, i1, 1);
                 const int n2 = __shfl_down_sync(FULL, i2, 1);
                 same = same && i0 == n0 && i1 == n1 && i2 == n2;
             }
-            const bool occ_p = occupied<MAXL>(a, x0, x1, x2, sl0);
-            const int c = g + lane;
+            const bool occ_p = occupied_in<MAXL>(g, x0, x1, x2, sl0);
+            const int c = grp + lane;
             const bool exists = lane < 31 && c < max_ch;
             const bool uni = exists && same;
             if (uni) {
@@ -126,7 +127,7 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
             }
             unsigned pend = __ballot_sync(FULL, exists && !uni);
             while (pend) {
-                const int cc = g + __ffs(pend) - 1;
+                const int cc = grp + __ffs(pend) - 1;
                 pend &= pend - 1;
                 const int k = (cc << 5) + lane;
                 float ks, kn;
@@ -142,7 +143,7 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
                 if (k < nk && ks < far) {
                     const float ke = kn < far ? kn : far;
                     const float km = __fmul_rn(__fadd_rn(ks, ke), 0.5f);
-                    occ = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], km)), __fadd_rn(o[1], __fmul_rn(d[1], km)),
+                    occ = occupied_in<MAXL>(g, __fadd_rn(o[0], __fmul_rn(d[0], km)), __fadd_rn(o[1], __fmul_rn(d[1], km)),
                                          __fadd_rn(o[2], __fmul_rn(d[2], km)), sl0);
                 }
                 const unsigned m = __ballot_sync(FULL, occ);
@@ -163,7 +164,7 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
                 const float tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf0, 1.0f), dt));
                 const float te = tn < far ? tn : far;
                 const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
-                occ0 = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)), __fadd_rn(o[1], __fmul_rn(d[1], mid)),
+                occ0 = occupied_in<MAXL>(g, __fadd_rn(o[0], __fmul_rn(d[0], mid)), __fadd_rn(o[1], __fmul_rn(d[1], mid)),
                                       __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0);
             }
             if (k1 < nk) {
@@ -171,7 +172,7 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
                 const float tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf1, 1.0f), dt));
                 const float te = tn < far ? tn : far;
                 const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
-                occ1 = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)), __fadd_rn(o[1], __fmul_rn(d[1], mid)),
+                occ1 = occupied_in<MAXL>(g, __fadd_rn(o[0], __fmul_rn(d[0], mid)), __fadd_rn(o[1], __fmul_rn(d[1], mid)),
                                       __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0);
             }
             const unsigned m0 = __ballot_sync(FULL, occ0);
@@ -200,7 +201,7 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
                 const float tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
                 const float te = tn < far ? tn : far;
                 const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
-                return level0_word(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)), __fadd_rn(o[1], __fmul_rn(d[1], mid)),
+                return level0_word(g, __fadd_rn(o[0], __fmul_rn(d[0], mid)), __fadd_rn(o[1], __fmul_rn(d[1], mid)),
                                    __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0, cell);
             };
             if (nfull > 0) {
@@ -229,7 +230,7 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
                 }
                 const float te = tn < far ? tn : far;
                 const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
-                const bool occ = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)),
+                const bool occ = occupied_in<MAXL>(g, __fadd_rn(o[0], __fmul_rn(d[0], mid)),
                                                 __fadd_rn(o[1], __fmul_rn(d[1], mid)),
                                                 __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0);
                 const unsigned m = __ballot_sync(FULL, occ);
@@ -251,7 +252,7 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
             if (k < nk && ts < far) {
                 const float te = tn < far ? tn : far;
                 const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
-                occ = occupied<MAXL>(a, __fadd_rn(o[0], __fmul_rn(d[0], mid)), __fadd_rn(o[1], __fmul_rn(d[1], mid)),
+                occ = occupied_in<MAXL>(g, __fadd_rn(o[0], __fmul_rn(d[0], mid)), __fadd_rn(o[1], __fmul_rn(d[1], mid)),
                                      __fadd_rn(o[2], __fmul_rn(d[2], mid)), sl0);
             }
             const unsigned m = __ballot_sync(FULL, occ);
@@ -291,7 +292,7 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const float o[3
                 const float x0 = __fadd_rn(o[0], __fmul_rn(d[0], mid));
                 const float x1 = __fadd_rn(o[1], __fmul_rn(d[1], mid));
                 const float x2 = __fadd_rn(o[2], __fmul_rn(d[2], mid));
-                occ = occupied<MAXL>(a, x0, x1, x2, sl0);
+                occ = occupied_in<MAXL>(g, x0, x1, x2, sl0);
             }
             const unsigned m = __ballot_sync(FULL, occ);
             if (lane == 0) row[c] = m;
@@ -396,19 +397,45 @@ __device__ __forceinline__ void finish_tile(const MarchArgs& a, const uint32_t* 
 // kernels
 // ---------------------------------------------------------------------------
 
+// Batch of scenes with their own grids: the scene of ray r, the first whose
+// consecutive rays end after r, found by the whole warp 32 scenes at a time
+// starting from `from` (a scene that starts at or before r: the warp's rays only
+// grow).
+__device__ __forceinline__ int scene_of(const MarchArgs& a, int r, int from, int lane) {
+    for (int base = from; base < a.n_scenes; base += 32) {
+        const int s = base + lane;
+        const unsigned past = __ballot_sync(FULL, s < a.n_scenes && __ldg(a.scene_end + s) > r);
+        if (past) return base + __ffs(past) - 1;
+    }
+    return a.n_scenes - 1;  // not reached: the last scene's rays end at n_rays
+}
+
+// The warp's copy of a scene's geometry in shared memory.
+__device__ __forceinline__ void load_scene(const MarchArgs& a, int scene, SceneGeom* dst, int lane) {
+    constexpr int kWords = (int)(sizeof(SceneGeom) / sizeof(uint32_t));
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(a.scenes + scene);
+    uint32_t* out = reinterpret_cast<uint32_t*>(dst);
+    __syncwarp();
+    for (int k = lane; k < kWords; k += 32) out[k] = __ldg(src + k);
+    __syncwarp();
+}
+
 // Lattice walk: the warp takes the tile's rays one at a time. Tiles go two deep:
 // the warp runs the ballot pass of a new tile and publishes its total before it
 // waits for the offset of the tile it did before (whose rows sit in the other
 // half of the warp's shared memory), so the look-back rarely stalls.
-template <int MAXL, int MINB, bool CONE, bool UNROLL2 = false, bool COARSE = false>
+// BATCHED: every ray looks up its scene's own grid (nacc_march_rays_batched).
+template <int MAXL, int MINB, bool CONE, bool UNROLL2 = false, bool COARSE = false, bool BATCHED = false>
 __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const MarchArgs a) {
     extern __shared__ uint32_t s_masks[];  // per warp: 2 x [tile_rays][row_stride]
     __shared__ float s_lat[kWarps][36];    // cone steps with a ray-specific start
+    __shared__ SceneGeom s_scene[BATCHED ? kWarps : 1];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const size_t tile_words = (size_t)a.tile_rays * a.row_stride;
     uint32_t* wbase = s_masks + (size_t)warp * 2 * tile_words;
     float* lat = s_lat[warp];
+    int scene = 0, held = -1;  // BATCHED: scene of the current ray; scene held in s_scene[warp]
 
     TileState prev;
     bool have_prev = false;
@@ -437,13 +464,34 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
                 }
                 float near = 0.0f, far = 0.0f;
                 int count = 0, nch = 0, pts = 0;
-                const int slot = slot_of(a, r);
-                const bool slot_ok = slot >= 0 && slot < a.n_slots;
-                if (!slot_ok && lane == 0) raise_status(a.d_status, NACC_STATUS_BAD_INDEX);
-                if (slot_ok && clip_ray<MAXL == 0>(a, o, d, near, far))
-                    walk_lattice<MAXL, CONE, UNROLL2, COARSE>(a, o, d, near, far,
-                                                              (unsigned)slot * (unsigned)a.n_levels,
-                                                              wmask + i * a.row_stride, lat, lane, count, nch, pts);
+                uint32_t* row = wmask + i * a.row_stride;
+                if constexpr (BATCHED) {
+                    scene = scene_of(a, r, scene, lane);
+                    if (scene != held) {
+                        load_scene(a, scene, &s_scene[warp], lane);
+                        held = scene;
+                    }
+                    if constexpr (MAXL <= 1) {
+                        const RegGeom g(s_scene[warp]);
+                        if (clip_ray_in<MAXL == 0>(a, g, o, d, near, far))
+                            walk_lattice<MAXL, CONE, UNROLL2, COARSE>(a, g, o, d, near, far, 0u, row, lat, lane,
+                                                                      count, nch, pts);
+                    } else {
+                        const SmemGeom g{&s_scene[warp]};
+                        if (clip_ray_in<false>(a, g, o, d, near, far))
+                            walk_lattice<MAXL, CONE, UNROLL2, COARSE>(a, g, o, d, near, far, 0u, row, lat, lane,
+                                                                      count, nch, pts);
+                    }
+                } else {
+                    const int slot = slot_of(a, r);
+                    const bool slot_ok = slot >= 0 && slot < a.n_slots;
+                    if (!slot_ok && lane == 0) raise_status(a.d_status, NACC_STATUS_BAD_INDEX);
+                    const ArgGeom g{a};
+                    if (slot_ok && clip_ray_in<MAXL == 0>(a, g, o, d, near, far))
+                        walk_lattice<MAXL, CONE, UNROLL2, COARSE>(a, g, o, d, near, far,
+                                                                  (unsigned)slot * (unsigned)a.n_levels, row, lat,
+                                                                  lane, count, nch, pts);
+                }
                 tile_pts += pts;
                 if (lane == i) {
                     my_count = count;
@@ -517,6 +565,88 @@ void launch_walk(bool cone, bool occ, bool unroll, bool coarse, size_t smem, int
     else launch_variant<MAXL, 1>(cone, unroll, coarse, smem, need, st, a);
 }
 
+
+// Scene table upload for a batch of scenes: the host-formed SceneGeom entries
+// reach the workspace as kernel parameters (no host buffer has to outlive the
+// call, and the upload can be captured in a CUDA graph).
+constexpr int kSceneChunk = 16;
+struct SceneUpload {
+    SceneGeom g[kSceneChunk];
+    int32_t end[kSceneChunk];
+    int32_t first, count;
+    SceneGeom* dst;
+    int32_t* dst_end;
+};
+
+__global__ void scene_upload_kernel(const __grid_constant__ SceneUpload u) {
+    constexpr int kWords = (int)(sizeof(SceneGeom) / sizeof(uint32_t));
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(u.g);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(u.dst + u.first);
+    for (int i = threadIdx.x; i < u.count * kWords; i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x < u.count) u.dst_end[u.first + threadIdx.x] = u.end[threadIdx.x];
+}
+
+// Batched variants: the uniform or cone walk, no two-chunk unrolling or coarse pass.
+template <int MAXL, int MINB>
+void launch_batched(bool cone, size_t smem, int need, cudaStream_t st, const MarchArgs& a) {
+    if (cone) launch_uniform(march_uniform_kernel<MAXL, MINB, true, false, false, true>, smem, need, st, a);
+    else launch_uniform(march_uniform_kernel<MAXL, MINB, false, false, false, true>, smem, need, st, a);
+}
+
+size_t batched_table_bytes(int32_t n_scenes) {
+    return align_up((size_t)n_scenes * sizeof(SceneGeom), 256) + align_up((size_t)n_scenes * sizeof(int32_t), 256);
+}
+
+// What nacc_march_rays and nacc_march_rays_batched share once the arguments are
+// checked and `a` holds rays, step rule and geometry: outputs, workspace
+// pointers, the cone table prologue, and the walk's launch.
+int march_launch(MarchArgs& a, const nacc_march_params* p, int32_t* packed_info, float* t_starts, float* t_ends,
+                 int32_t* ray_indices, int64_t capacity, int64_t* n_samples, int32_t* d_status, void* workspace,
+                 cudaStream_t st, bool batched) {
+    a.packed_info = packed_info;
+    a.t_starts = t_starts;
+    a.t_ends = t_ends;
+    a.ray_indices = ray_indices;
+    a.capacity = capacity;
+    a.n_samples = n_samples;
+    a.d_status = d_status;
+    a.ticket = (unsigned int*)workspace;
+    a.lattice_points = (unsigned long long*)((char*)workspace + 8);
+    a.tile_status = (unsigned long long*)((char*)workspace + kTicketBytes);
+    a.hooks = lookback_hooks();
+    const bool cone = p->cone > 0.0f;
+    const bool occ = tune_get(NACC_TUNE_MARCH_OCCUPANCY) != 0;
+    a.tile_rays = tile_rays_for(a.mask_words);
+
+    a.n_tiles = (a.n_rays + a.tile_rays - 1) / a.tile_rays;
+    const size_t clear = kTicketBytes + (size_t)a.n_tiles * sizeof(unsigned long long);
+    cudaError_t e = cudaMemsetAsync(workspace, 0, clear, st);
+    if (e != cudaSuccess) return NACC_ERR_CUDA;
+    if (cone) {
+        float* table = (float*)((char*)workspace + status_bytes_for(a.n_rays));
+        a.cone_table = table;
+        cone_table_kernel<<<1, 32, 0, st>>>(a, table);
+    }
+    const size_t smem = (size_t)kWarps * 2 * a.tile_rays * a.row_stride * sizeof(uint32_t);
+    const int need = (a.n_tiles + kWarps - 1) / kWarps;
+    if (batched) {
+        // one level in registers fits 4 blocks of 256 threads per SM like the
+        // single-grid walk; cascades and contracted space run uncapped
+        if (a.contract) launch_batched<0, 1>(cone, smem, need, st, a);
+        else if (a.n_levels == 1) launch_batched<1, 4>(cone, smem, need, st, a);
+        else if (a.n_levels <= 4) launch_batched<4, 1>(cone, smem, need, st, a);
+        else launch_batched<NACC_MAX_LEVELS, 1>(cone, smem, need, st, a);
+        return launch_status(cudaGetLastError());
+    }
+    const bool unroll = tune_get(NACC_TUNE_MARCH_UNROLL) != 0;
+    const bool coarse = tune_get(NACC_TUNE_MARCH_COARSE) != 0;
+    if (a.contract) launch_walk<0>(cone, occ, false, false, smem, need, st, a);
+    else if (a.n_levels == 1) launch_walk<1>(cone, occ, unroll, coarse, smem, need, st, a);
+    else if (a.n_levels <= 4) launch_walk<4>(cone, occ, unroll, coarse, smem, need, st, a);
+    else launch_walk<NACC_MAX_LEVELS>(cone, occ, unroll, coarse, smem, need, st, a);
+    return launch_status(cudaGetLastError());
+}
+
 }  // namespace
 }  // namespace nacc
 
@@ -545,38 +675,78 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
 
     cudaStream_t st = (cudaStream_t)stream;
     if (n_rays == 0) return launch_status(cudaMemsetAsync(n_samples, 0, sizeof(int64_t), st));
+    return march_launch(a, p, packed_info, t_starts, t_ends, ray_indices, capacity, n_samples, d_status, workspace,
+                        st, false);
+}
 
-    a.packed_info = packed_info;
-    a.t_starts = t_starts;
-    a.t_ends = t_ends;
-    a.ray_indices = ray_indices;
-    a.capacity = capacity;
-    a.n_samples = n_samples;
-    a.d_status = d_status;
-    a.ticket = (unsigned int*)workspace;
-    a.lattice_points = (unsigned long long*)((char*)workspace + 8);
-    a.tile_status = (unsigned long long*)((char*)workspace + kTicketBytes);
-    a.hooks = lookback_hooks();
-    const bool cone = p->cone > 0.0f;
-    const bool occ = tune_get(NACC_TUNE_MARCH_OCCUPANCY) != 0;
-    a.tile_rays = tile_rays_for(a.mask_words);
+extern "C" size_t nacc_march_batched_workspace_size(int32_t n_scenes, int32_t n_rays,
+                                                    const nacc_march_params* params) {
+    if (n_rays < 0 || n_scenes < 0) return 0;
+    return workspace_bytes_for(n_rays, params) + batched_table_bytes(n_scenes);
+}
 
-    a.n_tiles = (n_rays + a.tile_rays - 1) / a.tile_rays;
-    const size_t clear = kTicketBytes + (size_t)a.n_tiles * sizeof(unsigned long long);
-    cudaError_t e = cudaMemsetAsync(workspace, 0, clear, st);
-    if (e != cudaSuccess) return NACC_ERR_CUDA;
-    if (cone) {
-        float* table = (float*)((char*)workspace + status_bytes_for(n_rays));
-        a.cone_table = table;
-        cone_table_kernel<<<1, 32, 0, st>>>(a, table);
+extern "C" int nacc_march_rays_batched(const nacc_scene_desc* scenes, int32_t n_scenes, const float* rays_o,
+                                       const float* rays_d, int32_t n_rays, const nacc_march_params* p,
+                                       int32_t* packed_info, float* t_starts, float* t_ends, int32_t* ray_indices,
+                                       int64_t capacity, int64_t* n_samples, int32_t* d_status, void* workspace,
+                                       size_t workspace_bytes, void* stream) {
+    if (capacity < 0 || !n_samples || n_scenes < 1 || !scenes || !p || n_rays < 0) return NACC_ERR_INVALID_ARG;
+    if (n_rays > 0 && !packed_info) return NACC_ERR_INVALID_ARG;
+    if (capacity > 0 && (!t_starts || !t_ends || !ray_indices)) return NACC_ERR_INVALID_ARG;
+    // every scene: a valid grid of its own, its consecutive rays; one contraction mode
+    long long total = 0;
+    int max_levels = 1, first_with_rays = -1;
+    for (int s = 0; s < n_scenes; ++s) {
+        const nacc_scene_desc& d = scenes[s];
+        nacc_grid g{d.bits, {d.res[0], d.res[1], d.res[2]}, d.n_levels, 1,
+                    {d.aabb[0], d.aabb[1], d.aabb[2], d.aabb[3], d.aabb[4], d.aabb[5]}, d.contraction};
+        if (check_grid(&g) != NACC_OK || d.n_rays < 0) return NACC_ERR_INVALID_ARG;
+        if (d.contraction != scenes[0].contraction) return NACC_ERR_INVALID_ARG;
+        if (d.n_rays > 0 && !d.bits) return NACC_ERR_INVALID_ARG;
+        if (d.n_rays > 0 && first_with_rays < 0) first_with_rays = s;
+        max_levels = d.n_levels > max_levels ? d.n_levels : max_levels;
+        total += d.n_rays;
     }
-    const size_t smem = (size_t)kWarps * 2 * a.tile_rays * a.row_stride * sizeof(uint32_t);
-    const int need = (a.n_tiles + kWarps - 1) / kWarps;
-    const bool unroll = tune_get(NACC_TUNE_MARCH_UNROLL) != 0;
-    const bool coarse = tune_get(NACC_TUNE_MARCH_COARSE) != 0;
-    if (a.contract) launch_walk<0>(cone, occ, false, false, smem, need, st, a);
-    else if (a.n_levels == 1) launch_walk<1>(cone, occ, unroll, coarse, smem, need, st, a);
-    else if (a.n_levels <= 4) launch_walk<4>(cone, occ, unroll, coarse, smem, need, st, a);
-    else launch_walk<NACC_MAX_LEVELS>(cone, occ, unroll, coarse, smem, need, st, a);
-    return launch_status(cudaGetLastError());
+    if (total != n_rays) return NACC_ERR_INVALID_ARG;
+    const nacc_scene_desc& d0 = scenes[first_with_rays < 0 ? 0 : first_with_rays];
+    nacc_grid g0{d0.bits, {d0.res[0], d0.res[1], d0.res[2]}, d0.n_levels, 1,
+                 {d0.aabb[0], d0.aabb[1], d0.aabb[2], d0.aabb[3], d0.aabb[4], d0.aabb[5]}, d0.contraction};
+    MarchArgs a;
+    const int setup = march_setup(rays_o, rays_d, nullptr, nullptr, n_rays, &g0, p, a);
+    if (setup != NACC_OK) return setup;
+    const size_t base = workspace_bytes_for(n_rays, p);
+    if (!workspace || workspace_bytes < base + batched_table_bytes(n_scenes)) return NACC_ERR_INVALID_ARG;
+    if (((uintptr_t)workspace & 255u) != 0) return NACC_ERR_INVALID_ARG;
+    if (((uintptr_t)packed_info & 7u) != 0) return NACC_ERR_INVALID_ARG;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_rays == 0) return launch_status(cudaMemsetAsync(n_samples, 0, sizeof(int64_t), st));
+
+    SceneGeom* table = (SceneGeom*)((char*)workspace + base);
+    int32_t* ends = (int32_t*)((char*)table + align_up((size_t)n_scenes * sizeof(SceneGeom), 256));
+    SceneUpload u;
+    memset(&u, 0, sizeof(u));
+    u.dst = table;
+    u.dst_end = ends;
+    int32_t end = 0;
+    for (int s0 = 0; s0 < n_scenes; s0 += kSceneChunk) {
+        u.first = s0;
+        u.count = n_scenes - s0 < kSceneChunk ? n_scenes - s0 : kSceneChunk;
+        for (int j = 0; j < u.count; ++j) {
+            const nacc_scene_desc& d = scenes[s0 + j];
+            nacc_grid g{d.bits, {d.res[0], d.res[1], d.res[2]}, d.n_levels, 1,
+                        {d.aabb[0], d.aabb[1], d.aabb[2], d.aabb[3], d.aabb[4], d.aabb[5]}, d.contraction};
+            scene_geom_for(g, u.g[j]);
+            end += d.n_rays;
+            u.end[j] = end;
+        }
+        scene_upload_kernel<<<1, 256, 0, st>>>(u);
+    }
+    a.scenes = table;
+    a.scene_end = ends;
+    a.n_scenes = n_scenes;
+    a.n_levels = max_levels;
+    a.contract = scenes[0].contraction;
+    return march_launch(a, p, packed_info, t_starts, t_ends, ray_indices, capacity, n_samples, d_status, workspace,
+                        st, true);
 }

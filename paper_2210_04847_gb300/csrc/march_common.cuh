@@ -25,6 +25,20 @@ struct Levels {
     float box_hi[3];
 };
 
+// One scene of a batch with per-scene grids (nacc_march_rays_batched), as the
+// kernels read it from the workspace: the scene's bitfield (its level 0 at word
+// 0), resolution, level boxes and contraction constants, formed on the host by
+// the same float32 operations as a single grid's.
+struct SceneGeom {
+    const uint32_t* bits;
+    int32_t res[3];
+    int32_t n_levels;
+    Levels L;
+    float cc[3], inv_h[3], qres[3];
+    int32_t pad[3];
+};
+static_assert(sizeof(SceneGeom) % 16 == 0, "scene table entries stay 16-byte aligned");
+
 struct MarchArgs {
     const float* rays_o;
     const float* rays_d;
@@ -58,16 +72,93 @@ struct MarchArgs {
     float qres[3];            // contraction: res / 4 (the grid spans [-2, 2])
     float inv_dt;             // 1 / dt_min, for the first guess of a uniform lattice's length
     LookbackHooks hooks;      // look-back poll budget (test hooks)
+    const SceneGeom* scenes;  // batch of scenes with their own grids (else null)
+    const int32_t* scene_end; // exclusive end of each scene's consecutive rays
+    int32_t n_scenes;
     Levels L;
+};
+
+// ---------------------------------------------------------------------------
+// grid geometry as the lookup reads it
+// ---------------------------------------------------------------------------
+// The call's grid lives in the kernel parameters (ArgGeom). For a batch of
+// scenes with their own grids the walk reads the current ray's scene from
+// registers (RegGeom: one level or contracted space) or from the warp's copy of
+// the scene in shared memory (SmemGeom: cascades). The lookup arithmetic is the
+// same for all three.
+
+struct ArgGeom {
+    const MarchArgs& a;
+    __device__ __forceinline__ float lo(int l, int k) const { return a.L.lo[l][k]; }
+    __device__ __forceinline__ float scale(int l, int k) const { return a.L.scale[l][k]; }
+    __device__ __forceinline__ float box_lo(int k) const { return a.L.box_lo[k]; }
+    __device__ __forceinline__ float box_hi(int k) const { return a.L.box_hi[k]; }
+    __device__ __forceinline__ float cc(int k) const { return a.cc[k]; }
+    __device__ __forceinline__ float inv_h(int k) const { return a.inv_h[k]; }
+    __device__ __forceinline__ float qres(int k) const { return a.qres[k]; }
+    __device__ __forceinline__ int res0() const { return a.res0; }
+    __device__ __forceinline__ int res1() const { return a.res1; }
+    __device__ __forceinline__ int res2() const { return a.res2; }
+    __device__ __forceinline__ int n_levels() const { return a.n_levels; }
+    __device__ __forceinline__ const uint32_t* bits() const { return a.bits; }
+};
+
+struct SmemGeom {
+    const SceneGeom* g;
+    __device__ __forceinline__ float lo(int l, int k) const { return g->L.lo[l][k]; }
+    __device__ __forceinline__ float scale(int l, int k) const { return g->L.scale[l][k]; }
+    __device__ __forceinline__ float box_lo(int k) const { return g->L.box_lo[k]; }
+    __device__ __forceinline__ float box_hi(int k) const { return g->L.box_hi[k]; }
+    __device__ __forceinline__ float cc(int k) const { return g->cc[k]; }
+    __device__ __forceinline__ float inv_h(int k) const { return g->inv_h[k]; }
+    __device__ __forceinline__ float qres(int k) const { return g->qres[k]; }
+    __device__ __forceinline__ int res0() const { return g->res[0]; }
+    __device__ __forceinline__ int res1() const { return g->res[1]; }
+    __device__ __forceinline__ int res2() const { return g->res[2]; }
+    __device__ __forceinline__ int n_levels() const { return g->n_levels; }
+    __device__ __forceinline__ const uint32_t* bits() const { return g->bits; }
+};
+
+// One level (or contracted space) in registers, loaded once per ray.
+struct RegGeom {
+    float lo_[3], scale_[3], blo_[3], bhi_[3], cc_[3], ih_[3], q_[3];
+    int r_[3];
+    const uint32_t* b_;
+    __device__ __forceinline__ explicit RegGeom(const SceneGeom& s) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lo_[k] = s.L.lo[0][k];
+            scale_[k] = s.L.scale[0][k];
+            blo_[k] = s.L.box_lo[k];
+            bhi_[k] = s.L.box_hi[k];
+            cc_[k] = s.cc[k];
+            ih_[k] = s.inv_h[k];
+            q_[k] = s.qres[k];
+            r_[k] = s.res[k];
+        }
+        b_ = s.bits;
+    }
+    __device__ __forceinline__ float lo(int, int k) const { return lo_[k]; }
+    __device__ __forceinline__ float scale(int, int k) const { return scale_[k]; }
+    __device__ __forceinline__ float box_lo(int k) const { return blo_[k]; }
+    __device__ __forceinline__ float box_hi(int k) const { return bhi_[k]; }
+    __device__ __forceinline__ float cc(int k) const { return cc_[k]; }
+    __device__ __forceinline__ float inv_h(int k) const { return ih_[k]; }
+    __device__ __forceinline__ float qres(int k) const { return q_[k]; }
+    __device__ __forceinline__ int res0() const { return r_[0]; }
+    __device__ __forceinline__ int res1() const { return r_[1]; }
+    __device__ __forceinline__ int res2() const { return r_[2]; }
+    __device__ __forceinline__ int n_levels() const { return 1; }
+    __device__ __forceinline__ const uint32_t* bits() const { return b_; }
 };
 
 __device__ __forceinline__ bool finite32(float v) { return fabsf(v) <= 3.402823466e+38f; }
 
 // Slab clip against the outermost level box, float32 (ties and zero
 // directions as the oracle defines them). CONTRACT: contracted space has no box.
-template <bool CONTRACT>
-__device__ __forceinline__ bool clip_ray(const MarchArgs& a, const float o[3], const float d[3],
-                                         float& near, float& far) {
+template <bool CONTRACT, typename G>
+__device__ __forceinline__ bool clip_ray_in(const MarchArgs& a, const G& g, const float o[3], const float d[3],
+                                            float& near, float& far) {
 #pragma unroll
     for (int k = 0; k < 3; ++k)
         if (!finite32(o[k]) || !finite32(d[k])) return false;
@@ -80,12 +171,12 @@ __device__ __forceinline__ bool clip_ray(const MarchArgs& a, const float o[3], c
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         if (d[k] == 0.0f) {
-            if (o[k] < a.L.box_lo[k] || o[k] > a.L.box_hi[k]) return false;
+            if (o[k] < g.box_lo(k) || o[k] > g.box_hi(k)) return false;
             continue;
         }
         float inv = __frcp_rn(d[k]);  // the correctly rounded 1/d, as the IEEE division gives
-        float t0 = __fmul_rn(__fsub_rn(a.L.box_lo[k], o[k]), inv);
-        float t1 = __fmul_rn(__fsub_rn(a.L.box_hi[k], o[k]), inv);
+        float t0 = __fmul_rn(__fsub_rn(g.box_lo(k), o[k]), inv);
+        float t1 = __fmul_rn(__fsub_rn(g.box_hi(k), o[k]), inv);
         float tmin = t0 < t1 ? t0 : t1;
         float tmax = t0 < t1 ? t1 : t0;
         if (tmin > t_in) t_in = tmin;
@@ -94,6 +185,12 @@ __device__ __forceinline__ bool clip_ray(const MarchArgs& a, const float o[3], c
     near = t_in > a.near_plane ? t_in : a.near_plane;
     far = t_out < a.far_plane ? t_out : a.far_plane;
     return near < far;
+}
+
+template <bool CONTRACT>
+__device__ __forceinline__ bool clip_ray(const MarchArgs& a, const float o[3], const float d[3], float& near,
+                                         float& far) {
+    return clip_ray_in<CONTRACT>(a, ArgGeom{a}, o, d, near, far);
 }
 
 __device__ __forceinline__ int slot_of(const MarchArgs& a, int r) {
@@ -112,12 +209,11 @@ __device__ __forceinline__ int slot_of(const MarchArgs& a, int r) {
 // i = floor(u) with 0 <= i < res is the same test as 0 <= u < res followed by
 // truncation (u is finite here: o, d and the lattice are finite).
 // MAXL == 0: contracted unbounded space (one level, see nacc_grid).
-template <int MAXL>
-__device__ __forceinline__ bool occupied(const MarchArgs& a, float x0, float x1, float x2,
-                                         unsigned slot_level0) {
+template <int MAXL, typename G>
+__device__ __forceinline__ bool occupied_in(const G& g, float x0, float x1, float x2, unsigned slot_level0) {
     if constexpr (MAXL == 0) {
-        float x[3] = {__fmul_rn(__fsub_rn(x0, a.cc[0]), a.inv_h[0]), __fmul_rn(__fsub_rn(x1, a.cc[1]), a.inv_h[1]),
-                      __fmul_rn(__fsub_rn(x2, a.cc[2]), a.inv_h[2])};
+        float x[3] = {__fmul_rn(__fsub_rn(x0, g.cc(0)), g.inv_h(0)), __fmul_rn(__fsub_rn(x1, g.cc(1)), g.inv_h(1)),
+                      __fmul_rn(__fsub_rn(x2, g.cc(2)), g.inv_h(2))};
         const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(x[0], x[0]), __fmul_rn(x[1], x[1])), __fmul_rn(x[2], x[2]));
         if (!(n2 <= 1.0f)) {
             const float n = __fsqrt_rn(n2);
@@ -125,30 +221,36 @@ __device__ __forceinline__ bool occupied(const MarchArgs& a, float x0, float x1,
 #pragma unroll
             for (int k = 0; k < 3; ++k) x[k] = __fmul_rn(x[k], s);
         }
-        const int i0 = __float2int_rd(__fmul_rn(__fadd_rn(x[0], 2.0f), a.qres[0]));
-        const int i1 = __float2int_rd(__fmul_rn(__fadd_rn(x[1], 2.0f), a.qres[1]));
-        const int i2 = __float2int_rd(__fmul_rn(__fadd_rn(x[2], 2.0f), a.qres[2]));
-        if ((unsigned)i0 < (unsigned)a.res0 && (unsigned)i1 < (unsigned)a.res1 && (unsigned)i2 < (unsigned)a.res2) {
-            const unsigned cell = ((slot_level0 * a.res0 + i0) * a.res1 + i1) * a.res2 + i2;
-            const unsigned w = __ldg(a.bits + (cell >> 5));
+        const int i0 = __float2int_rd(__fmul_rn(__fadd_rn(x[0], 2.0f), g.qres(0)));
+        const int i1 = __float2int_rd(__fmul_rn(__fadd_rn(x[1], 2.0f), g.qres(1)));
+        const int i2 = __float2int_rd(__fmul_rn(__fadd_rn(x[2], 2.0f), g.qres(2)));
+        if ((unsigned)i0 < (unsigned)g.res0() && (unsigned)i1 < (unsigned)g.res1() && (unsigned)i2 < (unsigned)g.res2()) {
+            const unsigned cell = ((slot_level0 * g.res0() + i0) * g.res1() + i1) * g.res2() + i2;
+            const unsigned w = __ldg(g.bits() + (cell >> 5));
             return (w >> (cell & 31u)) & 1u;
         }
         return false;
     } else {
 #pragma unroll
         for (int l = 0; l < MAXL; ++l) {
-            if (MAXL > 1 && l >= a.n_levels) break;  // single-level kernels run only for n_levels == 1
-            const int i0 = __float2int_rd(__fmul_rn(__fsub_rn(x0, a.L.lo[l][0]), a.L.scale[l][0]));
-            const int i1 = __float2int_rd(__fmul_rn(__fsub_rn(x1, a.L.lo[l][1]), a.L.scale[l][1]));
-            const int i2 = __float2int_rd(__fmul_rn(__fsub_rn(x2, a.L.lo[l][2]), a.L.scale[l][2]));
-            if ((unsigned)i0 < (unsigned)a.res0 && (unsigned)i1 < (unsigned)a.res1 && (unsigned)i2 < (unsigned)a.res2) {
-                const unsigned cell = (((slot_level0 + l) * a.res0 + i0) * a.res1 + i1) * a.res2 + i2;
-                const unsigned w = __ldg(a.bits + (cell >> 5));
+            if (MAXL > 1 && l >= g.n_levels()) break;  // single-level kernels run only for n_levels == 1
+            const int i0 = __float2int_rd(__fmul_rn(__fsub_rn(x0, g.lo(l, 0)), g.scale(l, 0)));
+            const int i1 = __float2int_rd(__fmul_rn(__fsub_rn(x1, g.lo(l, 1)), g.scale(l, 1)));
+            const int i2 = __float2int_rd(__fmul_rn(__fsub_rn(x2, g.lo(l, 2)), g.scale(l, 2)));
+            if ((unsigned)i0 < (unsigned)g.res0() && (unsigned)i1 < (unsigned)g.res1() &&
+                (unsigned)i2 < (unsigned)g.res2()) {
+                const unsigned cell = (((slot_level0 + l) * g.res0() + i0) * g.res1() + i1) * g.res2() + i2;
+                const unsigned w = __ldg(g.bits() + (cell >> 5));
                 return (w >> (cell & 31u)) & 1u;
             }
         }
         return false;
     }
+}
+
+template <int MAXL>
+__device__ __forceinline__ bool occupied(const MarchArgs& a, float x0, float x1, float x2, unsigned slot_level0) {
+    return occupied_in<MAXL>(ArgGeom{a}, x0, x1, x2, slot_level0);
 }
 
 __device__ __forceinline__ float lattice_t(float near, int k, float dt) {
@@ -309,26 +411,54 @@ int blocks_for(K kernel, size_t smem, int n_work_blocks) {
     return n_work_blocks < want ? n_work_blocks : want;
 }
 
-// Checks the arguments every marching entry point shares (rays, grid, step
-// parameters) and fills the corresponding fields of `a` (zeroing the rest).
-int march_setup(const float* rays_o, const float* rays_d, const float* ray_time, const int32_t* ray_slot,
-                int32_t n_rays, const nacc_grid* grid, const nacc_march_params* p, MarchArgs& a) {
-    if (n_rays < 0 || !grid || !p) return NACC_ERR_INVALID_ARG;
-    if (n_rays > 0 && (!rays_o || !rays_d || !grid->bits)) return NACC_ERR_INVALID_ARG;
+// The shape of a grid (levels, slots, resolution, box, contraction); bits are
+// checked by the caller.
+int check_grid(const nacc_grid* grid) {
+    if (!grid) return NACC_ERR_INVALID_ARG;
     if (grid->n_levels < 1 || grid->n_levels > NACC_MAX_LEVELS || grid->n_slots < 1) return NACC_ERR_INVALID_ARG;
     if (grid->contraction != 0 && (grid->contraction != 1 || grid->n_levels != 1)) return NACC_ERR_INVALID_ARG;
     if (grid->res[0] < 1 || grid->res[1] < 1 || grid->res[2] < 1) return NACC_ERR_INVALID_ARG;
     if (grid->res[0] > (1 << 22) || grid->res[1] > (1 << 22) || grid->res[2] > (1 << 22)) return NACC_ERR_INVALID_ARG;
     const long long cells = (long long)grid->res[0] * grid->res[1] * grid->res[2] * grid->n_levels * grid->n_slots;
     if (cells >= (1LL << 31)) return NACC_ERR_INVALID_ARG;
-    if (p->max_steps < 1 || p->max_steps > 32768) return NACC_ERR_INVALID_ARG;
-    if (!(p->dt_min > 0.0f) || !(p->dt_min < INFINITY) || p->cone < 0.0f || !(p->cone < INFINITY))
-        return NACC_ERR_INVALID_ARG;
-    if (p->cone > 0.0f && !(p->dt_max >= p->dt_min)) return NACC_ERR_INVALID_ARG;
     for (int k = 0; k < 6; ++k)
         if (!(fabsf(grid->aabb[k]) < INFINITY)) return NACC_ERR_INVALID_ARG;
     for (int k = 0; k < 3; ++k)
         if (!(grid->aabb[k] < grid->aabb[3 + k])) return NACC_ERR_INVALID_ARG;
+    return NACC_OK;
+}
+
+// Contraction constants of a grid's box: centre, 1 / half size, res / 4.
+void contraction_consts(const nacc_grid& grid, float cc[3], float inv_h[3], float qres[3]) {
+    for (int k = 0; k < 3; ++k) {
+        const float lo = grid.aabb[k], hi = grid.aabb[3 + k];
+        cc[k] = (lo + hi) * 0.5f;
+        inv_h[k] = 1.0f / ((hi - lo) * 0.5f);
+        qres[k] = (float)grid.res[k] * 0.25f;
+    }
+}
+
+// A scene's geometry as the batched kernels read it (the grid checked already).
+void scene_geom_for(const nacc_grid& grid, SceneGeom& g) {
+    memset(&g, 0, sizeof(g));
+    g.bits = grid.bits;
+    for (int k = 0; k < 3; ++k) g.res[k] = grid.res[k];
+    g.n_levels = grid.n_levels;
+    make_levels(grid, g.L);
+    contraction_consts(grid, g.cc, g.inv_h, g.qres);
+}
+
+// Checks the arguments every marching entry point shares (rays, grid, step
+// parameters) and fills the corresponding fields of `a` (zeroing the rest).
+int march_setup(const float* rays_o, const float* rays_d, const float* ray_time, const int32_t* ray_slot,
+                int32_t n_rays, const nacc_grid* grid, const nacc_march_params* p, MarchArgs& a) {
+    if (n_rays < 0 || !grid || !p) return NACC_ERR_INVALID_ARG;
+    if (n_rays > 0 && (!rays_o || !rays_d || !grid->bits)) return NACC_ERR_INVALID_ARG;
+    if (check_grid(grid) != NACC_OK) return NACC_ERR_INVALID_ARG;
+    if (p->max_steps < 1 || p->max_steps > 32768) return NACC_ERR_INVALID_ARG;
+    if (!(p->dt_min > 0.0f) || !(p->dt_min < INFINITY) || p->cone < 0.0f || !(p->cone < INFINITY))
+        return NACC_ERR_INVALID_ARG;
+    if (p->cone > 0.0f && !(p->dt_max >= p->dt_min)) return NACC_ERR_INVALID_ARG;
 
     memset(&a, 0, sizeof(a));
     a.rays_o = rays_o;
@@ -356,12 +486,7 @@ int march_setup(const float* rays_o, const float* rays_d, const float* ray_time,
     a.row_stride = a.mask_words;
     make_levels(*grid, a.L);
     a.contract = grid->contraction;
-    for (int k = 0; k < 3; ++k) {
-        const float lo = grid->aabb[k], hi = grid->aabb[3 + k];
-        a.cc[k] = (lo + hi) * 0.5f;
-        a.inv_h[k] = 1.0f / ((hi - lo) * 0.5f);
-        a.qres[k] = (float)grid->res[k] * 0.25f;
-    }
+    contraction_consts(*grid, a.cc, a.inv_h, a.qres);
     return NACC_OK;
 }
 

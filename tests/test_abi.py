@@ -149,3 +149,37 @@ def test_lookback_test_hooks_validate_and_default(libs):
     assert lib.nacc_test_hook_get(7) == _lib.ERR_INVALID_ARG
     assert lib.nacc_test_hook_set(0, 17) == _lib.OK and lib.nacc_test_hook_get(0) == 17
     assert lib.nacc_test_hook_set(0, 1 << 22) == _lib.OK and lib.nacc_test_hook_get(0) == 1 << 22
+
+
+def test_batched_march_arguments_rejected_on_host(libs):
+    lib, _ = libs
+    p = _lib.make_params(0.0, 1e10, 0.01, None, 0.0, 64)
+
+    def desc(res=(8, 8, 8), n_levels=1, contraction=0, n_rays=2, aabb=(-1, -1, -1, 1, 1, 1), bits=4096):
+        d = _lib.SceneDesc()
+        d.bits = bits
+        for k in range(3):
+            d.res[k] = res[k]
+        for k in range(6):
+            d.aabb[k] = aabb[k]
+        d.n_levels, d.contraction, d.n_rays = n_levels, contraction, n_rays
+        return d
+
+    def call(ds, n_rays=4, wsb=1 << 20):
+        arr = (_lib.SceneDesc * len(ds))(*ds)
+        # every call below is rejected before a pointer is touched
+        return lib.nacc_march_rays_batched(arr, len(ds), ctypes.c_void_p(256), ctypes.c_void_p(512), n_rays,
+                                           ctypes.byref(p), ctypes.c_void_p(1024), None, None, None, 0,
+                                           ctypes.c_void_p(2048), None, ctypes.c_void_p(1 << 20), wsb, None)
+
+    assert call([desc(), desc(n_rays=3)]) == _lib.ERR_INVALID_ARG  # counts sum to 5, not 4
+    assert call([desc(), desc(res=(0, 8, 8))]) == _lib.ERR_INVALID_ARG
+    assert call([desc(), desc(n_levels=17)]) == _lib.ERR_INVALID_ARG
+    assert call([desc(), desc(contraction=1)]) == _lib.ERR_INVALID_ARG  # mixed contraction
+    assert call([desc(), desc(aabb=(1, -1, -1, -1, 1, 1))]) == _lib.ERR_INVALID_ARG
+    assert call([desc(), desc(bits=None)]) == _lib.ERR_INVALID_ARG  # rays but no grid
+    assert call([desc(), desc(n_rays=-1), desc(n_rays=3)]) == _lib.ERR_INVALID_ARG
+    assert call([desc(), desc()], wsb=16) == _lib.ERR_INVALID_ARG  # workspace too small
+    assert call([]) == _lib.ERR_INVALID_ARG  # no scenes
+    assert lib.nacc_march_batched_workspace_size(64, 1 << 18, ctypes.byref(p)) > \
+        lib.nacc_march_workspace_size(1 << 18, ctypes.byref(p)) + 64 * 400
