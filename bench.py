@@ -197,14 +197,17 @@ def stage_bytes(R, M, M_read, S, grid_bytes, n_cells, n_grid, saved_od=False):
     }
 
 
-def launches_per_step(w, n_cells: int, n_grid: int, ema_ptr: int) -> int:
+def launches_per_step(w, n_cells: int, n_grid: int, ema_ptr: int, sat: bool = False) -> int:
     """Library kernels one timed step launches: march (plus the cone-table prologue
     for cone steps), prune, render forward, render backward, the grid sampler, the
     decay pass (four cells per thread over whole 128-cell steps of an aligned
-    grid, one cell per thread for the rest) and the scatter."""
+    grid, one cell per thread for the rest), the scatter, and with the box walk
+    the three passes that rebuild the updated grid's summed-area table."""
     n = 4 + (1 if w.cone > 0 else 0)
     if n_grid > 0:
         n += 2  # sampler + scatter
+        if sat:
+            n += 3
     steps = n_cells >> 7 if ema_ptr % 16 == 0 else 0
     n += (1 if steps > 0 else 0) + (1 if (steps << 7) < n_cells else 0)
     return n
@@ -423,6 +426,8 @@ def run_ours(args):
             k, v = kv.split("=")
             if k.strip() == "save_optical_depth":
                 hp.save_optical_depth = bool(int(v))
+            elif k.strip() == "march_sat":
+                hp.use_sat = hp.sat_ok and bool(int(v))
             else:
                 _lib.tune_set(k.strip(), int(v))
             tuned[k.strip()] = {"best": int(v), "fixed": True}
@@ -548,7 +553,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms_all, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
-        "tuned": dict({k: _lib.tune_get(k) for k in _lib.TUNE_KNOBS}, save_optical_depth=int(hp.save_optical_depth)),
+        "tuned": dict({k: _lib.tune_get(k) for k in _lib.TUNE_KNOBS}, save_optical_depth=int(hp.save_optical_depth),
+                      march_sat=int(hp.use_sat)),
         "tuning_ms": {k: v.get("ms") for k, v in tuned.items() if v.get("ms")},
         "stages_ms": {s: round(avg[s], 4) for s in stages},
         "stage_gbs": {s: round(sb[s] / (avg[s] / 1e3) / 1e9, 1) for s in stages},
@@ -564,7 +570,7 @@ def run_ours(args):
                      "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes": int(sb[dom]), "limiter": LIMITER[dom]},
         "wall_s_timed_loop_incl_field": round(t_wall, 3),
-        "gpu_launches": launches_per_step(w, sc.n_cells, sc.n_grid, hp.ema.data_ptr()) * args.steps,
+        "gpu_launches": launches_per_step(w, sc.n_cells, sc.n_grid, hp.ema.data_ptr(), hp.use_sat) * args.steps,
         "clocks": clk,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define NACC_VERSION 200
+#define NACC_VERSION 300
 
 /* host return codes */
 #define NACC_OK 0
@@ -83,7 +83,27 @@ typedef struct nacc_grid {
     int32_t n_slots;  /* >= 1 */
     float aabb[6];
     int32_t contraction; /* 0: boxes (cascade); 1: contracted unbounded space */
+    const uint16_t* sat; /* device or NULL: the summed-area table of `bits`, see nacc_build_grid_sat */
 } nacc_grid;
+
+/*
+ * Summed-area table of a grid (an acceleration structure of this library, not
+ * part of the paper's method): for each slot and level g, one uint16 entry per
+ * cell corner (x, y, z) in [0, res0] x [0, res1] x [0, res2],
+ *     S_g[x][y][z] = number of occupied cells (i, j, k) of g with i < x, j < y, k < z
+ * modulo 2^16, corners x-major and z fastest, grids in slot-major, level order.
+ * Built from grid->bits on `stream`; rebuild it whenever the bits change.
+ * Marching a one-level, uncontracted grid that carries its table
+ * (nacc_grid.sat) decides every 32-point lattice chunk whose box of cells (from
+ * the chunk's first point to the point after the chunk: every cell index is
+ * monotone along the ray) is all occupied or all empty from one box count
+ * (exact for boxes of fewer than 2^16 cells), and tests the other chunks point
+ * by point. Results are identical with and without the table. sat:
+ * nacc_grid_sat_bytes() bytes, 2-byte aligned; the corners over all slots and
+ * levels must number below 2^31.
+ */
+size_t nacc_grid_sat_bytes(const nacc_grid* grid);
+int nacc_build_grid_sat(const nacc_grid* grid, uint16_t* sat, void* stream);
 
 /*
  * Marching parameters (Sec. 3 listing: near_plane, far_plane; the step rule is
@@ -161,6 +181,7 @@ typedef struct nacc_scene_desc {
     float aabb[6];
     int32_t contraction; /* the same for every scene of a call */
     int32_t n_rays;
+    const uint16_t* sat; /* NULL or the scene's summed-area table (nacc_build_grid_sat, one slot) */
 } nacc_scene_desc;
 
 /* Bytes of device workspace nacc_march_rays_batched needs. */
@@ -509,7 +530,9 @@ int nacc_sample_grid_cells(uint64_t seed, uint64_t stream, int64_t n, const nacc
 #define NACC_TUNE_RENDER_BWD_PREFETCH 9 /* 0/1: backward issues the next chunk's loads early */
 #define NACC_TUNE_MARCH_COARSE 10       /* 0/1: first test one lattice point in 32, fill chunks that lie in one cell */
 #define NACC_TUNE_FUSED_OCCUPANCY 11    /* 0: compiler's register use; 1: nacc_march_fused capped at 64 registers */
-#define NACC_TUNE_COUNT 12
+#define NACC_TUNE_MARCH_BOX_TILE 12     /* 0/1: box walk (grid with its summed-area table, uniform steps) ray by ray,
+                                          or over all chunks of a tile at once */
+#define NACC_TUNE_COUNT 13
 
 /* Set a knob; NACC_ERR_INVALID_ARG for an unknown knob or out-of-range value. */
 int nacc_tune_set(int knob, int value);

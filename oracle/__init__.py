@@ -248,6 +248,22 @@ def update_grid(ema, cells, sigmas, decay, thre, alpha_step=None):
     return e, bits
 
 
+def grid_sat(bits, res, n_grids=1):
+    """Summed-area table of a bit-packed grid (the marcher's acceleration structure,
+    not part of the paper's method), by its definition: per grid g, entry (x, y, z)
+    of the (res0+1, res1+1, res2+1) corner lattice counts the occupied cells
+    (i, j, k) with i < x, j < y, k < z; kept modulo 2^16 as uint16; grids one after
+    the other, x-major, z fastest."""
+    r0, r1, r2 = (int(v) for v in res)
+    n = n_grids * r0 * r1 * r2
+    w = np.ascontiguousarray(bits, dtype=np.uint32)
+    occ = ((w[np.arange(n) >> 5] >> (np.arange(n) & 31).astype(np.uint32)) & 1).astype(np.int64)
+    occ = occ.reshape(n_grids, r0, r1, r2)
+    s = np.zeros((n_grids, r0 + 1, r1 + 1, r2 + 1), np.int64)
+    s[:, 1:, 1:, 1:] = occ.cumsum(1).cumsum(2).cumsum(3)
+    return (s % 65536).astype(np.uint16).reshape(-1)
+
+
 def field_query(field, field_box, xyz):
     """Density field of the fused path (F1 in oracle.c): trilinear between the
     vertex values field[i, j, k] of a lattice over field_box = (lo, hi), zero

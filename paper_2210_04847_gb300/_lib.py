@@ -33,6 +33,7 @@ STATUS_OVERFLOW = 0x10
 MAX_LEVELS = 16
 
 EXPORTS = (
+    "nacc_grid_sat_bytes", "nacc_build_grid_sat",
     "nacc_march_workspace_size", "nacc_march_rays", "nacc_march_rays_static", "nacc_march_batched_workspace_size",
     "nacc_march_rays_batched", "nacc_prune_workspace_size",
     "nacc_prune_samples", "nacc_march_fused", "nacc_density_field_at_samples", "nacc_density_field_query",
@@ -49,7 +50,7 @@ TUNE_PRUNE_TILE_RAYS = 2
 TUNE_KNOBS = {"render_fwd_prefetch": 0, "march_tile_rays": 1, "prune_tile_rays": 2, "march_occupancy": 3,
               "prune_occupancy": 4, "render_fwd_occupancy": 5, "render_bwd_occupancy": 6, "march_unroll": 7,
               "prune_interleave": 8, "render_bwd_prefetch": 9,
-              "march_coarse": 10, "fused_occupancy": 11}
+              "march_coarse": 10, "fused_occupancy": 11, "march_box_tile": 12}
 
 
 class NaccError(RuntimeError):
@@ -64,6 +65,7 @@ class Grid(ctypes.Structure):
         ("n_slots", ctypes.c_int32),
         ("aabb", ctypes.c_float * 6),
         ("contraction", ctypes.c_int32),
+        ("sat", ctypes.c_void_p),
     ]
 
 
@@ -76,6 +78,7 @@ class SceneDesc(ctypes.Structure):
         ("aabb", ctypes.c_float * 6),
         ("contraction", ctypes.c_int32),
         ("n_rays", ctypes.c_int32),
+        ("sat", ctypes.c_void_p),
     ]
 
 
@@ -114,6 +117,8 @@ def load() -> ctypes.CDLL:
     GP, MP = ctypes.POINTER(Grid), ctypes.POINTER(MarchParams)
     FP = ctypes.POINTER(DensityField)
     sig = {
+        "nacc_grid_sat_bytes": (sz, [GP]),
+        "nacc_build_grid_sat": (ctypes.c_int, [GP, P, P]),
         "nacc_march_workspace_size": (sz, [i32, MP]),
         "nacc_march_rays": (ctypes.c_int, [P, P, P, P, i32, GP, MP, P, P, P, P, i64, P, P, P, sz, P]),
         "nacc_march_rays_static": (ctypes.c_int, [P, P, P, P, i32, GP, MP, P, P, P, P, i64, P, P, P]),
@@ -218,10 +223,15 @@ def _rc(code: int, fn: str):
 
 
 def make_grid(bits: torch.Tensor, res: Sequence[int], aabb: Sequence[float], n_levels=1, n_slots=1,
-              contraction: int = 0) -> Grid:
+              contraction: int = 0, sat: Optional[torch.Tensor] = None) -> Grid:
+    """nacc_grid over a bits tensor; ``sat`` (int16 tensor from ``build_grid_sat``)
+    lets one-level grids take the box walk."""
     _check(bits, torch.int32, "grid bits")
+    _check(sat, torch.int16, "grid sat", optional=True)
     g = Grid()
     g._keepalive = bits  # the struct holds a raw pointer: keep the tensor alive with it
+    g._keepalive_sat = sat
+    g.sat = None if sat is None else sat.data_ptr()
     g.contraction = int(contraction)
     g.bits = bits.data_ptr()
     for k in range(3):
@@ -234,15 +244,19 @@ def make_grid(bits: torch.Tensor, res: Sequence[int], aabb: Sequence[float], n_l
 
 
 def make_scenes(scenes) -> ctypes.Array:
-    """Array of nacc_scene_desc from (bits tensor, res, aabb, n_levels, contraction, n_rays)
-    tuples; the array keeps the bits tensors alive."""
+    """Array of nacc_scene_desc from (bits tensor, res, aabb, n_levels, contraction, n_rays[,
+    sat tensor]) tuples; the array keeps the tensors alive."""
     arr = (SceneDesc * len(scenes))()
     keep = []
-    for k, (bits, res, aabb, n_levels, contraction, n_rays) in enumerate(scenes):
+    for k, sc in enumerate(scenes):
+        bits, res, aabb, n_levels, contraction, n_rays = sc[:6]
+        sat = sc[6] if len(sc) > 6 else None
         _check(bits, torch.int32, "scene bits")
+        _check(sat, torch.int16, "scene sat", optional=True)
         d = arr[k]
         d.bits = bits.data_ptr()
-        keep.append(bits)
+        d.sat = None if sat is None else sat.data_ptr()
+        keep.append((bits, sat))
         for j in range(3):
             d.res[j] = int(res[j])
         d.n_levels = int(n_levels)
@@ -252,6 +266,27 @@ def make_scenes(scenes) -> ctypes.Array:
         d.n_rays = int(n_rays)
     arr._keepalive = keep
     return arr
+
+
+def grid_sat_bytes(grid: Grid) -> int:
+    return int(load().nacc_grid_sat_bytes(ctypes.byref(grid)))
+
+
+def build_grid_sat(grid: Grid, sat: Optional[torch.Tensor] = None, stream=None, defer: bool = False):
+    """nacc_build_grid_sat: the summed-area table of the grid's bits (uint16 entries,
+    held in an int16 tensor), into ``sat`` or a new tensor, which is returned (with
+    ``defer``: the marshalled call, to run later)."""
+    n = grid_sat_bytes(grid) // 2
+    if n <= 0:
+        raise NaccError("invalid grid for a summed-area table")
+    if sat is None:
+        sat = torch.empty(n, dtype=torch.int16, device="cuda")
+    _check(sat, torch.int16, "sat", n)
+    run = _call("nacc_build_grid_sat", (ctypes.byref(grid), _ptr(sat), _stream(stream)), True)
+    if defer:
+        return run
+    run()
+    return sat
 
 
 def make_density_field(sigma: torch.Tensor, aabb: Sequence[float]) -> DensityField:

@@ -45,6 +45,12 @@ class OccupancyGrid:
         self.ema = torch.zeros(self.n_cells, dtype=torch.float32, device=device)
         self.bits = torch.zeros((self.n_cells + 31) // 32, dtype=torch.int32, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        # one-level grids keep the summed-area table of their bits, so marching takes
+        # the box walk; rebuilt after every update and whenever the bits tensor is
+        # modified by torch (its version counter moves)
+        self.use_sat = self.n_levels == 1 and not self.contraction
+        self.sat = None
+        self._sat_version = None
 
     @classmethod
     def from_bits(cls, bits: np.ndarray, res, aabb, n_levels=1, n_slots=1, device="cuda", contraction=0):
@@ -54,11 +60,32 @@ class OccupancyGrid:
         g.bits.copy_(torch.from_numpy(w))
         return g
 
-    def struct(self) -> _lib.Grid:
+    def _plain(self) -> _lib.Grid:
         s = getattr(self, "_struct", None)
         if s is None or s._keepalive is not self.bits:  # built once per bits tensor
             s = _lib.make_grid(self.bits, self.res, self.aabb, self.n_levels, self.n_slots, self.contraction)
             self._struct = s
+        return s
+
+    def _rebuild_sat(self):
+        g = self._plain()
+        if self.sat is None or self.sat.numel() * 2 != _lib.grid_sat_bytes(g):
+            self.sat = torch.empty(_lib.grid_sat_bytes(g) // 2, dtype=torch.int16, device=self.bits.device)
+            self._sat_struct = None
+        _lib.build_grid_sat(g, self.sat)
+        self._sat_version = (id(self.bits), self.bits._version)
+
+    def struct(self) -> _lib.Grid:
+        """The nacc_grid of this grid (with its summed-area table when it keeps one)."""
+        if not self.use_sat:
+            return self._plain()
+        if self._sat_version != (id(self.bits), self.bits._version):
+            self._rebuild_sat()
+        s = getattr(self, "_sat_struct", None)
+        if s is None or s._keepalive is not self.bits or s._keepalive_sat is not self.sat:
+            s = _lib.make_grid(self.bits, self.res, self.aabb, self.n_levels, self.n_slots, self.contraction,
+                               sat=self.sat)
+            self._sat_struct = s
         return s
 
     def sample_cells(self, n: int, seed: int = 0, step: int = 0):
@@ -80,6 +107,8 @@ class OccupancyGrid:
         Sec. 2.1), applied by the library as the equivalent density threshold."""
         _lib.update_occupancy_grid(self.ema, self.bits, cells, sigmas, decay, thre, self.status,
                                    alpha_step=0.0 if alpha_step is None else float(alpha_step))
+        if self.use_sat:
+            self._rebuild_sat()
 
     def state_dict(self):
         return {"ema": self.ema.clone(), "bits": self.bits.clone(), "res": self.res, "aabb": self.aabb,

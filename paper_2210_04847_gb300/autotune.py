@@ -21,6 +21,7 @@ CANDIDATES = {
     "march_occupancy": (0, 1),
     "march_unroll": (0, 1),
     "march_coarse": (0, 1),
+    "march_box_tile": (0, 1),
     "prune_tile_rays": (2, 4, 6, 8, 12, 16, 24, 32),
     "prune_occupancy": (0, 1, 2),
     "prune_interleave": (2, 4),
@@ -118,6 +119,19 @@ def tune_hot_path(hp, sc, batch: int = 0, reps: int = 7, flush: Callable[[], Non
     rec.append(tk("march_occupancy", march))
     rec.append(tk("march_unroll", march))
     rec.append(tk("march_coarse", march))
+    if hp.sat_ok:  # the box walk (summed-area table) against the walks above
+        # the table is rebuilt at every grid update, once per step: charge that to the box walk
+        build = hp.sat_rebuild_call()
+        times = {}
+        for use in (True, False):
+            hp.use_sat = use
+            times[int(use)] = time_ms((lambda: (march(), build())) if use else march, reps=reps, before=flush)
+        hp.use_sat = times[1] <= times[0]
+        rec.append({"knob": "march_sat", "best": int(hp.use_sat), "ms": {str(k): round(v, 4) for k, v in times.items()},
+                    "note": "1: march plus the table's rebuild; 0: march"})
+        if hp.use_sat:
+            rec.append(tk("march_box_tile", march))
+            rec.append(tk("march_tile_rays", march))  # the box walks favour other tile sizes
     march()
     M = int(hp.n_m.item())
     sc.field_marched(hp, batch, M)

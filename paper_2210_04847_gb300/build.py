@@ -30,7 +30,8 @@ COMMON = ARCH + [
 NO_FMAD = {"march.cu", "prune.cu", "fused.cu"}
 
 LIBS = {
-    "libnacc.so": ["march.cu", "march_static.cu", "fused.cu", "prune.cu", "render.cu", "grid.cu", "device.cu"],
+    "libnacc.so": ["march.cu", "march_static.cu", "fused.cu", "prune.cu", "render.cu", "grid.cu", "sat.cu",
+                   "device.cu"],
     "libnacc_field.so": ["field.cu"],
 }
 

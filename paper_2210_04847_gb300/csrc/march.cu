@@ -53,11 +53,133 @@ __device__ __forceinline__ unsigned level0_word(const G& g, float x0, float x1, 
     return in ? __ldg(g.bits() + (cell >> 5)) : 0u;
 }
 
+// Box test of the walks that use a grid's summed-area table. Every cell index
+// along each axis is a monotone function of the lattice index k (t_k, the
+// midpoints and the rounded index arithmetic all are), so the cells of the points
+// between two points lie in the box their cells span (indices clamped to
+// [-1, res]). If every cell of that box is inside the grid and occupied, every
+// point between is occupied; if no in-grid cell of the box is occupied, none is
+// (points outside the grid are empty). The table gives the box's count from eight
+// entries, exactly when the box has fewer than 2^16 cells.
+
+// Clamped cell indices of point x of the level-0 grid.
+template <typename G>
+__device__ __forceinline__ void clamped_cell(const G& g, float x0, float x1, float x2, int& i0, int& i1, int& i2) {
+    i0 = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x0, g.lo(0, 0)), g.scale(0, 0))), -1), g.res0());
+    i1 = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x1, g.lo(0, 1)), g.scale(0, 1))), -1), g.res1());
+    i2 = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x2, g.lo(0, 2)), g.scale(0, 2))), -1), g.res2());
+}
+
+// Decides the box spanned by cells (i0, i1, i2) and (n0, n1, n2) of grid slot
+// sl0: full (all inside and occupied), empty (no in-grid cell occupied), or
+// neither (undecided: test the points).
+template <typename G>
+__device__ __forceinline__ void box_decide(const G& g, unsigned sl0, int i0, int i1, int i2, int n0, int n1, int n2,
+                                           bool& full, bool& empty) {
+    const int r0 = g.res0(), r1 = g.res1(), r2 = g.res2();
+    const int lo0 = min(i0, n0), hi0 = max(i0, n0);
+    const int lo1 = min(i1, n1), hi1 = max(i1, n1);
+    const int lo2 = min(i2, n2), hi2 = max(i2, n2);
+    const bool inside = lo0 >= 0 && lo1 >= 0 && lo2 >= 0 && hi0 < r0 && hi1 < r1 && hi2 < r2;
+    // in-grid part of the box: corners [a, b) per axis
+    const int a0 = max(lo0, 0), a1 = max(lo1, 0), a2 = max(lo2, 0);
+    const int b0 = min(hi0, r0 - 1) + 1, b1 = min(hi1, r1 - 1) + 1, b2 = min(hi2, r2 - 1) + 1;
+    full = empty = false;
+    if (b0 <= a0 || b1 <= a1 || b2 <= a2) {
+        empty = true;  // no point lies inside the grid
+        return;
+    }
+    const unsigned long long vol =
+        (unsigned long long)(b0 - a0) * (unsigned long long)(b1 - a1) * (unsigned long long)(b2 - a2);
+    if (vol >= 65536ull) return;
+    const unsigned sy = (unsigned)(r2 + 1), sx = (unsigned)(r1 + 1) * sy;  // corner strides
+    const uint16_t* t = g.sat() + sl0 * sx * (unsigned)(r0 + 1);
+    const unsigned xa = (unsigned)a0 * sx, xb = (unsigned)b0 * sx, ya = (unsigned)a1 * sy, yb = (unsigned)b1 * sy;
+    const unsigned za = (unsigned)a2, zb = (unsigned)b2;
+    const unsigned cnt = ((unsigned)__ldg(t + xb + yb + zb) - (unsigned)__ldg(t + xa + yb + zb) -
+                          (unsigned)__ldg(t + xb + ya + zb) - (unsigned)__ldg(t + xb + yb + za) +
+                          (unsigned)__ldg(t + xa + ya + zb) + (unsigned)__ldg(t + xa + yb + za) +
+                          (unsigned)__ldg(t + xb + ya + za) - (unsigned)__ldg(t + xa + ya + za)) &
+                         0xffffu;
+    empty = cnt == 0u;
+    full = inside && cnt == (unsigned)vol;
+}
+
+// Box walk of one ray (a one-level grid with its table; shared lattices): lane j
+// takes the first point of chunk grp + j (31 chunks per group) and the box up to
+// the next chunk's first point (the lattice's last point for the last chunk);
+// chunks whose box is full or empty take their ballot word from it, the others
+// are tested point by point. Writes row[0 .. max_ch) and returns the sample
+// count (summed over the warp).
+template <bool CONE, typename G>
+__device__ __forceinline__ int walk_box(const MarchArgs& a, const G& g, const float o[3], const float d[3],
+                                        float near, float far, int nk, int max_ch, unsigned sl0, uint32_t* row,
+                                        int lane) {
+    const float dt = a.dt_min;
+    int part = 0, count = 0;
+    for (int grp = 0; grp < max_ch; grp += 31) {
+        const int kp = min((grp + lane) << 5, nk - 1);
+        float ts, tn;
+        if (!CONE) {
+            const float kf = __int2float_rn(kp);
+            ts = __fadd_rn(near, __fmul_rn(kf, dt));
+            tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+        } else {
+            ts = __ldg(a.cone_table + min(kp, a.max_steps));
+            tn = __ldg(a.cone_table + min(kp + 1, a.max_steps));
+        }
+        const float te = tn < far ? tn : far;
+        const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
+        int i0, i1, i2;
+        clamped_cell(g, __fadd_rn(o[0], __fmul_rn(d[0], mid)), __fadd_rn(o[1], __fmul_rn(d[1], mid)),
+                     __fadd_rn(o[2], __fmul_rn(d[2], mid)), i0, i1, i2);
+        const int n0 = __shfl_down_sync(FULL, i0, 1);
+        const int n1 = __shfl_down_sync(FULL, i1, 1);
+        const int n2 = __shfl_down_sync(FULL, i2, 1);
+        const int c = grp + lane;
+        const bool exists = lane < 31 && c < max_ch;
+        bool full = false, empty = false;
+        if (exists) box_decide(g, sl0, i0, i1, i2, n0, n1, n2, full, empty);
+        if (full || empty) {
+            const int n = min(32, nk - (c << 5));
+            const uint32_t m = full ? (n >= 32 ? ~0u : (1u << n) - 1u) : 0u;
+            row[c] = m;
+            part += __popc(m);
+        }
+        unsigned pend = __ballot_sync(FULL, exists && !full && !empty);
+        while (pend) {
+            const int cc = grp + __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int k = (cc << 5) + lane;
+            float ks, kn;
+            if (!CONE) {
+                const float kf = __int2float_rn(k);
+                ks = __fadd_rn(near, __fmul_rn(kf, dt));
+                kn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+            } else {
+                ks = __ldg(a.cone_table + min(k, a.max_steps));
+                kn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+            }
+            bool occ = false;
+            if (k < nk) {
+                const float ke = kn < far ? kn : far;
+                const float km = __fmul_rn(__fadd_rn(ks, ke), 0.5f);
+                occ = occupied_in<1>(g, __fadd_rn(o[0], __fmul_rn(d[0], km)), __fadd_rn(o[1], __fmul_rn(d[1], km)),
+                                     __fadd_rn(o[2], __fmul_rn(d[2], km)), sl0);
+            }
+            const unsigned m = __ballot_sync(FULL, occ);
+            if (lane == 0) row[cc] = m;
+            count += __popc(m);
+        }
+    }
+    return count + __reduce_add_sync(FULL, part);
+}
+
 // One ray, all 32 lanes: one ballot word per 32 lattice points into row[c].
 // count = samples, nch = ballot words written (row[0..nch)).
 // COARSE (shared lattices): first one point every 32 per lane, and chunks that
 // lie in a single cell take their word from one occupancy test (see below).
-template <int MAXL, bool CONE, bool UNROLL2, bool COARSE, typename G>
+template <int MAXL, bool CONE, bool UNROLL2, bool COARSE, int BOX, typename G>
 __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, const float o[3], const float d[3],
                                              float near, float far, unsigned sl0, uint32_t* row, float* lat, int lane,
                                              int& count_out, int& nch_out, int& pts_out) {
@@ -73,6 +195,13 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, con
     const int max_ch = min((nk + 31) >> 5, a.mask_words);
     int count = 0, nch = 0;
     pts_out = shared ? nk : 0;  // own cone lattices are counted as they are walked
+    if constexpr (BOX != 0 && MAXL == 1) {
+        if (shared && g.sat()) {
+            count_out = max_ch > 0 ? walk_box<CONE>(a, g, o, d, near, far, nk, max_ch, sl0, row, lane) : 0;
+            nch_out = max_ch;
+            return;
+        }
+    }
     if (COARSE && MAXL > 0 && shared) {  // contracted indices are not monotone along a ray
         // Every cell index along each axis, at each level, is a monotone function
         // of k (t_k, the midpoints and the rounded index arithmetic all are), and so
@@ -307,6 +436,122 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, con
     nch_out = nch;
 }
 
+// Point k of a uniform lattice: its midpoint's position.
+__device__ __forceinline__ void uniform_midpoint(float near, float far, float dt, int k, float o0, float o1,
+                                                 float o2, float d0, float d1, float d2, float& x0, float& x1,
+                                                 float& x2) {
+    const float kf = __int2float_rn(k);
+    const float ts = __fadd_rn(near, __fmul_rn(kf, dt));
+    const float tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+    const float te = tn < far ? tn : far;
+    const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
+    x0 = __fadd_rn(o0, __fmul_rn(d0, mid));
+    x1 = __fadd_rn(o1, __fmul_rn(d1, mid));
+    x2 = __fadd_rn(o2, __fmul_rn(d2, mid));
+}
+
+// Phase 1 of a tile for the box walk with uniform steps on one grid: the whole
+// tile at once. Lane i clips ray i and sizes its lattice; the tile's chunks then
+// form one list, ray after ray, taken 32 at a time: lane j evaluates the first
+// point of its chunk and the point after the chunk (the next chunk's first, or
+// the lattice's last) and decides the chunk from the box of the two cells. The
+// chunks left undecided are tested point by point by the whole warp. The ray
+// loads and the table loads of 32 chunks are in flight together, instead of a
+// few dependent round trips per ray.
+__device__ __forceinline__ void box_tile_uniform(const MarchArgs& a, int ray0, int nr, uint32_t* wmask, int lane,
+                                                 int& my_count, int& my_nch, float& my_near, float& my_far,
+                                                 int& tile_pts) {
+    const ArgGeom g{a};
+    const float dt = a.dt_min;
+    float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f, d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, near = 0.0f, far = 0.0f;
+    int nk = 0;
+    unsigned sl0 = 0;
+    if (lane < nr) {
+        const int r = ray0 + lane;
+        float o[3], d[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            o[k] = __ldg(a.rays_o + 3 * (size_t)r + k);
+            d[k] = __ldg(a.rays_d + 3 * (size_t)r + k);
+        }
+        const int slot = slot_of(a, r);
+        if (slot >= 0 && slot < a.n_slots) {
+            sl0 = (unsigned)slot * (unsigned)a.n_levels;
+            if (clip_ray_in<false>(a, g, o, d, near, far)) nk = lattice_count(a, near, far, dt);
+        } else {
+            raise_status(a.d_status, NACC_STATUS_BAD_INDEX);
+        }
+        o0 = o[0], o1 = o[1], o2 = o[2], d0 = d[0], d1 = d[1], d2 = d[2];
+    }
+    const int nch = min((nk + 31) >> 5, a.mask_words);
+    const int incl = warp_incl_scan_int(nch, lane);  // lanes past the tile's rays add 0
+    const int start = incl - nch;
+    const int total = __shfl_sync(FULL, incl, 31);
+    for (int f0 = 0; f0 < total; f0 += 32) {
+        const int f = f0 + lane;
+        const bool valid = f < total;
+        int ri = 0;  // the ray of chunk f: the last ray whose chunks start at or before f
+        for (int q = 1; q < nr; ++q)
+            if (__shfl_sync(FULL, start, q) <= f) ri = q;
+        const float r_o0 = __shfl_sync(FULL, o0, ri), r_o1 = __shfl_sync(FULL, o1, ri);
+        const float r_o2 = __shfl_sync(FULL, o2, ri), r_d0 = __shfl_sync(FULL, d0, ri);
+        const float r_d1 = __shfl_sync(FULL, d1, ri), r_d2 = __shfl_sync(FULL, d2, ri);
+        const float r_near = __shfl_sync(FULL, near, ri), r_far = __shfl_sync(FULL, far, ri);
+        const int r_nk = __shfl_sync(FULL, nk, ri), r_start = __shfl_sync(FULL, start, ri);
+        const unsigned r_sl0 = __shfl_sync(FULL, sl0, ri);
+        const int c = f - r_start;
+        const int ka = c << 5, kb = min(ka + 32, r_nk - 1);
+        bool full = false, empty = false;
+        if (valid) {
+            float x0, x1, x2;
+            int i0, i1, i2, n0, n1, n2;
+            uniform_midpoint(r_near, r_far, dt, ka, r_o0, r_o1, r_o2, r_d0, r_d1, r_d2, x0, x1, x2);
+            clamped_cell(g, x0, x1, x2, i0, i1, i2);
+            uniform_midpoint(r_near, r_far, dt, kb, r_o0, r_o1, r_o2, r_d0, r_d1, r_d2, x0, x1, x2);
+            clamped_cell(g, x0, x1, x2, n0, n1, n2);
+            box_decide(g, r_sl0, i0, i1, i2, n0, n1, n2, full, empty);
+            if (full || empty) {
+                const int n = min(32, r_nk - ka);
+                wmask[ri * a.row_stride + c] = full ? (n >= 32 ? ~0u : (1u << n) - 1u) : 0u;
+            }
+        }
+        unsigned pend = __ballot_sync(FULL, valid && !full && !empty);
+        while (pend) {
+            const int p = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int pri = __shfl_sync(FULL, ri, p), pc = __shfl_sync(FULL, c, p);
+            const float p_o0 = __shfl_sync(FULL, o0, pri), p_o1 = __shfl_sync(FULL, o1, pri);
+            const float p_o2 = __shfl_sync(FULL, o2, pri), p_d0 = __shfl_sync(FULL, d0, pri);
+            const float p_d1 = __shfl_sync(FULL, d1, pri), p_d2 = __shfl_sync(FULL, d2, pri);
+            const float p_near = __shfl_sync(FULL, near, pri), p_far = __shfl_sync(FULL, far, pri);
+            const int p_nk = __shfl_sync(FULL, nk, pri);
+            const unsigned p_sl0 = __shfl_sync(FULL, sl0, pri);
+            const int k = (pc << 5) + lane;
+            bool occ = false;
+            if (k < p_nk) {
+                float x0, x1, x2;
+                uniform_midpoint(p_near, p_far, dt, k, p_o0, p_o1, p_o2, p_d0, p_d1, p_d2, x0, x1, x2);
+                occ = occupied_in<1>(g, x0, x1, x2, p_sl0);
+            }
+            const unsigned m = __ballot_sync(FULL, occ);
+            if (lane == 0) wmask[pri * a.row_stride + pc] = m;
+        }
+    }
+    __syncwarp();
+    for (int i = 0; i < nr; ++i) {  // samples per ray from its finished row
+        const int n_i = __shfl_sync(FULL, nch, i);
+        const uint32_t* row = wmask + i * a.row_stride;
+        int part = 0;
+        for (int w = lane; w < n_i; w += 32) part += __popc(row[w]);
+        const int cnt = __reduce_add_sync(FULL, part);
+        if (lane == i) my_count = cnt;
+    }
+    my_nch = nch;
+    my_near = near;
+    my_far = far;
+    tile_pts = __reduce_add_sync(FULL, nk);
+}
+
 // ---------------------------------------------------------------------------
 // phases 2 and 3 of a tile (shared by both phase-1 strategies)
 // ---------------------------------------------------------------------------
@@ -364,6 +609,52 @@ __device__ __forceinline__ void finish_tile(const MarchArgs& a, const uint32_t* 
         const int r = ray0 + i;
         const uint32_t* row = wmask + i * a.row_stride;
         unsigned base = (unsigned)excl + (unsigned)__shfl_sync(FULL, my_excl, i);
+        if (shared) {
+            // a shared lattice: four chunks' words read before any is used, so the
+            // shared-memory reads overlap the stores of the chunks before; a full
+            // word (most chunks) stores lane l at base + l; when the whole ray lands
+            // below capacity no store checks it
+            const bool fits = (unsigned long long)base + (unsigned)cnt <= (unsigned long long)cap;
+            for (int c0 = 0; c0 < nch; c0 += 4) {
+                uint32_t m4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) m4[u] = c0 + u < nch ? row[c0 + u] : 0u;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned m = m4[u];
+                    if (m == 0u) continue;
+                    const int k = ((c0 + u) << 5) + lane;
+                    float ts, tn;
+                    if (!CONE) {
+                        const float kf = __int2float_rn(k);
+                        ts = __fadd_rn(near, __fmul_rn(kf, dt));
+                        tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+                    } else {
+                        ts = __ldg(a.cone_table + min(k, a.max_steps));
+                        tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                    }
+                    const float te = tn < far ? tn : far;
+                    if (m == ~0u) {
+                        const unsigned pos = base + (unsigned)lane;
+                        if (fits || pos < cap) {
+                            a.t_starts[pos] = ts;
+                            a.t_ends[pos] = te;
+                            a.ray_indices[pos] = r;
+                        }
+                        base += 32u;
+                    } else {
+                        const unsigned pos = base + __popc(m & lt);
+                        if (((m >> lane) & 1u) && (fits || pos < cap)) {
+                            a.t_starts[pos] = ts;
+                            a.t_ends[pos] = te;
+                            a.ray_indices[pos] = r;
+                        }
+                        base += __popc(m);
+                    }
+                }
+            }
+            continue;
+        }
         float tcur = near;
         for (int c = 0; c < nch; ++c) {
             const unsigned m = row[c];
@@ -425,7 +716,10 @@ __device__ __forceinline__ void load_scene(const MarchArgs& a, int scene, SceneG
 // waits for the offset of the tile it did before (whose rows sit in the other
 // half of the warp's shared memory), so the look-back rarely stalls.
 // BATCHED: every ray looks up its scene's own grid (nacc_march_rays_batched).
-template <int MAXL, int MINB, bool CONE, bool UNROLL2 = false, bool COARSE = false, bool BATCHED = false>
+// BOX: 0 no table; 1 the box walk ray by ray; 2 the whole tile's chunks at once
+// (uniform steps, one grid; otherwise as 1).
+template <int MAXL, int MINB, bool CONE, bool UNROLL2 = false, bool COARSE = false, bool BATCHED = false,
+          int BOX = 0>
 __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const MarchArgs a) {
     extern __shared__ uint32_t s_masks[];  // per warp: 2 x [tile_rays][row_stride]
     __shared__ float s_lat[kWarps][36];    // cone steps with a ray-specific start
@@ -454,7 +748,10 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
             int my_count = 0, my_nch = 0;
             float my_near = 0.0f, my_far = 0.0f;
             int tile_pts = 0;  // at most tile_rays * max_steps
-            for (int i = 0; i < cur.nr; ++i) {
+            constexpr bool kTileBox = BOX == 2 && !CONE && !BATCHED && MAXL == 1;
+            if constexpr (kTileBox)
+                box_tile_uniform(a, cur.ray0, cur.nr, wmask, lane, my_count, my_nch, my_near, my_far, tile_pts);
+            for (int i = 0; i < (kTileBox ? 0 : cur.nr); ++i) {
                 const int r = cur.ray0 + i;
                 float o[3], d[3];
 #pragma unroll
@@ -474,12 +771,12 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
                     if constexpr (MAXL <= 1) {
                         const RegGeom g(s_scene[warp]);
                         if (clip_ray_in<MAXL == 0>(a, g, o, d, near, far))
-                            walk_lattice<MAXL, CONE, UNROLL2, COARSE>(a, g, o, d, near, far, 0u, row, lat, lane,
+                            walk_lattice<MAXL, CONE, UNROLL2, COARSE, BOX>(a, g, o, d, near, far, 0u, row, lat, lane,
                                                                       count, nch, pts);
                     } else {
                         const SmemGeom g{&s_scene[warp]};
                         if (clip_ray_in<false>(a, g, o, d, near, far))
-                            walk_lattice<MAXL, CONE, UNROLL2, COARSE>(a, g, o, d, near, far, 0u, row, lat, lane,
+                            walk_lattice<MAXL, CONE, UNROLL2, COARSE, BOX>(a, g, o, d, near, far, 0u, row, lat, lane,
                                                                       count, nch, pts);
                     }
                 } else {
@@ -488,7 +785,7 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
                     if (!slot_ok && lane == 0) raise_status(a.d_status, NACC_STATUS_BAD_INDEX);
                     const ArgGeom g{a};
                     if (slot_ok && clip_ray_in<MAXL == 0>(a, g, o, d, near, far))
-                        walk_lattice<MAXL, CONE, UNROLL2, COARSE>(a, g, o, d, near, far,
+                        walk_lattice<MAXL, CONE, UNROLL2, COARSE, BOX>(a, g, o, d, near, far,
                                                                   (unsigned)slot * (unsigned)a.n_levels, row, lat,
                                                                   lane, count, nch, pts);
                 }
@@ -586,11 +883,42 @@ __global__ void scene_upload_kernel(const __grid_constant__ SceneUpload u) {
     if (threadIdx.x < u.count) u.dst_end[u.first + threadIdx.x] = u.end[threadIdx.x];
 }
 
-// Batched variants: the uniform or cone walk, no two-chunk unrolling or coarse pass.
-template <int MAXL, int MINB>
+// Batched variants: the uniform or cone walk, no two-chunk unrolling or coarse
+// pass; one-level scenes with summed-area tables take the box walk.
+template <int MAXL, int MINB, int BOX = 0>
 void launch_batched(bool cone, size_t smem, int need, cudaStream_t st, const MarchArgs& a) {
-    if (cone) launch_uniform(march_uniform_kernel<MAXL, MINB, true, false, false, true>, smem, need, st, a);
-    else launch_uniform(march_uniform_kernel<MAXL, MINB, false, false, false, true>, smem, need, st, a);
+    if (cone) launch_uniform(march_uniform_kernel<MAXL, MINB, true, false, false, true, BOX>, smem, need, st, a);
+    else launch_uniform(march_uniform_kernel<MAXL, MINB, false, false, false, true, BOX>, smem, need, st, a);
+}
+
+// Resident blocks per SM the box walks are compiled for (their registers fit
+// without spills).
+constexpr int kBoxMinBlocks = 4;
+constexpr int kBoxTileMinBlocks = 4;
+constexpr int kBoxBatchedMinBlocks = 3;
+
+// One-level grid with its summed-area table: the box walk, ray by ray or (uniform
+// steps, tuning knob) the whole tile's chunks at once.
+void launch_box(bool cone, bool tile, size_t smem, int need, cudaStream_t st, const MarchArgs& a) {
+    if (cone)
+        launch_uniform(march_uniform_kernel<1, kBoxMinBlocks, true, false, false, false, 1>, smem, need, st, a);
+    else if (tile)
+        launch_uniform(march_uniform_kernel<1, kBoxTileMinBlocks, false, false, false, false, 2>, smem, need, st, a);
+    else
+        launch_uniform(march_uniform_kernel<1, kBoxMinBlocks, false, false, false, false, 1>, smem, need, st, a);
+}
+
+// A scene's grid as a one-slot nacc_grid.
+nacc_grid grid_of(const nacc_scene_desc& d) {
+    nacc_grid g;
+    g.bits = d.bits;
+    for (int k = 0; k < 3; ++k) g.res[k] = d.res[k];
+    g.n_levels = d.n_levels;
+    g.n_slots = 1;
+    for (int k = 0; k < 6; ++k) g.aabb[k] = d.aabb[k];
+    g.contraction = d.contraction;
+    g.sat = d.sat;
+    return g;
 }
 
 size_t batched_table_bytes(int32_t n_scenes) {
@@ -602,7 +930,7 @@ size_t batched_table_bytes(int32_t n_scenes) {
 // pointers, the cone table prologue, and the walk's launch.
 int march_launch(MarchArgs& a, const nacc_march_params* p, int32_t* packed_info, float* t_starts, float* t_ends,
                  int32_t* ray_indices, int64_t capacity, int64_t* n_samples, int32_t* d_status, void* workspace,
-                 cudaStream_t st, bool batched) {
+                 cudaStream_t st, bool batched, bool box) {
     a.packed_info = packed_info;
     a.t_starts = t_starts;
     a.t_ends = t_ends;
@@ -633,9 +961,14 @@ int march_launch(MarchArgs& a, const nacc_march_params* p, int32_t* packed_info,
         // one level in registers fits 4 blocks of 256 threads per SM like the
         // single-grid walk; cascades and contracted space run uncapped
         if (a.contract) launch_batched<0, 1>(cone, smem, need, st, a);
+        else if (a.n_levels == 1 && box) launch_batched<1, kBoxBatchedMinBlocks, 1>(cone, smem, need, st, a);
         else if (a.n_levels == 1) launch_batched<1, 4>(cone, smem, need, st, a);
         else if (a.n_levels <= 4) launch_batched<4, 1>(cone, smem, need, st, a);
         else launch_batched<NACC_MAX_LEVELS, 1>(cone, smem, need, st, a);
+        return launch_status(cudaGetLastError());
+    }
+    if (box && !a.contract && a.n_levels == 1) {
+        launch_box(cone, tune_get(NACC_TUNE_MARCH_BOX_TILE) != 0, smem, need, st, a);
         return launch_status(cudaGetLastError());
     }
     const bool unroll = tune_get(NACC_TUNE_MARCH_UNROLL) != 0;
@@ -676,7 +1009,7 @@ extern "C" int nacc_march_rays(const float* rays_o, const float* rays_d, const f
     cudaStream_t st = (cudaStream_t)stream;
     if (n_rays == 0) return launch_status(cudaMemsetAsync(n_samples, 0, sizeof(int64_t), st));
     return march_launch(a, p, packed_info, t_starts, t_ends, ray_indices, capacity, n_samples, d_status, workspace,
-                        st, false);
+                        st, false, grid->sat != nullptr);
 }
 
 extern "C" size_t nacc_march_batched_workspace_size(int32_t n_scenes, int32_t n_rays,
@@ -696,21 +1029,21 @@ extern "C" int nacc_march_rays_batched(const nacc_scene_desc* scenes, int32_t n_
     // every scene: a valid grid of its own, its consecutive rays; one contraction mode
     long long total = 0;
     int max_levels = 1, first_with_rays = -1;
+    bool any_sat = false;
     for (int s = 0; s < n_scenes; ++s) {
         const nacc_scene_desc& d = scenes[s];
-        nacc_grid g{d.bits, {d.res[0], d.res[1], d.res[2]}, d.n_levels, 1,
-                    {d.aabb[0], d.aabb[1], d.aabb[2], d.aabb[3], d.aabb[4], d.aabb[5]}, d.contraction};
+        const nacc_grid g = grid_of(d);
         if (check_grid(&g) != NACC_OK || d.n_rays < 0) return NACC_ERR_INVALID_ARG;
         if (d.contraction != scenes[0].contraction) return NACC_ERR_INVALID_ARG;
         if (d.n_rays > 0 && !d.bits) return NACC_ERR_INVALID_ARG;
         if (d.n_rays > 0 && first_with_rays < 0) first_with_rays = s;
+        any_sat = any_sat || d.sat != nullptr;
         max_levels = d.n_levels > max_levels ? d.n_levels : max_levels;
         total += d.n_rays;
     }
     if (total != n_rays) return NACC_ERR_INVALID_ARG;
     const nacc_scene_desc& d0 = scenes[first_with_rays < 0 ? 0 : first_with_rays];
-    nacc_grid g0{d0.bits, {d0.res[0], d0.res[1], d0.res[2]}, d0.n_levels, 1,
-                 {d0.aabb[0], d0.aabb[1], d0.aabb[2], d0.aabb[3], d0.aabb[4], d0.aabb[5]}, d0.contraction};
+    const nacc_grid g0 = grid_of(d0);
     MarchArgs a;
     const int setup = march_setup(rays_o, rays_d, nullptr, nullptr, n_rays, &g0, p, a);
     if (setup != NACC_OK) return setup;
@@ -734,9 +1067,7 @@ extern "C" int nacc_march_rays_batched(const nacc_scene_desc* scenes, int32_t n_
         u.count = n_scenes - s0 < kSceneChunk ? n_scenes - s0 : kSceneChunk;
         for (int j = 0; j < u.count; ++j) {
             const nacc_scene_desc& d = scenes[s0 + j];
-            nacc_grid g{d.bits, {d.res[0], d.res[1], d.res[2]}, d.n_levels, 1,
-                        {d.aabb[0], d.aabb[1], d.aabb[2], d.aabb[3], d.aabb[4], d.aabb[5]}, d.contraction};
-            scene_geom_for(g, u.g[j]);
+            scene_geom_for(grid_of(d), u.g[j]);
             end += d.n_rays;
             u.end[j] = end;
         }
@@ -748,5 +1079,5 @@ extern "C" int nacc_march_rays_batched(const nacc_scene_desc* scenes, int32_t n_
     a.n_levels = max_levels;
     a.contract = scenes[0].contraction;
     return march_launch(a, p, packed_info, t_starts, t_ends, ray_indices, capacity, n_samples, d_status, workspace,
-                        st, true);
+                        st, true, any_sat);
 }

@@ -31,11 +31,12 @@ struct Levels {
 // the same float32 operations as a single grid's.
 struct SceneGeom {
     const uint32_t* bits;
+    const uint16_t* sat;  // summed-area table of bits, or null
     int32_t res[3];
     int32_t n_levels;
     Levels L;
     float cc[3], inv_h[3], qres[3];
-    int32_t pad[3];
+    int32_t pad;
 };
 static_assert(sizeof(SceneGeom) % 16 == 0, "scene table entries stay 16-byte aligned");
 
@@ -72,6 +73,7 @@ struct MarchArgs {
     float qres[3];            // contraction: res / 4 (the grid spans [-2, 2])
     float inv_dt;             // 1 / dt_min, for the first guess of a uniform lattice's length
     LookbackHooks hooks;      // look-back poll budget (test hooks)
+    const uint16_t* sat;      // summed-area table of the grid's bits, or null
     const SceneGeom* scenes;  // batch of scenes with their own grids (else null)
     const int32_t* scene_end; // exclusive end of each scene's consecutive rays
     int32_t n_scenes;
@@ -101,6 +103,7 @@ struct ArgGeom {
     __device__ __forceinline__ int res2() const { return a.res2; }
     __device__ __forceinline__ int n_levels() const { return a.n_levels; }
     __device__ __forceinline__ const uint32_t* bits() const { return a.bits; }
+    __device__ __forceinline__ const uint16_t* sat() const { return a.sat; }
 };
 
 struct SmemGeom {
@@ -117,6 +120,7 @@ struct SmemGeom {
     __device__ __forceinline__ int res2() const { return g->res[2]; }
     __device__ __forceinline__ int n_levels() const { return g->n_levels; }
     __device__ __forceinline__ const uint32_t* bits() const { return g->bits; }
+    __device__ __forceinline__ const uint16_t* sat() const { return g->sat; }
 };
 
 // One level (or contracted space) in registers, loaded once per ray.
@@ -124,6 +128,7 @@ struct RegGeom {
     float lo_[3], scale_[3], blo_[3], bhi_[3], cc_[3], ih_[3], q_[3];
     int r_[3];
     const uint32_t* b_;
+    const uint16_t* sat_;
     __device__ __forceinline__ explicit RegGeom(const SceneGeom& s) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -137,6 +142,7 @@ struct RegGeom {
             r_[k] = s.res[k];
         }
         b_ = s.bits;
+        sat_ = s.sat;
     }
     __device__ __forceinline__ float lo(int, int k) const { return lo_[k]; }
     __device__ __forceinline__ float scale(int, int k) const { return scale_[k]; }
@@ -150,6 +156,7 @@ struct RegGeom {
     __device__ __forceinline__ int res2() const { return r_[2]; }
     __device__ __forceinline__ int n_levels() const { return 1; }
     __device__ __forceinline__ const uint32_t* bits() const { return b_; }
+    __device__ __forceinline__ const uint16_t* sat() const { return sat_; }
 };
 
 __device__ __forceinline__ bool finite32(float v) { return fabsf(v) <= 3.402823466e+38f; }
@@ -421,6 +428,9 @@ int check_grid(const nacc_grid* grid) {
     if (grid->res[0] > (1 << 22) || grid->res[1] > (1 << 22) || grid->res[2] > (1 << 22)) return NACC_ERR_INVALID_ARG;
     const long long cells = (long long)grid->res[0] * grid->res[1] * grid->res[2] * grid->n_levels * grid->n_slots;
     if (cells >= (1LL << 31)) return NACC_ERR_INVALID_ARG;
+    const long long corners = (grid->res[0] + 1LL) * (grid->res[1] + 1LL) * (grid->res[2] + 1LL) * grid->n_levels *
+                              grid->n_slots;  // entries of the summed-area table
+    if (grid->sat && (corners >= (1LL << 31) || ((uintptr_t)grid->sat & 1u))) return NACC_ERR_INVALID_ARG;
     for (int k = 0; k < 6; ++k)
         if (!(fabsf(grid->aabb[k]) < INFINITY)) return NACC_ERR_INVALID_ARG;
     for (int k = 0; k < 3; ++k)
@@ -442,6 +452,7 @@ void contraction_consts(const nacc_grid& grid, float cc[3], float inv_h[3], floa
 void scene_geom_for(const nacc_grid& grid, SceneGeom& g) {
     memset(&g, 0, sizeof(g));
     g.bits = grid.bits;
+    g.sat = grid.sat;
     for (int k = 0; k < 3; ++k) g.res[k] = grid.res[k];
     g.n_levels = grid.n_levels;
     make_levels(grid, g.L);
@@ -467,6 +478,7 @@ int march_setup(const float* rays_o, const float* rays_d, const float* ray_time,
     a.ray_slot = ray_slot;
     a.n_rays = n_rays;
     a.bits = grid->bits;
+    a.sat = grid->sat;
     a.res0 = grid->res[0];
     a.res1 = grid->res[1];
     a.res2 = grid->res[2];

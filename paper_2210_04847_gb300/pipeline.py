@@ -65,6 +65,14 @@ class HotPath:
         self.ema = torch.zeros(self.n_cells, dtype=torch.float32, device=device)
         self.params = _lib.make_params(w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone, w.max_steps)
         self.grid = _lib.make_grid(self.bits, w.res, w.aabb, w.n_levels, w.n_slots, w.contraction)
+        # one-level grids march with their summed-area table (the box walk);
+        # every grid update rebuilds the table of the bits it writes
+        self.sat_ok = w.n_levels == 1 and not w.contraction
+        self.use_sat = self.sat_ok
+        self.sat = _lib.build_grid_sat(self.grid) if self.sat_ok else None
+        self.grid_sat = (_lib.make_grid(self.bits, w.res, w.aabb, w.n_levels, w.n_slots, w.contraction, sat=self.sat)
+                         if self.sat_ok else self.grid)
+        self.upd_sat = None
         f32, i32 = torch.float32, torch.int32
         z = lambda n, dt=f32: torch.zeros(max(int(n), 1), dtype=dt, device=device)
         self.cap_m, self.cap_k = int(cap_marched), int(cap_kept)
@@ -94,7 +102,8 @@ class HotPath:
     # Each stage runs now, or with defer=True returns the marshalled call to run
     # later (so a timed region can start right before the C call).
     def march(self, rays_o, rays_d, ray_time=None, ray_slot=None, defer=False):
-        return _lib.march_rays(rays_o, rays_d, self.grid, self.params, self.pi_m, self.ts_m[: self.cap_m],
+        grid = self.grid_sat if self.use_sat else self.grid
+        return _lib.march_rays(rays_o, rays_d, grid, self.params, self.pi_m, self.ts_m[: self.cap_m],
                                self.te_m[: self.cap_m], self.ri_m[: self.cap_m], self.n_m, self.status, self.ws_march,
                                ray_time=ray_time, ray_slot=ray_slot, defer=defer)
 
@@ -129,10 +138,38 @@ class HotPath:
                                           defer=defer)
         return (lambda: None) if defer else None
 
+    def sat_rebuild_call(self):
+        """The marshalled rebuild of the marched grid's summed-area table (what every
+        grid update adds when the path marches with the table)."""
+        return _lib.build_grid_sat(self.grid, self.sat, defer=True)
+
     def grid_update(self, decay=0.95, thre=0.01, bits=None, defer=False):
-        """EMA update of ``self.ema``; writes ``bits`` (default: the bitfield marched by this path)."""
-        return _lib.update_occupancy_grid(self.ema, self.bits if bits is None else bits, self.cells[: self.n_grid],
-                                          self.cell_sig[: self.n_grid], decay, thre, self.status, defer=defer)
+        """EMA update of ``self.ema``; writes ``bits`` (default: the bitfield marched by this
+        path) and, when the path marches with a summed-area table, rebuilds the table of
+        the bits written (into the marched table when ``bits`` is the marched bitfield)."""
+        out = self.bits if bits is None else bits
+        upd = _lib.update_occupancy_grid(self.ema, out, self.cells[: self.n_grid], self.cell_sig[: self.n_grid], decay,
+                                         thre, self.status, defer=True)
+        sat_call = lambda: None
+        if self.use_sat:
+            w = self.w
+            g = _lib.make_grid(out, w.res, w.aabb, w.n_levels, w.n_slots, w.contraction)
+            if out is self.bits:
+                target = self.sat
+            else:
+                if self.upd_sat is None:
+                    self.upd_sat = torch.empty_like(self.sat)
+                target = self.upd_sat
+            sat_call = _lib.build_grid_sat(g, target, defer=True)
+            sat_call._grid = g  # the call holds a pointer into g
+
+        def run():
+            upd()
+            sat_call()
+        if defer:
+            return run
+        run()
+        return None
 
     # -- user side (stand-in field, loss) ----------------------------------
     def field_marched(self, field: StandInField, rays_o, rays_d, n_marched, ray_time=None):

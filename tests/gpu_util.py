@@ -40,6 +40,11 @@ def gpu_march(w: synth.Workload, capacity=None, rays=None, n_levels=None):
     return _run_march(o, d, bits, w, params, ws, capacity)
 
 
+# When set (by a test fixture), marching calls carry the grid's summed-area table,
+# so one-level grids take the box walk.
+USE_SAT = False
+
+
 def _run_march(o, d, bits, w, params, ws, capacity):
     R = o.shape[0]
     packed = torch.full((R, 2), -7, dtype=torch.int32, device="cuda")
@@ -48,9 +53,12 @@ def _run_march(o, d, bits, w, params, ws, capacity):
     ri = torch.full((capacity,), -1, dtype=torch.int32, device="cuda")
     total = torch.full((1,), -1, dtype=torch.int64, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    _lib.march_rays(o, d, _lib.make_grid(bits, w.res, w.aabb, w.n_levels, w.n_slots, w.contraction), params, packed,
-                    ts, te, ri,
-                    total, status, ws, ray_time=dev(w.ray_time), ray_slot=dev(w.ray_slot))
+    grid = _lib.make_grid(bits, w.res, w.aabb, w.n_levels, w.n_slots, w.contraction)
+    if USE_SAT:
+        grid = _lib.make_grid(bits, w.res, w.aabb, w.n_levels, w.n_slots, w.contraction,
+                              sat=_lib.build_grid_sat(grid))
+    _lib.march_rays(o, d, grid, params, packed, ts, te, ri, total, status, ws, ray_time=dev(w.ray_time),
+                    ray_slot=dev(w.ray_slot))
     torch.cuda.synchronize()
     n = int(total.item())
     k = min(n, capacity)

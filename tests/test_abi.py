@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(libs):
 
 def test_version_and_error_strings(libs):
     lib, _ = libs
-    assert lib.nacc_version() == 200
+    assert lib.nacc_version() == 300
     assert lib.nacc_error_string(-1) == b"invalid argument"
     assert lib.nacc_error_string(12345) == b"unknown error code"
 
@@ -183,3 +183,29 @@ def test_batched_march_arguments_rejected_on_host(libs):
     assert call([]) == _lib.ERR_INVALID_ARG  # no scenes
     assert lib.nacc_march_batched_workspace_size(64, 1 << 18, ctypes.byref(p)) > \
         lib.nacc_march_workspace_size(1 << 18, ctypes.byref(p)) + 64 * 400
+
+
+def test_grid_sat_sizes_and_rejections(libs):
+    lib, _ = libs
+    g = _lib.Grid()
+    g.res[0], g.res[1], g.res[2] = 128, 96, 7
+    g.n_levels, g.n_slots = 2, 3
+    for k in range(3):
+        g.aabb[k], g.aabb[3 + k] = -1.0, 1.0
+    assert lib.nacc_grid_sat_bytes(ctypes.byref(g)) == 2 * 3 * 129 * 97 * 8 * 2
+    assert lib.nacc_build_grid_sat(ctypes.byref(g), ctypes.c_void_p(4096), None) == _lib.ERR_INVALID_ARG  # no bits
+    g.bits = 4096
+    assert lib.nacc_build_grid_sat(ctypes.byref(g), None, None) == _lib.ERR_INVALID_ARG  # no table
+    g.res[0] = 0
+    assert lib.nacc_grid_sat_bytes(ctypes.byref(g)) == 0
+    assert lib.nacc_build_grid_sat(ctypes.byref(g), ctypes.c_void_p(4096), None) == _lib.ERR_INVALID_ARG
+    g.res[0], g.res[1], g.res[2] = 1300, 1300, 1300  # corners over 2^31
+    g.n_levels, g.n_slots = 1, 1
+    assert lib.nacc_build_grid_sat(ctypes.byref(g), ctypes.c_void_p(4096), None) == _lib.ERR_INVALID_ARG
+    # marching rejects a table that is misaligned or whose grid has too many corners
+    p = _lib.make_params(0.0, 1e10, 0.01, None, 0.0, 64)
+    g.res[0], g.res[1], g.res[2] = 8, 8, 8
+    g.sat = 4097
+    assert lib.nacc_march_rays(None, None, None, None, 0, ctypes.byref(g), ctypes.byref(p), None, None, None, None, 0,
+                               ctypes.c_void_p(256), None, ctypes.c_void_p(1 << 20), 1 << 20, None) == \
+        _lib.ERR_INVALID_ARG

@@ -14,6 +14,20 @@ if not torch.cuda.is_available():  # pragma: no cover
 from gpu_util import assert_march_equal, gpu_march, oracle_march  # noqa: E402
 
 
+@pytest.fixture(autouse=True, params=[0, 1, 2], ids=["plain", "box", "box_tile"])
+def box_walk(request):
+    """Every case without and with the grid's summed-area table (the box walk on
+    one-level grids, ray by ray or over a whole tile; other grids ignore it)."""
+    import gpu_util
+
+    old = _lib.tune_get("march_box_tile")
+    _lib.tune_set("march_box_tile", 1 if request.param == 2 else 0)
+    gpu_util.USE_SAT = request.param > 0
+    yield request.param
+    gpu_util.USE_SAT = False
+    _lib.tune_set("march_box_tile", old)
+
+
 def test_tiny_config_bitexact(orc):
     w = synth.tiny_config(0, device="cuda")
     assert_march_equal(gpu_march(w), oracle_march(orc, w))
@@ -119,7 +133,7 @@ def test_cone_mixed_starts_bitexact(orc):
 
 
 @pytest.mark.parametrize("cfg", ["bounded", "cone"])
-def test_lattice_point_counter(orc, cfg):
+def test_lattice_point_counter(orc, cfg, box_walk):
     """The workspace's lattice-point counter equals the samples the oracle emits on
     the same rays over an all-ones grid (where every lattice point is a sample)."""
     if cfg == "bounded":
@@ -140,8 +154,10 @@ def test_lattice_point_counter(orc, cfg):
     n = torch.zeros(1, dtype=torch.int64, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     bits = torch.from_numpy(w.bits.view(np.int32)).cuda()
-    _lib.march_rays(o, d, _lib.make_grid(bits, w.res, w.aabb, w.n_levels, w.n_slots), params, pi, ts, te, ri, n, st,
-                    ws)
+    grid = _lib.make_grid(bits, w.res, w.aabb, w.n_levels, w.n_slots)
+    if box_walk:
+        grid = _lib.make_grid(bits, w.res, w.aabb, w.n_levels, w.n_slots, sat=_lib.build_grid_sat(grid))
+    _lib.march_rays(o, d, grid, params, pi, ts, te, ri, n, st, ws)
     torch.cuda.synchronize()
     assert int(st.item()) == 0
     counted = int(ws[8:16].cpu().numpy().view(np.uint64)[0])

@@ -42,8 +42,8 @@ def _run(orc, scenes, near, far, dt_min, dt_max, cone, max_steps):
     R = o.shape[0]
     params = _lib.make_params(near, far, dt_min, dt_max, cone, max_steps)
     bits_t = [dev(s["bits"]) for s in scenes]
-    descs = _lib.make_scenes([(b, s["res"], s["aabb"], s["n_levels"], s["contraction"], s["o"].shape[0])
-                              for b, s in zip(bits_t, scenes)])
+    descs = _lib.make_scenes([(b, s["res"], s["aabb"], s["n_levels"], s["contraction"], s["o"].shape[0],
+                               s.get("sat")) for b, s in zip(bits_t, scenes)])
     # the oracle, scene by scene, stitched into one packed batch
     pis, ts, te, ri = [], [], [], []
     off, base = 0, 0

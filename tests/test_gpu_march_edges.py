@@ -1,4 +1,5 @@
-"""Marching against the oracle, bit-exact, with and without the coarse pass, on
+"""Marching against the oracle, bit-exact, point by point, with the coarse pass and
+with the box walk, on
 inputs aimed at the float32 cell decisions: midpoints exactly on cell faces, directions with tiny or zero
 components, directions far from unit length, origins far from the grid (large
 rounding), cascades with uniform steps, cells smaller than one step, a negative
@@ -22,14 +23,22 @@ from paper_2210_04847_gb300 import _lib  # noqa: E402
 from gpu_util import assert_march_equal, gpu_march, oracle_march  # noqa: E402
 
 
-@pytest.fixture(autouse=True, params=[0, 1], ids=["pointwise", "coarse"])
+@pytest.fixture(autouse=True, params=[0, 1, 2, 3], ids=["pointwise", "coarse", "box", "box_tile"])
 def coarse(request):
-    """Every case with and without the coarse pass (chunks inside one cell filled
-    from a single occupancy test)."""
-    old = _lib.tune_get("march_coarse")
-    _lib.tune_set("march_coarse", request.param)
+    """Every case point by point, with the coarse pass (chunks inside one cell
+    filled from a single occupancy test), and with the grid's summed-area table
+    (one-level grids take the box walk: chunks whose box of cells is all occupied
+    or all empty filled from one box count), ray by ray and over a whole tile."""
+    import gpu_util
+
+    old = _lib.tune_get("march_coarse"), _lib.tune_get("march_box_tile")
+    _lib.tune_set("march_coarse", 1 if request.param == 1 else 0)
+    _lib.tune_set("march_box_tile", 1 if request.param == 3 else 0)
+    gpu_util.USE_SAT = request.param >= 2
     yield request.param
-    _lib.tune_set("march_coarse", old)
+    gpu_util.USE_SAT = False
+    _lib.tune_set("march_coarse", old[0])
+    _lib.tune_set("march_box_tile", old[1])
 
 def _workload(o, d, occ, res, aabb, n_levels=1, near=0.0, far=1e10, dt_min=0.05, dt_max=0.05, cone=0.0,
               max_steps=1024):

@@ -351,3 +351,30 @@ def test_contraction_along_an_axis(orc, sign):
                   far_plane=100.0, dt_min=1.0 / 64, dt_max=1.0 / 64, max_steps=8192, contraction=1)
     assert m.n_samples == 128
     np.testing.assert_array_equal(m.t_starts, np.arange(128, 256, dtype=np.float32) / 64)
+
+
+def test_grid_sat_definition_by_brute_force(orc):
+    """oracle.grid_sat against a triple loop over cells on random small grids (two
+    grids, anisotropic), and box counts from it modulo 2^16 on a grid whose totals
+    wrap: every box below 2^16 cells gets its exact count."""
+    res = (3, 5, 4)
+    occ = synth.rand_uniform(3, 1, 2 * 60) < 0.45
+    s = orc.grid_sat(synth.pack_bits(occ), res, 2).reshape(2, 4, 6, 5)
+    o = occ.reshape(2, 3, 5, 4)
+    for g in range(2):
+        for x in range(4):
+            for y in range(6):
+                for z in range(5):
+                    assert s[g, x, y, z] == o[g, :x, :y, :z].sum()
+    res = (64, 64, 64)  # 262144 cells, mostly occupied: totals wrap modulo 2^16
+    occ = synth.rand_uniform(3, 2, 64 ** 3) < 0.9
+    s = orc.grid_sat(synth.pack_bits(occ), res).reshape(65, 65, 65).astype(np.int64)
+    o = occ.reshape(64, 64, 64)
+    assert s[64, 64, 64] == o.sum() % 65536
+    lo = synth.rand_int(3, 3, 60, 40).reshape(20, 3)
+    ext = 1 + synth.rand_int(3, 4, 60, 24).reshape(20, 3)
+    for (x0, y0, z0), (ex, ey, ez) in zip(lo, ext):
+        x1, y1, z1 = x0 + ex, y0 + ey, z0 + ez
+        cnt = (s[x1, y1, z1] - s[x0, y1, z1] - s[x1, y0, z1] - s[x1, y1, z0] + s[x0, y0, z1] + s[x0, y1, z0]
+               + s[x1, y0, z0] - s[x0, y0, z0]) % 65536
+        assert cnt == o[x0:x1, y0:y1, z0:z1].sum()
