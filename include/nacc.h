@@ -530,8 +530,8 @@ int nacc_sample_grid_cells(uint64_t seed, uint64_t stream, int64_t n, const nacc
 #define NACC_TUNE_RENDER_BWD_PREFETCH 9 /* 0/1: backward issues the next chunk's loads early */
 #define NACC_TUNE_MARCH_COARSE 10       /* 0/1: first test one lattice point in 32, fill chunks that lie in one cell */
 #define NACC_TUNE_FUSED_OCCUPANCY 11    /* 0: compiler's register use; 1: nacc_march_fused capped at 64 registers */
-#define NACC_TUNE_MARCH_BOX_TILE 12     /* 0/1: box walk (grid with its summed-area table, uniform steps) ray by ray,
-                                          or over all chunks of a tile at once */
+#define NACC_TUNE_MARCH_BOX_TILE 12     /* box walk (grid with its summed-area table, uniform steps): 0 ray by ray;
+                                          1, 2, 3 over all chunks of a tile at once, for 4, 5, 6 blocks per SM */
 #define NACC_TUNE_COUNT 13
 
 /* Set a knob; NACC_ERR_INVALID_ARG for an unknown knob or out-of-range value. */

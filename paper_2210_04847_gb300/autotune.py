@@ -21,7 +21,7 @@ CANDIDATES = {
     "march_occupancy": (0, 1),
     "march_unroll": (0, 1),
     "march_coarse": (0, 1),
-    "march_box_tile": (0, 1),
+    "march_box_tile": (0, 1, 2, 3),
     "prune_tile_rays": (2, 4, 6, 8, 12, 16, 24, 32),
     "prune_occupancy": (0, 1, 2),
     "prune_interleave": (2, 4),

@@ -42,7 +42,7 @@ int g_tune[NACC_TUNE_COUNT] = {
     0,  // NACC_TUNE_MARCH_BOX_TILE
 };
 const int g_tune_lo[NACC_TUNE_COUNT] = {0, 1, 2, 0, 0, 0, 0, 0, 2, 0, 0, 0, 0};
-const int g_tune_hi[NACC_TUNE_COUNT] = {1, 32, 32, 1, 2, 2, 2, 1, 4, 1, 1, 1, 1};
+const int g_tune_hi[NACC_TUNE_COUNT] = {1, 32, 32, 1, 2, 2, 2, 1, 4, 1, 1, 1, 3};
 }  // namespace
 
 int tune_get(int knob) { return (knob >= 0 && knob < NACC_TUNE_COUNT) ? g_tune[knob] : 0; }

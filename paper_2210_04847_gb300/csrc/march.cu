@@ -894,16 +894,20 @@ void launch_batched(bool cone, size_t smem, int need, cudaStream_t st, const Mar
 // Resident blocks per SM the box walks are compiled for (their registers fit
 // without spills).
 constexpr int kBoxMinBlocks = 4;
-constexpr int kBoxTileMinBlocks = 4;
 constexpr int kBoxBatchedMinBlocks = 3;
 
 // One-level grid with its summed-area table: the box walk, ray by ray or (uniform
-// steps, tuning knob) the whole tile's chunks at once.
-void launch_box(bool cone, bool tile, size_t smem, int need, cudaStream_t st, const MarchArgs& a) {
+// steps, tuning knob: 1, 2, 3) the whole tile's chunks at once, compiled for 4, 5
+// or 6 resident blocks per SM (55 registers; 48 and 40 with a few spills).
+void launch_box(bool cone, int tile, size_t smem, int need, cudaStream_t st, const MarchArgs& a) {
     if (cone)
         launch_uniform(march_uniform_kernel<1, kBoxMinBlocks, true, false, false, false, 1>, smem, need, st, a);
-    else if (tile)
-        launch_uniform(march_uniform_kernel<1, kBoxTileMinBlocks, false, false, false, false, 2>, smem, need, st, a);
+    else if (tile == 1)
+        launch_uniform(march_uniform_kernel<1, 4, false, false, false, false, 2>, smem, need, st, a);
+    else if (tile == 2)
+        launch_uniform(march_uniform_kernel<1, 5, false, false, false, false, 2>, smem, need, st, a);
+    else if (tile == 3)
+        launch_uniform(march_uniform_kernel<1, 6, false, false, false, false, 2>, smem, need, st, a);
     else
         launch_uniform(march_uniform_kernel<1, kBoxMinBlocks, false, false, false, false, 1>, smem, need, st, a);
 }
@@ -968,7 +972,7 @@ int march_launch(MarchArgs& a, const nacc_march_params* p, int32_t* packed_info,
         return launch_status(cudaGetLastError());
     }
     if (box && !a.contract && a.n_levels == 1) {
-        launch_box(cone, tune_get(NACC_TUNE_MARCH_BOX_TILE) != 0, smem, need, st, a);
+        launch_box(cone, tune_get(NACC_TUNE_MARCH_BOX_TILE), smem, need, st, a);
         return launch_status(cudaGetLastError());
     }
     const bool unroll = tune_get(NACC_TUNE_MARCH_UNROLL) != 0;

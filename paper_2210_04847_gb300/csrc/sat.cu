@@ -145,6 +145,43 @@ __global__ void __launch_bounds__(kSliceThreads) sat_slab_kernel(const SatArgs a
         for (int z = lane; z < nz; z += 32) base[xx * plane + z] = p[xx * nz + z];
 }
 
+// Many grids: pass 1 as one thread per corner column (g, x, z), consecutive
+// threads on consecutive z: a running sum along y of the row prefixes, each the
+// popcount of the row's first z bits. Enough threads to fill the GPU, and a few
+// instructions per entry.
+__global__ void __launch_bounds__(kThreads) sat_columns_kernel(const SatArgs a) {
+    const int64_t lines = (int64_t)a.n_grids * (a.r0 + 1) * (a.r2 + 1);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= lines) return;
+    const int z = (int)(t % (a.r2 + 1));
+    const int64_t gx = t / (a.r2 + 1);  // g * (r0 + 1) + x
+    const int x = (int)(gx % (a.r0 + 1));
+    const int64_t g = gx / (a.r0 + 1);
+    const int64_t step = a.r2 + 1;
+    uint16_t* out = a.sat + gx * (a.r1 + 1) * step + z;
+    out[0] = 0;
+    if (x == 0 || z == 0) {
+        for (int y = 1; y <= a.r1; ++y) out[y * step] = 0;
+        return;
+    }
+    int64_t b = ((g * a.r0 + (x - 1)) * (int64_t)a.r1) * a.r2;  // first bit of row (x - 1, 0)
+    uint32_t s = 0;
+    for (int y = 1; y <= a.r1; ++y, b += a.r2) {
+        uint32_t cnt = 0;
+        int64_t p = b;
+        const int64_t e = b + z;
+        while (p < e) {
+            const int off = (int)(p & 31);
+            const int take = (int)(e - p < 32 - off ? e - p : 32 - off);
+            const uint32_t w = __ldg(a.bits + (p >> 5)) >> off;
+            cnt += __popc(take == 32 ? w : (w & ((1u << take) - 1u)));
+            p += take;
+        }
+        s += cnt;
+        out[y * step] = (uint16_t)s;
+    }
+}
+
 // Fallback pass 1: rows straight from global memory (one warp per corner row).
 __global__ void __launch_bounds__(32) sat_rows_kernel(const SatArgs a) {
     const int64_t row = blockIdx.x;  // (g * (r0 + 1) + x) * (r1 + 1) + y
@@ -225,15 +262,21 @@ extern "C" int nacc_build_grid_sat(const nacc_grid* grid, uint16_t* sat, void* s
     SatArgs a{grid->bits, sat, grid->res[0], grid->res[1], grid->res[2], (int32_t)grids};
     cudaStream_t st = (cudaStream_t)stream;
     const long long planes = grids * (r0 + 1);
+    // a single grid or two: a block per plane and slab (few blocks, so each short);
+    // more grids: a thread per column (more parallel work, fewer instructions)
+    const bool many = grids >= 4;
     // a plane's bits span at most r1 r2 / 32 + 2 words
-    if ((r1 + 1) * (r2 + 1) <= kSliceMax && r1 * r2 / 32 + 2 <= kPlaneWordsMax) {
+    if (many) {
+        const long long cols = planes * (r2 + 1);
+        sat_columns_kernel<<<(unsigned)((cols + kThreads - 1) / kThreads), kThreads, 0, st>>>(a);
+    } else if ((r1 + 1) * (r2 + 1) <= kSliceMax && r1 * r2 / 32 + 2 <= kPlaneWordsMax) {
         sat_plane_kernel<<<(unsigned)planes, kSliceThreads, 0, st>>>(a);
     } else {
         sat_rows_kernel<<<(unsigned)(planes * (r1 + 1)), 32, 0, st>>>(a);
         const long long ly = planes * (r2 + 1);
         sat_sum_kernel<1><<<(unsigned)((ly + kThreads - 1) / kThreads), kThreads, 0, st>>>(a);
     }
-    if ((r0 + 1) * (r2 + 1) <= kSliceMax) {
+    if (!many && (r0 + 1) * (r2 + 1) <= kSliceMax) {
         sat_slab_kernel<<<(unsigned)(grids * (r1 + 1)), kSliceThreads, 0, st>>>(a);
     } else {
         const long long lx = grids * (r1 + 1) * (r2 + 1);

@@ -14,14 +14,14 @@ if not torch.cuda.is_available():  # pragma: no cover
 from gpu_util import assert_march_equal, gpu_march, oracle_march  # noqa: E402
 
 
-@pytest.fixture(autouse=True, params=[0, 1, 2], ids=["plain", "box", "box_tile"])
+@pytest.fixture(autouse=True, params=[0, 1, 2, 4], ids=["plain", "box", "box_tile", "box_tile6"])
 def box_walk(request):
     """Every case without and with the grid's summed-area table (the box walk on
     one-level grids, ray by ray or over a whole tile; other grids ignore it)."""
     import gpu_util
 
     old = _lib.tune_get("march_box_tile")
-    _lib.tune_set("march_box_tile", 1 if request.param == 2 else 0)
+    _lib.tune_set("march_box_tile", {0: 0, 1: 0, 2: 1, 4: 3}[request.param])
     gpu_util.USE_SAT = request.param > 0
     yield request.param
     gpu_util.USE_SAT = False

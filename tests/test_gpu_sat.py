@@ -24,7 +24,8 @@ from gpu_util import assert_march_equal, dev, gpu_march, oracle_march  # noqa: E
 @pytest.mark.parametrize("res,n_levels,n_slots,p", [((128, 128, 128), 1, 1, 0.78), ((33, 47, 29), 2, 3, 0.5),
                                                      ((1, 5, 70), 1, 2, 0.9), ((64, 64, 64), 1, 1, 1.0),
                                                      ((7, 1, 1), 1, 1, 0.5), ((3, 300, 300), 1, 1, 0.95),
-                                                     ((300, 3, 200), 1, 1, 0.7)])
+                                                     ((300, 3, 200), 1, 1, 0.7), ((64, 64, 64), 1, 5, 0.8),
+                                                     ((31, 17, 45), 2, 2, 0.6)])
 def test_sat_matches_definition(orc, res, n_levels, n_slots, p):
     n = res[0] * res[1] * res[2] * n_levels * n_slots
     occ = synth.rand_uniform(n_slots, 40 + n_levels, n) < p
