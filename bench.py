@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -82,6 +83,8 @@ def parse():
     ap.add_argument("--ref-rays", type=int, default=1 << 12, help="rays per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="bounded workload: skip the dynamic step and the eighth-scale batched graph comparison")
     ap.add_argument("--pixel-stride", type=int, default=1,
                     help="inference workload: every n-th pixel of each image (smaller cases for profiling)")
     ap.add_argument("--no-two-call", action="store_true", help="inference workload: skip the two-call comparison")
@@ -383,13 +386,40 @@ def run_ours(args):
 
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
+    line = measure(args, args.workload)
+    if line is None:
+        return 0
+    if args.workload == "bounded" and world == 1 and not args.no_extra:
+        # the other configurations' headline figures in the same run (own scenarios,
+        # autotuned): the dynamic training step, and the batched workload at 1/8 of
+        # its rays per scene as one CUDA graph against 64 per-scene launch sequences
+        sub = argparse.Namespace(**vars(args))
+        sub.no_e2e = sub.no_cpu_baseline = True
+        sub.steps, sub.warmup = min(args.steps, 10), min(args.warmup, 3)
+        dyn = measure(sub, "dynamic")
+        line["dynamic_step"] = {k: dyn[k] for k in ("value", "ms_per_step", "stages_ms", "step_hbm", "tuned")}
+        bat = measure(sub, "batched", ray_scale=0.125)
+        line["batched_eighth_scale"] = {
+            "rays_per_step": bat["config"]["rays_per_step_per_gpu"], "value_single_launches": bat["value"],
+            "step_hbm": bat["step_hbm"], "graph": bat["graph"], "per_scene_plain": bat["per_scene_plain"],
+            "graph_over_per_scene": round(bat["graph"]["rays_per_s"] / bat["per_scene_plain"]["rays_per_s"], 3)}
+    print(json.dumps(line))
+    return 0
+
+
+def measure(args, workload, ray_scale=1.0):
+    """One workload's measurement: the timed step, its roofline and the extra legs;
+    returns the JSON line (None on ranks other than 0)."""
+    import torch
+
+    rank, world, local = dist_env()
     dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
     from paper_2210_04847_gb300 import _lib, autotune
     from paper_2210_04847_gb300.pipeline import HotPath
     from paper_2210_04847_gb300.scenarios import make_scenario
 
-    n_rays = args.rays if args.rays != N_RAYS or args.workload == "bounded" else None
-    sc = make_scenario(args.workload, rank, dev, n_rays=n_rays)
+    n_rays = args.rays if args.rays != N_RAYS or workload == "bounded" else None
+    sc = make_scenario(workload, rank, dev, n_rays=n_rays, ray_scale=ray_scale)
     w = sc.w
     R = w.n_rays
     n_pool = len(sc.batches)
@@ -525,25 +555,25 @@ def run_ours(args):
     avg = {s: sum(v) / len(v) for s, v in stage_ms.items()}
     dom = max(stages, key=lambda s: avg[s])
     achieved = sb[dom] / (avg[dom] / 1e3) / 1e9
-    traffic = NCU_TRAFFIC.get((dom, kernel_source_sha(dom))) if args.workload == "bounded" and R == N_RAYS else None
+    traffic = NCU_TRAFFIC.get((dom, kernel_source_sha(dom))) if workload == "bounded" and R == N_RAYS else None
     step_bytes = sum(sb.values())
 
     extra = {}
-    if args.workload == "batched" and not args.no_batched_compare:
+    if workload == "batched" and not args.no_batched_compare:
         extra["per_scene_plain"] = run_per_scene_plain(args, sc, hp, dev)
         extra["graph"] = run_graph(args, sc, hp)
     e2e = None
-    if not args.no_e2e and args.workload == "bounded":
+    if not args.no_e2e and workload == "bounded":
         e2e = run_e2e(args, dev, sc)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "bounded":
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and workload == "bounded":
         cpu = cpu_baseline(sc.scenes[0], w.aabb, w.bits, R, args.cpu_rays)
 
     if rank != 0:
-        return 0
+        return None
     cfg = {"workload": w.name, "rays_per_step_per_gpu": R}
-    cfg.update(WORKLOAD_CONFIG[args.workload])
+    cfg.update(WORKLOAD_CONFIG[workload])
     cfg.update({
         "grid_update_samples": sc.n_grid, "parallelism": "rays sharded per GPU (weak), %d GPU(s)" % world,
         "l2": "flushed before every step (256 MB write); per-step working set > 1 GB",
@@ -576,8 +606,7 @@ def run_ours(args):
         "e2e": e2e,
     }
     line.update(extra)
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 INFER_METRIC = "rays/s (inference: march with the density field's transmittance + render fwd) on one GB300"
@@ -1109,8 +1138,13 @@ def run_per_scene_plain(args, sc, hp_all, dev):
 
 
 def run_e2e(args, dev, sc):
-    """Same metric through the public API: rays + targets copied from pinned host
-    memory each step, colours and loss copied back; field time subtracted."""
+    """Same metric through the public API, as a training loop runs it: each step's
+    rays + targets copied from pinned host memory (double-buffered on a copy stream,
+    so step i + 1's copy overlaps step i), the grid update, then
+    ray_marching + rendering + autograd backward in capacity mode (no host read
+    inside the step), and the colours, the loss and the status word read back
+    (one synchronisation per step). Field callbacks are timed by events and
+    subtracted."""
     import torch
 
     from paper_2210_04847_gb300 import api, synth
@@ -1125,8 +1159,14 @@ def run_e2e(args, dev, sc):
     # rays and targets of a batch in one pinned buffer (o | d | target), one copy per step
     host = [torch.from_numpy(np.concatenate([b["host"].rays_o.ravel(), b["host"].rays_d.ravel(),
                                              b["host"].target_rgb.ravel()])).pin_memory() for b in sc.batches]
-    out_host = torch.empty((R, 3), dtype=torch.float32).pin_memory()
-    loss_host = torch.empty((), dtype=torch.float32).pin_memory()
+    dbuf = [torch.empty(9 * R, dtype=torch.float32, device=dev) for _ in range(2)]
+    copied = [torch.cuda.Event() for _ in range(2)]
+    copy_stream = torch.cuda.Stream(device=dev)
+    # each step's results land in pinned buffers of its parity; a step's results are
+    # read (checked) after the next step is issued, so the GPU never waits for the host
+    out_host = [torch.empty((R, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
+    loss_host = [torch.empty((), dtype=torch.float32).pin_memory() for _ in range(2)]
+    status_host = [torch.empty(1, dtype=torch.int32).pin_memory() for _ in range(2)]
     dt = synth.SQRT3 * 3.0 / 1024.0
     field_ms = []
 
@@ -1136,7 +1176,7 @@ def run_e2e(args, dev, sc):
             e0.record()
             out = fn(*a)
             e1.record()
-            field_ms.append((e0, e1))
+            field_ms[-1].append((e0, e1))
             return out
         return wrapped
 
@@ -1155,40 +1195,79 @@ def run_e2e(args, dev, sc):
         return rgb.requires_grad_(True), sig.view(-1, 1).requires_grad_(True)
 
     sig_cells = torch.empty(N_GRID_SAMPLES, dtype=torch.float32, device=dev)
+    # the step's sample capacities: this batch's marched and kept counts plus 30%
+    b0 = sc.batches[0]
+    state["o"], state["d"] = b0["o"], b0["d"]
+    _, ts0, _ = api.ray_marching(b0["o"], b0["d"], grid, render_step_size=dt, max_steps=1024)
+    cap = int(ts0.shape[0] * 1.3) + 4096
+    _, ts0, _ = api.ray_marching(b0["o"], b0["d"], grid, sigma_fn=sigma_fn, render_step_size=dt, max_steps=1024,
+                                 early_stop_eps=1e-4, alpha_thre=1e-2)
+    cap_kept = int(ts0.shape[0] * 1.15) + 4096
+    del ts0
+
+    def copy_in(i):
+        with torch.cuda.stream(copy_stream):
+            dbuf[i % 2].copy_(host[i % len(host)], non_blocking=True)
+            copied[i % 2].record(copy_stream)
 
     def one(i):
-        field_ms.clear()
+        fms = []
+        field_ms.append(fms)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        flat = host[i % len(host)].to(dev, non_blocking=True)
+        torch.cuda.current_stream().wait_event(copied[i % 2])
+        flat = dbuf[i % 2]
         o, d, tgt = (flat[k * 3 * R:(k + 1) * 3 * R].view(R, 3) for k in range(3))
         state["o"], state["d"] = o, d
+        copy_in(i + 1)  # the next step's inputs, while this step runs
         # the grid update first, as a training loop does at the start of each step
         cells, xyz = upd.sample_cells(N_GRID_SAMPLES, 0, i % POOL)
         timed_field(lambda: field.points(xyz, N_GRID_SAMPLES, sig_cells))()
         upd.update(cells, sig_cells, 0.95, 0.01)
-        packed, ts, te, ri = api.ray_marching(o, d, grid, sigma_fn=timed_field(sigma_fn), render_step_size=dt,
-                                              max_steps=1024, early_stop_eps=1e-4, alpha_thre=1e-2,
-                                              return_ray_indices=True)
-        color, opacity, depth = api.rendering(timed_field(rgb_sigma_fn), packed, ts, te, ray_indices=ri)
+        packed, ts, te, ri, n = api.ray_marching(o, d, grid, sigma_fn=timed_field(sigma_fn), render_step_size=dt,
+                                                 max_steps=1024, early_stop_eps=1e-4, alpha_thre=1e-2, capacity=cap,
+                                                 kept_capacity=cap_kept)
+        color, opacity, depth = api.rendering(timed_field(rgb_sigma_fn), packed, ts, te, ray_indices=ri, n_samples=n,
+                                              save_optical_depth=True)
         loss = torch.nn.functional.mse_loss(color, tgt)
         loss.backward()
-        out_host.copy_(color.detach(), non_blocking=True)
-        loss_host.copy_(loss.detach(), non_blocking=True)
+        out_host[i % 2].copy_(color.detach(), non_blocking=True)
+        loss_host[i % 2].copy_(loss.detach(), non_blocking=True)
+        status_host[i % 2].copy_(api.step_status(dev), non_blocking=True)
+        api.step_status(dev).zero_()
         e1.record()
-        torch.cuda.synchronize()
-        total = e0.elapsed_time(e1)
-        f = sum(a.elapsed_time(b) for a, b in field_ms)
-        return total - f
+        return e0, e1
 
-    for i in range(args.warmup):
-        one(i)
-    ms = [one(args.warmup + i) for i in range(args.steps)]
+    def finish(i, ev):
+        """The step's results, read once its events are reached; its device time
+        minus the field's."""
+        e0, e1 = ev
+        e1.synchronize()
+        api.check_status(dev, int(status_host[i % 2][0]))
+        if not math.isfinite(float(loss_host[i % 2])):
+            raise RuntimeError("e2e: non-finite loss")
+        return e0.elapsed_time(e1) - sum(a.elapsed_time(b) for a, b in field_ms[i])
+
+    copy_in(0)
+    ms, pend = [], None
+    for i in range(args.warmup + args.steps):
+        ev = one(i)
+        if pend is not None:  # the previous step's results, read while this step runs
+            t = finish(*pend)
+            if pend[0] >= args.warmup:
+                ms.append(t)
+        pend = (i, ev)
+    ms.append(finish(*pend))
+    torch.cuda.synchronize()
     mean = sum(ms) / len(ms)
     return {"value": R / (mean / 1e3), "unit": "rays/s", "ms_per_step": round(mean, 4),
-            "h2d_bytes_per_step": 3 * 12 * R, "d2h_bytes_per_step": 12 * R + 4,
-            "note": "public API (grid update, then ray_marching + rendering + autograd backward), host-pinned rays "
-                    "and targets in, colours and loss out; field callbacks timed by events and subtracted"}
+            "h2d_bytes_per_step": 3 * 12 * R, "d2h_bytes_per_step": 12 * R + 4 + 4, "sample_capacity": cap,
+            "kept_capacity": cap_kept,
+            "note": "public API in capacity mode (grid update, then ray_marching + rendering with the optical depth "
+                    "saved + autograd backward, no host read inside the step); rays and targets copied from pinned "
+                    "host memory each step (the next step's copy overlaps this step); colours, loss and status "
+                    "copied to pinned memory each step and read after the next step is issued (one synchronisation "
+                    "per step, one step behind); field callbacks timed by events and subtracted"}
 
 
 def main():

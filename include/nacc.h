@@ -443,6 +443,16 @@ int nacc_render_bwd(const int32_t* packed_info, int32_t n_rays, const float* t_s
                     const float* g_opacity, const float* g_depth, float* d_sigmas,
                     float* d_rgbs, int32_t* d_status, void* stream);
 
+/*
+ * Capacity-sized sample arrays whose count stays on the device (a training step
+ * without host reads): value into arr[i * width + c] for every i in
+ * [*n_dev, capacity) and c < width, *n_dev read on the device (clamped to
+ * [0, capacity]). For example the gradients of samples past the kept count,
+ * which no packed run covers. arr (capacity, width) float32; n_dev device int64.
+ */
+int nacc_fill_tail_f32(float* arr, int64_t width, int64_t capacity, const int64_t* n_dev, float value,
+                       void* stream);
+
 /* ray_indices[i] = r for every sample i of ray r (the inverse of packed_info). */
 int nacc_unpack_info(const int32_t* packed_info, int32_t n_rays, int64_t n_samples,
                      int32_t* ray_indices, int32_t* d_status, void* stream);

@@ -39,7 +39,7 @@ EXPORTS = (
     "nacc_prune_samples", "nacc_march_fused", "nacc_density_field_at_samples", "nacc_density_field_query",
     "nacc_render_weights", "nacc_accumulate_along_rays", "nacc_render_weights_bwd",
     "nacc_accumulate_along_rays_bwd", "nacc_render_fwd", "nacc_render_bwd",
-    "nacc_unpack_info", "nacc_update_occupancy_grid", "nacc_density_threshold", "nacc_sample_grid_cells", "nacc_tune_set", "nacc_tune_get",
+    "nacc_unpack_info", "nacc_fill_tail_f32", "nacc_update_occupancy_grid", "nacc_density_threshold", "nacc_sample_grid_cells", "nacc_tune_set", "nacc_tune_get",
     "nacc_test_hook_set", "nacc_test_hook_get", "nacc_error_string",
     "nacc_version",
 )
@@ -137,6 +137,7 @@ def load() -> ctypes.CDLL:
         "nacc_render_fwd": (ctypes.c_int, [P, i32, P, P, P, P, i64, P, P, P, P, P, P]),
         "nacc_render_bwd": (ctypes.c_int, [P, i32, P, P, P, P, P, i64, P, P, P, P, P, P, P]),
         "nacc_unpack_info": (ctypes.c_int, [P, i32, i64, P, P, P]),
+        "nacc_fill_tail_f32": (ctypes.c_int, [P, i64, i64, P, f32, P]),
         "nacc_update_occupancy_grid": (ctypes.c_int, [P, P, i64, P, P, i64, f32, f32, f32, P, P]),
         "nacc_density_threshold": (ctypes.c_float, [f32, f32]),
         "nacc_sample_grid_cells": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, i64, GP, P, P, P]),
@@ -573,6 +574,16 @@ def unpack_info(packed_info, n_samples: int, ray_indices, d_status=None, stream=
     rc = load().nacc_unpack_info(_ptr(packed_info), n, int(n_samples), _ptr(ray_indices), _ptr(d_status),
                                  _stream(stream))
     _rc(rc, "nacc_unpack_info")
+
+
+def fill_tail(arr, n_dev, value: float = 0.0, stream=None):
+    """nacc_fill_tail_f32: rows [*n_dev, len(arr)) of a float32 array set to value."""
+    _check(arr, torch.float32, "arr")
+    _check(n_dev, torch.int64, "n_dev", 1)
+    cap = arr.shape[0] if arr.dim() > 0 else 0
+    width = arr.numel() // max(cap, 1) if cap else 1
+    _rc(load().nacc_fill_tail_f32(_ptr(arr), int(width), int(cap), _ptr(n_dev), float(value), _stream(stream)),
+        "nacc_fill_tail_f32")
 
 
 def update_occupancy_grid(ema, bits, cells, sigmas, decay, thre, d_status=None, alpha_step: float = 0.0, stream=None,

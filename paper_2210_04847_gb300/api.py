@@ -307,13 +307,96 @@ def prune_samples(packed_info, t_starts, t_ends, sigmas, early_stop_eps=1e-4, al
     return packed, ts[:n], te[:n], ri[:n]
 
 
+def _dev_key(device) -> str:
+    d = torch.device(device)
+    if d.type == "cuda" and d.index is None:
+        d = torch.device("cuda", torch.cuda.current_device())
+    return str(d)
+
+
+def step_status(device) -> torch.Tensor:
+    """The device status word (int32, NACC_STATUS_* bits) that calls in capacity mode
+    accumulate on ``device``; read it with the step's results and pass it to
+    ``check_status``, or call ``check_status(device)`` (one host read)."""
+    key = ("step_status", _dev_key(device))
+    st = _SCRATCH.bufs.get(key)
+    if st is None:
+        st = _SCRATCH.bufs[key] = torch.zeros(1, dtype=torch.int32, device=device)
+    return st
+
+
+def check_status(device, value: Optional[int] = None):
+    """Raise if the capacity-mode calls on ``device`` reported a problem (a capacity
+    too small for the samples, a timed-out wait, bad indices); then clear the word.
+    ``value``: the word already read back (no further host read)."""
+    st = step_status(device)
+    v = int(st.item()) if value is None else int(value)
+    st.zero_()
+    if v:
+        raise _lib.NaccError("device status 0x%x%s" % (v, " (capacity too small)" if v & _lib.STATUS_CAPACITY else ""))
+
+
+def _capacity_buffers(tag, device, R: int, capacity: int):
+    """Sample buffers reused by every capacity-mode call of the same shape. The
+    sample arrays start zeroed, so entries past a call's count always hold valid
+    ray indices and finite intervals (a previous call's samples or zeros)."""
+    key = ("cap", tag, _dev_key(device), R, capacity)
+    b = _SCRATCH.bufs.get(key)
+    if b is None:
+        z = lambda dt: torch.zeros(max(capacity, 1), dtype=dt, device=device)
+        b = _SCRATCH.bufs[key] = dict(packed=torch.zeros((R, 2), dtype=torch.int32, device=device),
+                                      ts=z(torch.float32), te=z(torch.float32), ri=z(torch.int32),
+                                      n=torch.zeros(1, dtype=torch.int64, device=device))
+    return b
+
+
+def _ray_marching_capacity(rays_o, rays_d, grid, sigma_fn, params, early_stop_eps, alpha_thre, ray_time, ray_slot,
+                           capacity: int, kept_capacity: int):
+    dev = rays_o.device
+    R = rays_o.shape[0]
+    st = step_status(dev)
+    m = _capacity_buffers("march", dev, R, capacity)
+    ws = _SCRATCH.get("march_ws", _lib.march_workspace_size(R, params), dev)
+    _lib.march_rays(rays_o, rays_d, grid.struct(), params, m["packed"], m["ts"][:capacity], m["te"][:capacity],
+                    m["ri"][:capacity], m["n"], st, ws, ray_time=ray_time, ray_slot=ray_slot)
+    if sigma_fn is None or not (early_stop_eps > 0 or alpha_thre > 0):
+        return m["packed"], m["ts"][:capacity].view(-1, 1), m["te"][:capacity].view(-1, 1), m["ri"][:capacity], m["n"]
+    with torch.no_grad():
+        sig = sigma_fn(m["ts"][:capacity].view(-1, 1), m["te"][:capacity].view(-1, 1), m["ri"][:capacity])
+    kc = kept_capacity
+    k = _capacity_buffers("prune", dev, R, kc)
+    wsp = _SCRATCH.get("prune_ws", _lib.prune_workspace_size(R, capacity), dev)
+    _lib.prune_samples(m["packed"], m["ts"][:capacity], m["te"][:capacity], sig.contiguous().view(-1).float(),
+                       capacity, early_stop_eps, alpha_thre, k["packed"], k["ts"][:kc], k["te"][:kc], k["ri"][:kc],
+                       k["n"], st, wsp)
+    return k["packed"], k["ts"][:kc].view(-1, 1), k["te"][:kc].view(-1, 1), k["ri"][:kc], k["n"]
+
+
 def ray_marching(rays_o, rays_d, grid: Optional[OccupancyGrid] = None, sigma_fn: Optional[Callable] = None,
                  near_plane=0.0, far_plane=1e10, render_step_size=1e-2, cone_angle=0.0, dt_max=None, max_steps=1024,
-                 early_stop_eps=1e-4, alpha_thre=0.0, ray_time=None, ray_slot=None, return_ray_indices=False):
+                 early_stop_eps=1e-4, alpha_thre=0.0, ray_time=None, ray_slot=None, return_ray_indices=False,
+                 capacity: Optional[int] = None, kept_capacity: Optional[int] = None):
     """March rays through the occupancy grid (or, with grid None, every step between
     the planes), then (if sigma_fn is given) prune by transmittance < early_stop_eps
     and opacity < alpha_thre, with the density queried without gradients (Sec. 2.1).
-    Returns (packed_info, t_starts (n,1), t_ends (n,1))."""
+    Returns (packed_info, t_starts (n,1), t_ends (n,1)).
+
+    capacity: a step with no host read. The outputs are then capacity-sized views
+    of buffers the next call with the same ray count and capacity reuses, and the
+    call returns (packed_info, t_starts, t_ends, ray_indices, n_samples) with
+    n_samples a device int64 tensor: samples past it are padding that no packed
+    run covers (valid ray indices, finite intervals). sigma_fn is called on the
+    capacity-sized marched samples; kept_capacity (default: capacity) sizes the
+    samples pruning keeps, which is what rendering and its gradient then run
+    over. A capacity that is too small is reported in ``step_status`` (check it
+    with the step's results)."""
+    if capacity is not None:
+        dev = rays_o.device
+        return _ray_marching_capacity(rays_o.contiguous().float(), rays_d.contiguous().float(),
+                                      _no_grid(dev) if grid is None else grid, sigma_fn,
+                                      _params(near_plane, far_plane, render_step_size, dt_max, cone_angle, max_steps),
+                                      early_stop_eps, alpha_thre, ray_time, ray_slot, int(capacity),
+                                      int(capacity if kept_capacity is None else kept_capacity))
     packed, ts, te, ri = march_rays(rays_o, rays_d, grid, near_plane, far_plane, render_step_size, cone_angle,
                                     dt_max, max_steps, ray_time, ray_slot)
     if sigma_fn is not None and (early_stop_eps > 0 or alpha_thre > 0) and ts.numel() > 0:
@@ -331,10 +414,12 @@ def unpack_info(packed_info: torch.Tensor, n_samples: int) -> torch.Tensor:
 
 
 class _RenderFn(torch.autograd.Function):
-    """Eq. 1 forward and its hand-written backward (reverse segmented scan)."""
+    """Eq. 1 forward and its hand-written backward (reverse segmented scan).
+    ``n_dev`` (capacity mode): the device count of valid samples; the gradients of
+    the padding past it are set to zero."""
 
     @staticmethod
-    def forward(ctx, sigmas, rgbs, packed_info, t_starts, t_ends, save_optical_depth: bool):
+    def forward(ctx, sigmas, rgbs, packed_info, t_starts, t_ends, save_optical_depth: bool, n_dev=None):
         R = packed_info.shape[0]
         M = t_starts.numel()
         dev = packed_info.device
@@ -348,6 +433,7 @@ class _RenderFn(torch.autograd.Function):
         ctx.save_for_backward(sg, rgb, packed_info, t_starts, t_ends, *( [od] if od is not None else [] ))
         ctx.sig_shape = sigmas.shape
         ctx.rgb_shape = rgbs.shape
+        ctx.n_dev = n_dev
         return color, opacity, depth
 
     @staticmethod
@@ -361,21 +447,29 @@ class _RenderFn(torch.autograd.Function):
         f = lambda g: None if g is None else g.contiguous().float()
         _lib.render_bwd(packed_info, t_starts, t_ends, sg, rgb, M, f(g_color), f(g_opacity), f(g_depth), d_sig, d_rgb,
                         optical_depth=od)
-        return d_sig.view(ctx.sig_shape), d_rgb.view(ctx.rgb_shape), None, None, None, None
+        if ctx.n_dev is not None:  # padding past the device count: no run covers it
+            _lib.fill_tail(d_sig, ctx.n_dev)
+            _lib.fill_tail(d_rgb, ctx.n_dev)
+        return d_sig.view(ctx.sig_shape), d_rgb.view(ctx.rgb_shape), None, None, None, None, None
 
 
-def render_packed(sigmas, rgbs, packed_info, t_starts, t_ends, save_optical_depth=False):
-    """Differentiable Eq. 1 over packed samples: (color (R,3), opacity (R,1), depth (R,1))."""
+def render_packed(sigmas, rgbs, packed_info, t_starts, t_ends, save_optical_depth=False, n_samples=None):
+    """Differentiable Eq. 1 over packed samples: (color (R,3), opacity (R,1), depth (R,1)).
+    n_samples: the device count of capacity-sized inputs (their padding gets zero gradients)."""
     return _RenderFn.apply(sigmas, rgbs, packed_info.contiguous(), t_starts.contiguous().view(-1),
-                           t_ends.contiguous().view(-1), save_optical_depth)
+                           t_ends.contiguous().view(-1), save_optical_depth, n_samples)
 
 
-def rendering(rgb_sigma_fn: Callable, packed_info, t_starts, t_ends, ray_indices=None, save_optical_depth=False):
-    """Query the user's field with gradients and render (Sec. 2.2). Returns (color, opacity, depth)."""
+def rendering(rgb_sigma_fn: Callable, packed_info, t_starts, t_ends, ray_indices=None, save_optical_depth=False,
+              n_samples=None):
+    """Query the user's field with gradients and render (Sec. 2.2). Returns (color, opacity, depth).
+    n_samples: the device count that ``ray_marching(capacity=...)`` returned."""
     if ray_indices is None:
+        if n_samples is not None:
+            raise ValueError("capacity mode: pass the ray_indices ray_marching returned (padding needs valid indices)")
         ray_indices = unpack_info(packed_info, t_starts.numel())
     rgbs, sigmas = rgb_sigma_fn(t_starts.view(-1, 1), t_ends.view(-1, 1), ray_indices)
-    return render_packed(sigmas, rgbs, packed_info, t_starts, t_ends, save_optical_depth)
+    return render_packed(sigmas, rgbs, packed_info, t_starts, t_ends, save_optical_depth, n_samples)
 
 
 class _WeightsFn(torch.autograd.Function):

@@ -812,6 +812,17 @@ __global__ void __launch_bounds__(kThreads) unpack_kernel(const int32_t* packed_
     }
 }
 
+// value into arr[i * width + c] for n <= i < capacity (n read on the device,
+// clamped to [0, capacity]).
+__global__ void __launch_bounds__(kThreads) fill_tail_kernel(float* arr, int64_t width, int64_t capacity,
+                                                             const int64_t* n_dev, float value) {
+    int64_t n = *n_dev;
+    n = n < 0 ? 0 : (n > capacity ? capacity : n);
+    const int64_t begin = n * width, end = capacity * width;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end; i += stride) arr[i] = value;
+}
+
 template <typename K>
 int grid_for(K kernel, int n_rays) {
     const DeviceInfo dev = current_device();
@@ -979,5 +990,15 @@ extern "C" int nacc_unpack_info(const int32_t* packed_info, int32_t n_rays, int6
     if (n_rays == 0) return NACC_OK;
     unpack_kernel<<<grid_for(unpack_kernel, n_rays), kThreads, 0, (cudaStream_t)stream>>>(
         packed_info, n_rays, n_samples, ray_indices, d_status);
+    return launch_status(cudaGetLastError());
+}
+
+extern "C" int nacc_fill_tail_f32(float* arr, int64_t width, int64_t capacity, const int64_t* n_dev, float value,
+                                  void* stream) {
+    if (width < 1 || capacity < 0 || !n_dev || (capacity > 0 && !arr)) return NACC_ERR_INVALID_ARG;
+    if (capacity == 0) return NACC_OK;
+    const DeviceInfo dev = current_device();
+    const long long blocks = (long long)dev.sm_count * 4;
+    fill_tail_kernel<<<(int)blocks, kThreads, 0, (cudaStream_t)stream>>>(arr, width, capacity, n_dev, value);
     return launch_status(cudaGetLastError());
 }

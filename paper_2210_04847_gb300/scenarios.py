@@ -154,8 +154,9 @@ class Scenario:
         return torch.cat(parts)
 
 
-def make_scenario(name: str, rank: int = 0, device="cuda", n_rays=None, pool: int = 4) -> Scenario:
-    """Seeded scenario; each rank draws its own ray batches (ranks share no work)."""
+def make_scenario(name: str, rank: int = 0, device="cuda", n_rays=None, pool: int = 4, ray_scale: float = 1.0) -> Scenario:
+    """Seeded scenario; each rank draws its own ray batches (ranks share no work).
+    ray_scale: the batched workload's rays per scene scaled (a smaller case)."""
     batches = [rank * 1000 + b for b in range(pool)]
     if name == "bounded":
         sg = synth.bounded_scene(0, device=device)
@@ -172,7 +173,7 @@ def make_scenario(name: str, rank: int = 0, device="cuda", n_rays=None, pool: in
         ws = [synth.unbounded_config(0, n_rays=n_rays or (1 << 20), device=device, batch=b) for b in batches[:1]]
         return Scenario(name, ws, ws[0].scenes, device, rank=rank)
     if name == "batched":
-        w = synth.batched_config(0, device=device)
+        w = synth.batched_config(0, device=device, ray_scale=ray_scale)
         return Scenario(name, [w], w.scenes, device, rank=rank)
     if name == "dynamic_shared":
         ws = [synth.dynamic_shared_config(0, n_rays=n_rays or (1 << 19), device=device, batch=b) for b in batches[:2]]

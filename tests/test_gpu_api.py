@@ -201,3 +201,69 @@ def test_march_without_a_grid_then_render_with_gradients(orc):
     packed, ts, te, ri = nacc.march_rays(rays_o, rays_d, near_plane=0.2, far_plane=1.0)
     assert np.array_equal(packed.cpu().numpy(), m.packed_info) and bits_equal(ts.cpu().numpy(), m.t_starts)
     assert float(opacity.detach().max()) > 0.5 and float(opacity.detach().min()) >= 0.0
+
+
+def test_capacity_mode_step_matches_exact_mode():
+    """ray_marching(capacity=...) + rendering(n_samples=...): no host read during the
+    step; the same packed samples, colours and gradients as the exact mode, zero
+    gradients on the padding past the device count, and a capacity too small
+    reported in the step's status word."""
+    w = synth.bounded_config(4, n_rays=2000, device="cuda")
+    scene = w.scenes[0]
+    grid = api.OccupancyGrid.from_bits(w.bits, w.res, w.aabb)
+    o, d = torch.from_numpy(w.rays_o).cuda(), torch.from_numpy(w.rays_d).cuda()
+    from paper_2210_04847_gb300.pipeline import StandInField
+
+    field = StandInField(scene, "cuda")
+
+    def sigma_fn(ts, te, ri):
+        sig = torch.empty(ts.shape[0], device="cuda")
+        field.samples(o, d, ri, ts.view(-1), te.view(-1), ts.shape[0], sig)
+        return sig.view(-1, 1)
+
+    def rgb_sigma_fn(ts, te, ri):
+        sig = torch.empty(ts.shape[0], device="cuda")
+        rgb = torch.empty((ts.shape[0], 3), device="cuda")
+        field.samples(o, d, ri, ts.view(-1), te.view(-1), ts.shape[0], sig, rgb)
+        return rgb.requires_grad_(True), sig.view(-1, 1).requires_grad_(True)
+
+    kw = dict(near_plane=w.near_plane, far_plane=w.far_plane, render_step_size=w.dt_min, max_steps=w.max_steps,
+              early_stop_eps=w.early_stop_eps, alpha_thre=w.alpha_thre)
+    tgt = torch.from_numpy(w.target_rgb).cuda()
+    grads = {}
+
+    def grab(name):
+        def fn(ts, te, ri):
+            rgb, sig = rgb_sigma_fn(ts, te, ri)
+            grads[name] = (rgb, sig)
+            return rgb, sig
+        return fn
+
+    packed, ts, te, ri = api.ray_marching(o, d, grid, sigma_fn=sigma_fn, return_ray_indices=True, **kw)
+    col, _, _ = api.rendering(grab("exact"), packed, ts, te, ray_indices=ri)
+    torch.nn.functional.mse_loss(col, tgt).backward()
+    S = ts.shape[0]
+    cap = S + 5000  # room for the marched samples too (pruning keeps fewer)
+    cap = max(cap, int(1.3 * 2000 * 500))
+    api.check_status("cuda")
+    packed_c, ts_c, te_c, ri_c, n_c = api.ray_marching(o, d, grid, sigma_fn=sigma_fn, capacity=cap,
+                                                       kept_capacity=S + 777, **kw)
+    col_c, _, _ = api.rendering(grab("cap"), packed_c, ts_c, te_c, ray_indices=ri_c, n_samples=n_c)
+    torch.nn.functional.mse_loss(col_c, tgt).backward()
+    api.check_status("cuda")
+    assert int(n_c.item()) == S and torch.equal(packed_c, packed)
+    assert torch.equal(ts_c[:S].view(-1), ts.view(-1)) and torch.equal(ri_c[:S], ri)
+    assert torch.equal(col_c, col)
+    (r_e, s_e), (r_c, s_c) = grads["exact"], grads["cap"]
+    assert torch.equal(s_c.grad[:S], s_e.grad) and torch.equal(r_c.grad[:S], r_e.grad)
+    assert (s_c.grad[S:] == 0).all() and (r_c.grad[S:] == 0).all()
+    # a capacity below the marched count: reported, nothing written past it
+    api.ray_marching(o, d, grid, sigma_fn=sigma_fn, capacity=1000, **kw)
+    with pytest.raises(_lib_error()):
+        api.check_status("cuda")
+
+
+def _lib_error():
+    from paper_2210_04847_gb300 import _lib
+
+    return _lib.NaccError
