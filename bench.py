@@ -46,15 +46,16 @@ POOL = 4  # distinct ray batches cycled through the steps (L2 is flushed between
 # from one ncu capture, keyed by the SHA-256 of the kernel's source file. A
 # source change invalidates the figure (reported as null until re-captured).
 NCU_TRAFFIC = {
-    # profiles/march_dram_bounded-2^18.md: 9070336 B read + 1477548544 B written
-    ("march", "2bbafd758c7197be50a94f2fa9a44fac3fb5ab3389194cc2aaa80ab2867e80af"): 1486618880,
+    # profiles/march_dram_bounded-2^18.md: 14640640 B read + 1478211072 B written (box walk)
+    ("march", "d8f68d6c0c85a6274c7d51a68d8f8287ef723cc3f3179bcda505f60258fcea77"): 1492851712,
     # profiles/march_fused_inference-800x800.md: 22437376 B read + 1169642240 B written (camera 0's image)
     ("march_fused", "c86e1bad5b55ca339d49805cf9ac418869661e8853df2abc21f41da92b781990"): 1192079616,
 }
 
 # What limits each stage (from the ncu captures summarised under profiles/).
 LIMITER = {
-    "march": "issue: bit-exact float32 lattice arithmetic, ~74% issue-active at ~32% DRAM",
+    "march": "store phase near the write bandwidth plus the latency of the ray, table and bitfield loads (box walk: "
+             "67% issue-active at 43% DRAM, long-scoreboard stalls first)",
     "prune": "DRAM latency (long-scoreboard stalls)",
     "render_fwd": "DRAM latency / issue",
     "render_bwd": "DRAM latency (long-scoreboard stalls)",
@@ -219,7 +220,7 @@ def launches_per_step(w, n_cells: int, n_grid: int, ema_ptr: int, sat: bool = Fa
 def kernel_source_sha(stage: str) -> str:
     """SHA-256 over the sources a stage's kernel is compiled from."""
     files = {"march": ("march.cu", "march_common.cuh", "nacc_internal.cuh"), "prune": ("prune.cu", "nacc_internal.cuh"),
-             "render_fwd": ("render.cu",), "render_bwd": ("render.cu",), "grid_update": ("grid.cu",),
+             "render_fwd": ("render.cu",), "render_bwd": ("render.cu",), "grid_update": ("grid.cu", "sat.cu"),
              "march_fused": ("fused.cu", "march_common.cuh", "nacc_internal.cuh")}[stage]
     h = hashlib.sha256()
     for f in files:
