@@ -206,15 +206,26 @@ def launches_per_step(w, n_cells: int, n_grid: int, ema_ptr: int, sat: bool = Fa
     for cone steps), prune, render forward, render backward, the grid sampler, the
     decay pass (four cells per thread over whole 128-cell steps of an aligned
     grid, one cell per thread for the rest), the scatter, and with the box walk
-    the three passes that rebuild the updated grid's summed-area table."""
+    the passes that rebuild the updated grid's summed-area table (two: planes or
+    columns, then the sum along x; three when a plane exceeds shared memory)."""
     n = 4 + (1 if w.cone > 0 else 0)
     if n_grid > 0:
         n += 2  # sampler + scatter
         if sat:
-            n += 3
+            n += sat_launches(w.res, w.n_levels * w.n_slots)
     steps = n_cells >> 7 if ema_ptr % 16 == 0 else 0
     n += (1 if steps > 0 else 0) + (1 if (steps << 7) < n_cells else 0)
     return n
+
+
+def sat_launches(res, grids: int) -> int:
+    """Kernels one summed-area-table build launches (the rule of nacc_build_grid_sat)."""
+    r0, r1, r2 = res
+    slice_max, words_max = 20 * 1024, 2048
+    if grids >= 4:
+        return 2
+    first = 1 if ((r1 + 1) * (r2 + 1) <= slice_max and r1 * r2 // 32 + 2 <= words_max) else 2
+    return first + 1
 
 
 def kernel_source_sha(stage: str) -> str:
@@ -558,6 +569,14 @@ def measure(args, workload, ray_scale=1.0):
     achieved = sb[dom] / (avg[dom] / 1e3) / 1e9
     traffic = NCU_TRAFFIC.get((dom, kernel_source_sha(dom))) if workload == "bounded" and R == N_RAYS else None
     step_bytes = sum(sb.values())
+    # the path's bytes by the per-step formula with every marched sample read once by
+    # pruning (104R + 24M + 76S with pruning on, 88R + 76M with it off; 8S more when
+    # the forward saves O for the backward), the bitfield once, plus the grid update
+    if S_avg < M_avg:
+        formula_bytes = 104 * R + 24 * M_avg + 76 * S_avg
+    else:
+        formula_bytes = 88 * R + 76 * M_avg
+    formula_bytes += (8 * S_avg if hp.save_optical_depth else 0) + grid_bytes + sb["grid_update"]
 
     extra = {}
     if workload == "batched" and not args.no_batched_compare:
@@ -597,6 +616,10 @@ def measure(args, workload, ray_scale=1.0):
         "step_hbm": {"algorithmic_bytes": int(step_bytes), "gbs": round(step_bytes / (mean_ms / 1e3) / 1e9, 1),
                      "frac": round(step_bytes / (mean_ms / 1e3) / 1e9 / peak, 4), "peak_gbs": peak,
                      "peak_kind": peak_kind},
+        "step_hbm_formula": {"bytes": "104R + 24M + 76S (pruning on; 88R + 76M off) + 8S saved O + bitfield + "
+                                      "grid update: pruning counted as reading every marched sample",
+                             "algorithmic_bytes": int(formula_bytes),
+                             "frac": round(formula_bytes / (mean_ms / 1e3) / 1e9 / peak, 4)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes": int(sb[dom]), "limiter": LIMITER[dom]},

@@ -415,3 +415,51 @@ def test_prune_uneven_rays_every_tile_shape(orc, tile_rays):
         assert cg == co and bits_equal(g["ts"][og : og + cg], p.t_starts[oo : oo + co])
         assert np.all(g["ri"][og : og + cg] == r)
     assert len(flipped) <= 2 and p.n_samples > 1000
+
+
+@pytest.mark.parametrize("shift", [(0, 0, 0), (2, 2, 2), (0, 2, 0), (2, 0, 2), (0, 0, 2), (2, 2, 0)])
+def test_prune_alignment_phases(orc, shift):
+    """Input arrays at different addresses modulo 16 (each 8-byte aligned, as the
+    ABI accepts), with runs starting at every offset modulo 4: results equal the
+    oracle's whatever the arrays' relative alignment."""
+    rng = np.random.default_rng(7)
+    lens = rng.choice([0, 1, 2, 3, 5, 63, 64, 65, 66, 67, 130, 700], size=400)
+    off = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    pi = np.stack([off, lens], axis=1).astype(np.int32)
+    M = int(lens.sum())
+    ts = np.zeros(M, np.float32)
+    for o, c in pi:
+        ts[o : o + c] = np.arange(c, dtype=np.float32) * np.float32(0.01) + np.float32(0.25)
+    te = (ts + np.float32(0.01)).astype(np.float32)
+    sg = (rng.random(M) ** 3 * 80).astype(np.float32)
+    p, keep, od = orc.prune(pi, ts, te, sg, 1e-4, 1e-2)
+
+    def shifted(x, k):
+        buf = torch.zeros(M + 4, dtype=torch.float32, device="cuda")
+        buf[k : k + M] = torch.from_numpy(x).cuda()
+        return buf[k : k + M]
+
+    d_ts, d_te, d_sg = shifted(ts, shift[0]), shifted(te, shift[1]), shifted(sg, shift[2])
+    R = pi.shape[0]
+    ws = torch.zeros(_lib.prune_workspace_size(R, M), dtype=torch.uint8, device="cuda")
+    o_pi = torch.full((R, 2), -3, dtype=torch.int32, device="cuda")
+    o_ts, o_te = torch.zeros(M, device="cuda"), torch.zeros(M, device="cuda")
+    o_ri = torch.zeros(M, dtype=torch.int32, device="cuda")
+    n = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    km = torch.full((M,), 7, dtype=torch.uint8, device="cuda")
+    _lib.prune_samples(dev(pi), d_ts, d_te, d_sg, M, 1e-4, 1e-2, o_pi, o_ts, o_te, o_ri, n, st, ws, keep_mask=km)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    keep_g = km.cpu().numpy().astype(bool)
+    near = near_threshold(pi, ts, te, sg, 1e-4, od)
+    assert not ((keep_g != keep) & ~near).any()
+    flipped = set(np.searchsorted(pi[:, 0], np.nonzero(keep_g != keep)[0], side="right") - 1)
+    g_pi, g_ts, g_ri = o_pi.cpu().numpy(), o_ts.cpu().numpy(), o_ri.cpu().numpy()
+    for r in range(R):
+        if r in flipped:
+            continue
+        (og, cg), (oo, co) = g_pi[r], p.packed_info[r]
+        assert cg == co and bits_equal(g_ts[og : og + cg], p.t_starts[oo : oo + co])
+        assert np.all(g_ri[og : og + cg] == r)
+    assert len(flipped) <= 2 and int(n.item()) == int(keep_g.sum()) and p.n_samples > 1000
