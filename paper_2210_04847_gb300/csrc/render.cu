@@ -76,6 +76,7 @@ struct FwdArgs {
 };
 
 constexpr int kRenderThreads = 128;
+constexpr int kRayVals = 9;  // backward: per-ray values staged in shared memory
 constexpr int kGroup = 4;  // consecutive rays per warp (lane i holds ray i's run)
 
 // Runs of the warp's group of rays; lanes >= nr and invalid runs hold (0, 0).
@@ -624,27 +625,49 @@ __device__ __forceinline__ void pair_tau(const BwdArgs& a, unsigned abase, unsig
 template <int MINB, bool PREFETCH, bool WEIGHTS = false>
 __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const BwdArgs a) {
     __shared__ float s_carry[kRenderThreads / 32][kCarryCap];
+    // per ray of the group: its upstream gradients and first sample, loaded by
+    // lane i for ray i before any ray is processed (one round trip for the group)
+    __shared__ float s_ray[kRenderThreads / 32][kGroup][kRayVals];
     const int lane = threadIdx.x & 31;
     float* carries = s_carry[threadIdx.x >> 5];
+    float(*ray_vals)[kRayVals] = s_ray[threadIdx.x >> 5];
     const int ray0 = global_warp() * kGroup;
     if (ray0 >= a.n_rays) return;
     const int nr = min(kGroup, a.n_rays - ray0);
     int my_off, my_cnt;
     load_group(a.packed_info, ray0, nr, a.n_samples, a.d_status, lane, my_off, my_cnt);
     const bool saved = a.optical_depth != nullptr;
+    if (lane < nr && my_cnt > 0) {
+        const size_t r = (size_t)ray0 + lane;
+        float* v = ray_vals[lane];
+        if constexpr (WEIGHTS) {
+            v[0] = a.g_ref ? __ldg(a.g_ref + r) : __ldg(a.g_weights + my_off);
+        } else {
+            v[0] = a.g_color ? a.g_color[3 * r] : 0.0f;
+            v[1] = a.g_color ? a.g_color[3 * r + 1] : 0.0f;
+            v[2] = a.g_color ? a.g_color[3 * r + 2] : 0.0f;
+            v[3] = a.g_opacity ? a.g_opacity[r] : 0.0f;
+            v[4] = a.g_depth ? a.g_depth[r] : 0.0f;
+            v[5] = __ldg(a.rgbs + 3 * (size_t)my_off);
+            v[6] = __ldg(a.rgbs + 3 * (size_t)my_off + 1);
+            v[7] = __ldg(a.rgbs + 3 * (size_t)my_off + 2);
+            v[8] = (__ldg(a.t_starts + my_off) + __ldg(a.t_ends + my_off)) * 0.5f;
+        }
+    }
+    __syncwarp();
     for (int ri = 0; ri < nr; ++ri) {
         const unsigned lo = __shfl_sync(FULL, my_off, ri);
         const int cnt = __shfl_sync(FULL, my_cnt, ri);
         if (cnt == 0) continue;
         const unsigned hi = lo + cnt;
         const unsigned abase = lo & ~1u;
-        const int r = ray0 + ri;
         const int nch = (int)((hi - abase + 63) >> 6);
-        const float gc0 = !WEIGHTS && a.g_color ? a.g_color[3 * (size_t)r] : 0.0f;
-        const float gc1 = !WEIGHTS && a.g_color ? a.g_color[3 * (size_t)r + 1] : 0.0f;
-        const float gc2 = !WEIGHTS && a.g_color ? a.g_color[3 * (size_t)r + 2] : 0.0f;
-        const float ga = !WEIGHTS && a.g_opacity ? a.g_opacity[r] : 0.0f;
-        const float gd = !WEIGHTS && a.g_depth ? a.g_depth[r] : 0.0f;
+        const float* rv = ray_vals[ri];
+        const float gc0 = WEIGHTS ? 0.0f : rv[0];
+        const float gc1 = WEIGHTS ? 0.0f : rv[1];
+        const float gc2 = WEIGHTS ? 0.0f : rv[2];
+        const float ga = WEIGHTS ? 0.0f : rv[3];
+        const float gd = WEIGHTS ? 0.0f : rv[4];
 
         // pass A (recompute mode): optical-depth carry at the start of each chunk,
         // the next chunk's loads in flight while the current one is scanned
@@ -680,17 +703,13 @@ __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const 
         // centred input itself
         float r_ref = 0.0f, g_ref = 0.0f, b_ref = 0.0f, tm_ref = 0.0f, a_ref, a_sub = 0.0f;
         if constexpr (WEIGHTS) {
-            if (a.g_ref) {
-                a_ref = __ldg(a.g_ref + r);
-            } else {
-                a_ref = __ldg(a.g_weights + lo);
-                a_sub = a_ref;
-            }
+            a_ref = rv[0];
+            if (!a.g_ref) a_sub = a_ref;
         } else {
-            r_ref = __ldg(a.rgbs + 3 * lo);
-            g_ref = __ldg(a.rgbs + 3 * lo + 1);
-            b_ref = __ldg(a.rgbs + 3 * lo + 2);
-            tm_ref = (__ldg(a.t_starts + lo) + __ldg(a.t_ends + lo)) * 0.5f;
+            r_ref = rv[5];
+            g_ref = rv[6];
+            b_ref = rv[7];
+            tm_ref = rv[8];
             a_ref = gc0 * r_ref + gc1 * g_ref + gc2 * b_ref + ga + gd * tm_ref;
         }
         const unsigned last = hi - 1 - abase;  // position of the ray's last sample in its chunks
