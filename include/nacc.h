@@ -93,12 +93,16 @@ typedef struct nacc_grid {
  *     S_g[x][y][z] = number of occupied cells (i, j, k) of g with i < x, j < y, k < z
  * modulo 2^16, corners x-major and z fastest, grids in slot-major, level order.
  * Built from grid->bits on `stream`; rebuild it whenever the bits change.
- * Marching a one-level, uncontracted grid that carries its table
+ * Marching an uncontracted grid of up to four levels that carries its table
  * (nacc_grid.sat) decides every 32-point lattice chunk whose box of cells (from
- * the chunk's first point to the point after the chunk: every cell index is
- * monotone along the ray) is all occupied or all empty from one box count
- * (exact for boxes of fewer than 2^16 cells), and tests the other chunks point
- * by point. Results are identical with and without the table. sat:
+ * the chunk's first point to the point after the chunk: every cell index of
+ * every level is monotone along the ray) is all occupied or all empty from one
+ * box count (exact for boxes of fewer than 2^16 cells). In a cascade the box is
+ * taken at the first level the chunk can reach; it decides when every point
+ * lies in that level (its box inside the level) or outside all levels (the
+ * outermost). The other chunks are tested point by point. Results are identical
+ * with and without the table (shared lattices; rays with their own cone
+ * recurrence are always tested point by point). sat:
  * nacc_grid_sat_bytes() bytes, 2-byte aligned; the corners over all slots and
  * levels must number below 2^31.
  */

@@ -45,10 +45,10 @@ class OccupancyGrid:
         self.ema = torch.zeros(self.n_cells, dtype=torch.float32, device=device)
         self.bits = torch.zeros((self.n_cells + 31) // 32, dtype=torch.int32, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
-        # one-level grids keep the summed-area table of their bits, so marching takes
-        # the box walk; rebuilt after every update and whenever the bits tensor is
-        # modified by torch (its version counter moves)
-        self.use_sat = self.n_levels == 1 and not self.contraction
+        # uncontracted grids of up to four levels keep the summed-area table of their
+        # bits, so marching takes the box walk; rebuilt after every update and
+        # whenever the bits tensor is modified by torch (its version counter moves)
+        self.use_sat = self.n_levels <= 4 and not self.contraction
         self.sat = None
         self._sat_version = None
 

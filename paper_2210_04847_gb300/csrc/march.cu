@@ -175,6 +175,115 @@ __device__ __forceinline__ int walk_box(const MarchArgs& a, const G& g, const fl
     return count + __reduce_add_sync(FULL, part);
 }
 
+// Box walk of one ray over a cascade (2..MAXL levels, each with its table;
+// shared lattices). A point's level is the first whose cell indices are all in
+// range, and every level's clamped index along each axis is monotone along the
+// ray, so for the box of a chunk (lane j: chunk grp + j, from its first point to
+// the next chunk's first point) at level l:
+//   - an axis on which both ends are below 0 (or both at res) puts no point of
+//     the chunk inside level l (the level is excluded);
+//   - with L the first level not excluded, no point lies in a finer level; if
+//     L's box is inside the grid, every point lies in L and its cells are in the
+//     box, which the table of L decides as full or empty; if L is the outermost
+//     level, points outside it lie outside every level (empty), so the in-grid
+//     part's count decides empty;
+//   - every level excluded: the chunk is empty.
+// Other chunks are tested point by point.
+template <int MAXL, bool CONE, typename G>
+__device__ __forceinline__ int walk_box_levels(const MarchArgs& a, const G& g, const float o[3], const float d[3],
+                                               float near, float far, int nk, int max_ch, unsigned sl0,
+                                               uint32_t* row, int lane) {
+    const float dt = a.dt_min;
+    const int nl = g.n_levels();
+    const int r0 = g.res0(), r1 = g.res1(), r2 = g.res2();
+    int part = 0, count = 0;
+    for (int grp = 0; grp < max_ch; grp += 31) {
+        const int kp = min((grp + lane) << 5, nk - 1);
+        float ts, tn;
+        if (!CONE) {
+            const float kf = __int2float_rn(kp);
+            ts = __fadd_rn(near, __fmul_rn(kf, dt));
+            tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+        } else {
+            ts = __ldg(a.cone_table + min(kp, a.max_steps));
+            tn = __ldg(a.cone_table + min(kp + 1, a.max_steps));
+        }
+        const float te = tn < far ? tn : far;
+        const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
+        const float x0 = __fadd_rn(o[0], __fmul_rn(d[0], mid));
+        const float x1 = __fadd_rn(o[1], __fmul_rn(d[1], mid));
+        const float x2 = __fadd_rn(o[2], __fmul_rn(d[2], mid));
+        // the first level not excluded, with both ends' clamped cells there
+        int L = -1, i0 = 0, i1 = 0, i2 = 0, n0 = 0, n1 = 0, n2 = 0;
+#pragma unroll
+        for (int l = 0; l < MAXL; ++l) {
+            if (l >= nl) break;  // uniform
+            const int c0 = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x0, g.lo(l, 0)), g.scale(l, 0))), -1), r0);
+            const int c1 = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x1, g.lo(l, 1)), g.scale(l, 1))), -1), r1);
+            const int c2 = min(max(__float2int_rd(__fmul_rn(__fsub_rn(x2, g.lo(l, 2)), g.scale(l, 2))), -1), r2);
+            const int e0 = __shfl_down_sync(FULL, c0, 1);
+            const int e1 = __shfl_down_sync(FULL, c1, 1);
+            const int e2 = __shfl_down_sync(FULL, c2, 1);
+            const bool excluded = (c0 < 0 && e0 < 0) || (c0 >= r0 && e0 >= r0) || (c1 < 0 && e1 < 0) ||
+                                  (c1 >= r1 && e1 >= r1) || (c2 < 0 && e2 < 0) || (c2 >= r2 && e2 >= r2);
+            if (L < 0 && !excluded) {
+                L = l;
+                i0 = c0;
+                i1 = c1;
+                i2 = c2;
+                n0 = e0;
+                n1 = e1;
+                n2 = e2;
+            }
+        }
+        const int c = grp + lane;
+        const bool exists = lane < 31 && c < max_ch;
+        bool full = false, empty = false;
+        if (exists) {
+            if (L < 0) {
+                empty = true;
+            } else {
+                const bool inside = min(i0, n0) >= 0 && min(i1, n1) >= 0 && min(i2, n2) >= 0 && max(i0, n0) < r0 &&
+                                    max(i1, n1) < r1 && max(i2, n2) < r2;
+                if (inside || L == nl - 1) box_decide(g, sl0 + (unsigned)L, i0, i1, i2, n0, n1, n2, full, empty);
+            }
+        }
+        if (full || empty) {
+            const int n = min(32, nk - (c << 5));
+            const uint32_t m = full ? (n >= 32 ? ~0u : (1u << n) - 1u) : 0u;
+            row[c] = m;
+            part += __popc(m);
+        }
+        unsigned pend = __ballot_sync(FULL, exists && !full && !empty);
+        while (pend) {
+            const int cc = grp + __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int k = (cc << 5) + lane;
+            float ks, kn;
+            if (!CONE) {
+                const float kf = __int2float_rn(k);
+                ks = __fadd_rn(near, __fmul_rn(kf, dt));
+                kn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+            } else {
+                ks = __ldg(a.cone_table + min(k, a.max_steps));
+                kn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+            }
+            bool occ = false;
+            if (k < nk) {
+                const float ke = kn < far ? kn : far;
+                const float km = __fmul_rn(__fadd_rn(ks, ke), 0.5f);
+                occ = occupied_in<MAXL>(g, __fadd_rn(o[0], __fmul_rn(d[0], km)),
+                                        __fadd_rn(o[1], __fmul_rn(d[1], km)), __fadd_rn(o[2], __fmul_rn(d[2], km)),
+                                        sl0);
+            }
+            const unsigned m = __ballot_sync(FULL, occ);
+            if (lane == 0) row[cc] = m;
+            count += __popc(m);
+        }
+    }
+    return count + __reduce_add_sync(FULL, part);
+}
+
 // One ray, all 32 lanes: one ballot word per 32 lattice points into row[c].
 // count = samples, nch = ballot words written (row[0..nch)).
 // COARSE (shared lattices): first one point every 32 per lane, and chunks that
@@ -198,6 +307,14 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, con
     if constexpr (BOX != 0 && MAXL == 1) {
         if (shared && g.sat()) {
             count_out = max_ch > 0 ? walk_box<CONE>(a, g, o, d, near, far, nk, max_ch, sl0, row, lane) : 0;
+            nch_out = max_ch;
+            return;
+        }
+    }
+    if constexpr (BOX != 0 && MAXL > 1) {
+        if (shared && g.sat()) {
+            count_out = max_ch > 0 ? walk_box_levels<MAXL, CONE>(a, g, o, d, near, far, nk, max_ch, sl0, row, lane)
+                                   : 0;
             nch_out = max_ch;
             return;
         }
@@ -973,6 +1090,11 @@ int march_launch(MarchArgs& a, const nacc_march_params* p, int32_t* packed_info,
     }
     if (box && !a.contract && a.n_levels == 1) {
         launch_box(cone, tune_get(NACC_TUNE_MARCH_BOX_TILE), smem, need, st, a);
+        return launch_status(cudaGetLastError());
+    }
+    if (box && !a.contract && a.n_levels <= 4) {  // cascades: the box walk over levels, 64 registers
+        if (cone) launch_uniform(march_uniform_kernel<4, 4, true, false, false, false, 1>, smem, need, st, a);
+        else launch_uniform(march_uniform_kernel<4, 4, false, false, false, false, 1>, smem, need, st, a);
         return launch_status(cudaGetLastError());
     }
     const bool unroll = tune_get(NACC_TUNE_MARCH_UNROLL) != 0;

@@ -65,9 +65,9 @@ class HotPath:
         self.ema = torch.zeros(self.n_cells, dtype=torch.float32, device=device)
         self.params = _lib.make_params(w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone, w.max_steps)
         self.grid = _lib.make_grid(self.bits, w.res, w.aabb, w.n_levels, w.n_slots, w.contraction)
-        # one-level grids march with their summed-area table (the box walk);
-        # every grid update rebuilds the table of the bits it writes
-        self.sat_ok = w.n_levels == 1 and not w.contraction
+        # uncontracted grids of up to four levels can march with their summed-area
+        # table (the box walk); every grid update rebuilds the table of the bits it writes
+        self.sat_ok = w.n_levels <= 4 and not w.contraction
         self.use_sat = self.sat_ok
         self.sat = _lib.build_grid_sat(self.grid) if self.sat_ok else None
         self.grid_sat = (_lib.make_grid(self.bits, w.res, w.aabb, w.n_levels, w.n_slots, w.contraction, sat=self.sat)

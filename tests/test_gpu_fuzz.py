@@ -50,12 +50,20 @@ def _config(seed):
 
 @pytest.mark.parametrize("seed", range(16))
 def test_fuzz_march_bitexact(orc, seed):
+    """Each configuration without and with the grid's summed-area table (the box
+    walk for one level and for cascades of up to four levels)."""
+    import gpu_util
+
     w, rng = _config(seed)
     old = _lib.tune_get("march_tile_rays")
     try:
         _lib.tune_set("march_tile_rays", int(rng.choice([1, 2, 4, 8, 16, 32])))
-        assert_march_equal(gpu_march(w), oracle_march(orc, w))
+        ref = oracle_march(orc, w)
+        assert_march_equal(gpu_march(w), ref)
+        gpu_util.USE_SAT = True
+        assert_march_equal(gpu_march(w), ref)
     finally:
+        gpu_util.USE_SAT = False
         _lib.tune_set("march_tile_rays", old)
 
 
