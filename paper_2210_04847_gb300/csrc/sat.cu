@@ -20,7 +20,10 @@
 //   2. slabs: a block per (g, y) loads the (x, z) slab of those plane tables and
 //      runs the sum along x.
 // The running sums are warp scans over columns (a warp per column).
-// Planes or slabs too large for shared memory take slower global-memory passes.
+// Four or more grids have enough planes to fill the GPU with a warp per plane
+// instead: a lane keeps four running sums along y in registers, then a warp per
+// (g, y, z block) runs the sums along x. Planes or slabs too large for shared
+// memory take slower global-memory passes.
 #include "nacc_internal.cuh"
 
 namespace nacc {
@@ -145,40 +148,120 @@ __global__ void __launch_bounds__(kSliceThreads) sat_slab_kernel(const SatArgs a
         for (int z = lane; z < nz; z += 32) base[xx * plane + z] = p[xx * nz + z];
 }
 
-// Many grids: pass 1 as one thread per corner column (g, x, z), consecutive
-// threads on consecutive z: a running sum along y of the row prefixes, each the
-// popcount of the row's first z bits. Enough threads to fill the GPU, and a few
-// instructions per entry.
-__global__ void __launch_bounds__(kThreads) sat_columns_kernel(const SatArgs a) {
-    const int64_t lines = (int64_t)a.n_grids * (a.r0 + 1) * (a.r2 + 1);
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= lines) return;
-    const int z = (int)(t % (a.r2 + 1));
-    const int64_t gx = t / (a.r2 + 1);  // g * (r0 + 1) + x
-    const int x = (int)(gx % (a.r0 + 1));
-    const int64_t g = gx / (a.r0 + 1);
-    const int64_t step = a.r2 + 1;
-    uint16_t* out = a.sat + gx * (a.r1 + 1) * step + z;
-    out[0] = 0;
-    if (x == 0 || z == 0) {
-        for (int y = 1; y <= a.r1; ++y) out[y * step] = 0;
-        return;
-    }
-    int64_t b = ((g * a.r0 + (x - 1)) * (int64_t)a.r1) * a.r2;  // first bit of row (x - 1, 0)
-    uint32_t s = 0;
-    for (int y = 1; y <= a.r1; ++y, b += a.r2) {
-        uint32_t cnt = 0;
-        int64_t p = b;
-        const int64_t e = b + z;
-        while (p < e) {
-            const int off = (int)(p & 31);
-            const int take = (int)(e - p < 32 - off ? e - p : 32 - off);
-            const uint32_t w = __ldg(a.bits + (p >> 5)) >> off;
-            cnt += __popc(take == 32 ? w : (w & ((1u << take) - 1u)));
-            p += take;
+// Many grids, pass 1: a warp per corner plane (g, x). For each block of 128
+// cells along z, lane l takes corners z = zb + 4l + 1 .. zb + 4l + 4: every row's
+// 128 bits of the block are read by all lanes (broadcast), realigned to the
+// block's first cell by funnel shifts, and a lane's counts are the popcounts of
+// the words below its own plus the masked part of its word; running sums along y
+// are kept in the lane's registers. Bits before the block (zb > 0) are counted by
+// the warp, one word per lane.
+__global__ void __launch_bounds__(kThreads) sat_plane_warp_kernel(const SatArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // g (r0 + 1) + x
+    if (p >= (int64_t)a.n_grids * (a.r0 + 1)) return;                         // whole warps
+    const int x = (int)(p % (a.r0 + 1));
+    const int64_t g = p / (a.r0 + 1);
+    const int ny = a.r1 + 1, nz = a.r2 + 1;
+    uint16_t* out = a.sat + p * (int64_t)ny * nz;
+    const int64_t n_words = ((int64_t)a.n_grids * a.r0 * a.r1 * a.r2 + 31) >> 5;
+    for (int y = lane; y < ny; y += 32) out[(int64_t)y * nz] = 0;  // z = 0
+    const int64_t first = (g * a.r0 + (x - 1)) * (int64_t)a.r1 * a.r2;  // bit of cell (x - 1, 0, 0)
+    const int q = lane >> 3, j0 = 4 * (lane & 7);  // the lane's word of the block and first bit in it
+    constexpr int kRows = 4;  // rows whose words are loaded together
+    for (int zb = 0; zb < a.r2; zb += 128) {
+        uint32_t run[4] = {0u, 0u, 0u, 0u};
+        for (int y0 = 0; y0 < ny; y0 += kRows) {
+            uint32_t w[kRows][5];
+#pragma unroll
+            for (int u = 0; u < kRows; ++u) {
+                const int y = y0 + u;
+                const int64_t k = (first + (int64_t)(y - 1) * a.r2 + zb) >> 5;
+                const bool live = y > 0 && y < ny && x > 0;
+#pragma unroll
+                for (int i = 0; i < 5; ++i) w[u][i] = live && k + i < n_words ? __ldg(a.bits + k + i) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kRows; ++u) {
+                const int y = y0 + u;
+                if (y >= ny) break;  // uniform
+                if (y > 0 && x > 0) {
+                    const int64_t row = first + (int64_t)(y - 1) * a.r2;
+                    uint32_t before = 0;  // bits [row, row + zb)
+                    if (zb > 0) {
+                        for (int64_t w0 = row >> 5; (w0 << 5) < row + zb; w0 += 32) {
+                            const int64_t k = w0 + lane, lo = k << 5;
+                            if (lo < row + zb) {
+                                uint32_t m = k < n_words ? __ldg(a.bits + k) : 0u;
+                                if (lo < row) m &= ~0u << (int)(row - lo);
+                                if (lo + 32 > row + zb) m &= (1u << (int)(row + zb - lo)) - 1u;
+                                before += __popc(m);
+                            }
+                        }
+                        for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(FULL, before, o);
+                    }
+                    const unsigned off = (unsigned)((row + zb) & 31);
+                    uint32_t v[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) v[i] = __funnelshift_r(w[u][i], w[u][i + 1], off);
+                    const uint32_t c1 = __popc(v[0]), c2 = c1 + __popc(v[1]), c3 = c2 + __popc(v[2]);
+                    const uint32_t mine = q == 0 ? v[0] : q == 1 ? v[1] : q == 2 ? v[2] : v[3];
+                    const uint32_t below = before + (q == 0 ? 0u : q == 1 ? c1 : q == 2 ? c2 : c3);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int nb = j0 + i + 1;  // bits of the lane's word below its corner
+                        run[i] += below + __popc(mine & (nb >= 32 ? ~0u : (1u << nb) - 1u));
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int z = zb + 4 * lane + i + 1;
+                    if (z <= a.r2) out[(int64_t)y * nz + z] = (uint16_t)run[i];
+                }
+            }
         }
-        s += cnt;
-        out[y * step] = (uint16_t)s;
+    }
+}
+
+// Many grids, pass 2: a warp per (g, y, block of 128 z); lane l runs the sums
+// along x of corners z = zb + 4l + 1 .. zb + 4l + 4, eight planes loaded ahead.
+__global__ void __launch_bounds__(kThreads) sat_xsum_warp_kernel(const SatArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int zblocks = (a.r2 + 127) / 128;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= (int64_t)a.n_grids * (a.r1 + 1) * zblocks) return;  // whole warps
+    const int zb = 128 * (int)(w % zblocks);
+    const int64_t gy = w / zblocks;  // g (r1 + 1) + y
+    const int y = (int)(gy % (a.r1 + 1));
+    const int64_t g = gy / (a.r1 + 1);
+    const int nx = a.r0 + 1, nz = a.r2 + 1;
+    const int64_t plane = (int64_t)(a.r1 + 1) * nz;
+    const int nv = min(4, a.r2 - (zb + 4 * lane));  // the lane's corners inside the grid (may be <= 0)
+    uint16_t* col = a.sat + g * nx * plane + (int64_t)y * nz + (nv > 0 ? zb + 4 * lane + 1 : 0);
+    uint32_t run[4] = {0u, 0u, 0u, 0u};
+    constexpr int kPlanes = 8;  // planes loaded ahead
+    int x = 0;
+    for (; x + kPlanes <= nx; x += kPlanes) {
+        uint32_t v[kPlanes][4];
+#pragma unroll
+        for (int u = 0; u < kPlanes; ++u)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[u][i] = i < nv ? col[(int64_t)(x + u) * plane + i] : 0u;
+#pragma unroll
+        for (int u = 0; u < kPlanes; ++u)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                run[i] += v[u][i];
+                if (i < nv) col[(int64_t)(x + u) * plane + i] = (uint16_t)run[i];
+            }
+    }
+    for (; x < nx; ++x) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (i < nv) {
+                run[i] += col[(int64_t)x * plane + i];
+                col[(int64_t)x * plane + i] = (uint16_t)run[i];
+            }
+        }
     }
 }
 
@@ -262,21 +345,23 @@ extern "C" int nacc_build_grid_sat(const nacc_grid* grid, uint16_t* sat, void* s
     SatArgs a{grid->bits, sat, grid->res[0], grid->res[1], grid->res[2], (int32_t)grids};
     cudaStream_t st = (cudaStream_t)stream;
     const long long planes = grids * (r0 + 1);
-    // a single grid or two: a block per plane and slab (few blocks, so each short);
-    // more grids: a thread per column (more parallel work, fewer instructions)
+    // up to three grids: a block per plane and slab (few blocks, so each short);
+    // more grids: a warp per plane, then a warp per row of z blocks
     const bool many = grids >= 4;
-    // a plane's bits span at most r1 r2 / 32 + 2 words
     if (many) {
-        const long long cols = planes * (r2 + 1);
-        sat_columns_kernel<<<(unsigned)((cols + kThreads - 1) / kThreads), kThreads, 0, st>>>(a);
+        const long long zblocks = (r2 + 127) / 128, w1 = planes, w2 = grids * (r1 + 1) * zblocks;
+        sat_plane_warp_kernel<<<(unsigned)((w1 * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(a);
+        sat_xsum_warp_kernel<<<(unsigned)((w2 * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(a);
+        return launch_status(cudaGetLastError());
     } else if ((r1 + 1) * (r2 + 1) <= kSliceMax && r1 * r2 / 32 + 2 <= kPlaneWordsMax) {
+        // a plane's bits span at most r1 r2 / 32 + 2 words
         sat_plane_kernel<<<(unsigned)planes, kSliceThreads, 0, st>>>(a);
     } else {
         sat_rows_kernel<<<(unsigned)(planes * (r1 + 1)), 32, 0, st>>>(a);
         const long long ly = planes * (r2 + 1);
         sat_sum_kernel<1><<<(unsigned)((ly + kThreads - 1) / kThreads), kThreads, 0, st>>>(a);
     }
-    if (!many && (r0 + 1) * (r2 + 1) <= kSliceMax) {
+    if ((r0 + 1) * (r2 + 1) <= kSliceMax) {
         sat_slab_kernel<<<(unsigned)(grids * (r1 + 1)), kSliceThreads, 0, st>>>(a);
     } else {
         const long long lx = grids * (r1 + 1) * (r2 + 1);
