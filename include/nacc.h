@@ -546,7 +546,11 @@ int nacc_sample_grid_cells(uint64_t seed, uint64_t stream, int64_t n, const nacc
 #define NACC_TUNE_FUSED_OCCUPANCY 11    /* 0: compiler's register use; 1: nacc_march_fused capped at 64 registers */
 #define NACC_TUNE_MARCH_BOX_TILE 12     /* box walk (grid with its summed-area table, uniform steps): 0 ray by ray;
                                           1, 2, 3 over all chunks of a tile at once, for 4, 5, 6 blocks per SM */
-#define NACC_TUNE_COUNT 13
+#define NACC_TUNE_RENDER_FWD_STAGES 13  /* forward: 0 loads into registers; 2, 3, 4: chunks staged in shared
+                                          memory by bulk copies, that many stages per warp (16-byte aligned
+                                          arrays; others take the register path) */
+#define NACC_TUNE_RENDER_BWD_STAGES 14  /* backward with the saved optical depth: as NACC_TUNE_RENDER_FWD_STAGES */
+#define NACC_TUNE_COUNT 15
 
 /* Set a knob; NACC_ERR_INVALID_ARG for an unknown knob or out-of-range value. */
 int nacc_tune_set(int knob, int value);
@@ -570,12 +574,20 @@ int nacc_tune_get(int knob);
  *   (default 2^22: about a second with the back-off between polls).
  * NACC_TEST_HOOK_WITHHOLD_FIRST_TILE: 0 (default) or 1. With 1 the first tile
  *   never publishes its total, so every wait that reaches it runs out.
+ * The render passes with staged chunks (NACC_TUNE_RENDER_*_STAGES) wait, a
+ * bounded number of polls, for each chunk's bulk copies to land; a wait that
+ * gives up raises NACC_STATUS_TIMEOUT, waits (bounded) for the warp's copies in
+ * flight and ends the warp's walk, leaving its rays' outputs unwritten.
+ * NACC_TEST_HOOK_SPIN_LIMIT also sets that poll budget when below its default.
+ * NACC_TEST_HOOK_OVERSTATE_STAGE_BYTES: 0 (default) or 1. With 1 each warp's
+ *   first chunk announces 16 bytes more than it copies, so its wait runs out.
  * Not synchronised: change hooks only while no other host thread launches
  * library work. NACC_ERR_INVALID_ARG for an unknown hook or a value out of range.
  */
 #define NACC_TEST_HOOK_SPIN_LIMIT 0
 #define NACC_TEST_HOOK_WITHHOLD_FIRST_TILE 1
-#define NACC_TEST_HOOK_COUNT 2
+#define NACC_TEST_HOOK_OVERSTATE_STAGE_BYTES 2
+#define NACC_TEST_HOOK_COUNT 3
 int nacc_test_hook_set(int hook, int value);
 int nacc_test_hook_get(int hook);
 

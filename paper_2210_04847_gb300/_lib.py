@@ -50,7 +50,8 @@ TUNE_PRUNE_TILE_RAYS = 2
 TUNE_KNOBS = {"render_fwd_prefetch": 0, "march_tile_rays": 1, "prune_tile_rays": 2, "march_occupancy": 3,
               "prune_occupancy": 4, "render_fwd_occupancy": 5, "render_bwd_occupancy": 6, "march_unroll": 7,
               "prune_interleave": 8, "render_bwd_prefetch": 9,
-              "march_coarse": 10, "fused_occupancy": 11, "march_box_tile": 12}
+              "march_coarse": 10, "fused_occupancy": 11, "march_box_tile": 12,
+              "render_fwd_stages": 13, "render_bwd_stages": 14}
 
 
 class NaccError(RuntimeError):
@@ -622,7 +623,7 @@ def tune_set(knob, value: int):
     _rc(load().nacc_tune_set(k, int(value)), "nacc_tune_set")
 
 
-TEST_HOOKS = {"spin_limit": 0, "withhold_first_tile": 1}
+TEST_HOOKS = {"spin_limit": 0, "withhold_first_tile": 1, "overstate_stage_bytes": 2}
 SPIN_LIMIT_DEFAULT = 1 << 22
 
 

@@ -29,6 +29,8 @@ CANDIDATES = {
     "render_fwd_occupancy": (0, 1, 2),
     "render_bwd_occupancy": (0, 1, 2),
     "render_bwd_prefetch": (0, 1),
+    "render_fwd_stages": (0, 2, 3, 4),
+    "render_bwd_stages": (0, 2, 3, 4),
 }
 
 
@@ -145,10 +147,17 @@ def tune_hot_path(hp, sc, batch: int = 0, reps: int = 7, flush: Callable[[], Non
     fwd = lambda: hp.render_fwd(S)
     rec.append(tk("render_fwd_prefetch", fwd))
     rec.append(tk("render_fwd_occupancy", fwd))
+    rec.append(tk("render_fwd_stages", fwd))
     hp.render_fwd(S)
     hp.g_color.uniform_(-1e-6, 1e-6)
     rec.append(tk("render_bwd_occupancy", lambda: hp.render_bwd(S)))
     rec.append(tk("render_bwd_prefetch", lambda: hp.render_bwd(S)))
+    # the staged backward reads the optical depth the forward saved
+    saved0 = hp.save_optical_depth
+    hp.save_optical_depth = True
+    hp.render_fwd(S)
+    rec.append(tk("render_bwd_stages", lambda: hp.render_bwd(S)))
+    hp.save_optical_depth = saved0
     # forward + backward with the optical depth recomputed, or saved by the forward
     times = {}
     for saved in (False, True):

@@ -40,9 +40,11 @@ int g_tune[NACC_TUNE_COUNT] = {
     0,  // NACC_TUNE_MARCH_COARSE
     1,  // NACC_TUNE_FUSED_OCCUPANCY
     0,  // NACC_TUNE_MARCH_BOX_TILE
+    0,  // NACC_TUNE_RENDER_FWD_STAGES
+    2,  // NACC_TUNE_RENDER_BWD_STAGES
 };
-const int g_tune_lo[NACC_TUNE_COUNT] = {0, 1, 2, 0, 0, 0, 0, 0, 2, 0, 0, 0, 0};
-const int g_tune_hi[NACC_TUNE_COUNT] = {1, 32, 32, 1, 2, 2, 2, 1, 4, 1, 1, 1, 3};
+const int g_tune_lo[NACC_TUNE_COUNT] = {0, 1, 2, 0, 0, 0, 0, 0, 2, 0, 0, 0, 0, 0, 0};
+const int g_tune_hi[NACC_TUNE_COUNT] = {1, 32, 32, 1, 2, 2, 2, 1, 4, 1, 1, 1, 3, 4, 4};
 }  // namespace
 
 int tune_get(int knob) { return (knob >= 0 && knob < NACC_TUNE_COUNT) ? g_tune[knob] : 0; }
@@ -50,13 +52,14 @@ int tune_get(int knob) { return (knob >= 0 && knob < NACC_TUNE_COUNT) ? g_tune[k
 namespace {
 // Test hooks of the look-back waits, read at every launch (defaults: the full
 // poll budget, every tile publishes).
-int g_hook[NACC_TEST_HOOK_COUNT] = {kSpinLimit, 0};
-const int g_hook_lo[NACC_TEST_HOOK_COUNT] = {0, 0};
-const int g_hook_hi[NACC_TEST_HOOK_COUNT] = {kSpinLimit, 1};
+int g_hook[NACC_TEST_HOOK_COUNT] = {kSpinLimit, 0, 0};
+const int g_hook_lo[NACC_TEST_HOOK_COUNT] = {0, 0, 0};
+const int g_hook_hi[NACC_TEST_HOOK_COUNT] = {kSpinLimit, 1, 1};
 }  // namespace
 
 LookbackHooks lookback_hooks() {
-    return LookbackHooks{g_hook[NACC_TEST_HOOK_WITHHOLD_FIRST_TILE] ? 0ull : kFlagInc, g_hook[NACC_TEST_HOOK_SPIN_LIMIT]};
+    return LookbackHooks{g_hook[NACC_TEST_HOOK_WITHHOLD_FIRST_TILE] ? 0ull : kFlagInc, g_hook[NACC_TEST_HOOK_SPIN_LIMIT],
+                         g_hook[NACC_TEST_HOOK_OVERSTATE_STAGE_BYTES]};
 }
 
 }  // namespace nacc
@@ -66,6 +69,8 @@ extern "C" int nacc_tune_set(int knob, int value) {
     if (value < nacc::g_tune_lo[knob] || value > nacc::g_tune_hi[knob]) return NACC_ERR_INVALID_ARG;
     if (knob == NACC_TUNE_PRUNE_TILE_RAYS && (value & 1)) return NACC_ERR_INVALID_ARG;
     if (knob == NACC_TUNE_PRUNE_INTERLEAVE && value != 2 && value != 4) return NACC_ERR_INVALID_ARG;
+    if ((knob == NACC_TUNE_RENDER_FWD_STAGES || knob == NACC_TUNE_RENDER_BWD_STAGES) && value == 1)
+        return NACC_ERR_INVALID_ARG;
     nacc::g_tune[knob] = value;
     return NACC_OK;
 }

@@ -73,6 +73,8 @@ struct FwdArgs {
     float* depth;
     float* optical_depth;
     int32_t* d_status;
+    int stage_polls;       // staged kernel: polls of a stage's barrier before the walk gives up
+    unsigned stage_extra;  // staged kernel, test hook: bytes announced beyond the first chunk's copies
 };
 
 constexpr int kRenderThreads = 128;
@@ -599,6 +601,8 @@ struct BwdArgs {
     int32_t* d_status;
     const float* g_weights;  // weights mode: dL/dw_i (no rgb, g_color, d_rgbs)
     const float* g_ref;      // weights mode, centred input: dL/dw_i = g_ref[r] + g_weights[i]
+    int stage_polls;         // as FwdArgs
+    unsigned stage_extra;
 };
 
 // tau of both samples of the lane's pair in chunk c of a ray (pass A of the backward).
@@ -817,6 +821,421 @@ __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const 
 }
 
 // ---------------------------------------------------------------------------
+// forward and backward with the chunks staged in shared memory by bulk copies
+// ---------------------------------------------------------------------------
+//
+// The same walk, lane mapping and arithmetic as the register kernels above (so
+// the results are bit-identical), but a chunk's arrays reach the warp through
+// a ring of NST shared-memory stages: lane 0 issues one bulk copy per array and
+// chunk, up to NST - 1 chunks ahead of the chunk being computed, across the
+// rays of the warp's group (the backward walks each ray's chunks last to
+// first). Several chunks' loads are then in flight per warp without holding
+// registers. A stage holds a 68-sample window: the chunk's 64 samples from
+// the 16-byte boundary at or below its first pair. Samples from n4 =
+// n_samples & ~3 on (the arrays' last partial 16 bytes) are read from global
+// memory directly. Needs t_starts, t_ends, sigmas, rgbs (and the optical
+// depth in the backward) 16-byte aligned; the entry points use the register
+// kernels otherwise.
+
+constexpr int kSpan = 68;                        // samples per stage window
+constexpr int kFwdStage = 3 * kSpan + 3 * kSpan;  // t_s, t_e, sigma, rgb (floats)
+constexpr int kBwdStage = 4 * kSpan + 3 * kSpan;  // t_s, t_e, sigma, O, rgb
+constexpr int kBarBytes = 256;                   // mbarriers of the block (up to 8 stages x 4 warps)
+constexpr int kStageWaitPolls = 1 << 20;         // polls of a stage's barrier before the walk gives up
+constexpr int kBulkMinBlocks = 8;                // register cap of the staged kernels (64 per thread)
+
+static_assert((kRenderThreads / 32) * 8 * 8 <= kBarBytes, "barrier area");
+static_assert(kSpan % 4 == 0 && kFwdStage % 4 == 0 && kBwdStage % 4 == 0, "16-byte stage layout");
+
+size_t bulk_smem_bytes(int nst, bool bwd) {
+    return kBarBytes + (size_t)(kRenderThreads / 32) * nst * (bwd ? kBwdStage : kFwdStage) * sizeof(float);
+}
+
+// Copied window [lo, hi) of chunk c of the run [rlo, rhi): from the 16-byte
+// boundary at or below the chunk's first pair to the one at or above its last
+// sample, clipped to n4.
+struct Win {
+    unsigned lo, hi;
+};
+
+__device__ __forceinline__ Win chunk_window(unsigned rlo, unsigned rhi, int c, unsigned n4) {
+    const unsigned c0 = (rlo & ~1u) + ((unsigned)c << 6);
+    const unsigned end = min(c0 + 64u, rhi);
+    Win w;
+    w.lo = c0 & ~3u;
+    w.hi = min((end + 3u) & ~3u, n4);
+    if (w.hi < w.lo) w.hi = w.lo;
+    return w;
+}
+
+// Lane 0: announce the window's bytes on the stage's barrier and copy the arrays
+// (od may be null: forward layout).
+__device__ __forceinline__ void issue_window(float* st, uint64_t* bar, Win w, const float* ts, const float* te,
+                                             const float* sg, const float* od, const float* rgb, unsigned extra = 0) {
+    const unsigned n = w.hi - w.lo, b = 4u * n;
+    mbar_arrive_expect_tx(bar, (od ? 7u * b : 6u * b) + extra);
+    if (n) {
+        bulk_copy_g2s(st, ts + w.lo, b, bar);
+        bulk_copy_g2s(st + kSpan, te + w.lo, b, bar);
+        bulk_copy_g2s(st + 2 * kSpan, sg + w.lo, b, bar);
+        if (od) {
+            bulk_copy_g2s(st + 3 * kSpan, od + w.lo, b, bar);
+            bulk_copy_g2s(st + 4 * kSpan, rgb + 3 * (size_t)w.lo, 3u * b, bar);
+        } else {
+            bulk_copy_g2s(st + 3 * kSpan, rgb + 3 * (size_t)w.lo, 3u * b, bar);
+        }
+    }
+}
+
+// The lane's pair j0, j0 + 1 of a run [lo, hi) from a stage holding window w
+// (rgb at st + rgb_at), as load_pair gives it; samples past the window (at
+// or beyond n4) come from global memory.
+__device__ __forceinline__ void stage_pair(const float* st, int rgb_at, Win w, const float* __restrict__ ts,
+                                           const float* __restrict__ te, const float* __restrict__ sig,
+                                           const float* __restrict__ rgbs, unsigned j0, unsigned lo, unsigned hi,
+                                           Pair& q) {
+    q.v0 = j0 >= lo && j0 < hi;
+    q.v1 = j0 + 1 >= lo && j0 + 1 < hi;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) q.s0[k] = q.s1[k] = q.sg[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) q.rgb[k] = 0.0f;
+    const unsigned p = j0 - w.lo;  // even: j0 and w.lo are
+    if (q.v0 && q.v1 && j0 + 1 < w.hi) {
+        const float2 u = *reinterpret_cast<const float2*>(st + p);
+        const float2 v = *reinterpret_cast<const float2*>(st + kSpan + p);
+        const float2 g = *reinterpret_cast<const float2*>(st + 2 * kSpan + p);
+        const float2* c = reinterpret_cast<const float2*>(st + rgb_at + 3 * p);
+        const float2 c0 = c[0], c1 = c[1], c2 = c[2];
+        q.s0[0] = u.x; q.s0[1] = u.y;
+        q.s1[0] = v.x; q.s1[1] = v.y;
+        q.sg[0] = g.x; q.sg[1] = g.y;
+        q.rgb[0] = c0.x; q.rgb[1] = c0.y; q.rgb[2] = c1.x;
+        q.rgb[3] = c1.y; q.rgb[4] = c2.x; q.rgb[5] = c2.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (k == 0 ? q.v0 : q.v1) {
+                const unsigned j = j0 + k;
+                if (j < w.hi) {
+                    const unsigned l = p + k;
+                    q.s0[k] = st[l];
+                    q.s1[k] = st[kSpan + l];
+                    q.sg[k] = st[2 * kSpan + l];
+                    q.rgb[3 * k] = st[rgb_at + 3 * l];
+                    q.rgb[3 * k + 1] = st[rgb_at + 3 * l + 1];
+                    q.rgb[3 * k + 2] = st[rgb_at + 3 * l + 2];
+                } else {
+                    q.s0[k] = __ldg(ts + j);
+                    q.s1[k] = __ldg(te + j);
+                    q.sg[k] = __ldg(sig + j);
+                    q.rgb[3 * k] = __ldg(rgbs + 3 * (size_t)j);
+                    q.rgb[3 * k + 1] = __ldg(rgbs + 3 * (size_t)j + 1);
+                    q.rgb[3 * k + 2] = __ldg(rgbs + 3 * (size_t)j + 2);
+                }
+            }
+        }
+    }
+}
+
+// Cursor over the chunks of the rays of a warp's group: rays in order (set bits
+// of `todo`, lane i = ray i), chunks first to last, or last to first (REV).
+template <bool REV>
+struct ChunkCursor {
+    unsigned todo, lo, hi;
+    int i, c, nch;
+    __device__ __forceinline__ void ray(int my_off, int my_cnt, int my_nch) {
+        i = __ffs(todo) - 1;
+        todo &= todo - 1;
+        lo = (unsigned)__shfl_sync(FULL, my_off, i);
+        hi = lo + (unsigned)__shfl_sync(FULL, my_cnt, i);
+        nch = __shfl_sync(FULL, my_nch, i);
+        c = REV ? nch - 1 : 0;
+    }
+    // next chunk; returns true when it starts a new ray
+    __device__ __forceinline__ bool next(int my_off, int my_cnt, int my_nch) {
+        c += REV ? -1 : 1;
+        if (REV ? c < 0 : c >= nch) {
+            if (todo) ray(my_off, my_cnt, my_nch);
+            return true;
+        }
+        return false;
+    }
+};
+
+// After a stage wait gave up: report it, then wait (bounded) for the copies the
+// warp has in flight, so that none lands after the block has exited. A first
+// chunk whose announced bytes were overstated by the test hook never completes
+// and has no copy outstanding: it is not waited for.
+template <int NST>
+__device__ __forceinline__ void drain_stages(uint64_t* bars, int k, int total, bool poisoned, int32_t* d_status,
+                                             int lane) {
+    if (lane == 0) raise_status(d_status, NACC_STATUS_TIMEOUT);
+    const int end = min(k + NST, total);
+    for (int d = k; d < end; ++d)
+        if (!(d == 0 && poisoned)) mbar_wait_bounded(&bars[d % NST], (unsigned)(d / NST) & 1u, kSpinLimit);
+    __syncwarp();
+}
+
+template <int NST>
+__global__ void __launch_bounds__(kRenderThreads, kBulkMinBlocks) render_fwd_bulk_kernel(const FwdArgs a) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(dyn_smem) + wib * NST;
+    float* stages = reinterpret_cast<float*>(dyn_smem + kBarBytes) + (size_t)wib * NST * kFwdStage;
+    const int ray0 = global_warp() * kGroup;
+    if (ray0 >= a.n_rays) return;
+    const int nr = min(kGroup, a.n_rays - ray0);
+    int my_off, my_cnt;
+    load_group(a.packed_info, ray0, nr, a.n_samples, a.d_status, lane, my_off, my_cnt);
+    if (lane < nr && my_cnt == 0) {
+        const int r = ray0 + lane;
+        if (a.color) {
+            a.color[3 * (size_t)r] = 0.0f;
+            a.color[3 * (size_t)r + 1] = 0.0f;
+            a.color[3 * (size_t)r + 2] = 0.0f;
+        }
+        if (a.opacity) a.opacity[r] = 0.0f;
+        if (a.depth) a.depth[r] = 0.0f;
+    }
+    const unsigned todo = __ballot_sync(FULL, my_cnt > 0);
+    if (todo == 0u) return;
+    const int my_nch = my_cnt > 0 ? (int)(((unsigned)my_off + my_cnt - ((unsigned)my_off & ~1u) + 63u) >> 6) : 0;
+    int total = my_nch;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(FULL, total, o);
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    const unsigned n4 = (unsigned)a.n_samples & ~3u;
+
+    ChunkCursor<false> P;  // producer: the next chunk to copy
+    P.todo = todo;
+    P.ray(my_off, my_cnt, my_nch);
+    const int pre = min(NST, total);
+    for (int k = 0; k < pre; ++k) {
+        if (lane == 0)
+            issue_window(stages + k * kFwdStage, &bars[k], chunk_window(P.lo, P.hi, P.c, n4), a.t_starts, a.t_ends,
+                         a.sigmas, nullptr, a.rgbs, k == 0 ? a.stage_extra : 0u);
+        P.next(my_off, my_cnt, my_nch);
+    }
+
+    ChunkCursor<false> C;  // consumer: the chunk being computed
+    C.todo = todo;
+    C.ray(my_off, my_cnt, my_nch);
+    float carry = 0.0f;
+    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, op = 0.0f, dp = 0.0f;
+    for (int k = 0; k < total; ++k) {
+        const int s = k % NST;
+        float* st = stages + s * kFwdStage;
+        const bool ok = mbar_wait_bounded(&bars[s], (unsigned)(k / NST) & 1u, a.stage_polls);
+        if (!__all_sync(FULL, ok)) {
+            drain_stages<NST>(bars, k, total, a.stage_extra != 0u, a.d_status, lane);
+            return;
+        }
+        const unsigned qj0 = (C.lo & ~1u) + ((unsigned)C.c << 6) + 2 * lane;
+        Pair q;
+        stage_pair(st, 3 * kSpan, chunk_window(C.lo, C.hi, C.c, n4), a.t_starts, a.t_ends, a.sigmas, a.rgbs, qj0,
+                   C.lo, C.hi, q);
+        const float tau0 = q.v0 ? tau_of(q.s0[0], q.s1[0], q.sg[0]) : 0.0f;
+        const float tau1 = q.v1 ? tau_of(q.s0[1], q.s1[1], q.sg[1]) : 0.0f;
+        float O0, O1;
+        pair_optical_depth(tau0, tau1, carry, lane, O0, O1);
+        const float w0 = q.v0 ? __expf(-O0) * alpha_of(tau0) : 0.0f;
+        const float w1 = q.v1 ? __expf(-O1) * alpha_of(tau1) : 0.0f;
+        c0 += w0 * q.rgb[0] + w1 * q.rgb[3];
+        c1 += w0 * q.rgb[1] + w1 * q.rgb[4];
+        c2 += w0 * q.rgb[2] + w1 * q.rgb[5];
+        op += w0 + w1;
+        dp += w0 * ((q.s0[0] + q.s1[0]) * 0.5f) + w1 * ((q.s0[1] + q.s1[1]) * 0.5f);
+        if (a.optical_depth) {
+            if (q.v0) a.optical_depth[qj0] = O0;
+            if (q.v1) a.optical_depth[qj0 + 1] = O1;
+        }
+        // the stage is read: refill it with the chunk NST ahead
+        __syncwarp();
+        if (k + NST < total) {
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                issue_window(st, &bars[s], chunk_window(P.lo, P.hi, P.c, n4), a.t_starts, a.t_ends, a.sigmas, nullptr,
+                             a.rgbs);
+            }
+            P.next(my_off, my_cnt, my_nch);
+        }
+        if (C.c + 1 == C.nch) {
+            const float sum = warp_sum5(c0, c1, c2, op, dp, lane);
+            const size_t r = (size_t)ray0 + C.i;
+            if (lane == 0 && a.color) a.color[3 * r] = sum;
+            if (lane == 4 && a.color) a.color[3 * r + 1] = sum;
+            if (lane == 8 && a.color) a.color[3 * r + 2] = sum;
+            if (lane == 12 && a.opacity) a.opacity[r] = sum;
+            if (lane == 16 && a.depth) a.depth[r] = sum;
+            carry = 0.0f;
+            c0 = c1 = c2 = op = dp = 0.0f;
+        }
+        C.next(my_off, my_cnt, my_nch);
+    }
+}
+
+// Backward with the optical depth saved by the forward (colour mode).
+template <int NST>
+__global__ void __launch_bounds__(kRenderThreads, kBulkMinBlocks) render_bwd_bulk_kernel(const BwdArgs a) {
+    __shared__ float s_ray[kRenderThreads / 32][kGroup][kRayVals];
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float(*ray_vals)[kRayVals] = s_ray[wib];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(dyn_smem) + wib * NST;
+    float* stages = reinterpret_cast<float*>(dyn_smem + kBarBytes) + (size_t)wib * NST * kBwdStage;
+    const int ray0 = global_warp() * kGroup;
+    if (ray0 >= a.n_rays) return;
+    const int nr = min(kGroup, a.n_rays - ray0);
+    int my_off, my_cnt;
+    load_group(a.packed_info, ray0, nr, a.n_samples, a.d_status, lane, my_off, my_cnt);
+    if (lane < nr && my_cnt > 0) {
+        const size_t r = (size_t)ray0 + lane;
+        float* v = ray_vals[lane];
+        v[0] = a.g_color ? a.g_color[3 * r] : 0.0f;
+        v[1] = a.g_color ? a.g_color[3 * r + 1] : 0.0f;
+        v[2] = a.g_color ? a.g_color[3 * r + 2] : 0.0f;
+        v[3] = a.g_opacity ? a.g_opacity[r] : 0.0f;
+        v[4] = a.g_depth ? a.g_depth[r] : 0.0f;
+        v[5] = __ldg(a.rgbs + 3 * (size_t)my_off);
+        v[6] = __ldg(a.rgbs + 3 * (size_t)my_off + 1);
+        v[7] = __ldg(a.rgbs + 3 * (size_t)my_off + 2);
+        v[8] = (__ldg(a.t_starts + my_off) + __ldg(a.t_ends + my_off)) * 0.5f;
+    }
+    const unsigned todo = __ballot_sync(FULL, my_cnt > 0);
+    if (todo == 0u) return;
+    const int my_nch = my_cnt > 0 ? (int)(((unsigned)my_off + my_cnt - ((unsigned)my_off & ~1u) + 63u) >> 6) : 0;
+    int total = my_nch;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(FULL, total, o);
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    const unsigned n4 = (unsigned)a.n_samples & ~3u;
+
+    ChunkCursor<true> P;
+    P.todo = todo;
+    P.ray(my_off, my_cnt, my_nch);
+    const int pre = min(NST, total);
+    for (int k = 0; k < pre; ++k) {
+        if (lane == 0)
+            issue_window(stages + k * kBwdStage, &bars[k], chunk_window(P.lo, P.hi, P.c, n4), a.t_starts, a.t_ends,
+                         a.sigmas, a.optical_depth, a.rgbs, k == 0 ? a.stage_extra : 0u);
+        P.next(my_off, my_cnt, my_nch);
+    }
+
+    ChunkCursor<true> C;
+    C.todo = todo;
+    C.ray(my_off, my_cnt, my_nch);
+    // per-ray values (see render_bwd_kernel for the centred form)
+    float gc0 = 0.0f, gc1 = 0.0f, gc2 = 0.0f, gd = 0.0f;
+    float r_ref = 0.0f, g_ref = 0.0f, b_ref = 0.0f, tm_ref = 0.0f, a_ref = 0.0f;
+    int last_lane = 0;
+    bool last_odd = false;
+    float t_end = 0.0f, carry_s = 0.0f;
+    auto begin_ray = [&]() {
+        const float* rv = ray_vals[C.i];
+        gc0 = rv[0];
+        gc1 = rv[1];
+        gc2 = rv[2];
+        const float ga = rv[3];
+        gd = rv[4];
+        r_ref = rv[5];
+        g_ref = rv[6];
+        b_ref = rv[7];
+        tm_ref = rv[8];
+        a_ref = gc0 * r_ref + gc1 * g_ref + gc2 * b_ref + ga + gd * tm_ref;
+        const unsigned last = C.hi - 1 - (C.lo & ~1u);
+        last_lane = (int)((last >> 1) & 31);
+        last_odd = (last & 1) != 0;
+        t_end = 0.0f;
+        carry_s = 0.0f;
+    };
+    __syncwarp();  // ray_vals written by their lanes
+    begin_ray();
+    for (int k = 0; k < total; ++k) {
+        const int s = k % NST;
+        float* st = stages + s * kBwdStage;
+        const bool ok = mbar_wait_bounded(&bars[s], (unsigned)(k / NST) & 1u, a.stage_polls);
+        if (!__all_sync(FULL, ok)) {
+            drain_stages<NST>(bars, k, total, a.stage_extra != 0u, a.d_status, lane);
+            return;
+        }
+        const Win w = chunk_window(C.lo, C.hi, C.c, n4);
+        const unsigned j0 = (C.lo & ~1u) + ((unsigned)C.c << 6) + 2 * lane;
+        Pair q;
+        stage_pair(st, 4 * kSpan, w, a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0, C.lo, C.hi, q);
+        float O0 = 0.0f, O1 = 0.0f;
+        {
+            const unsigned p = j0 - w.lo;
+            if (q.v0) O0 = j0 < w.hi ? st[3 * kSpan + p] : __ldg(a.optical_depth + j0);
+            if (q.v1) O1 = j0 + 1 < w.hi ? st[3 * kSpan + p + 1] : __ldg(a.optical_depth + j0 + 1);
+        }
+        const float tau0 = q.v0 ? tau_of(q.s0[0], q.s1[0], q.sg[0]) : 0.0f;
+        const float tau1 = q.v1 ? tau_of(q.s0[1], q.s1[1], q.sg[1]) : 0.0f;
+        // the stage is read: refill it with the chunk NST ahead
+        __syncwarp();
+        if (k + NST < total) {
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                issue_window(st, &bars[s], chunk_window(P.lo, P.hi, P.c, n4), a.t_starts, a.t_ends, a.sigmas,
+                             a.optical_depth, a.rgbs);
+            }
+            P.next(my_off, my_cnt, my_nch);
+        }
+        const float T0 = __expf(-O0);
+        const float T1 = __expf(-O1);
+        const float T2 = __expf(-__fadd_rn(O1, tau1));
+        const float Tn0 = q.v1 ? T1 : __expf(-__fadd_rn(O0, tau0));
+        if (C.c == C.nch - 1) t_end = __shfl_sync(FULL, last_odd ? T2 : Tn0, last_lane);
+        const float w0 = q.v0 ? T0 * alpha_of(tau0) : 0.0f;
+        const float w1 = q.v1 ? T1 * alpha_of(tau1) : 0.0f;
+        const float tm0 = (q.s0[0] + q.s1[0]) * 0.5f, tm1 = (q.s0[1] + q.s1[1]) * 0.5f;
+        const float b0 = gc0 * (q.rgb[0] - r_ref) + gc1 * (q.rgb[1] - g_ref) + gc2 * (q.rgb[2] - b_ref) +
+                         gd * (tm0 - tm_ref);
+        const float b1 = gc0 * (q.rgb[3] - r_ref) + gc1 * (q.rgb[4] - g_ref) + gc2 * (q.rgb[5] - b_ref) +
+                         gd * (tm1 - tm_ref);
+        const float bw0 = q.v0 ? b0 * w0 : 0.0f;
+        const float bw1 = q.v1 ? b1 * w1 : 0.0f;
+        const float suf = warp_incl_suffix(bw0 + bw1, lane);
+        float later = __shfl_down_sync(FULL, suf, 1);
+        if (lane == 31) later = 0.0f;
+        const float S1 = carry_s + later;
+        const float S0 = S1 + bw1;
+        carry_s = carry_s + __shfl_sync(FULL, suf, 0);
+        const float base_g = a_ref * t_end;
+        const float ds0 = (q.s1[0] - q.s0[0]) * (base_g + (b0 * Tn0 - S0));
+        const float ds1 = (q.s1[1] - q.s0[1]) * (base_g + (b1 * T2 - S1));
+        if (q.v0 && q.v1) {
+            *reinterpret_cast<float2*>(a.d_sigmas + j0) = make_float2(ds0, ds1);
+            float2* dr = reinterpret_cast<float2*>(a.d_rgbs + 3 * (size_t)j0);
+            dr[0] = make_float2(w0 * gc0, w0 * gc1);
+            dr[1] = make_float2(w0 * gc2, w1 * gc0);
+            dr[2] = make_float2(w1 * gc1, w1 * gc2);
+        } else if (q.v0) {
+            a.d_sigmas[j0] = ds0;
+            a.d_rgbs[3 * (size_t)j0] = w0 * gc0;
+            a.d_rgbs[3 * (size_t)j0 + 1] = w0 * gc1;
+            a.d_rgbs[3 * (size_t)j0 + 2] = w0 * gc2;
+        } else if (q.v1) {
+            a.d_sigmas[j0 + 1] = ds1;
+            a.d_rgbs[3 * (size_t)j0 + 3] = w1 * gc0;
+            a.d_rgbs[3 * (size_t)j0 + 4] = w1 * gc1;
+            a.d_rgbs[3 * (size_t)j0 + 5] = w1 * gc2;
+        }
+        if (C.next(my_off, my_cnt, my_nch) && k + 1 < total) begin_ray();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // ray index of every sample
 // ---------------------------------------------------------------------------
 
@@ -859,6 +1278,50 @@ int group_blocks(int n_rays) {
     return (int)((groups + kRenderThreads / 32 - 1) / (kRenderThreads / 32));
 }
 
+// Launch of a bulk-staged render kernel (the shared-memory carveout raised once
+// per kernel, so that the stages of several blocks fit on an SM).
+template <typename K, typename A>
+int launch_bulk(K kernel, bool& carveout_set, int nst, bool bwd, int n_rays, cudaStream_t st, const A& a) {
+    if (!carveout_set) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        carveout_set = true;
+    }
+    kernel<<<group_blocks(n_rays), kRenderThreads, bulk_smem_bytes(nst, bwd), st>>>(a);
+    return launch_status(cudaGetLastError());
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Stages 2, 3 or 4 per warp. (Registers capped for 12 blocks per SM instead of 8
+// spill and measured slower in both passes.)
+// Poll budget of the stage waits and the test hook's overstated bytes.
+template <typename A>
+void set_stage_hooks(A& a) {
+    const LookbackHooks h = lookback_hooks();
+    a.stage_polls = h.spin_limit < kSpinLimit ? h.spin_limit : kStageWaitPolls;
+    a.stage_extra = h.overstate_stage ? 16u : 0u;
+}
+
+int launch_fwd_bulk(int nst, int n_rays, cudaStream_t st, FwdArgs a) {
+    set_stage_hooks(a);
+    static bool set2, set3, set4;
+    switch (nst) {
+        case 2: return launch_bulk(render_fwd_bulk_kernel<2>, set2, 2, false, n_rays, st, a);
+        case 3: return launch_bulk(render_fwd_bulk_kernel<3>, set3, 3, false, n_rays, st, a);
+        default: return launch_bulk(render_fwd_bulk_kernel<4>, set4, 4, false, n_rays, st, a);
+    }
+}
+
+int launch_bwd_bulk(int nst, int n_rays, cudaStream_t st, BwdArgs a) {
+    set_stage_hooks(a);
+    static bool set2, set3, set4;
+    switch (nst) {
+        case 2: return launch_bulk(render_bwd_bulk_kernel<2>, set2, 2, true, n_rays, st, a);
+        case 3: return launch_bulk(render_bwd_bulk_kernel<3>, set3, 3, true, n_rays, st, a);
+        default: return launch_bulk(render_bwd_bulk_kernel<4>, set4, 4, true, n_rays, st, a);
+    }
+}
+
 bool sizes_ok(int32_t n_rays, int64_t n_samples) {
     return n_rays >= 0 && n_samples >= 0 && n_samples < (1LL << 31);
 }
@@ -882,6 +1345,9 @@ extern "C" int nacc_render_fwd(const int32_t* packed_info, int32_t n_rays, const
     FwdArgs a{packed_info, n_rays, t_starts, t_ends, sigmas, rgbs, n_samples, color, opacity, depth, optical_depth, d_status};
     const int nb = group_blocks(n_rays);
     cudaStream_t st = (cudaStream_t)stream;
+    const int nst = tune_get(NACC_TUNE_RENDER_FWD_STAGES);
+    if (nst >= 2 && n_samples > 0 && aligned16(t_starts) && aligned16(t_ends) && aligned16(sigmas) && aligned16(rgbs))
+        return launch_fwd_bulk(nst, n_rays, st, a);
     const bool pf = tune_get(NACC_TUNE_RENDER_FWD_PREFETCH) != 0;
     switch (tune_get(NACC_TUNE_RENDER_OCCUPANCY)) {
         case 1:
@@ -984,6 +1450,10 @@ extern "C" int nacc_render_bwd(const int32_t* packed_info, int32_t n_rays, const
               g_color, g_opacity, g_depth, d_sigmas, d_rgbs, d_status, nullptr, nullptr};
     const int nb = group_blocks(n_rays);
     cudaStream_t st = (cudaStream_t)stream;
+    const int nst = tune_get(NACC_TUNE_RENDER_BWD_STAGES);
+    if (nst >= 2 && n_samples > 0 && optical_depth && aligned16(t_starts) && aligned16(t_ends) && aligned16(sigmas) &&
+        aligned16(rgbs) && aligned16(optical_depth))
+        return launch_bwd_bulk(nst, n_rays, st, a);
     const bool pf = tune_get(NACC_TUNE_RENDER_BWD_PREFETCH) != 0;
     switch (tune_get(NACC_TUNE_RENDER_BWD_OCCUPANCY)) {
         case 1:

@@ -142,10 +142,12 @@ def test_fused_and_density_field_arguments_rejected_on_host(libs):
 def test_lookback_test_hooks_validate_and_default(libs):
     lib, _ = libs
     assert lib.nacc_test_hook_get(0) == 1 << 22 and lib.nacc_test_hook_get(1) == 0
+    assert lib.nacc_test_hook_get(2) == 0
     assert lib.nacc_test_hook_set(0, -1) == _lib.ERR_INVALID_ARG
     assert lib.nacc_test_hook_set(0, (1 << 22) + 1) == _lib.ERR_INVALID_ARG
     assert lib.nacc_test_hook_set(1, 2) == _lib.ERR_INVALID_ARG
-    assert lib.nacc_test_hook_set(2, 0) == _lib.ERR_INVALID_ARG
+    assert lib.nacc_test_hook_set(2, 2) == _lib.ERR_INVALID_ARG
+    assert lib.nacc_test_hook_set(3, 0) == _lib.ERR_INVALID_ARG
     assert lib.nacc_test_hook_get(7) == _lib.ERR_INVALID_ARG
     assert lib.nacc_test_hook_set(0, 17) == _lib.OK and lib.nacc_test_hook_get(0) == 17
     assert lib.nacc_test_hook_set(0, 1 << 22) == _lib.OK and lib.nacc_test_hook_get(0) == 1 << 22

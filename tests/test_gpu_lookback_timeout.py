@@ -28,6 +28,7 @@ GUARD = 4096
 def hooks():
     yield _lib
     _lib.test_hook_set("withhold_first_tile", 0)
+    _lib.test_hook_set("overstate_stage_bytes", 0)
     _lib.test_hook_set("spin_limit", _lib.SPIN_LIMIT_DEFAULT)
 
 
@@ -110,3 +111,57 @@ def test_prune_wait_runs_out_and_reports_timeout(hooks, orc):
     again = prune(M)
     assert again[5] == 0 and again[4] == total and torch.equal(again[0], good[0])
     assert torch.equal(again[3][:total], good[3][:total])
+
+
+@pytest.mark.parametrize("which", ["fwd", "bwd"])
+def test_staged_render_wait_runs_out_and_reports_timeout(hooks, orc, which):
+    """The render passes with chunks staged by bulk copies wait for each chunk's
+    copies on a barrier. A hook makes each warp's first chunk announce more bytes
+    than it copies, so that wait never completes: the call returns, the status
+    word holds NACC_STATUS_TIMEOUT, nothing past the arrays is written, and with
+    the hook off the same calls give the same results as before."""
+    w = synth.bounded_config(9, n_rays=3000, device="cuda")
+    m = orc.march(w.rays_o, w.rays_d, w.bits, w.res, w.aabb, w.near_plane, w.far_plane, w.dt_min, w.dt_max, w.cone,
+                  w.max_steps)
+    sig, rgb = synth.sample_field(w.scenes[0], w.rays_o, w.rays_d, m.t_starts, m.t_ends, m.ray_indices)
+    R, M = w.n_rays, m.n_samples
+    pi, ts, te, sg, cl = dev(m.packed_info), dev(m.t_starts), dev(m.t_ends), dev(sig), dev(rgb)
+    gc = dev((synth.rand_uniform(9, 4, 3 * R, -1, 1).reshape(R, 3) / R).astype(np.float32))
+
+    def run():
+        col = torch.full((R, 3), np.nan, device="cuda")
+        od = torch.full((M + GUARD,), np.nan, device="cuda")
+        ds = torch.full((M + GUARD,), np.nan, device="cuda")
+        dr = torch.full((M + GUARD, 3), np.nan, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        _lib.render_fwd(pi, ts, te, sg, cl, M, col, None, None, optical_depth=od[:M], d_status=st)
+        torch.cuda.synchronize()
+        s_fwd = int(st.item())
+        _lib.render_bwd(pi, ts, te, sg, cl, M, gc, None, None, ds[:M], dr[:M], optical_depth=od[:M], d_status=st)
+        torch.cuda.synchronize()
+        return col, od, ds, dr, s_fwd, int(st.item())
+
+    knob = "render_%s_stages" % which
+    old = _lib.tune_get(knob)
+    _lib.tune_set(knob, 2)
+    try:
+        good = run()
+        assert good[4] == 0 and good[5] == 0
+        hooks.test_hook_set("spin_limit", 64)
+        hooks.test_hook_set("overstate_stage_bytes", 1)
+        col, od, ds, dr, s_fwd, s_all = run()
+        if which == "fwd":
+            assert s_fwd & _lib.STATUS_TIMEOUT
+        else:
+            assert s_fwd == 0 and s_all & _lib.STATUS_TIMEOUT
+            assert torch.equal(od[:M].view(torch.int32), good[1][:M].view(torch.int32))
+        # the walks that gave up left their rays unwritten; nothing past the arrays
+        assert torch.isnan(od[M:]).all() and torch.isnan(ds[M:]).all() and torch.isnan(dr[M:]).all()
+        hooks.test_hook_set("overstate_stage_bytes", 0)
+        hooks.test_hook_set("spin_limit", _lib.SPIN_LIMIT_DEFAULT)
+        again = run()
+        assert again[4] == 0 and again[5] == 0
+        for a, b in zip(again[:4], good[:4]):
+            assert torch.equal(a.view(torch.int32), b.view(torch.int32))
+    finally:
+        _lib.tune_set(knob, old)
