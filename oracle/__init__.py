@@ -264,6 +264,34 @@ def grid_sat(bits, res, n_grids=1):
     return (s % 65536).astype(np.uint16).reshape(-1)
 
 
+def grid_brick_summary(bits, res, n_grids=1):
+    """Brick summary stored after the summed-area table (also an acceleration
+    structure of the marcher, not part of the paper's method), by its definition:
+    per grid, for every brick of 8 x 8 x 8 cells (clipped at the grid's faces),
+    2 bits: 1 when none of its cells is occupied, 2 when all are; 8 bricks per
+    uint16 entry (brick b in bits 2 (b mod 8) .. 2 (b mod 8) + 1 of entry b // 8),
+    bricks x-major and z fastest, ceil(nb0 nb1 nb2 / 8) entries per grid,
+    nb_k = ceil(res_k / 8). Computed from the cells, not from the table."""
+    r0, r1, r2 = (int(v) for v in res)
+    n = n_grids * r0 * r1 * r2
+    w = np.ascontiguousarray(bits, dtype=np.uint32)
+    occ = ((w[np.arange(n) >> 5] >> (np.arange(n) & 31).astype(np.uint32)) & 1).astype(bool)
+    occ = occ.reshape(n_grids, r0, r1, r2)
+    nb = [(r + 7) // 8 for r in (r0, r1, r2)]
+    per = (nb[0] * nb[1] * nb[2] + 7) // 8
+    out = np.zeros((n_grids, per), np.uint16)
+    for g in range(n_grids):
+        b = 0
+        for bx in range(nb[0]):
+            for by in range(nb[1]):
+                for bz in range(nb[2]):
+                    cells = occ[g, 8 * bx:8 * bx + 8, 8 * by:8 * by + 8, 8 * bz:8 * bz + 8]
+                    v = (1 if not cells.any() else 0) | (2 if cells.all() else 0)
+                    out[g, b // 8] |= np.uint16(v << (2 * (b % 8)))
+                    b += 1
+    return out.reshape(-1)
+
+
 def field_query(field, field_box, xyz):
     """Density field of the fused path (F1 in oracle.c): trilinear between the
     vertex values field[i, j, k] of a lattice over field_box = (lo, hi), zero

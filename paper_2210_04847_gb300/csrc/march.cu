@@ -89,6 +89,31 @@ __device__ __forceinline__ void box_decide(const G& g, unsigned sl0, int i0, int
         empty = true;  // no point lies inside the grid
         return;
     }
+    // the brick summary first (shared memory, no table reads): a box within
+    // 2 x 2 x 2 bricks of 8^3 cells is empty when they all are, and, inside the
+    // grid, full when they all are
+    if (const uint16_t* bm = g.bricks()) {
+        const int x0 = a0 >> 3, x1 = (b0 - 1) >> 3, y0 = a1 >> 3, y1 = (b1 - 1) >> 3, z0 = a2 >> 3, z1 = (b2 - 1) >> 3;
+        if (x1 - x0 <= 1 && y1 - y0 <= 1 && z1 - z0 <= 1) {
+            const int nb1 = g.brick_nb1(), nb2 = g.brick_nb2();
+            const uint16_t* gm = bm + sl0 * (unsigned)g.brick_per_grid();
+            unsigned acc = 3u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int bx = (q & 4) ? x1 : x0, by = (q & 2) ? y1 : y0, bz = (q & 1) ? z1 : z0;
+                const unsigned b = (unsigned)((bx * nb1 + by) * nb2 + bz);
+                acc &= (unsigned)gm[b >> 3] >> ((b & 7u) * 2u);
+            }
+            if (acc & 1u) {
+                empty = true;
+                return;
+            }
+            if ((acc & 2u) && inside) {
+                full = true;
+                return;
+            }
+        }
+    }
     const unsigned long long vol =
         (unsigned long long)(b0 - a0) * (unsigned long long)(b1 - a1) * (unsigned long long)(b2 - a2);
     if (vol >= 65536ull) return;
@@ -575,10 +600,10 @@ __device__ __forceinline__ void uniform_midpoint(float near, float far, float dt
 // chunks left undecided are tested point by point by the whole warp. The ray
 // loads and the table loads of 32 chunks are in flight together, instead of a
 // few dependent round trips per ray.
-__device__ __forceinline__ void box_tile_uniform(const MarchArgs& a, int ray0, int nr, uint32_t* wmask, int lane,
-                                                 int& my_count, int& my_nch, float& my_near, float& my_far,
-                                                 int& tile_pts) {
-    const ArgGeom g{a};
+__device__ __forceinline__ void box_tile_uniform(const MarchArgs& a, const uint16_t* s_bricks, int ray0, int nr,
+                                                 uint32_t* wmask, int lane, int& my_count, int& my_nch,
+                                                 float& my_near, float& my_far, int& tile_pts) {
+    const ArgGeom g{a, s_bricks};
     const float dt = a.dt_min;
     float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f, d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, near = 0.0f, far = 0.0f;
     int nk = 0;
@@ -838,12 +863,18 @@ __device__ __forceinline__ void load_scene(const MarchArgs& a, int scene, SceneG
 template <int MAXL, int MINB, bool CONE, bool UNROLL2 = false, bool COARSE = false, bool BATCHED = false,
           int BOX = 0>
 __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const MarchArgs a) {
-    extern __shared__ uint32_t s_masks[];  // per warp: 2 x [tile_rays][row_stride]
+    extern __shared__ uint32_t s_masks[];  // per warp: 2 x [tile_rays][row_stride]; then the brick summary
     __shared__ float s_lat[kWarps][36];    // cone steps with a ray-specific start
     __shared__ SceneGeom s_scene[BATCHED ? kWarps : 1];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const size_t tile_words = (size_t)a.tile_rays * a.row_stride;
+    uint16_t* s_bricks = nullptr;
+    if (!BATCHED && a.bricks) {
+        s_bricks = reinterpret_cast<uint16_t*>(s_masks + (size_t)kWarps * 2 * tile_words);
+        for (int k = threadIdx.x; k < a.brick_entries; k += kThreads) s_bricks[k] = __ldg(a.bricks + k);
+        __syncthreads();
+    }
     uint32_t* wbase = s_masks + (size_t)warp * 2 * tile_words;
     float* lat = s_lat[warp];
     int scene = 0, held = -1;  // BATCHED: scene of the current ray; scene held in s_scene[warp]
@@ -867,7 +898,8 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
             int tile_pts = 0;  // at most tile_rays * max_steps
             constexpr bool kTileBox = BOX == 2 && !CONE && !BATCHED && MAXL == 1;
             if constexpr (kTileBox)
-                box_tile_uniform(a, cur.ray0, cur.nr, wmask, lane, my_count, my_nch, my_near, my_far, tile_pts);
+                box_tile_uniform(a, s_bricks, cur.ray0, cur.nr, wmask, lane, my_count, my_nch, my_near, my_far,
+                                 tile_pts);
             for (int i = 0; i < (kTileBox ? 0 : cur.nr); ++i) {
                 const int r = cur.ray0 + i;
                 float o[3], d[3];
@@ -900,7 +932,7 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
                     const int slot = slot_of(a, r);
                     const bool slot_ok = slot >= 0 && slot < a.n_slots;
                     if (!slot_ok && lane == 0) raise_status(a.d_status, NACC_STATUS_BAD_INDEX);
-                    const ArgGeom g{a};
+                    const ArgGeom g{a, s_bricks};
                     if (slot_ok && clip_ray_in<MAXL == 0>(a, g, o, d, near, far))
                         walk_lattice<MAXL, CONE, UNROLL2, COARSE, BOX>(a, g, o, d, near, far,
                                                                   (unsigned)slot * (unsigned)a.n_levels, row, lat,
@@ -1011,6 +1043,7 @@ void launch_batched(bool cone, size_t smem, int need, cudaStream_t st, const Mar
 // Resident blocks per SM the box walks are compiled for (their registers fit
 // without spills).
 constexpr int kBoxMinBlocks = 4;
+constexpr size_t kBrickSmemMax = 16 * 1024;  // largest brick summary the walk keeps in shared memory
 constexpr int kBoxBatchedMinBlocks = 3;
 
 // One-level grid with its summed-area table: the box walk, ray by ray or (uniform
@@ -1076,7 +1109,22 @@ int march_launch(MarchArgs& a, const nacc_march_params* p, int32_t* packed_info,
         a.cone_table = table;
         cone_table_kernel<<<1, 32, 0, st>>>(a, table);
     }
-    const size_t smem = (size_t)kWarps * 2 * a.tile_rays * a.row_stride * sizeof(uint32_t);
+    size_t smem = (size_t)kWarps * 2 * a.tile_rays * a.row_stride * sizeof(uint32_t);
+    // the box walk keeps the table's brick summary in shared memory when it is small
+    a.bricks = nullptr;
+    a.brick_entries = 0;
+    if (!batched && box && a.sat && !a.contract) {
+        const SatLayout L = sat_layout((long long)a.n_slots * a.n_levels, a.res0, a.res1, a.res2);
+        const size_t entries = (size_t)a.n_slots * a.n_levels * L.per_grid;
+        if (entries * sizeof(uint16_t) <= kBrickSmemMax) {
+            a.bricks = a.sat + L.summary_offset;
+            a.brick_entries = (int32_t)entries;
+            a.brick_nb1 = L.nb1;
+            a.brick_nb2 = L.nb2;
+            a.brick_per_grid = (int32_t)L.per_grid;
+            smem += align_up(entries * sizeof(uint16_t), 16);
+        }
+    }
     const int need = (a.n_tiles + kWarps - 1) / kWarps;
     if (batched) {
         // one level in registers fits 4 blocks of 256 threads per SM like the

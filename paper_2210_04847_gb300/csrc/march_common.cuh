@@ -74,6 +74,9 @@ struct MarchArgs {
     float inv_dt;             // 1 / dt_min, for the first guess of a uniform lattice's length
     LookbackHooks hooks;      // look-back poll budget (test hooks)
     const uint16_t* sat;      // summed-area table of the grid's bits, or null
+    const uint16_t* bricks;   // the table's brick summary (global), when the walk keeps it in shared memory
+    int32_t brick_entries;    // uint16 entries of the summary over all grids
+    int32_t brick_nb1, brick_nb2, brick_per_grid;  // bricks along y and z; summary entries per grid
     const SceneGeom* scenes;  // batch of scenes with their own grids (else null)
     const int32_t* scene_end; // exclusive end of each scene's consecutive rays
     int32_t n_scenes;
@@ -91,6 +94,7 @@ struct MarchArgs {
 
 struct ArgGeom {
     const MarchArgs& a;
+    const uint16_t* s_bricks = nullptr;  // the brick summary in shared memory, or null
     __device__ __forceinline__ float lo(int l, int k) const { return a.L.lo[l][k]; }
     __device__ __forceinline__ float scale(int l, int k) const { return a.L.scale[l][k]; }
     __device__ __forceinline__ float box_lo(int k) const { return a.L.box_lo[k]; }
@@ -104,6 +108,10 @@ struct ArgGeom {
     __device__ __forceinline__ int n_levels() const { return a.n_levels; }
     __device__ __forceinline__ const uint32_t* bits() const { return a.bits; }
     __device__ __forceinline__ const uint16_t* sat() const { return a.sat; }
+    __device__ __forceinline__ const uint16_t* bricks() const { return s_bricks; }
+    __device__ __forceinline__ int brick_nb1() const { return a.brick_nb1; }
+    __device__ __forceinline__ int brick_nb2() const { return a.brick_nb2; }
+    __device__ __forceinline__ int brick_per_grid() const { return a.brick_per_grid; }
 };
 
 struct SmemGeom {
@@ -121,6 +129,10 @@ struct SmemGeom {
     __device__ __forceinline__ int n_levels() const { return g->n_levels; }
     __device__ __forceinline__ const uint32_t* bits() const { return g->bits; }
     __device__ __forceinline__ const uint16_t* sat() const { return g->sat; }
+    __device__ __forceinline__ const uint16_t* bricks() const { return nullptr; }
+    __device__ __forceinline__ int brick_nb1() const { return 0; }
+    __device__ __forceinline__ int brick_nb2() const { return 0; }
+    __device__ __forceinline__ int brick_per_grid() const { return 0; }
 };
 
 // One level (or contracted space) in registers, loaded once per ray.
@@ -157,6 +169,10 @@ struct RegGeom {
     __device__ __forceinline__ int n_levels() const { return 1; }
     __device__ __forceinline__ const uint32_t* bits() const { return b_; }
     __device__ __forceinline__ const uint16_t* sat() const { return sat_; }
+    __device__ __forceinline__ const uint16_t* bricks() const { return nullptr; }
+    __device__ __forceinline__ int brick_nb1() const { return 0; }
+    __device__ __forceinline__ int brick_nb2() const { return 0; }
+    __device__ __forceinline__ int brick_per_grid() const { return 0; }
 };
 
 __device__ __forceinline__ bool finite32(float v) { return fabsf(v) <= 3.402823466e+38f; }

@@ -239,6 +239,31 @@ LookbackHooks lookback_hooks();
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Layout of a grid's summed-area table buffer (nacc_build_grid_sat): the table's
+// uint16 corner entries for every grid, then, from the first 16-byte boundary,
+// the brick summary: 2 bits per brick of 8^3 cells (bit 0: no cell occupied,
+// bit 1: every in-grid cell occupied), 8 bricks per uint16 entry, bricks
+// x-major and z fastest, ceil(nb0 nb1 nb2 / 8) entries per grid, nb_k = ceil(res_k / 8).
+struct SatLayout {
+    size_t table_entries;   // uint16 corner entries over all grids
+    size_t summary_offset;  // uint16 entries before the brick summary
+    int nb0, nb1, nb2;      // bricks per axis
+    size_t per_grid;        // summary entries per grid
+    size_t total_entries;   // uint16 entries of the whole buffer
+};
+
+inline SatLayout sat_layout(long long grids, int r0, int r1, int r2) {
+    SatLayout L;
+    L.table_entries = (size_t)grids * (size_t)(r0 + 1) * (size_t)(r1 + 1) * (size_t)(r2 + 1);
+    L.summary_offset = align_up(L.table_entries, 8);
+    L.nb0 = (r0 + 7) >> 3;
+    L.nb1 = (r1 + 7) >> 3;
+    L.nb2 = (r2 + 7) >> 3;
+    L.per_grid = ((size_t)L.nb0 * L.nb1 * L.nb2 + 7) >> 3;
+    L.total_entries = L.summary_offset + (size_t)grids * L.per_grid;
+    return L;
+}
+
 inline int launch_status(cudaError_t e) { return e == cudaSuccess ? NACC_OK : NACC_ERR_CUDA; }
 
 }  // namespace nacc

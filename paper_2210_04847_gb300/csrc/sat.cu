@@ -24,6 +24,10 @@
 // instead: a lane keeps four running sums along y in registers, then a warp per
 // (g, y, z block) runs the sums along x. Planes or slabs too large for shared
 // memory take slower global-memory passes.
+// A last pass writes the brick summary after the table (see sat_layout): for
+// every block of 8^3 cells, whether none or all of its cells are occupied. It is
+// small enough for the marcher to keep in shared memory and decide most boxes
+// without reading the table.
 #include "nacc_internal.cuh"
 
 namespace nacc {
@@ -320,6 +324,38 @@ __global__ void __launch_bounds__(kThreads) sat_sum_kernel(const SatArgs a) {
     }
 }
 
+
+// Brick summary (layout: sat_layout): a thread per brick forms its 2-bit state
+// from its box count in the finished table (a brick holds at most 512 cells, so
+// the modular count is exact); groups of 8 lanes pack their states into one entry.
+__global__ void __launch_bounds__(kThreads) brick_summary_kernel(const SatArgs a, uint16_t* out, int nb0, int nb1,
+                                                                int nb2, int per_grid) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (grid, brick slot)
+    const long long slots = (long long)a.n_grids * per_grid * 8;
+    const int g = (int)(i / ((long long)per_grid * 8)), b = (int)(i % ((long long)per_grid * 8));
+    unsigned v = 0u;
+    if (i < slots && b < nb0 * nb1 * nb2) {
+        const unsigned sy = (unsigned)(a.r2 + 1), sx = (unsigned)(a.r1 + 1) * sy;
+        const uint16_t* t = a.sat + (size_t)g * sx * (unsigned)(a.r0 + 1);
+        const int bz = b % nb2, by = (b / nb2) % nb1, bx = b / (nb1 * nb2);
+        const int x0 = 8 * bx, y0 = 8 * by, z0 = 8 * bz;
+        const int x1 = min(x0 + 8, a.r0), y1 = min(y0 + 8, a.r1), z1 = min(z0 + 8, a.r2);
+        const unsigned xa = x0 * sx, xb = x1 * sx, ya = y0 * sy, yb = y1 * sy;
+        const unsigned cnt = ((unsigned)t[xb + yb + z1] - (unsigned)t[xa + yb + z1] - (unsigned)t[xb + ya + z1] -
+                              (unsigned)t[xb + yb + z0] + (unsigned)t[xa + ya + z1] + (unsigned)t[xa + yb + z0] +
+                              (unsigned)t[xb + ya + z0] - (unsigned)t[xa + ya + z0]) &
+                             0xffffu;
+        const unsigned vol = (unsigned)((x1 - x0) * (y1 - y0) * (z1 - z0));
+        v = (cnt == 0u ? 1u : 0u) | (cnt == vol ? 2u : 0u);
+    }
+    // slots are whole warps' worth of entries (8 per entry, entries never straddle warps)
+    v <<= 2 * (threadIdx.x & 7);
+    v |= __shfl_xor_sync(FULL, v, 1);
+    v |= __shfl_xor_sync(FULL, v, 2);
+    v |= __shfl_xor_sync(FULL, v, 4);
+    if ((threadIdx.x & 7) == 0 && i < slots) out[i >> 3] = (uint16_t)v;
+}
+
 }  // namespace
 }  // namespace nacc
 
@@ -329,8 +365,8 @@ extern "C" size_t nacc_grid_sat_bytes(const nacc_grid* grid) {
     if (!grid || grid->n_levels < 1 || grid->n_slots < 1) return 0;
     for (int k = 0; k < 3; ++k)
         if (grid->res[k] < 1) return 0;
-    return (size_t)grid->n_slots * grid->n_levels * (size_t)(grid->res[0] + 1) * (grid->res[1] + 1) *
-           (grid->res[2] + 1) * sizeof(uint16_t);
+    return sat_layout((long long)grid->n_slots * grid->n_levels, grid->res[0], grid->res[1], grid->res[2])
+               .total_entries * sizeof(uint16_t);
 }
 
 extern "C" int nacc_build_grid_sat(const nacc_grid* grid, uint16_t* sat, void* stream) {
@@ -352,7 +388,6 @@ extern "C" int nacc_build_grid_sat(const nacc_grid* grid, uint16_t* sat, void* s
         const long long zblocks = (r2 + 127) / 128, w1 = planes, w2 = grids * (r1 + 1) * zblocks;
         sat_plane_warp_kernel<<<(unsigned)((w1 * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(a);
         sat_xsum_warp_kernel<<<(unsigned)((w2 * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(a);
-        return launch_status(cudaGetLastError());
     } else if ((r1 + 1) * (r2 + 1) <= kSliceMax && r1 * r2 / 32 + 2 <= kPlaneWordsMax) {
         // a plane's bits span at most r1 r2 / 32 + 2 words
         sat_plane_kernel<<<(unsigned)planes, kSliceThreads, 0, st>>>(a);
@@ -361,11 +396,18 @@ extern "C" int nacc_build_grid_sat(const nacc_grid* grid, uint16_t* sat, void* s
         const long long ly = planes * (r2 + 1);
         sat_sum_kernel<1><<<(unsigned)((ly + kThreads - 1) / kThreads), kThreads, 0, st>>>(a);
     }
-    if ((r0 + 1) * (r2 + 1) <= kSliceMax) {
-        sat_slab_kernel<<<(unsigned)(grids * (r1 + 1)), kSliceThreads, 0, st>>>(a);
-    } else {
-        const long long lx = grids * (r1 + 1) * (r2 + 1);
-        sat_sum_kernel<0><<<(unsigned)((lx + kThreads - 1) / kThreads), kThreads, 0, st>>>(a);
+    if (!many) {
+        if ((r0 + 1) * (r2 + 1) <= kSliceMax) {
+            sat_slab_kernel<<<(unsigned)(grids * (r1 + 1)), kSliceThreads, 0, st>>>(a);
+        } else {
+            const long long lx = grids * (r1 + 1) * (r2 + 1);
+            sat_sum_kernel<0><<<(unsigned)((lx + kThreads - 1) / kThreads), kThreads, 0, st>>>(a);
+        }
     }
+    // the brick summary, from the finished table
+    const SatLayout L = sat_layout(grids, grid->res[0], grid->res[1], grid->res[2]);
+    const long long slots = grids * (long long)L.per_grid * 8;
+    brick_summary_kernel<<<(unsigned)((slots + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+        a, sat + L.summary_offset, L.nb0, L.nb1, L.nb2, (int)L.per_grid);
     return launch_status(cudaGetLastError());
 }

@@ -194,7 +194,9 @@ def test_grid_sat_sizes_and_rejections(libs):
     g.n_levels, g.n_slots = 2, 3
     for k in range(3):
         g.aabb[k], g.aabb[3 + k] = -1.0, 1.0
-    assert lib.nacc_grid_sat_bytes(ctypes.byref(g)) == 2 * 3 * 129 * 97 * 8 * 2
+    # the table's corners (a multiple of 8 entries here), then 2-bit states of the
+    # 16 x 12 x 1 bricks of 8^3 cells, 8 per entry, for each of the 6 grids
+    assert lib.nacc_grid_sat_bytes(ctypes.byref(g)) == (2 * 3 * 129 * 97 * 8 + 6 * (16 * 12 * 1 // 8)) * 2
     assert lib.nacc_build_grid_sat(ctypes.byref(g), ctypes.c_void_p(4096), None) == _lib.ERR_INVALID_ARG  # no bits
     g.bits = 4096
     assert lib.nacc_build_grid_sat(ctypes.byref(g), None, None) == _lib.ERR_INVALID_ARG  # no table

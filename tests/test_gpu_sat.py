@@ -34,7 +34,13 @@ def test_sat_matches_definition(orc, res, n_levels, n_slots, p):
     sat = _lib.build_grid_sat(grid)
     torch.cuda.synchronize()
     ref = orc.grid_sat(bits, res, n_levels * n_slots)
-    assert np.array_equal(sat.cpu().numpy().view(np.uint16), ref)  # totals of the larger grids wrap modulo 2^16
+    got = sat.cpu().numpy().view(np.uint16)
+    assert np.array_equal(got[: ref.size], ref)  # totals of the larger grids wrap modulo 2^16
+    # the brick summary from the first 16-byte boundary after the table
+    off = (ref.size + 7) // 8 * 8
+    summ = orc.grid_brick_summary(bits, res, n_levels * n_slots)
+    assert got.size == off + summ.size
+    assert np.array_equal(got[off:], summ)
 
 
 def test_box_walk_boxes_too_large_for_the_table(orc):

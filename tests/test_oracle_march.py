@@ -378,3 +378,35 @@ def test_grid_sat_definition_by_brute_force(orc):
         cnt = (s[x1, y1, z1] - s[x0, y1, z1] - s[x1, y0, z1] - s[x1, y1, z0] + s[x0, y0, z1] + s[x0, y1, z0]
                + s[x1, y0, z0] - s[x0, y0, z0]) % 65536
         assert cnt == o[x0:x1, y0:y1, z0:z1].sum()
+
+
+def _brick_states(summary, per_grid, g, n_bricks):
+    """2-bit state of each brick of grid g from the packed summary."""
+    e = summary[g * per_grid:(g + 1) * per_grid].astype(np.int64)
+    return np.array([(e[b // 8] >> (2 * (b % 8))) & 3 for b in range(n_bricks)])
+
+
+def test_brick_summary_by_construction():
+    """The marcher's brick summary (2 bits per 8^3 block of cells: 1 empty, 2 full),
+    on grids whose answer is known: empty, full (bricks clipped at the faces count
+    their in-grid cells), one occupied cell, one fully occupied brick."""
+    from oracle import grid_brick_summary
+    res = (20, 9, 17)  # bricks 3 x 2 x 3, the last ones clipped
+    n = 20 * 9 * 17
+    nb = 18
+    per = (nb + 7) // 8
+    empty = grid_brick_summary(synth.pack_bits(np.zeros(n, bool)), res)
+    full = grid_brick_summary(synth.pack_bits(np.ones(n, bool)), res)
+    assert np.all(_brick_states(empty, per, 0, nb) == 1) and np.all(_brick_states(full, per, 0, nb) == 2)
+    occ = np.zeros((20, 9, 17), bool)
+    occ[11, 8, 16] = True  # brick (1, 1, 2) = index (1 * 2 + 1) * 3 + 2 = 11
+    st = _brick_states(grid_brick_summary(synth.pack_bits(occ.reshape(-1)), res), per, 0, nb)
+    assert st[11] == 0 and np.all(np.delete(st, 11) == 1)
+    occ[:] = False
+    occ[16:20, 8:9, 0:8] = True  # brick (2, 1, 0), clipped to 4 x 1 x 8 cells: index (2 * 2 + 1) * 3 = 15
+    st = _brick_states(grid_brick_summary(synth.pack_bits(occ.reshape(-1)), res), per, 0, nb)
+    assert st[15] == 2 and np.all(np.delete(st, 15) == 1)
+    # two grids one after the other
+    two = np.concatenate([np.ones(n, bool), np.zeros(n, bool)])
+    s2 = grid_brick_summary(synth.pack_bits(two), res, 2)
+    assert np.all(_brick_states(s2, per, 0, nb) == 2) and np.all(_brick_states(s2, per, 1, nb) == 1)
