@@ -102,9 +102,16 @@ typedef struct nacc_grid {
  * lies in that level (its box inside the level) or outside all levels (the
  * outermost). The other chunks are tested point by point. Results are identical
  * with and without the table (shared lattices; rays with their own cone
- * recurrence are always tested point by point). sat:
- * nacc_grid_sat_bytes() bytes, 2-byte aligned; the corners over all slots and
- * levels must number below 2^31.
+ * recurrence are always tested point by point). After the corners, from the
+ * first 16-byte boundary of the buffer, the build also writes a brick summary:
+ * 2 bits per block of 8^3 cells (clipped at the grid's faces; bit 0: no cell
+ * occupied, bit 1: every cell occupied), 8 bricks per uint16 entry, bricks
+ * x-major and z fastest, ceil(nb0 nb1 nb2 / 8) entries per grid with
+ * nb_k = ceil(res_k / 8), grids in the table's order. When the summary of all
+ * grids fits 16 KiB, marching keeps it in shared memory and decides a box that
+ * lies within 2 x 2 x 2 bricks from it, without reading the table (same
+ * decisions). sat: nacc_grid_sat_bytes() bytes (corners, then the summary),
+ * 2-byte aligned; the corners over all slots and levels must number below 2^31.
  */
 size_t nacc_grid_sat_bytes(const nacc_grid* grid);
 int nacc_build_grid_sat(const nacc_grid* grid, uint16_t* sat, void* stream);
