@@ -189,19 +189,24 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned by
                  : "memory");
 }
 
+// One poll: the thread is suspended until the phase completes or about
+// kWaitHintNs nanoseconds have passed (no spinning while the copies are in flight).
+constexpr unsigned kWaitHintNs = 1000;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kWaitHintNs)
         : "memory");
     return done != 0;
 }
 
-// Waits (at most `limit` polls) for the phase of the given parity to complete.
+// Waits (at most `limit` polls, each at most about kWaitHintNs) for the phase of
+// the given parity to complete.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int limit) {
     for (int i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
