@@ -231,7 +231,8 @@ def sat_launches(res, grids: int) -> int:
 def kernel_source_sha(stage: str) -> str:
     """SHA-256 over the sources a stage's kernel is compiled from."""
     files = {"march": ("march.cu", "march_common.cuh", "nacc_internal.cuh"), "prune": ("prune.cu", "nacc_internal.cuh"),
-             "render_fwd": ("render.cu",), "render_bwd": ("render.cu",), "grid_update": ("grid.cu", "sat.cu"),
+             "render_fwd": ("render.cu", "bulk_copy.cuh"), "render_bwd": ("render.cu", "bulk_copy.cuh"),
+             "grid_update": ("grid.cu", "sat.cu"),
              "march_fused": ("fused.cu", "march_common.cuh", "nacc_internal.cuh")}[stage]
     h = hashlib.sha256()
     for f in files:

@@ -14,6 +14,7 @@
 #include <math.h>
 #include <string.h>
 
+#include "bulk_copy.cuh"
 #include "nacc_internal.cuh"
 
 namespace nacc {
