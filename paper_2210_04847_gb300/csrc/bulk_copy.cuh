@@ -65,6 +65,13 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
         : "memory");
 }
 
+// As bulk_copy_g2s, with the destination and barrier as shared-memory addresses.
+__device__ __forceinline__ void bulk_copy_g2s_addr(uint32_t dst, const void* src, unsigned bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 // Orders this thread's earlier shared-memory accesses before later bulk copies
 // into the same memory (reuse of a stage that was read with ordinary loads).
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

@@ -870,7 +870,8 @@ __device__ __forceinline__ Win chunk_window(unsigned rlo, unsigned rhi, int c, u
 }
 
 // Lane 0: announce the window's bytes on the stage's barrier and copy the arrays
-// (od may be null: forward layout).
+// (od may be null: forward layout). (Copies issued by lanes 0 .. 4 at once, one
+// array each, measured slower.)
 __device__ __forceinline__ void issue_window(float* st, uint64_t* bar, Win w, const float* ts, const float* te,
                                              const float* sg, const float* od, const float* rgb, unsigned extra = 0) {
     const unsigned n = w.hi - w.lo, b = 4u * n;
@@ -888,21 +889,21 @@ __device__ __forceinline__ void issue_window(float* st, uint64_t* bar, Win w, co
     }
 }
 
-// The lane's pair j0, j0 + 1 of a run [lo, hi) from a stage holding window w
-// (rgb at st + rgb_at), as load_pair gives it; samples past the window (at
-// or beyond n4) come from global memory.
-__device__ __forceinline__ void stage_pair(const float* st, int rgb_at, Win w, const float* __restrict__ ts,
-                                           const float* __restrict__ te, const float* __restrict__ sig,
-                                           const float* __restrict__ rgbs, unsigned j0, unsigned lo, unsigned hi,
-                                           Pair& q) {
+// The lane's pair j0, j0 + 1 of a run [lo, hi) from a stage whose window starts
+// at wlo (rgb at st + rgb_at), as load_pair gives it. Every sample of the
+// chunk below n4 is in the window; those at or beyond n4 come from global memory.
+__device__ __forceinline__ void stage_pair(const float* st, int rgb_at, unsigned wlo, unsigned n4,
+                                           const float* __restrict__ ts, const float* __restrict__ te,
+                                           const float* __restrict__ sig, const float* __restrict__ rgbs,
+                                           unsigned j0, unsigned lo, unsigned hi, Pair& q) {
     q.v0 = j0 >= lo && j0 < hi;
     q.v1 = j0 + 1 >= lo && j0 + 1 < hi;
 #pragma unroll
     for (int k = 0; k < 2; ++k) q.s0[k] = q.s1[k] = q.sg[k] = 0.0f;
 #pragma unroll
     for (int k = 0; k < 6; ++k) q.rgb[k] = 0.0f;
-    const unsigned p = j0 - w.lo;  // even: j0 and w.lo are
-    if (q.v0 && q.v1 && j0 + 1 < w.hi) {
+    const unsigned p = j0 - wlo;  // even: j0 and wlo are
+    if (q.v0 && q.v1 && j0 + 1 < n4) {
         const float2 u = *reinterpret_cast<const float2*>(st + p);
         const float2 v = *reinterpret_cast<const float2*>(st + kSpan + p);
         const float2 g = *reinterpret_cast<const float2*>(st + 2 * kSpan + p);
@@ -918,7 +919,7 @@ __device__ __forceinline__ void stage_pair(const float* st, int rgb_at, Win w, c
         for (int k = 0; k < 2; ++k) {
             if (k == 0 ? q.v0 : q.v1) {
                 const unsigned j = j0 + k;
-                if (j < w.hi) {
+                if (j < n4) {
                     const unsigned l = p + k;
                     q.s0[k] = st[l];
                     q.s1[k] = st[kSpan + l];
@@ -1039,8 +1040,8 @@ __global__ void __launch_bounds__(kRenderThreads, kBulkMinBlocks) render_fwd_bul
         }
         const unsigned qj0 = (C.lo & ~1u) + ((unsigned)C.c << 6) + 2 * lane;
         Pair q;
-        stage_pair(st, 3 * kSpan, chunk_window(C.lo, C.hi, C.c, n4), a.t_starts, a.t_ends, a.sigmas, a.rgbs, qj0,
-                   C.lo, C.hi, q);
+        stage_pair(st, 3 * kSpan, ((C.lo & ~1u) + ((unsigned)C.c << 6)) & ~3u, n4, a.t_starts, a.t_ends, a.sigmas,
+                   a.rgbs, qj0, C.lo, C.hi, q);
         const float tau0 = q.v0 ? tau_of(q.s0[0], q.s1[0], q.sg[0]) : 0.0f;
         const float tau1 = q.v1 ? tau_of(q.s0[1], q.s1[1], q.sg[1]) : 0.0f;
         float O0, O1;
@@ -1170,15 +1171,15 @@ __global__ void __launch_bounds__(kRenderThreads, kBulkMinBlocks) render_bwd_bul
             drain_stages<NST>(bars, k, total, a.stage_extra != 0u, a.d_status, lane);
             return;
         }
-        const Win w = chunk_window(C.lo, C.hi, C.c, n4);
-        const unsigned j0 = (C.lo & ~1u) + ((unsigned)C.c << 6) + 2 * lane;
+        const unsigned c0 = (C.lo & ~1u) + ((unsigned)C.c << 6), wlo = c0 & ~3u;
+        const unsigned j0 = c0 + 2 * lane;
         Pair q;
-        stage_pair(st, 4 * kSpan, w, a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0, C.lo, C.hi, q);
+        stage_pair(st, 4 * kSpan, wlo, n4, a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0, C.lo, C.hi, q);
         float O0 = 0.0f, O1 = 0.0f;
         {
-            const unsigned p = j0 - w.lo;
-            if (q.v0) O0 = j0 < w.hi ? st[3 * kSpan + p] : __ldg(a.optical_depth + j0);
-            if (q.v1) O1 = j0 + 1 < w.hi ? st[3 * kSpan + p + 1] : __ldg(a.optical_depth + j0 + 1);
+            const unsigned p = j0 - wlo;
+            if (q.v0) O0 = j0 < n4 ? st[3 * kSpan + p] : __ldg(a.optical_depth + j0);
+            if (q.v1) O1 = j0 + 1 < n4 ? st[3 * kSpan + p + 1] : __ldg(a.optical_depth + j0 + 1);
         }
         const float tau0 = q.v0 ? tau_of(q.s0[0], q.s1[0], q.sg[0]) : 0.0f;
         const float tau1 = q.v1 ? tau_of(q.s0[1], q.s1[1], q.sg[1]) : 0.0f;
