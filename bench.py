@@ -54,11 +54,11 @@ NCU_TRAFFIC = {
 
 # What limits each stage (from the ncu captures summarised under profiles/).
 LIMITER = {
-    "march": "store phase near the write bandwidth plus the latency of the ray, table and bitfield loads (box walk: "
-             "67% issue-active at 43% DRAM, long-scoreboard stalls first)",
+    "march": "issue (68% issue-active with 30 warps per SM, register-limited) plus the L1-to-L2 requests of the "
+             "stores and the table reads the brick summary leaves (59% busy), at 46% DRAM",
     "prune": "DRAM latency (long-scoreboard stalls)",
     "render_fwd": "DRAM latency / issue",
-    "render_bwd": "DRAM latency (long-scoreboard stalls)",
+    "render_bwd": "issue (76% issue-active; chunks staged by bulk copies, long-scoreboard stalls 1 per issue)",
     "grid_update": "latency of 2^21 random atomics",
 }
 
