@@ -51,20 +51,24 @@ def _config(seed):
 @pytest.mark.parametrize("seed", range(16))
 def test_fuzz_march_bitexact(orc, seed):
     """Each configuration without and with the grid's summed-area table (the box
-    walk for one level and for cascades of up to four levels)."""
+    walk for one level and for cascades of up to four levels), ray by ray and over
+    each tile's chunks at once."""
     import gpu_util
 
     w, rng = _config(seed)
-    old = _lib.tune_get("march_tile_rays")
+    old = _lib.tune_get("march_tile_rays"), _lib.tune_get("march_box_tile")
     try:
         _lib.tune_set("march_tile_rays", int(rng.choice([1, 2, 4, 8, 16, 32])))
         ref = oracle_march(orc, w)
         assert_march_equal(gpu_march(w), ref)
         gpu_util.USE_SAT = True
-        assert_march_equal(gpu_march(w), ref)
+        for box_tile in (0, 1):
+            _lib.tune_set("march_box_tile", box_tile)
+            assert_march_equal(gpu_march(w), ref)
     finally:
         gpu_util.USE_SAT = False
-        _lib.tune_set("march_tile_rays", old)
+        _lib.tune_set("march_tile_rays", old[0])
+        _lib.tune_set("march_box_tile", old[1])
 
 
 @pytest.mark.parametrize("seed", range(8))
