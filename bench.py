@@ -46,8 +46,8 @@ POOL = 4  # distinct ray batches cycled through the steps (L2 is flushed between
 # from one ncu capture, keyed by the SHA-256 of the kernel's source file. A
 # source change invalidates the figure (reported as null until re-captured).
 NCU_TRAFFIC = {
-    # profiles/march_dram_bounded-2^18.md: 19033088 B read + 1477945600 B written (box walk, brick summary)
-    ("march", "412b1761579eb61d53c2e5fb4851fe1f00cdfbb696db39afe1c52dc8638be5ae"): 1496978688,
+    # profiles/march_dram_bounded-2^18.md: 18993920 B read + 1478312960 B written (box walk, brick summary)
+    ("march", "f406db2f593624e8e17148e8dde60de500d04b63d53c093ebd78f80c40f5c2d4"): 1497306880,
     # profiles/march_fused_inference-800x800.md: 22437376 B read + 1169642240 B written (camera 0's image)
     ("march_fused", "c86e1bad5b55ca339d49805cf9ac418869661e8853df2abc21f41da92b781990"): 1192079616,
 }
