@@ -60,6 +60,7 @@ LIMITER = {
     "render_fwd": "DRAM latency / issue",
     "render_bwd": "issue (76% issue-active; chunks staged by bulk copies, long-scoreboard stalls 1 per issue)",
     "grid_update": "latency of 2^21 random atomics",
+    "render_fused": "DRAM latency of the forward's chunk loads; the backward re-reads the ray from L2",
 }
 
 
@@ -89,6 +90,9 @@ def parse():
     ap.add_argument("--pixel-stride", type=int, default=1,
                     help="inference workload: every n-th pixel of each image (smaller cases for profiling)")
     ap.add_argument("--no-two-call", action="store_true", help="inference workload: skip the two-call comparison")
+    ap.add_argument("--fused-loss", action="store_true",
+                    help="bounded workload: render forward, the MSE loss gradient and the backward as one call "
+                         "(nacc_render_mse_fused) instead of three")
     ap.add_argument("--knobs", default="", help="fixed launch-shape knobs, e.g. march_tile_rays=8,prune_tile_rays=8 "
                     "(skips the autotuner)")
     return ap.parse_args()
@@ -198,17 +202,22 @@ def stage_bytes(R, M, M_read, S, grid_bytes, n_cells, n_grid, saved_od=False):
         # write the sampled cells + points (16/sample); read + write the float32 grid (8/cell), write
         # the bits (1/8 per cell), read cells + sigmas (8/sample)
         "grid_update": 16 * n_grid + 8 * n_cells + n_cells // 8 + 8 * n_grid,
+        # fused forward + loss gradient + backward: read packed_info (8R), the target (12R) and
+        # (sigma, rgb, t_start, t_end) once (24S); write rgb, opacity, depth (20R) and dsigma, drgb (16S)
+        "render_fused": 8 * R + 12 * R + 24 * S + 20 * R + 16 * S,
     }
 
 
-def launches_per_step(w, n_cells: int, n_grid: int, ema_ptr: int, sat: bool = False) -> int:
+def launches_per_step(w, n_cells: int, n_grid: int, ema_ptr: int, sat: bool = False, fused: bool = False) -> int:
     """Library kernels one timed step launches: march (plus the cone-table prologue
     for cone steps), prune, render forward, render backward, the grid sampler, the
     decay pass (four cells per thread over whole 128-cell steps of an aligned
     grid, one cell per thread for the rest), the scatter, and with the box walk
     the passes that rebuild the updated grid's summed-area table (two: planes or
-    columns, then the sum along x; three when a plane exceeds shared memory)."""
-    n = 4 + (1 if w.cone > 0 else 0)
+    columns, then the sum along x; three when a plane exceeds shared memory) and
+    its brick summary. fused: one render launch for forward, loss gradient and
+    backward."""
+    n = (3 if fused else 4) + (1 if w.cone > 0 else 0)
     if n_grid > 0:
         n += 2  # sampler + scatter
         if sat:
@@ -219,19 +228,21 @@ def launches_per_step(w, n_cells: int, n_grid: int, ema_ptr: int, sat: bool = Fa
 
 
 def sat_launches(res, grids: int) -> int:
-    """Kernels one summed-area-table build launches (the rule of nacc_build_grid_sat)."""
+    """Kernels one summed-area-table build launches (the rule of nacc_build_grid_sat):
+    the table's passes, then the brick summary."""
     r0, r1, r2 = res
     slice_max, words_max = 20 * 1024, 2048
     if grids >= 4:
-        return 2
+        return 2 + 1
     first = 1 if ((r1 + 1) * (r2 + 1) <= slice_max and r1 * r2 // 32 + 2 <= words_max) else 2
-    return first + 1
+    return first + 1 + 1
 
 
 def kernel_source_sha(stage: str) -> str:
     """SHA-256 over the sources a stage's kernel is compiled from."""
     files = {"march": ("march.cu", "march_common.cuh", "nacc_internal.cuh"), "prune": ("prune.cu", "nacc_internal.cuh"),
              "render_fwd": ("render.cu", "bulk_copy.cuh"), "render_bwd": ("render.cu", "bulk_copy.cuh"),
+             "render_fused": ("render.cu",),
              "grid_update": ("grid.cu", "sat.cu"),
              "march_fused": ("fused.cu", "march_common.cuh", "nacc_internal.cuh")}[stage]
     h = hashlib.sha256()
@@ -399,7 +410,7 @@ def run_ours(args):
 
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    line = measure(args, args.workload)
+    line = measure(args, args.workload, fused=args.fused_loss and args.workload == "bounded")
     if line is None:
         return 0
     if args.workload == "bounded" and world == 1 and not args.no_extra:
@@ -411,6 +422,12 @@ def run_ours(args):
         sub.steps, sub.warmup = min(args.steps, 10), min(args.warmup, 3)
         dyn = measure(sub, "dynamic")
         line["dynamic_step"] = {k: dyn[k] for k in ("value", "ms_per_step", "stages_ms", "step_hbm", "tuned")}
+        if not args.fused_loss:
+            fus = measure(sub, "bounded", fused=True)
+            line["fused_loss_step"] = dict(
+                {k: fus[k] for k in ("value", "ms_per_step", "stages_ms", "step_hbm", "step_hbm_formula")},
+                note="the same step with render forward, the MSE loss gradient and the backward as one call "
+                     "(nacc_render_mse_fused): the kept samples are read once")
         bat = measure(sub, "batched", ray_scale=0.125)
         line["batched_eighth_scale"] = {
             "rays_per_step": bat["config"]["rays_per_step_per_gpu"], "value_single_launches": bat["value"],
@@ -420,9 +437,10 @@ def run_ours(args):
     return 0
 
 
-def measure(args, workload, ray_scale=1.0):
+def measure(args, workload, ray_scale=1.0, fused=False):
     """One workload's measurement: the timed step, its roofline and the extra legs;
-    returns the JSON line (None on ranks other than 0)."""
+    returns the JSON line (None on ranks other than 0). fused: render forward, the
+    loss gradient and the backward as one call (nacc_render_mse_fused)."""
     import torch
 
     rank, world, local = dist_env()
@@ -477,7 +495,7 @@ def measure(args, workload, ray_scale=1.0):
     else:
         tuned = autotune.tune_hot_path(hp, sc, 0, flush=flush.zero_)
 
-    stages = ["march", "prune", "render_fwd", "render_bwd", "grid_update"]
+    stages = ["march", "prune"] + (["render_fused"] if fused else ["render_fwd", "render_bwd"]) + ["grid_update"]
     ev = {s: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for s in stages}
     ev_sample = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     stage_ms = {s: [] for s in stages}
@@ -504,15 +522,21 @@ def measure(args, workload, ray_scale=1.0):
         ev["prune"][1].record()
         S = int(hp.n_k.item())
         sc.field_kept(hp, b, S)
-        run = hp.render_fwd(S, defer=True)
-        ev["render_fwd"][0].record()
-        run()
-        ev["render_fwd"][1].record()
-        hp.loss_grad(bt["tgt"])
-        run = hp.render_bwd(S, defer=True)
-        ev["render_bwd"][0].record()
-        run()
-        ev["render_bwd"][1].record()
+        if fused:
+            run = hp.render_mse(S, bt["tgt"], defer=True)
+            ev["render_fused"][0].record()
+            run()
+            ev["render_fused"][1].record()
+        else:
+            run = hp.render_fwd(S, defer=True)
+            ev["render_fwd"][0].record()
+            run()
+            ev["render_fwd"][1].record()
+            hp.loss_grad(bt["tgt"])
+            run = hp.render_bwd(S, defer=True)
+            ev["render_bwd"][0].record()
+            run()
+            ev["render_bwd"][1].record()
         # the update's random cells and points come from the library (device
         # sampler, the same streams as the host generator behind grid_inputs, so
         # gi describes the same points for the field's per-scene grouping)
@@ -569,15 +593,18 @@ def measure(args, workload, ray_scale=1.0):
     dom = max(stages, key=lambda s: avg[s])
     achieved = sb[dom] / (avg[dom] / 1e3) / 1e9
     traffic = NCU_TRAFFIC.get((dom, kernel_source_sha(dom))) if workload == "bounded" and R == N_RAYS else None
-    step_bytes = sum(sb.values())
+    step_bytes = sum(sb[s] for s in stages)
     # the path's bytes by the per-step formula with every marched sample read once by
     # pruning (104R + 24M + 76S with pruning on, 88R + 76M with it off; 8S more when
-    # the forward saves O for the backward), the bitfield once, plus the grid update
-    if S_avg < M_avg:
+    # the forward saves O for the backward; fused rendering reads the kept samples once:
+    # 88R + 24M + 52S, or 72R + 52M), the bitfield once, plus the grid update
+    if fused:
+        formula_bytes = 88 * R + 24 * M_avg + 52 * S_avg if S_avg < M_avg else 72 * R + 52 * M_avg
+    elif S_avg < M_avg:
         formula_bytes = 104 * R + 24 * M_avg + 76 * S_avg
     else:
         formula_bytes = 88 * R + 76 * M_avg
-    formula_bytes += (8 * S_avg if hp.save_optical_depth else 0) + grid_bytes + sb["grid_update"]
+    formula_bytes += (8 * S_avg if hp.save_optical_depth and not fused else 0) + grid_bytes + sb["grid_update"]
 
     extra = {}
     if workload == "batched" and not args.no_batched_compare:
@@ -598,7 +625,9 @@ def measure(args, workload, ray_scale=1.0):
     cfg.update({
         "grid_update_samples": sc.n_grid, "parallelism": "rays sharded per GPU (weak), %d GPU(s)" % world,
         "l2": "flushed before every step (256 MB write); per-step working set > 1 GB",
-        "timed": "march + prune + render_fwd + render_bwd + grid_update (field and loss are user code, untimed)",
+        "timed": ("march + prune + render_fused (forward, MSE loss gradient, backward in one call) + grid_update "
+                  "(field is user code, untimed)") if fused else
+                 "march + prune + render_fwd + render_bwd + grid_update (field and loss are user code, untimed)",
     })
     line = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
@@ -625,7 +654,7 @@ def measure(args, workload, ray_scale=1.0):
                      "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes": int(sb[dom]), "limiter": LIMITER[dom]},
         "wall_s_timed_loop_incl_field": round(t_wall, 3),
-        "gpu_launches": launches_per_step(w, sc.n_cells, sc.n_grid, hp.ema.data_ptr(), hp.use_sat) * args.steps,
+        "gpu_launches": launches_per_step(w, sc.n_cells, sc.n_grid, hp.ema.data_ptr(), hp.use_sat, fused) * args.steps,
         "clocks": clk,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -455,6 +455,26 @@ int nacc_render_bwd(const int32_t* packed_info, int32_t n_rays, const float* t_s
                     float* d_rgbs, int32_t* d_status, void* stream);
 
 /*
+ * Forward rendering, the gradient of a squared-error loss on the colours and the
+ * backward, in one pass (Eq. 1 and Sec. 2.2, for the photometric loss of the
+ * Sec. 3 listing). With L = (grad_scale / 2) * sum_r |C_r - C*_r|^2 (grad_scale =
+ * 2 / (3 n_rays): the mean squared error over rays and channels), dL/dC_r =
+ * grad_scale * (C_r - C*_r) is known once ray r is rendered, so each ray is
+ * rendered forward and then differentiated while its samples are still cached:
+ * the samples are read from memory once and no optical depth is stored.
+ * Outputs equal nacc_render_fwd's (color, opacity, depth; each nullable) and
+ * nacc_render_bwd's for g_color = (C - C*) * grad_scale formed in float32 (two
+ * roundings), g_opacity = g_depth = 0 (d_sigmas (n_samples,), d_rgbs
+ * (n_samples,3)). target (n_rays,3) float32; sq_err (n_rays,) or NULL: sum over
+ * channels of (C - C*)^2 per ray (the loss is grad_scale / 2 times its sum).
+ * Float arrays and packed_info 8-byte aligned; grad_scale finite.
+ */
+int nacc_render_mse_fused(const int32_t* packed_info, int32_t n_rays, const float* t_starts,
+                          const float* t_ends, const float* sigmas, const float* rgbs, int64_t n_samples,
+                          const float* target, float grad_scale, float* color, float* opacity, float* depth,
+                          float* sq_err, float* d_sigmas, float* d_rgbs, int32_t* d_status, void* stream);
+
+/*
  * Capacity-sized sample arrays whose count stays on the device (a training step
  * without host reads): value into arr[i * width + c] for every i in
  * [*n_dev, capacity) and c < width, *n_dev read on the device (clamped to

@@ -38,7 +38,7 @@ EXPORTS = (
     "nacc_march_rays_batched", "nacc_prune_workspace_size",
     "nacc_prune_samples", "nacc_march_fused", "nacc_density_field_at_samples", "nacc_density_field_query",
     "nacc_render_weights", "nacc_accumulate_along_rays", "nacc_render_weights_bwd",
-    "nacc_accumulate_along_rays_bwd", "nacc_render_fwd", "nacc_render_bwd",
+    "nacc_accumulate_along_rays_bwd", "nacc_render_fwd", "nacc_render_bwd", "nacc_render_mse_fused",
     "nacc_unpack_info", "nacc_fill_tail_f32", "nacc_update_occupancy_grid", "nacc_density_threshold", "nacc_sample_grid_cells", "nacc_tune_set", "nacc_tune_get",
     "nacc_test_hook_set", "nacc_test_hook_get", "nacc_error_string",
     "nacc_version",
@@ -137,6 +137,7 @@ def load() -> ctypes.CDLL:
         "nacc_accumulate_along_rays_bwd": (ctypes.c_int, [P, i32, P, P, i32, i64, P, P, P, P, P, P]),
         "nacc_render_fwd": (ctypes.c_int, [P, i32, P, P, P, P, i64, P, P, P, P, P, P]),
         "nacc_render_bwd": (ctypes.c_int, [P, i32, P, P, P, P, P, i64, P, P, P, P, P, P, P]),
+        "nacc_render_mse_fused": (ctypes.c_int, [P, i32, P, P, P, P, i64, P, f32, P, P, P, P, P, P, P, P]),
         "nacc_unpack_info": (ctypes.c_int, [P, i32, i64, P, P, P]),
         "nacc_fill_tail_f32": (ctypes.c_int, [P, i64, i64, P, f32, P]),
         "nacc_update_occupancy_grid": (ctypes.c_int, [P, P, i64, P, P, i64, f32, f32, f32, P, P]),
@@ -565,6 +566,30 @@ def render_bwd(packed_info, t_starts, t_ends, sigmas, rgbs, n_samples: int, g_co
     return _call("nacc_render_bwd", (_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), _ptr(rgbs),
                                      _ptr(optical_depth), int(n_samples), _ptr(g_color), _ptr(g_opacity), _ptr(g_depth),
                                      _ptr(d_sigmas), _ptr(d_rgbs), _ptr(d_status), _stream(stream)), defer)
+
+
+def render_mse_fused(packed_info, t_starts, t_ends, sigmas, rgbs, n_samples: int, target, grad_scale: float, color,
+                     d_sigmas, d_rgbs, opacity=None, depth=None, sq_err=None, d_status=None, stream=None,
+                     defer: bool = False):
+    """nacc_render_mse_fused: forward, the squared-error loss gradient
+    grad_scale * (C - target) and the backward in one pass."""
+    n = packed_info.shape[0]
+    _check(packed_info, torch.int32, "packed_info", 2 * n)
+    for t, nm in ((t_starts, "t_starts"), (t_ends, "t_ends"), (sigmas, "sigmas")):
+        _check(t, torch.float32, nm, n_samples)
+    _check(rgbs, torch.float32, "rgbs", 3 * n_samples)
+    _check(target, torch.float32, "target", 3 * n)
+    _check(color, torch.float32, "color", 3 * n, optional=True)
+    _check(opacity, torch.float32, "opacity", n, optional=True)
+    _check(depth, torch.float32, "depth", n, optional=True)
+    _check(sq_err, torch.float32, "sq_err", n, optional=True)
+    _check(d_sigmas, torch.float32, "d_sigmas", n_samples)
+    _check(d_rgbs, torch.float32, "d_rgbs", 3 * n_samples)
+    _check(d_status, torch.int32, "d_status", 1, optional=True)
+    return _call("nacc_render_mse_fused", (_ptr(packed_info), n, _ptr(t_starts), _ptr(t_ends), _ptr(sigmas),
+                                           _ptr(rgbs), int(n_samples), _ptr(target), float(grad_scale), _ptr(color),
+                                           _ptr(opacity), _ptr(depth), _ptr(sq_err), _ptr(d_sigmas), _ptr(d_rgbs),
+                                           _ptr(d_status), _stream(stream)), defer)
 
 
 def unpack_info(packed_info, n_samples: int, ray_indices, d_status=None, stream=None):

@@ -460,6 +460,66 @@ def render_packed(sigmas, rgbs, packed_info, t_starts, t_ends, save_optical_dept
                            t_ends.contiguous().view(-1), save_optical_depth, n_samples)
 
 
+class _RenderMseFn(torch.autograd.Function):
+    """Eq. 1 forward, the mean squared error of the colours against a target and
+    its gradient in one call (nacc_render_mse_fused); the backward scales the
+    gradients the call formed by the loss's incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, sigmas, rgbs, packed_info, t_starts, t_ends, target, n_dev=None):
+        R = packed_info.shape[0]
+        M = t_starts.numel()
+        dev = packed_info.device
+        sg = sigmas.detach().contiguous().view(-1).float()
+        rgb = rgbs.detach().contiguous().view(-1, 3).float()
+        tgt = target.detach().contiguous().view(-1, 3).float()
+        color = torch.empty((R, 3), dtype=torch.float32, device=dev)
+        opacity = torch.empty((R, 1), dtype=torch.float32, device=dev)
+        depth = torch.empty((R, 1), dtype=torch.float32, device=dev)
+        sq_err = torch.empty(R, dtype=torch.float32, device=dev)
+        d_sig = torch.empty(M, dtype=torch.float32, device=dev)
+        d_rgb = torch.empty((M, 3), dtype=torch.float32, device=dev)
+        # L = mean over rays and channels of (C - C*)^2: dL/dC = 2 (C - C*) / (3 R)
+        _lib.render_mse_fused(packed_info, t_starts, t_ends, sg, rgb, M, tgt, 2.0 / (3.0 * max(R, 1)), color, d_sig,
+                              d_rgb, opacity=opacity, depth=depth, sq_err=sq_err)
+        if n_dev is not None:  # padding past the device count: no run covers it
+            _lib.fill_tail(d_sig, n_dev)
+            _lib.fill_tail(d_rgb, n_dev)
+        ctx.save_for_backward(d_sig, d_rgb)
+        ctx.sig_shape = sigmas.shape
+        ctx.rgb_shape = rgbs.shape
+        loss = sq_err.sum() / (3.0 * max(R, 1))
+        ctx.mark_non_differentiable(color, opacity, depth)
+        return loss, color, opacity, depth
+
+    @staticmethod
+    def backward(ctx, g_loss, g_color, g_opacity, g_depth):
+        d_sig, d_rgb = ctx.saved_tensors
+        g = g_loss.float()
+        return (d_sig * g).view(ctx.sig_shape), (d_rgb * g).view(ctx.rgb_shape), None, None, None, None, None
+
+
+def render_packed_mse(sigmas, rgbs, packed_info, t_starts, t_ends, target, n_samples=None):
+    """Eq. 1 over packed samples with the mean-squared-error loss against ``target``
+    (R,3) in one call: (loss, color (R,3), opacity (R,1), depth (R,1)). Only the loss
+    is differentiable; its gradient w.r.t. sigmas and rgbs is formed in the same
+    pass as the colours, reading the samples once (the loss of the Sec. 3 listing,
+    fused with rendering). n_samples: as in ``render_packed``."""
+    return _RenderMseFn.apply(sigmas, rgbs, packed_info.contiguous(), t_starts.contiguous().view(-1),
+                              t_ends.contiguous().view(-1), target, n_samples)
+
+
+def rendering_mse(rgb_sigma_fn: Callable, packed_info, t_starts, t_ends, target, ray_indices=None, n_samples=None):
+    """``rendering`` with the mean-squared-error loss against ``target`` fused in:
+    (loss, color, opacity, depth), the loss differentiable w.r.t. the field."""
+    if ray_indices is None:
+        if n_samples is not None:
+            raise ValueError("capacity mode: pass the ray_indices ray_marching returned (padding needs valid indices)")
+        ray_indices = unpack_info(packed_info, t_starts.numel())
+    rgbs, sigmas = rgb_sigma_fn(t_starts.view(-1, 1), t_ends.view(-1, 1), ray_indices)
+    return render_packed_mse(sigmas, rgbs, packed_info, t_starts, t_ends, target, n_samples)
+
+
 def rendering(rgb_sigma_fn: Callable, packed_info, t_starts, t_ends, ray_indices=None, save_optical_depth=False,
               n_samples=None):
     """Query the user's field with gradients and render (Sec. 2.2). Returns (color, opacity, depth).

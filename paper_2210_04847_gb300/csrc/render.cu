@@ -1238,6 +1238,174 @@ __global__ void __launch_bounds__(kRenderThreads, kBulkMinBlocks) render_bwd_bul
 }
 
 // ---------------------------------------------------------------------------
+// forward, squared-error loss gradient and backward in one pass
+// ---------------------------------------------------------------------------
+//
+// For a loss L = (s / 2) sum_r |C_r - C*_r|^2 (s = 2 / (3 R): the mean squared
+// error of the colours) dL/dC_r = s (C_r - C*_r) is known as soon as ray r's
+// colour is: the warp renders the ray forward (render_fwd_kernel's arithmetic,
+// keeping each chunk's optical-depth carry in shared memory), forms the
+// gradient, and runs the reverse scan (render_bwd_kernel's recompute path) over
+// the same samples while they are still in L2. The samples are read from DRAM
+// once instead of twice and no optical depth is stored; the results equal those
+// of nacc_render_fwd, the gradient formed as (C - C*) * s in float32, and
+// nacc_render_bwd.
+
+struct MseArgs {
+    const int32_t* packed_info;
+    int32_t n_rays;
+    const float* t_starts;
+    const float* t_ends;
+    const float* sigmas;
+    const float* rgbs;
+    int64_t n_samples;
+    const float* target;  // (n_rays, 3)
+    float grad_scale;     // s
+    float* color;
+    float* opacity;
+    float* depth;
+    float* sq_err;  // per ray sum_c (C - C*)^2, or null
+    float* d_sigmas;
+    float* d_rgbs;
+    int32_t* d_status;
+};
+
+template <int MINB>
+__global__ void __launch_bounds__(kRenderThreads, MINB) render_mse_kernel(const MseArgs a) {
+    __shared__ float s_carry[kRenderThreads / 32][kCarryCap];
+    const int lane = threadIdx.x & 31;
+    float* carries = s_carry[threadIdx.x >> 5];
+    const int ray0 = global_warp() * kGroup;
+    if (ray0 >= a.n_rays) return;
+    const int nr = min(kGroup, a.n_rays - ray0);
+    int my_off, my_cnt;
+    load_group(a.packed_info, ray0, nr, a.n_samples, a.d_status, lane, my_off, my_cnt);
+    for (int ri = 0; ri < nr; ++ri) {
+        const unsigned lo = __shfl_sync(FULL, my_off, ri);
+        const int cnt = __shfl_sync(FULL, my_cnt, ri);
+        const size_t r = (size_t)ray0 + ri;
+        const unsigned hi = lo + cnt;
+        const unsigned abase = lo & ~1u;
+        const int nch = cnt > 0 ? (int)((hi - abase + 63) >> 6) : 0;
+
+        // forward: chunks in order, the carry at the start of each chunk kept
+        float carry = 0.0f;
+        float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, op = 0.0f, dp = 0.0f;
+        for (int c = 0; c < nch; ++c) {
+            if (lane == 0 && c < kCarryCap) carries[c] = carry;
+            Pair q;
+            load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, abase + ((unsigned)c << 6) + 2 * lane, lo, hi, q);
+            const float tau0 = q.v0 ? tau_of(q.s0[0], q.s1[0], q.sg[0]) : 0.0f;
+            const float tau1 = q.v1 ? tau_of(q.s0[1], q.s1[1], q.sg[1]) : 0.0f;
+            float O0, O1;
+            pair_optical_depth(tau0, tau1, carry, lane, O0, O1);
+            const float w0 = q.v0 ? __expf(-O0) * alpha_of(tau0) : 0.0f;
+            const float w1 = q.v1 ? __expf(-O1) * alpha_of(tau1) : 0.0f;
+            c0 += w0 * q.rgb[0] + w1 * q.rgb[3];
+            c1 += w0 * q.rgb[1] + w1 * q.rgb[4];
+            c2 += w0 * q.rgb[2] + w1 * q.rgb[5];
+            op += w0 + w1;
+            dp += w0 * ((q.s0[0] + q.s1[0]) * 0.5f) + w1 * ((q.s0[1] + q.s1[1]) * 0.5f);
+        }
+        const float sum = warp_sum5(c0, c1, c2, op, dp, lane);
+        if (lane == 0 && a.color) a.color[3 * r] = sum;
+        if (lane == 4 && a.color) a.color[3 * r + 1] = sum;
+        if (lane == 8 && a.color) a.color[3 * r + 2] = sum;
+        if (lane == 12 && a.opacity) a.opacity[r] = sum;
+        if (lane == 16 && a.depth) a.depth[r] = sum;
+        const float e0 = __fsub_rn(__shfl_sync(FULL, sum, 0), __ldg(a.target + 3 * r));
+        const float e1 = __fsub_rn(__shfl_sync(FULL, sum, 4), __ldg(a.target + 3 * r + 1));
+        const float e2 = __fsub_rn(__shfl_sync(FULL, sum, 8), __ldg(a.target + 3 * r + 2));
+        if (lane == 0 && a.sq_err) a.sq_err[r] = e0 * e0 + e1 * e1 + e2 * e2;
+        if (nch == 0) continue;
+        const float gc0 = __fmul_rn(e0, a.grad_scale);
+        const float gc1 = __fmul_rn(e1, a.grad_scale);
+        const float gc2 = __fmul_rn(e2, a.grad_scale);
+        const float ga = 0.0f, gd = 0.0f;
+        __syncwarp();  // the carries
+
+        // backward (render_bwd_kernel, recompute path): chunks in reverse order
+        const float r_ref = __ldg(a.rgbs + 3 * (size_t)lo);
+        const float g_ref = __ldg(a.rgbs + 3 * (size_t)lo + 1);
+        const float b_ref = __ldg(a.rgbs + 3 * (size_t)lo + 2);
+        const float tm_ref = (__ldg(a.t_starts + lo) + __ldg(a.t_ends + lo)) * 0.5f;
+        const float a_ref = gc0 * r_ref + gc1 * g_ref + gc2 * b_ref + ga + gd * tm_ref;
+        const unsigned last = hi - 1 - abase;
+        const int last_lane = (int)((last >> 1) & 31);
+        const bool last_odd = (last & 1) != 0;
+        float t_end = 0.0f;
+        float carry_s = 0.0f;
+        for (int c = nch - 1; c >= 0; --c) {
+            float carry_o;
+            if (c < kCarryCap) {
+                carry_o = carries[c];
+            } else {  // rays longer than the shared-memory record: rescan from the last record
+                carry_o = carries[kCarryCap - 1];
+                for (int p = kCarryCap - 1; p < c; ++p) {
+                    const unsigned pj = abase + ((unsigned)p << 6) + 2 * lane;
+                    const bool pv0 = pj >= lo && pj < hi, pv1 = pj + 1 >= lo && pj + 1 < hi;
+                    const float t0 = pv0 ? tau_of(__ldg(a.t_starts + pj), __ldg(a.t_ends + pj), __ldg(a.sigmas + pj))
+                                         : 0.0f;
+                    const float t1 = pv1 ? tau_of(__ldg(a.t_starts + pj + 1), __ldg(a.t_ends + pj + 1),
+                                                  __ldg(a.sigmas + pj + 1))
+                                         : 0.0f;
+                    float O0, O1;
+                    pair_optical_depth(t0, t1, carry_o, lane, O0, O1);
+                }
+            }
+            const unsigned j0 = abase + ((unsigned)c << 6) + 2 * lane;
+            Pair q;
+            load_pair(a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0, lo, hi, q);
+            const float tau0 = q.v0 ? tau_of(q.s0[0], q.s1[0], q.sg[0]) : 0.0f;
+            const float tau1 = q.v1 ? tau_of(q.s0[1], q.s1[1], q.sg[1]) : 0.0f;
+            float O0, O1;
+            pair_optical_depth(tau0, tau1, carry_o, lane, O0, O1);
+            const float T0 = __expf(-O0);
+            const float T1 = __expf(-O1);
+            const float T2 = __expf(-__fadd_rn(O1, tau1));
+            const float Tn0 = q.v1 ? T1 : __expf(-__fadd_rn(O0, tau0));
+            if (c == nch - 1) t_end = __shfl_sync(FULL, last_odd ? T2 : Tn0, last_lane);
+            const float w0 = q.v0 ? T0 * alpha_of(tau0) : 0.0f;
+            const float w1 = q.v1 ? T1 * alpha_of(tau1) : 0.0f;
+            const float tm0 = (q.s0[0] + q.s1[0]) * 0.5f, tm1 = (q.s0[1] + q.s1[1]) * 0.5f;
+            const float b0 = gc0 * (q.rgb[0] - r_ref) + gc1 * (q.rgb[1] - g_ref) + gc2 * (q.rgb[2] - b_ref) +
+                             gd * (tm0 - tm_ref);
+            const float b1 = gc0 * (q.rgb[3] - r_ref) + gc1 * (q.rgb[4] - g_ref) + gc2 * (q.rgb[5] - b_ref) +
+                             gd * (tm1 - tm_ref);
+            const float bw0 = q.v0 ? b0 * w0 : 0.0f;
+            const float bw1 = q.v1 ? b1 * w1 : 0.0f;
+            const float suf = warp_incl_suffix(bw0 + bw1, lane);
+            float later = __shfl_down_sync(FULL, suf, 1);
+            if (lane == 31) later = 0.0f;
+            const float S1 = carry_s + later;
+            const float S0 = S1 + bw1;
+            carry_s = carry_s + __shfl_sync(FULL, suf, 0);
+            const float base_g = a_ref * t_end;
+            const float ds0 = (q.s1[0] - q.s0[0]) * (base_g + (b0 * Tn0 - S0));
+            const float ds1 = (q.s1[1] - q.s0[1]) * (base_g + (b1 * T2 - S1));
+            if (q.v0 && q.v1) {
+                *reinterpret_cast<float2*>(a.d_sigmas + j0) = make_float2(ds0, ds1);
+                float2* dr = reinterpret_cast<float2*>(a.d_rgbs + 3 * (size_t)j0);
+                dr[0] = make_float2(w0 * gc0, w0 * gc1);
+                dr[1] = make_float2(w0 * gc2, w1 * gc0);
+                dr[2] = make_float2(w1 * gc1, w1 * gc2);
+            } else if (q.v0) {
+                a.d_sigmas[j0] = ds0;
+                a.d_rgbs[3 * (size_t)j0] = w0 * gc0;
+                a.d_rgbs[3 * (size_t)j0 + 1] = w0 * gc1;
+                a.d_rgbs[3 * (size_t)j0 + 2] = w0 * gc2;
+            } else if (q.v1) {
+                a.d_sigmas[j0 + 1] = ds1;
+                a.d_rgbs[3 * (size_t)j0 + 3] = w1 * gc0;
+                a.d_rgbs[3 * (size_t)j0 + 4] = w1 * gc1;
+                a.d_rgbs[3 * (size_t)j0 + 5] = w1 * gc2;
+            }
+        }
+        __syncwarp();  // the carries are read before the next ray writes them
+    }
+}
+
+// ---------------------------------------------------------------------------
 // ray index of every sample
 // ---------------------------------------------------------------------------
 
@@ -1470,6 +1638,32 @@ extern "C" int nacc_render_bwd(const int32_t* packed_info, int32_t n_rays, const
             if (pf) render_bwd_kernel<1, true><<<nb, kRenderThreads, 0, st>>>(a);
             else render_bwd_kernel<1, false><<<nb, kRenderThreads, 0, st>>>(a);
             break;
+    }
+    return launch_status(cudaGetLastError());
+}
+
+extern "C" int nacc_render_mse_fused(const int32_t* packed_info, int32_t n_rays, const float* t_starts,
+                                     const float* t_ends, const float* sigmas, const float* rgbs, int64_t n_samples,
+                                     const float* target, float grad_scale, float* color, float* opacity,
+                                     float* depth, float* sq_err, float* d_sigmas, float* d_rgbs, int32_t* d_status,
+                                     void* stream) {
+    if (!sizes_ok(n_rays, n_samples)) return NACC_ERR_INVALID_ARG;
+    if (n_rays > 0 && (!packed_info || !target)) return NACC_ERR_INVALID_ARG;
+    if (n_samples > 0 && (!t_starts || !t_ends || !sigmas || !rgbs || !d_sigmas || !d_rgbs))
+        return NACC_ERR_INVALID_ARG;
+    if (!(fabsf(grad_scale) <= 3.402823466e+38f)) return NACC_ERR_INVALID_ARG;
+    if (n_rays == 0) return NACC_OK;
+    if ((((uintptr_t)packed_info | (uintptr_t)t_starts | (uintptr_t)t_ends | (uintptr_t)sigmas | (uintptr_t)rgbs |
+          (uintptr_t)d_sigmas | (uintptr_t)d_rgbs) & 7u) != 0)
+        return NACC_ERR_INVALID_ARG;
+    MseArgs a{packed_info, n_rays, t_starts, t_ends, sigmas, rgbs, n_samples, target, grad_scale,
+              color, opacity, depth, sq_err, d_sigmas, d_rgbs, d_status};
+    const int nb = group_blocks(n_rays);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (tune_get(NACC_TUNE_RENDER_BWD_OCCUPANCY)) {
+        case 1: render_mse_kernel<16><<<nb, kRenderThreads, 0, st>>>(a); break;
+        case 2: render_mse_kernel<12><<<nb, kRenderThreads, 0, st>>>(a); break;
+        default: render_mse_kernel<1><<<nb, kRenderThreads, 0, st>>>(a); break;
     }
     return launch_status(cudaGetLastError());
 }

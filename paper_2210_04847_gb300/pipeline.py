@@ -131,6 +131,13 @@ class HotPath:
                                None, None, self.d_sig[:S], self.d_rgb[:S], optical_depth=od, d_status=self.status,
                                defer=defer)
 
+    def render_mse(self, n_kept: int, target, defer=False):
+        """Forward, the mean-squared-error gradient against ``target`` and the backward in one call."""
+        S = min(int(n_kept), self.cap_k)
+        return _lib.render_mse_fused(self.pi_k, self.ts_k[:S], self.te_k[:S], self.sig_k[:S], self.rgb_k[:S], S,
+                                     target, 2.0 / (3.0 * self.R), self.color, self.d_sig[:S], self.d_rgb[:S],
+                                     opacity=self.opacity, depth=self.depth, d_status=self.status, defer=defer)
+
     def sample_cells(self, seed: int, step: int, defer=False):
         """Random cells of the grid and a point in each for the update (``cells``, ``cell_xyz``)."""
         if self.n_grid:
