@@ -577,7 +577,9 @@ int nacc_sample_grid_cells(uint64_t seed, uint64_t stream, int64_t n, const nacc
                                           memory by bulk copies, that many stages per warp (16-byte aligned
                                           arrays; others take the register path) */
 #define NACC_TUNE_RENDER_BWD_STAGES 14  /* backward with the saved optical depth: as NACC_TUNE_RENDER_FWD_STAGES */
-#define NACC_TUNE_COUNT 15
+#define NACC_TUNE_RENDER_MSE_OCCUPANCY 15 /* nacc_render_mse_fused: 0 compiler's register use; capped for 1: 8,
+                                            2: 12 blocks/SM */
+#define NACC_TUNE_COUNT 16
 
 /* Set a knob; NACC_ERR_INVALID_ARG for an unknown knob or out-of-range value. */
 int nacc_tune_set(int knob, int value);

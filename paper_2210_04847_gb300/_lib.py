@@ -51,7 +51,8 @@ TUNE_KNOBS = {"render_fwd_prefetch": 0, "march_tile_rays": 1, "prune_tile_rays":
               "prune_occupancy": 4, "render_fwd_occupancy": 5, "render_bwd_occupancy": 6, "march_unroll": 7,
               "prune_interleave": 8, "render_bwd_prefetch": 9,
               "march_coarse": 10, "fused_occupancy": 11, "march_box_tile": 12,
-              "render_fwd_stages": 13, "render_bwd_stages": 14}
+              "render_fwd_stages": 13, "render_bwd_stages": 14,
+              "render_mse_occupancy": 15}
 
 
 class NaccError(RuntimeError):

@@ -31,6 +31,7 @@ CANDIDATES = {
     "render_bwd_prefetch": (0, 1),
     "render_fwd_stages": (0, 2, 3, 4),
     "render_bwd_stages": (0, 2, 3, 4),
+    "render_mse_occupancy": (0, 1, 2),
 }
 
 
@@ -158,6 +159,9 @@ def tune_hot_path(hp, sc, batch: int = 0, reps: int = 7, flush: Callable[[], Non
     hp.render_fwd(S)
     rec.append(tk("render_bwd_stages", lambda: hp.render_bwd(S)))
     hp.save_optical_depth = saved0
+    # forward + loss gradient + backward in one call (the fused alternative)
+    if bt.get("tgt") is not None:
+        rec.append(tk("render_mse_occupancy", lambda: hp.render_mse(S, bt["tgt"])))
     # forward + backward with the optical depth recomputed, or saved by the forward
     times = {}
     for saved in (False, True):

@@ -42,9 +42,10 @@ int g_tune[NACC_TUNE_COUNT] = {
     0,  // NACC_TUNE_MARCH_BOX_TILE
     0,  // NACC_TUNE_RENDER_FWD_STAGES
     2,  // NACC_TUNE_RENDER_BWD_STAGES
+    2,  // NACC_TUNE_RENDER_MSE_OCCUPANCY
 };
-const int g_tune_lo[NACC_TUNE_COUNT] = {0, 1, 2, 0, 0, 0, 0, 0, 2, 0, 0, 0, 0, 0, 0};
-const int g_tune_hi[NACC_TUNE_COUNT] = {1, 32, 32, 1, 2, 2, 2, 1, 4, 1, 1, 1, 3, 4, 4};
+const int g_tune_lo[NACC_TUNE_COUNT] = {0, 1, 2, 0, 0, 0, 0, 0, 2, 0, 0, 0, 0, 0, 0, 0};
+const int g_tune_hi[NACC_TUNE_COUNT] = {1, 32, 32, 1, 2, 2, 2, 1, 4, 1, 1, 1, 3, 4, 4, 2};
 }  // namespace
 
 int tune_get(int knob) { return (knob >= 0 && knob < NACC_TUNE_COUNT) ? g_tune[knob] : 0; }

@@ -1660,8 +1660,8 @@ extern "C" int nacc_render_mse_fused(const int32_t* packed_info, int32_t n_rays,
               color, opacity, depth, sq_err, d_sigmas, d_rgbs, d_status};
     const int nb = group_blocks(n_rays);
     cudaStream_t st = (cudaStream_t)stream;
-    switch (tune_get(NACC_TUNE_RENDER_BWD_OCCUPANCY)) {
-        case 1: render_mse_kernel<16><<<nb, kRenderThreads, 0, st>>>(a); break;
+    switch (tune_get(NACC_TUNE_RENDER_MSE_OCCUPANCY)) {
+        case 1: render_mse_kernel<8><<<nb, kRenderThreads, 0, st>>>(a); break;
         case 2: render_mse_kernel<12><<<nb, kRenderThreads, 0, st>>>(a); break;
         default: render_mse_kernel<1><<<nb, kRenderThreads, 0, st>>>(a); break;
     }

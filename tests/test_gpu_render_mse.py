@@ -93,12 +93,12 @@ def scene(orc):
 @pytest.mark.parametrize("occupancy", [0, 1, 2])
 def test_fused_equals_separate_pruned(scene, orc, occupancy):
     p = scene["p"]
-    old = _lib.tune_get("render_bwd_occupancy")
+    old = _lib.tune_get("render_mse_occupancy")
     try:
-        _lib.tune_set("render_bwd_occupancy", occupancy)
+        _lib.tune_set("render_mse_occupancy", occupancy)
         _check(orc, p.packed_info, p.t_starts, p.t_ends, scene["sig2"], scene["rgb2"], 1)
     finally:
-        _lib.tune_set("render_bwd_occupancy", old)
+        _lib.tune_set("render_mse_occupancy", old)
 
 
 def test_fused_equals_separate_unpruned(scene, orc):
