@@ -646,8 +646,11 @@ def measure(args, workload, ray_scale=1.0, fused=False):
         "step_hbm": {"algorithmic_bytes": int(step_bytes), "gbs": round(step_bytes / (mean_ms / 1e3) / 1e9, 1),
                      "frac": round(step_bytes / (mean_ms / 1e3) / 1e9 / peak, 4), "peak_gbs": peak,
                      "peak_kind": peak_kind},
-        "step_hbm_formula": {"bytes": "104R + 24M + 76S (pruning on; 88R + 76M off) + 8S saved O + bitfield + "
-                                      "grid update: pruning counted as reading every marched sample",
+        "step_hbm_formula": {"bytes": ("88R + 24M + 52S (pruning on; 72R + 52M off; rendering fused: the kept "
+                                       "samples read once) + bitfield + grid update: pruning counted as reading every "
+                                       "marched sample") if fused else
+                                      ("104R + 24M + 76S (pruning on; 88R + 76M off) + 8S saved O + bitfield + "
+                                       "grid update: pruning counted as reading every marched sample"),
                              "algorithmic_bytes": int(formula_bytes),
                              "frac": round(formula_bytes / (mean_ms / 1e3) / 1e9 / peak, 4)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
