@@ -751,6 +751,113 @@ __device__ __forceinline__ void finish_tile(const MarchArgs& a, const uint32_t* 
         const int r = ray0 + i;
         const uint32_t* row = wmask + i * a.row_stride;
         unsigned base = (unsigned)excl + (unsigned)__shfl_sync(FULL, my_excl, i);
+        if (shared && a.vec_out) {
+            // a shared lattice with 16-byte aligned outputs: the words are taken 32 at a
+            // time; in a run of full words output p holds lattice point
+            // k = k_run + (p - p_run), so lane l writes four consecutive samples with one
+            // 16-byte store per array (t_k .. t_{k+4} give their four intervals), after
+            // a scalar head up to the 16-byte boundary; other words as below
+            const bool fits = (unsigned long long)base + (unsigned)cnt <= (unsigned long long)cap;
+            for (int c0 = 0; c0 < nch; c0 += 32) {
+                const uint32_t mw = c0 + lane < nch ? row[c0 + lane] : 0u;
+                const unsigned fullb = __ballot_sync(FULL, mw == ~0u);
+                const unsigned nonz = __ballot_sync(FULL, mw != 0u);
+                int w = 0;
+                const int nw = min(32, nch - c0);
+                while (w < nw) {
+                    const unsigned rest = nonz >> w;
+                    if (rest == 0u) break;
+                    w += __ffs(rest) - 1;  // the next non-empty word
+                    if ((fullb >> w) & 1u) {
+                        const unsigned fr = ~(fullb >> w);
+                        const int run = fr ? __ffs(fr) - 1 : 32 - w;  // consecutive full words from w
+                        const unsigned n = 32u * (unsigned)run;
+                        const int k0 = (c0 + w) << 5;
+                        const unsigned head = min((4u - (base & 3u)) & 3u, n);
+                        const unsigned groups = (n - head) >> 2;
+                        for (unsigned q = (unsigned)lane; q < groups; q += 32u) {
+                            const unsigned p = base + head + 4u * q;
+                            const int k = k0 + (int)(head + 4u * q);
+                            float t[5];
+#pragma unroll
+                            for (int j = 0; j < 5; ++j) {
+                                if (!CONE) {
+                                    t[j] = __fadd_rn(near, __fmul_rn(__int2float_rn(k + j), dt));
+                                } else {
+                                    t[j] = __ldg(a.cone_table + min(k + j, a.max_steps));
+                                }
+                            }
+                            const float4 ts4 = make_float4(t[0], t[1], t[2], t[3]);
+                            const float4 te4 = make_float4(t[1] < far ? t[1] : far, t[2] < far ? t[2] : far,
+                                                           t[3] < far ? t[3] : far, t[4] < far ? t[4] : far);
+                            if (fits || p + 3u < cap) {
+                                *reinterpret_cast<float4*>(a.t_starts + p) = ts4;
+                                *reinterpret_cast<float4*>(a.t_ends + p) = te4;
+                                *reinterpret_cast<int4*>(a.ray_indices + p) = make_int4(r, r, r, r);
+                            } else {
+                                const float sv[4] = {ts4.x, ts4.y, ts4.z, ts4.w};
+                                const float ev[4] = {te4.x, te4.y, te4.z, te4.w};
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    if (p + j < cap) {
+                                        a.t_starts[p + j] = sv[j];
+                                        a.t_ends[p + j] = ev[j];
+                                        a.ray_indices[p + j] = r;
+                                    }
+                                }
+                            }
+                        }
+                        // head (lanes 0 .. head - 1) and tail (the last (n - head) & 3 samples)
+                        const unsigned tail = (n - head) & 3u;
+                        const int sl = lane < (int)head ? lane : lane - (int)head;
+                        const bool is_head = lane < (int)head;
+                        const bool is_tail = !is_head && sl < (int)tail;
+                        if (is_head || is_tail) {
+                            const unsigned off = is_head ? (unsigned)lane : head + 4u * groups + (unsigned)sl;
+                            const unsigned pos = base + off;
+                            const int k = k0 + (int)off;
+                            float ts, tn;
+                            if (!CONE) {
+                                const float kf = __int2float_rn(k);
+                                ts = __fadd_rn(near, __fmul_rn(kf, dt));
+                                tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+                            } else {
+                                ts = __ldg(a.cone_table + min(k, a.max_steps));
+                                tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                            }
+                            if (fits || pos < cap) {
+                                a.t_starts[pos] = ts;
+                                a.t_ends[pos] = tn < far ? tn : far;
+                                a.ray_indices[pos] = r;
+                            }
+                        }
+                        base += n;
+                        w += run;
+                    } else {
+                        const unsigned m = __shfl_sync(FULL, mw, w);
+                        const int k = ((c0 + w) << 5) + lane;
+                        float ts, tn;
+                        if (!CONE) {
+                            const float kf = __int2float_rn(k);
+                            ts = __fadd_rn(near, __fmul_rn(kf, dt));
+                            tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
+                        } else {
+                            ts = __ldg(a.cone_table + min(k, a.max_steps));
+                            tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                        }
+                        const unsigned pos = base + __popc(m & lt);
+                        if (((m >> lane) & 1u) && (fits || pos < cap)) {
+                            a.t_starts[pos] = ts;
+                            a.t_ends[pos] = tn < far ? tn : far;
+                            a.ray_indices[pos] = r;
+                        }
+                        base += __popc(m);
+                        ++w;
+                    }
+                }
+            }
+            continue;
+        }
         if (shared) {
             // a shared lattice: four chunks' words read before any is used, so the
             // shared-memory reads overlap the stores of the chunks before; a full
@@ -1089,6 +1196,7 @@ int march_launch(MarchArgs& a, const nacc_march_params* p, int32_t* packed_info,
     a.t_starts = t_starts;
     a.t_ends = t_ends;
     a.ray_indices = ray_indices;
+    a.vec_out = ((((uintptr_t)t_starts | (uintptr_t)t_ends | (uintptr_t)ray_indices) & 15u) == 0) ? 1 : 0;
     a.capacity = capacity;
     a.n_samples = n_samples;
     a.d_status = d_status;

@@ -57,6 +57,7 @@ struct MarchArgs {
     float* t_starts;
     float* t_ends;
     int32_t* ray_indices;
+    int32_t vec_out;          // the three outputs are 16-byte aligned (16-byte stores for runs of full words)
     int64_t capacity;
     int64_t* n_samples;
     int32_t* d_status;
