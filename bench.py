@@ -46,8 +46,10 @@ POOL = 4  # distinct ray batches cycled through the steps (L2 is flushed between
 # from one ncu capture, keyed by the SHA-256 of the kernel's source file. A
 # source change invalidates the figure (reported as null until re-captured).
 NCU_TRAFFIC = {
-    # profiles/march_dram_bounded-2^18.md: 18993920 B read + 1478312960 B written (box walk, brick summary)
-    ("march", "f406db2f593624e8e17148e8dde60de500d04b63d53c093ebd78f80c40f5c2d4"): 1497306880,
+    # profiles/march_dram_bounded-2^18.md: 21322240 B read + 1476599040 B written (box walk, vector stores)
+    ("march", "5375087dc02a78305a0f1403806470e8f69f56a4245bfbfadb2d1f1785904618"): 1497921280,
+    # profiles/prune_dram_bounded-2^18.md: 1320007680 B read + 348302336 B written
+    ("prune", "072ed911e1ae6636de3d862a79ce81821140af2ef8ebe323831c1cd5ab57879c"): 1668310016,
     # profiles/march_fused_inference-800x800.md: 22437376 B read + 1169642240 B written (camera 0's image)
     ("march_fused", "c86e1bad5b55ca339d49805cf9ac418869661e8853df2abc21f41da92b781990"): 1192079616,
 }
@@ -56,7 +58,8 @@ NCU_TRAFFIC = {
 LIMITER = {
     "march": "issue (68% issue-active with 30 warps per SM, register-limited) plus the L1-to-L2 requests of the "
              "stores and the table reads the brick summary leaves (59% busy), at 46% DRAM",
-    "prune": "DRAM latency (long-scoreboard stalls)",
+    "prune": "latency of the chunk loads (long-scoreboard stalls); DRAM reads 1.46x the algorithmic reads, because "
+             "the store phase re-reads the kept samples after the next tile's decisions",
     "render_fwd": "DRAM latency / issue",
     "render_bwd": "issue (76% issue-active; chunks staged by bulk copies, long-scoreboard stalls 1 per issue)",
     "grid_update": "latency of 2^21 random atomics",
