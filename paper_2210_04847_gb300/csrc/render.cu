@@ -831,22 +831,26 @@ __global__ void __launch_bounds__(kRenderThreads, MINB) render_bwd_kernel(const 
 // chunk, up to NST - 1 chunks ahead of the chunk being computed, across the
 // rays of the warp's group (the backward walks each ray's chunks last to
 // first). Several chunks' loads are then in flight per warp without holding
-// registers. A stage holds a 68-sample window: the chunk's 64 samples from
-// the 16-byte boundary at or below its first pair. Samples from n4 =
+// registers. A forward stage holds a 68-sample window: the chunk's 64 samples
+// from the 16-byte boundary at or below its first pair; a backward stage holds
+// two consecutive chunks of a ray (132 samples), halving the per-chunk cost of
+// the waits, copies and cursors. Samples from n4 =
 // n_samples & ~3 on (the arrays' last partial 16 bytes) are read from global
 // memory directly. Needs t_starts, t_ends, sigmas, rgbs (and the optical
 // depth in the backward) 16-byte aligned; the entry points use the register
 // kernels otherwise.
 
-constexpr int kSpan = 68;                        // samples per stage window
+constexpr int kSpan = 68;                        // forward: samples per stage window (one chunk)
+constexpr int kBwdSpan = 132;                    // backward: two consecutive chunks per stage
 constexpr int kFwdStage = 3 * kSpan + 3 * kSpan;  // t_s, t_e, sigma, rgb (floats)
-constexpr int kBwdStage = 4 * kSpan + 3 * kSpan;  // t_s, t_e, sigma, O, rgb
+constexpr int kBwdStage = 4 * kBwdSpan + 3 * kBwdSpan;  // t_s, t_e, sigma, O, rgb
 constexpr int kBarBytes = 256;                   // mbarriers of the block (up to 8 stages x 4 warps)
 constexpr int kStageWaitPolls = 1 << 20;         // polls of a stage's barrier before the walk gives up
 constexpr int kBulkMinBlocks = 8;                // register cap of the staged kernels (64 per thread)
 
 static_assert((kRenderThreads / 32) * 8 * 8 <= kBarBytes, "barrier area");
-static_assert(kSpan % 4 == 0 && kFwdStage % 4 == 0 && kBwdStage % 4 == 0, "16-byte stage layout");
+static_assert(kSpan % 4 == 0 && kBwdSpan % 4 == 0 && kFwdStage % 4 == 0 && kBwdStage % 4 == 0,
+              "16-byte stage layout");
 
 size_t bulk_smem_bytes(int nst, bool bwd) {
     return kBarBytes + (size_t)(kRenderThreads / 32) * nst * (bwd ? kBwdStage : kFwdStage) * sizeof(float);
@@ -869,22 +873,37 @@ __device__ __forceinline__ Win chunk_window(unsigned rlo, unsigned rhi, int c, u
     return w;
 }
 
+// The window of chunks c - 1 and c (c alone when c = 0): from the 16-byte boundary
+// at or below chunk c - 1's first pair to the one at or above chunk c's last
+// sample, clipped to n4 (at most 132 samples).
+__device__ __forceinline__ Win pair_window(unsigned rlo, unsigned rhi, int c, unsigned n4) {
+    const unsigned c1 = (rlo & ~1u) + ((unsigned)c << 6);
+    const unsigned c0 = c > 0 ? c1 - 64u : c1;
+    const unsigned end = min(c1 + 64u, rhi);
+    Win w;
+    w.lo = c0 & ~3u;
+    w.hi = min((end + 3u) & ~3u, n4);
+    if (w.hi < w.lo) w.hi = w.lo;
+    return w;
+}
+
 // Lane 0: announce the window's bytes on the stage's barrier and copy the arrays
 // (od may be null: forward layout). (Copies issued by lanes 0 .. 4 at once, one
 // array each, measured slower.)
+template <int SPAN>
 __device__ __forceinline__ void issue_window(float* st, uint64_t* bar, Win w, const float* ts, const float* te,
                                              const float* sg, const float* od, const float* rgb, unsigned extra = 0) {
     const unsigned n = w.hi - w.lo, b = 4u * n;
     mbar_arrive_expect_tx(bar, (od ? 7u * b : 6u * b) + extra);
     if (n) {
         bulk_copy_g2s(st, ts + w.lo, b, bar);
-        bulk_copy_g2s(st + kSpan, te + w.lo, b, bar);
-        bulk_copy_g2s(st + 2 * kSpan, sg + w.lo, b, bar);
+        bulk_copy_g2s(st + SPAN, te + w.lo, b, bar);
+        bulk_copy_g2s(st + 2 * SPAN, sg + w.lo, b, bar);
         if (od) {
-            bulk_copy_g2s(st + 3 * kSpan, od + w.lo, b, bar);
-            bulk_copy_g2s(st + 4 * kSpan, rgb + 3 * (size_t)w.lo, 3u * b, bar);
+            bulk_copy_g2s(st + 3 * SPAN, od + w.lo, b, bar);
+            bulk_copy_g2s(st + 4 * SPAN, rgb + 3 * (size_t)w.lo, 3u * b, bar);
         } else {
-            bulk_copy_g2s(st + 3 * kSpan, rgb + 3 * (size_t)w.lo, 3u * b, bar);
+            bulk_copy_g2s(st + 3 * SPAN, rgb + 3 * (size_t)w.lo, 3u * b, bar);
         }
     }
 }
@@ -892,6 +911,7 @@ __device__ __forceinline__ void issue_window(float* st, uint64_t* bar, Win w, co
 // The lane's pair j0, j0 + 1 of a run [lo, hi) from a stage whose window starts
 // at wlo (rgb at st + rgb_at), as load_pair gives it. Every sample of the
 // chunk below n4 is in the window; those at or beyond n4 come from global memory.
+template <int SPAN>
 __device__ __forceinline__ void stage_pair(const float* st, int rgb_at, unsigned wlo, unsigned n4,
                                            const float* __restrict__ ts, const float* __restrict__ te,
                                            const float* __restrict__ sig, const float* __restrict__ rgbs,
@@ -905,8 +925,8 @@ __device__ __forceinline__ void stage_pair(const float* st, int rgb_at, unsigned
     const unsigned p = j0 - wlo;  // even: j0 and wlo are
     if (q.v0 && q.v1 && j0 + 1 < n4) {
         const float2 u = *reinterpret_cast<const float2*>(st + p);
-        const float2 v = *reinterpret_cast<const float2*>(st + kSpan + p);
-        const float2 g = *reinterpret_cast<const float2*>(st + 2 * kSpan + p);
+        const float2 v = *reinterpret_cast<const float2*>(st + SPAN + p);
+        const float2 g = *reinterpret_cast<const float2*>(st + 2 * SPAN + p);
         const float2* c = reinterpret_cast<const float2*>(st + rgb_at + 3 * p);
         const float2 c0 = c[0], c1 = c[1], c2 = c[2];
         q.s0[0] = u.x; q.s0[1] = u.y;
@@ -922,8 +942,8 @@ __device__ __forceinline__ void stage_pair(const float* st, int rgb_at, unsigned
                 if (j < n4) {
                     const unsigned l = p + k;
                     q.s0[k] = st[l];
-                    q.s1[k] = st[kSpan + l];
-                    q.sg[k] = st[2 * kSpan + l];
+                    q.s1[k] = st[SPAN + l];
+                    q.sg[k] = st[2 * SPAN + l];
                     q.rgb[3 * k] = st[rgb_at + 3 * l];
                     q.rgb[3 * k + 1] = st[rgb_at + 3 * l + 1];
                     q.rgb[3 * k + 2] = st[rgb_at + 3 * l + 2];
@@ -942,7 +962,7 @@ __device__ __forceinline__ void stage_pair(const float* st, int rgb_at, unsigned
 
 // Cursor over the chunks of the rays of a warp's group: rays in order (set bits
 // of `todo`, lane i = ray i), chunks first to last, or last to first (REV).
-template <bool REV>
+template <bool REV, int STEP = 1>
 struct ChunkCursor {
     unsigned todo, lo, hi;
     int i, c, nch;
@@ -954,9 +974,9 @@ struct ChunkCursor {
         nch = __shfl_sync(FULL, my_nch, i);
         c = REV ? nch - 1 : 0;
     }
-    // next chunk; returns true when it starts a new ray
+    // next chunk (STEP chunks on); returns true when it starts a new ray
     __device__ __forceinline__ bool next(int my_off, int my_cnt, int my_nch) {
-        c += REV ? -1 : 1;
+        c += REV ? -STEP : STEP;
         if (REV ? c < 0 : c >= nch) {
             if (todo) ray(my_off, my_cnt, my_nch);
             return true;
@@ -1020,7 +1040,8 @@ __global__ void __launch_bounds__(kRenderThreads, kBulkMinBlocks) render_fwd_bul
     const int pre = min(NST, total);
     for (int k = 0; k < pre; ++k) {
         if (lane == 0)
-            issue_window(stages + k * kFwdStage, &bars[k], chunk_window(P.lo, P.hi, P.c, n4), a.t_starts, a.t_ends,
+            issue_window<kSpan>(stages + k * kFwdStage, &bars[k], chunk_window(P.lo, P.hi, P.c, n4), a.t_starts,
+                                a.t_ends,
                          a.sigmas, nullptr, a.rgbs, k == 0 ? a.stage_extra : 0u);
         P.next(my_off, my_cnt, my_nch);
     }
@@ -1040,7 +1061,7 @@ __global__ void __launch_bounds__(kRenderThreads, kBulkMinBlocks) render_fwd_bul
         }
         const unsigned qj0 = (C.lo & ~1u) + ((unsigned)C.c << 6) + 2 * lane;
         Pair q;
-        stage_pair(st, 3 * kSpan, ((C.lo & ~1u) + ((unsigned)C.c << 6)) & ~3u, n4, a.t_starts, a.t_ends, a.sigmas,
+        stage_pair<kSpan>(st, 3 * kSpan, ((C.lo & ~1u) + ((unsigned)C.c << 6)) & ~3u, n4, a.t_starts, a.t_ends, a.sigmas,
                    a.rgbs, qj0, C.lo, C.hi, q);
         const float tau0 = q.v0 ? tau_of(q.s0[0], q.s1[0], q.sg[0]) : 0.0f;
         const float tau1 = q.v1 ? tau_of(q.s0[1], q.s1[1], q.sg[1]) : 0.0f;
@@ -1062,7 +1083,7 @@ __global__ void __launch_bounds__(kRenderThreads, kBulkMinBlocks) render_fwd_bul
         if (k + NST < total) {
             if (lane == 0) {
                 fence_proxy_async_smem();
-                issue_window(st, &bars[s], chunk_window(P.lo, P.hi, P.c, n4), a.t_starts, a.t_ends, a.sigmas, nullptr,
+                issue_window<kSpan>(st, &bars[s], chunk_window(P.lo, P.hi, P.c, n4), a.t_starts, a.t_ends, a.sigmas, nullptr,
                              a.rgbs);
             }
             P.next(my_off, my_cnt, my_nch);
@@ -1112,7 +1133,8 @@ __global__ void __launch_bounds__(kRenderThreads, kBulkMinBlocks) render_bwd_bul
     const unsigned todo = __ballot_sync(FULL, my_cnt > 0);
     if (todo == 0u) return;
     const int my_nch = my_cnt > 0 ? (int)(((unsigned)my_off + my_cnt - ((unsigned)my_off & ~1u) + 63u) >> 6) : 0;
-    int total = my_nch;
+    // a stage holds chunks c and c - 1 of a ray (c alone when c = 0), walked c first
+    int total = (my_nch + 1) >> 1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(FULL, total, o);
     if (lane == 0) {
@@ -1123,18 +1145,18 @@ __global__ void __launch_bounds__(kRenderThreads, kBulkMinBlocks) render_bwd_bul
     __syncwarp();
     const unsigned n4 = (unsigned)a.n_samples & ~3u;
 
-    ChunkCursor<true> P;
+    ChunkCursor<true, 2> P;
     P.todo = todo;
     P.ray(my_off, my_cnt, my_nch);
     const int pre = min(NST, total);
     for (int k = 0; k < pre; ++k) {
         if (lane == 0)
-            issue_window(stages + k * kBwdStage, &bars[k], chunk_window(P.lo, P.hi, P.c, n4), a.t_starts, a.t_ends,
-                         a.sigmas, a.optical_depth, a.rgbs, k == 0 ? a.stage_extra : 0u);
+            issue_window<kBwdSpan>(stages + k * kBwdStage, &bars[k], pair_window(P.lo, P.hi, P.c, n4), a.t_starts,
+                                   a.t_ends, a.sigmas, a.optical_depth, a.rgbs, k == 0 ? a.stage_extra : 0u);
         P.next(my_off, my_cnt, my_nch);
     }
 
-    ChunkCursor<true> C;
+    ChunkCursor<true, 2> C;
     C.todo = todo;
     C.ray(my_off, my_cnt, my_nch);
     // per-ray values (see render_bwd_kernel for the centred form)
@@ -1171,67 +1193,74 @@ __global__ void __launch_bounds__(kRenderThreads, kBulkMinBlocks) render_bwd_bul
             drain_stages<NST>(bars, k, total, a.stage_extra != 0u, a.d_status, lane);
             return;
         }
-        const unsigned c0 = (C.lo & ~1u) + ((unsigned)C.c << 6), wlo = c0 & ~3u;
-        const unsigned j0 = c0 + 2 * lane;
-        Pair q;
-        stage_pair(st, 4 * kSpan, wlo, n4, a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0, C.lo, C.hi, q);
-        float O0 = 0.0f, O1 = 0.0f;
-        {
-            const unsigned p = j0 - wlo;
-            if (q.v0) O0 = j0 < n4 ? st[3 * kSpan + p] : __ldg(a.optical_depth + j0);
-            if (q.v1) O1 = j0 + 1 < n4 ? st[3 * kSpan + p + 1] : __ldg(a.optical_depth + j0 + 1);
-        }
-        const float tau0 = q.v0 ? tau_of(q.s0[0], q.s1[0], q.sg[0]) : 0.0f;
-        const float tau1 = q.v1 ? tau_of(q.s0[1], q.s1[1], q.sg[1]) : 0.0f;
-        // the stage is read: refill it with the chunk NST ahead
-        __syncwarp();
-        if (k + NST < total) {
-            if (lane == 0) {
-                fence_proxy_async_smem();
-                issue_window(st, &bars[s], chunk_window(P.lo, P.hi, P.c, n4), a.t_starts, a.t_ends, a.sigmas,
-                             a.optical_depth, a.rgbs);
+        const unsigned abase = C.lo & ~1u;
+        const unsigned wlo = (abase + ((unsigned)(C.c > 0 ? C.c - 1 : 0) << 6)) & ~3u;
+        const int n_in = C.c > 0 ? 2 : 1;
+        for (int u = 0; u < n_in; ++u) {
+            const int c = C.c - u;
+            const unsigned j0 = abase + ((unsigned)c << 6) + 2 * lane;
+            Pair q;
+            stage_pair<kBwdSpan>(st, 4 * kBwdSpan, wlo, n4, a.t_starts, a.t_ends, a.sigmas, a.rgbs, j0, C.lo, C.hi,
+                                 q);
+            float O0 = 0.0f, O1 = 0.0f;
+            {
+                const unsigned p = j0 - wlo;
+                if (q.v0) O0 = j0 < n4 ? st[3 * kBwdSpan + p] : __ldg(a.optical_depth + j0);
+                if (q.v1) O1 = j0 + 1 < n4 ? st[3 * kBwdSpan + p + 1] : __ldg(a.optical_depth + j0 + 1);
             }
-            P.next(my_off, my_cnt, my_nch);
-        }
-        const float T0 = __expf(-O0);
-        const float T1 = __expf(-O1);
-        const float T2 = __expf(-__fadd_rn(O1, tau1));
-        const float Tn0 = q.v1 ? T1 : __expf(-__fadd_rn(O0, tau0));
-        if (C.c == C.nch - 1) t_end = __shfl_sync(FULL, last_odd ? T2 : Tn0, last_lane);
-        const float w0 = q.v0 ? T0 * alpha_of(tau0) : 0.0f;
-        const float w1 = q.v1 ? T1 * alpha_of(tau1) : 0.0f;
-        const float tm0 = (q.s0[0] + q.s1[0]) * 0.5f, tm1 = (q.s0[1] + q.s1[1]) * 0.5f;
-        const float b0 = gc0 * (q.rgb[0] - r_ref) + gc1 * (q.rgb[1] - g_ref) + gc2 * (q.rgb[2] - b_ref) +
-                         gd * (tm0 - tm_ref);
-        const float b1 = gc0 * (q.rgb[3] - r_ref) + gc1 * (q.rgb[4] - g_ref) + gc2 * (q.rgb[5] - b_ref) +
-                         gd * (tm1 - tm_ref);
-        const float bw0 = q.v0 ? b0 * w0 : 0.0f;
-        const float bw1 = q.v1 ? b1 * w1 : 0.0f;
-        const float suf = warp_incl_suffix(bw0 + bw1, lane);
-        float later = __shfl_down_sync(FULL, suf, 1);
-        if (lane == 31) later = 0.0f;
-        const float S1 = carry_s + later;
-        const float S0 = S1 + bw1;
-        carry_s = carry_s + __shfl_sync(FULL, suf, 0);
-        const float base_g = a_ref * t_end;
-        const float ds0 = (q.s1[0] - q.s0[0]) * (base_g + (b0 * Tn0 - S0));
-        const float ds1 = (q.s1[1] - q.s0[1]) * (base_g + (b1 * T2 - S1));
-        if (q.v0 && q.v1) {
-            *reinterpret_cast<float2*>(a.d_sigmas + j0) = make_float2(ds0, ds1);
-            float2* dr = reinterpret_cast<float2*>(a.d_rgbs + 3 * (size_t)j0);
-            dr[0] = make_float2(w0 * gc0, w0 * gc1);
-            dr[1] = make_float2(w0 * gc2, w1 * gc0);
-            dr[2] = make_float2(w1 * gc1, w1 * gc2);
-        } else if (q.v0) {
-            a.d_sigmas[j0] = ds0;
-            a.d_rgbs[3 * (size_t)j0] = w0 * gc0;
-            a.d_rgbs[3 * (size_t)j0 + 1] = w0 * gc1;
-            a.d_rgbs[3 * (size_t)j0 + 2] = w0 * gc2;
-        } else if (q.v1) {
-            a.d_sigmas[j0 + 1] = ds1;
-            a.d_rgbs[3 * (size_t)j0 + 3] = w1 * gc0;
-            a.d_rgbs[3 * (size_t)j0 + 4] = w1 * gc1;
-            a.d_rgbs[3 * (size_t)j0 + 5] = w1 * gc2;
+            const float tau0 = q.v0 ? tau_of(q.s0[0], q.s1[0], q.sg[0]) : 0.0f;
+            const float tau1 = q.v1 ? tau_of(q.s0[1], q.s1[1], q.sg[1]) : 0.0f;
+            if (u == n_in - 1) {  // the stage is read: refill it with the stage NST ahead
+                __syncwarp();
+                if (k + NST < total) {
+                    if (lane == 0) {
+                        fence_proxy_async_smem();
+                        issue_window<kBwdSpan>(st, &bars[s], pair_window(P.lo, P.hi, P.c, n4), a.t_starts, a.t_ends,
+                                               a.sigmas, a.optical_depth, a.rgbs);
+                    }
+                    P.next(my_off, my_cnt, my_nch);
+                }
+            }
+            const float T0 = __expf(-O0);
+            const float T1 = __expf(-O1);
+            const float T2 = __expf(-__fadd_rn(O1, tau1));
+            const float Tn0 = q.v1 ? T1 : __expf(-__fadd_rn(O0, tau0));
+            if (c == C.nch - 1) t_end = __shfl_sync(FULL, last_odd ? T2 : Tn0, last_lane);
+            const float w0 = q.v0 ? T0 * alpha_of(tau0) : 0.0f;
+            const float w1 = q.v1 ? T1 * alpha_of(tau1) : 0.0f;
+            const float tm0 = (q.s0[0] + q.s1[0]) * 0.5f, tm1 = (q.s0[1] + q.s1[1]) * 0.5f;
+            const float b0 = gc0 * (q.rgb[0] - r_ref) + gc1 * (q.rgb[1] - g_ref) + gc2 * (q.rgb[2] - b_ref) +
+                             gd * (tm0 - tm_ref);
+            const float b1 = gc0 * (q.rgb[3] - r_ref) + gc1 * (q.rgb[4] - g_ref) + gc2 * (q.rgb[5] - b_ref) +
+                             gd * (tm1 - tm_ref);
+            const float bw0 = q.v0 ? b0 * w0 : 0.0f;
+            const float bw1 = q.v1 ? b1 * w1 : 0.0f;
+            const float suf = warp_incl_suffix(bw0 + bw1, lane);
+            float later = __shfl_down_sync(FULL, suf, 1);
+            if (lane == 31) later = 0.0f;
+            const float S1 = carry_s + later;
+            const float S0 = S1 + bw1;
+            carry_s = carry_s + __shfl_sync(FULL, suf, 0);
+            const float base_g = a_ref * t_end;
+            const float ds0 = (q.s1[0] - q.s0[0]) * (base_g + (b0 * Tn0 - S0));
+            const float ds1 = (q.s1[1] - q.s0[1]) * (base_g + (b1 * T2 - S1));
+            if (q.v0 && q.v1) {
+                *reinterpret_cast<float2*>(a.d_sigmas + j0) = make_float2(ds0, ds1);
+                float2* dr = reinterpret_cast<float2*>(a.d_rgbs + 3 * (size_t)j0);
+                dr[0] = make_float2(w0 * gc0, w0 * gc1);
+                dr[1] = make_float2(w0 * gc2, w1 * gc0);
+                dr[2] = make_float2(w1 * gc1, w1 * gc2);
+            } else if (q.v0) {
+                a.d_sigmas[j0] = ds0;
+                a.d_rgbs[3 * (size_t)j0] = w0 * gc0;
+                a.d_rgbs[3 * (size_t)j0 + 1] = w0 * gc1;
+                a.d_rgbs[3 * (size_t)j0 + 2] = w0 * gc2;
+            } else if (q.v1) {
+                a.d_sigmas[j0 + 1] = ds1;
+                a.d_rgbs[3 * (size_t)j0 + 3] = w1 * gc0;
+                a.d_rgbs[3 * (size_t)j0 + 4] = w1 * gc1;
+                a.d_rgbs[3 * (size_t)j0 + 5] = w1 * gc2;
+            }
         }
         if (C.next(my_off, my_cnt, my_nch) && k + 1 < total) begin_ray();
     }
@@ -1452,11 +1481,13 @@ int group_blocks(int n_rays) {
 // per kernel, so that the stages of several blocks fit on an SM).
 template <typename K, typename A>
 int launch_bulk(K kernel, bool& carveout_set, int nst, bool bwd, int n_rays, cudaStream_t st, const A& a) {
+    const size_t smem = bulk_smem_bytes(nst, bwd);
     if (!carveout_set) {
         cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         carveout_set = true;
     }
-    kernel<<<group_blocks(n_rays), kRenderThreads, bulk_smem_bytes(nst, bwd), st>>>(a);
+    kernel<<<group_blocks(n_rays), kRenderThreads, smem, st>>>(a);
     return launch_status(cudaGetLastError());
 }
 
