@@ -23,8 +23,9 @@
 //     Every ray that starts inside the outermost box starts at near_plane, so a
 //     one-thread prologue writes that shared lattice once per call into the
 //     workspace and the warps read t_k from it, lane-parallel, exactly as for
-//     uniform steps. A ray with another start has lane 0 extend its own
-//     recurrence 32 steps at a time into the warp's shared memory.
+//     uniform steps (each block first copies it into shared memory when it
+//     fits). A ray with another start has lane 0 extend its own recurrence 32
+//     steps at a time into the warp's shared memory.
 //   * The tile's total becomes its global offset through a bounded decoupled
 //     look-back run by the warp itself; the warp then re-expands the ballot
 //     words into compacted, coalesced stores of (t_start, t_end, ray).
@@ -32,6 +33,30 @@
 
 namespace nacc {
 namespace {
+
+// The shared cone lattice t_0 .. t_max_steps as the block reads it: its copy in
+// the block's shared memory when it fits (kConeSmemMax entries), else the table in
+// global memory. Set by the kernel before any walk (cone steps only).
+constexpr int kConeSmemMax = 8193;
+__shared__ const float* s_cone;
+
+__device__ __forceinline__ float cone_t(const MarchArgs& a, int k) { return s_cone[min(k, a.max_steps)]; }
+
+// table_count (march_common.cuh) on the block's copy (plain loads: it may be
+// shared memory).
+__device__ __forceinline__ int cone_count(float far, int max_steps, int lane) {
+    int lo = 0, hi = max_steps;
+    while (lo < hi) {
+        const int step = (hi - lo + 31) >> 5;
+        const int k = lo + lane * step;
+        const unsigned below = __ballot_sync(FULL, k < hi && s_cone[k] < far);
+        const int nb = __popc(below);
+        if (nb == 0) break;
+        hi = min(lo + nb * step, hi);
+        lo = lo + (nb - 1) * step + 1;
+    }
+    return lo;
+}
 
 // ---------------------------------------------------------------------------
 // lattice walk: the warp evaluates 32 lattice points of one ray at a time
@@ -150,8 +175,8 @@ __device__ __forceinline__ int walk_box(const MarchArgs& a, const G& g, const fl
             ts = __fadd_rn(near, __fmul_rn(kf, dt));
             tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
         } else {
-            ts = __ldg(a.cone_table + min(kp, a.max_steps));
-            tn = __ldg(a.cone_table + min(kp + 1, a.max_steps));
+            ts = cone_t(a, kp);
+            tn = cone_t(a, kp + 1);
         }
         const float te = tn < far ? tn : far;
         const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
@@ -182,8 +207,8 @@ __device__ __forceinline__ int walk_box(const MarchArgs& a, const G& g, const fl
                 ks = __fadd_rn(near, __fmul_rn(kf, dt));
                 kn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
             } else {
-                ks = __ldg(a.cone_table + min(k, a.max_steps));
-                kn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                ks = cone_t(a, k);
+                kn = cone_t(a, k + 1);
             }
             bool occ = false;
             if (k < nk) {
@@ -230,8 +255,8 @@ __device__ __forceinline__ int walk_box_levels(const MarchArgs& a, const G& g, c
             ts = __fadd_rn(near, __fmul_rn(kf, dt));
             tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
         } else {
-            ts = __ldg(a.cone_table + min(kp, a.max_steps));
-            tn = __ldg(a.cone_table + min(kp + 1, a.max_steps));
+            ts = cone_t(a, kp);
+            tn = cone_t(a, kp + 1);
         }
         const float te = tn < far ? tn : far;
         const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
@@ -290,8 +315,8 @@ __device__ __forceinline__ int walk_box_levels(const MarchArgs& a, const G& g, c
                 ks = __fadd_rn(near, __fmul_rn(kf, dt));
                 kn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
             } else {
-                ks = __ldg(a.cone_table + min(k, a.max_steps));
-                kn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                ks = cone_t(a, k);
+                kn = cone_t(a, k + 1);
             }
             bool occ = false;
             if (k < nk) {
@@ -321,7 +346,7 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, con
     const bool shared = !CONE || near == a.near_plane;
     // shared lattices know their length; an own cone lattice ends when t_k >= far
     int nk = !CONE ? lattice_count(a, near, far, dt)
-                   : (shared ? table_count(a.cone_table, a.max_steps, far, lane) : a.max_steps);
+                   : (shared ? cone_count(far, a.max_steps, lane) : a.max_steps);
     if (CONE && shared && nk > 32 * a.mask_words) {  // the host's bound on cone lattices was passed
         if (lane == 0) raise_status(a.d_status, NACC_STATUS_OVERFLOW);
         nk = 32 * a.mask_words;
@@ -363,8 +388,8 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, con
                 ts = __fadd_rn(near, __fmul_rn(kf, dt));
                 tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
             } else {
-                ts = __ldg(a.cone_table + min(kp, a.max_steps));
-                tn = __ldg(a.cone_table + min(kp + 1, a.max_steps));
+                ts = cone_t(a, kp);
+                tn = cone_t(a, kp + 1);
             }
             const float te = tn < far ? tn : far;
             const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
@@ -407,8 +432,8 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, con
                     ks = __fadd_rn(near, __fmul_rn(kf, dt));
                     kn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
                 } else {
-                    ks = __ldg(a.cone_table + min(k, a.max_steps));
-                    kn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                    ks = cone_t(a, k);
+                    kn = cone_t(a, k + 1);
                 }
                 bool occ = false;
                 if (k < nk && ks < far) {
@@ -496,8 +521,8 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, con
                     ts = __fadd_rn(near, __fmul_rn(kf, dt));
                     tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
                 } else {
-                    ts = __ldg(a.cone_table + min(k, a.max_steps));
-                    tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                    ts = cone_t(a, k);
+                    tn = cone_t(a, k + 1);
                 }
                 const float te = tn < far ? tn : far;
                 const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
@@ -516,8 +541,8 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, con
                 ts = __fadd_rn(near, __fmul_rn(kf, dt));
                 tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
             } else {
-                ts = __ldg(a.cone_table + min(k, a.max_steps));
-                tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                ts = cone_t(a, k);
+                tn = cone_t(a, k + 1);
             }
             bool occ = false;
             if (k < nk && ts < far) {
@@ -545,8 +570,8 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, con
                 ts = __fadd_rn(near, __fmul_rn(kf, dt));
                 tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
             } else if (shared) {
-                ts = __ldg(a.cone_table + min(k, a.max_steps));
-                tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                ts = cone_t(a, k);
+                tn = cone_t(a, k + 1);
             } else {
                 cone_extend(a, lat, tcur, lane);
                 ts = lat[lane];
@@ -784,7 +809,7 @@ __device__ __forceinline__ void finish_tile(const MarchArgs& a, const uint32_t* 
                                 if (!CONE) {
                                     t[j] = __fadd_rn(near, __fmul_rn(__int2float_rn(k + j), dt));
                                 } else {
-                                    t[j] = __ldg(a.cone_table + min(k + j, a.max_steps));
+                                    t[j] = cone_t(a, k + j);
                                 }
                             }
                             const float4 ts4 = make_float4(t[0], t[1], t[2], t[3]);
@@ -822,8 +847,8 @@ __device__ __forceinline__ void finish_tile(const MarchArgs& a, const uint32_t* 
                                 ts = __fadd_rn(near, __fmul_rn(kf, dt));
                                 tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
                             } else {
-                                ts = __ldg(a.cone_table + min(k, a.max_steps));
-                                tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                                ts = cone_t(a, k);
+                                tn = cone_t(a, k + 1);
                             }
                             if (fits || pos < cap) {
                                 a.t_starts[pos] = ts;
@@ -842,8 +867,8 @@ __device__ __forceinline__ void finish_tile(const MarchArgs& a, const uint32_t* 
                             ts = __fadd_rn(near, __fmul_rn(kf, dt));
                             tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
                         } else {
-                            ts = __ldg(a.cone_table + min(k, a.max_steps));
-                            tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                            ts = cone_t(a, k);
+                            tn = cone_t(a, k + 1);
                         }
                         const unsigned pos = base + __popc(m & lt);
                         if (((m >> lane) & 1u) && (fits || pos < cap)) {
@@ -879,8 +904,8 @@ __device__ __forceinline__ void finish_tile(const MarchArgs& a, const uint32_t* 
                         ts = __fadd_rn(near, __fmul_rn(kf, dt));
                         tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
                     } else {
-                        ts = __ldg(a.cone_table + min(k, a.max_steps));
-                        tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                        ts = cone_t(a, k);
+                        tn = cone_t(a, k + 1);
                     }
                     const float te = tn < far ? tn : far;
                     if (m == ~0u) {
@@ -915,8 +940,8 @@ __device__ __forceinline__ void finish_tile(const MarchArgs& a, const uint32_t* 
                 ts = __fadd_rn(near, __fmul_rn(kf, dt));
                 tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
             } else if (shared) {
-                ts = __ldg(a.cone_table + min(k, a.max_steps));
-                tn = __ldg(a.cone_table + min(k + 1, a.max_steps));
+                ts = cone_t(a, k);
+                tn = cone_t(a, k + 1);
             } else {
                 cone_extend(a, lat, tcur, lane);
                 ts = lat[lane];
@@ -980,6 +1005,16 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
     if (!BATCHED && a.bricks) {
         s_bricks = reinterpret_cast<uint16_t*>(s_masks + (size_t)kWarps * 2 * tile_words);
         for (int k = threadIdx.x; k < a.brick_entries; k += kThreads) s_bricks[k] = __ldg(a.bricks + k);
+        __syncthreads();
+    }
+    if constexpr (CONE) {
+        if (a.cone_smem_at >= 0) {
+            float* tab = reinterpret_cast<float*>(s_masks) + a.cone_smem_at;
+            for (int k = threadIdx.x; k <= a.max_steps; k += kThreads) tab[k] = __ldg(a.cone_table + k);
+            if (threadIdx.x == 0) s_cone = tab;
+        } else if (threadIdx.x == 0) {
+            s_cone = a.cone_table;
+        }
         __syncthreads();
     }
     uint32_t* wbase = s_masks + (size_t)warp * 2 * tile_words;
@@ -1078,7 +1113,9 @@ __global__ void __launch_bounds__(kThreads, MINB) march_uniform_kernel(const Mar
 
 template <typename K>
 void launch_uniform(K kernel, size_t smem, int need, cudaStream_t st, const MarchArgs& a) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // without the opt-in, static and dynamic shared memory together are limited to
+    // 48 KB; the kernels' static part is below 8 KB
+    if (smem > 40 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int blocks = blocks_for(kernel, smem, need);
     kernel<<<blocks, kThreads, smem, st>>>(a);
 }
@@ -1232,6 +1269,13 @@ int march_launch(MarchArgs& a, const nacc_march_params* p, int32_t* packed_info,
             a.brick_per_grid = (int32_t)L.per_grid;
             smem += align_up(entries * sizeof(uint16_t), 16);
         }
+    }
+    // cone steps: each block keeps the shared lattice in shared memory when it fits
+    a.cone_smem_at = -1;
+    if (cone && a.max_steps + 1 <= kConeSmemMax) {
+        smem = align_up(smem, 16);
+        a.cone_smem_at = (int32_t)(smem / sizeof(float));
+        smem += align_up((size_t)(a.max_steps + 1) * sizeof(float), 16);
     }
     const int need = (a.n_tiles + kWarps - 1) / kWarps;
     if (batched) {

@@ -69,6 +69,7 @@ struct MarchArgs {
     int32_t row_stride;       // words between consecutive rows in shared memory (= mask_words)
     int32_t tile_rays;
     const float* cone_table;  // t_0 = near_plane, t_1, ..., t_max_steps (cone steps only)
+    int32_t cone_smem_at;     // float offset of the table's copy in dynamic shared memory, or -1
     int32_t contract;         // contracted unbounded space (one level, no box clip)
     float cc[3], inv_h[3];    // contraction: box centre and 1 / half size
     float qres[3];            // contraction: res / 4 (the grid spans [-2, 2])

@@ -1484,7 +1484,8 @@ int launch_bulk(K kernel, bool& carveout_set, int nst, bool bwd, int n_rays, cud
     const size_t smem = bulk_smem_bytes(nst, bwd);
     if (!carveout_set) {
         cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // static and dynamic shared memory together are limited to 48 KB without the opt-in
+        if (smem > 40 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         carveout_set = true;
     }
     kernel<<<group_blocks(n_rays), kRenderThreads, smem, st>>>(a);

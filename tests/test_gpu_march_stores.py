@@ -101,3 +101,21 @@ def test_capacity_cuts_a_run_at_every_residue(cases, shift):
         assert np.array_equal(_bits(te[:cap]), _bits(ora.t_ends[:cap]))
         assert np.array_equal(ri[:cap], ora.ray_indices[:cap])
         assert np.all(np.isnan(ts[cap:])) and np.all(np.isnan(te[cap:])) and np.all(ri[cap:] == -1)
+
+
+@pytest.mark.parametrize("tile_rays", [1, 2, 4, 8, 16, 32])
+def test_cone_cascade_every_tile_size(cases, tile_rays):
+    """Cone steps keep the shared lattice in each block's shared memory next to the
+    tile rows and the brick summary: every tile size (the largest need more than
+    the default 48 KB of shared memory per block) marches bit-exactly."""
+    w, ora = cases["cascade_cone"]
+    old = _lib.tune_get("march_tile_rays")
+    try:
+        _lib.tune_set("march_tile_rays", tile_rays)
+        for use_sat in (False, True):
+            pi, ts, te, ri, n, st = _march(w, ora.n_samples, 0, use_sat)
+            assert st == 0 and n == ora.n_samples
+            assert np.array_equal(pi, ora.packed_info)
+            assert np.array_equal(_bits(ts[:n]), _bits(ora.t_starts)) and np.array_equal(ri[:n], ora.ray_indices)
+    finally:
+        _lib.tune_set("march_tile_rays", old)
