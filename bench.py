@@ -61,7 +61,8 @@ LIMITER = {
     "prune": "latency of the chunk loads (long-scoreboard stalls); DRAM reads 1.46x the algorithmic reads, because "
              "the store phase re-reads the kept samples after the next tile's decisions",
     "render_fwd": "DRAM latency / issue",
-    "render_bwd": "issue (76% issue-active; chunks staged by bulk copies, long-scoreboard stalls 1 per issue)",
+    "render_bwd": "issue (71% issue-active; two chunks of a ray staged per bulk copy, long-scoreboard stalls 1.3 per "
+                  "issue, 64% DRAM)",
     "grid_update": "latency of 2^21 random atomics",
     "render_fused": "DRAM latency of the forward's chunk loads; the backward re-reads the ray from L2",
 }
