@@ -46,8 +46,8 @@ POOL = 4  # distinct ray batches cycled through the steps (L2 is flushed between
 # from one ncu capture, keyed by the SHA-256 of the kernel's source file. A
 # source change invalidates the figure (reported as null until re-captured).
 NCU_TRAFFIC = {
-    # profiles/march_dram_bounded-2^18.md: 21322240 B read + 1476599040 B written (box walk, vector stores)
-    ("march", "5375087dc02a78305a0f1403806470e8f69f56a4245bfbfadb2d1f1785904618"): 1497921280,
+    # profiles/march_dram_bounded-2^18.md: 21084672 B read + 1477180672 B written (box walk, vector stores)
+    ("march", "eed1ba37db8b8172a1101685b104bbeebc9bb459554d6e42adeca6aeda033a83"): 1498265344,
     # profiles/prune_dram_bounded-2^18.md: 1320007680 B read + 348302336 B written
     ("prune", "072ed911e1ae6636de3d862a79ce81821140af2ef8ebe323831c1cd5ab57879c"): 1668310016,
     # profiles/march_fused_inference-800x800.md: 22215168 B read + 1169534464 B written (camera 0's image)
