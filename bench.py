@@ -57,7 +57,7 @@ NCU_TRAFFIC = {
 # What limits each stage (from the ncu captures summarised under profiles/).
 LIMITER = {
     "march": "issue (68% issue-active with 30 warps per SM, register-limited) plus the L1-to-L2 requests of the "
-             "stores and the table reads the brick summary leaves (59% busy), at 46% DRAM",
+             "stores and the table reads the brick summary leaves (54% busy), at 54% DRAM",
     "prune": "latency of the chunk loads (long-scoreboard stalls); DRAM reads 1.46x the algorithmic reads, because "
              "the store phase re-reads the kept samples after the next tile's decisions",
     "render_fwd": "DRAM latency / issue",
