@@ -596,6 +596,11 @@ def measure(args, workload, ray_scale=1.0, fused=False):
     avg = {s: sum(v) / len(v) for s, v in stage_ms.items()}
     dom = max(stages, key=lambda s: avg[s])
     achieved = sb[dom] / (avg[dom] / 1e3) / 1e9
+    # the same stage's bytes by the per-stage formula that counts every marched
+    # sample as read by pruning (12M instead of 12 M_read); the other stages' bytes
+    # are the same either way
+    sb_formula = stage_bytes(R, M_avg, M_avg, S_avg, grid_bytes, sc.n_cells, sc.n_grid, hp.save_optical_depth)
+    achieved_formula = sb_formula[dom] / (avg[dom] / 1e3) / 1e9
     traffic = NCU_TRAFFIC.get((dom, kernel_source_sha(dom))) if workload == "bounded" and R == N_RAYS else None
     step_bytes = sum(sb[s] for s in stages)
     # the path's bytes by the per-step formula with every marched sample read once by
@@ -659,7 +664,12 @@ def measure(args, workload, ray_scale=1.0, fused=False):
                              "frac": round(formula_bytes / (mean_ms / 1e3) / 1e9 / peak, 4)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
-                     "algorithmic_bytes": int(sb[dom]), "limiter": LIMITER[dom]},
+                     "algorithmic_bytes": int(sb[dom]), "limiter": LIMITER[dom],
+                     "formula": {"algorithmic_bytes": int(sb_formula[dom]), "achieved": round(achieved_formula, 1),
+                                 "frac": round(achieved_formula / peak, 4),
+                                 "bytes": "pruning counted as reading every marched sample (16R + 12M + 12S); "
+                                          "the figures above count the samples it reads up to each ray's "
+                                          "termination (16R + 12 M_read + 12S)"}},
         "wall_s_timed_loop_incl_field": round(t_wall, 3),
         "gpu_launches": launches_per_step(w, sc.n_cells, sc.n_grid, hp.ema.data_ptr(), hp.use_sat, fused) * args.steps,
         "clocks": clk,
