@@ -143,27 +143,20 @@ def test_cone_cascade_mixed_starts(orc):
     assert_march_equal(g, oracle_march(orc, w))
 
 
-@pytest.mark.parametrize("use_sat", [False, True])
 @pytest.mark.parametrize("max_steps", [8192, 8193])
-def test_cone_lattice_at_the_shared_memory_limit(orc, max_steps, use_sat):
+def test_cone_lattice_at_the_shared_memory_limit(orc, max_steps):
     """Each block keeps the shared cone lattice t_0 .. t_max_steps in shared memory
     up to 8193 entries and reads it from the workspace above that. Both sides of
-    the limit, point by point and by the box walk over levels, with rays inside the
-    box that march to the last entries, are bit-exact."""
-    import gpu_util
-
+    the limit (in every walk mode of the module's fixture, the box walk over levels
+    included), with rays inside the box that march to the last entries, are
+    bit-exact."""
     n = 600
     o, d = _random_rays(16, n, spread=9.0, box=3.0)
     o[:300] = synth.rand_uniform(16, 7, 900, -0.9, 0.9).reshape(300, 3)
     occ = synth.rand_uniform(16, 5, 3 * 32 ** 3) < 0.9
     w = _workload(o, d, occ, (32, 32, 32), (-1, -1, -1, 1, 1, 1), n_levels=3, near=0.0, far=100.0, dt_min=1e-4,
                   dt_max=0.2, cone=1.0 / 4096, max_steps=max_steps)
-    old = gpu_util.USE_SAT
-    try:
-        gpu_util.USE_SAT = use_sat
-        g = gpu_march(w)
-    finally:
-        gpu_util.USE_SAT = old
+    g = gpu_march(w)
     ora = oracle_march(orc, w)
     # rays from inside the box take the shared lattice up to its last entry
     assert int(np.max(ora.packed_info[:300, 1])) == max_steps
