@@ -42,6 +42,14 @@ __shared__ const float* s_cone;
 
 __device__ __forceinline__ float cone_t(const MarchArgs& a, int k) { return s_cone[min(k, a.max_steps)]; }
 
+// The contracted walk reads the global table through the read-only path (its
+// blocks keep no copy: that measured slower there).
+template <bool GLOBAL>
+__device__ __forceinline__ float lattice_t(const MarchArgs& a, int k) {
+    if constexpr (GLOBAL) return __ldg(a.cone_table + min(k, a.max_steps));
+    else return cone_t(a, k);
+}
+
 // table_count (march_common.cuh) on the block's copy (plain loads: it may be
 // shared memory).
 __device__ __forceinline__ int cone_count(float far, int max_steps, int lane) {
@@ -346,7 +354,7 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, con
     const bool shared = !CONE || near == a.near_plane;
     // shared lattices know their length; an own cone lattice ends when t_k >= far
     int nk = !CONE ? lattice_count(a, near, far, dt)
-                   : (shared ? cone_count(far, a.max_steps, lane) : a.max_steps);
+                   : (shared ? (MAXL == 0 ? table_count(a.cone_table, a.max_steps, far, lane) : cone_count(far, a.max_steps, lane)) : a.max_steps);
     if (CONE && shared && nk > 32 * a.mask_words) {  // the host's bound on cone lattices was passed
         if (lane == 0) raise_status(a.d_status, NACC_STATUS_OVERFLOW);
         nk = 32 * a.mask_words;
@@ -388,8 +396,8 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, con
                 ts = __fadd_rn(near, __fmul_rn(kf, dt));
                 tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
             } else {
-                ts = cone_t(a, kp);
-                tn = cone_t(a, kp + 1);
+                ts = lattice_t<MAXL == 0>(a, kp);
+                tn = lattice_t<MAXL == 0>(a, kp + 1);
             }
             const float te = tn < far ? tn : far;
             const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
@@ -432,8 +440,8 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, con
                     ks = __fadd_rn(near, __fmul_rn(kf, dt));
                     kn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
                 } else {
-                    ks = cone_t(a, k);
-                    kn = cone_t(a, k + 1);
+                    ks = lattice_t<MAXL == 0>(a, k);
+                    kn = lattice_t<MAXL == 0>(a, k + 1);
                 }
                 bool occ = false;
                 if (k < nk && ks < far) {
@@ -521,8 +529,8 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, con
                     ts = __fadd_rn(near, __fmul_rn(kf, dt));
                     tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
                 } else {
-                    ts = cone_t(a, k);
-                    tn = cone_t(a, k + 1);
+                    ts = lattice_t<MAXL == 0>(a, k);
+                    tn = lattice_t<MAXL == 0>(a, k + 1);
                 }
                 const float te = tn < far ? tn : far;
                 const float mid = __fmul_rn(__fadd_rn(ts, te), 0.5f);
@@ -541,8 +549,8 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, con
                 ts = __fadd_rn(near, __fmul_rn(kf, dt));
                 tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
             } else {
-                ts = cone_t(a, k);
-                tn = cone_t(a, k + 1);
+                ts = lattice_t<MAXL == 0>(a, k);
+                tn = lattice_t<MAXL == 0>(a, k + 1);
             }
             bool occ = false;
             if (k < nk && ts < far) {
@@ -570,8 +578,8 @@ __device__ __forceinline__ void walk_lattice(const MarchArgs& a, const G& g, con
                 ts = __fadd_rn(near, __fmul_rn(kf, dt));
                 tn = __fadd_rn(near, __fmul_rn(__fadd_rn(kf, 1.0f), dt));
             } else if (shared) {
-                ts = cone_t(a, k);
-                tn = cone_t(a, k + 1);
+                ts = lattice_t<MAXL == 0>(a, k);
+                tn = lattice_t<MAXL == 0>(a, k + 1);
             } else {
                 cone_extend(a, lat, tcur, lane);
                 ts = lat[lane];
@@ -1270,9 +1278,10 @@ int march_launch(MarchArgs& a, const nacc_march_params* p, int32_t* packed_info,
             smem += align_up(entries * sizeof(uint16_t), 16);
         }
     }
-    // cone steps: each block keeps the shared lattice in shared memory when it fits
+    // cone steps over uncontracted grids: each block keeps the shared lattice in
+    // shared memory when it fits
     a.cone_smem_at = -1;
-    if (cone && a.max_steps + 1 <= kConeSmemMax) {
+    if (cone && !a.contract && a.max_steps + 1 <= kConeSmemMax) {
         smem = align_up(smem, 16);
         a.cone_smem_at = (int32_t)(smem / sizeof(float));
         smem += align_up((size_t)(a.max_steps + 1) * sizeof(float), 16);
